@@ -1,0 +1,467 @@
+/*
+ * GEMPE CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 restatement of one GEMPE epoch
+ * (Boehm & Plant, "Massively Parallel Graph Drawing and Representation
+ * Learning", arXiv 2011.03479).  Only the tests, the package's smoke check
+ * and the benchmark's CPU-baseline leg load this file; the CUDA engine never
+ * calls it, includes it or shares a line of code with it.
+ *
+ * What each function follows:
+ *   orc_h_basic            Eq. 1 (basic entropy of the adjacency matrix)
+ *   orc_dl                 Sec. II.B: description lengths dl+ / dl- of the
+ *                          sigmoid s+ = 1/2 - 1/2 erf((delta-mu)/(sqrt2 sigma))
+ *   orc_parabola           Eq. 4 (w) and Eq. 5 (d) for edges, and the same
+ *                          formulas with the marked "-" signs turned into "+"
+ *                          for non-edges (Sec. II.C)
+ *   orc_epoch              one iteration of Fig. 4: zero y,z; edge parabolas;
+ *                          sampled non-edges (Fig. 2 semantics, Sec. III.C);
+ *                          Eq. 3 numerators/denominators; x_i := y_i / z_i;
+ *                          distance histograms (Sec. III.F)
+ *   orc_sigma_fit          Sec. III.F: bisection for dPE/dsigma = 0 on the
+ *                          edge / non-edge distance histograms, mu fixed
+ *   orc_loss_exact         Eq. 2 at a given sigma, all n(n-1)/2 pairs
+ *   orc_loss_sampled       Eq. 2 estimated from all edges plus sampled
+ *                          non-edges weighted to the non-edge count
+ *   orc_edge_terms_*       the edge part of Eq. 3 in the paper's edge-list
+ *                          form (Fig. 4) and in the per-vertex CSR form
+ *   orc_surrogate_L        sum of dl over a frozen pair list (for the
+ *                          gradient identity of Eq. 3)
+ *
+ * Choices where the paper is silent (the "readings"):
+ *   - negative samples are drawn per vertex, k per vertex per epoch, with a
+ *     Philox4x32-10 counter stream; a draw g is rejected when g == i or
+ *     (i,g) is an edge, and redrawn at most max_retries times (Fig. 2 loops
+ *     without bound);
+ *   - membership is exact (binary search in the sorted CSR row) instead of
+ *     the lossy byte-map hash of Sec. III.C;
+ *   - w_formula 0 ("derived"): the first term of Eq. 4 uses 1/(pi ln2), the
+ *     factor that matching the second derivative actually gives; w_formula 1
+ *     ("printed") keeps the 2/(pi ln2) printed in Eq. 4.  Eq. 5 is used as
+ *     printed in both cases;
+ *   - clamp_neg_d: d := max(d, 0);
+ *   - x_i is left unchanged when z_i < z_min;
+ *   - non-edge histogram weight of a sample anchored at i is
+ *     (n-1-deg_i) / (2 * accepted_i); edges are binned once (j > i) with
+ *     weight 1; bin = min(floor(delta / (hist_max/B)), B-1), value = centre;
+ *   - sigma bisection runs in log sigma on [1e-3, 1e3]; without a sign change
+ *     the bracket end with the lower entropy is taken.
+ *
+ * Counter-based random numbers (Philox4x32-10, Salmon, Moraes, Dror & Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC 2011), key =
+ * (seed_lo, seed_hi); counter words:
+ *   initial positions  (i, q, 0, 0x0A000000)         -> coordinates 4q..4q+3
+ *   epoch samples      (i, epoch, t, 0x0B000000|a>>2) -> word a&3 (attempt a)
+ *   loss samples       (i, epoch, t, 0x0E000000|a>>2) -> word a&3
+ * A 32-bit word r maps to vertex floor(r * n / 2^32).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_LN2 0.69314718055994530942
+#define ORC_PI 3.14159265358979323846
+#define ORC_SQRT2 1.41421356237309504880
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                       */
+/* ------------------------------------------------------------------ */
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c[4] = { ctr[0], ctr[1], ctr[2], ctr[3] };
+    uint32_t k[2] = { key[0], key[1] };
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c, k);
+        k[0] += 0x9E3779B9u;   /* Weyl sequence increments */
+        k[1] += 0xBB67AE85u;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+static uint32_t draw_vertex(uint32_t r, uint32_t n) { return (uint32_t)(((uint64_t)r * n) >> 32); }
+
+static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int word) {
+    uint32_t ctr[4] = { c0, c1, c2, c3 };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* Initial positions (Fig. 4: uniform random), U[-R, R) in FP32. */
+void orc_init_positions(int32_t n, int32_t d, uint64_t seed, float range, float* x) {
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t c = 0; c < d; ++c) {
+            uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)(c / 4), 0u, 0x0A000000u, c % 4);
+            double unit = (double)(r >> 8) * (1.0 / 8388608.0) - 1.0;   /* exact in [-1,1) */
+            x[(int64_t)i * d + c] = (float)(unit * (double)range);       /* one rounding */
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Graph membership: binary search in the sorted CSR row               */
+/* ------------------------------------------------------------------ */
+int orc_is_edge(const int32_t* row_ptr, const int32_t* col_idx, int32_t i, int32_t j) {
+    int32_t lo = row_ptr[i], hi = row_ptr[i + 1];
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (col_idx[mid] == j) return 1;
+        if (col_idx[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 1 and Sec. II.B                                                  */
+/* ------------------------------------------------------------------ */
+double orc_h_basic(double n, double m) {
+    double N = 0.5 * n * (n - 1.0);
+    double p = m / N, q = (N - m) / N;
+    double h = 0.0;
+    if (p > 0.0) h -= p * log2(p);
+    if (q > 0.0) h -= q * log2(q);
+    return h;
+}
+
+/* Laplace's continued fraction for the Mills ratio: with
+ * Q(u)/phi(u) = 1/(u + 1/(u + 2/(u + 3/(u + ...)))), the tail ratio
+ * phi(u)/Q(u) equals u + T(u), T(u) = 1/(u + 2/(u + 3/(u + ...))).
+ * Used only for u >= 25 where erfc underflows in double precision. */
+static double mills_tail_T(double u) {
+    double t = u;
+    for (int k = 80; k >= 2; --k) t = u + (double)k / t;
+    return 1.0 / t;
+}
+
+/* phi(u) / Q(u) with Q the upper normal tail, Q(u) = 1/2 erfc(u/sqrt2). */
+static double inv_mills(double u) {
+    if (u >= 25.0) return u + mills_tail_T(u);
+    double phi = exp(-0.5 * u * u) / sqrt(2.0 * ORC_PI);
+    return phi / (0.5 * erfc(u / ORC_SQRT2));
+}
+
+/* -log2 Q(u) */
+static double neg_log2_Q(double u) {
+    if (u >= 25.0) {
+        /* Q = phi(u) / (u + T(u)) */
+        double lnq = -0.5 * u * u - 0.5 * log(2.0 * ORC_PI) - log(u + mills_tail_T(u));
+        return -lnq / ORC_LN2;
+    }
+    if (u < 0.0)      /* Q(u) = 1 - Q(-u) close to 1: keep the digits of Q(-u) */
+        return -log1p(-0.5 * erfc(-u / ORC_SQRT2)) / ORC_LN2;
+    return -log2(0.5 * erfc(u / ORC_SQRT2));
+}
+
+/* dl+ (is_edge = 1) or dl- (is_edge = 0) of distance delta. */
+double orc_dl(double delta, double mu, double sigma, int is_edge) {
+    double u = (delta - mu) / sigma;
+    /* s+ = 1/2 - 1/2 erf(u/sqrt2) = Q(u);  s- = 1/2 + 1/2 erf(u/sqrt2) = Q(-u) */
+    return is_edge ? neg_log2_Q(u) : neg_log2_Q(-u);
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 4 / Eq. 5: the parabola w (delta - d)^2 of one pair              */
+/* ------------------------------------------------------------------ */
+void orc_parabola(double delta, double mu, double sigma, int is_edge, int w_formula, int clamp_neg_d,
+                  double* d_out, double* w_out) {
+    const double c1 = (w_formula == 1) ? 2.0 : 1.0;       /* first-term factor of Eq. 4 */
+    const double u = (delta - mu) / sigma;
+    const double sgn = is_edge ? -1.0 : 1.0;              /* the red operators of Eq. 4/5 */
+    double w, d;
+    if ((is_edge && u < 25.0) || (!is_edge && u > -25.0)) {
+        /* Eq. 4 / 5 as printed, with 1 -/+ erf(x) evaluated as erfc(+/-x) */
+        const double e = exp(-(delta - mu) * (delta - mu) / (2.0 * sigma * sigma));
+        const double D = is_edge ? erfc(u / ORC_SQRT2) : erfc(-u / ORC_SQRT2);
+        const double a = c1 / (ORC_PI * ORC_LN2);
+        const double b = 1.0 / (sqrt(2.0 * ORC_PI) * ORC_LN2);
+        w = a * e * e / (sigma * sigma * D * D) + sgn * b * (delta - mu) * e / (sigma * sigma * sigma * D);
+        d = delta + sgn * b * e / (w * sigma * D);
+    } else {
+        /* far tail (erfc underflows): same quantities through the Mills
+         * ratio, h = phi(v)/Q(v), v = u for edges and -u for non-edges. */
+        const double v = is_edge ? u : -u;
+        const double h = v + mills_tail_T(v);
+        /* in Eq. 4 the first term equals c1 h^2 / (2 ln2 sigma^2) and the
+         * second v h / (2 ln2 sigma^2) with the operator sign folded into v */
+        w = (c1 * h * h - v * h) / (2.0 * ORC_LN2 * sigma * sigma);
+        d = delta + sgn * h / (2.0 * ORC_LN2 * sigma * w);
+    }
+    if (clamp_neg_d && d < 0.0) d = 0.0;
+    *d_out = d;
+    *w_out = w;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 3 contribution of one pair to vertex a (partner b)               */
+/* ------------------------------------------------------------------ */
+static double dist(const double* x, int32_t d, int64_t a, int64_t b) {
+    double s = 0.0;
+    for (int32_t c = 0; c < d; ++c) {
+        double t = x[a * d + c] - x[b * d + c];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+static void add_wm_term(double* y, double* z, const double* x, int32_t d, int64_t a, int64_t b,
+                        double delta, double dd, double w) {
+    if (!(w > 0.0)) return;   /* an underflowed weight contributes nothing */
+    double s = (delta != 0.0) ? dd / delta : 0.0;
+    for (int32_t c = 0; c < d; ++c)
+        y[a * d + c] += w * (x[b * d + c] + s * (x[a * d + c] - x[b * d + c]));
+    z[a] += w;
+}
+
+static int32_t hist_bin(double delta, int32_t B, double hist_max) {
+    double f = floor(delta / (hist_max / (double)B));
+    if (f >= (double)(B - 1)) return B - 1;
+    if (f < 0.0) return 0;
+    return (int32_t)f;
+}
+
+/* Accepted non-edge partners of vertex i for sample slots t = 0..k-1
+ * (g or -1 when all attempts hit an edge or i itself). */
+static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
+                          int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
+                          int32_t* out, int64_t* rejected, int64_t* exhausted) {
+    for (int32_t t = 0; t < k; ++t) {
+        int32_t got = -1;
+        for (int32_t a = 0; a < max_retries; ++a) {
+            uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t,
+                                     tag | ((uint32_t)a >> 2), a & 3);
+            int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
+            if (g != i && !orc_is_edge(row_ptr, col_idx, i, g)) { got = g; break; }
+            if (rejected) ++*rejected;
+        }
+        if (got < 0 && exhausted) ++*exhausted;
+        out[t] = got;
+    }
+}
+
+void orc_sample(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t epoch,
+                uint64_t seed, int32_t loss_stream, int32_t k, int32_t max_retries, int32_t* samples) {
+    uint32_t tag = loss_stream ? 0x0E000000u : 0x0B000000u;
+    for (int32_t i = 0; i < n; ++i)
+        sample_vertex(row_ptr, col_idx, n, i, epoch, seed, tag, k, max_retries,
+                      samples + (int64_t)i * k, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* One epoch (Fig. 4) in the per-vertex CSR form                        */
+/* ------------------------------------------------------------------ */
+int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+              const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
+              int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
+              int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
+              double* y, double* z, double* x_new, double* hist_e, double* hist_n,
+              int32_t* samples_out, int64_t* stats) {
+    int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+    if (!smp) return -1;
+    memset(y, 0, sizeof(double) * (size_t)n * d);          /* zero numerators ... */
+    memset(z, 0, sizeof(double) * (size_t)n);              /* ... and denominators */
+    if (hist_e) memset(hist_e, 0, sizeof(double) * (size_t)B);
+    if (hist_n) memset(hist_n, 0, sizeof(double) * (size_t)B);
+    int64_t accepted = 0, rejected = 0, exhausted = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        /* edges: every CSR slot (i,j) contributes to y_i, z_i */
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            double delta = dist(x, d, i, j), dd, w;
+            orc_parabola(delta, mu, sigma, 1, w_formula, clamp_neg_d, &dd, &w);
+            add_wm_term(y, z, x, d, i, j, delta, dd, w);
+            if (hist_e && j > i) hist_e[hist_bin(delta, B, hist_max)] += 1.0;
+        }
+        /* sampled non-edges anchored at i */
+        sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp,
+                      &rejected, &exhausted);
+        int32_t acc = 0;
+        for (int32_t t = 0; t < k; ++t) acc += (smp[t] >= 0);
+        accepted += acc;
+        double deg = (double)(row_ptr[i + 1] - row_ptr[i]);
+        double omega = acc ? ((double)n - 1.0 - deg) / (2.0 * acc) : 0.0;
+        for (int32_t t = 0; t < k; ++t) {
+            if (samples_out) samples_out[(int64_t)i * k + t] = smp[t];
+            int32_t g = smp[t];
+            if (g < 0) continue;
+            double delta = dist(x, d, i, g), dd, w;
+            orc_parabola(delta, mu, sigma, 0, w_formula, clamp_neg_d, &dd, &w);
+            add_wm_term(y, z, x, d, i, g, delta, dd, w);
+            if (symmetric) add_wm_term(y, z, x, d, g, i, delta, dd, w);
+            if (hist_n) hist_n[hist_bin(delta, B, hist_max)] += omega;
+        }
+    }
+    /* x_i := y_i / z_i */
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t c = 0; c < d; ++c)
+            x_new[(int64_t)i * d + c] = (z[i] >= z_min) ? y[(int64_t)i * d + c] / z[i]
+                                                         : x[(int64_t)i * d + c];
+    if (stats) { stats[0] = accepted; stats[1] = rejected; stats[2] = exhausted; stats[3] = accepted + rejected; }
+    free(smp);
+    return 0;
+}
+
+/* Edge part of Eq. 3 as the paper organises it (Fig. 4): a loop over the
+ * undirected edge list, each edge updating both endpoints. */
+void orc_edge_terms_edgelist(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                             const double* x, double sigma, double mu, int32_t w_formula,
+                             int32_t clamp_neg_d, double* y, double* z) {
+    memset(y, 0, sizeof(double) * (size_t)n * d);
+    memset(z, 0, sizeof(double) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            if (j < i) continue;             /* undirected edge list: (i,j), i < j */
+            double delta = dist(x, d, i, j), dd, w;
+            orc_parabola(delta, mu, sigma, 1, w_formula, clamp_neg_d, &dd, &w);
+            add_wm_term(y, z, x, d, i, j, delta, dd, w);
+            add_wm_term(y, z, x, d, j, i, delta, dd, w);
+        }
+}
+
+/* Edge part of Eq. 3 in the per-vertex CSR form used by orc_epoch. */
+void orc_edge_terms_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                        const double* x, double sigma, double mu, int32_t w_formula,
+                        int32_t clamp_neg_d, double* y, double* z) {
+    memset(y, 0, sizeof(double) * (size_t)n * d);
+    memset(z, 0, sizeof(double) * (size_t)n);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            double delta = dist(x, d, i, j), dd, w;
+            orc_parabola(delta, mu, sigma, 1, w_formula, clamp_neg_d, &dd, &w);
+            add_wm_term(y, z, x, d, i, j, delta, dd, w);
+        }
+}
+
+/* Sum of dl over all undirected edges and over a list of sampled non-edges
+ * (samples[i*k+t] = partner of anchor i, or -1). */
+double orc_surrogate_L(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                       const double* x, double sigma, double mu, int32_t k, const int32_t* samples) {
+    double L = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col_idx[e] > i) L += orc_dl(dist(x, d, i, col_idx[e]), mu, sigma, 1);
+        for (int32_t t = 0; t < k; ++t) {
+            int32_t g = samples[(int64_t)i * k + t];
+            if (g >= 0) L += orc_dl(dist(x, d, i, g), mu, sigma, 0);
+        }
+    }
+    return L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. III.F: slope optimisation on distance histograms                */
+/* ------------------------------------------------------------------ */
+/* dPE/dsigma (up to the positive factor 1/N) on histogram bins:
+ * d dl+/dsigma = -u h(u) / (sigma ln2), d dl-/dsigma = u g(u) / (sigma ln2)
+ * with h(u) = phi(u)/Q(u), g(u) = phi(u)/Q(-u), u = (delta-mu)/sigma. */
+double orc_dpe_dsigma(const double* hist_e, const double* hist_n, int32_t B, double hist_max,
+                      double mu, double sigma) {
+    double bw = hist_max / (double)B, s = 0.0;
+    for (int32_t b = 0; b < B; ++b) {
+        if (hist_e[b] == 0.0 && hist_n[b] == 0.0) continue;
+        double u = (((double)b + 0.5) * bw - mu) / sigma;
+        if (hist_e[b] != 0.0) s += hist_e[b] * (-u * inv_mills(u));
+        if (hist_n[b] != 0.0) s += hist_n[b] * (u * inv_mills(-u));
+    }
+    return s / (sigma * ORC_LN2);
+}
+
+/* Histogram entropy sum at sigma: sum_b c_e dl+(centre) + c_n dl-(centre). */
+double orc_hist_pe(const double* hist_e, const double* hist_n, int32_t B, double hist_max,
+                   double mu, double sigma) {
+    double bw = hist_max / (double)B, s = 0.0;
+    for (int32_t b = 0; b < B; ++b) {
+        double c = ((double)b + 0.5) * bw;
+        if (hist_e[b] != 0.0) s += hist_e[b] * orc_dl(c, mu, sigma, 1);
+        if (hist_n[b] != 0.0) s += hist_n[b] * orc_dl(c, mu, sigma, 0);
+    }
+    return s;
+}
+
+double orc_sigma_fit(const double* hist_e, const double* hist_n, int32_t B, double hist_max,
+                     double mu, double lo, double hi, int32_t iters) {
+    double flo = orc_dpe_dsigma(hist_e, hist_n, B, hist_max, mu, lo);
+    double fhi = orc_dpe_dsigma(hist_e, hist_n, B, hist_max, mu, hi);
+    if ((flo > 0.0) == (fhi > 0.0))
+        return (flo > 0.0) ? lo : hi;   /* monotone on the bracket: its lower-entropy end */
+    int lo_pos = flo > 0.0;
+    for (int32_t it = 0; it < iters; ++it) {
+        double mid = sqrt(lo * hi);
+        double fm = orc_dpe_dsigma(hist_e, hist_n, B, hist_max, mu, mid);
+        if ((fm > 0.0) == lo_pos) lo = mid; else hi = mid;
+    }
+    return sqrt(lo * hi);
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 2: predictive entropy                                            */
+/* ------------------------------------------------------------------ */
+double orc_loss_exact(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                      const double* x, double sigma, double mu) {
+    double N = 0.5 * (double)n * ((double)n - 1.0), s = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j)
+            s += orc_dl(dist(x, d, i, j), mu, sigma, orc_is_edge(row_ptr, col_idx, i, j));
+    return s / N;
+}
+
+double orc_loss_sampled(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                        const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
+                        int32_t k, int32_t max_retries) {
+    double N = 0.5 * (double)n * ((double)n - 1.0), s = 0.0;
+    int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+    if (!smp) return NAN;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col_idx[e] > i) s += orc_dl(dist(x, d, i, col_idx[e]), mu, sigma, 1);
+        sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0E000000u, k, max_retries, smp, NULL, NULL);
+        int32_t acc = 0;
+        for (int32_t t = 0; t < k; ++t) acc += (smp[t] >= 0);
+        if (!acc) continue;
+        double omega = ((double)n - 1.0 - (double)(row_ptr[i + 1] - row_ptr[i])) / (2.0 * acc);
+        for (int32_t t = 0; t < k; ++t)
+            if (smp[t] >= 0) s += omega * orc_dl(dist(x, d, i, smp[t]), mu, sigma, 0);
+    }
+    free(smp);
+    return s / N;
+}
+
+/* ------------------------------------------------------------------ */
+/* Full run: Fig. 4 repeated for a fixed number of epochs               */
+/* ------------------------------------------------------------------ */
+int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+            double* x, double* sigma, double mu, int32_t epoch0, int32_t epochs, uint64_t seed,
+            int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
+            double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats) {
+    size_t nd = (size_t)n * d;
+    double* y = (double*)malloc(nd * sizeof(double));
+    double* z = (double*)malloc((size_t)n * sizeof(double));
+    double* xn = (double*)malloc(nd * sizeof(double));
+    double* he = (double*)malloc((size_t)B * sizeof(double));
+    double* hn = (double*)malloc((size_t)B * sizeof(double));
+    if (!y || !z || !xn || !he || !hn) { free(y); free(z); free(xn); free(he); free(hn); return -1; }
+    int64_t st[4];
+    if (stats) memset(stats, 0, 4 * sizeof(int64_t));
+    for (int32_t e = 0; e < epochs; ++e) {
+        int32_t ep = epoch0 + e;
+        orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
+                  w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st);
+        memcpy(x, xn, nd * sizeof(double));
+        if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0)
+            *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);
+        if (stats) for (int q = 0; q < 4; ++q) stats[q] += st[q];
+    }
+    free(y); free(z); free(xn); free(he); free(hn);
+    return 0;
+}

@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle against what the paper and the mathematics fix:
+an independent library (cuRAND's host Philox, mpmath, scipy), closed forms
+(tests/golden/), derivative identities by finite differences, brute force on
+tiny graphs, and invariants of Fig. 2 / Fig. 4.  None of them calls the CUDA
+engine.
+"""
+import ctypes
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MU = 1.5
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 against cuRAND's host generator (an independent implementation)
+# ---------------------------------------------------------------------------
+def _curand_host(seed, count, offset=0):
+    path = None
+    for cand in ("/usr/local/cuda/lib64/libcurand.so", "libcurand.so", "libcurand.so.10"):
+        try:
+            lib = ctypes.CDLL(cand)
+            path = cand
+            break
+        except OSError:
+            continue
+    if path is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) != 0:  # PHILOX4_32_10
+        pytest.skip("cuRAND host generator unavailable")
+    assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+    if offset:
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+    out = np.zeros(count, dtype=np.uint32)
+    assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(count)) == 0
+    lib.curandDestroyGenerator(gen)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x6E6D7065, (0xDEADBEEF << 32) | 0x12345678])
+def test_philox_matches_curand_host(oracle_mod, seed):
+    # cuRAND's host Philox emits block b as Philox(ctr=(0,0,b,0), key=(seed_lo, seed_hi));
+    # a small generator offset of 4*b words starts at block b.  Counter words 0, 1 and 3
+    # stay zero only in the first round: rounds 2-10 mix every word, so the whole round
+    # function and key schedule are exercised.
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    out = _curand_host(seed, 4 * 64)
+    for b in range(64):
+        np.testing.assert_array_equal(oracle_mod.philox4x32_10([0, 0, b, 0], key), out[4 * b: 4 * b + 4])
+    for blk in (1000, 12345, 40000):
+        got = _curand_host(seed, 8, offset=4 * blk)
+        ctr = [0, 0, blk & 0xFFFFFFFF, blk >> 32]
+        np.testing.assert_array_equal(oracle_mod.philox4x32_10(ctr, key), got[:4])
+
+
+def test_philox_counter_words_all_matter(oracle_mod):
+    base = oracle_mod.philox4x32_10([1, 2, 3, 4], [5, 6])
+    for w in range(4):
+        c = [1, 2, 3, 4]
+        c[w] ^= 1
+        assert not np.array_equal(oracle_mod.philox4x32_10(c, [5, 6]), base)
+
+
+def test_vertex_draws_uniform(oracle_mod, sbm_small):
+    # chi-square on the mapped draws of an empty-ish graph: every vertex equally likely
+    n = 97
+    rp = np.zeros(n + 1, dtype=np.int32)
+    ci = np.zeros(0, dtype=np.int32)
+    s = oracle_mod.sample(rp, ci, epoch=3, seed=99, k=200, max_retries=1)
+    counts = np.zeros(n)
+    for i in range(n):
+        row = s[i][s[i] >= 0]
+        assert np.all(row != i)
+        np.add.at(counts, row, 1)
+    # self draws are rejected (max_retries=1) so vertex j receives draws from n-1 anchors
+    draws = (s >= 0).sum()
+    expected = draws / n
+    chi2 = ((counts - expected) ** 2 / expected).sum()
+    from scipy.stats import chi2 as chi2d
+    assert chi2d.sf(chi2, n - 1) > 1e-4
+
+
+def test_init_positions_exact_grid(oracle_mod):
+    x = oracle_mod.init_positions(500, 3, seed=11)
+    assert x.dtype == np.float32 and x.shape == (500, 3)
+    assert x.min() >= -1.0 and x.max() < 1.0
+    # values are k * 2^-23 - 1: exactly representable, no rounding happened
+    k = (x.astype(np.float64) + 1.0) * 2 ** 23
+    np.testing.assert_array_equal(k, np.round(k))
+    assert abs(x.mean()) < 0.05
+    x2 = oracle_mod.init_positions(500, 3, seed=11, init_range=0.25)
+    np.testing.assert_array_equal(x2, (x.astype(np.float64) * 0.25).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# Membership
+# ---------------------------------------------------------------------------
+def test_membership_all_pairs(oracle_mod, sbm_small):
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    dense = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        dense[i, ci[rp[i]:rp[i + 1]]] = True
+    assert np.array_equal(dense, dense.T) and not dense.diagonal().any()
+    for i in range(n):
+        for j in range(n):
+            assert oracle_mod.is_edge(rp, ci, i, j) == dense[i, j]
+
+
+# ---------------------------------------------------------------------------
+# Description length (Sec. II.B) against mpmath
+# ---------------------------------------------------------------------------
+def _mp_dl(delta, mu, sigma, edge):
+    # evaluated at the caller's working precision (see _mp)
+    x = (mp.mpf(delta) - mu) / (mp.sqrt(2) * sigma)
+    # 1/2 -/+ 1/2 erf(x) written as 1/2 erfc(+/-x); when that is close to 1 the
+    # logarithm is taken as log1p of minus the other tail, exact in any precision
+    a = x if edge else -x
+    if a < 0:
+        return -mp.log1p(-mp.erfc(-a) / 2) / mp.log(2)
+    return -mp.log(mp.erfc(a) / 2, 2)
+
+
+@pytest.mark.parametrize("sigma", [0.05, 0.3, 1.0, 2.5])
+def test_dl_matches_mpmath(oracle_mod, sigma):
+    for delta in [0.0, 0.01, 0.5, 1.2, 1.5, 1.9, 3.0, 7.5, 20.0]:
+        for edge in (True, False):
+            with mp.workdps(60):
+                ref = float(_mp_dl(delta, MU, sigma, edge))
+            got = oracle_mod.dl(delta, MU, sigma, edge)
+            assert got == pytest.approx(ref, rel=1e-12, abs=1e-300), (delta, sigma, edge)
+
+
+def test_h_basic_closed_forms(oracle_mod):
+    n = 101
+    N = n * (n - 1) / 2
+    assert oracle_mod.h_basic(n, N / 2) == pytest.approx(1.0, abs=1e-15)
+    assert oracle_mod.h_basic(n, 0) == 0.0
+    assert oracle_mod.h_basic(n, N) == 0.0
+    assert oracle_mod.h_basic(n, N / 4) == pytest.approx(oracle_mod.h_basic(n, 3 * N / 4), rel=1e-14)
+    p = 0.1
+    assert oracle_mod.h_basic(n, p * N) == pytest.approx(-(p * math.log2(p) + (1 - p) * math.log2(1 - p)))
+
+
+# ---------------------------------------------------------------------------
+# Parabola (Eq. 4 / Eq. 5)
+# ---------------------------------------------------------------------------
+def test_parabola_golden_closed_forms(oracle_mod):
+    path = os.path.join(HERE, "golden", "parabola_closed_forms.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert rows
+    for reading, kind, mu, sigma, w, d in rows:
+        dd, ww = oracle_mod.parabola(float(mu), float(mu), float(sigma), kind == "edge",
+                                     w_formula=(reading == "printed"), clamp_neg_d=0)
+        assert ww == pytest.approx(float(w), rel=1e-13)
+        assert dd == pytest.approx(float(d), rel=1e-13)
+
+
+def _mp_derivs(delta, mu, sigma, edge):
+    with mp.workdps(80):
+        f = lambda t: _mp_dl(t, mu, sigma, edge)
+        return mp.diff(f, mp.mpf(delta), 1), mp.diff(f, mp.mpf(delta), 2)
+
+
+@pytest.mark.parametrize("sigma", [0.1, 0.7, 1.0, 3.0])
+def test_parabola_matches_dl_derivatives(oracle_mod, sigma):
+    """Sec. II.C: the parabola w(delta-d)^2 agrees with dl in the first and
+    second derivative at the current distance (derived reading); the printed
+    Eq. 4 agrees in the first derivative only."""
+    deltas = [0.0, 0.2, 0.9, 1.5, 2.2, 4.0]
+    deltas += [MU + sigma * u for u in (-30.0, -8.0, 6.0, 27.0, 40.0)]   # tail branches
+    for delta in deltas:
+        if delta < 0:
+            continue
+        for edge in (True, False):
+            d1, d2 = _mp_derivs(delta, MU, sigma, edge)
+            d1, d2 = float(d1), float(d2)
+            dd, w = oracle_mod.parabola(delta, MU, sigma, edge, w_formula=0, clamp_neg_d=0)
+            if d2 < 1e-250:      # both derivatives underflow in double: w underflows too
+                assert w < 1e-200
+                continue
+            assert 2 * w == pytest.approx(d2, rel=1e-9), (delta, edge)
+            assert 2 * w * (delta - dd) == pytest.approx(d1, rel=1e-9), (delta, edge)
+            dp, wp = oracle_mod.parabola(delta, MU, sigma, edge, w_formula=1, clamp_neg_d=0)
+            assert 2 * wp * (delta - dp) == pytest.approx(d1, rel=1e-9), (delta, edge)
+            assert wp >= w > 0   # the printed form adds c1 h^2, negligible when h underflows
+
+
+def test_parabola_limits(oracle_mod):
+    L2 = math.log(2)
+    sigma = 0.8
+    # far edge, u -> +inf: with h - u = 1/u - 2/u^3 + O(u^-5) (Mills ratio expansion),
+    # d+ = mu - 2 sigma/u + O(u^-3) and w+ -> 1/(2 ln2 sigma^2) (derived reading)
+    for u in (30.0, 200.0):
+        dd, w = oracle_mod.parabola(MU + u * sigma, MU, sigma, True, clamp_neg_d=0)
+        assert dd == pytest.approx(MU - 2 * sigma / u, abs=20 * sigma / u ** 3)
+        assert w == pytest.approx(1 / (2 * L2 * sigma ** 2), rel=3 / u ** 2)
+    # close non-edge, u -> -inf: mirror image, d- = mu + 2 sigma/|u| + O(|u|^-3)
+    for u in (-30.0, -100.0):
+        dd, w = oracle_mod.parabola(MU + u * sigma, MU, sigma, False, clamp_neg_d=0)
+        assert dd == pytest.approx(MU + 2 * sigma / -u, abs=20 * sigma / u ** 2 / -u)
+    # negative d+ for a close edge with a wide sigmoid, clamped to 0
+    dd, _ = oracle_mod.parabola(0.1, MU, 1.0, True, clamp_neg_d=0)
+    assert dd == pytest.approx(-0.5400, abs=1e-3)
+    dd, _ = oracle_mod.parabola(0.1, MU, 1.0, True, clamp_neg_d=1)
+    assert dd == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3: the update is a scaled gradient step on the frozen-pair surrogate
+# ---------------------------------------------------------------------------
+def test_eq3_gradient_identity(oracle_mod, sbm_small):
+    """y_i - z_i x_i = -1/2 dL/dx_i with L = sum of dl over the epoch's pairs
+    (all edges once, every sampled non-edge once, symmetric updates)."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.5, 1.5, size=(n, 3))
+    sigma, k, seed, ep = 0.6, 4, 1234, 7
+    r = oracle_mod.epoch(rp, ci, x, sigma, ep, seed, k, clamp_neg_d=0, symmetric=1)
+    samples = r["samples"]
+    h = 1e-6
+    for i in range(0, n, 7):
+        for c in range(3):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            g = (oracle_mod.surrogate_L(rp, ci, xp, sigma, samples)
+                 - oracle_mod.surrogate_L(rp, ci, xm, sigma, samples)) / (2 * h)
+            assert r["delta"][i, c] == pytest.approx(-0.5 * g, rel=2e-6, abs=1e-8), (i, c)
+    # the update itself: x_new = y / z
+    np.testing.assert_allclose(r["x_new"], r["y"] / r["z"][:, None], rtol=1e-15)
+
+
+def test_edge_list_form_equals_csr_form(oracle_mod, sbm_small):
+    """Fig. 4 walks the edge list and updates both endpoints; the per-vertex
+    CSR sweep reaches every edge from both rows.  Same sums up to order."""
+    rp, ci = sbm_small
+    x = np.random.default_rng(1).normal(size=(len(rp) - 1, 2))
+    for wf in (0, 1):
+        y1, z1 = oracle_mod.edge_terms(rp, ci, x, 0.9, w_formula=wf, form="edgelist")
+        y2, z2 = oracle_mod.edge_terms(rp, ci, x, 0.9, w_formula=wf, form="csr")
+        np.testing.assert_allclose(y1, y2, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(z1, z2, rtol=1e-12)
+
+
+def test_zmin_guard_keeps_isolated_far_vertex(oracle_mod):
+    # vertex 2 is isolated and far from everyone: all its non-edge weights underflow
+    rp = np.array([0, 1, 2, 2], dtype=np.int32)
+    ci = np.array([1, 0], dtype=np.int32)
+    x = np.array([[0.0, 0.0], [0.5, 0.0], [1e4, 1e4]])
+    r = oracle_mod.epoch(rp, ci, x, 0.5, 0, 3, 2)
+    assert r["z"][2] < 1e-30
+    np.testing.assert_array_equal(r["x_new"][2], x[2])
+
+
+# ---------------------------------------------------------------------------
+# Sampling (Fig. 2 semantics)
+# ---------------------------------------------------------------------------
+def test_sampling_semantics(oracle_mod, sbm_small):
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    k, seed, ep, R = 6, 77, 4, 32
+    s = oracle_mod.sample(rp, ci, ep, seed, k, max_retries=R)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    adj = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(n)]
+    rejected = 0
+    for i in range(n):
+        for t in range(k):
+            # replay the candidate sequence from the (pinned) Philox words
+            got = -1
+            for a in range(R):
+                r = int(oracle_mod.philox4x32_10([i, ep, t, 0x0B000000 | (a >> 2)], key)[a & 3])
+                g = (r * n) >> 32
+                if g != i and g not in adj[i]:
+                    got = g
+                    break
+                rejected += 1
+            assert s[i, t] == got
+            assert got == -1 or (got != i and got not in adj[i])
+    r = oracle_mod.epoch(rp, ci, np.zeros((n, 2)), 1.0, ep, seed, k)
+    assert r["rejected"] == rejected
+    np.testing.assert_array_equal(r["samples"], s)
+
+
+def test_sampling_exhaustion_on_complete_row(oracle_mod):
+    # star centre adjacent to everyone: every draw is an edge or itself
+    n = 9
+    rows = [list(range(1, n))] + [[0] for _ in range(1, n)]
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array(sum(rows, []), dtype=np.int32)
+    r = oracle_mod.epoch(rp, ci, np.random.default_rng(0).normal(size=(n, 2)), 1.0, 0, 5, 3,
+                         max_retries=8)
+    assert (r["samples"][0] == -1).all()
+    assert r["exhausted"] >= 3
+
+
+# ---------------------------------------------------------------------------
+# Slope optimisation (Sec. III.F)
+# ---------------------------------------------------------------------------
+def _epoch_hist(oracle_mod, sbm_1000, x_scale=1.0, sigma=1.0):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = oracle_mod.init_positions(len(rp) - 1, 2, seed=5).astype(np.float64) * x_scale
+    r = oracle_mod.epoch(rp, ci, x, sigma, 0, 5, 5)
+    return r["hist_e"], r["hist_n"]
+
+
+def test_dpe_dsigma_is_the_derivative(oracle_mod, sbm_1000):
+    he, hn = _epoch_hist(oracle_mod, sbm_1000, x_scale=2.0)
+    for s in (0.05, 0.4, 1.0, 3.0):
+        h = s * 1e-6
+        fd = (oracle_mod.hist_pe(he, hn, 12.0, MU, s + h) - oracle_mod.hist_pe(he, hn, 12.0, MU, s - h)) / (2 * h)
+        assert oracle_mod.dpe_dsigma(he, hn, 12.0, MU, s) == pytest.approx(fd, rel=1e-6)
+
+
+def test_sigma_fit_minimises_histogram_entropy(oracle_mod, sbm_1000):
+    from scipy.optimize import minimize_scalar
+    for scale in (1.0, 2.0, 4.0):
+        he, hn = _epoch_hist(oracle_mod, sbm_1000, x_scale=scale)
+        s = oracle_mod.sigma_fit(he, hn)
+        res = minimize_scalar(lambda t: oracle_mod.hist_pe(he, hn, 12.0, MU, math.exp(t)),
+                              bounds=(math.log(1e-3), math.log(1e3)), method="bounded",
+                              options=dict(xatol=1e-10))
+        assert s == pytest.approx(math.exp(res.x), rel=1e-4)
+
+
+def test_sigma_fit_separable_goes_to_bracket_floor(oracle_mod):
+    # edges all at 0.5, non-edges all at 3.0: entropy falls as sigma -> 0 (Sec. II.B: PE -> 0)
+    B = 1024
+    he = np.zeros(B); hn = np.zeros(B)
+    he[int(0.5 / (12.0 / B))] = 100
+    hn[int(3.0 / (12.0 / B))] = 5000
+    s = oracle_mod.sigma_fit(he, hn)
+    # any sigma whose entropy underflows to zero is a minimiser; the fit must reach one
+    assert oracle_mod.hist_pe(he, hn, 12.0, MU, s) < 1e-100
+    assert s < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2: predictive entropy
+# ---------------------------------------------------------------------------
+def test_loss_exact_against_scipy(oracle_mod, sbm_small):
+    from scipy.special import log_ndtr
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    x = np.random.default_rng(3).normal(size=(n, 2))
+    sigma = 0.7
+    adj = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        adj[i, ci[rp[i]:rp[i + 1]]] = True
+    iu = np.triu_indices(n, 1)
+    dist = np.linalg.norm(x[iu[0]] - x[iu[1]], axis=1)
+    u = (dist - MU) / sigma
+    # s+ = Q(u) = Phi(-u), s- = Phi(u)
+    dl = np.where(adj[iu], -log_ndtr(-u), -log_ndtr(u)) / math.log(2)
+    ref = dl.sum() / (n * (n - 1) / 2)
+    assert oracle_mod.loss_exact(rp, ci, x, sigma) == pytest.approx(ref, rel=1e-12)
+
+
+def test_sampled_loss_is_unbiased(oracle_mod, sbm_small):
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    x = np.random.default_rng(4).normal(size=(n, 2))
+    exact = oracle_mod.loss_exact(rp, ci, x, 0.8)
+    est = np.array([oracle_mod.loss_sampled(rp, ci, x, 0.8, ep, 21, 4) for ep in range(400)])
+    se = est.std(ddof=1) / math.sqrt(len(est))
+    assert abs(est.mean() - exact) < 3.5 * se + 1e-12
+
+
+def test_planted_embedding_entropy_vanishes(oracle_mod):
+    # two cliques far apart: edges at distance ~0, non-edges at distance 10
+    n = 12
+    rows = [[j for j in range(6) if j != i] if i < 6 else [j for j in range(6, 12) if j != i] for i in range(n)]
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array(sum(rows, []), dtype=np.int32)
+    x = np.zeros((n, 2)); x[6:, 0] = 10.0
+    x[:, 1] = np.arange(n) % 6 * 1e-3
+    pes = [oracle_mod.loss_exact(rp, ci, x, s) for s in (1.0, 0.3, 0.1)]
+    assert pes[0] > pes[1] > pes[2] and pes[2] < 1e-6
+
+
+def test_histograms_count_pairs(oracle_mod, sbm_1000):
+    """Sec. III.F histograms: every undirected edge once (weight 1); sampled
+    non-edges weighted so that their total is the number of non-edges."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    n = len(rp) - 1
+    m = len(ci) // 2
+    x = oracle_mod.init_positions(n, 2, seed=9).astype(np.float64) * 3.0
+    r = oracle_mod.epoch(rp, ci, x, 0.8, 2, 9, 5)
+    assert r["exhausted"] == 0
+    assert r["hist_e"].sum() == m
+    assert r["hist_n"].sum() == pytest.approx(n * (n - 1) / 2 - m, rel=1e-12)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    up = ci > rows
+    de = np.linalg.norm(x[rows[up]] - x[ci[up]], axis=1)
+    ref, _ = np.histogram(np.minimum(de, 12.0 - 1e-9), bins=1024, range=(0.0, 12.0))
+    np.testing.assert_array_equal(r["hist_e"], ref)
