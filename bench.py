@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""GEMPE epoch benchmark: pair-updates per second of one GEMPE epoch.
+
+Workload (default): the graph-drawing-at-scale setting -- an R-MAT graph with
+scale 16 (65,536 vertices) and edge factor 16 ((a,b,c,d) = (.57,.19,.19,.05),
+duplicates and self loops removed), d = 2 FP32 positions, 10 sampled non-edges
+per vertex per epoch, sigma refit after every epoch.  Synthetic, seeded.
+
+A step is one epoch (pair sweep + position update + sigma refit) through the
+C ABI (gempe_sweep, gempe_update) on a torch CUDA stream.  Each step is timed
+with CUDA events on that stream; the L2 cache is flushed (a 256 MiB write)
+between steps, outside the events.  Pair-updates per epoch = m undirected
+edges + accepted sampled non-edges.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gempe|reference]
+
+--impl reference times the FP64 CPU oracle (the method restated in plain C,
+single-threaded) on the same workload and metric: each step is one oracle
+epoch.  Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (no collective on the data path); value is the sum of
+all ranks' pair-updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-updates/sec per GEMPE epoch"
+UNIT = "pair-updates/s"
+WORKLOAD = "rmat-s16-ef16"
+L2_FLUSH_BYTES = 256 << 20
+EDGE_CHUNK = 64      # work-unit size of the sweep (CSR slots per unit)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweep_algorithmic_bytes(n, nnz, d, n_units, draws, accepted):
+    """Bytes one sweep launch must move at least, each random gather paid once
+    at its minimum size (no reuse): CSR streamed once, work units, own row,
+    one neighbour row per CSR slot, one 32-byte hash sector per draw, the
+    partner row and a read-modify-write of the partner's accumulator row per
+    accepted sample, a read-modify-write of the own accumulator row."""
+    row = 4 * d
+    acc_row = 4 * (((d + 1) + 3) // 4 * 4)
+    return (4 * (n + 1) + 4 * nnz + 16 * n_units + n * row + nnz * row + 32 * draws
+            + accepted * (row + 2 * acc_row) + n * 2 * acc_row)
+
+
+def work_units(row_ptr):
+    import numpy as np
+    deg = np.diff(row_ptr)
+    return int(np.maximum(1, (deg + EDGE_CHUNK - 1) // EDGE_CHUNK).sum())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single-threaded, bounded sample
+# ---------------------------------------------------------------------------
+def oracle_epochs(w, epochs, x0=None):
+    import numpy as np
+    import oracle
+    rp, ci = w["row_ptr"], w["col_idx"]
+    n = len(rp) - 1
+    from paper_2011_03479_gb300 import inputs
+    x = oracle.init_positions(n, w["d"], inputs.EMBED_SEED) if x0 is None else x0
+    m = len(ci) // 2
+    t0 = time.perf_counter()
+    xr, s, st = oracle.run(rp, ci, x, 1.0, epochs, inputs.EMBED_SEED, w["k"])
+    dt = time.perf_counter() - t0
+    return epochs * m + st["accepted"], dt, xr
+
+
+def cpu_baseline(w, budget_s=12.0):
+    # calibrate on one epoch, then run as many as fit in the budget
+    p1, t1, _ = oracle_epochs(w, 1)
+    epochs = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    p, t, _ = oracle_epochs(w, epochs)
+    return {"value": p / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{epochs} epochs of {w['name']} from the initial positions, FP64 oracle, one thread"}
+
+
+# ---------------------------------------------------------------------------
+def _dist():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def _profile_traffic(kernel_src_hash):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "sweep_rmat-s16-ef16.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_src_hash:
+        return None
+    return int(m.group(1))
+
+
+def kernel_source_hash():
+    hsh = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2011_03479_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            hsh.update(open(os.path.join(csrc, fn), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def run_gempe(args):
+    import numpy as np
+    import torch
+
+    from paper_2011_03479_gb300 import binding as B
+    from paper_2011_03479_gb300 import inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.WORKLOADS[WORKLOAD]()
+    rp, ci = w["row_ptr"], w["col_idx"]
+    n, nnz, d, k = len(rp) - 1, len(ci), w["d"], w["k"]
+    m = nnz // 2
+    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # ---------------- device-resident timing ----------------
+    ctx = B.gempe_create(rp, ci, d, p, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            B.gempe_sweep(ctx)
+            B.gempe_update(ctx)
+        torch.cuda.synchronize()
+        s0 = B.gempe_stats(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        wall0 = time.perf_counter()
+        for e0, e1, e2 in ev:
+            flush.zero_()          # L2 flush between steps, outside the events
+            e0.record(stream)
+            B.gempe_sweep(ctx)
+            e1.record(stream)
+            B.gempe_update(ctx)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        clk = clocks.stop()
+        s1 = B.gempe_stats(ctx)
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    sweep_ms = [a.elapsed_time(b) for a, b, c in ev]
+    accepted = s1["accepted"] - s0["accepted"]
+    draws = s1["draws"] - s0["draws"]
+    pairs = args.steps * m + accepted
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        pp = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        t_all, pairs_all = tt.item(), pp.item()
+    else:
+        t_all, pairs_all = t_total, float(pairs)
+    value = pairs_all / t_all
+    ctx.close()
+
+    # ---------------- end to end through the C ABI, host buffers ----------------
+    rp_pin = torch.from_numpy(rp).pin_memory().numpy()
+    ci_pin = torch.from_numpy(ci).pin_memory().numpy()
+    out_pin = torch.empty((n, d), dtype=torch.float32).pin_memory().numpy()
+    epochs = w["epochs"]
+    e2e_jobs = args.e2e_jobs
+
+    def job():
+        c = B.gempe_create(rp_pin, ci_pin, d, p, stream=stream)
+        st0 = B.gempe_stats(c)
+        B.gempe_step(c, epochs)
+        B.gempe_positions(c, out_pin)
+        st1 = B.gempe_stats(c)
+        c.close()
+        return epochs * m + (st1["accepted"] - st0["accepted"])
+
+    job()   # warm-up (builds nothing new: the library is loaded, the GPU is warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_pairs = sum(job() for _ in range(e2e_jobs))
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": e2e_pairs / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
+           "d2h_bytes_per_step": int(out_pin.nbytes),
+           "step": f"one {epochs}-epoch embedding job: gempe_create from pinned host CSR, "
+                   f"gempe_step({epochs}), gempe_positions to pinned host memory",
+           "ms_per_job": 1e3 * e2e_t / e2e_jobs}
+    if world > 1:
+        import torch.distributed as dist
+        v = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        e2e["value"] = v.item()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    units = work_units(rp)
+    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, units, draws / args.steps, accepted / args.steps)
+    sweep_s = statistics.mean(sweep_ms) / 1e3
+    achieved = bytes_per_sweep / sweep_s / 1e9
+    traffic = _profile_traffic(kernel_source_hash())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "d": d, "k": k, "sigma_every": 1,
+                   "step": "one epoch: gempe_sweep + gempe_update",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "pairs_per_epoch": pairs / args.steps,
+        "sweep_ms": statistics.mean(sweep_ms),
+        "update_ms": statistics.mean(step_ms) - statistics.mean(sweep_ms),
+        "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
+                     "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2011_03479_gb300 import inputs
+    oracle.build()
+    w = inputs.WORKLOADS[WORKLOAD]()
+    m = len(w["col_idx"]) // 2
+    _, _, x = oracle_epochs(w, args.warmup) if args.warmup else (0, 0, None)
+    times, pairs = [], 0
+    for s in range(args.steps):
+        p, t, x = oracle_epochs(w, 1, x0=x)
+        times.append(t)
+        pairs += p
+    value = pairs / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": len(w["row_ptr"]) - 1, "m": m, "d": w["d"], "k": w["k"],
+                   "step": "one epoch of the FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed epochs of {WORKLOAD} after {args.warmup} warm-up epochs"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gempe", "reference"], default="gempe")
+    ap.add_argument("--e2e-jobs", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.steps > 50:
+            args.steps = 50      # each oracle epoch takes a fraction of a second: keep the run bounded
+        run_reference(args)
+    else:
+        run_gempe(args)
+
+
+if __name__ == "__main__":
+    main()

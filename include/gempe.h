@@ -1,0 +1,182 @@
+/*
+ * gempe.h -- C ABI of the GB300 GEMPE epoch engine.
+ *
+ * GEMPE (Graph Embedding by Minimizing the Predictive Entropy; Boehm & Plant,
+ * "Massively Parallel Graph Drawing and Representation Learning", IEEE
+ * BigData 2020, arXiv 2011.03479) places the n vertices of an undirected,
+ * unweighted graph G = (V, E) at points x_i in R^d (Sec. II.A) so that the
+ * predictive entropy PE of Eq. 2 is small.  One epoch (Fig. 4) fits, for
+ * every edge and for randomly sampled non-edges, a parabola w (delta - d)^2
+ * to the description length (Eq. 4, Eq. 5), accumulates the weighted-
+ * majorization numerator y_i and denominator z_i (Eq. 3) per vertex, moves
+ * every vertex to x_i = y_i / z_i and refits the sigmoid slope sigma on
+ * distance histograms (Sec. III.F).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns a gempe_status and never throws or aborts.  On
+ *    failure gempe_last_error() holds a message for the calling thread.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device.  The caller owns every array it
+ *    passes; inputs are copied before the call returns unless stated.
+ *  - Positions are FP32, row-major [n][d].  Graphs are int32 CSR matrices
+ *    (row_ptr[n+1], col_idx[nnz]) that must be symmetric, with strictly
+ *    increasing column indices per row and no self loops; nnz counts each
+ *    undirected edge twice.
+ *  - A context owns all device memory it allocates.  Work is ordered on the
+ *    context's CUDA stream; calls that return data to the host synchronise
+ *    that stream.  Device-side failures (non-finite positions) are recorded
+ *    in a device status word and reported by the next synchronising call.
+ *  - A context may be used from one host thread at a time.
+ */
+#ifndef GEMPE_H
+#define GEMPE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gempe_status {
+    GEMPE_OK = 0,
+    GEMPE_E_INVALID_ARG = -1,    /* a null pointer, a size out of range, a wrong count */
+    GEMPE_E_INVALID_GRAPH = -2,  /* CSR not symmetric / unsorted / self loop / duplicate / range */
+    GEMPE_E_OOM = -3,            /* device allocation failed */
+    GEMPE_E_CUDA = -4,           /* a CUDA runtime call failed (message has the CUDA error) */
+    GEMPE_E_TIMEOUT = -5,        /* a bounded device wait gave up */
+    GEMPE_E_NUMERIC = -6,        /* a position became non-finite; the vertex kept its old value */
+    GEMPE_E_BUDGET = -7          /* request exceeds a memory budget */
+} gempe_status;
+
+/* Parameters of the method.  gempe_default_params() fills the paper's values. */
+typedef struct gempe_params {
+    float mu;               /* sigmoid position, fixed at 1.5 (Sec. III.F) */
+    float sigma0;           /* initial slope, 1.0 (Fig. 4) */
+    int32_t sigma_every;    /* refit sigma after every sigma_every-th epoch (Sec. III.F); 0 = fixed */
+    int32_t neg_per_vertex; /* k: non-edges sampled per vertex per epoch (Sec. III.C), 0..32 */
+    int32_t max_retries;    /* draws per sample before it is dropped (Fig. 2 retries without bound) */
+    int32_t symmetric_neg;  /* 1: the sampled partner g also receives the pair's term (Fig. 4) */
+    int32_t w_formula;      /* 0: w from second-derivative matching (Sec. II.C text);
+                               1: Eq. 4 as printed (first term doubled) */
+    int32_t clamp_neg_d;    /* 1: d := max(d, 0) */
+    float z_min;            /* x_i is kept when z_i < z_min (1e-30) */
+    float init_range;       /* initial x uniform in [-init_range, init_range) (Fig. 4) */
+    uint64_t seed;          /* Philox4x32-10 key */
+    int32_t hist_bins;      /* B distance-histogram bins on [0, hist_max) (Sec. III.F), 16..4096 */
+    float hist_max;         /* 12.0 */
+    /* Optional device allocator (e.g. a framework's caching allocator).  When
+     * dev_alloc is null the engine uses cudaMalloc / cudaFree. */
+    void* (*dev_alloc)(size_t bytes, void* user);
+    void (*dev_free)(void* ptr, void* user);
+    void* alloc_user;
+} gempe_params;
+
+typedef struct gempe_stats_t {
+    int32_t epoch;                 /* epochs completed */
+    float sigma;                   /* current slope */
+    uint64_t accepted;             /* sampled non-edges used (cumulative) */
+    uint64_t rejected;             /* draws that hit an edge or the anchor itself */
+    uint64_t exhausted;            /* samples dropped after max_retries rejected draws */
+    uint64_t draws;                /* accepted + rejected */
+    int64_t n_edges;               /* m, undirected */
+    int32_t n, d, k;
+} gempe_stats_t;
+
+typedef struct gempe_ctx gempe_ctx;
+
+/* Fill *p with the defaults: mu 1.5, sigma0 1, sigma_every 1, k 5, max_retries
+ * 32, symmetric 1, derived w, clamp 1, z_min 1e-30, init_range 1, seed
+ * 0x6E6D7065, 1024 bins on [0, 12), no custom allocator. */
+void gempe_default_params(gempe_params* p);
+
+/* Create an embedding context from a host CSR graph (Sec. II.A: G, n, d).
+ * row_ptr: host int32[n+1]; col_idx: host int32[row_ptr[n]].  d must be one
+ * of 1,2,3,4,8,16,32,64,128,256.  cuda_stream: a cudaStream_t for all work of
+ * the context, or NULL for a stream the context creates.  Validates the
+ * graph (GEMPE_E_INVALID_GRAPH), uploads it, builds the exact edge hash set,
+ * draws the initial positions (Fig. 4: uniform random) and sets sigma = sigma0,
+ * epoch = 0.  On success *out owns the context; on failure *out is NULL. */
+gempe_status gempe_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
+                          const gempe_params* p, void* cuda_stream, gempe_ctx** out);
+
+/* Same as gempe_create with the CSR arrays in device memory (copied). */
+gempe_status gempe_create_device(const int32_t* d_row_ptr, const int32_t* d_col_idx, int32_t n,
+                                 int64_t nnz, int32_t d, const gempe_params* p, void* cuda_stream,
+                                 gempe_ctx** out);
+
+void gempe_destroy(gempe_ctx* ctx);
+
+/* Run `iters` full epochs (Fig. 4): sweep + position update + sigma refit.
+ * Asynchronous on the context stream (replays a captured CUDA graph). */
+gempe_status gempe_step(gempe_ctx* ctx, int32_t iters);
+
+/* The first half of one epoch (the same kernel gempe_step runs): zeroed
+ * accumulators receive the Eq. 3 terms of every edge slot and every accepted
+ * sampled non-edge (Fig. 2), and the distance histograms are filled
+ * (Sec. III.F).  Positions, sigma and the epoch counter are unchanged; the
+ * sums stay for gempe_accumulators / gempe_histograms until gempe_update.
+ * host_samples: NULL, or host int32[n*k] that receives the accepted partner
+ * of each (vertex, sample slot), -1 if dropped (synchronises).
+ * gempe_step between gempe_sweep and gempe_update is GEMPE_E_INVALID_ARG. */
+gempe_status gempe_sweep(gempe_ctx* ctx, int32_t* host_samples);
+
+/* The second half: x_i := y_i / z_i for z_i >= z_min (Fig. 4), accumulators
+ * and histograms cleared, sigma refit when due, epoch counter + 1. */
+gempe_status gempe_update(gempe_ctx* ctx);
+
+/* Copy the positions to host float[n*d] (synchronises).  count must be n*d. */
+gempe_status gempe_positions(gempe_ctx* ctx, float* host_out, size_t count);
+
+/* Borrow a device pointer to the FP32 positions [n][d]; valid until the next
+ * call that changes them or gempe_destroy. */
+gempe_status gempe_positions_device(gempe_ctx* ctx, const float** d_view);
+
+/* Overwrite the positions from host float[n*d] (count must be n*d). */
+gempe_status gempe_set_positions(gempe_ctx* ctx, const float* host_x, size_t count);
+
+/* Set / read sigma and the epoch counter (the epoch keys the sampler). */
+gempe_status gempe_set_state(gempe_ctx* ctx, float sigma, int32_t epoch);
+gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
+
+/* Copy the accumulators after gempe_sweep to host float[n*(d+1)]: for each
+ * vertex d values of y_i - z_i x_i (the Eq. 3 numerator minus z_i x_i; the
+ * update is x_i + that / z_i = y_i / z_i), then z_i.  Synchronises. */
+gempe_status gempe_accumulators(gempe_ctx* ctx, float* host_out, size_t count);
+
+/* Copy the distance histograms to host float[2*B]: B edge bins, then B
+ * non-edge bins (Sec. III.F).  Synchronises. */
+gempe_status gempe_histograms(gempe_ctx* ctx, float* host_out, size_t count);
+
+/* Draw the sampled non-edges of the current epoch without using them:
+ * host int32[n*k] partners or -1.  stream_id 0 = the epoch's sampler, 1 =
+ * the loss estimator's sampler.  Synchronises. */
+gempe_status gempe_sample(gempe_ctx* ctx, int32_t stream_id, int32_t* host_out, size_t count);
+
+/* Membership test against the device edge hash set (Sec. III.C, exact):
+ * host int32 pairs[2*count] (i0,j0,i1,j1,...) -> host uint8 out[count],
+ * 1 if (i,j) is an edge.  Pairs out of range give GEMPE_E_INVALID_ARG. */
+gempe_status gempe_is_edge(gempe_ctx* ctx, const int32_t* host_pairs, size_t count, uint8_t* host_out);
+
+/* Sampled predictive entropy (Eq. 2) at the current positions and sigma, mu
+ * fixed: (sum over edges of dl+ + sum over k loss-stream samples per vertex
+ * of (n-1-deg_i)/(2 k_i) dl-) / (n(n-1)/2).  Per-pair dl in FP32, sums in
+ * FP64.  Synchronises. */
+gempe_status gempe_loss(gempe_ctx* ctx, double* out_pe_bits, float* out_sigma);
+
+/* Slope fit of Sec. III.F on a given histogram (host float[2*B], edge bins
+ * then non-edge bins) on the GPU: bisection of dPE/dsigma = 0 in log sigma
+ * on [1e-3, 1e3]; without a sign change the end with the lower entropy.
+ * cuda_stream may be NULL.  Synchronises. */
+gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_max, float mu,
+                             void* cuda_stream, float* out_sigma);
+
+gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* gempe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEMPE_H */

@@ -1,0 +1,318 @@
+"""ctypes binding of the C ABI in ``include/gempe.h``.
+
+Argument marshalling only: every step of the epoch runs in ``libgempe.so``'s
+CUDA kernels.  The functions keep the C names.  Host arrays are numpy arrays;
+device arrays may be torch CUDA tensors (their ``data_ptr()`` is passed) and a
+``stream`` argument may be a ``torch.cuda.Stream`` or a raw ``cudaStream_t``.
+
+Importing this module does not need a GPU; loading the library does not
+either.  If the library cannot be built or loaded the import fails: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+GEMPE_OK = 0
+STATUS_NAMES = {0: "GEMPE_OK", -1: "GEMPE_E_INVALID_ARG", -2: "GEMPE_E_INVALID_GRAPH",
+                -3: "GEMPE_E_OOM", -4: "GEMPE_E_CUDA", -5: "GEMPE_E_TIMEOUT",
+                -6: "GEMPE_E_NUMERIC", -7: "GEMPE_E_BUDGET"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class gempe_params(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_float),
+        ("sigma0", ctypes.c_float),
+        ("sigma_every", ctypes.c_int32),
+        ("neg_per_vertex", ctypes.c_int32),
+        ("max_retries", ctypes.c_int32),
+        ("symmetric_neg", ctypes.c_int32),
+        ("w_formula", ctypes.c_int32),
+        ("clamp_neg_d", ctypes.c_int32),
+        ("z_min", ctypes.c_float),
+        ("init_range", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+        ("hist_bins", ctypes.c_int32),
+        ("hist_max", ctypes.c_float),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class gempe_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("epoch", ctypes.c_int32),
+        ("sigma", ctypes.c_float),
+        ("accepted", ctypes.c_uint64),
+        ("rejected", ctypes.c_uint64),
+        ("exhausted", ctypes.c_uint64),
+        ("draws", ctypes.c_uint64),
+        ("n_edges", ctypes.c_int64),
+        ("n", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+    ]
+
+
+class GempeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.GEMPE_LIB
+
+
+def load(build: bool = True):
+    """Load libgempe.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build_gempe() if build else _build.GEMPE_LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"GEMPE CUDA engine not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    st = ctypes.c_int
+    sig = {
+        "gempe_default_params": (None, [P(gempe_params)]),
+        "gempe_create": (st, [vp, vp, i32, i32, P(gempe_params), vp, P(vp)]),
+        "gempe_create_device": (st, [vp, vp, i32, i64, i32, P(gempe_params), vp, P(vp)]),
+        "gempe_destroy": (None, [vp]),
+        "gempe_step": (st, [vp, i32]),
+        "gempe_sweep": (st, [vp, vp]),
+        "gempe_update": (st, [vp]),
+        "gempe_positions": (st, [vp, vp, sz]),
+        "gempe_positions_device": (st, [vp, P(vp)]),
+        "gempe_set_positions": (st, [vp, vp, sz]),
+        "gempe_set_state": (st, [vp, ctypes.c_float, i32]),
+        "gempe_get_state": (st, [vp, P(ctypes.c_float), P(i32)]),
+        "gempe_accumulators": (st, [vp, vp, sz]),
+        "gempe_histograms": (st, [vp, vp, sz]),
+        "gempe_sample": (st, [vp, i32, vp, sz]),
+        "gempe_is_edge": (st, [vp, vp, sz, vp]),
+        "gempe_loss": (st, [vp, P(ctypes.c_double), P(ctypes.c_float)]),
+        "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
+        "gempe_stats": (st, [vp, P(gempe_stats_t)]),
+        "gempe_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != GEMPE_OK:
+        msg = load().gempe_last_error()
+        raise GempeError(status, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(None)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# The C calls, same names
+# ---------------------------------------------------------------------------
+def gempe_default_params(**overrides) -> gempe_params:
+    p = gempe_params()
+    load().gempe_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class _Ctx:
+    """Owned context handle (destroyed with gempe_destroy on close / GC)."""
+
+    def __init__(self, handle, n, d, k, keep=()):
+        self.handle = handle
+        self.n, self.d, self.k = n, d, k
+        self._keep = keep   # allocator callbacks must outlive the context
+
+    def close(self):
+        if self.handle:
+            load().gempe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def gempe_create(row_ptr, col_idx, d: int, params: gempe_params | None = None, stream=None) -> _Ctx:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    n = len(rp) - 1
+    p = params or gempe_default_params()
+    h = ctypes.c_void_p()
+    _check(load().gempe_create(_ptr(rp), _ptr(ci) if len(ci) else ctypes.c_void_p(None), n, d,
+                               ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,))
+
+
+def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | None = None,
+                        stream=None) -> _Ctx:
+    """CSR given as torch CUDA int32 tensors."""
+    n = d_row_ptr.numel() - 1
+    nnz = d_col_idx.numel()
+    p = params or gempe_default_params()
+    h = ctypes.c_void_p()
+    _check(load().gempe_create_device(ctypes.c_void_p(d_row_ptr.data_ptr()),
+                                      ctypes.c_void_p(d_col_idx.data_ptr() if nnz else None), n, nnz, d,
+                                      ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,))
+
+
+def gempe_destroy(ctx: _Ctx) -> None:
+    ctx.close()
+
+
+def gempe_step(ctx: _Ctx, iters: int = 1) -> None:
+    _check(load().gempe_step(ctx.handle, int(iters)))
+
+
+def gempe_sweep(ctx: _Ctx, record_samples: bool = False):
+    if record_samples and ctx.k > 0:
+        out = np.empty(ctx.n * ctx.k, dtype=np.int32)
+        _check(load().gempe_sweep(ctx.handle, _ptr(out)))
+        return out.reshape(ctx.n, ctx.k)
+    _check(load().gempe_sweep(ctx.handle, ctypes.c_void_p(None)))
+    return None
+
+
+def gempe_update(ctx: _Ctx) -> None:
+    _check(load().gempe_update(ctx.handle))
+
+
+def gempe_positions(ctx: _Ctx, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((ctx.n, ctx.d), dtype=np.float32)
+    assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == ctx.n * ctx.d
+    _check(load().gempe_positions(ctx.handle, _ptr(out), out.size))
+    return out
+
+
+def gempe_positions_device(ctx: _Ctx) -> int:
+    v = ctypes.c_void_p()
+    _check(load().gempe_positions_device(ctx.handle, ctypes.byref(v)))
+    return v.value
+
+
+def gempe_set_positions(ctx: _Ctx, x) -> None:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    _check(load().gempe_set_positions(ctx.handle, _ptr(x), x.size))
+
+
+def gempe_set_state(ctx: _Ctx, sigma: float, epoch: int) -> None:
+    _check(load().gempe_set_state(ctx.handle, float(sigma), int(epoch)))
+
+
+def gempe_get_state(ctx: _Ctx):
+    s = ctypes.c_float()
+    e = ctypes.c_int32()
+    _check(load().gempe_get_state(ctx.handle, ctypes.byref(s), ctypes.byref(e)))
+    return s.value, e.value
+
+
+def gempe_accumulators(ctx: _Ctx):
+    """Returns (delta, z): delta[i] = y_i - z_i x_i (Eq. 3), z[i] = z_i."""
+    out = np.empty((ctx.n, ctx.d + 1), dtype=np.float32)
+    _check(load().gempe_accumulators(ctx.handle, _ptr(out), out.size))
+    return out[:, : ctx.d].copy(), out[:, ctx.d].copy()
+
+
+def gempe_histograms(ctx: _Ctx, bins: int):
+    out = np.empty(2 * bins, dtype=np.float32)
+    _check(load().gempe_histograms(ctx.handle, _ptr(out), out.size))
+    return out[:bins].copy(), out[bins:].copy()
+
+
+def gempe_sample(ctx: _Ctx, loss_stream: bool = False) -> np.ndarray:
+    out = np.empty(ctx.n * ctx.k, dtype=np.int32)
+    _check(load().gempe_sample(ctx.handle, 1 if loss_stream else 0, _ptr(out), out.size))
+    return out.reshape(ctx.n, ctx.k)
+
+
+def gempe_is_edge(ctx: _Ctx, pairs) -> np.ndarray:
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    out = np.empty(len(pairs), dtype=np.uint8)
+    _check(load().gempe_is_edge(ctx.handle, _ptr(pairs), len(pairs), _ptr(out)))
+    return out.astype(bool)
+
+
+def gempe_loss(ctx: _Ctx):
+    pe = ctypes.c_double()
+    s = ctypes.c_float()
+    _check(load().gempe_loss(ctx.handle, ctypes.byref(pe), ctypes.byref(s)))
+    return pe.value, s.value
+
+
+def gempe_fit_sigma(hist_e, hist_n, hist_max: float = 12.0, mu: float = 1.5, stream=None) -> float:
+    h = np.ascontiguousarray(np.concatenate([hist_e, hist_n]), dtype=np.float32)
+    out = ctypes.c_float()
+    _check(load().gempe_fit_sigma(_ptr(h), len(h) // 2, float(hist_max), float(mu),
+                                  _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def gempe_stats(ctx: _Ctx) -> dict:
+    s = gempe_stats_t()
+    _check(load().gempe_stats(ctx.handle, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in gempe_stats_t._fields_}
+
+
+def gempe_last_error() -> str:
+    return load().gempe_last_error().decode()
+
+
+def torch_allocator(device=None):
+    """(alloc, free) callbacks routing engine allocations through torch's caching allocator."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+
+    @ALLOC_FN
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:
+            return None
+
+    @FREE_FN
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _alloc, _free

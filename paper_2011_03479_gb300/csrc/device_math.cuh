@@ -1,0 +1,155 @@
+// Device arithmetic of the GEMPE epoch: counter-based random numbers, the
+// edge-set hash, and the Eq. 3-5 pair term in FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gempe {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two
+// 32x32->64 multiplications with Weyl-sequence key increments.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& r, int w) {
+    return w == 0 ? r.x : (w == 1 ? r.y : (w == 2 ? r.z : r.w));
+}
+
+// Random 32-bit word -> vertex in [0, n): floor(r * n / 2^32).
+__device__ __forceinline__ int32_t draw_vertex(uint32_t r, uint32_t n) { return (int32_t)__umulhi(r, n); }
+
+// Stream tags in the fourth counter word.
+constexpr uint32_t kTagInit = 0x0A000000u;
+constexpr uint32_t kTagEpoch = 0x0B000000u;
+constexpr uint32_t kTagLoss = 0x0E000000u;
+
+// --------------------------------------------------------------------------
+// Exact edge set: open addressing over 64-bit keys (i << 32 | j), buckets of
+// four 8-byte slots (one 32-byte sector), linear probing bucket by bucket.
+// --------------------------------------------------------------------------
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long edge_key(int32_t i, int32_t j) {
+    return ((unsigned long long)(uint32_t)i << 32) | (uint32_t)j;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood, OOPSLA 2014) as the bucket hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Membership of key in the table of (bucket_mask + 1) buckets.
+__device__ __forceinline__ bool hash_contains(const unsigned long long* __restrict__ keys,
+                                              unsigned long long bucket_mask, unsigned long long key) {
+    unsigned long long b = mix64(key) & bucket_mask;
+    for (unsigned long long probe = 0; probe <= bucket_mask; ++probe) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(keys + 4 * b);
+        const ulonglong2 s01 = __ldg(p), s23 = __ldg(p + 1);
+        if (s01.x == key || s01.y == key || s23.x == key || s23.y == key) return true;
+        if (s01.x == kEmptyKey || s01.y == kEmptyKey || s23.x == kEmptyKey || s23.y == kEmptyKey)
+            return false;
+        b = (b + 1) & bucket_mask;
+    }
+    return false;
+}
+
+// --------------------------------------------------------------------------
+// Pair arithmetic (Sec. II.B/C) in FP32.
+//
+// With u = (delta - mu)/sigma, the edge sigmoid is s+ = Q(u) (upper normal
+// tail) and the non-edge one s- = Q(-u).  Writing v = u for an edge and
+// v = -u for a non-edge, both cases use h = phi(v)/Q(v) and T = h - v > 0:
+//   dl'(delta)  = +-h / (sigma ln2)            (+ edge, - non-edge)
+//   w (derived) = h T / (2 ln2 sigma^2)        (matches dl'' as Sec. II.C asks)
+//   w (printed) = h (h + T) / (2 ln2 sigma^2)  (Eq. 4 with its first term as printed)
+//   d           = delta - dl' / (2 w)          (Eq. 5, both readings)
+// Eq. 3 adds w (x_j + s (x_i - x_j)) to y_i, s = d/delta.  The engine keeps
+// y_i - z_i x_i instead of y_i, i.e. adds c (x_i - x_j) with
+//   c = w (s - 1) = -dl' / (2 delta),
+// which avoids the cancellation of forming y_i - z_i x_i at the end; when
+// delta = 0, or when d < 0 is clamped to 0, s = 0 and c = -w.
+// --------------------------------------------------------------------------
+struct PairConsts {
+    float mu, inv_sigma;
+    float w_scale;    // 1 / (2 ln2 sigma^2)
+    float g_scale;    // 1 / (2 ln2 sigma)
+    int printed;      // w_formula == 1
+    int clamp;        // clamp_neg_d
+};
+
+__device__ __forceinline__ PairConsts make_pair_consts(float mu, float sigma, int printed, int clamp) {
+    PairConsts k;
+    const float ln2 = 0.69314718055994531f;
+    k.mu = mu;
+    k.inv_sigma = 1.0f / sigma;
+    k.w_scale = 1.0f / (2.0f * ln2 * sigma * sigma);
+    k.g_scale = 1.0f / (2.0f * ln2 * sigma);
+    k.printed = printed;
+    k.clamp = clamp;
+    return k;
+}
+
+// h(v) = phi(v)/Q(v) and T(v) = h(v) - v.  Below v = 4 through erfcx
+// (Q(v) = 1/2 exp(-v^2/2) erfcx(v/sqrt2), so h = sqrt(2/pi) / erfcx(v/sqrt2));
+// from v = 4 on, T by Laplace's continued fraction
+// T = 1/(v + 2/(v + 3/(v + ...))) truncated after the 12th partial
+// denominator (relative truncation error < 3e-8 for v >= 4), so that T never
+// comes from the difference of two nearly equal numbers.
+__device__ __forceinline__ void mills(float v, float& h, float& T) {
+    if (v < 4.0f) {
+        const float ex = erfcxf(v * 0.70710678118654752f);
+        h = 0.79788456080286536f / ex;
+        T = h - v;
+    } else {
+        float t = v;
+#pragma unroll
+        for (int k = 12; k >= 2; --k) t = v + __fdividef((float)k, t);
+        T = 1.0f / t;
+        h = v + T;
+    }
+}
+
+struct PairTerm {
+    float c;   // coefficient of (x_self - x_other)
+    float w;   // weight added to z_self
+};
+
+__device__ __forceinline__ PairTerm pair_term(float delta, bool edge, const PairConsts& K) {
+    const float u = (delta - K.mu) * K.inv_sigma;
+    const float v = edge ? u : -u;
+    float h, T;
+    mills(v, h, T);
+    const float w = h * (K.printed ? (h + T) : T) * K.w_scale;
+    const float g = h * K.g_scale;                   // |dl'| / 2
+    // d = delta - g/w (edge) < 0  <=>  g > w delta
+    const bool s_zero = !(delta > 0.0f) || (K.clamp && edge && g > w * delta);
+    PairTerm r;
+    r.w = w;
+    r.c = s_zero ? -w : (edge ? -g : g) / delta;
+    return r;
+}
+
+// -log2 Q(v): the description length of an edge (v = u) or non-edge (v = -u).
+__device__ __forceinline__ float neg_log2_Q(float v) {
+    const float inv_ln2 = 1.4426950408889634f;
+    if (v > 0.0f) {
+        const float ex = erfcxf(v * 0.70710678118654752f);
+        return (0.5f * v * v - logf(0.5f * ex)) * inv_ln2;
+    }
+    return -log1pf(-0.5f * erfcf(-v * 0.70710678118654752f)) * inv_ln2;
+}
+
+}  // namespace gempe

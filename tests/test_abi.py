@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports what include/gempe.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(gempe_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_calls():
+    names = _declared_functions()
+    for required in ("gempe_create", "gempe_step", "gempe_positions", "gempe_loss", "gempe_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2011_03479_gb300 import binding
+    lib = binding.load()
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_are_the_papers():
+    from paper_2011_03479_gb300 import binding
+    p = binding.gempe_default_params()
+    assert p.mu == 1.5 and p.sigma0 == 1.0          # Sec. III.F, Fig. 4
+    assert p.sigma_every == 1 and p.neg_per_vertex == 5 and p.max_retries == 32
+    assert p.symmetric_neg == 1 and p.w_formula == 0 and p.clamp_neg_d == 1
+    assert p.hist_bins == 1024 and p.hist_max == 12.0 and p.seed == 0x6E6D7065
+
+
+def _status(fn, *args):
+    from paper_2011_03479_gb300 import binding
+    h = ctypes.c_void_p()
+    return fn(*args, ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("case", ["asym", "loop", "dup", "range", "unsorted"])
+def test_invalid_graphs_rejected_on_host(case):
+    from paper_2011_03479_gb300 import binding
+    lib = binding.load()
+    rows = {"asym": [[1], [], []], "loop": [[0, 1], [0], []], "dup": [[1, 1], [0, 0], []],
+            "range": [[5], [0], []], "unsorted": [[2, 1], [0], [0]]}[case]
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array(sum(rows, []), dtype=np.int32)
+    p = binding.gempe_default_params()
+    st, h = _status(lib.gempe_create, ci.ctypes.data and ctypes.c_void_p(rp.ctypes.data),
+                    ctypes.c_void_p(ci.ctypes.data), len(rows), 2, ctypes.byref(p), None)
+    assert st == -2, binding.gempe_last_error()
+    assert not h.value
+
+
+def test_invalid_args_rejected_on_host():
+    from paper_2011_03479_gb300 import binding
+    lib = binding.load()
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([1, 0], dtype=np.int32)
+    for d, k in ((5, 5), (0, 5), (2, 33), (2, -1)):
+        p = binding.gempe_default_params(neg_per_vertex=k)
+        st, _ = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data),
+                        2, d, ctypes.byref(p), None)
+        assert st == -1
+    p = binding.gempe_default_params()
+    st, _ = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data),
+                    1, 2, ctypes.byref(p), None)
+    assert st == -1
+    with pytest.raises(binding.GempeError):
+        binding.gempe_create(np.array([0, 1, 1], np.int32), np.array([1], np.int32), 2)
+
+
+def test_generated_graphs_are_valid_csr(sbm_1000):
+    from paper_2011_03479_gb300 import inputs
+    for rp, ci in ((sbm_1000["row_ptr"], sbm_1000["col_idx"]), inputs.rmat(10, 8, seed=3),
+                   inputs.barabasi_albert(2000, 3, seed=4)):
+        n = len(rp) - 1
+        assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and rp[-1] == len(ci)
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        assert np.all(ci != rows)
+        for i in range(0, n, max(1, n // 200)):
+            r = ci[rp[i]:rp[i + 1]]
+            assert np.all(np.diff(r) > 0)
+        a = set(zip(rows.tolist(), ci.tolist()))
+        assert all((j, i) in a for i, j in a)

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: initial positions, membership and sampled pairs bit-exact; per-step
+FP32 results within 1e-4 relative (per vertex, against
+max(|ref|, 1e-6 * mean |ref|)); the slope fit within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from conftest import gpu_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL = 1e-4
+
+
+def _rel_err_rows(got, ref):
+    """Per-row ||got-ref|| / max(||ref||, 1e-6 mean ||ref||)."""
+    got = np.asarray(got, np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    nr = np.linalg.norm(ref, axis=1)
+    floor = 1e-6 * max(nr.mean(), 1e-300)
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(nr, floor)
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2011_03479_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def rmat_s12():
+    from paper_2011_03479_gb300 import inputs
+    return inputs.rmat(12, 16, seed=77)
+
+
+def _ctx(B, rp, ci, d, **kw):
+    p = B.gempe_default_params(**kw)
+    return B.gempe_create(rp, ci, d, p), p
+
+
+# ---------------------------------------------------------------------------
+def test_init_positions_bit_exact(B, O, sbm_1000):
+    for d in (2, 3, 64):
+        ctx, p = _ctx(B, sbm_1000["row_ptr"], sbm_1000["col_idx"], d, seed=12345)
+        with ctx:
+            np.testing.assert_array_equal(B.gempe_positions(ctx), O.init_positions(1000, d, 12345))
+
+
+def test_membership_all_pairs(B, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    n = len(rp) - 1
+    dense = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        dense[i, ci[rp[i]:rp[i + 1]]] = True
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    with _ctx(B, rp, ci, 2)[0] as ctx:
+        got = B.gempe_is_edge(ctx, np.stack([ii.ravel(), jj.ravel()], 1))
+    np.testing.assert_array_equal(got.reshape(n, n), dense)
+
+
+def test_membership_rmat_random_pairs(B, rmat_s12):
+    rp, ci = rmat_s12
+    n = len(rp) - 1
+    rng = np.random.default_rng(3)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    edges = np.stack([rows, ci], 1)
+    rand = rng.integers(0, n, size=(200000, 2))
+    pairs = np.concatenate([edges, rand]).astype(np.int32)
+    keyset = set((rows.astype(np.int64) * n + ci).tolist())
+    ref = np.array([a * n + b in keyset for a, b in pairs.tolist()])
+    with _ctx(B, rp, ci, 2)[0] as ctx:
+        np.testing.assert_array_equal(B.gempe_is_edge(ctx, pairs), ref)
+
+
+@pytest.mark.parametrize("epoch", [0, 7, 123456])
+def test_sampler_bit_exact(B, O, rmat_s12, epoch):
+    rp, ci = rmat_s12
+    for k in (1, 10, 32):
+        ctx, p = _ctx(B, rp, ci, 2, neg_per_vertex=k, seed=0xABCDEF0123)
+        with ctx:
+            B.gempe_set_state(ctx, 1.0, epoch)
+            for loss_stream in (False, True):
+                got = B.gempe_sample(ctx, loss_stream)
+                ref = O.sample(rp, ci, epoch, p.seed, k, loss_stream=loss_stream)
+                np.testing.assert_array_equal(got, ref)
+
+
+def _sweep_compare(B, O, rp, ci, d, x, sigma, epoch, **kw):
+    ctx, p = _ctx(B, rp, ci, d, **kw)
+    with ctx:
+        B.gempe_set_positions(ctx, x)
+        B.gempe_set_state(ctx, sigma, epoch)
+        samples = B.gempe_sweep(ctx, record_samples=True)
+        delta, z = B.gempe_accumulators(ctx)
+        he, hn = B.gempe_histograms(ctx, p.hist_bins)
+        B.gempe_update(ctx)
+        xn = B.gempe_positions(ctx)
+        s_new, e_new = B.gempe_get_state(ctx)
+    ref = O.epoch(rp, ci, x.astype(np.float64), sigma, epoch, p.seed, p.neg_per_vertex,
+                  mu=p.mu, max_retries=p.max_retries, symmetric=p.symmetric_neg,
+                  w_formula=p.w_formula, clamp_neg_d=p.clamp_neg_d, z_min=p.z_min,
+                  hist_bins=p.hist_bins, hist_max=p.hist_max)
+    if p.neg_per_vertex:
+        np.testing.assert_array_equal(samples, ref["samples"])
+    return dict(delta=delta, z=z, he=he, hn=hn, xn=xn, sigma=s_new, epoch=e_new, ref=ref, p=p)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 16, 32, 64, 128])
+def test_sweep_and_update_parity(B, O, sbm_1000, d):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    rng = np.random.default_rng(d)
+    x = (rng.standard_normal((1000, d)) * 1.2).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, d, x, 0.7, 5, neg_per_vertex=5)
+    ref = r["ref"]
+    assert _rel_err_rows(r["delta"], ref["delta"]).max() <= TOL
+    assert _rel_err_rows(r["z"], ref["z"]).max() <= TOL
+    assert _rel_err_rows(r["xn"], ref["x_new"]).max() <= TOL
+    assert r["epoch"] == 6
+
+
+@pytest.mark.parametrize("w_formula,clamp,symmetric", [(1, 1, 1), (0, 0, 1), (0, 1, 0)])
+def test_sweep_readings(B, O, sbm_1000, w_formula, clamp, symmetric):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(9).uniform(-2, 2, (1000, 2))).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, 2, x, 1.3, 3, neg_per_vertex=7, w_formula=w_formula,
+                       clamp_neg_d=clamp, symmetric_neg=symmetric)
+    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
+
+
+@pytest.mark.parametrize("sigma", [0.02, 0.15, 3.0])
+def test_sweep_extreme_slopes(B, O, sbm_1000, sigma):
+    # small sigma drives |u| far into both tails (continued fraction, underflowed weights)
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(1).uniform(-3, 3, (1000, 2))).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, 2, x, sigma, 0, neg_per_vertex=5)
+    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
+    assert _rel_err_rows(r["xn"], r["ref"]["x_new"]).max() <= TOL
+
+
+def test_histograms_and_sigma_fit(B, O, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(2).uniform(-2, 2, (1000, 2))).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, 2, x, 0.9, 0, neg_per_vertex=5)
+    ref = r["ref"]
+    m = len(ci) // 2
+    assert r["he"].sum() == m
+    # a pair may land in a neighbouring bin when its FP32 distance rounds across a bin edge
+    assert np.abs(r["he"] - ref["hist_e"]).sum() <= 2 * 4
+    assert r["hn"].sum() == pytest.approx(ref["hist_n"].sum(), rel=1e-5)
+    # device slope fit on its own histogram vs the oracle's bisection on the same one
+    s_dev = B.gempe_fit_sigma(r["he"], r["hn"])
+    s_ref = O.sigma_fit(r["he"].astype(np.float64), r["hn"].astype(np.float64))
+    assert s_dev == pytest.approx(s_ref, rel=TOL)
+    assert r["sigma"] == pytest.approx(s_dev, rel=1e-6)
+
+
+def test_sigma_fit_parity_many_histograms(B, O):
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        he = np.zeros(1024); hn = np.zeros(1024)
+        ce = rng.uniform(0.1, 2.0); cn = rng.uniform(1.0, 8.0)
+        de = np.clip(rng.normal(ce, 0.5, 5000), 0, 11.99)
+        dn = np.clip(rng.normal(cn, 1.5, 5000), 0, 11.99)
+        np.add.at(he, (de / (12 / 1024)).astype(int), 1.0)
+        np.add.at(hn, (dn / (12 / 1024)).astype(int), rng.uniform(10, 1000))
+        he32, hn32 = he.astype(np.float32), hn.astype(np.float32)
+        s_dev = B.gempe_fit_sigma(he32, hn32)
+        s_ref = O.sigma_fit(he32.astype(np.float64), hn32.astype(np.float64))
+        assert s_dev == pytest.approx(s_ref, rel=TOL)
+
+
+def test_loss_parity(B, O, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(4).uniform(-2, 2, (1000, 2))).astype(np.float32)
+    ctx, p = _ctx(B, rp, ci, 2, neg_per_vertex=8)
+    with ctx:
+        B.gempe_set_positions(ctx, x)
+        B.gempe_set_state(ctx, 0.6, 42)
+        pe, s = B.gempe_loss(ctx)
+    ref = O.loss_sampled(rp, ci, x, 0.6, 42, p.seed, 8)
+    assert s == pytest.approx(0.6)
+    assert pe == pytest.approx(ref, rel=1e-5)
+
+
+def test_rmat_epoch_parity_full(B, O):
+    """The bench workload's graph (R-MAT scale 16, ef 16, k 10): one epoch, all vertices."""
+    from paper_2011_03479_gb300 import inputs
+    w = inputs.rmat_s16()
+    rp, ci = w["row_ptr"], w["col_idx"]
+    x = O.init_positions(len(rp) - 1, 2, inputs.EMBED_SEED) * np.float32(2.5)
+    r = _sweep_compare(B, O, rp, ci, 2, x, 0.8, 17, neg_per_vertex=10, seed=inputs.EMBED_SEED)
+    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
+    assert _rel_err_rows(r["xn"], r["ref"]["x_new"]).max() <= TOL
+
+
+def test_edge_cases(B, O):
+    # isolated vertices, a near-complete row (exhaustion), n = 2, k = 0
+    n = 40
+    rows = [list(range(1, n))] + [[0] for _ in range(1, n - 5)] + [[] for _ in range(5)]
+    rows[0] = list(range(1, n - 5))
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array(sum(rows, []), dtype=np.int32)
+    x = np.random.default_rng(0).uniform(-1, 1, (n, 2)).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, 2, x, 1.0, 0, neg_per_vertex=32, max_retries=4)
+    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    r = _sweep_compare(B, O, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), 2,
+                       np.array([[0, 0], [0.3, 0.4]], np.float32), 1.0, 0, neg_per_vertex=3)
+    np.testing.assert_allclose(r["xn"], r["ref"]["x_new"], rtol=TOL, atol=1e-7)
+    r = _sweep_compare(B, O, rp, ci, 2, x, 1.0, 0, neg_per_vertex=0)
+    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+
+
+def test_coincident_points(B, O, sbm_1000):
+    # delta = 0 pairs: s = 0 in Eq. 3, no NaN
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = np.zeros((1000, 2), np.float32)
+    x[::2] = 0.5
+    r = _sweep_compare(B, O, rp, ci, 2, x, 1.0, 0, neg_per_vertex=5)
+    assert np.isfinite(r["xn"]).all()
+    assert _rel_err_rows(r["xn"], r["ref"]["x_new"]).max() <= TOL
+
+
+def test_step_equals_sweep_update(B, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    with _ctx(B, rp, ci, 2)[0] as a, _ctx(B, rp, ci, 2)[0] as b:
+        B.gempe_step(a, 3)
+        for _ in range(3):
+            B.gempe_sweep(b)
+            B.gempe_update(b)
+        xa, xb = B.gempe_positions(a), B.gempe_positions(b)
+        assert B.gempe_get_state(a)[1] == 3 == B.gempe_get_state(b)[1]
+    # the partner updates use atomics: equal up to FP32 summation order
+    assert _rel_err_rows(xa, xb).max() <= 1e-3
+
+
+def test_full_run_loss_matches_oracle(B, O, sbm_1000):
+    """200 epochs of the SBM drawing: final sampled PE within 1% of the oracle's run."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    ctx, p = _ctx(B, rp, ci, 2, neg_per_vertex=5)
+    with ctx:
+        x0 = B.gempe_positions(ctx)
+        B.gempe_step(ctx, 200)
+        pe_gpu, s_gpu = B.gempe_loss(ctx)
+    xr, sr, _ = O.run(rp, ci, x0, 1.0, 200, p.seed, 5)
+    pe_ref = O.loss_sampled(rp, ci, xr, sr, 200, p.seed, 5)
+    assert pe_gpu == pytest.approx(pe_ref, rel=0.01)
