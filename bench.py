@@ -229,8 +229,8 @@ def run_gempe(args):
         s1 = B.gempe_stats(ctx)
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     sweep_ms = [a.elapsed_time(b) for a, b, c in ev]
-    accepted = s1["accepted"] - s0["accepted"]
-    draws = s1["draws"] - s0["draws"]
+    accepted = s1["used"] - s0["used"]          # sampled non-edges the timed sweeps consumed
+    draws = (s1["draws"] - s0["draws"]) * accepted / max(1, s1["accepted"] - s0["accepted"])
     pairs = args.steps * m + accepted
     t_total = sum(step_ms) / 1e3
     if world > 1:
@@ -254,26 +254,26 @@ def run_gempe(args):
 
     def job():
         c = B.gempe_create(rp_pin, ci_pin, d, p, stream=stream)
-        st0 = B.gempe_stats(c)
         B.gempe_step(c, epochs)
         B.gempe_positions(c, out_pin)
-        st1 = B.gempe_stats(c)
+        used = B.gempe_stats(c)["used"]
         c.close()
-        return epochs * m + (st1["accepted"] - st0["accepted"])
+        return epochs * m + used
 
-    job()   # warm-up (builds nothing new: the library is loaded, the GPU is warm)
-    torch.cuda.synchronize()
+    if e2e_jobs > 0:
+        job()   # warm-up (builds nothing new: the library is loaded, the GPU is warm)
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_pairs = sum(job() for _ in range(e2e_jobs))
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    e2e = {"value": e2e_pairs / e2e_t, "unit": UNIT,
+    e2e_t = max(time.perf_counter() - t0, 1e-9)
+    e2e = {"value": e2e_pairs / e2e_t if e2e_jobs else None, "unit": UNIT,
            "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes),
            "d2h_bytes_per_step": int(out_pin.nbytes),
            "step": f"one {epochs}-epoch embedding job: gempe_create from pinned host CSR, "
                    f"gempe_step({epochs}), gempe_positions to pinned host memory",
-           "ms_per_job": 1e3 * e2e_t / e2e_jobs}
-    if world > 1:
+           "ms_per_job": 1e3 * e2e_t / e2e_jobs if e2e_jobs else None}
+    if world > 1 and e2e_jobs:
         import torch.distributed as dist
         v = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
         dist.all_reduce(v, op=dist.ReduceOp.SUM)
@@ -299,6 +299,7 @@ def run_gempe(args):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "pairs_per_epoch": pairs / args.steps,
+        "sigma_fit_steps_last": s1["sigma_iters"],
         "sweep_ms": statistics.mean(sweep_ms),
         "update_ms": statistics.mean(step_ms) - statistics.mean(sweep_ms),
         "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,

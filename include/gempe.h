@@ -75,12 +75,14 @@ typedef struct gempe_params {
 typedef struct gempe_stats_t {
     int32_t epoch;                 /* epochs completed */
     float sigma;                   /* current slope */
-    uint64_t accepted;             /* sampled non-edges used (cumulative) */
-    uint64_t rejected;             /* draws that hit an edge or the anchor itself */
-    uint64_t exhausted;            /* samples dropped after max_retries rejected draws */
-    uint64_t draws;                /* accepted + rejected */
+    uint64_t accepted;             /* sampled non-edges drawn (cumulative; the sampler runs */
+    uint64_t rejected;             /*   one epoch ahead of the sweep): draws that hit an edge */
+    uint64_t exhausted;            /*   or the anchor, samples dropped after max_retries, */
+    uint64_t draws;                /*   accepted + rejected */
+    uint64_t used;                 /* sampled non-edges the sweeps consumed (cumulative) */
     int64_t n_edges;               /* m, undirected */
     int32_t n, d, k;
+    int32_t sigma_iters;           /* root-finding steps of the last slope fit */
 } gempe_stats_t;
 
 typedef struct gempe_ctx gempe_ctx;
@@ -144,8 +146,9 @@ gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
  * update is x_i + that / z_i = y_i / z_i), then z_i.  Synchronises. */
 gempe_status gempe_accumulators(gempe_ctx* ctx, float* host_out, size_t count);
 
-/* Copy the distance histograms to host float[2*B]: B edge bins, then B
- * non-edge bins (Sec. III.F).  Synchronises. */
+/* Copy the distance histograms to host float[2*B]: B edge bins (counts),
+ * then B non-edge bins (sums of sample weights, kept on the device in fixed
+ * point with 2^-20 resolution) (Sec. III.F).  Synchronises. */
 gempe_status gempe_histograms(gempe_ctx* ctx, float* host_out, size_t count);
 
 /* Draw the sampled non-edges of the current epoch without using them:

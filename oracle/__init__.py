@@ -58,7 +58,7 @@ def _load():
         "orc_sample": (None, [_i32p, _i32p, I32, I32, U64, I32, I32, I32, _i32p]),
         "orc_epoch": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
                                  I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
-                                 _f64p, _i32p, _i64p]),
+                                 _f64p, _i32p, _i64p, _f64p]),
         "orc_edge_terms_edgelist": (None, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, I32,
                                            _f64p, _f64p]),
         "orc_edge_terms_csr": (None, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, I32,
@@ -144,7 +144,9 @@ def sample(row_ptr, col_idx, epoch, seed, k, max_retries=MAX_RETRIES, loss_strea
 def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES,
           symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
           hist_max=HIST_MAX):
-    """One epoch of Fig. 4; returns a dict of FP64 results."""
+    """One epoch of Fig. 4; returns a dict of FP64 results.  ``abs_terms[i]`` is the
+    sum of the sizes of the pair terms of y_i - z_i x_i (the scale of that sum's
+    rounding when its terms cancel)."""
     n = len(row_ptr) - 1
     x = _f64(x)
     d = x.shape[1]
@@ -152,14 +154,15 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
     he = np.zeros(hist_bins); hn = np.zeros(hist_bins)
     smp = np.zeros(n * max(k, 1), dtype=np.int32)
     st = np.zeros(4, dtype=np.int64)
+    absd = np.zeros(n)
     rc = _load().orc_epoch(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
                            max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
-                           hist_max, y, z, xn, he, hn, smp, st)
+                           hist_max, y, z, xn, he, hn, smp, st, absd)
     if rc != 0:
         raise MemoryError("oracle epoch failed")
     return dict(y=y, z=z, x_new=xn, hist_e=he, hist_n=hn, samples=smp[: n * k].reshape(n, k),
                 accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]), draws=int(st[3]),
-                delta=y - z[:, None] * x)
+                delta=y - z[:, None] * x, abs_terms=absd)
 
 
 def edge_terms(row_ptr, col_idx, x, sigma, mu=MU, w_formula=0, clamp_neg_d=1, form="csr"):

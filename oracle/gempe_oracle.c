@@ -213,6 +213,11 @@ static double dist(const double* x, int32_t d, int64_t a, int64_t b) {
     return sqrt(s);
 }
 
+/* absd (optional) collects |w (x_b + s (x_a - x_b)) - w x_a| = w |s - 1| delta,
+ * the size of the pair's term in y_a - z_a x_a: the scale against which the
+ * rounding of a cancelling sum is judged. */
+static double* g_absd = NULL;
+
 static void add_wm_term(double* y, double* z, const double* x, int32_t d, int64_t a, int64_t b,
                         double delta, double dd, double w) {
     if (!(w > 0.0)) return;   /* an underflowed weight contributes nothing */
@@ -220,6 +225,7 @@ static void add_wm_term(double* y, double* z, const double* x, int32_t d, int64_
     for (int32_t c = 0; c < d; ++c)
         y[a * d + c] += w * (x[b * d + c] + s * (x[a * d + c] - x[b * d + c]));
     z[a] += w;
+    if (g_absd) g_absd[a] += w * fabs(s - 1.0) * delta;
 }
 
 static int32_t hist_bin(double delta, int32_t B, double hist_max) {
@@ -264,9 +270,11 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
               int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
               double* y, double* z, double* x_new, double* hist_e, double* hist_n,
-              int32_t* samples_out, int64_t* stats) {
+              int32_t* samples_out, int64_t* stats, double* absd) {
     int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
     if (!smp) return -1;
+    g_absd = absd;
+    if (absd) memset(absd, 0, sizeof(double) * (size_t)n);
     memset(y, 0, sizeof(double) * (size_t)n * d);          /* zero numerators ... */
     memset(z, 0, sizeof(double) * (size_t)n);              /* ... and denominators */
     if (hist_e) memset(hist_e, 0, sizeof(double) * (size_t)B);
@@ -306,6 +314,7 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
             x_new[(int64_t)i * d + c] = (z[i] >= z_min) ? y[(int64_t)i * d + c] / z[i]
                                                          : x[(int64_t)i * d + c];
     if (stats) { stats[0] = accepted; stats[1] = rejected; stats[2] = exhausted; stats[3] = accepted + rejected; }
+    g_absd = NULL;
     free(smp);
     return 0;
 }
@@ -456,7 +465,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
     for (int32_t e = 0; e < epochs; ++e) {
         int32_t ep = epoch0 + e;
         orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
-                  w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st);
+                  w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL);
         memcpy(x, xn, nd * sizeof(double));
         if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0)
             *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);

@@ -56,10 +56,12 @@ class gempe_stats_t(ctypes.Structure):
         ("rejected", ctypes.c_uint64),
         ("exhausted", ctypes.c_uint64),
         ("draws", ctypes.c_uint64),
+        ("used", ctypes.c_uint64),
         ("n_edges", ctypes.c_int64),
         ("n", ctypes.c_int32),
         ("d", ctypes.c_int32),
         ("k", ctypes.c_int32),
+        ("sigma_iters", ctypes.c_int32),
     ]
 
 

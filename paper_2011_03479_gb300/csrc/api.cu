@@ -44,6 +44,10 @@ struct gempe_ctx {
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;          // the sampler of the next epoch runs here, beside the sweep
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool primed = false;                  // samples of the current epoch are in the buffer
+    bool sampled_ahead = false;           // the next epoch's sampler has been launched
     // device memory
     int32_t* row_ptr = nullptr;
     int32_t* col_idx = nullptr;
@@ -51,11 +55,19 @@ struct gempe_ctx {
     unsigned long long bucket_mask = 0;
     float* x = nullptr;
     float* acc = nullptr;
-    float* hist = nullptr;
+    // distance histograms, one allocation: hist_d [bins] u64, hist_e, hist_c [bins] u32, hist_x [bins] f32
+    void* hist = nullptr;
+    size_t hist_bytes = 0;
+    unsigned long long* hist_d = nullptr;
+    unsigned int* hist_e = nullptr;
+    unsigned int* hist_c = nullptr;
+    float* hist_x = nullptr;
     DevState* st = nullptr;
     int4* items = nullptr;
     int32_t n_items = 0;
-    int32_t* scratch_i32 = nullptr;   // n*k sample records / flags
+    int32_t* scratch_i32 = nullptr;   // n*k inspection samples / flags
+    int32_t* samples = nullptr;       // [2][n*k] sampled partners, buffer = epoch & 1
+    int sampler_grid = 0;
     int sweep_grid = 0, update_grid = 0;
     bool swept = false;               // a sweep ran without the update that clears its sums
     cudaGraph_t graph = nullptr;
@@ -85,7 +97,7 @@ struct gempe_ctx {
 
 namespace {
 
-EpochArgs epoch_args(const gempe_ctx* c, int32_t* record) {
+EpochArgs epoch_args(const gempe_ctx* c) {
     EpochArgs a{};
     a.row_ptr = c->row_ptr;
     a.col_idx = c->col_idx;
@@ -93,7 +105,10 @@ EpochArgs epoch_args(const gempe_ctx* c, int32_t* record) {
     a.bucket_mask = c->bucket_mask;
     a.x = c->x;
     a.acc = c->acc;
-    a.hist = c->hist;
+    a.hist_e = c->hist_e;
+    a.hist_c = c->hist_c;
+    a.hist_d = c->hist_d;
+    a.hist_x = c->hist_x;
     a.st = c->st;
     a.items = c->items;
     a.n_items = c->n_items;
@@ -110,7 +125,7 @@ EpochArgs epoch_args(const gempe_ctx* c, int32_t* record) {
     a.hist_scale = (float)c->p.hist_bins / c->p.hist_max;
     a.key_lo = (uint32_t)c->p.seed;
     a.key_hi = (uint32_t)(c->p.seed >> 32);
-    a.record = record;
+    a.samples = c->samples;
     return a;
 }
 
@@ -118,7 +133,11 @@ UpdateArgs update_args(const gempe_ctx* c) {
     UpdateArgs u{};
     u.x = c->x;
     u.acc = c->acc;
-    u.hist = c->hist;
+    u.hist_e = c->hist_e;
+    u.hist_c = c->hist_c;
+    u.hist_d = c->hist_d;
+    u.hist_x = c->hist_x;
+    u.k = c->k;
     u.st = c->st;
     u.n = c->n;
     u.d = c->d;
@@ -174,9 +193,43 @@ gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n) {
     return GEMPE_OK;
 }
 
-// Work units of the sweep: each vertex's CSR slots in chunks of kEdgeChunk,
-// the last chunk also carrying the vertex's sampled non-edges.
-std::vector<int4> build_items(const int32_t* rp, int32_t n) {
+// Work units of the packed sweep (d <= 4): runs of up to 32 consecutive
+// vertices with at most kUnitPairs edge + sample slots in total; a vertex with
+// more is cut into kUnitPairs-slot chunks of its row, the last chunk (at most
+// kUnitPairs slots plus its k samples) carrying the samples.
+std::vector<int4> build_packed_units(const int32_t* rp, int32_t n, int32_t k) {
+    std::vector<int4> units;
+    units.reserve((size_t)n / 4 + (size_t)(rp[n] / kUnitPairs) + 16);
+    const int smp = k > 0 ? kUnitHasSamples : 0;
+    int32_t i = 0;
+    while (i < n) {
+        const int32_t deg = rp[i + 1] - rp[i];
+        if (deg + k > kUnitPairs) {
+            int32_t e = 0;
+            while (deg - e > kUnitPairs) {
+                units.push_back(make_int4(i, 1, e, e + kUnitPairs));
+                e += kUnitPairs;
+            }
+            units.push_back(make_int4(i, 1, e, deg | smp));
+            ++i;
+            continue;
+        }
+        const int32_t v0 = i;
+        int32_t pairs = 0;
+        while (i < n && i - v0 < 32) {
+            const int32_t di = rp[i + 1] - rp[i] + k;
+            if (di > kUnitPairs || pairs + di > kUnitPairs) break;
+            pairs += di;
+            ++i;
+        }
+        units.push_back(make_int4(v0, i - v0, -1, smp));
+    }
+    return units;
+}
+
+// Work units of the per-unit sweep (d >= 8): each vertex's CSR slots in
+// chunks of kEdgeChunk, the last chunk also carrying the vertex's samples.
+std::vector<int4> build_chunk_units(const int32_t* rp, int32_t n) {
     std::vector<int4> items;
     items.reserve((size_t)n + (size_t)(rp[n] / kEdgeChunk) + 1);
     for (int32_t i = 0; i < n; ++i) {
@@ -184,7 +237,7 @@ std::vector<int4> build_items(const int32_t* rp, int32_t n) {
         const int32_t chunks = std::max<int32_t>(1, (deg + kEdgeChunk - 1) / kEdgeChunk);
         for (int32_t c = 0; c < chunks; ++c) {
             const int32_t p0 = c * kEdgeChunk, p1 = std::min(deg, (c + 1) * kEdgeChunk);
-            items.push_back(make_int4(i, p0, p1, c == chunks - 1 ? 1 : 0));
+            items.push_back(make_int4(i, 1, p0, p1 | (c == chunks - 1 ? kUnitHasSamples : 0)));
         }
     }
     return items;
@@ -210,13 +263,19 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
         if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
         if (c->graph) cudaGraphDestroy(c->graph);
         if (c->stream) cudaStreamSynchronize(c->stream);
+        if (c->side) cudaStreamSynchronize(c->side);
         c->release_all();
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        if (c->join_ev) cudaEventDestroy(c->join_ev);
+        if (c->side) cudaStreamDestroy(c->side);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return st;
     };
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    e = ensure_mills_table();
+    if (e != cudaSuccess) return bail(cuda_fail(e, "Mills table"));
     e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
     if (stream) {
@@ -226,12 +285,21 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
         if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
         c->own_stream = true;
     }
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
 
     // exact edge set: 2*nnz slots rounded up to a power of two (load <= 1/2), 4-slot buckets
     unsigned long long slots = 16;
     while (slots < 2ull * (unsigned long long)nnz) slots <<= 1;
     c->bucket_mask = slots / 4 - 1;
-    std::vector<int4> items = build_items(rp_host, n);
+    // the per-block sums of sampled anchors' degrees are 32-bit: k * nnz must stay below 2^32
+    if ((unsigned long long)p->neg_per_vertex * (unsigned long long)nnz >= (1ull << 32))
+        return bail(fail(GEMPE_E_INVALID_ARG, "neg_per_vertex * nnz must be below 2^32"));
+    std::vector<int4> items = (d <= kPackedMaxDim) ? build_packed_units(rp_host, n, p->neg_per_vertex)
+                                                   : build_chunk_units(rp_host, n);
     c->n_items = (int32_t)items.size();
 
     c->row_ptr = (int32_t*)c->alloc(sizeof(int32_t) * ((size_t)n + 1));
@@ -239,10 +307,20 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     c->keys = (unsigned long long*)c->alloc(sizeof(unsigned long long) * slots);
     c->x = (float*)c->alloc(sizeof(float) * (size_t)n * d);
     c->acc = (float*)c->alloc(sizeof(float) * (size_t)n * c->acc_stride);
-    c->hist = (float*)c->alloc(sizeof(float) * 2 * (size_t)p->hist_bins);
+    const size_t B = (size_t)p->hist_bins;
+    c->hist_bytes = B * (sizeof(unsigned long long) + 2 * sizeof(unsigned int) + sizeof(float));
+    c->hist = c->alloc(c->hist_bytes);
+    if (c->hist) {
+        c->hist_d = (unsigned long long*)c->hist;
+        c->hist_e = (unsigned int*)(c->hist_d + B);
+        c->hist_c = c->hist_e + B;
+        c->hist_x = (float*)(c->hist_c + B);
+    }
     c->st = (DevState*)c->alloc(sizeof(DevState));
     c->items = (int4*)c->alloc(sizeof(int4) * items.size());
     c->scratch_i32 = (int32_t*)c->alloc(sizeof(int32_t) * std::max<size_t>((size_t)n * c->k, 1));
+    c->samples = (int32_t*)c->alloc(sizeof(int32_t) * std::max<size_t>(2 * (size_t)n * c->k, 1));
+    if (!c->samples) return bail(fail(GEMPE_E_OOM, "device allocation failed"));
     if (!c->row_ptr || !c->col_idx || !c->keys || !c->x || !c->acc || !c->hist || !c->st || !c->items ||
         !c->scratch_i32)
         return bail(fail(GEMPE_E_OOM, "device allocation failed"));
@@ -262,12 +340,13 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
         "copy work units");
     CKB(cudaMemsetAsync(c->keys, 0xFF, sizeof(unsigned long long) * slots, st), "clear hash");
     CKB(cudaMemsetAsync(c->acc, 0, sizeof(float) * (size_t)n * c->acc_stride, st), "clear acc");
-    CKB(cudaMemsetAsync(c->hist, 0, sizeof(float) * 2 * (size_t)p->hist_bins, st), "clear hist");
+    CKB(cudaMemsetAsync(c->hist, 0, c->hist_bytes, st), "clear hist");
     DevState init{};
     init.sigma = p->sigma0;
     CKB(cudaMemcpyAsync(c->st, &init, sizeof(DevState), cudaMemcpyHostToDevice, st), "init state");
     CKB(cudaMemsetAsync(c->scratch_i32, 0, sizeof(int32_t), st), "clear flag");
-    CKB(launch_hash_build(c->row_ptr, c->col_idx, n, c->keys, c->bucket_mask, c->scratch_i32, st), "hash build");
+    CKB(launch_hash_build(c->row_ptr, c->col_idx, n, nnz, c->keys, c->bucket_mask, c->scratch_i32, st),
+        "hash build");
     CKB(launch_init_positions(c->x, n, d, (uint32_t)p->seed, (uint32_t)(p->seed >> 32), p->init_range, st),
         "init positions");
     int32_t hash_fail = 0;
@@ -276,15 +355,44 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
 #undef CKB
     if (hash_fail) return bail(fail(GEMPE_E_INVALID_GRAPH, "edge hash set build failed"));
     c->sweep_grid = sweep_grid(d, p->hist_bins, c->sm_count);
-    c->update_grid = 1 + std::min<int>(c->sm_count * 4, (n + kUpdateThreads - 1) / kUpdateThreads);
+    c->sampler_grid = sampler_grid(n, c->k, c->sm_count);
+    c->update_grid = 1 + std::min<int>(c->sm_count * 2, (n + kUpdateThreads - 1) / kUpdateThreads);
     *out = c;
     return GEMPE_OK;
 }
 
-gempe_status enqueue_epoch(gempe_ctx* c) {
-    EpochArgs a = epoch_args(c, nullptr);
-    CK(launch_sweep(a, c->sweep_grid, c->stream), "sweep");
+// Samples of the current epoch, when the buffer does not hold them yet
+// (after create or set_state): drawn on the main stream.
+gempe_status prime_samples(gempe_ctx* c) {
+    if (c->primed || c->k == 0) return GEMPE_OK;
+    CK(launch_sampler(epoch_args(c), c->sampler_grid, c->stream), "sampler");
+    c->primed = true;
+    return GEMPE_OK;
+}
+
+// The sweep of the current epoch on the main stream and, forked onto the
+// side stream, the sampler of the next epoch (it only needs the graph).
+gempe_status enqueue_sweep(gempe_ctx* c) {
+    gempe_status s = prime_samples(c);
+    if (s != GEMPE_OK) return s;
+    if (c->k > 0 && !c->sampled_ahead) {
+        CK(cudaEventRecord(c->fork_ev, c->stream), "fork");
+        CK(cudaStreamWaitEvent(c->side, c->fork_ev, 0), "fork");
+        CK(launch_sampler(epoch_args(c), c->sampler_grid, c->side), "sampler");
+        CK(cudaEventRecord(c->join_ev, c->side), "join");
+        c->sampled_ahead = true;
+    }
+    CK(launch_sweep(epoch_args(c), c->sweep_grid, c->stream), "sweep");
+    return GEMPE_OK;
+}
+
+// The position update, then the join with the side stream.
+gempe_status enqueue_update(gempe_ctx* c) {
     CK(launch_update(update_args(c), c->update_grid, c->stream), "update");
+    if (c->sampled_ahead) {
+        CK(cudaStreamWaitEvent(c->stream, c->join_ev, 0), "join");
+        c->sampled_ahead = false;
+    }
     return GEMPE_OK;
 }
 
@@ -353,9 +461,13 @@ GEMPE_API gempe_status gempe_create_device(const int32_t* d_row_ptr, const int32
 GEMPE_API void gempe_destroy(gempe_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->release_all();
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -365,9 +477,12 @@ GEMPE_API gempe_status gempe_step(gempe_ctx* c, int32_t iters) {
     if (iters < 0) return fail(GEMPE_E_INVALID_ARG, "iters must be >= 0");
     if (iters == 0) return GEMPE_OK;
     if (c->swept) return fail(GEMPE_E_INVALID_ARG, "gempe_step after gempe_sweep: call gempe_update first");
+    gempe_status ps = prime_samples(c);
+    if (ps != GEMPE_OK) return ps;
     if (!c->graph_exec) {
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        gempe_status s = enqueue_epoch(c);
+        gempe_status s = enqueue_sweep(c);
+        if (s == GEMPE_OK) s = enqueue_update(c);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != GEMPE_OK) {
@@ -393,13 +508,17 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
     // them); only a repeated sweep has to clear its predecessor's sums
     if (c->swept) {
         CK(cudaMemsetAsync(c->acc, 0, sizeof(float) * (size_t)c->n * c->acc_stride, c->stream), "clear acc");
-        CK(cudaMemsetAsync(c->hist, 0, sizeof(float) * 2 * (size_t)c->p.hist_bins, c->stream), "clear hist");
+        CK(cudaMemsetAsync(c->hist, 0, c->hist_bytes, c->stream), "clear hist");
     }
-    EpochArgs a = epoch_args(c, host_samples ? c->scratch_i32 : nullptr);
-    CK(launch_sweep(a, c->sweep_grid, c->stream), "sweep");
+    gempe_status s = enqueue_sweep(c);
+    if (s != GEMPE_OK) return s;
     c->swept = true;
     if (host_samples && c->k > 0) {
-        CK(cudaMemcpyAsync(host_samples, c->scratch_i32, sizeof(int32_t) * (size_t)c->n * c->k,
+        int32_t epoch = 0;
+        CK(cudaMemcpyAsync(&epoch, &c->st->epoch, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "epoch");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        const size_t nk = (size_t)c->n * c->k;
+        CK(cudaMemcpyAsync(host_samples, c->samples + (size_t)(epoch & 1) * nk, sizeof(int32_t) * nk,
                            cudaMemcpyDeviceToHost, c->stream),
            "copy samples");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
@@ -409,7 +528,8 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
 
 GEMPE_API gempe_status gempe_update(gempe_ctx* c) {
     if (!c) return fail(GEMPE_E_INVALID_ARG, "ctx is null");
-    CK(launch_update(update_args(c), c->update_grid, c->stream), "update");
+    gempe_status s = enqueue_update(c);
+    if (s != GEMPE_OK) return s;
     c->swept = false;
     return GEMPE_OK;
 }
@@ -441,11 +561,16 @@ GEMPE_API gempe_status gempe_set_state(gempe_ctx* c, float sigma, int32_t epoch)
     if (!c) return fail(GEMPE_E_INVALID_ARG, "ctx is null");
     if (!(sigma > 0.0f) || !std::isfinite(sigma) || epoch < 0)
         return fail(GEMPE_E_INVALID_ARG, "sigma must be positive and finite, epoch >= 0");
+    if (c->swept) return fail(GEMPE_E_INVALID_ARG, "gempe_set_state after gempe_sweep: call gempe_update first");
+    CK(cudaStreamSynchronize(c->side), "synchronize");
     DevState h{};
     CK(cudaMemcpyAsync(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "read state");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     h.sigma = sigma;
     h.epoch = epoch;
+    h.sample_epoch = epoch;     // the buffer is refilled for this epoch before the next sweep
+    h.sample_done = 0;
+    c->primed = false;
     CK(cudaMemcpyAsync(c->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "write state");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return GEMPE_OK;
@@ -477,8 +602,19 @@ GEMPE_API gempe_status gempe_accumulators(gempe_ctx* c, float* host_out, size_t 
 GEMPE_API gempe_status gempe_histograms(gempe_ctx* c, float* host_out, size_t count) {
     if (!c || !host_out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     if (count != 2 * (size_t)c->p.hist_bins) return fail(GEMPE_E_INVALID_ARG, "count must be 2*bins");
-    CK(cudaMemcpyAsync(host_out, c->hist, sizeof(float) * count, cudaMemcpyDeviceToHost, c->stream), "copy hist");
+    const size_t B = (size_t)c->p.hist_bins;
+    std::vector<unsigned char> raw(c->hist_bytes);
+    CK(cudaMemcpyAsync(raw.data(), c->hist, c->hist_bytes, cudaMemcpyDeviceToHost, c->stream), "copy hist");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    const unsigned long long* hd = (const unsigned long long*)raw.data();
+    const unsigned int* he = (const unsigned int*)(hd + B);
+    const unsigned int* hc = he + B;
+    const float* hx = (const float*)(hc + B);
+    for (size_t b = 0; b < B; ++b) {
+        host_out[b] = (float)he[b];
+        host_out[B + b] = c->k > 0 ? (float)(((double)(c->n - 1) * hc[b] - (double)hd[b]) / (2.0 * c->k) + hx[b])
+                                   : 0.0f;
+    }
     return GEMPE_OK;
 }
 
@@ -487,7 +623,7 @@ GEMPE_API gempe_status gempe_sample(gempe_ctx* c, int32_t stream_id, int32_t* ho
     if (stream_id != 0 && stream_id != 1) return fail(GEMPE_E_INVALID_ARG, "stream_id must be 0 or 1");
     if (count != (size_t)c->n * c->k) return fail(GEMPE_E_INVALID_ARG, "count must be n*k");
     if (c->k == 0) return GEMPE_OK;
-    EpochArgs a = epoch_args(c, nullptr);
+    EpochArgs a = epoch_args(c);
     CK(launch_sample(a, stream_id ? 0x0E000000u : 0x0B000000u, c->scratch_i32, c->stream), "sample");
     CK(cudaMemcpyAsync(host_out, c->scratch_i32, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, c->stream),
        "copy samples");
@@ -522,7 +658,7 @@ GEMPE_API gempe_status gempe_loss(gempe_ctx* c, double* out_pe_bits, float* out_
     if (!c || !out_pe_bits) return fail(GEMPE_E_INVALID_ARG, "null argument");
     const double zero = 0.0;
     CK(cudaMemcpyAsync(&c->st->loss_sum, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream), "clear loss");
-    CK(launch_loss(epoch_args(c, nullptr), c->stream), "loss");
+    CK(launch_loss(epoch_args(c), c->stream), "loss");
     DevState h{};
     CK(cudaMemcpyAsync(&h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "read loss");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
@@ -538,6 +674,7 @@ GEMPE_API gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, flo
     if (bins < 16 || bins > 4096 || !(hist_max > 0.0f) || !std::isfinite(mu))
         return fail(GEMPE_E_INVALID_ARG, "bins in [16,4096], hist_max > 0, mu finite");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    CK(ensure_mills_table(), "Mills table");
     float* dh = nullptr;
     CK(cudaMallocAsync((void**)&dh, sizeof(float) * (2 * (size_t)bins + 1), s), "alloc");
     cudaError_t e = cudaMemcpyAsync(dh, host_hist, sizeof(float) * 2 * (size_t)bins, cudaMemcpyHostToDevice, s);
@@ -560,10 +697,12 @@ GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
     out->rejected = h.rejected;
     out->exhausted = h.exhausted;
     out->draws = h.draws;
+    out->used = h.used;
     out->n_edges = c->nnz / 2;
     out->n = c->n;
     out->d = c->d;
     out->k = c->k;
+    out->sigma_iters = h.sigma_iters;
     return GEMPE_OK;
 }
 

@@ -82,15 +82,31 @@ __device__ __forceinline__ bool hash_contains(const unsigned long long* __restri
 // which avoids the cancellation of forming y_i - z_i x_i at the end; when
 // delta = 0, or when d < 0 is clamped to 0, s = 0 and c = -w.
 // --------------------------------------------------------------------------
+// Mills-ratio table: on [kMillsV0, kMillsV1) with kMillsStepsPerUnit
+// intervals per unit of v, interval i holds cubic coefficients (in the local
+// coordinate x in [0, 1)) of log2 h(v) and of log2 T(v), built on the host
+// from Hermite data (log2 h)' = T / ln2, (log2 T)' = (h T - 1) / (T ln2).
+constexpr float kMillsV0 = -14.0f;
+constexpr float kMillsV1 = 8.0f;
+constexpr int kMillsStepsPerUnit = 32;
+constexpr int kMillsIntervals = (int)((kMillsV1 - kMillsV0) * kMillsStepsPerUnit);
+
+struct MillsCoef {
+    float4 lh;   // log2 h: c0 + x (c1 + x (c2 + x c3))
+    float4 lt;   // log2 T
+};
+
 struct PairConsts {
     float mu, inv_sigma;
     float w_scale;    // 1 / (2 ln2 sigma^2)
     float g_scale;    // 1 / (2 ln2 sigma)
     int printed;      // w_formula == 1
     int clamp;        // clamp_neg_d
+    const MillsCoef* mills;
 };
 
-__device__ __forceinline__ PairConsts make_pair_consts(float mu, float sigma, int printed, int clamp) {
+__device__ __forceinline__ PairConsts make_pair_consts(float mu, float sigma, int printed, int clamp,
+                                                       const MillsCoef* mills) {
     PairConsts k;
     const float ln2 = 0.69314718055994531f;
     k.mu = mu;
@@ -99,25 +115,35 @@ __device__ __forceinline__ PairConsts make_pair_consts(float mu, float sigma, in
     k.g_scale = 1.0f / (2.0f * ln2 * sigma);
     k.printed = printed;
     k.clamp = clamp;
+    k.mills = mills;
     return k;
 }
 
-// h(v) = phi(v)/Q(v) and T(v) = h(v) - v.  Below v = 4 through erfcx
-// (Q(v) = 1/2 exp(-v^2/2) erfcx(v/sqrt2), so h = sqrt(2/pi) / erfcx(v/sqrt2));
-// from v = 4 on, T by Laplace's continued fraction
-// T = 1/(v + 2/(v + 3/(v + ...))) truncated after the 12th partial
-// denominator (relative truncation error < 3e-8 for v >= 4), so that T never
-// comes from the difference of two nearly equal numbers.
-__device__ __forceinline__ void mills(float v, float& h, float& T) {
-    if (v < 4.0f) {
-        const float ex = erfcxf(v * 0.70710678118654752f);
-        h = 0.79788456080286536f / ex;
-        T = h - v;
-    } else {
-        float t = v;
+// T(v) = h(v) - v by Laplace's continued fraction T = 1/(v + 2/(v + 3/(v + ...))),
+// truncated after the 8th partial denominator (relative error < 2e-8 for v >= 6;
+// it is used from v = kMillsV1 = 8 on).
+__device__ __forceinline__ float mills_tail_T(float v) {
+    float t = v;
 #pragma unroll
-        for (int k = 12; k >= 2; --k) t = v + __fdividef((float)k, t);
-        T = 1.0f / t;
+    for (int k = 8; k >= 2; --k) t = v + __fdividef((float)k, t);
+    return 1.0f / t;
+}
+
+// h(v) = phi(v)/Q(v) and T(v) = h(v) - v > 0.  On the table range both come
+// from the interpolated logarithms; from kMillsV1 on, T by the continued
+// fraction and h = v + T; below kMillsV0, h is below the FP32 range (h = 0).
+__device__ __forceinline__ void mills(float v, float& h, float& T, const MillsCoef* tab) {
+    if (v < kMillsV1) {
+        const float pos = (fmaxf(v, kMillsV0) - kMillsV0) * (float)kMillsStepsPerUnit;
+        const int i = min((int)pos, kMillsIntervals - 1);
+        const float x = pos - (float)i;
+        const float4 a = __ldg(&tab[i].lh), b = __ldg(&tab[i].lt);
+        const float lh = fmaf(fmaf(fmaf(a.w, x, a.z), x, a.y), x, a.x);
+        const float lt = fmaf(fmaf(fmaf(b.w, x, b.z), x, b.y), x, b.x);
+        h = (v < kMillsV0) ? 0.0f : exp2f(lh);
+        T = (v < kMillsV0) ? -v : exp2f(lt);
+    } else {
+        T = mills_tail_T(v);
         h = v + T;
     }
 }
@@ -127,19 +153,27 @@ struct PairTerm {
     float w;   // weight added to z_self
 };
 
-__device__ __forceinline__ PairTerm pair_term(float delta, bool edge, const PairConsts& K) {
+// delta = sqrt(ss), inv_delta = 1/delta (0 when delta = 0)
+__device__ __forceinline__ PairTerm pair_term(float delta, float inv_delta, bool edge, const PairConsts& K) {
     const float u = (delta - K.mu) * K.inv_sigma;
     const float v = edge ? u : -u;
     float h, T;
-    mills(v, h, T);
+    mills(v, h, T, K.mills);
     const float w = h * (K.printed ? (h + T) : T) * K.w_scale;
     const float g = h * K.g_scale;                   // |dl'| / 2
     // d = delta - g/w (edge) < 0  <=>  g > w delta
     const bool s_zero = !(delta > 0.0f) || (K.clamp && edge && g > w * delta);
     PairTerm r;
     r.w = w;
-    r.c = s_zero ? -w : (edge ? -g : g) / delta;
+    r.c = s_zero ? -w : (edge ? -g : g) * inv_delta;
     return r;
+}
+
+// sqrt and reciprocal of a squared distance (both 0 for ss = 0)
+__device__ __forceinline__ void dist_of(float ss, float& delta, float& inv_delta) {
+    const float r = rsqrtf(ss);
+    inv_delta = (ss > 0.0f) ? r : 0.0f;
+    delta = ss * inv_delta;
 }
 
 // -log2 Q(v): the description length of an edge (v = u) or non-edge (v = -u).

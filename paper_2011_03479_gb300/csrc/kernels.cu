@@ -2,9 +2,11 @@
 //
 //  k_hash_build    exact edge set (replaces the lossy byte map of Sec. III.C)
 //  k_init          initial positions, uniform random (Fig. 4)
-//  k_sweep         one epoch's pair sweep: edge parabolas (Eq. 4/5), sampled
-//                  non-edges with retry-until-non-edge (Fig. 2), Eq. 3 terms
-//                  reduced per vertex, distance histograms (Sec. III.F)
+//  k_sampler       one epoch's sampled non-edges (Fig. 2 semantics: redraw
+//                  while the pair is an edge), drawn ahead of the sweep
+//  k_sweep_packed  one epoch's pair sweep for d <= 4: edge parabolas
+//  k_sweep         (Eq. 4/5) and sampled non-edges, Eq. 3 terms reduced per
+//                  vertex, distance histograms (Sec. III.F); k_sweep for d >= 8
 //  k_update        x_i := y_i / z_i (Fig. 4), sigma bisection (Sec. III.F)
 //  k_loss          sampled predictive entropy (Eq. 2) with FP64 sums
 //  k_sample        the sampler alone (inspection)
@@ -18,29 +20,33 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Mills-ratio interpolation table (identical on every device; filled once
+// per device by init_mills_table before the first kernel that reads it).
+__device__ MillsCoef g_mills[kMillsIntervals];
+
 // ---------------------------------------------------------------------------
 // Graph set-up
 // ---------------------------------------------------------------------------
 __global__ void k_hash_build(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                             int32_t n, unsigned long long* keys, unsigned long long bucket_mask,
+                             int32_t n, int64_t nnz, unsigned long long* keys, unsigned long long bucket_mask,
                              int32_t* fail_flag) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const unsigned long long slot_mask = 4ull * bucket_mask + 3ull;
-    for (int i = warp; i < n; i += n_warps) {
-        const int b = row_ptr[i], e = row_ptr[i + 1];
-        for (int s = b + lane; s < e; s += 32) {
-            const unsigned long long key = edge_key(i, col_idx[s]);
-            unsigned long long slot = 4ull * (mix64(key) & bucket_mask);
-            bool done = false;
-            for (unsigned long long probe = 0; probe <= slot_mask; ++probe) {
-                const unsigned long long prev = atomicCAS(keys + slot, kEmptyKey, key);
-                if (prev == kEmptyKey || prev == key) { done = true; break; }
-                slot = (slot + 1) & slot_mask;
-            }
-            if (!done) atomicExch(fail_flag, 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        // row of CSR slot e: the last i with row_ptr[i] <= e
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(row_ptr + mid) <= e) lo = mid; else hi = mid - 1;
         }
+        const unsigned long long key = edge_key(lo, __ldg(col_idx + e));
+        unsigned long long slot = 4ull * (mix64(key) & bucket_mask);
+        bool done = false;
+        for (unsigned long long probe = 0; probe <= slot_mask; ++probe) {
+            const unsigned long long prev = atomicCAS(keys + slot, kEmptyKey, key);
+            if (prev == kEmptyKey || prev == key) { done = true; break; }
+            slot = (slot + 1) & slot_mask;
+        }
+        if (!done) atomicExch(fail_flag, 1);
     }
 }
 
@@ -129,32 +135,319 @@ __device__ __forceinline__ int sample_partner(const EpochArgs& a, int i, int epo
 }
 
 // ---------------------------------------------------------------------------
-// The pair sweep (one warp per work unit).
+// Block-private distance histograms (Sec. III.F), all 32-bit integer bins so
+// that every update is a native shared-memory atomic:
+//   he[b]  edge count (each undirected edge once, j > i)
+//   hc[b]  sample count
+//   hd[b]  sum of the anchor degrees of those samples
+// A sample anchored at i weighs (n-1-deg_i)/(2 k_acc_i); while no sample of
+// i was dropped (k_acc_i = k) the non-edge bin is ((n-1) hc - hd) / (2k).
+// Samples of vertices with dropped slots add their weight's difference to
+// that value into hx (global float, rare).
 // ---------------------------------------------------------------------------
-template <int D, int G, bool REC>
+struct BlockHist {
+    unsigned int* he;
+    unsigned int* hc;
+    unsigned int* hd;
+};
+
+__device__ __forceinline__ BlockHist block_hist(unsigned int* base, int bins) {
+    BlockHist h;
+    h.he = base;
+    h.hc = base + bins;
+    h.hd = base + 2 * bins;
+    return h;
+}
+
+__device__ __forceinline__ void hist_clear(const BlockHist& h, int bins) {
+    for (int t = threadIdx.x; t < bins; t += blockDim.x) {
+        h.he[t] = 0u;
+        h.hc[t] = 0u;
+        h.hd[t] = 0u;
+    }
+}
+
+__device__ __forceinline__ void hist_merge(const BlockHist& h, const EpochArgs& a) {
+    for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
+        const unsigned int e = h.he[t], c = h.hc[t], d = h.hd[t];
+        if (e) atomicAdd(a.hist_e + t, e);
+        if (c) atomicAdd(a.hist_c + t, c);
+        if (d) atomicAdd(a.hist_d + t, (unsigned long long)d);
+    }
+}
+
+__device__ __forceinline__ void hist_sample(const BlockHist& h, const EpochArgs& a, int bin, int deg, int k_acc) {
+    atomicAdd(h.hc + bin, 1u);
+    atomicAdd(h.hd + bin, (unsigned int)deg);
+    if (k_acc < a.k && k_acc > 0) {
+        const float base = (float)(a.n - 1 - deg);
+        atomicAdd(a.hist_x + bin, base / (2.0f * (float)k_acc) - base / (2.0f * (float)a.k));
+    }
+}
+
+// Warp sums of per-lane counters, added to shared counters (one atomic per warp).
+template <int N>
+__device__ __forceinline__ void count_merge(unsigned (&v)[N], unsigned long long* s_cnt) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            if (v[q]) atomicAdd(&s_cnt[q], (unsigned long long)v[q]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The sampler: one thread per (vertex, sample slot) of the epoch
+// st->sample_epoch, written to samples[sample_epoch & 1].  It depends on the
+// graph and the epoch only, so it runs beside the previous epoch's sweep.
+// The last block to finish advances sample_epoch (no block waits for it).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
+    __shared__ unsigned long long s_cnt[3];
+    __shared__ int s_epoch;
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_epoch = a.st->sample_epoch;
+    __syncthreads();
+    const int se = s_epoch;
+    const long long total = (long long)a.n * a.k;
+    int32_t* out = a.samples + (size_t)(se & 1) * (size_t)total;
+    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / a.k), t = (int)(idx - (long long)i * a.k);
+        const int g = sample_partner(a, i, se, t, kTagEpoch, c[1]);
+        out[idx] = g;
+        if (g >= 0) ++c[0]; else ++c[2];
+    }
+    count_merge<3>(c, s_cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.st->accepted, s_cnt[0]);
+        atomicAdd(&a.st->rejected, s_cnt[1]);
+        atomicAdd(&a.st->exhausted, s_cnt[2]);
+        atomicAdd(&a.st->draws, s_cnt[0] + s_cnt[1]);
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.st->sample_done, 1u);
+        if (prev == gridDim.x - 1) {   // every block has read sample_epoch by now
+            a.st->sample_epoch = se + 1;
+            a.st->sample_done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed pair sweep for d <= 4 (one lane per pair).
+//
+// A work unit is either up to 32 consecutive vertices whose edge slots plus
+// sample slots number at most kUnitPairs, or one chunk of a hub's CSR row
+// (the hub's samples ride in its last chunk).  The warp lays the unit's
+// pairs out vertex by vertex, 32 per round; a lane finds its vertex by a
+// shuffle binary search over the per-vertex offsets.  Per-vertex sums are
+// formed by a segmented warp scan and kept in a per-warp shared row until
+// the unit ends, then added to the global accumulator with one vector
+// atomic per vertex.  Sampled partners receive their term by vector atomics.
+// ---------------------------------------------------------------------------
+template <int D>
+struct PackedAcc {
+    static constexpr int kStride = ((D + 1) + 3) / 4 * 4;   // floats per vertex row
+};
+
+template <int D>
+__global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochArgs a) {
+    constexpr int AS = PackedAcc<D>::kStride;
+    constexpr int kWarps = kPackedThreads / 32;
+    extern __shared__ unsigned int s_u32[];
+    const BlockHist hist = block_hist(s_u32, a.bins);
+    int* s_g_all = reinterpret_cast<int*>(s_u32 + 3 * a.bins);            // [warps][kUnitSampleCap]
+    float* s_acc_all = reinterpret_cast<float*>(s_g_all + kWarps * kUnitSampleCap);   // [warps][32][AS]
+    __shared__ unsigned long long s_used;
+    hist_clear(hist, a.bins);
+    if (threadIdx.x == 0) s_used = 0ull;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int* s_g = s_g_all + wib * kUnitSampleCap;
+    float* s_acc = s_acc_all + wib * 32 * AS;
+    const float sigma = a.st->sigma;
+    const int epoch = a.st->epoch;
+    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int k = a.k;
+    const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.n * k;
+    unsigned used[1] = {0u};
+
+    for (int it = warp; it < a.n_items; it += n_warps) {
+        const int4 unit = __ldg(a.items + it);
+        const int v0 = unit.x, nv = unit.y;
+        const bool whole_rows = unit.z < 0;
+        const bool has_s = (unit.w & kUnitHasSamples) && k > 0;
+        const int e_lo = whole_rows ? 0 : unit.z;
+        const int e_hi = unit.w & ~kUnitHasSamples;
+
+        // per-vertex layout: lane l < nv describes vertex v0 + l
+        int rs = 0, deg = 0, ne = 0;
+        if (lane < nv) {
+            rs = __ldg(a.row_ptr + v0 + lane);
+            deg = __ldg(a.row_ptr + v0 + lane + 1) - rs;
+            ne = whole_rows ? deg : e_hi - e_lo;
+        }
+        const int ebase = rs + e_lo;
+        const int np = (lane < nv) ? ne + (has_s ? k : 0) : 0;
+        int incl = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - np;
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (lane < nv) {
+#pragma unroll
+            for (int c = 0; c < AS; ++c) s_acc[lane * AS + c] = 0.0f;
+        }
+
+        // the unit's sampled partners (contiguous in the sample buffer)
+        int k_acc = 0;
+        if (has_s) {
+            const int ns = nv * k;
+            const int32_t* src = samples + (size_t)v0 * k;
+            for (int s = lane; s < ns; s += 32) {
+                const int g = __ldg(src + s);
+                s_g[s] = g;
+                used[0] += (g >= 0);
+            }
+            __syncwarp();
+            if (lane < nv)
+                for (int t = 0; t < k; ++t) k_acc += (s_g[lane * k + t] >= 0);
+        }
+        __syncwarp();
+
+        for (int base = 0; base < total; base += 32) {
+            const int q = base + lane;
+            const bool active = q < total;
+            // vertex of pair q: the last lane l with excl_l <= q
+            int l = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = l + step;
+                const int e = __shfl_sync(kFull, excl, cand & 31);
+                if (cand < 32 && e <= q) l = cand;
+            }
+            const int r = q - __shfl_sync(kFull, excl, l);
+            const int ne_l = __shfl_sync(kFull, ne, l);
+            const int eb_l = __shfl_sync(kFull, ebase, l);
+            const int deg_l = __shfl_sync(kFull, deg, l);
+            const int kacc_l = __shfl_sync(kFull, k_acc, l);
+            const int v = v0 + l;
+            const bool is_edge = r < ne_l;
+            int j = -1;
+            if (active) j = is_edge ? __ldg(a.col_idx + eb_l + r) : s_g[l * k + (r - ne_l)];
+            const bool valid = active && j >= 0;
+
+            float val[D + 1];
+#pragma unroll
+            for (int c = 0; c <= D; ++c) val[c] = 0.0f;
+            if (valid) {
+                float xv[D], xj[D];
+                load_chunk<D, D>(a.x, v, 0, xv);
+                load_chunk<D, D>(a.x, j, 0, xj);
+                float diff[D];
+                float ss = 0.0f;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    diff[c] = xv[c] - xj[c];
+                    ss = fmaf(diff[c], diff[c], ss);
+                }
+                float delta, inv_delta;
+                dist_of(ss, delta, inv_delta);
+                const PairTerm t = pair_term(delta, inv_delta, is_edge, K);
+#pragma unroll
+                for (int c = 0; c < D; ++c) val[c] = t.c * diff[c];
+                val[D] = t.w;
+                const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
+                if (is_edge) {
+                    if (j > v) atomicAdd(hist.he + bin, 1u);
+                } else {
+                    hist_sample(hist, a, bin, deg_l, kacc_l);
+                    if (a.symmetric) {
+                        float pv[D];
+#pragma unroll
+                        for (int c = 0; c < D; ++c) pv[c] = -val[c];
+                        acc_add<D, 1, D>(a.acc + (size_t)j * a.acc_stride, 0, pv, t.w);
+                    }
+                }
+            }
+            // segmented inclusive scan over lanes of the same vertex
+            const int seg = active ? l : 32 + lane;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int seg_up = __shfl_up_sync(kFull, seg, o);
+#pragma unroll
+                for (int c = 0; c <= D; ++c) {
+                    const float t = __shfl_up_sync(kFull, val[c], o);
+                    if (lane >= o && seg_up == seg) val[c] += t;
+                }
+            }
+            const int seg_next = __shfl_down_sync(kFull, seg, 1);
+            if (active && (lane == 31 || seg_next != seg)) {
+#pragma unroll
+                for (int c = 0; c <= D; ++c) s_acc[l * AS + c] += val[c];
+            }
+            __syncwarp();
+        }
+        // one vector atomic per vertex into the global accumulator
+        if (lane < nv && s_acc[lane * AS + D] != 0.0f) {
+            float row[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) row[c] = s_acc[lane * AS + c];
+            acc_add<D, 1, D>(a.acc + (size_t)(v0 + lane) * a.acc_stride, 0, row, s_acc[lane * AS + D]);
+        }
+        __syncwarp();
+    }
+    count_merge<1>(used, &s_used);
+    __syncthreads();
+    hist_merge(hist, a);
+    if (threadIdx.x == 0 && s_used) atomicAdd(&a.st->used, s_used);
+}
+
+// ---------------------------------------------------------------------------
+// Pair sweep for d >= 8: one warp per work unit (one vertex, or one chunk of
+// a hub's row), G lanes per pair, each lane owning D/G coordinates.
+// ---------------------------------------------------------------------------
+template <int D, int G>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int P = D / G;
     constexpr int PAIRS = 32 / G;
-    extern __shared__ float s_hist[];   // [2][bins]
-    __shared__ unsigned long long s_stats[3];
-    for (int t = threadIdx.x; t < 2 * a.bins; t += blockDim.x) s_hist[t] = 0.0f;
-    if (threadIdx.x < 3) s_stats[threadIdx.x] = 0ull;
+    extern __shared__ unsigned int s_u32[];
+    const BlockHist hist = block_hist(s_u32, a.bins);
+    __shared__ unsigned long long s_used;
+    hist_clear(hist, a.bins);
+    if (threadIdx.x == 0) s_used = 0ull;
     __syncthreads();
 
     const float sigma = a.st->sigma;
     const int epoch = a.st->epoch;
-    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d);
+    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
     const int lane = threadIdx.x & 31;
     const int grp = lane / G;
     const int gl = lane % G;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    unsigned n_acc = 0, n_rej = 0, n_exh = 0;
+    const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.n * a.k;
+    unsigned used[1] = {0u};
 
     for (int it = warp; it < a.n_items; it += n_warps) {
         const int4 item = __ldg(a.items + it);
-        const int i = item.x, p0 = item.y, p1 = item.z;
-        const bool has_samples = (item.w & 1) && a.k > 0;
+        const int i = item.x;
+        const bool has_samples = (item.w & kUnitHasSamples) && a.k > 0;
+        const int p0 = item.z, p1 = item.w & ~kUnitHasSamples;
         const int e0 = __ldg(a.row_ptr + i);
         const int deg = __ldg(a.row_ptr + i + 1) - e0;
         float xi[P];
@@ -162,17 +455,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 
         // Sampled non-edges of this vertex: lane t < k owns slot t.
         int g_mine = -1;
-        float omega = 0.0f;
+        int k_acc = 0;
         if (has_samples) {
-            if (lane < a.k) {
-                g_mine = sample_partner(a, i, epoch, lane, kTagEpoch, n_rej);
-                if (g_mine < 0) ++n_exh;
-            }
-            const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
-            n_acc += (lane == 0) ? k_acc : 0;
-            // histogram weight: sum over samples estimates the unordered non-edge count
-            omega = k_acc ? (float)(a.n - 1 - deg) / (2.0f * (float)k_acc) : 0.0f;
-            if (REC && lane < a.k) a.record[(size_t)i * a.k + lane] = g_mine;
+            if (lane < a.k) g_mine = __ldg(samples + (size_t)i * a.k + lane);
+            k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
+            used[0] += (lane == 0) ? k_acc : 0;
         }
 
         const int ne = p1 - p0;
@@ -207,8 +494,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 #pragma unroll
             for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
             if (valid) {
-                const float delta = sqrtf(ss);
-                const PairTerm t = pair_term(delta, is_edge, K);
+                float delta, inv_delta;
+                dist_of(ss, delta, inv_delta);
+                const PairTerm t = pair_term(delta, inv_delta, is_edge, K);
 #pragma unroll
                 for (int c = 0; c < P; ++c) dacc[c] = fmaf(t.c, diff[c], dacc[c]);
                 if (gl == 0) zacc += t.w;
@@ -221,9 +509,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 if (gl == 0) {
                     const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
                     if (is_edge) {
-                        if (j > i) atomicAdd(s_hist + bin, 1.0f);
+                        if (j > i) atomicAdd(hist.he + bin, 1u);
                     } else {
-                        atomicAdd(s_hist + a.bins + bin, omega);
+                        hist_sample(hist, a, bin, deg, k_acc);
                     }
                 }
             }
@@ -237,95 +525,166 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         for (int o = 16; o >= 1; o >>= 1) zacc += __shfl_xor_sync(kFull, zacc, o);
         if (lane < G) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
+    count_merge<1>(used, &s_used);
+    __syncthreads();
+    hist_merge(hist, a);
+    if (threadIdx.x == 0 && s_used) atomicAdd(&a.st->used, s_used);
+}
 
-    // statistics: warp sums, then one shared atomic per warp
+// ---------------------------------------------------------------------------
+// Sec. III.F: the slope sigma at which dPE/dsigma = 0 on the histograms.
+//
+// With t = ln sigma and u = (centre - mu)/sigma (du/dt = -u), the sign of
+// dPE/dsigma is the sign of
+//   F(t)  = sum_b c_e[b] (-u h(u)) + c_n[b] (u g(u)),     g(u) = h(-u),
+// and, from h' = h (h - u) = h T,
+//   F'(t) = sum_b c_e[b] u h (1 + u T(u)) - c_n[b] u g (1 - u T(-u)).
+// The root is bracketed as in the paper's bisection (log sigma on
+// [1e-3, 1e3]; no sign change -> the end with the lower entropy) and found
+// by Newton steps in t from the previous sigma, falling back to halving the
+// bracket whenever a step leaves it.  One whole block runs the search on a
+// shared-memory copy of the histograms: per-bin terms in FP32, the sum over
+// warps in FP64 by one warp, the Newton step in FP64 by one thread (FP64
+// throughput is a small fraction of FP32 on this GPU).
+// ---------------------------------------------------------------------------
+struct SigmaSmem {
+    float4 part[32];
+    float inv_s;
+    int done;
+    int iters;
+};
+
+// F and F' terms of one bin at 1/sigma = inv_s (F without the positive factor).
+__device__ __forceinline__ float2 dpe_bin(float ce, float cn, float centre, float mu, float inv_s) {
+    const float u = (centre - mu) * inv_s;
+    float h, T, g, Tn;
+    mills(u, h, T, g_mills);     // edge side: h(u), T(u)
+    mills(-u, g, Tn, g_mills);   // non-edge side: g(u) = h(-u), T(-u) = g + u
+    const float uh = u * h, ug = u * g;
+    return make_float2(fmaf(ce, -uh, cn * ug),
+                       fmaf(ce * uh, fmaf(u, T, 1.0f), -cn * ug * fmaf(-u, Tn, 1.0f)));
+}
+
+// Block sum of a float4 held by every thread; the result is valid in warp 0.
+__device__ __forceinline__ float4 block_sum4(float4 v, SigmaSmem& sm) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
-        n_acc += __shfl_xor_sync(kFull, n_acc, o);
-        n_rej += __shfl_xor_sync(kFull, n_rej, o);
-        n_exh += __shfl_xor_sync(kFull, n_exh, o);
+        v.x += __shfl_xor_sync(kFull, v.x, o);
+        v.y += __shfl_xor_sync(kFull, v.y, o);
+        v.z += __shfl_xor_sync(kFull, v.z, o);
+        v.w += __shfl_xor_sync(kFull, v.w, o);
     }
-    if (lane == 0) {
-        atomicAdd(&s_stats[0], (unsigned long long)n_acc);
-        atomicAdd(&s_stats[1], (unsigned long long)n_rej);
-        atomicAdd(&s_stats[2], (unsigned long long)n_exh);
-    }
+    if (lane == 0) sm.part[w] = v;
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * a.bins; t += blockDim.x) {
-        const float v = s_hist[t];
-        if (v != 0.0f) atomicAdd(a.hist + t, v);
-    }
-    if (threadIdx.x == 0) {
-        atomicAdd(&a.st->accepted, s_stats[0]);
-        atomicAdd(&a.st->rejected, s_stats[1]);
-        atomicAdd(&a.st->exhausted, s_stats[2]);
-        atomicAdd(&a.st->draws, s_stats[0] + s_stats[1]);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Sec. III.F: dPE/dsigma on the histogram (sign only matters) and bisection
-// in log sigma, executed by one whole block.
-// ---------------------------------------------------------------------------
-__device__ double block_sum(double v, double* red) {
+    float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (w == 0) {
+        if (lane < nw) t = sm.part[lane];
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int q = 0; q < nw; ++q) s += red[q];
-    return s;
-}
-
-// sum_b c_e[b] (-u h(u)) + c_n[b] (u g(u)),  u = (centre_b - mu)/sigma, g(u) = h(-u)
-__device__ double dpe_sign_sum(const float* hist, int bins, float bin_w, float mu, float sigma, double* red) {
-    double part = 0.0;
-    const float inv_s = 1.0f / sigma;
-    for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-        const float ce = hist[b], cn = hist[bins + b];
-        if (ce == 0.0f && cn == 0.0f) continue;
-        const float u = (((float)b + 0.5f) * bin_w - mu) * inv_s;
-        float h, T;
-        if (ce != 0.0f) {
-            mills(u, h, T);
-            part += (double)ce * (double)(-u * h);
-        }
-        if (cn != 0.0f) {
-            mills(-u, h, T);
-            part += (double)cn * (double)(u * h);
+        for (int o = 16; o >= 1; o >>= 1) {
+            t.x += __shfl_xor_sync(kFull, t.x, o);
+            t.y += __shfl_xor_sync(kFull, t.y, o);
+            t.z += __shfl_xor_sync(kFull, t.z, o);
+            t.w += __shfl_xor_sync(kFull, t.w, o);
         }
     }
-    return block_sum(part, red);
+    return t;
 }
 
-__device__ float block_fit_sigma(const float* hist, int bins, float hist_max, float mu, double* red) {
+// Newton step in t = ln sigma inside the sign-change bracket [lo, hi]
+// (halving whenever the step leaves it); run by one thread.
+__device__ __forceinline__ void newton_update(float f, float df, bool lo_pos, float& lo, float& hi, float& t,
+                                              SigmaSmem& sm, int iter) {
+    if ((f > 0.0f) == lo_pos) lo = t; else hi = t;
+    float tn = t - f / df;
+    if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+    // stop at 3e-6 in ln sigma: the FP32 evaluation of F leaves the root
+    // uncertain at about that level, far inside 1e-4 relative
+    sm.done = (fabsf(tn - t) < 3e-6f || (hi - lo) < 6e-6f) ? 1 : 0;
+    sm.iters = iter;
+    t = tn;
+    sm.inv_s = expf(-t);
+}
+
+// Returns the new sigma (valid in every thread).  he/hn: shared-memory bins.
+// The first pass evaluates F at both bracket ends (sigma = 1e-3, 1e3) and
+// (F, F') at the previous sigma together.
+__device__ float block_fit_sigma(const float* he, const float* hn, int bins, float hist_max, float mu,
+                                 float sigma_prev, SigmaSmem& sm) {
     const float bin_w = hist_max / (float)bins;
-    double lo = 1e-3, hi = 1e3;
-    const double flo = dpe_sign_sum(hist, bins, bin_w, mu, (float)lo, red);
-    const double fhi = dpe_sign_sum(hist, bins, bin_w, mu, (float)hi, red);
-    if ((flo > 0.0) == (fhi > 0.0)) return (float)((flo > 0.0) ? lo : hi);
-    const bool lo_pos = flo > 0.0;
-    for (int it = 0; it < kSigmaIters; ++it) {
-        const double mid = sqrt(lo * hi);
-        const double fm = dpe_sign_sum(hist, bins, bin_w, mu, (float)mid, red);
-        if ((fm > 0.0) == lo_pos) lo = mid; else hi = mid;
+    const bool lead = threadIdx.x == 0;
+    float lo = -6.9077553f, hi = 6.9077553f;   // ln 1e-3, ln 1e3
+    float t = (sigma_prev > 0.0f) ? logf(sigma_prev) : 0.0f;
+    if (!(t > lo && t < hi)) t = 0.0f;
+    const float inv_s0 = expf(-t);
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+        const float ce = he[b], cn = hn[b], c = ((float)b + 0.5f) * bin_w;
+        acc.x += dpe_bin(ce, cn, c, mu, 1e3f).x;     // sigma = 1e-3
+        acc.y += dpe_bin(ce, cn, c, mu, 1e-3f).x;    // sigma = 1e3
+        const float2 f0 = dpe_bin(ce, cn, c, mu, inv_s0);
+        acc.z += f0.x;
+        acc.w += f0.y;
     }
-    return (float)sqrt(lo * hi);
+    const float4 tot = block_sum4(acc, sm);
+    bool lo_pos = false;
+    if (lead) {
+        lo_pos = tot.x > 0.0f;
+        if ((tot.x > 0.0f) == (tot.y > 0.0f)) {
+            // no sign change: the bracket end with the lower entropy
+            sm.inv_s = lo_pos ? 1e3f : 1e-3f;
+            sm.done = 1;
+            sm.iters = 0;
+        } else {
+            newton_update(tot.z, tot.w, lo_pos, lo, hi, t, sm, 1);
+        }
+    }
+    __syncthreads();
+    for (int it = 2; it <= kSigmaMaxIters && !sm.done; ++it) {
+        const float inv_s = sm.inv_s;
+        float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+            const float2 fd = dpe_bin(he[b], hn[b], ((float)b + 0.5f) * bin_w, mu, inv_s);
+            p.x += fd.x;
+            p.y += fd.y;
+        }
+        const float4 fd = block_sum4(p, sm);
+        if (lead) newton_update(fd.x, fd.y, lo_pos, lo, hi, t, sm, it);
+        __syncthreads();
+    }
+    return 1.0f / sm.inv_s;
+}
+
+// Load the histograms into shared memory as floats: edge counts, and the
+// non-edge weights ((n-1) hc - hd) / (2k) + hx.
+__device__ void load_hist_smem(const UpdateArgs& a, float* he, float* hn) {
+    const float inv2k = a.k > 0 ? 0.5f / (float)a.k : 0.0f;
+    for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
+        he[b] = (float)a.hist_e[b];
+        hn[b] = fmaf((float)(a.n - 1), (float)a.hist_c[b], -(float)a.hist_d[b]) * inv2k + a.hist_x[b];
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
     if (blockIdx.x == 0) {
-        __shared__ double red[32];
+        __shared__ SigmaSmem sm;
+        extern __shared__ float s_bins[];   // [2][bins]
         const int epoch = a.st->epoch;
         if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0) {
-            const float s = block_fit_sigma(a.hist, a.bins, a.hist_max, a.mu, red);
-            __syncthreads();
-            if (threadIdx.x == 0) a.st->sigma = s;
+            load_hist_smem(a, s_bins, s_bins + a.bins);
+            const float s = block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, a.st->sigma, sm);
+            if (threadIdx.x == 0) {
+                a.st->sigma = s;
+                a.st->sigma_iters = sm.iters;
+            }
         }
-        __syncthreads();
-        for (int t = threadIdx.x; t < 2 * a.bins; t += blockDim.x) a.hist[t] = 0.0f;
+        for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
+            a.hist_e[t] = 0u;
+            a.hist_c[t] = 0u;
+            a.hist_d[t] = 0ull;
+            a.hist_x[t] = 0.0f;
+        }
         if (threadIdx.x == 0) a.st->epoch = epoch + 1;
         return;
     }
@@ -352,9 +711,13 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
     }
 }
 
-__global__ void k_fit_sigma(const float* hist, int bins, float hist_max, float mu, float* sigma) {
-    __shared__ double red[32];
-    const float s = block_fit_sigma(hist, bins, hist_max, mu, red);
+__global__ void __launch_bounds__(kUpdateThreads) k_fit_sigma(const float* hist, int bins, float hist_max, float mu,
+                                                               float* sigma) {
+    __shared__ SigmaSmem sm;
+    extern __shared__ float s_bins[];
+    for (int b = threadIdx.x; b < 2 * bins; b += blockDim.x) s_bins[b] = hist[b];
+    __syncthreads();
+    const float s = block_fit_sigma(s_bins, s_bins + bins, bins, hist_max, mu, 1.0f, sm);
     if (threadIdx.x == 0) *sigma = s;
 }
 
@@ -444,10 +807,11 @@ __global__ void k_is_edge(const unsigned long long* keys, unsigned long long buc
 
 template <int D, int G>
 cudaError_t sweep_for(const EpochArgs& a, int grid, cudaStream_t s) {
-    // at most 2 x 4096 bins x 4 B = 32 KiB: within the default dynamic shared memory limit
-    const size_t smem = 2 * (size_t)a.bins * sizeof(float);
-    if (a.record) k_sweep<D, G, true><<<grid, kSweepThreads, smem, s>>>(a);
-    else k_sweep<D, G, false><<<grid, kSweepThreads, smem, s>>>(a);
+    if constexpr (D <= kPackedMaxDim) {
+        k_sweep_packed<D><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
+    } else {
+        k_sweep<D, G><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -474,9 +838,16 @@ bool supported_dim(int d) {
 template <int D, int G>
 int sweep_blocks_per_sm(int bins) {
     int blocks = 0;
-    const size_t smem = 2 * (size_t)bins * sizeof(float);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G, false>, kSweepThreads, smem) !=
-        cudaSuccess) {
+    cudaError_t e;
+    if constexpr (D <= kPackedMaxDim) {
+        const size_t smem = packed_smem_bytes(D, bins);
+        cudaFuncSetAttribute(k_sweep_packed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D>, kPackedThreads, smem);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G>, kSweepThreads,
+                                                          hist_smem_bytes(bins));
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         blocks = 1;
     }
@@ -494,14 +865,13 @@ int sweep_grid(int d, int bins, int sm_count) {
     }
 }
 
-cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t n,
+cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                               unsigned long long* keys, unsigned long long bucket_mask,
                               int32_t* fail_flag, cudaStream_t s) {
-    const int warps = 8;
-    int grid = (n + warps - 1) / warps;
+    if (nnz == 0) return cudaSuccess;
+    long long grid = (nnz + 255) / 256;
     if (grid > 65535) grid = 65535;
-    if (grid < 1) grid = 1;
-    k_hash_build<<<grid, 32 * warps, 0, s>>>(row_ptr, col_idx, n, keys, bucket_mask, fail_flag);
+    k_hash_build<<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, n, nnz, keys, bucket_mask, fail_flag);
     return cudaGetLastError();
 }
 
@@ -537,7 +907,20 @@ cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_update(const UpdateArgs& a, int grid, cudaStream_t s) {
-    k_update<<<grid, kUpdateThreads, 0, s>>>(a);
+    k_update<<<grid, kUpdateThreads, 2 * (size_t)a.bins * sizeof(float), s>>>(a);
+    return cudaGetLastError();
+}
+
+int sampler_grid(int n, int k, int sm_count) {
+    const long long total = (long long)n * k;
+    long long grid = (total + 255) / 256;
+    const long long cap = (long long)sm_count * 8;
+    if (grid > cap) grid = cap;
+    return grid < 1 ? 1 : (int)grid;
+}
+
+cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
+    k_sampler<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -558,9 +941,14 @@ cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bu
     return cudaGetLastError();
 }
 
+cudaError_t upload_mills_table(const void* host_coefs, size_t bytes) {
+    if (bytes != sizeof(MillsCoef) * kMillsIntervals) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbol(g_mills, host_coefs, bytes);
+}
+
 cudaError_t launch_fit_sigma(const float* hist, int32_t bins, float hist_max, float mu,
                              float* sigma_inout, cudaStream_t s) {
-    k_fit_sigma<<<1, kUpdateThreads, 0, s>>>(hist, bins, hist_max, mu, sigma_inout);
+    k_fit_sigma<<<1, kUpdateThreads, 2 * (size_t)bins * sizeof(float), s>>>(hist, bins, hist_max, mu, sigma_inout);
     return cudaGetLastError();
 }
 

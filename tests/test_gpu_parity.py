@@ -1,8 +1,17 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Bars: initial positions, membership and sampled pairs bit-exact; per-step
-FP32 results within 1e-4 relative (per vertex, against
-max(|ref|, 1e-6 * mean |ref|)); the slope fit within 1e-4 relative.
+FP32 results within 1e-4 relative per vertex, against
+max(|ref|, 1e-6 * mean |ref|); the slope fit within 1e-4 relative.
+
+For y_i - z_i x_i (a sum whose pair terms can cancel) the reference scale is
+also floored at 1e-2 * A_i, A_i = sum of the sizes of its terms: the terms are
+FP32 numbers, each carrying rounding of a few units of 2^-24 of its size, so
+no accumulation order brings the error of a sum with A_i / |sum| = 3000 below
+1e-4 of |sum|.  The floor allows an absolute error of 1e-6 A_i (about 17 FP32
+ulps of the terms); measured on the R-MAT bench graph the largest error is
+3.3e-7 A_i, and 99.9% of vertices have A_i / |sum| below 61, where the plain
+1e-4 relative bar holds unchanged.
 """
 import numpy as np
 import pytest
@@ -15,13 +24,19 @@ pytestmark = [pytest.mark.gpu,
 TOL = 1e-4
 
 
-def _rel_err_rows(got, ref):
-    """Per-row ||got-ref|| / max(||ref||, 1e-6 mean ||ref||)."""
+def _rel_err_rows(got, ref, abs_terms=None):
+    """Per-row ||got-ref|| / max(||ref||, 1e-6 mean ||ref||[, 1e-2 abs_terms])."""
     got = np.asarray(got, np.float64).reshape(len(ref), -1)
     ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
     nr = np.linalg.norm(ref, axis=1)
-    floor = 1e-6 * max(nr.mean(), 1e-300)
-    return np.linalg.norm(got - ref, axis=1) / np.maximum(nr, floor)
+    scale = np.maximum(nr, 1e-6 * max(nr.mean(), 1e-300))
+    if abs_terms is not None:
+        scale = np.maximum(scale, 1e-2 * np.asarray(abs_terms, np.float64))
+    return np.linalg.norm(got - ref, axis=1) / scale
+
+
+def _delta_err(r):
+    return _rel_err_rows(r["delta"], r["ref"]["delta"], r["ref"]["abs_terms"])
 
 
 @pytest.fixture(scope="module")
@@ -123,7 +138,7 @@ def test_sweep_and_update_parity(B, O, sbm_1000, d):
     x = (rng.standard_normal((1000, d)) * 1.2).astype(np.float32)
     r = _sweep_compare(B, O, rp, ci, d, x, 0.7, 5, neg_per_vertex=5)
     ref = r["ref"]
-    assert _rel_err_rows(r["delta"], ref["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
     assert _rel_err_rows(r["z"], ref["z"]).max() <= TOL
     assert _rel_err_rows(r["xn"], ref["x_new"]).max() <= TOL
     assert r["epoch"] == 6
@@ -135,7 +150,7 @@ def test_sweep_readings(B, O, sbm_1000, w_formula, clamp, symmetric):
     x = (np.random.default_rng(9).uniform(-2, 2, (1000, 2))).astype(np.float32)
     r = _sweep_compare(B, O, rp, ci, 2, x, 1.3, 3, neg_per_vertex=7, w_formula=w_formula,
                        clamp_neg_d=clamp, symmetric_neg=symmetric)
-    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
     assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
 
 
@@ -145,7 +160,7 @@ def test_sweep_extreme_slopes(B, O, sbm_1000, sigma):
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     x = (np.random.default_rng(1).uniform(-3, 3, (1000, 2))).astype(np.float32)
     r = _sweep_compare(B, O, rp, ci, 2, x, sigma, 0, neg_per_vertex=5)
-    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
     assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
     assert _rel_err_rows(r["xn"], r["ref"]["x_new"]).max() <= TOL
 
@@ -202,7 +217,7 @@ def test_rmat_epoch_parity_full(B, O):
     rp, ci = w["row_ptr"], w["col_idx"]
     x = O.init_positions(len(rp) - 1, 2, inputs.EMBED_SEED) * np.float32(2.5)
     r = _sweep_compare(B, O, rp, ci, 2, x, 0.8, 17, neg_per_vertex=10, seed=inputs.EMBED_SEED)
-    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
     assert _rel_err_rows(r["z"], r["ref"]["z"]).max() <= TOL
     assert _rel_err_rows(r["xn"], r["ref"]["x_new"]).max() <= TOL
 
@@ -216,12 +231,12 @@ def test_edge_cases(B, O):
     ci = np.array(sum(rows, []), dtype=np.int32)
     x = np.random.default_rng(0).uniform(-1, 1, (n, 2)).astype(np.float32)
     r = _sweep_compare(B, O, rp, ci, 2, x, 1.0, 0, neg_per_vertex=32, max_retries=4)
-    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
     r = _sweep_compare(B, O, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), 2,
                        np.array([[0, 0], [0.3, 0.4]], np.float32), 1.0, 0, neg_per_vertex=3)
     np.testing.assert_allclose(r["xn"], r["ref"]["x_new"], rtol=TOL, atol=1e-7)
     r = _sweep_compare(B, O, rp, ci, 2, x, 1.0, 0, neg_per_vertex=0)
-    assert _rel_err_rows(r["delta"], r["ref"]["delta"]).max() <= TOL
+    assert _delta_err(r).max() <= TOL
 
 
 def test_coincident_points(B, O, sbm_1000):
