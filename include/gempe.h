@@ -174,6 +174,20 @@ gempe_status gempe_loss(gempe_ctx* ctx, double* out_pe_bits, float* out_sigma);
 gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_max, float mu,
                              void* cuda_stream, float* out_sigma);
 
+/* gempe_fit_sigma without device allocation (the paper has no counterpart:
+ * this is a convenience of the library).  For callers that must not allocate
+ * device memory where they call it -- inside another allocator's callbacks,
+ * in serving loops where cudaMalloc/cudaFree would synchronise the device, or
+ * in a process whose device memory a framework has already reserved.  The
+ * histogram is staged in a 32 KiB static device array (held by every GPU that
+ * loads the library until exit), so bins is limited to 4096 per side
+ * (GEMPE_E_INVALID_ARG beyond).  Arguments and result are those of
+ * gempe_fit_sigma; synchronises cuda_stream.  The first call on a device
+ * looks up the array's device address and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race. */
+gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float hist_max, float mu,
+                                    void* cuda_stream, float* out_sigma);
+
 gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
 
 /* Message of the last failure on this thread ("" if none). */

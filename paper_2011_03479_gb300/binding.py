@@ -109,6 +109,7 @@ def load(build: bool = True):
         "gempe_is_edge": (st, [vp, vp, sz, vp]),
         "gempe_loss": (st, [vp, P(ctypes.c_double), P(ctypes.c_float)]),
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
+        "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
         "gempe_last_error": (ctypes.c_char_p, []),
     }
@@ -288,6 +289,15 @@ def gempe_fit_sigma(hist_e, hist_n, hist_max: float = 12.0, mu: float = 1.5, str
     out = ctypes.c_float()
     _check(load().gempe_fit_sigma(_ptr(h), len(h) // 2, float(hist_max), float(mu),
                                   _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def gempe_fit_sigma_static(hist_e, hist_n, hist_max: float = 12.0, mu: float = 1.5, stream=None) -> float:
+    """gempe_fit_sigma without device allocation (static 4096-bin scratch)."""
+    h = np.ascontiguousarray(np.concatenate([hist_e, hist_n]), dtype=np.float32)
+    out = ctypes.c_float()
+    _check(load().gempe_fit_sigma_static(_ptr(h), len(h) // 2, float(hist_max), float(mu),
+                                         _stream_handle(stream), ctypes.byref(out)))
     return out.value
 
 

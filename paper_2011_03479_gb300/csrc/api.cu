@@ -707,3 +707,7 @@ GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
 }
 
 GEMPE_API const char* gempe_last_error(void) { return g_last_error.c_str(); }
+
+namespace gempe {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace gempe

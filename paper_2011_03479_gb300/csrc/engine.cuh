@@ -91,6 +91,9 @@ int sampler_grid(int n, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s);
+// Message for gempe_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Mills-ratio table (host side): builds the coefficients and uploads them to
 // the current device once.
 cudaError_t ensure_mills_table();
