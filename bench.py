@@ -40,7 +40,8 @@ METRIC = "pair-updates/sec per GEMPE epoch"
 UNIT = "pair-updates/s"
 WORKLOAD = "rmat-s16-ef16"
 L2_FLUSH_BYTES = 256 << 20
-EDGE_CHUNK = 64      # work-unit size of the sweep (CSR slots per unit)
+EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
+UNIT_PAIRS = 128     # edge + sample slots per packed work unit of the d <= 4 sweep
 
 
 def _peaks():
@@ -52,22 +53,42 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def sweep_algorithmic_bytes(n, nnz, d, n_units, draws, accepted):
+def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted):
     """Bytes one sweep launch must move at least, each random gather paid once
-    at its minimum size (no reuse): CSR streamed once, work units, own row,
-    one neighbour row per CSR slot, one 32-byte hash sector per draw, the
-    partner row and a read-modify-write of the partner's accumulator row per
-    accepted sample, a read-modify-write of the own accumulator row."""
+    at its minimum size (no reuse): CSR streamed once, work units, the sample
+    slots, own row, one neighbour row per CSR slot, the partner row and a
+    read-modify-write of the partner's accumulator row per accepted sample,
+    a read-modify-write of every own accumulator row."""
     row = 4 * d
     acc_row = 4 * (((d + 1) + 3) // 4 * 4)
-    return (4 * (n + 1) + 4 * nnz + 16 * n_units + n * row + nnz * row + 32 * draws
+    return (4 * (n + 1) + 4 * nnz + 16 * n_units + 4 * n * k + n * row + nnz * row
             + accepted * (row + 2 * acc_row) + n * 2 * acc_row)
 
 
-def work_units(row_ptr):
+def sampler_algorithmic_bytes(n, k, draws):
+    """One 32-byte hash-set sector per draw and the 4-byte partner per slot."""
+    return 32 * draws + 4 * n * k
+
+
+def work_units(row_ptr, k, d):
+    """Number of sweep work units (mirrors the library's unit building)."""
     import numpy as np
-    deg = np.diff(row_ptr)
-    return int(np.maximum(1, (deg + EDGE_CHUNK - 1) // EDGE_CHUNK).sum())
+    deg = np.diff(row_ptr).astype(np.int64)
+    if d > 4:
+        return int(np.maximum(1, (deg + EDGE_CHUNK - 1) // EDGE_CHUNK).sum())
+    units, i, n = 0, 0, len(deg)
+    pairs = deg + k
+    while i < n:
+        if pairs[i] > UNIT_PAIRS:
+            units += int((deg[i] - 1) // UNIT_PAIRS) + 1 if deg[i] > UNIT_PAIRS else 1
+            i += 1
+            continue
+        v0, tot = i, 0
+        while i < n and i - v0 < 32 and pairs[i] <= UNIT_PAIRS and tot + pairs[i] <= UNIT_PAIRS:
+            tot += pairs[i]
+            i += 1
+        units += 1
+    return units
 
 
 # ---------------------------------------------------------------------------
@@ -285,8 +306,8 @@ def run_gempe(args):
         return
 
     peak, peak_kind = _peaks()
-    units = work_units(rp)
-    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, units, draws / args.steps, accepted / args.steps)
+    units = work_units(rp, k, d)
+    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, k, units, accepted / args.steps)
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = bytes_per_sweep / sweep_s / 1e9
     traffic = _profile_traffic(kernel_source_hash())
@@ -304,7 +325,9 @@ def run_gempe(args):
         "update_ms": statistics.mean(step_ms) - statistics.mean(sweep_ms),
         "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
-                     "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic},
+                     "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic,
+                     "note": "sweep window = sweep kernel with the next epoch's sampler running beside it"},
+        "sampler_algorithmic_bytes_per_launch": sampler_algorithmic_bytes(n, k, draws / args.steps),
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
