@@ -53,7 +53,15 @@
  *   initial positions  (i, q, 0, 0x0A000000)         -> coordinates 4q..4q+3
  *   epoch samples      (i, epoch, t, 0x0B000000|a>>2) -> word a&3 (attempt a)
  *   loss samples       (i, epoch, t, 0x0E000000|a>>2) -> word a&3
+ *   block partners     (tile, epoch, p>>2, 0x0D000000) -> word p&3
  * A 32-bit word r maps to vertex floor(r * n / 2^32).
+ *
+ * Block sampling (the representation-learning form): vertices are cut into
+ * tiles of T consecutive ids; every vertex of a tile takes the same P
+ * partners, drawn per tile and epoch.  A pair (i, g) whose partner is i
+ * itself or a neighbour of i is masked (skipped, not redrawn); the unmasked
+ * partners of i are its sampled non-edges for the epoch, with histogram
+ * weight (n-1-deg_i) / (2 * unmasked_i).
  */
 #include <math.h>
 #include <stdint.h>
@@ -254,6 +262,14 @@ static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_
     }
 }
 
+/* Partners of tile `tile` in block sampling (P of them, duplicates kept). */
+void orc_block_partners(int32_t n, int32_t tile, int32_t epoch, uint64_t seed, int32_t P, int32_t* out) {
+    for (int32_t p = 0; p < P; ++p) {
+        uint32_t r = philox_word(seed, (uint32_t)tile, (uint32_t)epoch, (uint32_t)(p >> 2), 0x0D000000u, p & 3);
+        out[p] = (int32_t)draw_vertex(r, (uint32_t)n);
+    }
+}
+
 void orc_sample(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t epoch,
                 uint64_t seed, int32_t loss_stream, int32_t k, int32_t max_retries, int32_t* samples) {
     uint32_t tag = loss_stream ? 0x0E000000u : 0x0B000000u;
@@ -270,9 +286,13 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
               int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
               double* y, double* z, double* x_new, double* hist_e, double* hist_n,
-              int32_t* samples_out, int64_t* stats, double* absd) {
+              int32_t* samples_out, int64_t* stats, double* absd,
+              int32_t block_P, int32_t block_T, int32_t* partners_out) {
+    /* block sampling replaces the per-vertex samples */
+    if (block_P > 0) k = 0;
     int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
-    if (!smp) return -1;
+    int32_t* part = (int32_t*)malloc((size_t)(block_P > 0 ? block_P : 1) * sizeof(int32_t));
+    if (!smp || !part) { free(smp); free(part); return -1; }
     g_absd = absd;
     if (absd) memset(absd, 0, sizeof(double) * (size_t)n);
     memset(y, 0, sizeof(double) * (size_t)n * d);          /* zero numerators ... */
@@ -308,6 +328,32 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
             if (hist_n) hist_n[hist_bin(delta, B, hist_max)] += omega;
         }
     }
+    /* block-sampled non-edges: every vertex of a tile against the tile's partners */
+    if (block_P > 0) {
+        int32_t n_tiles = (n + block_T - 1) / block_T;
+        for (int32_t tile = 0; tile < n_tiles; ++tile) {
+            orc_block_partners(n, tile, epoch, seed, block_P, part);
+            if (partners_out) memcpy(partners_out + (int64_t)tile * block_P, part, sizeof(int32_t) * (size_t)block_P);
+            for (int32_t i = tile * block_T; i < n && i < (tile + 1) * block_T; ++i) {
+                int32_t acc = 0;
+                for (int32_t p = 0; p < block_P; ++p)
+                    acc += (part[p] != i && !orc_is_edge(row_ptr, col_idx, i, part[p]));
+                accepted += acc;
+                rejected += block_P - acc;
+                double deg = (double)(row_ptr[i + 1] - row_ptr[i]);
+                double omega = acc ? ((double)n - 1.0 - deg) / (2.0 * acc) : 0.0;
+                for (int32_t p = 0; p < block_P; ++p) {
+                    int32_t g = part[p];
+                    if (g == i || orc_is_edge(row_ptr, col_idx, i, g)) continue;   /* masked */
+                    double delta = dist(x, d, i, g), dd, w;
+                    orc_parabola(delta, mu, sigma, 0, w_formula, clamp_neg_d, &dd, &w);
+                    add_wm_term(y, z, x, d, i, g, delta, dd, w);
+                    if (symmetric) add_wm_term(y, z, x, d, g, i, delta, dd, w);
+                    if (hist_n) hist_n[hist_bin(delta, B, hist_max)] += omega;
+                }
+            }
+        }
+    }
     /* x_i := y_i / z_i */
     for (int32_t i = 0; i < n; ++i)
         for (int32_t c = 0; c < d; ++c)
@@ -316,6 +362,7 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
     if (stats) { stats[0] = accepted; stats[1] = rejected; stats[2] = exhausted; stats[3] = accepted + rejected; }
     g_absd = NULL;
     free(smp);
+    free(part);
     return 0;
 }
 
@@ -452,7 +499,8 @@ double orc_loss_sampled(int32_t n, const int32_t* row_ptr, const int32_t* col_id
 int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
             double* x, double* sigma, double mu, int32_t epoch0, int32_t epochs, uint64_t seed,
             int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
-            double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats) {
+            double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats,
+            int32_t block_P, int32_t block_T) {
     size_t nd = (size_t)n * d;
     double* y = (double*)malloc(nd * sizeof(double));
     double* z = (double*)malloc((size_t)n * sizeof(double));
@@ -465,7 +513,8 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
     for (int32_t e = 0; e < epochs; ++e) {
         int32_t ep = epoch0 + e;
         orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
-                  w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL);
+                  w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL,
+                  block_P, block_T, NULL);
         memcpy(x, xn, nd * sizeof(double));
         if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0)
             *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);

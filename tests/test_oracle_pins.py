@@ -401,3 +401,46 @@ def test_histograms_count_pairs(oracle_mod, sbm_1000):
     de = np.linalg.norm(x[rows[up]] - x[ci[up]], axis=1)
     ref, _ = np.histogram(np.minimum(de, 12.0 - 1e-9), bins=1024, range=(0.0, 12.0))
     np.testing.assert_array_equal(r["hist_e"], ref)
+
+
+# ---------------------------------------------------------------------------
+# Block sampling (representation-learning form)
+# ---------------------------------------------------------------------------
+def test_block_sampling_semantics(oracle_mod, sbm_small):
+    """Every vertex of a tile meets the tile's partners; pairs with the vertex
+    itself or a neighbour are masked (not redrawn); the weights of the
+    unmasked pairs add up to the number of non-edges; the gradient identity
+    of Eq. 3 holds for the block pairs as for any pair list."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    T, P, seed, ep = 16, 12, 91, 3
+    adj = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(n)]
+    x = np.random.default_rng(8).normal(size=(n, 2)) * 1.3
+    r = oracle_mod.epoch(rp, ci, x, 0.8, ep, seed, k=5, block_partners=P, tile_vertices=T, clamp_neg_d=0)
+    parts = r["partners"]
+    assert parts.shape == ((n + T - 1) // T, P)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    masked = 0
+    samples = np.full((n, P), -1, dtype=np.int32)
+    for tile in range(parts.shape[0]):
+        for p in range(P):
+            word = int(oracle_mod.philox4x32_10([tile, ep, p >> 2, 0x0D000000], key)[p & 3])
+            assert parts[tile, p] == (word * n) >> 32
+        for i in range(tile * T, min(n, (tile + 1) * T)):
+            for p in range(P):
+                g = int(parts[tile, p])
+                if g == i or g in adj[i]:
+                    masked += 1
+                else:
+                    samples[i, p] = g
+    assert r["rejected"] == masked and r["accepted"] == n * P - masked
+    assert r["hist_n"].sum() == pytest.approx(n * (n - 1) / 2 - len(ci) // 2, rel=1e-12)
+    # the per-vertex sample lists reproduce the epoch's sums through the identity
+    h = 1e-6
+    for i in range(0, n, 11):
+        for c in range(2):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            g = (oracle_mod.surrogate_L(rp, ci, xp, 0.8, samples)
+                 - oracle_mod.surrogate_L(rp, ci, xm, 0.8, samples)) / (2 * h)
+            assert r["delta"][i, c] == pytest.approx(-0.5 * g, rel=2e-6, abs=1e-8)
