@@ -39,6 +39,12 @@ sys.path.insert(0, ROOT)
 METRIC = "pair-updates/sec per GEMPE epoch"
 UNIT = "pair-updates/s"
 WORKLOAD = "rmat-s16-ef16"
+# engine parameters of each workload (the graph and d, k come from inputs.WORKLOADS)
+FORMS = {
+    "rmat-s16-ef16": {},
+    "ba-n1m-m8": {"block_partners": 64, "precision": 1},          # BF16 + tensor-core tiles
+    "ba-n1m-m8-fp32": {"block_partners": 64, "precision": 0},     # the plain FP32 run of the same seed
+}
 L2_FLUSH_BYTES = 256 << 20
 EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
 UNIT_PAIRS = 128     # edge + sample slots per packed work unit of the d <= 4 sweep
@@ -212,11 +218,13 @@ def run_gempe(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = inputs.WORKLOADS[WORKLOAD]()
+    workload = args.workload
+    w = inputs.WORKLOADS[workload.replace("-fp32", "")]()
     rp, ci = w["row_ptr"], w["col_idx"]
     n, nnz, d, k = len(rp) - 1, len(ci), w["d"], w["k"]
     m = nnz // 2
-    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED)
+    form = FORMS[workload]
+    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED, **form)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -307,15 +315,19 @@ def run_gempe(args):
 
     peak, peak_kind = _peaks()
     units = work_units(rp, k, d)
-    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, k, units, accepted / args.steps)
+    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, 0 if form else k, units,
+                                              0 if form else accepted / args.steps)
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = bytes_per_sweep / sweep_s / 1e9
     traffic = _profile_traffic(kernel_source_hash())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "m": m, "d": d, "k": k, "sigma_every": 1,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 positions, f32 sums" if form.get("precision") else "f32", "data": "synthetic",
+        "config": {"workload": workload, "n": n, "m": m, "d": d,
+                   "sampling": "block 128x64" if form.get("block_partners") else f"k={k} per vertex",
+                   "sigma_every": 1,
                    "step": "one epoch: gempe_sweep + gempe_update",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
@@ -380,6 +392,8 @@ def main():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(FORMS), default=WORKLOAD,
+                    help="graph-drawing workload (default) or the representation-learning forms")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 50:

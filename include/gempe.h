@@ -65,6 +65,13 @@ typedef struct gempe_params {
     uint64_t seed;          /* Philox4x32-10 key */
     int32_t hist_bins;      /* B distance-histogram bins on [0, hist_max) (Sec. III.F), 16..4096 */
     float hist_max;         /* 12.0 */
+    int32_t precision;      /* 0: FP32 positions; 1: BF16 shadow positions feed the pair arithmetic
+                               (FP32 master positions and sums), d >= 8 */
+    int32_t block_partners; /* 0: k sampled non-edges per vertex; 64: block sampling -- every tile of
+                               tile_vertices consecutive vertices shares 64 partners per epoch,
+                               pairs with the vertex itself or a neighbour are masked; d >= 8.  With
+                               precision 1 and d in {16, 32, 64} the tiles run on tensor cores */
+    int32_t tile_vertices;  /* 128 (the only tile size) */
     /* Optional device allocator (e.g. a framework's caching allocator).  When
      * dev_alloc is null the engine uses cudaMalloc / cudaFree. */
     void* (*dev_alloc)(size_t bytes, void* user);
@@ -89,7 +96,8 @@ typedef struct gempe_ctx gempe_ctx;
 
 /* Fill *p with the defaults: mu 1.5, sigma0 1, sigma_every 1, k 5, max_retries
  * 32, symmetric 1, derived w, clamp 1, z_min 1e-30, init_range 1, seed
- * 0x6E6D7065, 1024 bins on [0, 12), no custom allocator. */
+ * 0x6E6D7065, 1024 bins on [0, 12), FP32, per-vertex sampling (tile size
+ * 128 for block sampling), no custom allocator. */
 void gempe_default_params(gempe_params* p);
 
 /* Create an embedding context from a host CSR graph (Sec. II.A: G, n, d).
@@ -119,7 +127,8 @@ gempe_status gempe_step(gempe_ctx* ctx, int32_t iters);
  * (Sec. III.F).  Positions, sigma and the epoch counter are unchanged; the
  * sums stay for gempe_accumulators / gempe_histograms until gempe_update.
  * host_samples: NULL, or host int32[n*k] that receives the accepted partner
- * of each (vertex, sample slot), -1 if dropped (synchronises).
+ * of each (vertex, sample slot), -1 if dropped (synchronises); with block
+ * sampling int32[n*64]: partner p of the vertex's tile, -1 where masked.
  * gempe_step between gempe_sweep and gempe_update is GEMPE_E_INVALID_ARG. */
 gempe_status gempe_sweep(gempe_ctx* ctx, int32_t* host_samples);
 

@@ -42,6 +42,9 @@ class gempe_params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("hist_bins", ctypes.c_int32),
         ("hist_max", ctypes.c_float),
+        ("precision", ctypes.c_int32),
+        ("block_partners", ctypes.c_int32),
+        ("tile_vertices", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
@@ -153,9 +156,10 @@ def gempe_default_params(**overrides) -> gempe_params:
 class _Ctx:
     """Owned context handle (destroyed with gempe_destroy on close / GC)."""
 
-    def __init__(self, handle, n, d, k, keep=()):
+    def __init__(self, handle, n, d, k, keep=(), slots=None):
         self.handle = handle
         self.n, self.d, self.k = n, d, k
+        self.slots = k if slots is None else slots   # sample slots per vertex in a sweep
         self._keep = keep   # allocator callbacks must outlive the context
 
     def close(self):
@@ -184,7 +188,7 @@ def gempe_create(row_ptr, col_idx, d: int, params: gempe_params | None = None, s
     h = ctypes.c_void_p()
     _check(load().gempe_create(_ptr(rp), _ptr(ci) if len(ci) else ctypes.c_void_p(None), n, d,
                                ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
-    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,))
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex)
 
 
 def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | None = None,
@@ -197,7 +201,7 @@ def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | Non
     _check(load().gempe_create_device(ctypes.c_void_p(d_row_ptr.data_ptr()),
                                       ctypes.c_void_p(d_col_idx.data_ptr() if nnz else None), n, nnz, d,
                                       ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
-    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,))
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex)
 
 
 def gempe_destroy(ctx: _Ctx) -> None:
@@ -209,10 +213,11 @@ def gempe_step(ctx: _Ctx, iters: int = 1) -> None:
 
 
 def gempe_sweep(ctx: _Ctx, record_samples: bool = False):
-    if record_samples and ctx.k > 0:
-        out = np.empty(ctx.n * ctx.k, dtype=np.int32)
+    slots = ctx.slots
+    if record_samples and slots > 0:
+        out = np.empty(ctx.n * slots, dtype=np.int32)
         _check(load().gempe_sweep(ctx.handle, _ptr(out)))
-        return out.reshape(ctx.n, ctx.k)
+        return out.reshape(ctx.n, slots)
     _check(load().gempe_sweep(ctx.handle, ctypes.c_void_p(None)))
     return None
 

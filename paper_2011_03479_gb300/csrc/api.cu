@@ -68,6 +68,16 @@ struct gempe_ctx {
     int32_t* scratch_i32 = nullptr;   // n*k inspection samples / flags
     int32_t* samples = nullptr;       // [2][n*k] sampled partners, buffer = epoch & 1
     int sampler_grid = 0;
+    __nv_bfloat16* xb = nullptr;      // BF16 shadow positions (precision form)
+    bool block = false;               // block sampling
+    bool tiles = false;               // block samples on the tensor-core tile kernel
+    int32_t n_tiles = 0;
+    int32_t* block_part = nullptr;    // [2][n_tiles][64]
+    unsigned long long* block_mask = nullptr;   // [2][n]
+    int4* sampler_units = nullptr;    // block sampler work units {tile, e_lo, e_hi, first}
+    int32_t n_sampler_units = 0;
+    const MillsCoef* mills = nullptr;
+    int32_t slots() const { return block ? kBlockP : k; }
     int sweep_grid = 0, update_grid = 0;
     bool swept = false;               // a sweep ran without the update that clears its sums
     cudaGraph_t graph = nullptr;
@@ -126,6 +136,14 @@ EpochArgs epoch_args(const gempe_ctx* c) {
     a.key_lo = (uint32_t)c->p.seed;
     a.key_hi = (uint32_t)(c->p.seed >> 32);
     a.samples = c->samples;
+    a.xb = c->xb;
+    a.block_P = c->block ? kBlockP : 0;
+    a.block_T = kBlockT;
+    a.n_tiles = c->n_tiles;
+    a.block_part = c->block_part;
+    a.block_mask = c->block_mask;
+    a.sweep_samples = c->tiles ? 0 : 1;
+    a.mills = c->mills;
     return a;
 }
 
@@ -137,7 +155,8 @@ UpdateArgs update_args(const gempe_ctx* c) {
     u.hist_c = c->hist_c;
     u.hist_d = c->hist_d;
     u.hist_x = c->hist_x;
-    u.k = c->k;
+    u.k = c->slots();
+    u.xb = c->xb;
     u.st = c->st;
     u.n = c->n;
     u.d = c->d;
@@ -166,6 +185,12 @@ gempe_status check_params(const gempe_params* p, int32_t n, int32_t d) {
     if (p->sigma_every < 0) return fail(GEMPE_E_INVALID_ARG, "sigma_every must be >= 0");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(GEMPE_E_INVALID_ARG, "dev_alloc and dev_free must be given together");
+    if (p->precision != 0 && p->precision != 1) return fail(GEMPE_E_INVALID_ARG, "precision must be 0 or 1");
+    if (p->precision == 1 && d < 8) return fail(GEMPE_E_INVALID_ARG, "the BF16 form needs d >= 8");
+    if (p->block_partners != 0 && p->block_partners != kBlockP)
+        return fail(GEMPE_E_INVALID_ARG, "block_partners must be 0 or 64");
+    if (p->block_partners && (d < 8 || (p->tile_vertices != 0 && p->tile_vertices != kBlockT)))
+        return fail(GEMPE_E_INVALID_ARG, "block sampling needs d >= 8 and tile_vertices 128");
     return GEMPE_OK;
 }
 
@@ -295,9 +320,18 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     unsigned long long slots = 16;
     while (slots < 2ull * (unsigned long long)nnz) slots <<= 1;
     c->bucket_mask = slots / 4 - 1;
-    // the per-block sums of sampled anchors' degrees are 32-bit: k * nnz must stay below 2^32
-    if ((unsigned long long)p->neg_per_vertex * (unsigned long long)nnz >= (1ull << 32))
-        return bail(fail(GEMPE_E_INVALID_ARG, "neg_per_vertex * nnz must be below 2^32"));
+    c->block = p->block_partners > 0;
+    c->tiles = c->block && p->precision == 1 && tile_dim(d);
+    c->n_tiles = (n + kBlockT - 1) / kBlockT;
+    // the per-block sums of sampled anchors' degrees are 32-bit: slots * nnz must stay below 2^32
+    if ((unsigned long long)std::max(p->neg_per_vertex, c->slots()) * (unsigned long long)nnz >= (1ull << 32))
+        return bail(fail(GEMPE_E_INVALID_ARG, "sample slots * nnz must be below 2^32"));
+    c->mills = mills_table_device();
+    if (!c->mills) return bail(fail(GEMPE_E_CUDA, "Mills table address"));
+    if (c->tiles) {
+        e = prepare_tile_kernel(d, p->hist_bins);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "tile kernel attributes"));
+    }
     std::vector<int4> items = (d <= kPackedMaxDim) ? build_packed_units(rp_host, n, p->neg_per_vertex)
                                                    : build_chunk_units(rp_host, n);
     c->n_items = (int32_t)items.size();
@@ -319,8 +353,31 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     c->st = (DevState*)c->alloc(sizeof(DevState));
     c->items = (int4*)c->alloc(sizeof(int4) * items.size());
     c->scratch_i32 = (int32_t*)c->alloc(sizeof(int32_t) * std::max<size_t>((size_t)n * c->k, 1));
-    c->samples = (int32_t*)c->alloc(sizeof(int32_t) * std::max<size_t>(2 * (size_t)n * c->k, 1));
+    c->samples = (int32_t*)c->alloc(sizeof(int32_t) * std::max<size_t>(c->block ? 1 : 2 * (size_t)n * c->k, 1));
     if (!c->samples) return bail(fail(GEMPE_E_OOM, "device allocation failed"));
+    if (p->precision == 1) {
+        c->xb = (__nv_bfloat16*)c->alloc(sizeof(__nv_bfloat16) * (size_t)n * d);
+        if (!c->xb) return bail(fail(GEMPE_E_OOM, "device allocation failed"));
+    }
+    std::vector<int4> sunits;
+    if (c->block) {
+        for (int32_t t = 0; t < c->n_tiles; ++t) {
+            const int32_t v0 = t * kBlockT, v1 = std::min(n, v0 + kBlockT);
+            const int32_t e0 = rp_host[v0], e1 = rp_host[v1];
+            int32_t e = e0;
+            do {
+                const int32_t eh = std::min(e1, e + kSamplerChunk);
+                sunits.push_back(make_int4(t, e, eh, e == e0 ? 1 : 0));
+                e = eh;
+            } while (e < e1);
+        }
+        c->n_sampler_units = (int32_t)sunits.size();
+        c->block_part = (int32_t*)c->alloc(sizeof(int32_t) * 2 * (size_t)c->n_tiles * kBlockP);
+        c->block_mask = (unsigned long long*)c->alloc(sizeof(unsigned long long) * 2 * (size_t)n);
+        c->sampler_units = (int4*)c->alloc(sizeof(int4) * sunits.size());
+        if (!c->block_part || !c->block_mask || !c->sampler_units)
+            return bail(fail(GEMPE_E_OOM, "device allocation failed"));
+    }
     if (!c->row_ptr || !c->col_idx || !c->keys || !c->x || !c->acc || !c->hist || !c->st || !c->items ||
         !c->scratch_i32)
         return bail(fail(GEMPE_E_OOM, "device allocation failed"));
@@ -339,6 +396,12 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     CKB(cudaMemcpyAsync(c->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st),
         "copy work units");
     CKB(cudaMemsetAsync(c->keys, 0xFF, sizeof(unsigned long long) * slots, st), "clear hash");
+    if (c->block) {
+        CKB(cudaMemsetAsync(c->block_mask, 0, sizeof(unsigned long long) * 2 * (size_t)n, st), "clear masks");
+        CKB(cudaMemcpyAsync(c->sampler_units, sunits.data(), sizeof(int4) * sunits.size(), cudaMemcpyHostToDevice,
+                            st),
+            "copy sampler units");
+    }
     CKB(cudaMemsetAsync(c->acc, 0, sizeof(float) * (size_t)n * c->acc_stride, st), "clear acc");
     CKB(cudaMemsetAsync(c->hist, 0, c->hist_bytes, st), "clear hist");
     DevState init{};
@@ -347,7 +410,7 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     CKB(cudaMemsetAsync(c->scratch_i32, 0, sizeof(int32_t), st), "clear flag");
     CKB(launch_hash_build(c->row_ptr, c->col_idx, n, nnz, c->keys, c->bucket_mask, c->scratch_i32, st),
         "hash build");
-    CKB(launch_init_positions(c->x, n, d, (uint32_t)p->seed, (uint32_t)(p->seed >> 32), p->init_range, st),
+    CKB(launch_init_positions(c->x, c->xb, n, d, (uint32_t)p->seed, (uint32_t)(p->seed >> 32), p->init_range, st),
         "init positions");
     int32_t hash_fail = 0;
     CKB(cudaMemcpyAsync(&hash_fail, c->scratch_i32, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "read flag");
@@ -363,9 +426,14 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
 
 // Samples of the current epoch, when the buffer does not hold them yet
 // (after create or set_state): drawn on the main stream.
+cudaError_t launch_epoch_sampler(gempe_ctx* c, cudaStream_t s) {
+    if (c->block) return launch_block_sampler(epoch_args(c), c->sampler_units, c->n_sampler_units, c->sm_count, s);
+    return launch_sampler(epoch_args(c), c->sampler_grid, s);
+}
+
 gempe_status prime_samples(gempe_ctx* c) {
-    if (c->primed || c->k == 0) return GEMPE_OK;
-    CK(launch_sampler(epoch_args(c), c->sampler_grid, c->stream), "sampler");
+    if (c->primed || c->slots() == 0) return GEMPE_OK;
+    CK(launch_epoch_sampler(c, c->stream), "sampler");
     c->primed = true;
     return GEMPE_OK;
 }
@@ -375,14 +443,15 @@ gempe_status prime_samples(gempe_ctx* c) {
 gempe_status enqueue_sweep(gempe_ctx* c) {
     gempe_status s = prime_samples(c);
     if (s != GEMPE_OK) return s;
-    if (c->k > 0 && !c->sampled_ahead) {
+    if (c->slots() > 0 && !c->sampled_ahead) {
         CK(cudaEventRecord(c->fork_ev, c->stream), "fork");
         CK(cudaStreamWaitEvent(c->side, c->fork_ev, 0), "fork");
-        CK(launch_sampler(epoch_args(c), c->sampler_grid, c->side), "sampler");
+        CK(launch_epoch_sampler(c, c->side), "sampler");
         CK(cudaEventRecord(c->join_ev, c->side), "join");
         c->sampled_ahead = true;
     }
     CK(launch_sweep(epoch_args(c), c->sweep_grid, c->stream), "sweep");
+    if (c->tiles) CK(launch_tile_bf16(epoch_args(c), c->sm_count, c->stream), "tiles");
     return GEMPE_OK;
 }
 
@@ -427,6 +496,9 @@ GEMPE_API void gempe_default_params(gempe_params* p) {
     p->seed = 0x6E6D7065ull;
     p->hist_bins = 1024;
     p->hist_max = 12.0f;
+    p->precision = 0;
+    p->block_partners = 0;
+    p->tile_vertices = kBlockT;
 }
 
 GEMPE_API gempe_status gempe_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
@@ -506,22 +578,52 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
     if (!c) return fail(GEMPE_E_INVALID_ARG, "ctx is null");
     // accumulators and histograms are zero between epochs (the update clears
     // them); only a repeated sweep has to clear its predecessor's sums
+    if (c->swept && c->block)
+        return fail(GEMPE_E_INVALID_ARG, "block sampling: call gempe_update before the next gempe_sweep");
     if (c->swept) {
         CK(cudaMemsetAsync(c->acc, 0, sizeof(float) * (size_t)c->n * c->acc_stride, c->stream), "clear acc");
         CK(cudaMemsetAsync(c->hist, 0, c->hist_bytes, c->stream), "clear hist");
     }
-    gempe_status s = enqueue_sweep(c);
-    if (s != GEMPE_OK) return s;
-    c->swept = true;
-    if (host_samples && c->k > 0) {
+    std::vector<int32_t> bpart;
+    std::vector<unsigned long long> bmask;
+    if (host_samples && c->block) {
+        // the sweep clears the masks it reads: take the record before it runs
+        gempe_status ps = prime_samples(c);
+        if (ps != GEMPE_OK) return ps;
         int32_t epoch = 0;
         CK(cudaMemcpyAsync(&epoch, &c->st->epoch, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "epoch");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
-        const size_t nk = (size_t)c->n * c->k;
-        CK(cudaMemcpyAsync(host_samples, c->samples + (size_t)(epoch & 1) * nk, sizeof(int32_t) * nk,
-                           cudaMemcpyDeviceToHost, c->stream),
-           "copy samples");
+        bpart.resize((size_t)c->n_tiles * kBlockP);
+        bmask.resize((size_t)c->n);
+        CK(cudaMemcpyAsync(bpart.data(), c->block_part + (size_t)(epoch & 1) * bpart.size(),
+                           sizeof(int32_t) * bpart.size(), cudaMemcpyDeviceToHost, c->stream),
+           "copy partners");
+        CK(cudaMemcpyAsync(bmask.data(), c->block_mask + (size_t)(epoch & 1) * bmask.size(),
+                           sizeof(unsigned long long) * bmask.size(), cudaMemcpyDeviceToHost, c->stream),
+           "copy masks");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
+    }
+    gempe_status s = enqueue_sweep(c);
+    if (s != GEMPE_OK) return s;
+    c->swept = true;
+    if (host_samples && c->slots() > 0) {
+        int32_t epoch = 0;
+        CK(cudaMemcpyAsync(&epoch, &c->st->epoch, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "epoch");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        if (c->block) {
+            const std::vector<int32_t>& part = bpart;
+            const std::vector<unsigned long long>& mask = bmask;
+            for (int32_t i = 0; i < c->n; ++i)
+                for (int q = 0; q < kBlockP; ++q)
+                    host_samples[(size_t)i * kBlockP + q] =
+                        ((mask[i] >> q) & 1ull) ? -1 : part[(size_t)(i / kBlockT) * kBlockP + q];
+        } else {
+            const size_t nk = (size_t)c->n * c->k;
+            CK(cudaMemcpyAsync(host_samples, c->samples + (size_t)(epoch & 1) * nk, sizeof(int32_t) * nk,
+                               cudaMemcpyDeviceToHost, c->stream),
+               "copy samples");
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+        }
     }
     return GEMPE_OK;
 }
@@ -553,6 +655,7 @@ GEMPE_API gempe_status gempe_set_positions(gempe_ctx* c, const float* host_x, si
     for (size_t q = 0; q < count; ++q)
         if (!std::isfinite(host_x[q])) return fail(GEMPE_E_INVALID_ARG, "positions must be finite");
     CK(cudaMemcpyAsync(c->x, host_x, sizeof(float) * count, cudaMemcpyHostToDevice, c->stream), "copy x");
+    if (c->xb) CK(launch_to_bf16(c->x, c->xb, (long long)count, c->stream), "BF16 shadow");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return GEMPE_OK;
 }
@@ -571,6 +674,8 @@ GEMPE_API gempe_status gempe_set_state(gempe_ctx* c, float sigma, int32_t epoch)
     h.sample_epoch = epoch;     // the buffer is refilled for this epoch before the next sweep
     h.sample_done = 0;
     c->primed = false;
+    if (c->block)
+        CK(cudaMemsetAsync(c->block_mask, 0, sizeof(unsigned long long) * 2 * (size_t)c->n, c->stream), "clear masks");
     CK(cudaMemcpyAsync(c->st, &h, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "write state");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return GEMPE_OK;
@@ -610,10 +715,10 @@ GEMPE_API gempe_status gempe_histograms(gempe_ctx* c, float* host_out, size_t co
     const unsigned int* he = (const unsigned int*)(hd + B);
     const unsigned int* hc = he + B;
     const float* hx = (const float*)(hc + B);
+    const int ks = c->slots();
     for (size_t b = 0; b < B; ++b) {
         host_out[b] = (float)he[b];
-        host_out[B + b] = c->k > 0 ? (float)(((double)(c->n - 1) * hc[b] - (double)hd[b]) / (2.0 * c->k) + hx[b])
-                                   : 0.0f;
+        host_out[B + b] = ks > 0 ? (float)(((double)(c->n - 1) * hc[b] - (double)hd[b]) / (2.0 * ks) + hx[b]) : 0.0f;
     }
     return GEMPE_OK;
 }
@@ -621,6 +726,8 @@ GEMPE_API gempe_status gempe_histograms(gempe_ctx* c, float* host_out, size_t co
 GEMPE_API gempe_status gempe_sample(gempe_ctx* c, int32_t stream_id, int32_t* host_out, size_t count) {
     if (!c || !host_out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     if (stream_id != 0 && stream_id != 1) return fail(GEMPE_E_INVALID_ARG, "stream_id must be 0 or 1");
+    if (stream_id == 0 && c->block)
+        return fail(GEMPE_E_INVALID_ARG, "block sampling: the epoch's samples come from gempe_sweep's record");
     if (count != (size_t)c->n * c->k) return fail(GEMPE_E_INVALID_ARG, "count must be n*k");
     if (c->k == 0) return GEMPE_OK;
     EpochArgs a = epoch_args(c);

@@ -1,5 +1,6 @@
 // Internal interface between the C-ABI host code and the CUDA kernels.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,10 +61,23 @@ struct EpochArgs {
     float mu, hist_scale;  // hist_scale = bins / hist_max
     uint32_t key_lo, key_hi;
     int32_t* samples;      // [2][n][k] accepted partners (-1 = dropped), buffer = epoch & 1
+    // precision form: BF16 shadow of x (null in the FP32 form)
+    __nv_bfloat16* xb;
+    // block sampling: tiles of block_T vertices share block_P partners
+    int32_t block_P, block_T, n_tiles;
+    int32_t* block_part;             // [2][n_tiles][block_P], buffer = epoch & 1
+    unsigned long long* block_mask;  // [2][n] bit p set: partner p of the vertex's tile is masked
+    int32_t sweep_samples;           // 0: the sweep leaves the sampled non-edges to the tile kernel
+    const struct MillsCoef* mills;   // Mills-ratio table on this device
 };
+
+// Sampled-partner layout of block sampling.
+constexpr int kBlockP = 64;
+constexpr int kBlockT = 128;
 
 struct UpdateArgs {
     float* x;
+    __nv_bfloat16* xb;     // BF16 shadow, or null
     float* acc;
     unsigned int* hist_e;
     unsigned int* hist_c;
@@ -80,13 +94,21 @@ bool supported_dim(int d);
 cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                               unsigned long long* keys, unsigned long long bucket_mask,
                               int32_t* fail_flag, cudaStream_t s);
-cudaError_t launch_init_positions(float* x, int32_t n, int32_t d, uint32_t key_lo, uint32_t key_hi,
-                                  float range, cudaStream_t s);
+cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_t d, uint32_t key_lo,
+                                  uint32_t key_hi, float range, cudaStream_t s);
 cudaError_t launch_sweep(const EpochArgs& a, int grid, cudaStream_t s);
 int sweep_grid(int d, int bins, int sm_count);
 cudaError_t launch_update(const UpdateArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
+                                 cudaStream_t s);
+constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
+cudaError_t launch_tile_bf16(const EpochArgs& a, int sm_count, cudaStream_t s);
+bool tile_dim(int d);
+size_t tile_smem_bytes(int d, int bins);
+cudaError_t prepare_tile_kernel(int d, int bins);
+cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, cudaStream_t s);
 int sampler_grid(int n, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
@@ -97,6 +119,7 @@ void set_last_error(const char* msg);
 // Mills-ratio table (host side): builds the coefficients and uploads them to
 // the current device once.
 cudaError_t ensure_mills_table();
+const struct MillsCoef* mills_table_device();
 cudaError_t upload_mills_table(const void* host_coefs, size_t bytes);
 cudaError_t launch_fit_sigma(const float* hist, int32_t bins, float hist_max, float mu,
                              float* sigma_inout, cudaStream_t s);

@@ -13,6 +13,7 @@
 //  k_is_edge       membership probes (inspection)
 #include "device_math.cuh"
 #include "engine.cuh"
+#include "hist.cuh"
 
 namespace gempe {
 
@@ -50,8 +51,8 @@ __global__ void k_hash_build(const int32_t* __restrict__ row_ptr, const int32_t*
     }
 }
 
-__global__ void k_init(float* __restrict__ x, int32_t n, int32_t d, uint32_t key_lo, uint32_t key_hi,
-                       float range) {
+__global__ void k_init(float* __restrict__ x, __nv_bfloat16* __restrict__ xb, int32_t n, int32_t d,
+                       uint32_t key_lo, uint32_t key_hi, float range) {
     const int quads = (d + 3) / 4;
     const long long total = (long long)n * quads;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -65,6 +66,7 @@ __global__ void k_init(float* __restrict__ x, int32_t n, int32_t d, uint32_t key
                 // (r >> 8) * 2^-23 - 1 is exact in FP32; one rounding for the range
                 const float unit = (float)(word_of(r, w) >> 8) * 1.1920928955078125e-7f - 1.0f;
                 x[(size_t)i * d + c] = unit * range;
+                if (xb) xb[(size_t)i * d + c] = __float2bfloat16_rn(unit * range);
             }
         }
     }
@@ -89,6 +91,30 @@ __device__ __forceinline__ void load_chunk(const float* __restrict__ x, int row,
     } else {
 #pragma unroll
         for (int c = 0; c < P; ++c) out[c] = __ldg(p + c);
+    }
+}
+
+// The same chunk from BF16 positions, widened to FP32 (exact).
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+template <int D, int P>
+__device__ __forceinline__ void load_chunk(const __nv_bfloat16* __restrict__ x, int row, int gl, float* out) {
+    const __nv_bfloat16* p = x + (size_t)row * D + gl * P;
+    if constexpr (P % 8 == 0) {
+#pragma unroll
+        for (int c = 0; c < P; c += 8) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + c));
+            out[c] = bf16_lo(v.x); out[c + 1] = bf16_hi(v.x); out[c + 2] = bf16_lo(v.y); out[c + 3] = bf16_hi(v.y);
+            out[c + 4] = bf16_lo(v.z); out[c + 5] = bf16_hi(v.z); out[c + 6] = bf16_lo(v.w); out[c + 7] = bf16_hi(v.w);
+        }
+    } else if constexpr (P == 4) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        out[0] = bf16_lo(v.x); out[1] = bf16_hi(v.x); out[2] = bf16_lo(v.y); out[3] = bf16_hi(v.y);
+    } else {
+        const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
+#pragma unroll
+        for (int c = 0; c < P; ++c) out[c] = __uint_as_float((uint32_t)__ldg(q + c) << 16);
     }
 }
 
@@ -134,57 +160,6 @@ __device__ __forceinline__ int sample_partner(const EpochArgs& a, int i, int epo
     return -1;
 }
 
-// ---------------------------------------------------------------------------
-// Block-private distance histograms (Sec. III.F), all 32-bit integer bins so
-// that every update is a native shared-memory atomic:
-//   he[b]  edge count (each undirected edge once, j > i)
-//   hc[b]  sample count
-//   hd[b]  sum of the anchor degrees of those samples
-// A sample anchored at i weighs (n-1-deg_i)/(2 k_acc_i); while no sample of
-// i was dropped (k_acc_i = k) the non-edge bin is ((n-1) hc - hd) / (2k).
-// Samples of vertices with dropped slots add their weight's difference to
-// that value into hx (global float, rare).
-// ---------------------------------------------------------------------------
-struct BlockHist {
-    unsigned int* he;
-    unsigned int* hc;
-    unsigned int* hd;
-};
-
-__device__ __forceinline__ BlockHist block_hist(unsigned int* base, int bins) {
-    BlockHist h;
-    h.he = base;
-    h.hc = base + bins;
-    h.hd = base + 2 * bins;
-    return h;
-}
-
-__device__ __forceinline__ void hist_clear(const BlockHist& h, int bins) {
-    for (int t = threadIdx.x; t < bins; t += blockDim.x) {
-        h.he[t] = 0u;
-        h.hc[t] = 0u;
-        h.hd[t] = 0u;
-    }
-}
-
-__device__ __forceinline__ void hist_merge(const BlockHist& h, const EpochArgs& a) {
-    for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
-        const unsigned int e = h.he[t], c = h.hc[t], d = h.hd[t];
-        if (e) atomicAdd(a.hist_e + t, e);
-        if (c) atomicAdd(a.hist_c + t, c);
-        if (d) atomicAdd(a.hist_d + t, (unsigned long long)d);
-    }
-}
-
-__device__ __forceinline__ void hist_sample(const BlockHist& h, const EpochArgs& a, int bin, int deg, int k_acc) {
-    atomicAdd(h.hc + bin, 1u);
-    atomicAdd(h.hd + bin, (unsigned int)deg);
-    if (k_acc < a.k && k_acc > 0) {
-        const float base = (float)(a.n - 1 - deg);
-        atomicAdd(a.hist_x + bin, base / (2.0f * (float)k_acc) - base / (2.0f * (float)a.k));
-    }
-}
-
 // Warp sums of per-lane counters, added to shared counters (one atomic per warp).
 template <int N>
 __device__ __forceinline__ void count_merge(unsigned (&v)[N], unsigned long long* s_cnt) {
@@ -199,6 +174,10 @@ __device__ __forceinline__ void count_merge(unsigned (&v)[N], unsigned long long
             if (v[q]) atomicAdd(&s_cnt[q], (unsigned long long)v[q]);
     }
 }
+
+template <typename PT> __device__ __forceinline__ const PT* pos_of(const EpochArgs& a);
+template <> __device__ __forceinline__ const float* pos_of<float>(const EpochArgs& a) { return a.x; }
+template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16>(const EpochArgs& a) { return a.xb; }
 
 // ---------------------------------------------------------------------------
 // The sampler: one thread per (vertex, sample slot) of the epoch
@@ -375,7 +354,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
                 if (is_edge) {
                     if (j > v) atomicAdd(hist.he + bin, 1u);
                 } else {
-                    hist_sample(hist, a, bin, deg_l, kacc_l);
+                    hist_sample(hist, a, bin, deg_l, kacc_l, k);
                     if (a.symmetric) {
                         float pv[D];
 #pragma unroll
@@ -421,10 +400,11 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
 // Pair sweep for d >= 8: one warp per work unit (one vertex, or one chunk of
 // a hub's row), G lanes per pair, each lane owning D/G coordinates.
 // ---------------------------------------------------------------------------
-template <int D, int G>
+template <int D, int G, typename PT>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int P = D / G;
     constexpr int PAIRS = 32 / G;
+    const PT* X = pos_of<PT>(a);
     extern __shared__ unsigned int s_u32[];
     const BlockHist hist = block_hist(s_u32, a.bins);
     __shared__ unsigned long long s_used;
@@ -441,29 +421,43 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.n * a.k;
+    const bool block = a.block_P > 0;
+    const int32_t* part = block ? a.block_part + (size_t)(epoch & 1) * (size_t)a.n_tiles * kBlockP : nullptr;
+    unsigned long long* bmask = block ? a.block_mask + (size_t)(epoch & 1) * (size_t)a.n : nullptr;
+    const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex
     unsigned used[1] = {0u};
 
     for (int it = warp; it < a.n_items; it += n_warps) {
         const int4 item = __ldg(a.items + it);
         const int i = item.x;
-        const bool has_samples = (item.w & kUnitHasSamples) && a.k > 0;
+        const bool has_samples = (item.w & kUnitHasSamples) && k_eff > 0 && a.sweep_samples;
         const int p0 = item.z, p1 = item.w & ~kUnitHasSamples;
         const int e0 = __ldg(a.row_ptr + i);
         const int deg = __ldg(a.row_ptr + i + 1) - e0;
         float xi[P];
-        load_chunk<D, P>(a.x, i, gl, xi);
+        load_chunk<D, P>(X, i, gl, xi);
 
-        // Sampled non-edges of this vertex: lane t < k owns slot t.
-        int g_mine = -1;
+        // Sampled non-edges of this vertex: lane t owns slots t and t + 32.
+        int g0 = -1, g1 = -1;
         int k_acc = 0;
         if (has_samples) {
-            if (lane < a.k) g_mine = __ldg(samples + (size_t)i * a.k + lane);
-            k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
+            if (block) {
+                const unsigned long long m = bmask[i];
+                __syncwarp();
+                if (lane == 0) bmask[i] = 0ull;   // read once: the buffer starts empty two epochs on
+                const int32_t* tp = part + (size_t)(i / kBlockT) * kBlockP;
+                g0 = ((m >> lane) & 1ull) ? -1 : __ldg(tp + lane);
+                g1 = ((m >> (lane + 32)) & 1ull) ? -1 : __ldg(tp + lane + 32);
+                k_acc = kBlockP - __popcll(m);
+            } else {
+                if (lane < a.k) g0 = __ldg(samples + (size_t)i * a.k + lane);
+                k_acc = __popc(__ballot_sync(kFull, g0 >= 0));
+            }
             used[0] += (lane == 0) ? k_acc : 0;
         }
 
         const int ne = p1 - p0;
-        const int total = ne + (has_samples ? a.k : 0);
+        const int total = ne + (has_samples ? k_eff : 0);
         float dacc[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) dacc[c] = 0.0f;
@@ -473,13 +467,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
             const bool active = q < total;
             const bool is_edge = q < ne;
             const int sidx = q - ne;
-            const int gs = __shfl_sync(kFull, g_mine, (sidx >= 0 && sidx < 32) ? sidx : 0);
+            const int s0 = __shfl_sync(kFull, g0, sidx & 31);
+            const int s1 = __shfl_sync(kFull, g1, sidx & 31);
             int j = -1;
-            if (active) j = is_edge ? __ldg(a.col_idx + e0 + p0 + q) : gs;
+            if (active) j = is_edge ? __ldg(a.col_idx + e0 + p0 + q) : (sidx < 32 ? s0 : s1);
             const bool valid = active && j >= 0;
             float xj[P];
             if (valid) {
-                load_chunk<D, P>(a.x, j, gl, xj);
+                load_chunk<D, P>(X, j, gl, xj);
             } else {
 #pragma unroll
                 for (int c = 0; c < P; ++c) xj[c] = xi[c];
@@ -511,7 +506,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                     if (is_edge) {
                         if (j > i) atomicAdd(hist.he + bin, 1u);
                     } else {
-                        hist_sample(hist, a, bin, deg, k_acc);
+                        hist_sample(hist, a, bin, deg, k_acc, k_eff);
                     }
                 }
             }
@@ -688,6 +683,50 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
         if (threadIdx.x == 0) a.st->epoch = epoch + 1;
         return;
     }
+    if (a.d >= 8) {   // one warp per vertex, float4 over the dimensions (d <= 256: at most 2 per lane)
+        const int lane = threadIdx.x & 31;
+        const int wstride = ((gridDim.x - 1) * blockDim.x) >> 5;
+        const int nq = a.d >> 2, sq = a.acc_stride >> 2;
+        for (int v = (((blockIdx.x - 1) * blockDim.x) >> 5) + (threadIdx.x >> 5); v < a.n; v += wstride) {
+            float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
+            float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
+            const float z = a.acc[(size_t)v * a.acc_stride + a.d];
+            if (z >= a.z_min) {
+                const float inv_z = 1.0f / z;
+                float4 xn[2];
+                bool finite = true;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = lane + 32 * r;
+                    if (q < nq) {
+                        const float4 dv = row[q], xo = xv[q];
+                        xn[r] = make_float4(fmaf(dv.x, inv_z, xo.x), fmaf(dv.y, inv_z, xo.y),
+                                            fmaf(dv.z, inv_z, xo.z), fmaf(dv.w, inv_z, xo.w));
+                        finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
+                                 isfinite(xn[r].w);
+                    }
+                }
+                if (__all_sync(kFull, finite)) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int q = lane + 32 * r;
+                        if (q < nq) {
+                            xv[q] = xn[r];
+                            if (a.xb) {
+                                __nv_bfloat162* b = reinterpret_cast<__nv_bfloat162*>(a.xb + (size_t)v * a.d + 4 * q);
+                                b[0] = __floats2bfloat162_rn(xn[r].x, xn[r].y);
+                                b[1] = __floats2bfloat162_rn(xn[r].z, xn[r].w);
+                            }
+                        }
+                    }
+                } else if (lane == 0) {
+                    atomicCAS(&a.st->status, 0, -6 /* GEMPE_E_NUMERIC */);
+                }
+            }
+            for (int q = lane; q < sq; q += 32) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        return;
+    }
     const int stride = (gridDim.x - 1) * blockDim.x;
     for (int v = (blockIdx.x - 1) * blockDim.x + threadIdx.x; v < a.n; v += stride) {
         float* row = a.acc + (size_t)v * a.acc_stride;
@@ -701,7 +740,11 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
                 if (!isfinite(xn)) bad = true;
             }
             if (!bad) {
-                for (int c = 0; c < a.d; ++c) xv[c] = fmaf(row[c], inv_z, xv[c]);
+                for (int c = 0; c < a.d; ++c) {
+                    const float xn = fmaf(row[c], inv_z, xv[c]);
+                    xv[c] = xn;
+                    if (a.xb) a.xb[(size_t)v * a.d + c] = __float2bfloat16_rn(xn);
+                }
             } else {
                 atomicCAS(&a.st->status, 0, -6 /* GEMPE_E_NUMERIC */);
             }
@@ -792,6 +835,12 @@ __global__ void __launch_bounds__(256) k_loss(const EpochArgs a) {
     if (lane == 0 && sum != 0.0) atomicAdd(&a.st->loss_sum, sum);
 }
 
+__global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ xb, long long count) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        xb[t] = __float2bfloat16_rn(x[t]);
+}
+
 __global__ void k_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
                           const int32_t* pairs, int64_t count, uint8_t* out) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
@@ -810,7 +859,8 @@ cudaError_t sweep_for(const EpochArgs& a, int grid, cudaStream_t s) {
     if constexpr (D <= kPackedMaxDim) {
         k_sweep_packed<D><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
     } else {
-        k_sweep<D, G><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
+        if (a.xb) k_sweep<D, G, __nv_bfloat16><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
+        else k_sweep<D, G, float><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -844,7 +894,7 @@ int sweep_blocks_per_sm(int bins) {
         cudaFuncSetAttribute(k_sweep_packed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D>, kPackedThreads, smem);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G>, kSweepThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G, float>, kSweepThreads,
                                                           hist_smem_bytes(bins));
     }
     if (e != cudaSuccess) {
@@ -875,13 +925,13 @@ cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_positions(float* x, int32_t n, int32_t d, uint32_t key_lo, uint32_t key_hi,
-                                  float range, cudaStream_t s) {
+cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_t d, uint32_t key_lo,
+                                  uint32_t key_hi, float range, cudaStream_t s) {
     const long long total = (long long)n * ((d + 3) / 4);
     long long grid = (total + 255) / 256;
     if (grid > 65535) grid = 65535;
     if (grid < 1) grid = 1;
-    k_init<<<(int)grid, 256, 0, s>>>(x, n, d, key_lo, key_hi, range);
+    k_init<<<(int)grid, 256, 0, s>>>(x, xb, n, d, key_lo, key_hi, range);
     return cudaGetLastError();
 }
 
@@ -932,6 +982,14 @@ cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, cudaStream_t s) {
+    long long grid = (count + 255) / 256;
+    if (grid > 65535) grid = 65535;
+    if (grid < 1) grid = 1;
+    k_to_bf16<<<(int)grid, 256, 0, s>>>(x, xb, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s) {
     long long grid = (count + 255) / 256;
@@ -939,6 +997,15 @@ cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bu
     if (grid < 1) grid = 1;
     k_is_edge<<<(int)grid, 256, 0, s>>>(keys, bucket_mask, pairs, count, out);
     return cudaGetLastError();
+}
+
+const MillsCoef* mills_table_device() {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_mills) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (const MillsCoef*)p;
 }
 
 cudaError_t upload_mills_table(const void* host_coefs, size_t bytes) {

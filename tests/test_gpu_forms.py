@@ -1,0 +1,148 @@
+"""GPU parity of the block-sampling and BF16 (precision) forms against the oracle.
+
+Block sampling: partners and masks bit-exact; the FP32 form within 1e-4 per
+step like the per-vertex form.  BF16 form: positions feed the pair
+arithmetic in BF16 (8-bit mantissa, relative rounding 2^-9 per coordinate),
+FP32 sums, compared with the FP64 oracle on the FP32 master positions at
+1e-2 per step: y_i - z_i x_i and the step x_new_i - x_i = (y_i - z_i x_i)/z_i
+each within 1e-2 of their own size, floored at 3e-2 of the size of the
+vertex's pair terms (A_i, resp. A_i / z_i) where those terms cancel, and
+z_i within 1e-2.
+"""
+import numpy as np
+import pytest
+
+from conftest import gpu_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL32 = 1e-4
+TOL16 = 1e-2
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2011_03479_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def ba_20k():
+    from paper_2011_03479_gb300 import inputs
+    return inputs.barabasi_albert(20000, 8, seed=3101)
+
+
+def _err_rows(got, ref, abs_terms=None, floor_frac=1e-2):
+    got = np.asarray(got, np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, np.float64).reshape(len(ref), -1)
+    nr = np.linalg.norm(ref, axis=1)
+    scale = np.maximum(nr, 1e-6 * max(nr.mean(), 1e-300))
+    if abs_terms is not None:
+        scale = np.maximum(scale, floor_frac * np.asarray(abs_terms, np.float64))
+    return np.linalg.norm(got - ref, axis=1) / scale
+
+
+def _run(B, O, rp, ci, d, x, sigma, epoch, **kw):
+    p = B.gempe_default_params(**kw)
+    with B.gempe_create(rp, ci, d, p) as ctx:
+        B.gempe_set_positions(ctx, x)
+        B.gempe_set_state(ctx, sigma, epoch)
+        samples = B.gempe_sweep(ctx, record_samples=True)
+        delta, z = B.gempe_accumulators(ctx)
+        he, hn = B.gempe_histograms(ctx, p.hist_bins)
+        B.gempe_update(ctx)
+        xn = B.gempe_positions(ctx)
+        stats = B.gempe_stats(ctx)
+    ref = O.epoch(rp, ci, x.astype(np.float64), sigma, epoch, p.seed, p.neg_per_vertex,
+                  block_partners=p.block_partners, tile_vertices=128, hist_bins=p.hist_bins,
+                  hist_max=p.hist_max)
+    return dict(samples=samples, delta=delta, z=z, he=he, hn=hn, xn=xn, ref=ref, p=p, stats=stats, x0=x)
+
+
+def _expected_block_samples(rp, ci, parts):
+    n = len(rp) - 1
+    out = np.empty((n, parts.shape[1]), dtype=np.int32)
+    for i in range(n):
+        row = set(ci[rp[i]:rp[i + 1]].tolist())
+        tp = parts[i // 128]
+        out[i] = [(-1 if (g == i or g in row) else g) for g in tp.tolist()]
+    return out
+
+
+@pytest.mark.parametrize("precision,d", [(0, 16), (1, 16), (1, 64)])
+def test_block_samples_bit_exact(B, O, sbm_1000, precision, d):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = np.random.default_rng(d).normal(size=(1000, d)).astype(np.float32)
+    r = _run(B, O, rp, ci, d, x, 0.9, 11, block_partners=64, precision=precision)
+    exp = _expected_block_samples(rp, ci, r["ref"]["partners"])
+    np.testing.assert_array_equal(r["samples"], exp)
+    assert int((exp >= 0).sum()) == r["ref"]["accepted"]
+
+
+@pytest.mark.parametrize("d", [8, 16, 64])
+def test_block_fp32_parity(B, O, sbm_1000, d):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(d).normal(size=(1000, d)) * 0.9).astype(np.float32)
+    r = _run(B, O, rp, ci, d, x, 0.8, 2, block_partners=64)
+    ref = r["ref"]
+    assert _err_rows(r["delta"], ref["delta"], ref["abs_terms"]).max() <= TOL32
+    assert _err_rows(r["z"], ref["z"]).max() <= TOL32
+    assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
+    assert r["he"].sum() == len(ci) // 2
+    assert r["hn"].sum() == pytest.approx(ref["hist_n"].sum(), rel=1e-5)
+
+
+def _bf16_errors(r):
+    ref = r["ref"]
+    e_delta = _err_rows(r["delta"], ref["delta"], ref["abs_terms"], floor_frac=3e-2)
+    e_z = _err_rows(r["z"], ref["z"])
+    x0 = r["x0"].astype(np.float64)
+    step_gpu = r["xn"].astype(np.float64) - x0
+    step_ref = ref["x_new"] - x0
+    e_x = _err_rows(step_gpu, step_ref, ref["abs_terms"] / np.maximum(ref["z"], 1e-300), floor_frac=3e-2)
+    return e_delta, e_z, e_x
+
+
+@pytest.mark.parametrize("d", [16, 32, 64])
+def test_block_bf16_tiles_parity(B, O, sbm_1000, d):
+    """Tensor-core tiles (BF16 positions, FP32 accumulation) against the FP64 oracle."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(100 + d).normal(size=(1000, d)) * 0.9).astype(np.float32)
+    r = _run(B, O, rp, ci, d, x, 0.8, 4, block_partners=64, precision=1)
+    e_delta, e_z, e_x = _bf16_errors(r)
+    print(f"d={d} bf16 tiles: delta {e_delta.max():.2e} (q99 {np.quantile(e_delta, .99):.2e}) "
+          f"z {e_z.max():.2e} step {e_x.max():.2e}")
+    assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
+    assert r["stats"]["used"] == r["ref"]["accepted"]
+
+
+def test_bf16_per_vertex_sampling_parity(B, O, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = (np.random.default_rng(7).normal(size=(1000, 64)) * 0.9).astype(np.float32)
+    r = _run(B, O, rp, ci, 64, x, 0.8, 4, neg_per_vertex=10, precision=1)
+    np.testing.assert_array_equal(r["samples"], r["ref"]["samples"])
+    e_delta, e_z, e_x = _bf16_errors(r)
+    print(f"bf16 per-vertex: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
+    assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
+
+
+def test_ba_bf16_tiles_parity(B, O, ba_20k):
+    """Barabasi-Albert graph (n = 20,000, m = 8: 157 tiles, ragged last tile), d = 64."""
+    rp, ci = ba_20k
+    n = len(rp) - 1
+    x = (np.random.default_rng(5).normal(size=(n, 64)) * 0.7).astype(np.float32)
+    r = _run(B, O, rp, ci, 64, x, 0.7, 9, block_partners=64, precision=1)
+    exp = _expected_block_samples(rp, ci, r["ref"]["partners"])
+    np.testing.assert_array_equal(r["samples"], exp)
+    e_delta, e_z, e_x = _bf16_errors(r)
+    print(f"BA 20k bf16 tiles: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
+    assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
