@@ -462,51 +462,81 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 #pragma unroll
         for (int c = 0; c < P; ++c) dacc[c] = 0.0f;
         float zacc = 0.0f;
-        for (int base = 0; base < total; base += PAIRS) {
-            const int q = base + grp;
-            const bool active = q < total;
-            const bool is_edge = q < ne;
-            const int sidx = q - ne;
-            const int s0 = __shfl_sync(kFull, g0, sidx & 31);
-            const int s1 = __shfl_sync(kFull, g1, sidx & 31);
-            int j = -1;
-            if (active) j = is_edge ? __ldg(a.col_idx + e0 + p0 + q) : (sidx < 32 ? s0 : s1);
-            const bool valid = active && j >= 0;
-            float xj[P];
-            if (valid) {
-                load_chunk<D, P>(X, j, gl, xj);
-            } else {
+        // Macro-rounds of 32 pairs: (A) G sub-rounds of PAIRS pairs gather the
+        // squared distances, lane grp*G + s keeping sub-round s's pair; (B) each
+        // lane evaluates the pair term of its own pair (one math pass per 32
+        // pairs); (C) the terms go back to the groups for the vector sums.
+        for (int base = 0; base < total; base += 32) {
+            const int left = total - base;
+            const int nsub = min(G, (left + PAIRS - 1) / PAIRS);
+            float my_ss = 0.0f;
+            int my_j = -1, my_edge = 0;
+            for (int sr = 0; sr < nsub; ++sr) {
+                const int q = base + PAIRS * sr + grp;
+                const bool active = q < total;
+                const bool is_edge = q < ne;
+                const int sidx = q - ne;
+                const int s0 = __shfl_sync(kFull, g0, sidx & 31);
+                const int s1 = __shfl_sync(kFull, g1, sidx & 31);
+                int j = -1;
+                if (active) j = is_edge ? __ldg(a.col_idx + e0 + p0 + q) : (sidx < 32 ? s0 : s1);
+                const bool valid = active && j >= 0;
+                float xj[P];
+                if (valid) {
+                    load_chunk<D, P>(X, j, gl, xj);
+                } else {
 #pragma unroll
-                for (int c = 0; c < P; ++c) xj[c] = xi[c];
-            }
-            float diff[P];
-            float ss = 0.0f;
-#pragma unroll
-            for (int c = 0; c < P; ++c) {
-                diff[c] = xi[c] - xj[c];
-                ss = fmaf(diff[c], diff[c], ss);
-            }
-#pragma unroll
-            for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
-            if (valid) {
-                float delta, inv_delta;
-                dist_of(ss, delta, inv_delta);
-                const PairTerm t = pair_term(delta, inv_delta, is_edge, K);
-#pragma unroll
-                for (int c = 0; c < P; ++c) dacc[c] = fmaf(t.c, diff[c], dacc[c]);
-                if (gl == 0) zacc += t.w;
-                if (!is_edge && a.symmetric) {
-                    float pv[P];
-#pragma unroll
-                    for (int c = 0; c < P; ++c) pv[c] = -t.c * diff[c];
-                    acc_add<D, G, P>(a.acc + (size_t)j * a.acc_stride, gl, pv, t.w);
+                    for (int c = 0; c < P; ++c) xj[c] = xi[c];
                 }
-                if (gl == 0) {
-                    const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                    if (is_edge) {
-                        if (j > i) atomicAdd(hist.he + bin, 1u);
-                    } else {
-                        hist_sample(hist, a, bin, deg, k_acc, k_eff);
+                float ss = 0.0f;
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    const float df = xi[c] - xj[c];
+                    ss = fmaf(df, df, ss);
+                }
+#pragma unroll
+                for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+                if (gl == sr) {
+                    my_ss = ss;
+                    my_j = valid ? j : -1;
+                    my_edge = is_edge ? 1 : 0;
+                }
+            }
+            float my_c = 0.0f, my_w = 0.0f;
+            if (my_j >= 0) {
+                float delta, inv_delta;
+                dist_of(my_ss, delta, inv_delta);
+                const PairTerm t = pair_term(delta, inv_delta, my_edge != 0, K);
+                my_c = t.c;
+                my_w = t.w;
+                zacc += t.w;
+                const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
+                if (my_edge) {
+                    if (my_j > i) atomicAdd(hist.he + bin, 1u);
+                } else {
+                    hist_sample(hist, a, bin, deg, k_acc, k_eff);
+                }
+            }
+            for (int sr = 0; sr < nsub; ++sr) {
+                const int src = grp * G + sr;
+                const int j = __shfl_sync(kFull, my_j, src);
+                const float c = __shfl_sync(kFull, my_c, src);
+                const float wv = __shfl_sync(kFull, my_w, src);
+                const int e = __shfl_sync(kFull, my_edge, src);
+                if (j >= 0) {
+                    float xj[P];
+                    load_chunk<D, P>(X, j, gl, xj);
+                    float diff[P];
+#pragma unroll
+                    for (int cc = 0; cc < P; ++cc) {
+                        diff[cc] = xi[cc] - xj[cc];
+                        dacc[cc] = fmaf(c, diff[cc], dacc[cc]);
+                    }
+                    if (!e && a.symmetric) {
+                        float pv[P];
+#pragma unroll
+                        for (int cc = 0; cc < P; ++cc) pv[cc] = -c * diff[cc];
+                        acc_add<D, G, P>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
                     }
                 }
             }
@@ -683,21 +713,29 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
         if (threadIdx.x == 0) a.st->epoch = epoch + 1;
         return;
     }
-    if (a.d >= 8) {   // one warp per vertex, float4 over the dimensions (d <= 256: at most 2 per lane)
+    if (a.d >= 8) {
+        // L = min(32, d/4) lanes per vertex, float4 over the dimensions (at most 2 per lane)
         const int lane = threadIdx.x & 31;
-        const int wstride = ((gridDim.x - 1) * blockDim.x) >> 5;
         const int nq = a.d >> 2, sq = a.acc_stride >> 2;
-        for (int v = (((blockIdx.x - 1) * blockDim.x) >> 5) + (threadIdx.x >> 5); v < a.n; v += wstride) {
+        const int L = nq < 32 ? nq : 32;
+        const int vpw = 32 / L;                       // vertices per warp
+        const int sub = lane / L, ql = lane - sub * L;
+        const unsigned group = (L == 32) ? kFull : (((1u << L) - 1u) << (sub * L));
+        const int wstride = (((gridDim.x - 1) * blockDim.x) >> 5) * vpw;
+        for (int vb = ((((blockIdx.x - 1) * blockDim.x) >> 5) + (threadIdx.x >> 5)) * vpw; vb < a.n; vb += wstride) {
+            const int v = vb + sub;
+            const bool live = v < a.n;
             float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
             float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
-            const float z = a.acc[(size_t)v * a.acc_stride + a.d];
-            if (z >= a.z_min) {
+            const float z = live ? a.acc[(size_t)v * a.acc_stride + a.d] : 0.0f;
+            const bool upd = live && z >= a.z_min;
+            float4 xn[2];
+            bool finite = true;
+            if (upd) {
                 const float inv_z = 1.0f / z;
-                float4 xn[2];
-                bool finite = true;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const int q = lane + 32 * r;
+                    const int q = ql + L * r;
                     if (q < nq) {
                         const float4 dv = row[q], xo = xv[q];
                         xn[r] = make_float4(fmaf(dv.x, inv_z, xo.x), fmaf(dv.y, inv_z, xo.y),
@@ -706,10 +744,13 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
                                  isfinite(xn[r].w);
                     }
                 }
-                if (__all_sync(kFull, finite)) {
+            }
+            const bool all_finite = (__ballot_sync(kFull, !finite) & group) == 0u;
+            if (upd) {
+                if (all_finite) {
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
-                        const int q = lane + 32 * r;
+                        const int q = ql + L * r;
                         if (q < nq) {
                             xv[q] = xn[r];
                             if (a.xb) {
@@ -719,11 +760,12 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
                             }
                         }
                     }
-                } else if (lane == 0) {
+                } else if (ql == 0) {
                     atomicCAS(&a.st->status, 0, -6 /* GEMPE_E_NUMERIC */);
                 }
             }
-            for (int q = lane; q < sq; q += 32) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (live)
+                for (int q = ql; q < sq; q += L) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         return;
     }
@@ -849,10 +891,10 @@ __global__ void k_is_edge(const unsigned long long* keys, unsigned long long buc
 }
 
 // ---------------------------------------------------------------------------
-// Dispatch on the dimension: lanes per pair G grows with d so that each lane
-// gathers at most 8 coordinates (16-byte vector loads from d = 8 on).
+// Dispatch on the dimension: from d = 8 on, G = d/8 lanes share a pair and
+// each lane gathers 8 coordinates (one 16-byte BF16 or two FP32 vector loads).
 // ---------------------------------------------------------------------------
-#define GEMPE_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 2) X(16, 4) X(32, 8) X(64, 16) X(128, 32) X(256, 32)
+#define GEMPE_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 1) X(16, 2) X(32, 4) X(64, 8) X(128, 16) X(256, 32)
 
 template <int D, int G>
 cudaError_t sweep_for(const EpochArgs& a, int grid, cudaStream_t s) {
