@@ -44,7 +44,11 @@ FORMS = {
     "rmat-s16-ef16": {},
     "ba-n1m-m8": {"block_partners": 64, "precision": 1},          # BF16 + tensor-core tiles
     "ba-n1m-m8-fp32": {"block_partners": 64, "precision": 0},     # the plain FP32 run of the same seed
+    # batched form: 256 SBM graphs, d in {2, 16, 64}, one CUDA-graph launch per epoch
+    "sbm-batch-256": {"autotune": 1},
+    "sbm-batch-256-bf16": {"autotune": 1, "precision": 1},         # BF16 positions for the d >= 8 graphs
 }
+BATCH_WORKLOADS = {"sbm-batch-256", "sbm-batch-256-bf16"}
 L2_FLUSH_BYTES = 256 << 20
 EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
 UNIT_PAIRS = 128     # edge + sample slots per packed work unit of the d <= 4 sweep
@@ -76,21 +80,21 @@ def sampler_algorithmic_bytes(n, k, draws):
     return 32 * draws + 4 * n * k
 
 
-def work_units(row_ptr, k, d):
+def work_units(row_ptr, k, d, edge_chunk=EDGE_CHUNK, unit_pairs=UNIT_PAIRS):
     """Number of sweep work units (mirrors the library's unit building)."""
     import numpy as np
     deg = np.diff(row_ptr).astype(np.int64)
     if d > 4:
-        return int(np.maximum(1, (deg + EDGE_CHUNK - 1) // EDGE_CHUNK).sum())
+        return int(np.maximum(1, (deg + edge_chunk - 1) // edge_chunk).sum())
     units, i, n = 0, 0, len(deg)
     pairs = deg + k
     while i < n:
-        if pairs[i] > UNIT_PAIRS:
-            units += int((deg[i] - 1) // UNIT_PAIRS) + 1 if deg[i] > UNIT_PAIRS else 1
+        if pairs[i] > unit_pairs:
+            units += int((deg[i] - 1) // unit_pairs) + 1 if deg[i] > unit_pairs else 1
             i += 1
             continue
         v0, tot = i, 0
-        while i < n and i - v0 < 32 and pairs[i] <= UNIT_PAIRS and tot + pairs[i] <= UNIT_PAIRS:
+        while i < n and i - v0 < 32 and pairs[i] <= unit_pairs and tot + pairs[i] <= unit_pairs:
             tot += pairs[i]
             i += 1
         units += 1
@@ -352,6 +356,153 @@ def run_gempe(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """The batched form: every step is one epoch of all graphs of the batch
+    (gempe_batch_step(b, 1): one CUDA-graph launch whose per-dimension
+    branches run concurrently)."""
+    import numpy as np
+    import torch
+
+    from paper_2011_03479_gb300 import binding as B
+    from paper_2011_03479_gb300 import inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    workload = args.workload
+    w = inputs.sbm_batch_256()
+    graphs = w["graphs"]
+    k, epochs = w["k"], w["epochs"]
+    G = len(graphs)
+    form = FORMS[workload]
+    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED, **form)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    desc = [(g["row_ptr"], g["col_idx"], g["d"]) for g in graphs]
+    m_tot = sum(len(g["col_idx"]) // 2 for g in graphs)
+    n_tot = sum(len(g["row_ptr"]) - 1 for g in graphs)
+
+    t_create0 = time.perf_counter()
+    b = B.gempe_batch_create(desc, p, stream=stream)
+    create_s = time.perf_counter() - t_create0
+    shapes = {d: B.gempe_batch_shape(b, d) for d in sorted({g["d"] for g in graphs})}
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            B.gempe_batch_step(b, 1)
+        torch.cuda.synchronize()
+        used0 = sum(B.gempe_batch_stats(b, q)["used"] for q in range(G))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        wall0 = time.perf_counter()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            B.gempe_batch_step(b, 1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        clk = clocks.stop()
+        stats = [B.gempe_batch_stats(b, q) for q in range(G)]
+    used = sum(s["used"] for s in stats) - used0
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    pairs = args.steps * m_tot + used
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        pp = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        t_all, pairs_all = tt.item(), pp.item()
+    else:
+        t_all, pairs_all = t_total, float(pairs)
+    value = pairs_all / t_all
+    b.close()
+
+    # end to end: one batch job (create from pinned host CSR, `epochs` epochs, positions back)
+    pinned = [(torch.from_numpy(g["row_ptr"]).pin_memory().numpy(), torch.from_numpy(g["col_idx"]).pin_memory().numpy(),
+               g["d"]) for g in graphs]
+    e2e = None
+    if args.e2e_jobs > 0:
+        h2d = sum(a.nbytes + c.nbytes for a, c, _ in pinned)
+        d2h = sum(4 * (len(a) - 1) * d for a, _, d in pinned)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jb = B.gempe_batch_create(pinned, p, stream=stream)
+        B.gempe_batch_step(jb, epochs)
+        for q in range(G):
+            B.gempe_batch_positions(jb, q)
+        e2e_pairs = epochs * m_tot + sum(B.gempe_batch_stats(jb, q)["used"] for q in range(G))
+        jb.close()
+        e2e_t = time.perf_counter() - t0
+        e2e = {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "step": f"one batch job: gempe_batch_create of {G} graphs from pinned host CSR (host validation "
+                       f"included), gempe_batch_step({epochs}), gempe_batch_positions of every graph",
+               "ms_per_job": 1e3 * e2e_t}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    # algorithmic bytes of one epoch's sweeps, all packs (they run concurrently)
+    acc_per_epoch = used / args.steps
+    byts = 0.0
+    for g in graphs:
+        rp, ci, d = g["row_ptr"], g["col_idx"], g["d"]
+        n = len(rp) - 1
+        sh = shapes[d]
+        units = work_units(rp, k, d, edge_chunk=sh["unit"], unit_pairs=sh["unit"])
+        byts += sweep_algorithmic_bytes(n, len(ci), d, k, units, acc_per_epoch * (n / n_tot))
+    step_s = statistics.mean(step_ms) / 1e3
+    achieved = byts / step_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 positions (d >= 8), f32 sums" if form.get("precision") else "f32", "data": "synthetic",
+        "config": {"workload": workload, "graphs": G, "n_total": n_tot, "m_total": m_tot,
+                   "dims": {str(d): sum(1 for g in graphs if g["d"] == d) for d in shapes}, "k": k,
+                   "step": "one epoch of every graph: gempe_batch_step(b, 1), one CUDA-graph launch",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "pairs_per_epoch": pairs / args.steps,
+        "shapes": {str(d): sh for d, sh in shapes.items()},
+        "create_s": create_s,
+        "roofline": {"bound": "hbm", "kernel": "epoch (sweeps of all packs, concurrent)", "achieved": achieved,
+                     "peak": peak, "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": byts, "traffic": None,
+                     "note": "sweep algorithmic bytes of all packs over the whole epoch time"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (3 * len(shapes)),
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        budget, t_used, pairs_cpu, done = args.cpu_budget, 0.0, 0, []
+        for q, g in enumerate(graphs):
+            if t_used > budget:
+                break
+            wq = dict(name=f"graph {q}", row_ptr=g["row_ptr"], col_idx=g["col_idx"], d=g["d"], k=k)
+            pq, tq, _ = oracle_epochs(wq, 1)
+            pairs_cpu += pq
+            t_used += tq
+            done.append(q)
+        line["cpu_baseline"] = {"value": pairs_cpu / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 oracle epoch of each of graphs {done[0]}..{done[-1]} "
+                                          f"({len(done)} of {G}), one thread"}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,6 +550,8 @@ def main():
         if args.steps > 50:
             args.steps = 50      # each oracle epoch takes a fraction of a second: keep the run bounded
         run_reference(args)
+    elif args.workload in BATCH_WORKLOADS:
+        run_batch(args)
     else:
         run_gempe(args)
 

@@ -72,6 +72,9 @@ typedef struct gempe_params {
                                pairs with the vertex itself or a neighbour are masked; d >= 8.  With
                                precision 1 and d in {16, 32, 64} the tiles run on tensor cores */
     int32_t tile_vertices;  /* 128 (the only tile size) */
+    int32_t autotune;       /* 1: time the sweep's launch shapes (units, lanes per pair, CTAs per
+                               SM) on the graph at create and keep the fastest; 0: fixed defaults.
+                               Only the launch shape changes, never the arithmetic of a pair */
     /* Optional device allocator (e.g. a framework's caching allocator).  When
      * dev_alloc is null the engine uses cudaMalloc / cudaFree. */
     void* (*dev_alloc)(size_t bytes, void* user);
@@ -97,7 +100,7 @@ typedef struct gempe_ctx gempe_ctx;
 /* Fill *p with the defaults: mu 1.5, sigma0 1, sigma_every 1, k 5, max_retries
  * 32, symmetric 1, derived w, clamp 1, z_min 1e-30, init_range 1, seed
  * 0x6E6D7065, 1024 bins on [0, 12), FP32, per-vertex sampling (tile size
- * 128 for block sampling), no custom allocator. */
+ * 128 for block sampling), no autotuning, no custom allocator. */
 void gempe_default_params(gempe_params* p);
 
 /* Create an embedding context from a host CSR graph (Sec. II.A: G, n, d).
@@ -198,6 +201,47 @@ gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float 
                                     void* cuda_stream, float* out_sigma);
 
 gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent graphs stepped together.
+ *
+ * The graphs of a batch are grouped by dimension; each group lives in one
+ * set of device arrays (a "pack") and every kernel of an epoch runs once per
+ * pack over the work units of all its graphs.  One gempe_batch_step epoch
+ * is one CUDA-graph launch whose branches (one per pack) run concurrently.
+ * Graph g of the batch uses the Philox key seed ^ g and keeps its own sigma,
+ * epoch counter and histograms, so it draws the same samples as a context
+ * created alone with that seed and reaches the same positions up to FP32
+ * summation order.  precision 1 applies to the graphs with d >= 8 (the
+ * others stay FP32), and so does block sampling.
+ * ------------------------------------------------------------------------ */
+typedef struct gempe_graph_desc {
+    const int32_t* row_ptr;  /* host int32[n+1] */
+    const int32_t* col_idx;  /* host int32[row_ptr[n]] */
+    int32_t n;
+    int32_t d;               /* one of the dimensions gempe_create accepts */
+} gempe_graph_desc;
+
+typedef struct gempe_batch gempe_batch;
+
+/* Validate, upload and initialise n_graphs graphs (copied; the caller keeps
+ * ownership of the arrays).  cuda_stream as in gempe_create.  With
+ * p->autotune each pack's sweep shape is tuned before the first epoch. */
+gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_desc* graphs, const gempe_params* p,
+                                void* cuda_stream, gempe_batch** out);
+void gempe_batch_destroy(gempe_batch* b);
+/* `iters` epochs of every graph, asynchronous on the batch stream. */
+gempe_status gempe_batch_step(gempe_batch* b, int32_t iters);
+/* Positions of graph `graph` to host float[n*d] (synchronises). */
+gempe_status gempe_batch_positions(gempe_batch* b, int32_t graph, float* host_out, size_t count);
+/* Sampled predictive entropy of graph `graph` (as gempe_loss). */
+gempe_status gempe_batch_loss(gempe_batch* b, int32_t graph, double* out_pe_bits, float* out_sigma);
+gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_stats_t* out);
+/* Launch shape of the pack holding dimension d: out[0] unit pair budget
+ * (d <= 4) or CSR slots per unit (d >= 8), out[1] lanes per pair, out[2]
+ * sweep CTAs per SM (0 = all that fit), out[3] sweep grid, out[4] graphs in
+ * the pack, out[5] tuned sweep time in ns (0 if not tuned). */
+gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out6);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* gempe_last_error(void);

@@ -45,6 +45,7 @@ class gempe_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("block_partners", ctypes.c_int32),
         ("tile_vertices", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
@@ -65,6 +66,15 @@ class gempe_stats_t(ctypes.Structure):
         ("d", ctypes.c_int32),
         ("k", ctypes.c_int32),
         ("sigma_iters", ctypes.c_int32),
+    ]
+
+
+class gempe_graph_desc(ctypes.Structure):
+    _fields_ = [
+        ("row_ptr", ctypes.c_void_p),
+        ("col_idx", ctypes.c_void_p),
+        ("n", ctypes.c_int32),
+        ("d", ctypes.c_int32),
     ]
 
 
@@ -115,6 +125,13 @@ def load(build: bool = True):
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
         "gempe_last_error": (ctypes.c_char_p, []),
+        "gempe_batch_create": (st, [i32, P(gempe_graph_desc), P(gempe_params), vp, P(vp)]),
+        "gempe_batch_destroy": (None, [vp]),
+        "gempe_batch_step": (st, [vp, i32]),
+        "gempe_batch_positions": (st, [vp, i32, vp, sz]),
+        "gempe_batch_loss": (st, [vp, i32, P(ctypes.c_double), P(ctypes.c_float)]),
+        "gempe_batch_stats": (st, [vp, i32, P(gempe_stats_t)]),
+        "gempe_batch_shape": (st, [vp, i32, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -310,6 +327,87 @@ def gempe_stats(ctx: _Ctx) -> dict:
     s = gempe_stats_t()
     _check(load().gempe_stats(ctx.handle, ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in gempe_stats_t._fields_}
+
+
+class _Batch:
+    """Owned batch handle (gempe_batch_destroy on close / GC)."""
+
+    def __init__(self, handle, ns, ds, keep=()):
+        self.handle = handle
+        self.ns, self.ds = list(ns), list(ds)
+        self._keep = keep   # host CSR arrays and params stay alive with the handle
+
+    def close(self):
+        if self.handle:
+            load().gempe_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def gempe_batch_create(graphs, params: gempe_params | None = None, stream=None) -> _Batch:
+    """graphs: sequence of (row_ptr, col_idx, d)."""
+    keep = []
+    descs = (gempe_graph_desc * len(graphs))()
+    ns, ds = [], []
+    for q, (rp, ci, d) in enumerate(graphs):
+        rp = np.ascontiguousarray(rp, dtype=np.int32)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        keep += [rp, ci]
+        descs[q].row_ptr = rp.ctypes.data
+        descs[q].col_idx = ci.ctypes.data if len(ci) else None
+        descs[q].n = len(rp) - 1
+        descs[q].d = int(d)
+        ns.append(len(rp) - 1)
+        ds.append(int(d))
+    p = params or gempe_default_params()
+    h = ctypes.c_void_p()
+    _check(load().gempe_batch_create(len(graphs), descs, ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
+    return _Batch(h, ns, ds, keep=(p,))
+
+
+def gempe_batch_destroy(b: _Batch) -> None:
+    b.close()
+
+
+def gempe_batch_step(b: _Batch, iters: int = 1) -> None:
+    _check(load().gempe_batch_step(b.handle, int(iters)))
+
+
+def gempe_batch_positions(b: _Batch, graph: int) -> np.ndarray:
+    out = np.empty((b.ns[graph], b.ds[graph]), dtype=np.float32)
+    _check(load().gempe_batch_positions(b.handle, int(graph), _ptr(out), out.size))
+    return out
+
+
+def gempe_batch_loss(b: _Batch, graph: int):
+    pe = ctypes.c_double()
+    s = ctypes.c_float()
+    _check(load().gempe_batch_loss(b.handle, int(graph), ctypes.byref(pe), ctypes.byref(s)))
+    return pe.value, s.value
+
+
+def gempe_batch_stats(b: _Batch, graph: int) -> dict:
+    s = gempe_stats_t()
+    _check(load().gempe_batch_stats(b.handle, int(graph), ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in gempe_stats_t._fields_}
+
+
+def gempe_batch_shape(b: _Batch, d: int) -> dict:
+    out = (ctypes.c_int64 * 6)()
+    _check(load().gempe_batch_shape(b.handle, int(d), out))
+    return {"unit": out[0], "lanes": out[1], "blocks_per_sm": out[2], "grid": out[3], "graphs": out[4],
+            "tuned_sweep_ns": out[5]}
 
 
 def gempe_last_error() -> str:

@@ -57,50 +57,49 @@ __device__ __forceinline__ unsigned long long partner_bits(const WarpHash& h, in
     return 0ull;
 }
 
-// One warp per work unit {tile, e_lo, e_hi, first}: the unit recomputes its
-// tile's 64 partners into a small shared hash (partner id -> positions), the
-// tile's first unit writes the partners and the self-pair bits, and every
-// unit tests CSR slots [e_lo, e_hi) of the tile's rows against the partners,
-// OR-ing hits into the vertices' masks (cleared before the launch).  Hub
-// tiles are thereby spread over many warps.
+// One warp per work unit {tile, e_lo, e_hi, graph << 1 | first}: the unit
+// recomputes its tile's 64 partners into a small shared hash (partner row ->
+// positions), the tile's first unit writes the partners and the self-pair
+// bits, and every unit tests absolute CSR slots [e_lo, e_hi) of the tile's
+// rows against the partners, OR-ing hits into the vertices' masks (cleared
+// before the launch).  Hub tiles are thereby spread over many warps.  The
+// Philox counter takes the tile's index within its graph and the graph's
+// key, so a graph draws the same partners alone or in a pack.
 __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const EpochArgs a, const int4* units,
                                                                       int n_units) {
     __shared__ WarpHash s_hash[kSamplerWarps];
     __shared__ int s_rp[kSamplerWarps][kBlockT + 1];
-    __shared__ unsigned long long s_rej;
-    __shared__ int s_epoch;
-    if (threadIdx.x == 0) {
-        s_rej = 0ull;
-        s_epoch = a.st->sample_epoch;
-    }
-    __syncthreads();
-    const int se = s_epoch;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     WarpHash& h = s_hash[wib];
-    int32_t* part_out = a.block_part + (size_t)(se & 1) * (size_t)a.n_tiles * kBlockP;
-    unsigned long long* mask_out = a.block_mask + (size_t)(se & 1) * (size_t)a.n;
-    unsigned c_rej = 0;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
 
     for (int it = warp; it < n_units; it += n_warps) {
         const int4 u = __ldg(units + it);
-        const int tile = u.x, e_lo = u.y, e_hi = u.z, first = u.w;
+        const int tile = u.x, e_lo = u.y, e_hi = u.z, first = u.w & 1, graph = u.w >> 1;
+        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
+        const int gt0 = __ldg(&a.graphs[graph].t0);
+        const uint32_t key_lo = __ldg(&a.graphs[graph].key_lo), key_hi = __ldg(&a.graphs[graph].key_hi);
+        const int se = a.gst[graph].sample_epoch;
+        const int lt = tile - gt0;                 // tile within the graph
+        const int v0 = gv0 + lt * kBlockT;         // pack row of the tile's first vertex
+        const int nv = min(kBlockT, gn - lt * kBlockT);
+        int32_t* part_out = a.block_part + (size_t)(se & 1) * (size_t)a.n_tiles * kBlockP;
+        unsigned long long* mask_out = a.block_mask + (size_t)(se & 1) * (size_t)a.rows;
+        unsigned c_rej = 0;
         for (int q = lane; q < kMiniHash; q += 32) {
             h.key[q] = -1;
             h.lo[q] = 0u;
             h.hi[q] = 0u;
         }
-        const int v0 = tile * kBlockT;
-        const int nv = min(kBlockT, a.n - v0);
         for (int v = lane; v <= nv; v += 32) s_rp[wib][v] = __ldg(a.row_ptr + v0 + v);
         __syncwarp();
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int p = lane + 32 * half;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)tile, (uint32_t)se, (uint32_t)(p >> 2), kTagBlock),
-                                          a.key_lo, a.key_hi);
-            const int g = draw_vertex(word_of(r, p & 3), (uint32_t)a.n);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)lt, (uint32_t)se, (uint32_t)(p >> 2), kTagBlock),
+                                          key_lo, key_hi);
+            const int g = gv0 + draw_vertex(word_of(r, p & 3), (uint32_t)gn);
             if (first) part_out[(size_t)tile * kBlockP + p] = g;
             unsigned s = hash_slot(g);
             for (int probe = 0; probe < kMiniHash; ++probe) {
@@ -133,27 +132,35 @@ __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const Epoc
                 c_rej += __popcll(b);
             }
         }
+        // every masked bit is set by exactly one event (a slot or the self
+        // pair): accepted = slots - masked, the slots added at completion
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c_rej += __shfl_xor_sync(kFull, c_rej, o);
+        if (lane == 0 && c_rej) {
+            atomicAdd(&a.gst[graph].rejected, (unsigned long long)c_rej);
+            atomicAdd(&a.gst[graph].accepted, (unsigned long long)(-(long long)c_rej));
+        }
         __syncwarp();
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) c_rej += __shfl_xor_sync(kFull, c_rej, o);
-    if (lane == 0 && c_rej) atomicAdd(&s_rej, (unsigned long long)c_rej);
+    __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        // every masked bit is set by exactly one event (a slot or the self pair);
-        // accepted = slots - masked: each block subtracts its masked bits
-        atomicAdd(&a.st->rejected, s_rej);
-        atomicAdd(&a.st->accepted, (unsigned long long)(-(long long)s_rej));
         __threadfence();
-        const unsigned prev = atomicAdd(&a.st->sample_done, 1u);
-        if (prev == gridDim.x - 1) {   // every block has read sample_epoch by now
-            const unsigned long long slots = (unsigned long long)a.n * kBlockP;
-            atomicAdd(&a.st->accepted, slots);
-            atomicAdd(&a.st->draws, slots);
-            a.st->sample_epoch = se + 1;
-            a.st->sample_done = 0u;
-            __threadfence();
+        const unsigned prev = atomicAdd(&a.ps->sample_done, 1u);
+        s_last = (prev == gridDim.x - 1) ? 1 : 0;   // every block has read the sample epochs by now
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int t = threadIdx.x; t < a.n_active; t += blockDim.x) {
+            const int graph = a.active[t];
+            GraphState* st = a.gst + graph;
+            const unsigned long long slots = (unsigned long long)__ldg(&a.graphs[graph].n) * kBlockP;
+            atomicAdd(&st->accepted, slots);
+            atomicAdd(&st->draws, slots);
+            st->sample_epoch = st->sample_epoch + 1;
         }
+        if (threadIdx.x == 0) a.ps->sample_done = 0u;
+        __threadfence();
     }
 }
 
@@ -224,27 +231,46 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<D>& sm = *reinterpret_cast<TileSmem<D>*>(smem_raw);
     unsigned int* hist_base = reinterpret_cast<unsigned int*>(smem_raw + sizeof(TileSmem<D>));
-    const BlockHist hist = block_hist(hist_base, a.bins);
-    __shared__ unsigned long long s_used;
+    // tile items: a contiguous range per block in packs of several graphs
+    int it0, it1, istep, home;
+    if (a.blocked) {
+        it0 = (int)((long long)a.n_tile_items * blockIdx.x / gridDim.x);
+        it1 = (int)((long long)a.n_tile_items * (blockIdx.x + 1) / gridDim.x);
+        istep = 1;
+        home = it0 < it1 ? __ldg(&a.tile_items[it0].y) : -1;
+    } else {
+        it0 = blockIdx.x;
+        it1 = a.n_tile_items;
+        istep = gridDim.x;
+        home = a.n_graphs == 1 ? 0 : -1;
+    }
+    const BlockHist hist = block_hist(hist_base, a.bins, home);
+    __shared__ unsigned int s_used, s_tile_used;
     for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
         hist.he[t] = 0u;
         hist.hc[t] = 0u;
         hist.hd[t] = 0u;
     }
-    if (threadIdx.x == 0) s_used = 0ull;
+    if (threadIdx.x == 0) {
+        s_used = 0u;
+        s_tile_used = 0u;
+    }
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t4 = lane & 3;
-    const float sigma = a.st->sigma;
-    const int epoch = a.st->epoch;
-    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
-    const int32_t* part = a.block_part + (size_t)(epoch & 1) * (size_t)a.n_tiles * kBlockP;
-    unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.n;
-    unsigned used = 0;
 
-    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const int v0 = tile * kBlockT;
-        const int nv = min(kBlockT, a.n - v0);
+    for (int it = it0; it < it1; it += istep) {
+        const int2 ti = __ldg(a.tile_items + it);
+        const int tile = ti.x, graph = ti.y;
+        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
+        const int lt = tile - __ldg(&a.graphs[graph].t0);
+        const int v0 = gv0 + lt * kBlockT;
+        const int nv = min(kBlockT, gn - lt * kBlockT);
+        const float sigma = a.gst[graph].sigma;
+        const int epoch = a.gst[graph].epoch;
+        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
+        const int32_t* part = a.block_part + (size_t)(epoch & 1) * (size_t)a.n_tiles * kBlockP;
+        unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
         __syncthreads();   // the previous tile's shared data is no longer read
         // ---- stage partners, masks, degrees, X_T and X_P ----
         if (threadIdx.x < kBlockP) sm.part[threadIdx.x] = __ldg(part + (size_t)tile * kBlockP + threadIdx.x);
@@ -255,6 +281,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                 sm.mask[v] = m;
                 sm.deg[v] = __ldg(a.row_ptr + v0 + v + 1) - __ldg(a.row_ptr + v0 + v);
                 sm.kacc[v] = kBlockP - __popcll(m);
+                atomicAdd(&s_tile_used, (unsigned)(kBlockP - __popcll(m)));
             } else {
                 sm.mask[v] = ~0ull;
                 sm.deg[v] = 0;
@@ -275,6 +302,13 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
         }
         cp_async_wait_all();
         __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_tile_used) {
+                if (graph == home) s_used += s_tile_used;
+                else atomicAdd(&a.gst[graph].used, (unsigned long long)s_tile_used);
+            }
+            s_tile_used = 0u;
+        }
         for (int r = threadIdx.x; r < kBlockT + kBlockP; r += blockDim.x) {
             const __nv_bfloat16* row = (r < kBlockT) ? sm.xt + r * XS : sm.xp + (r - kBlockT) * XS;
             float s = 0.0f;
@@ -333,8 +367,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                     c = pt.c;
                     wv = pt.w;
                     const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                    hist_sample(hist, a, bin, sm.deg[il], sm.kacc[il], kBlockP);
-                    ++used;
+                    hist_sample(hist, a, graph, bin, sm.deg[il], sm.kacc[il], kBlockP);
                 }
                 cv[e] = c;
                 rc[e >> 1] += c;
@@ -463,13 +496,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
             }
         }
     }
-    // block totals
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) used += __shfl_xor_sync(kFull, used, o);
-    if (lane == 0 && used) atomicAdd(&s_used, (unsigned long long)used);
     __syncthreads();
     hist_merge(hist, a);
-    if (threadIdx.x == 0 && s_used) atomicAdd(&a.st->used, s_used);
+    if (threadIdx.x == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
 }
 
 }  // namespace
@@ -499,8 +528,7 @@ cudaError_t prepare_tile_kernel(int d, int bins) {
 
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
                                  cudaStream_t s) {
-    // the masks of the epoch being drawn start empty; the buffer index is read
-    // on the device, so clear both halves' target through the kernel's own epoch
+    // the masks of the epoch being drawn start empty (their consumers clear them)
     int grid = (n_units + kSamplerWarps - 1) / kSamplerWarps;
     if (grid > sm_count * 8) grid = sm_count * 8;
     if (grid < 1) grid = 1;
@@ -508,10 +536,16 @@ cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_un
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_bf16(const EpochArgs& a, int sm_count, cudaStream_t s) {
+// blocks_per_sm: 0 = two CTAs per SM (what fits with the histogram bins)
+int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm) {
+    const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    int grid = n_tile_items < sm_count * per_sm ? n_tile_items : sm_count * per_sm;
+    return grid < 1 ? 1 : grid;
+}
+
+cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s) {
+    if (a.n_tile_items == 0) return cudaSuccess;
     const size_t smem = tile_smem_bytes(a.d, a.bins);
-    int grid = a.n_tiles < sm_count * 2 ? a.n_tiles : sm_count * 2;
-    if (grid < 1) grid = 1;
     switch (a.d) {
         case 16: k_tile_bf16<16><<<grid, kTileThreads, smem, s>>>(a); break;
         case 32: k_tile_bf16<32><<<grid, kTileThreads, smem, s>>>(a); break;

@@ -1,4 +1,16 @@
-// Internal interface between the C-ABI host code and the CUDA kernels.
+// Internal interface between the host code (C ABI, packs, batches) and the
+// CUDA kernels.
+//
+// A pack is the unit the kernels run on: one or more graphs of the same
+// dimension d, laid out back to back in one set of device arrays.  Graph g
+// owns rows [v0, v0 + n) of the vertex arrays (positions, accumulators,
+// samples, masks) plus one spare row v0 + n that closes its CSR range; its
+// CSR slots are absolute offsets into one column array whose entries are
+// pack row ids; its exact edge set is its own table (local vertex ids) at
+// key_off in one key array; its Philox key, slope sigma, epoch and
+// histograms are its own.  A single graph is a pack of one, and a graph
+// gives the same samples and (up to FP32 summation order) the same epoch
+// alone or in any pack.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -6,35 +18,64 @@
 
 namespace gempe {
 
-// Per-context scalars that change on the device (so a captured epoch graph
-// can be replayed without new kernel arguments).
-struct DevState {
+// Per-graph constants (read-only while an epoch runs).  48 bytes, 16-byte
+// aligned: the kernels read the first 40 bytes as one int4, one
+// ulonglong2 and one u64.
+struct alignas(16) GraphInfo {
+    int32_t v0;                       // first row of the graph in the pack
+    int32_t n;                        // vertices
+    int32_t t0;                       // first tile of the graph (block sampling)
+    int32_t n_tiles;                  // tiles of the graph
+    uint32_t key_lo, key_hi;          // Philox key
+    unsigned long long key_off;       // first slot of the graph's edge table
+    unsigned long long bucket_mask;   // buckets - 1 of that table
+    unsigned long long reserved;
+};
+static_assert(sizeof(GraphInfo) == 48, "GraphInfo layout");
+
+// Per-graph scalars that change on the device, so that a captured epoch can
+// be replayed without new kernel arguments.
+struct GraphState {
     float sigma;
     int32_t epoch;          // epoch of the next sweep
-    int32_t status;         // 0 or a gempe_status set by a kernel
     int32_t sample_epoch;   // epoch whose samples the sampler draws next
-    unsigned int sample_done;   // blocks of the running sampler that finished
-    int32_t sigma_iters;        // Newton / halving steps of the last slope fit
+    int32_t sigma_iters;    // Newton / halving steps of the last slope fit
     unsigned long long accepted, rejected, exhausted, draws;   // sampler statistics
     unsigned long long used;    // sampled non-edges consumed by sweeps
     double loss_sum;
 };
 
-// Chunk size (CSR slots) of the per-unit sweep used for d >= 8.
+// Pack-wide device scalars.
+struct PackState {
+    int32_t status;             // 0 or a gempe_status set by a kernel
+    unsigned int sample_done;   // blocks of the running sampler that finished
+};
+
+// Chunk size (CSR slots) of the per-unit sweep used for d >= 8 (default;
+// the autotuner may pick another).
 constexpr int kEdgeChunk = 64;
 constexpr int kMaxK = 32;
 constexpr int kSweepThreads = 1024;
 constexpr int kUpdateThreads = 1024;
 constexpr int kSigmaMaxIters = 60;
+constexpr int kVChunk = 1024;          // vertices per vertex chunk
+constexpr int kSamplerSub = 128;       // vertices per sampler block iteration
+constexpr int kGraphShift = 8;         // unit.y = graph << kGraphShift | vertex count
 
-// Work units: int4 {v0, nv, e_lo, e_hi | flags}.  e_lo < 0: nv whole vertices;
-// else one vertex's CSR slots [e_lo, e_hi).  kUnitHasSamples: the unit also
-// carries the sampled non-edges of its vertices.
+// Work units: int4 {v0, graph << 8 | nv, e_lo, e_hi | flags}.  e_lo < 0: nv
+// whole vertices (rows v0 ..); else one vertex's CSR slots [e_lo, e_hi)
+// relative to its row start.  kUnitHasSamples: the unit also carries the
+// sampled non-edges of its vertices.  Units never cross graphs.
 constexpr int kUnitHasSamples = 1 << 30;
-constexpr int kUnitPairs = 128;          // pair budget of a packed unit (d <= 4)
+constexpr int kUnitPairs = 128;          // pair budget of a packed unit (d <= 4, default)
 constexpr int kUnitSampleCap = 128;      // samples one packed unit may hold
 constexpr int kPackedMaxDim = 4;
 constexpr int kPackedThreads = 512;
+
+// Sampled-partner layout of block sampling.
+constexpr int kBlockP = 64;
+constexpr int kBlockT = 128;
+constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
 
 inline size_t hist_smem_bytes(int bins) { return (size_t)bins * 3 * sizeof(unsigned int); }
 
@@ -44,72 +85,77 @@ inline size_t packed_smem_bytes(int d, int bins) {
 }
 
 struct EpochArgs {
-    const int32_t* row_ptr;
-    const int32_t* col_idx;
+    // graphs
+    const GraphInfo* graphs;
+    GraphState* gst;
+    PackState* ps;
+    int32_t n_graphs;
+    const int32_t* active;    // graphs this epoch steps (slope fit, epoch and sampler advance)
+    int32_t n_active;
+    // CSR, edge sets, positions, accumulators
+    const int32_t* row_ptr;   // [rows + 1] absolute slot offsets
+    const int32_t* col_idx;   // pack row ids
     const unsigned long long* keys;
-    unsigned long long bucket_mask;
-    const float* x;
-    float* acc;           // [n][acc_stride]: d values of y - z x, then z
-    unsigned int* hist_e;         // [bins] edge counts
-    unsigned int* hist_c;         // [bins] sample counts
-    unsigned long long* hist_d;   // [bins] sums of the samples' anchor degrees
-    float* hist_x;                // [bins] weight corrections of vertices with dropped samples
-    DevState* st;
-    const int4* items;
-    int32_t n_items;
-    int32_t n, d, acc_stride, k, max_retries, symmetric, w_formula, clamp_neg_d, bins;
-    float mu, hist_scale;  // hist_scale = bins / hist_max
-    uint32_t key_lo, key_hi;
-    int32_t* samples;      // [2][n][k] accepted partners (-1 = dropped), buffer = epoch & 1
-    // precision form: BF16 shadow of x (null in the FP32 form)
-    __nv_bfloat16* xb;
-    // block sampling: tiles of block_T vertices share block_P partners
-    int32_t block_P, block_T, n_tiles;
-    int32_t* block_part;             // [2][n_tiles][block_P], buffer = epoch & 1
-    unsigned long long* block_mask;  // [2][n] bit p set: partner p of the vertex's tile is masked
-    int32_t sweep_samples;           // 0: the sweep leaves the sampled non-edges to the tile kernel
-    const struct MillsCoef* mills;   // Mills-ratio table on this device
-};
-
-// Sampled-partner layout of block sampling.
-constexpr int kBlockP = 64;
-constexpr int kBlockT = 128;
-
-struct UpdateArgs {
     float* x;
-    __nv_bfloat16* xb;     // BF16 shadow, or null
-    float* acc;
-    unsigned int* hist_e;
-    unsigned int* hist_c;
-    unsigned long long* hist_d;
-    float* hist_x;
-    DevState* st;
-    int32_t n, d, acc_stride, bins, sigma_every, k;
-    float z_min, mu, hist_max;
+    __nv_bfloat16* xb;        // BF16 shadow of x (precision form), else null
+    float* acc;               // [rows][acc_stride]: d values of y - z x, then z
+    // histograms, [n_graphs][bins] each
+    unsigned int* hist_e;         // edge counts
+    unsigned int* hist_c;         // sample counts
+    unsigned long long* hist_d;   // sums of the samples' anchor degrees
+    float* hist_x;                // weight corrections of vertices with dropped samples
+    // work lists
+    const int4* items;        // sweep units
+    int32_t n_items;
+    int32_t blocked;          // 1: block b takes a contiguous range of units (packs of several graphs)
+    const int4* vchunks;      // {row begin, count <= kVChunk, graph, 0}
+    int32_t n_vchunks;
+    int32_t rows, d, acc_stride, k, max_retries, symmetric, w_formula, clamp_neg_d, bins;
+    float mu, hist_scale;     // hist_scale = bins / hist_max
+    int32_t* samples;         // [2][rows][k] accepted partners (-1 = dropped), buffer = epoch & 1
+    // block sampling: tiles of kBlockT rows share kBlockP partners
+    int32_t block_P, n_tiles;
+    int32_t* block_part;             // [2][n_tiles][kBlockP] partner rows, buffer = epoch & 1
+    unsigned long long* block_mask;  // [2][rows] bit p set: partner p of the row's tile is masked
+    const int2* tile_items;          // {tile, graph} of the tile kernel
+    int32_t n_tile_items;
+    int32_t sweep_samples;           // 0: the sweep leaves the sampled non-edges to the tile kernel
+    // update
+    int32_t sigma_every;
+    float z_min, hist_max;
+    const struct MillsCoef* mills;   // Mills-ratio table on this device
 };
 
 int acc_stride_for(int d);
 bool supported_dim(int d);
 
-cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+// Per-graph set-up (rows and slots of one graph of the pack).
+cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
                               unsigned long long* keys, unsigned long long bucket_mask,
                               int32_t* fail_flag, cudaStream_t s);
 cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_t d, uint32_t key_lo,
                                   uint32_t key_hi, float range, cudaStream_t s);
-cudaError_t launch_sweep(const EpochArgs& a, int grid, cudaStream_t s);
-int sweep_grid(int d, int bins, int sm_count);
-cudaError_t launch_update(const UpdateArgs& a, int grid, cudaStream_t s);
+
+// Sweep launch shape (chosen per pack, autotuned).
+struct SweepShape {
+    int grid = 0;
+    int lanes = 0;      // d >= 8: lanes per pair (0: d / 8)
+};
+cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream_t s);
+int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm);
+bool sweep_lanes_supported(int d, int lanes);
+cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
                                  cudaStream_t s);
-constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
-cudaError_t launch_tile_bf16(const EpochArgs& a, int sm_count, cudaStream_t s);
+cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s);
+int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm);
 bool tile_dim(int d);
 size_t tile_smem_bytes(int d, int bins);
 cudaError_t prepare_tile_kernel(int d, int bins);
 cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, cudaStream_t s);
-int sampler_grid(int n, int k, int sm_count);
+int sampler_grid(int rows, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s);

@@ -1,4 +1,6 @@
-// CUDA kernels of the GEMPE epoch (sm_103a).
+// CUDA kernels of the GEMPE epoch (sm_103a).  Every kernel runs on a pack:
+// one or more graphs of one dimension in shared device arrays, each work
+// unit naming its graph (see engine.cuh).
 //
 //  k_hash_build    exact edge set (replaces the lossy byte map of Sec. III.C)
 //  k_init          initial positions, uniform random (Fig. 4)
@@ -7,7 +9,7 @@
 //  k_sweep_packed  one epoch's pair sweep for d <= 4: edge parabolas
 //  k_sweep         (Eq. 4/5) and sampled non-edges, Eq. 3 terms reduced per
 //                  vertex, distance histograms (Sec. III.F); k_sweep for d >= 8
-//  k_update        x_i := y_i / z_i (Fig. 4), sigma bisection (Sec. III.F)
+//  k_update        x_i := y_i / z_i (Fig. 4), slope fit per graph (Sec. III.F)
 //  k_loss          sampled predictive entropy (Eq. 2) with FP64 sums
 //  k_sample        the sampler alone (inspection)
 //  k_is_edge       membership probes (inspection)
@@ -26,20 +28,21 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 __device__ MillsCoef g_mills[kMillsIntervals];
 
 // ---------------------------------------------------------------------------
-// Graph set-up
+// Graph set-up (one graph of the pack per launch)
 // ---------------------------------------------------------------------------
-__global__ void k_hash_build(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                             int32_t n, int64_t nnz, unsigned long long* keys, unsigned long long bucket_mask,
-                             int32_t* fail_flag) {
+__global__ void k_hash_build(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t v0,
+                             int32_t n, unsigned long long* keys, unsigned long long bucket_mask, int32_t* fail_flag) {
+    const int32_t* rp = row_ptr + v0;
+    const int64_t e0 = __ldg(rp), e1 = __ldg(rp + n);
     const unsigned long long slot_mask = 4ull * bucket_mask + 3ull;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-        // row of CSR slot e: the last i with row_ptr[i] <= e
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
+        // local row of CSR slot e: the last i with rp[i] <= e
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(row_ptr + mid) <= e) lo = mid; else hi = mid - 1;
+            if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
         }
-        const unsigned long long key = edge_key(lo, __ldg(col_idx + e));
+        const unsigned long long key = edge_key(lo, __ldg(col_idx + e) - v0);
         unsigned long long slot = 4ull * (mix64(key) & bucket_mask);
         bool done = false;
         for (unsigned long long probe = 0; probe <= slot_mask; ++probe) {
@@ -144,34 +147,85 @@ __device__ __forceinline__ void acc_add(float* row, int gl, const float* v, floa
     }
 }
 
-// Draw the accepted partner of sample slot t of vertex i (Fig. 2: redraw while
-// the pair is an edge; also redraw g == i), or -1 after max_retries draws.
-__device__ __forceinline__ int sample_partner(const EpochArgs& a, int i, int epoch, int t, uint32_t tag,
-                                              unsigned& rejected) {
+// Draw the accepted partner (local id) of sample slot t of local vertex i of
+// a graph (Fig. 2: redraw while the pair is an edge; also redraw g == i), or
+// -1 after max_retries draws.
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+                                              int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
+    const unsigned long long* table = keys + gi.key_off;
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    for (int att = 0; att < a.max_retries; ++att) {
+    for (int att = 0; att < max_retries; ++att) {
         if ((att & 3) == 0)
             r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
-                              a.key_lo, a.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)a.n);
-        if (g != i && !hash_contains(a.keys, a.bucket_mask, edge_key(i, g))) return g;
+                              gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        if (g != i && !hash_contains(table, gi.bucket_mask, edge_key(i, g))) return g;
         ++rejected;
     }
     return -1;
 }
 
-// Warp sums of per-lane counters, added to shared counters (one atomic per warp).
-template <int N>
-__device__ __forceinline__ void count_merge(unsigned (&v)[N], unsigned long long* s_cnt) {
+__device__ __forceinline__ GraphInfo load_graph(const EpochArgs& a, int g) {
+    GraphInfo gi;
+    const int4 w0 = __ldg(reinterpret_cast<const int4*>(a.graphs + g));
+    const ulonglong2 w1 = __ldg(reinterpret_cast<const ulonglong2*>(a.graphs + g) + 1);
+    const unsigned long long w2 = __ldg(reinterpret_cast<const unsigned long long*>(a.graphs + g) + 4);
+    gi.v0 = w0.x;
+    gi.n = w0.y;
+    gi.t0 = w0.z;
+    gi.n_tiles = w0.w;
+    gi.key_lo = (uint32_t)w1.x;
+    gi.key_hi = (uint32_t)(w1.x >> 32);
+    gi.key_off = w1.y;
+    gi.bucket_mask = w2;
+    return gi;
+}
+
+// Sum of a per-thread counter triple over the block, added to a graph's
+// sampler statistics by thread 0 (all threads must call it).
+__device__ __forceinline__ void block_count3(unsigned (&v)[3], unsigned* s_cnt, GraphState* st) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
+    for (int q = 0; q < 3; ++q) {
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], o);
     }
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int q = 0; q < N; ++q)
-            if (v[q]) atomicAdd(&s_cnt[q], (unsigned long long)v[q]);
+        for (int q = 0; q < 3; ++q)
+            if (v[q]) atomicAdd(&s_cnt[q], v[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned acc = s_cnt[0], rej = s_cnt[1], exh = s_cnt[2];
+        if (acc) atomicAdd(&st->accepted, (unsigned long long)acc);
+        if (rej) atomicAdd(&st->rejected, (unsigned long long)rej);
+        if (exh) atomicAdd(&st->exhausted, (unsigned long long)exh);
+        if (acc + rej) atomicAdd(&st->draws, (unsigned long long)(acc + rej));
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = 0u;
+}
+
+// Sampler completion: the last block to finish advances every stepped
+// graph's sample_epoch (every block has read them by then).
+__device__ __forceinline__ void sampler_done(const EpochArgs& a) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.ps->sample_done, 1u);
+        s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int t = threadIdx.x; t < a.n_active; t += blockDim.x) {
+            GraphState* st = a.gst + a.active[t];
+            st->sample_epoch = st->sample_epoch + 1;
+        }
+        if (threadIdx.x == 0) a.ps->sample_done = 0u;
+        __threadfence();
     }
 }
 
@@ -180,55 +234,53 @@ template <> __device__ __forceinline__ const float* pos_of<float>(const EpochArg
 template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16>(const EpochArgs& a) { return a.xb; }
 
 // ---------------------------------------------------------------------------
-// The sampler: one thread per (vertex, sample slot) of the epoch
-// st->sample_epoch, written to samples[sample_epoch & 1].  It depends on the
-// graph and the epoch only, so it runs beside the previous epoch's sweep.
-// The last block to finish advances sample_epoch (no block waits for it).
+// The sampler: for each stepped graph, one thread per (vertex, sample slot)
+// of the graph's epoch sample_epoch, written to samples[sample_epoch & 1] as
+// pack rows.  It depends on the graph and the epoch only, so it runs beside
+// the previous epoch's sweep.  Blocks take 128-vertex pieces of the vertex
+// chunks (one graph each).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
-    __shared__ unsigned long long s_cnt[3];
-    __shared__ int s_epoch;
-    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) s_epoch = a.st->sample_epoch;
+    __shared__ unsigned s_cnt[3];
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
-    const int se = s_epoch;
-    const long long total = (long long)a.n * a.k;
-    int32_t* out = a.samples + (size_t)(se & 1) * (size_t)total;
+    constexpr int kSubs = kVChunk / kSamplerSub;
+    const int n_sub = a.n_vchunks * kSubs;
+    const int k = a.k;
     unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / a.k), t = (int)(idx - (long long)i * a.k);
-        const int g = sample_partner(a, i, se, t, kTagEpoch, c[1]);
-        out[idx] = g;
-        if (g >= 0) ++c[0]; else ++c[2];
-    }
-    count_merge<3>(c, s_cnt);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&a.st->accepted, s_cnt[0]);
-        atomicAdd(&a.st->rejected, s_cnt[1]);
-        atomicAdd(&a.st->exhausted, s_cnt[2]);
-        atomicAdd(&a.st->draws, s_cnt[0] + s_cnt[1]);
-        __threadfence();
-        const unsigned prev = atomicAdd(&a.st->sample_done, 1u);
-        if (prev == gridDim.x - 1) {   // every block has read sample_epoch by now
-            a.st->sample_epoch = se + 1;
-            a.st->sample_done = 0u;
-            __threadfence();
+    for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + s / kSubs);
+        const int sub = s % kSubs;
+        const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
+        if (cnt <= 0) continue;   // uniform over the block
+        const int graph = ch.z;
+        const GraphInfo gi = load_graph(a, graph);
+        const int se = a.gst[graph].sample_epoch;
+        const int row0 = ch.x + sub * kSamplerSub;
+        const int local0 = row0 - gi.v0;
+        int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0) * k;
+        const int total = cnt * k;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int i = idx / k, t = idx - i * k;
+            const int g = sample_partner(gi, a.keys, a.max_retries, local0 + i, se, t, kTagEpoch, c[1]);
+            out[idx] = g >= 0 ? gi.v0 + g : -1;
+            if (g >= 0) ++c[0]; else ++c[2];
         }
+        block_count3(c, s_cnt, a.gst + graph);
     }
+    sampler_done(a);
 }
 
 // ---------------------------------------------------------------------------
 // Packed pair sweep for d <= 4 (one lane per pair).
 //
-// A work unit is either up to 32 consecutive vertices whose edge slots plus
-// sample slots number at most kUnitPairs, or one chunk of a hub's CSR row
-// (the hub's samples ride in its last chunk).  The warp lays the unit's
-// pairs out vertex by vertex, 32 per round; a lane finds its vertex by a
-// shuffle binary search over the per-vertex offsets.  Per-vertex sums are
-// formed by a segmented warp scan and kept in a per-warp shared row until
-// the unit ends, then added to the global accumulator with one vector
+// A work unit is either up to 32 consecutive vertices of one graph whose edge
+// slots plus sample slots number at most the unit pair budget, or one chunk
+// of a hub's CSR row (the hub's samples ride in its last chunk).  The warp
+// lays the unit's pairs out vertex by vertex, 32 per round; a lane finds its
+// vertex by a shuffle binary search over the per-vertex offsets.  Per-vertex
+// sums are formed by a segmented warp scan and kept in a per-warp shared row
+// until the unit ends, then added to the global accumulator with one vector
 // atomic per vertex.  Sampled partners receive their term by vector atomics.
 // ---------------------------------------------------------------------------
 template <int D>
@@ -241,34 +293,32 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
     constexpr int AS = PackedAcc<D>::kStride;
     constexpr int kWarps = kPackedThreads / 32;
     extern __shared__ unsigned int s_u32[];
-    const BlockHist hist = block_hist(s_u32, a.bins);
+    const BlockHist hist = block_hist(s_u32, a.bins, home_graph(a));
     int* s_g_all = reinterpret_cast<int*>(s_u32 + 3 * a.bins);            // [warps][kUnitSampleCap]
     float* s_acc_all = reinterpret_cast<float*>(s_g_all + kWarps * kUnitSampleCap);   // [warps][32][AS]
-    __shared__ unsigned long long s_used;
+    __shared__ unsigned int s_used;
     hist_clear(hist, a.bins);
-    if (threadIdx.x == 0) s_used = 0ull;
+    if (threadIdx.x == 0) s_used = 0u;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int* s_g = s_g_all + wib * kUnitSampleCap;
     float* s_acc = s_acc_all + wib * 32 * AS;
-    const float sigma = a.st->sigma;
-    const int epoch = a.st->epoch;
-    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int k = a.k;
-    const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.n * k;
-    unsigned used[1] = {0u};
+    const UnitRange ur = warp_units(a);
 
-    for (int it = warp; it < a.n_items; it += n_warps) {
+    for (int it = ur.begin; it < ur.end; it += ur.step) {
         const int4 unit = __ldg(a.items + it);
-        const int v0 = unit.x, nv = unit.y;
+        const int v0 = unit.x, nv = unit.y & ((1 << kGraphShift) - 1), graph = unit.y >> kGraphShift;
         const bool whole_rows = unit.z < 0;
         const bool has_s = (unit.w & kUnitHasSamples) && k > 0;
         const int e_lo = whole_rows ? 0 : unit.z;
         const int e_hi = unit.w & ~kUnitHasSamples;
+        const float sigma = a.gst[graph].sigma;
+        const int epoch = a.gst[graph].epoch;
+        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
+        const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.rows * k;
 
         // per-vertex layout: lane l < nv describes vertex v0 + l
         int rs = 0, deg = 0, ne = 0;
@@ -297,14 +347,17 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         if (has_s) {
             const int ns = nv * k;
             const int32_t* src = samples + (size_t)v0 * k;
-            for (int s = lane; s < ns; s += 32) {
-                const int g = __ldg(src + s);
-                s_g[s] = g;
-                used[0] += (g >= 0);
-            }
+            for (int s = lane; s < ns; s += 32) s_g[s] = __ldg(src + s);
             __syncwarp();
             if (lane < nv)
                 for (int t = 0; t < k; ++t) k_acc += (s_g[lane * k + t] >= 0);
+            int unit_used = k_acc;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) unit_used += __shfl_xor_sync(kFull, unit_used, o);
+            if (lane == 0 && unit_used) {
+                if (graph == hist.home) atomicAdd(&s_used, (unsigned)unit_used);
+                else atomicAdd(&a.gst[graph].used, (unsigned long long)unit_used);
+            }
         }
         __syncwarp();
 
@@ -352,9 +405,9 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
                 val[D] = t.w;
                 const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
                 if (is_edge) {
-                    if (j > v) atomicAdd(hist.he + bin, 1u);
+                    if (j > v) hist_edge(hist, a, graph, bin);
                 } else {
-                    hist_sample(hist, a, bin, deg_l, kacc_l, k);
+                    hist_sample(hist, a, graph, bin, deg_l, kacc_l, k);
                     if (a.symmetric) {
                         float pv[D];
 #pragma unroll
@@ -390,10 +443,9 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         }
         __syncwarp();
     }
-    count_merge<1>(used, &s_used);
     __syncthreads();
     hist_merge(hist, a);
-    if (threadIdx.x == 0 && s_used) atomicAdd(&a.st->used, s_used);
+    if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,32 +458,28 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int PAIRS = 32 / G;
     const PT* X = pos_of<PT>(a);
     extern __shared__ unsigned int s_u32[];
-    const BlockHist hist = block_hist(s_u32, a.bins);
-    __shared__ unsigned long long s_used;
+    const BlockHist hist = block_hist(s_u32, a.bins, home_graph(a));
+    __shared__ unsigned int s_used;
     hist_clear(hist, a.bins);
-    if (threadIdx.x == 0) s_used = 0ull;
+    if (threadIdx.x == 0) s_used = 0u;
     __syncthreads();
 
-    const float sigma = a.st->sigma;
-    const int epoch = a.st->epoch;
-    const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
     const int lane = threadIdx.x & 31;
     const int grp = lane / G;
     const int gl = lane % G;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.n * a.k;
     const bool block = a.block_P > 0;
-    const int32_t* part = block ? a.block_part + (size_t)(epoch & 1) * (size_t)a.n_tiles * kBlockP : nullptr;
-    unsigned long long* bmask = block ? a.block_mask + (size_t)(epoch & 1) * (size_t)a.n : nullptr;
     const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex
-    unsigned used[1] = {0u};
+    const UnitRange ur = warp_units(a);
 
-    for (int it = warp; it < a.n_items; it += n_warps) {
+    for (int it = ur.begin; it < ur.end; it += ur.step) {
         const int4 item = __ldg(a.items + it);
         const int i = item.x;
+        const int graph = item.y >> kGraphShift;
         const bool has_samples = (item.w & kUnitHasSamples) && k_eff > 0 && a.sweep_samples;
         const int p0 = item.z, p1 = item.w & ~kUnitHasSamples;
+        const float sigma = a.gst[graph].sigma;
+        const int epoch = a.gst[graph].epoch;
+        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
         const int e0 = __ldg(a.row_ptr + i);
         const int deg = __ldg(a.row_ptr + i + 1) - e0;
         float xi[P];
@@ -442,18 +490,25 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         int k_acc = 0;
         if (has_samples) {
             if (block) {
-                const unsigned long long m = bmask[i];
+                unsigned long long* bm = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows + i;
+                const unsigned long long m = *bm;
                 __syncwarp();
-                if (lane == 0) bmask[i] = 0ull;   // read once: the buffer starts empty two epochs on
-                const int32_t* tp = part + (size_t)(i / kBlockT) * kBlockP;
+                if (lane == 0) *bm = 0ull;   // read once: the buffer starts empty two epochs on
+                const int gv0 = __ldg(&a.graphs[graph].v0), gt0 = __ldg(&a.graphs[graph].t0);
+                const int tile = gt0 + (i - gv0) / kBlockT;
+                const int32_t* tp = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
                 g0 = ((m >> lane) & 1ull) ? -1 : __ldg(tp + lane);
                 g1 = ((m >> (lane + 32)) & 1ull) ? -1 : __ldg(tp + lane + 32);
                 k_acc = kBlockP - __popcll(m);
             } else {
-                if (lane < a.k) g0 = __ldg(samples + (size_t)i * a.k + lane);
+                const int32_t* samples = a.samples + ((size_t)(epoch & 1) * (size_t)a.rows + i) * a.k;
+                if (lane < a.k) g0 = __ldg(samples + lane);
                 k_acc = __popc(__ballot_sync(kFull, g0 >= 0));
             }
-            used[0] += (lane == 0) ? k_acc : 0;
+            if (lane == 0 && k_acc) {
+                if (graph == hist.home) atomicAdd(&s_used, (unsigned)k_acc);
+                else atomicAdd(&a.gst[graph].used, (unsigned long long)k_acc);
+            }
         }
 
         const int ne = p1 - p0;
@@ -512,9 +567,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 zacc += t.w;
                 const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
                 if (my_edge) {
-                    if (my_j > i) atomicAdd(hist.he + bin, 1u);
+                    if (my_j > i) hist_edge(hist, a, graph, bin);
                 } else {
-                    hist_sample(hist, a, bin, deg, k_acc, k_eff);
+                    hist_sample(hist, a, graph, bin, deg, k_acc, k_eff);
                 }
             }
             for (int sr = 0; sr < nsub; ++sr) {
@@ -550,10 +605,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         for (int o = 16; o >= 1; o >>= 1) zacc += __shfl_xor_sync(kFull, zacc, o);
         if (lane < G) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
-    count_merge<1>(used, &s_used);
     __syncthreads();
     hist_merge(hist, a);
-    if (threadIdx.x == 0 && s_used) atomicAdd(&a.st->used, s_used);
+    if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,9 +622,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 // [1e-3, 1e3]; no sign change -> the end with the lower entropy) and found
 // by Newton steps in t from the previous sigma, falling back to halving the
 // bracket whenever a step leaves it.  One whole block runs the search on a
-// shared-memory copy of the histograms: per-bin terms in FP32, the sum over
-// warps in FP64 by one warp, the Newton step in FP64 by one thread (FP64
-// throughput is a small fraction of FP32 on this GPU).
+// shared-memory copy of the histograms: per-bin terms in FP32, block sums
+// by warp shuffles, the Newton step by one thread.
 // ---------------------------------------------------------------------------
 struct SigmaSmem {
     float4 part[32];
@@ -680,39 +733,47 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
     return 1.0f / sm.inv_s;
 }
 
-// Load the histograms into shared memory as floats: edge counts, and the
-// non-edge weights ((n-1) hc - hd) / (2k) + hx.
-__device__ void load_hist_smem(const UpdateArgs& a, float* he, float* hn) {
-    const float inv2k = a.k > 0 ? 0.5f / (float)a.k : 0.0f;
+// Load one graph's histograms into shared memory as floats: edge counts, and
+// the non-edge weights ((n-1) hc - hd) / (2k) + hx.
+__device__ void load_hist_smem(const EpochArgs& a, size_t off, int n, int k_slots, float* he, float* hn) {
+    const float inv2k = k_slots > 0 ? 0.5f / (float)k_slots : 0.0f;
     for (int b = threadIdx.x; b < a.bins; b += blockDim.x) {
-        he[b] = (float)a.hist_e[b];
-        hn[b] = fmaf((float)(a.n - 1), (float)a.hist_c[b], -(float)a.hist_d[b]) * inv2k + a.hist_x[b];
+        he[b] = (float)a.hist_e[off + b];
+        hn[b] = fmaf((float)(n - 1), (float)a.hist_c[off + b], -(float)a.hist_d[off + b]) * inv2k + a.hist_x[off + b];
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
-    if (blockIdx.x == 0) {
+// Blocks [0, n_active): the slope fit, histogram reset and epoch advance of
+// one stepped graph each.  The other blocks: x_i := y_i / z_i over the vertex
+// chunks, accumulators cleared for the next epoch.
+__global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
+    if ((int)blockIdx.x < a.n_active) {
         __shared__ SigmaSmem sm;
         extern __shared__ float s_bins[];   // [2][bins]
-        const int epoch = a.st->epoch;
+        const int graph = a.active[blockIdx.x];
+        GraphState* st = a.gst + graph;
+        const size_t off = (size_t)graph * a.bins;
+        const int epoch = st->epoch;
         if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0) {
-            load_hist_smem(a, s_bins, s_bins + a.bins);
-            const float s = block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, a.st->sigma, sm);
+            const int k_slots = a.block_P > 0 ? kBlockP : a.k;
+            load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);
+            const float s = block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, st->sigma, sm);
             if (threadIdx.x == 0) {
-                a.st->sigma = s;
-                a.st->sigma_iters = sm.iters;
+                st->sigma = s;
+                st->sigma_iters = sm.iters;
             }
         }
         for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
-            a.hist_e[t] = 0u;
-            a.hist_c[t] = 0u;
-            a.hist_d[t] = 0ull;
-            a.hist_x[t] = 0.0f;
+            a.hist_e[off + t] = 0u;
+            a.hist_c[off + t] = 0u;
+            a.hist_d[off + t] = 0ull;
+            a.hist_x[off + t] = 0.0f;
         }
-        if (threadIdx.x == 0) a.st->epoch = epoch + 1;
+        if (threadIdx.x == 0) st->epoch = epoch + 1;
         return;
     }
+    const int vblk = blockIdx.x - a.n_active, n_vblk = gridDim.x - a.n_active;
     if (a.d >= 8) {
         // L = min(32, d/4) lanes per vertex, float4 over the dimensions (at most 2 per lane)
         const int lane = threadIdx.x & 31;
@@ -721,78 +782,85 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const UpdateArgs a) {
         const int vpw = 32 / L;                       // vertices per warp
         const int sub = lane / L, ql = lane - sub * L;
         const unsigned group = (L == 32) ? kFull : (((1u << L) - 1u) << (sub * L));
-        const int wstride = (((gridDim.x - 1) * blockDim.x) >> 5) * vpw;
-        for (int vb = ((((blockIdx.x - 1) * blockDim.x) >> 5) + (threadIdx.x >> 5)) * vpw; vb < a.n; vb += wstride) {
-            const int v = vb + sub;
-            const bool live = v < a.n;
-            float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
-            float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
-            const float z = live ? a.acc[(size_t)v * a.acc_stride + a.d] : 0.0f;
-            const bool upd = live && z >= a.z_min;
-            float4 xn[2];
-            bool finite = true;
-            if (upd) {
-                const float inv_z = 1.0f / z;
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int q = ql + L * r;
-                    if (q < nq) {
-                        const float4 dv = row[q], xo = xv[q];
-                        xn[r] = make_float4(fmaf(dv.x, inv_z, xo.x), fmaf(dv.y, inv_z, xo.y),
-                                            fmaf(dv.z, inv_z, xo.z), fmaf(dv.w, inv_z, xo.w));
-                        finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
-                                 isfinite(xn[r].w);
-                    }
-                }
-            }
-            const bool all_finite = (__ballot_sync(kFull, !finite) & group) == 0u;
-            if (upd) {
-                if (all_finite) {
+        const int per_pass = (blockDim.x >> 5) * vpw;
+        for (int c = vblk; c < a.n_vchunks; c += n_vblk) {
+            const int4 ch = __ldg(a.vchunks + c);
+            for (int vb = (threadIdx.x >> 5) * vpw; vb < ch.y; vb += per_pass) {
+                const bool live = vb + sub < ch.y;
+                const int v = ch.x + vb + sub;
+                float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
+                float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
+                const float z = live ? a.acc[(size_t)v * a.acc_stride + a.d] : 0.0f;
+                const bool upd = live && z >= a.z_min;
+                float4 xn[2];
+                bool finite = true;
+                if (upd) {
+                    const float inv_z = 1.0f / z;
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
                         const int q = ql + L * r;
                         if (q < nq) {
-                            xv[q] = xn[r];
-                            if (a.xb) {
-                                __nv_bfloat162* b = reinterpret_cast<__nv_bfloat162*>(a.xb + (size_t)v * a.d + 4 * q);
-                                b[0] = __floats2bfloat162_rn(xn[r].x, xn[r].y);
-                                b[1] = __floats2bfloat162_rn(xn[r].z, xn[r].w);
-                            }
+                            const float4 dv = row[q], xo = xv[q];
+                            xn[r] = make_float4(fmaf(dv.x, inv_z, xo.x), fmaf(dv.y, inv_z, xo.y),
+                                                fmaf(dv.z, inv_z, xo.z), fmaf(dv.w, inv_z, xo.w));
+                            finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
+                                     isfinite(xn[r].w);
                         }
                     }
-                } else if (ql == 0) {
-                    atomicCAS(&a.st->status, 0, -6 /* GEMPE_E_NUMERIC */);
                 }
+                const bool all_finite = (__ballot_sync(kFull, !finite) & group) == 0u;
+                if (upd) {
+                    if (all_finite) {
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int q = ql + L * r;
+                            if (q < nq) {
+                                xv[q] = xn[r];
+                                if (a.xb) {
+                                    __nv_bfloat162* b =
+                                        reinterpret_cast<__nv_bfloat162*>(a.xb + (size_t)v * a.d + 4 * q);
+                                    b[0] = __floats2bfloat162_rn(xn[r].x, xn[r].y);
+                                    b[1] = __floats2bfloat162_rn(xn[r].z, xn[r].w);
+                                }
+                            }
+                        }
+                    } else if (ql == 0) {
+                        atomicCAS(&a.ps->status, 0, -6 /* GEMPE_E_NUMERIC */);
+                    }
+                }
+                if (live)
+                    for (int q = ql; q < sq; q += L) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
-            if (live)
-                for (int q = ql; q < sq; q += L) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         return;
     }
-    const int stride = (gridDim.x - 1) * blockDim.x;
-    for (int v = (blockIdx.x - 1) * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-        float* row = a.acc + (size_t)v * a.acc_stride;
-        float* xv = a.x + (size_t)v * a.d;
-        const float z = row[a.d];
-        if (z >= a.z_min) {
-            const float inv_z = 1.0f / z;
-            bool bad = false;
-            for (int c = 0; c < a.d; ++c) {
-                const float xn = fmaf(row[c], inv_z, xv[c]);
-                if (!isfinite(xn)) bad = true;
-            }
-            if (!bad) {
-                for (int c = 0; c < a.d; ++c) {
-                    const float xn = fmaf(row[c], inv_z, xv[c]);
-                    xv[c] = xn;
-                    if (a.xb) a.xb[(size_t)v * a.d + c] = __float2bfloat16_rn(xn);
+    for (int c = vblk; c < a.n_vchunks; c += n_vblk) {
+        const int4 ch = __ldg(a.vchunks + c);
+        for (int vi = threadIdx.x; vi < ch.y; vi += blockDim.x) {
+            const int v = ch.x + vi;
+            float* row = a.acc + (size_t)v * a.acc_stride;
+            float* xv = a.x + (size_t)v * a.d;
+            const float z = row[a.d];
+            if (z >= a.z_min) {
+                const float inv_z = 1.0f / z;
+                bool bad = false;
+                for (int c2 = 0; c2 < a.d; ++c2) {
+                    const float xn = fmaf(row[c2], inv_z, xv[c2]);
+                    if (!isfinite(xn)) bad = true;
                 }
-            } else {
-                atomicCAS(&a.st->status, 0, -6 /* GEMPE_E_NUMERIC */);
+                if (!bad) {
+                    for (int c2 = 0; c2 < a.d; ++c2) {
+                        const float xn = fmaf(row[c2], inv_z, xv[c2]);
+                        xv[c2] = xn;
+                        if (a.xb) a.xb[(size_t)v * a.d + c2] = __float2bfloat16_rn(xn);
+                    }
+                } else {
+                    atomicCAS(&a.ps->status, 0, -6 /* GEMPE_E_NUMERIC */);
+                }
             }
+            for (int c2 = 0; c2 < a.acc_stride; c2 += 4)
+                *reinterpret_cast<float4*>(row + c2) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        for (int c = 0; c < a.acc_stride; c += 4)
-            *reinterpret_cast<float4*>(row + c) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
 }
 
@@ -809,72 +877,100 @@ __global__ void __launch_bounds__(kUpdateThreads) k_fit_sigma(const float* hist,
 // ---------------------------------------------------------------------------
 // Inspection kernels and the loss estimator
 // ---------------------------------------------------------------------------
+// Samples of the current epoch (tag kTagEpoch) or of the loss stream, as
+// pack rows, one warp per vertex.
 __global__ void k_sample(const EpochArgs a, uint32_t tag, int32_t* out) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int epoch = a.st->epoch;
-    for (int i = warp; i < a.n; i += n_warps) {
-        unsigned rej = 0;
-        if (lane < a.k) out[(size_t)i * a.k + lane] = sample_partner(a, i, epoch, lane, tag, rej);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < a.n_vchunks; c += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + c);
+        const GraphInfo gi = load_graph(a, ch.z);
+        const int epoch = a.gst[ch.z].epoch;
+        for (int vi = wib; vi < ch.y; vi += wpb) {
+            const int v = ch.x + vi;
+            unsigned rej = 0;
+            if (lane < a.k) {
+                const int g = sample_partner(gi, a.keys, a.max_retries, v - gi.v0, epoch, lane, tag, rej);
+                out[(size_t)v * a.k + lane] = g >= 0 ? gi.v0 + g : -1;
+            }
+        }
     }
 }
 
+// Sampled predictive entropy (Eq. 2) of each graph at its current sigma:
+// the graph's edges once each plus k fresh samples per vertex weighted by
+// (n-1-deg)/(2 k_acc); one block per vertex chunk, FP64 sums, one FP64
+// atomic per chunk into the graph's loss_sum.
 template <int D, int G>
 __global__ void __launch_bounds__(256) k_loss(const EpochArgs a) {
     constexpr int P = D / G;
     constexpr int PAIRS = 32 / G;
+    __shared__ double s_part[8];
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const float sigma = a.st->sigma;
-    const int epoch = a.st->epoch;
-    const float inv_sigma = 1.0f / sigma;
-    double sum = 0.0;
-    for (int i = warp; i < a.n; i += n_warps) {
-        const int e0 = __ldg(a.row_ptr + i);
-        const int deg = __ldg(a.row_ptr + i + 1) - e0;
-        float xi[P];
-        load_chunk<D, P>(a.x, i, gl, xi);
-        int g_mine = -1;
-        unsigned rej = 0;
-        if (lane < a.k) g_mine = sample_partner(a, i, epoch, lane, kTagLoss, rej);
-        const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
-        const double omega = k_acc ? (double)(a.n - 1 - deg) / (2.0 * k_acc) : 0.0;
-        const int total = deg + a.k;
-        for (int base = 0; base < total; base += PAIRS) {
-            const int q = base + grp;
-            const bool is_edge = q < deg;
-            const int sidx = q - deg;
-            const int gs = __shfl_sync(kFull, g_mine, (sidx >= 0 && sidx < 32) ? sidx : 0);
-            int j = -1;
-            if (q < total) j = is_edge ? __ldg(a.col_idx + e0 + q) : gs;
-            const bool valid = (q < total) && j >= 0 && (!is_edge || j > i);
-            float xj[P];
-            if (valid) {
-                load_chunk<D, P>(a.x, j, gl, xj);
-            } else {
-#pragma unroll
-                for (int c = 0; c < P; ++c) xj[c] = xi[c];
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < a.n_vchunks; c += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + c);
+        const int graph = ch.z;
+        const GraphInfo gi = load_graph(a, graph);
+        const float sigma = a.gst[graph].sigma;
+        const int epoch = a.gst[graph].epoch;
+        const float inv_sigma = 1.0f / sigma;
+        double sum = 0.0;
+        for (int vi = wib; vi < ch.y; vi += wpb) {
+            const int i = ch.x + vi;
+            const int e0 = __ldg(a.row_ptr + i);
+            const int deg = __ldg(a.row_ptr + i + 1) - e0;
+            float xi[P];
+            load_chunk<D, P>(a.x, i, gl, xi);
+            int g_mine = -1;
+            unsigned rej = 0;
+            if (lane < a.k) {
+                const int g = sample_partner(gi, a.keys, a.max_retries, i - gi.v0, epoch, lane, kTagLoss, rej);
+                g_mine = g >= 0 ? gi.v0 + g : -1;
             }
-            float ss = 0.0f;
+            const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
+            const double omega = k_acc ? (double)(gi.n - 1 - deg) / (2.0 * k_acc) : 0.0;
+            const int total = deg + a.k;
+            for (int base = 0; base < total; base += PAIRS) {
+                const int q = base + grp;
+                const bool is_edge = q < deg;
+                const int sidx = q - deg;
+                const int gs = __shfl_sync(kFull, g_mine, (sidx >= 0 && sidx < 32) ? sidx : 0);
+                int j = -1;
+                if (q < total) j = is_edge ? __ldg(a.col_idx + e0 + q) : gs;
+                const bool valid = (q < total) && j >= 0 && (!is_edge || j > i);
+                float xj[P];
+                if (valid) {
+                    load_chunk<D, P>(a.x, j, gl, xj);
+                } else {
 #pragma unroll
-            for (int c = 0; c < P; ++c) {
-                const float df = xi[c] - xj[c];
-                ss = fmaf(df, df, ss);
-            }
+                    for (int cc = 0; cc < P; ++cc) xj[cc] = xi[cc];
+                }
+                float ss = 0.0f;
 #pragma unroll
-            for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
-            if (valid && gl == 0) {
-                const float u = (sqrtf(ss) - a.mu) * inv_sigma;
-                const float dl = neg_log2_Q(is_edge ? u : -u);
-                sum += is_edge ? (double)dl : omega * (double)dl;
+                for (int cc = 0; cc < P; ++cc) {
+                    const float df = xi[cc] - xj[cc];
+                    ss = fmaf(df, df, ss);
+                }
+#pragma unroll
+                for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+                if (valid && gl == 0) {
+                    const float u = (sqrtf(ss) - a.mu) * inv_sigma;
+                    const float dl = neg_log2_Q(is_edge ? u : -u);
+                    sum += is_edge ? (double)dl : omega * (double)dl;
+                }
             }
         }
-    }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    if (lane == 0 && sum != 0.0) atomicAdd(&a.st->loss_sum, sum);
+        for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+        if (lane == 0) s_part[wib] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < wpb; ++w) t += s_part[w];
+            if (t != 0.0) atomicAdd(&a.gst[graph].loss_sum, t);
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ xb, long long count) {
@@ -891,19 +987,24 @@ __global__ void k_is_edge(const unsigned long long* keys, unsigned long long buc
 }
 
 // ---------------------------------------------------------------------------
-// Dispatch on the dimension: from d = 8 on, G = d/8 lanes share a pair and
-// each lane gathers 8 coordinates (one 16-byte BF16 or two FP32 vector loads).
+// Dispatch on the dimension.  d <= 4: the packed sweep.  d >= 8: G lanes per
+// pair, each lane gathering D/G coordinates; two lane counts per dimension
+// (8 or 4 coordinates per lane) for the autotuner, the first the default.
 // ---------------------------------------------------------------------------
-#define GEMPE_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 1) X(16, 2) X(32, 4) X(64, 8) X(128, 16) X(256, 32)
+#define GEMPE_PACKED_DIMS(X) X(1) X(2) X(3) X(4)
+#define GEMPE_WIDE(X) X(8, 1) X(8, 2) X(16, 2) X(16, 4) X(32, 4) X(32, 8) X(64, 8) X(64, 16) X(128, 16) X(128, 32) X(256, 32)
+#define GEMPE_LOSS_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 1) X(16, 2) X(32, 4) X(64, 8) X(128, 16) X(256, 32)
 
 template <int D, int G>
-cudaError_t sweep_for(const EpochArgs& a, int grid, cudaStream_t s) {
-    if constexpr (D <= kPackedMaxDim) {
-        k_sweep_packed<D><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
-    } else {
-        if (a.xb) k_sweep<D, G, __nv_bfloat16><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
-        else k_sweep<D, G, float><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
-    }
+cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
+    if (a.xb) k_sweep<D, G, __nv_bfloat16><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
+    else k_sweep<D, G, float><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t packed_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
+    k_sweep_packed<D><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -913,6 +1014,30 @@ cudaError_t loss_for(const EpochArgs& a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int D>
+int packed_blocks_per_sm(int bins) {
+    int blocks = 0;
+    const size_t smem = packed_smem_bytes(D, bins);
+    cudaFuncSetAttribute(k_sweep_packed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D>, kPackedThreads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    return blocks < 1 ? 1 : blocks;
+}
+
+template <int D, int G>
+int wide_blocks_per_sm(int bins) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G, float>, kSweepThreads,
+                                                      hist_smem_bytes(bins)) != cudaSuccess) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    return blocks < 1 ? 1 : blocks;
+}
+
 }  // namespace
 
 int acc_stride_for(int d) { return ((d + 1) + 3) / 4 * 4; }
@@ -920,50 +1045,52 @@ int acc_stride_for(int d) { return ((d + 1) + 3) / 4 * 4; }
 bool supported_dim(int d) {
     switch (d) {
 #define GEMPE_CASE(D, G) case D:
-        GEMPE_DIMS(GEMPE_CASE)
+        GEMPE_LOSS_DIMS(GEMPE_CASE)
 #undef GEMPE_CASE
         return true;
         default: return false;
     }
 }
 
-template <int D, int G>
-int sweep_blocks_per_sm(int bins) {
-    int blocks = 0;
-    cudaError_t e;
-    if constexpr (D <= kPackedMaxDim) {
-        const size_t smem = packed_smem_bytes(D, bins);
-        cudaFuncSetAttribute(k_sweep_packed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D>, kPackedThreads, smem);
-    } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep<D, G, float>, kSweepThreads,
-                                                          hist_smem_bytes(bins));
-    }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        blocks = 1;
-    }
-    return blocks < 1 ? 1 : blocks;
-}
-
-// One resident wave: SM count x blocks that fit per SM (the sweep strides
-// over its work units, so a second wave would only add histogram merges).
-int sweep_grid(int d, int bins, int sm_count) {
-    switch (d) {
-#define GEMPE_CASE(D, G) case D: return sm_count * sweep_blocks_per_sm<D, G>(bins);
-        GEMPE_DIMS(GEMPE_CASE)
+bool sweep_lanes_supported(int d, int lanes) {
+    if (d <= kPackedMaxDim) return lanes == 0 || lanes == 1;
+    if (lanes == 0) lanes = d / 8;
+#define GEMPE_CASE(D, G) \
+    if (d == D && lanes == G) return true;
+    GEMPE_WIDE(GEMPE_CASE)
 #undef GEMPE_CASE
-        default: return sm_count;
-    }
+    return false;
 }
 
-cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
-                              unsigned long long* keys, unsigned long long bucket_mask,
-                              int32_t* fail_flag, cudaStream_t s) {
+// One resident wave (SM count x blocks per SM, at most what fits): the
+// sweep strides over its work units, so a second wave would only add
+// histogram merges.
+int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm) {
+    int fit = 1;
+    if (lanes == 0) lanes = d <= kPackedMaxDim ? 1 : d / 8;
+    switch (d) {
+#define GEMPE_CASE(D) \
+    case D: fit = packed_blocks_per_sm<D>(bins); break;
+        GEMPE_PACKED_DIMS(GEMPE_CASE)
+#undef GEMPE_CASE
+        default:
+#define GEMPE_CASE(D, G) \
+    if (d == D && lanes == G) fit = wide_blocks_per_sm<D, G>(bins);
+            GEMPE_WIDE(GEMPE_CASE)
+#undef GEMPE_CASE
+            break;
+    }
+    const int b = (blocks_per_sm > 0 && blocks_per_sm < fit) ? blocks_per_sm : fit;
+    return sm_count * b;
+}
+
+cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
+                              unsigned long long* keys, unsigned long long bucket_mask, int32_t* fail_flag,
+                              cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     long long grid = (nnz + 255) / 256;
     if (grid > 65535) grid = 65535;
-    k_hash_build<<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, n, nnz, keys, bucket_mask, fail_flag);
+    k_hash_build<<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, v0, n, keys, bucket_mask, fail_flag);
     return cudaGetLastError();
 }
 
@@ -977,37 +1104,47 @@ cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream_t s) {
+    if (a.n_items == 0) return cudaSuccess;
+    const int lanes = shape.lanes ? shape.lanes : (a.d <= kPackedMaxDim ? 1 : a.d / 8);
     switch (a.d) {
-#define GEMPE_CASE(D, G) case D: return sweep_for<D, G>(a, grid, s);
-        GEMPE_DIMS(GEMPE_CASE)
+#define GEMPE_CASE(D) \
+    case D: return packed_sweep<D>(a, shape.grid, s);
+        GEMPE_PACKED_DIMS(GEMPE_CASE)
 #undef GEMPE_CASE
-        default: return cudaErrorInvalidValue;
+        default:
+#define GEMPE_CASE(D, G) \
+    if (a.d == D && lanes == G) return wide_sweep<D, G>(a, shape.grid, s);
+            GEMPE_WIDE(GEMPE_CASE)
+#undef GEMPE_CASE
+            return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s) {
-    int grid = (a.n + 7) / 8;
+    int grid = a.n_vchunks;
     if (grid > 4096) grid = 4096;
     if (grid < 1) grid = 1;
     switch (a.d) {
-#define GEMPE_CASE(D, G) case D: return loss_for<D, G>(a, grid, s);
-        GEMPE_DIMS(GEMPE_CASE)
+#define GEMPE_CASE(D, G) \
+    case D: return loss_for<D, G>(a, grid, s);
+        GEMPE_LOSS_DIMS(GEMPE_CASE)
 #undef GEMPE_CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_update(const UpdateArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {
     k_update<<<grid, kUpdateThreads, 2 * (size_t)a.bins * sizeof(float), s>>>(a);
     return cudaGetLastError();
 }
 
-int sampler_grid(int n, int k, int sm_count) {
-    const long long total = (long long)n * k;
-    long long grid = (total + 255) / 256;
+int sampler_grid(int rows, int k, int sm_count) {
+    const long long subs = ((long long)rows + kSamplerSub - 1) / kSamplerSub + 1;
+    long long grid = subs;
     const long long cap = (long long)sm_count * 8;
     if (grid > cap) grid = cap;
+    (void)k;
     return grid < 1 ? 1 : (int)grid;
 }
 
@@ -1017,7 +1154,7 @@ cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s) {
-    int grid = (a.n + 7) / 8;
+    int grid = a.n_vchunks;
     if (grid > 4096) grid = 4096;
     if (grid < 1) grid = 1;
     k_sample<<<grid, 256, 0, s>>>(a, tag, out);

@@ -1,0 +1,613 @@
+// Host side of a pack (see pack.cuh): layout, device copies, work lists,
+// epoch enqueueing and the sweep autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pack.cuh"
+
+namespace gempe {
+
+gempe_status pack_fail(gempe_status st, const std::string& msg) {
+    set_last_error(msg.c_str());
+    return st;
+}
+
+gempe_status pack_cuda_fail(cudaError_t e, const char* what) {
+    return pack_fail(e == cudaErrorMemoryAllocation ? GEMPE_E_OOM : GEMPE_E_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PK(call, what)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return pack_cuda_fail(e_, what); \
+    } while (0)
+
+gempe_status check_params(const gempe_params* p, int32_t d) {
+    if (!p) return pack_fail(GEMPE_E_INVALID_ARG, "params is null");
+    if (!supported_dim(d)) return pack_fail(GEMPE_E_INVALID_ARG, "d must be one of 1,2,3,4,8,16,32,64,128,256");
+    if (p->neg_per_vertex < 0 || p->neg_per_vertex > kMaxK)
+        return pack_fail(GEMPE_E_INVALID_ARG, "neg_per_vertex must be in [0, 32]");
+    if (p->max_retries < 1 || p->max_retries > 4096)
+        return pack_fail(GEMPE_E_INVALID_ARG, "max_retries must be in [1, 4096]");
+    if (p->hist_bins < 16 || p->hist_bins > 4096)
+        return pack_fail(GEMPE_E_INVALID_ARG, "hist_bins must be in [16, 4096]");
+    if (!(p->hist_max > 0.0f) || !(p->sigma0 > 0.0f) || !std::isfinite(p->mu) || !(p->init_range > 0.0f) ||
+        !(p->z_min > 0.0f))
+        return pack_fail(GEMPE_E_INVALID_ARG,
+                         "hist_max, sigma0, init_range and z_min must be positive, mu finite");
+    if (p->sigma_every < 0) return pack_fail(GEMPE_E_INVALID_ARG, "sigma_every must be >= 0");
+    if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
+        return pack_fail(GEMPE_E_INVALID_ARG, "dev_alloc and dev_free must be given together");
+    if (p->precision != 0 && p->precision != 1) return pack_fail(GEMPE_E_INVALID_ARG, "precision must be 0 or 1");
+    if (p->precision == 1 && d < 8) return pack_fail(GEMPE_E_INVALID_ARG, "the BF16 form needs d >= 8");
+    if (p->block_partners != 0 && p->block_partners != kBlockP)
+        return pack_fail(GEMPE_E_INVALID_ARG, "block_partners must be 0 or 64");
+    if (p->block_partners && (d < 8 || (p->tile_vertices != 0 && p->tile_vertices != kBlockT)))
+        return pack_fail(GEMPE_E_INVALID_ARG, "block sampling needs d >= 8 and tile_vertices 128");
+    if (p->autotune != 0 && p->autotune != 1) return pack_fail(GEMPE_E_INVALID_ARG, "autotune must be 0 or 1");
+    return GEMPE_OK;
+}
+
+// Symmetric, sorted, loop-free, duplicate-free, in-range CSR.
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n) {
+    if (rp[0] != 0) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr must be non-decreasing");
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = ci[e];
+            if (j < 0 || j >= n) return pack_fail(GEMPE_E_INVALID_GRAPH, "column index out of range");
+            if (j == i) return pack_fail(GEMPE_E_INVALID_GRAPH, "self loop at vertex " + std::to_string(i));
+            if (e > rp[i] && ci[e - 1] >= j)
+                return pack_fail(GEMPE_E_INVALID_GRAPH, "row " + std::to_string(i) + " not strictly increasing");
+        }
+    }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = ci[e];
+            if (!std::binary_search(ci + rp[j], ci + rp[j + 1], i))
+                return pack_fail(GEMPE_E_INVALID_GRAPH, "graph not symmetric: (" + std::to_string(i) + "," +
+                                                            std::to_string(j) + ") without its reverse");
+        }
+    return GEMPE_OK;
+}
+
+namespace {
+
+// Work units of the packed sweep (d <= 4) for rows [v0, v0 + n) of graph g:
+// runs of up to 32 consecutive vertices with at most `budget` edge + sample
+// slots in total; a vertex with more is cut into `budget`-slot chunks of its
+// row, the last chunk carrying the samples.
+void packed_units(const int32_t* rp, int32_t v0, int32_t n, int32_t k, int budget, int32_t g,
+                  std::vector<int4>& units) {
+    const int smp = k > 0 ? kUnitHasSamples : 0;
+    const int gy = g << kGraphShift;
+    int32_t i = v0;
+    const int32_t end = v0 + n;
+    while (i < end) {
+        const int32_t deg = rp[i + 1] - rp[i];
+        if (deg + k > budget) {
+            int32_t e = 0;
+            while (deg - e > budget) {
+                units.push_back(make_int4(i, gy | 1, e, e + budget));
+                e += budget;
+            }
+            units.push_back(make_int4(i, gy | 1, e, deg | smp));
+            ++i;
+            continue;
+        }
+        const int32_t u0 = i;
+        int32_t pairs = 0;
+        while (i < end && i - u0 < 32) {
+            const int32_t di = rp[i + 1] - rp[i] + k;
+            if (di > budget || pairs + di > budget) break;
+            pairs += di;
+            ++i;
+        }
+        units.push_back(make_int4(u0, gy | (i - u0), -1, smp));
+    }
+}
+
+// Work units of the per-unit sweep (d >= 8): each vertex's CSR slots in
+// chunks of `chunk`, the last chunk also carrying the vertex's samples.
+void chunk_units(const int32_t* rp, int32_t v0, int32_t n, int chunk, int32_t g, std::vector<int4>& units) {
+    const int gy = (g << kGraphShift) | 1;
+    for (int32_t i = v0; i < v0 + n; ++i) {
+        const int32_t deg = rp[i + 1] - rp[i];
+        const int32_t chunks = std::max<int32_t>(1, (deg + chunk - 1) / chunk);
+        for (int32_t c = 0; c < chunks; ++c) {
+            const int32_t p0 = c * chunk, p1 = std::min(deg, (c + 1) * chunk);
+            units.push_back(make_int4(i, gy, p0, p1 | (c == chunks - 1 ? kUnitHasSamples : 0)));
+        }
+    }
+}
+
+unsigned long long table_slots(int64_t nnz) {
+    unsigned long long s = 16;
+    while (s < 2ull * (unsigned long long)nnz) s <<= 1;
+    return s;
+}
+
+}  // namespace
+
+Pack::~Pack() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (side) cudaStreamSynchronize(side);
+    release_all();
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
+    if (side) cudaStreamDestroy(side);
+}
+
+void* Pack::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    if (p.dev_alloc) {
+        ptr = p.dev_alloc(bytes, p.alloc_user);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) allocations.push_back(ptr);
+    return ptr;
+}
+
+void Pack::release(void* ptr) {
+    if (!ptr) return;
+    auto it = std::find(allocations.begin(), allocations.end(), ptr);
+    if (it == allocations.end()) return;
+    allocations.erase(it);
+    if (p.dev_free) p.dev_free(ptr, p.alloc_user);
+    else cudaFree(ptr);
+}
+
+void Pack::release_all() {
+    for (void* ptr : allocations) {
+        if (p.dev_free) p.dev_free(ptr, p.alloc_user);
+        else cudaFree(ptr);
+    }
+    allocations.clear();
+}
+
+gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const gempe_params& params,
+                         cudaStream_t s, bool validate) {
+    gempe_status rc = check_params(&params, dim);
+    if (rc != GEMPE_OK) return rc;
+    if (gs.empty()) return pack_fail(GEMPE_E_INVALID_ARG, "a pack needs at least one graph");
+    if (gs.size() >= (1u << (31 - kGraphShift))) return pack_fail(GEMPE_E_INVALID_ARG, "too many graphs");
+    p = params;
+    d = dim;
+    k = p.neg_per_vertex;
+    acc_stride = acc_stride_for(d);
+    bins = p.hist_bins;
+    G = (int32_t)gs.size();
+    stream = s;
+    block = p.block_partners > 0;
+    tiles = block && p.precision == 1 && tile_dim(d);
+
+    // layout
+    long long rows_ll = 0, slots_ll = 0, tiles_ll = 0;
+    unsigned long long kslots = 0;
+    info.assign(G, GraphInfo{});
+    nnz.assign(G, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInput& in = gs[g];
+        if (!in.row_ptr || (!in.col_idx && in.n > 0 && in.row_ptr[in.n] > 0))
+            return pack_fail(GEMPE_E_INVALID_ARG, "null CSR array");
+        if (in.n < 2) return pack_fail(GEMPE_E_INVALID_ARG, "n must be at least 2");
+        if (in.row_ptr[in.n] < 0) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr[n] negative");
+        if (validate) {
+            rc = validate_csr(in.row_ptr, in.col_idx, in.n);
+            if (rc != GEMPE_OK) return rc;
+        }
+        nnz[g] = in.row_ptr[in.n];
+        // the per-block sums of sampled anchors' degrees are 32-bit
+        if ((unsigned long long)std::max(k, slots_per_vertex()) * (unsigned long long)nnz[g] >= (1ull << 32))
+            return pack_fail(GEMPE_E_INVALID_ARG, "sample slots * nnz must be below 2^32");
+        GraphInfo& gi = info[g];
+        gi.v0 = (int32_t)rows_ll;
+        gi.n = in.n;
+        gi.t0 = (int32_t)tiles_ll;
+        gi.n_tiles = block ? (in.n + kBlockT - 1) / kBlockT : 0;
+        gi.key_lo = (uint32_t)in.key;
+        gi.key_hi = (uint32_t)(in.key >> 32);
+        gi.key_off = kslots;
+        const unsigned long long ts = table_slots(nnz[g]);
+        gi.bucket_mask = ts / 4 - 1;
+        rows_ll += (long long)in.n + 1;
+        slots_ll += nnz[g];
+        tiles_ll += gi.n_tiles;
+        kslots += ts;
+    }
+    if (rows_ll >= INT32_MAX || slots_ll >= INT32_MAX)
+        return pack_fail(GEMPE_E_INVALID_ARG, "a pack holds below 2^31 vertices and CSR slots");
+    rows = (int32_t)rows_ll;
+    slots = slots_ll;
+    n_tiles = (int32_t)tiles_ll;
+    key_slots = kslots;
+
+    PK(cudaGetDevice(&device), "cudaGetDevice");
+    PK(ensure_mills_table(), "Mills table");
+    PK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device), "cudaDeviceGetAttribute");
+    PK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking), "cudaStreamCreate");
+    PK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming), "cudaEventCreate");
+    PK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming), "cudaEventCreate");
+    mills = mills_table_device();
+    if (!mills) return pack_fail(GEMPE_E_CUDA, "Mills table address");
+    if (tiles) PK(prepare_tile_kernel(d, bins), "tile kernel attributes");
+
+    // host copies of the pack CSR
+    row_ptr_h.assign((size_t)rows + 1, 0);
+    std::vector<int32_t> col_h((size_t)std::max<int64_t>(slots, 1));
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInput& in = gs[g];
+        const GraphInfo& gi = info[g];
+        const int32_t s0 = (int32_t)(g == 0 ? 0 : row_ptr_h[gi.v0]);
+        for (int32_t i = 0; i <= in.n; ++i) row_ptr_h[(size_t)gi.v0 + i] = s0 + in.row_ptr[i];
+        for (int64_t e = 0; e < nnz[g]; ++e) col_h[(size_t)s0 + e] = gi.v0 + in.col_idx[e];
+        // the spare row v0 + n closes the range; the next graph starts there
+        if (g + 1 < G) row_ptr_h[(size_t)gi.v0 + in.n + 1] = s0 + (int32_t)nnz[g];
+    }
+    row_ptr_h[(size_t)rows] = (int32_t)slots;
+    // vertex chunks and tile lists
+    std::vector<int4> vch;
+    std::vector<int2> titems;
+    std::vector<int4> sunits;
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInfo& gi = info[g];
+        for (int32_t o = 0; o < gi.n; o += kVChunk) vch.push_back(make_int4(gi.v0 + o, std::min(kVChunk, gi.n - o), g, 0));
+        for (int32_t t = 0; t < gi.n_tiles; ++t) {
+            titems.push_back(make_int2(gi.t0 + t, g));
+            const int32_t a0 = gi.v0 + t * kBlockT, a1 = gi.v0 + std::min(gi.n, (t + 1) * kBlockT);
+            const int32_t e0 = row_ptr_h[a0], e1 = row_ptr_h[a1];
+            int32_t e = e0;
+            do {
+                const int32_t eh = std::min(e1, e + kSamplerChunk);
+                sunits.push_back(make_int4(gi.t0 + t, e, eh, (g << 1) | (e == e0 ? 1 : 0)));
+                e = eh;
+            } while (e < e1);
+        }
+    }
+    n_vchunks = (int32_t)vch.size();
+    n_tile_items = tiles ? (int32_t)titems.size() : 0;
+    n_sampler_units = (int32_t)sunits.size();
+
+    // device memory
+    const size_t R = (size_t)rows;
+    row_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
+    col_idx = (int32_t*)alloc(sizeof(int32_t) * col_h.size());
+    keys = (unsigned long long*)alloc(sizeof(unsigned long long) * key_slots);
+    x = (float*)alloc(sizeof(float) * R * d);
+    acc = (float*)alloc(sizeof(float) * R * acc_stride);
+    const size_t GB = (size_t)G * bins;
+    hist_bytes = GB * (sizeof(unsigned long long) + 2 * sizeof(unsigned int) + sizeof(float));
+    hist = alloc(hist_bytes);
+    if (hist) {
+        hist_d = (unsigned long long*)hist;
+        hist_e = (unsigned int*)(hist_d + GB);
+        hist_c = hist_e + GB;
+        hist_x = (float*)(hist_c + GB);
+    }
+    graphs = (GraphInfo*)alloc(sizeof(GraphInfo) * G);
+    gst = (GraphState*)alloc(sizeof(GraphState) * G);
+    ps = (PackState*)alloc(sizeof(PackState));
+    active = (int32_t*)alloc(sizeof(int32_t) * G);
+    vchunks = (int4*)alloc(sizeof(int4) * vch.size());
+    scratch = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>(R * std::max(k, 1), 1));
+    samples = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>(block ? 1 : 2 * R * k, 1));
+    if (p.precision == 1) xb = (__nv_bfloat16*)alloc(sizeof(__nv_bfloat16) * R * d);
+    if (block) {
+        block_part = (int32_t*)alloc(sizeof(int32_t) * 2 * (size_t)std::max(n_tiles, 1) * kBlockP);
+        block_mask = (unsigned long long*)alloc(sizeof(unsigned long long) * 2 * R);
+        sampler_units = (int4*)alloc(sizeof(int4) * std::max<size_t>(sunits.size(), 1));
+        tile_items = (int2*)alloc(sizeof(int2) * std::max<size_t>(titems.size(), 1));
+        if (!block_part || !block_mask || !sampler_units || !tile_items)
+            return pack_fail(GEMPE_E_OOM, "device allocation failed");
+    }
+    if (!row_ptr || !col_idx || !keys || !x || !acc || !hist || !graphs || !gst || !ps || !active || !vchunks ||
+        !scratch || !samples || (p.precision == 1 && !xb))
+        return pack_fail(GEMPE_E_OOM, "device allocation failed");
+
+    std::vector<int32_t> act(G);
+    for (int32_t g = 0; g < G; ++g) act[g] = g;
+    std::vector<GraphState> st0(G);
+    std::memset(st0.data(), 0, sizeof(GraphState) * G);
+    for (auto& st : st0) st.sigma = p.sigma0;
+    PK(cudaMemcpyAsync(row_ptr, row_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s), "copy row_ptr");
+    PK(cudaMemcpyAsync(col_idx, col_h.data(), sizeof(int32_t) * col_h.size(), cudaMemcpyHostToDevice, s), "copy col_idx");
+    PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
+    PK(cudaMemcpyAsync(gst, st0.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, s), "init graph state");
+    PK(cudaMemsetAsync(ps, 0, sizeof(PackState), s), "init pack state");
+    PK(cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "copy active list");
+    PK(cudaMemcpyAsync(vchunks, vch.data(), sizeof(int4) * vch.size(), cudaMemcpyHostToDevice, s), "copy chunks");
+    PK(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * key_slots, s), "clear edge sets");
+    PK(cudaMemsetAsync(x, 0, sizeof(float) * R * d, s), "clear x");
+    if (xb) PK(cudaMemsetAsync(xb, 0, sizeof(__nv_bfloat16) * R * d, s), "clear xb");
+    PK(cudaMemsetAsync(acc, 0, sizeof(float) * R * acc_stride, s), "clear acc");
+    PK(cudaMemsetAsync(hist, 0, hist_bytes, s), "clear hist");
+    if (block) {
+        PK(cudaMemsetAsync(block_mask, 0, sizeof(unsigned long long) * 2 * R, s), "clear masks");
+        PK(cudaMemcpyAsync(sampler_units, sunits.data(), sizeof(int4) * sunits.size(), cudaMemcpyHostToDevice, s),
+           "copy sampler units");
+        PK(cudaMemcpyAsync(tile_items, titems.data(), sizeof(int2) * titems.size(), cudaMemcpyHostToDevice, s),
+           "copy tile list");
+    }
+    PK(cudaMemsetAsync(scratch, 0, sizeof(int32_t), s), "clear flag");
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInfo& gi = info[g];
+        PK(launch_hash_build(row_ptr, col_idx, gi.v0, gi.n, nnz[g], keys + gi.key_off, gi.bucket_mask, scratch, s),
+           "hash build");
+        PK(launch_init_positions(x + (size_t)gi.v0 * d, xb ? xb + (size_t)gi.v0 * d : nullptr, gi.n, d, gi.key_lo,
+                                 gi.key_hi, p.init_range, s),
+           "init positions");
+    }
+    int32_t hash_fail = 0;
+    PK(cudaMemcpyAsync(&hash_fail, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read flag");
+    PK(cudaStreamSynchronize(s), "create");
+    if (hash_fail) return pack_fail(GEMPE_E_INVALID_GRAPH, "edge hash set build failed");
+
+    sampler_grid = gempe::sampler_grid(rows, k, sm_count);
+    update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
+    tile_grid = gempe::tile_grid(n_tile_items, sm_count, 0);
+    return set_shape(PackShape{});
+}
+
+gempe_status Pack::set_shape(const PackShape& s) {
+    PackShape sh = s;
+    if (!sweep_lanes_supported(d, sh.lanes)) return pack_fail(GEMPE_E_INVALID_ARG, "unsupported lanes per pair");
+    std::vector<int4> units;
+    units.reserve((size_t)rows + (size_t)slots / 32 + 16);
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInfo& gi = info[g];
+        if (d <= kPackedMaxDim) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
+        else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, units);
+    }
+    if (items && (size_t)n_items < units.size()) {
+        release(items);
+        items = nullptr;
+    }
+    if (!items) {
+        items = (int4*)alloc(sizeof(int4) * std::max<size_t>(units.size(), 1));
+        if (!items) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+    }
+    n_items = (int32_t)units.size();
+    if (!units.empty())
+        PK(cudaMemcpyAsync(items, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, stream),
+           "copy work units");
+    PK(cudaStreamSynchronize(stream), "copy work units");
+    sweep_grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm);
+    shape = sh;
+    return GEMPE_OK;
+}
+
+EpochArgs Pack::args() const {
+    EpochArgs a{};
+    a.graphs = graphs;
+    a.gst = gst;
+    a.ps = ps;
+    a.n_graphs = G;
+    a.active = active;
+    a.n_active = G;
+    a.row_ptr = row_ptr;
+    a.col_idx = col_idx;
+    a.keys = keys;
+    a.x = x;
+    a.xb = xb;
+    a.acc = acc;
+    a.hist_e = hist_e;
+    a.hist_c = hist_c;
+    a.hist_d = hist_d;
+    a.hist_x = hist_x;
+    a.items = items;
+    a.n_items = n_items;
+    a.blocked = G > 1 ? 1 : 0;
+    a.vchunks = vchunks;
+    a.n_vchunks = n_vchunks;
+    a.rows = rows;
+    a.d = d;
+    a.acc_stride = acc_stride;
+    a.k = k;
+    a.max_retries = p.max_retries;
+    a.symmetric = p.symmetric_neg;
+    a.w_formula = p.w_formula;
+    a.clamp_neg_d = p.clamp_neg_d;
+    a.bins = bins;
+    a.mu = p.mu;
+    a.hist_scale = (float)bins / p.hist_max;
+    a.samples = samples;
+    a.block_P = block ? kBlockP : 0;
+    a.n_tiles = n_tiles;
+    a.block_part = block_part;
+    a.block_mask = block_mask;
+    a.tile_items = tile_items;
+    a.n_tile_items = n_tile_items;
+    a.sweep_samples = tiles ? 0 : 1;
+    a.sigma_every = p.sigma_every;
+    a.z_min = p.z_min;
+    a.hist_max = p.hist_max;
+    a.mills = mills;
+    return a;
+}
+
+namespace {
+cudaError_t launch_epoch_sampler(const Pack& pk, cudaStream_t s) {
+    if (pk.block) return launch_block_sampler(pk.args(), pk.sampler_units, pk.n_sampler_units, pk.sm_count, s);
+    return launch_sampler(pk.args(), pk.sampler_grid, s);
+}
+}  // namespace
+
+gempe_status Pack::prime() {
+    if (primed || slots_per_vertex() == 0) return GEMPE_OK;
+    PK(launch_epoch_sampler(*this, stream), "sampler");
+    primed = true;
+    return GEMPE_OK;
+}
+
+// The sweep of the current epoch on the stream and, forked onto the side
+// stream, the sampler of the next epoch (it only needs the graph).
+gempe_status Pack::enqueue_sweep() {
+    gempe_status s = prime();
+    if (s != GEMPE_OK) return s;
+    if (slots_per_vertex() > 0 && !sampled_ahead) {
+        PK(cudaEventRecord(fork_ev, stream), "fork");
+        PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
+        PK(launch_epoch_sampler(*this, side), "sampler");
+        PK(cudaEventRecord(join_ev, side), "join");
+        sampled_ahead = true;
+    }
+    SweepShape ss;
+    ss.grid = sweep_grid;
+    ss.lanes = shape.lanes;
+    PK(launch_sweep(args(), ss, stream), "sweep");
+    if (tiles) PK(launch_tile_bf16(args(), tile_grid, stream), "tiles");
+    return GEMPE_OK;
+}
+
+// The position update and slope fits, then the join with the side stream.
+gempe_status Pack::enqueue_update() {
+    PK(launch_update(args(), update_grid, stream), "update");
+    if (sampled_ahead) {
+        PK(cudaStreamWaitEvent(stream, join_ev, 0), "join");
+        sampled_ahead = false;
+    }
+    return GEMPE_OK;
+}
+
+gempe_status Pack::read_status() {
+    int32_t status = 0;
+    PK(cudaMemcpyAsync(&status, &ps->status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream), "status");
+    PK(cudaStreamSynchronize(stream), "synchronize");
+    if (status != 0) {
+        int32_t zero = 0;
+        cudaMemcpyAsync(&ps->status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, stream);
+        cudaStreamSynchronize(stream);
+        return pack_fail((gempe_status)status,
+                         "a position became non-finite during an update; it kept its old value");
+    }
+    return GEMPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner.  The candidates are the launch shapes the kernels support: for
+// d <= 4 the pair budget of a packed unit and the CTAs per SM; for d >= 8
+// the CSR slots per unit and the lanes per pair.  Each candidate's sweep is
+// timed (CUDA events, best of 3 after one warm-up) on the pack's own graphs
+// and current positions; the sums it leaves are cleared, the block masks it
+// consumes restored, and the graph statistics put back, so that the epoch
+// state is the same before and after.  The choice is cached per process by
+// (d, precision, sampling form, k, log2 rows, log2 slots, graphs > 1).
+// ---------------------------------------------------------------------------
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, PackShape> g_tune_cache;
+
+int ilog2(long long v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+}  // namespace
+
+gempe_status Pack::autotune() {
+    const TuneKey key{d, p.precision, block ? 1 : 0, k, ilog2(rows), ilog2(std::max<int64_t>(slots, 1)), G > 1};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return set_shape(it->second);
+    }
+    std::vector<PackShape> cands;
+    if (d <= kPackedMaxDim) {
+        for (int budget : {64, 128})
+            for (int bps : {0, 2}) {
+                PackShape s;
+                s.unit_pairs = budget;
+                s.blocks_per_sm = bps;
+                cands.push_back(s);
+            }
+    } else {
+        for (int lanes : {d / 8, d / 4})
+            for (int chunk : {32, 64, 128}) {
+                if (!sweep_lanes_supported(d, lanes)) continue;
+                PackShape s;
+                s.lanes = lanes;
+                s.edge_chunk = chunk;
+                cands.push_back(s);
+            }
+    }
+    gempe_status rc = prime();
+    if (rc != GEMPE_OK) return rc;
+    std::vector<GraphState> saved(G);
+    PK(cudaMemcpyAsync(saved.data(), gst, sizeof(GraphState) * G, cudaMemcpyDeviceToHost, stream), "save state");
+    // the sweep of the block form consumes the masks of the current epoch
+    unsigned long long* mask_copy = nullptr;
+    const size_t mask_bytes = sizeof(unsigned long long) * 2 * (size_t)rows;
+    const bool sweep_takes_masks = block && !tiles;
+    if (sweep_takes_masks) {
+        mask_copy = (unsigned long long*)alloc(mask_bytes);
+        if (!mask_copy) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+        PK(cudaMemcpyAsync(mask_copy, block_mask, mask_bytes, cudaMemcpyDeviceToDevice, stream), "save masks");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PK(cudaEventCreate(&e0), "cudaEventCreate");
+    PK(cudaEventCreate(&e1), "cudaEventCreate");
+    PackShape best;
+    float best_ms = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (const PackShape& c : cands) {
+        rc = set_shape(c);
+        if (rc != GEMPE_OK) break;
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+            if (sweep_takes_masks)
+                err = cudaMemcpyAsync(block_mask, mask_copy, mask_bytes, cudaMemcpyDeviceToDevice, stream);
+            SweepShape ss;
+            ss.grid = sweep_grid;
+            ss.lanes = shape.lanes;
+            if (err == cudaSuccess) err = cudaEventRecord(e0, stream);
+            if (err == cudaSuccess) err = launch_sweep(args(), ss, stream);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
+            if (err == cudaSuccess) err = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)rows * acc_stride, stream);
+            if (err == cudaSuccess) err = cudaMemsetAsync(hist, 0, hist_bytes, stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = std::min(t_min, ms);
+        }
+        if (err != cudaSuccess) break;
+        if (t_min < best_ms) {
+            best_ms = t_min;
+            best = shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (sweep_takes_masks && err == cudaSuccess)
+        err = cudaMemcpyAsync(block_mask, mask_copy, mask_bytes, cudaMemcpyDeviceToDevice, stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(gst, saved.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+    if (mask_copy) release(mask_copy);
+    if (err != cudaSuccess) return pack_cuda_fail(err, "autotune");
+    if (rc != GEMPE_OK) return rc;
+    best.sweep_us = best_ms * 1000.0f;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    return set_shape(best);
+}
+
+}  // namespace gempe

@@ -1,0 +1,118 @@
+// Host side of a pack: graphs of one dimension laid out back to back in one
+// set of device arrays (layout in engine.cuh), the work lists the kernels
+// stride over, and the enqueueing of one epoch.  A single-graph context is
+// a pack of one; a batch holds one pack per dimension.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+#include "gempe.h"
+
+namespace gempe {
+
+struct GraphInput {
+    const int32_t* row_ptr;   // host, n + 1
+    const int32_t* col_idx;   // host, row_ptr[n]
+    int32_t n;
+    uint64_t key;             // Philox key of the graph
+};
+
+// Launch shape of the sweep (the autotuner's search space).
+struct PackShape {
+    int unit_pairs = kUnitPairs;   // d <= 4: pair budget of a packed unit (64 or 128)
+    int edge_chunk = kEdgeChunk;   // d >= 8: CSR slots per work unit (32, 64, 128)
+    int lanes = 0;                 // d >= 8: lanes per pair (d/8 or d/4; 0 = d/8)
+    int blocks_per_sm = 0;         // sweep CTAs per SM (0 = as many as fit)
+    float sweep_us = 0.0f;         // measured sweep time of the chosen shape (autotuner)
+};
+
+// Message for gempe_last_error() and the status, in one call.
+gempe_status pack_fail(gempe_status st, const std::string& msg);
+gempe_status pack_cuda_fail(cudaError_t e, const char* what);
+gempe_status check_params(const gempe_params* p, int32_t d);
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n);
+
+struct Pack {
+    gempe_params p{};
+    int32_t d = 0, k = 0, acc_stride = 0, bins = 0;
+    int32_t G = 0, rows = 0, n_tiles = 0;
+    int64_t slots = 0;
+    unsigned long long key_slots = 0;
+    bool block = false, tiles = false;
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;   // set by the owner (context or batch), not owned
+    cudaStream_t side = nullptr;     // owned: the next epoch's sampler runs here
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool primed = false;             // samples of the current epoch are in the buffer
+    bool sampled_ahead = false;      // the next epoch's sampler has been enqueued
+    bool swept = false;              // a sweep ran without the update that clears its sums
+    std::vector<GraphInfo> info;     // host copies
+    std::vector<int64_t> nnz;
+    std::vector<int32_t> row_ptr_h;  // pack CSR offsets, rows + 1
+    PackShape shape;
+
+    // device memory
+    GraphInfo* graphs = nullptr;
+    GraphState* gst = nullptr;
+    PackState* ps = nullptr;
+    int32_t* active = nullptr;
+    int32_t* row_ptr = nullptr;
+    int32_t* col_idx = nullptr;
+    unsigned long long* keys = nullptr;
+    float* x = nullptr;
+    __nv_bfloat16* xb = nullptr;
+    float* acc = nullptr;
+    void* hist = nullptr;            // hist_d [G][bins] u64, hist_e, hist_c [G][bins] u32, hist_x [G][bins] f32
+    size_t hist_bytes = 0;
+    unsigned long long* hist_d = nullptr;
+    unsigned int* hist_e = nullptr;
+    unsigned int* hist_c = nullptr;
+    float* hist_x = nullptr;
+    int4* items = nullptr;
+    int32_t n_items = 0;
+    int4* vchunks = nullptr;
+    int32_t n_vchunks = 0;
+    int32_t* samples = nullptr;      // [2][rows][k]
+    int32_t* block_part = nullptr;   // [2][n_tiles][64]
+    unsigned long long* block_mask = nullptr;   // [2][rows]
+    int4* sampler_units = nullptr;   // block sampler {tile, e_lo, e_hi, graph << 1 | first}
+    int32_t n_sampler_units = 0;
+    int2* tile_items = nullptr;      // {tile, graph}
+    int32_t n_tile_items = 0;
+    int32_t* scratch = nullptr;      // rows * max(k, 1) int32: inspection samples, flags
+    const MillsCoef* mills = nullptr;
+    int sweep_grid = 0, sampler_grid = 0, update_grid = 0, tile_grid = 0;
+    std::vector<void*> allocations;
+
+    Pack() = default;
+    Pack(const Pack&) = delete;
+    Pack& operator=(const Pack&) = delete;
+    ~Pack();
+
+    void* alloc(size_t bytes);
+    void release(void* ptr);
+    void release_all();
+
+    // Lays the graphs out, copies them and builds their edge sets and initial
+    // positions on `stream` (synchronised before returning).
+    // validate = false: the caller has already run validate_csr on every graph.
+    gempe_status build(const std::vector<GraphInput>& graphs, int32_t d, const gempe_params& params,
+                       cudaStream_t stream, bool validate = true);
+    // Rebuilds the sweep units and grid for another launch shape.
+    gempe_status set_shape(const PackShape& s);
+    // Times the candidate shapes on this pack's own sweep and keeps the
+    // fastest (the epoch state is left as it was).
+    gempe_status autotune();
+
+    EpochArgs args() const;
+    gempe_status prime();            // samples of the current epoch, if the buffer lacks them
+    gempe_status enqueue_sweep();    // sweep (+ tiles); the next epoch's sampler forked to `side`
+    gempe_status enqueue_update();   // position update + slope fits; joins `side`
+    gempe_status read_status();      // synchronises; reports and clears a device-side error
+    int32_t slots_per_vertex() const { return block ? kBlockP : k; }
+};
+
+}  // namespace gempe

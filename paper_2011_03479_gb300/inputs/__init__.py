@@ -105,4 +105,35 @@ def ba_1m():
     return dict(name="ba-n1m-m8", row_ptr=rp, col_idx=ci, d=64, k=10, epochs=100)
 
 
+def sbm_batch(count: int, n_lo: int, n_hi: int, dims=(2, 16, 64), deg_lo: float = 4.0, deg_hi: float = 32.0,
+              blocks_lo: int = 2, blocks_hi: int = 8, intra: float = 0.9, seed: int = 4000):
+    """`count` independent SBM graphs: n log-uniform in [n_lo, n_hi], blocks
+    uniform in [blocks_lo, blocks_hi] (equal sizes, remainder spread), mean
+    degree uniform in [deg_lo, deg_hi] with a fraction `intra` of it inside
+    the vertex's block, d drawn from `dims`.  Graph q uses generator seed
+    seed + 1 + q; the shape parameters come from a numpy Generator(seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        nb = int(rng.integers(blocks_lo, blocks_hi + 1))
+        nb = max(1, min(nb, n // 2))
+        deg = float(rng.uniform(deg_lo, deg_hi))
+        d = int(rng.choice(np.asarray(dims)))
+        sizes = np.full(nb, n // nb, dtype=np.int64)
+        sizes[: n % nb] += 1
+        bs = n / nb
+        p_in = min(1.0, intra * deg / max(bs - 1.0, 1.0))
+        p_out = min(1.0, (1.0 - intra) * deg / max(n - bs, 1.0)) if nb > 1 else 0.0
+        rp, ci = sbm(sizes, p_in, p_out, seed=seed + 1 + q)
+        out.append(dict(row_ptr=rp, col_idx=ci, d=d, n=n, blocks=nb, mean_degree=deg))
+    return out
+
+
+def sbm_batch_256():
+    """256 SBMs, n log-uniform in [500, 50,000], 2-8 blocks, mean degree
+    U[4, 32] (90% inside the block), d in {2, 16, 64}; k=5, 200 epochs."""
+    return dict(name="sbm-batch-256", graphs=sbm_batch(256, 500, 50_000), k=5, epochs=200)
+
+
 WORKLOADS = {"sbm-n1000-b4": sbm_1000, "rmat-s16-ef16": rmat_s16, "ba-n1m-m8": ba_1m}

@@ -93,3 +93,17 @@ def test_generated_graphs_are_valid_csr(sbm_1000):
             assert np.all(np.diff(r) > 0)
         a = set(zip(rows.tolist(), ci.tolist()))
         assert all((j, i) in a for i, j in a)
+
+
+def test_batch_rejects_invalid_graphs_on_host():
+    """gempe_batch_create validates every graph on the host before any device
+    work: an asymmetric graph or an unsupported dimension fails cleanly."""
+    from paper_2011_03479_gb300 import binding
+    good = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), 2)
+    asym = (np.array([0, 1, 1], np.int32), np.array([1], np.int32), 2)
+    with pytest.raises(binding.GempeError) as ei:
+        binding.gempe_batch_create([good, asym])
+    assert ei.value.status == -2 and "graph 1" in str(ei.value)
+    with pytest.raises(binding.GempeError) as ei:
+        binding.gempe_batch_create([good, (good[0], good[1], 5)])
+    assert ei.value.status == -1
