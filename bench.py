@@ -49,6 +49,9 @@ FORMS = {
     "sbm-batch-256-bf16": {"autotune": 1, "precision": 1},         # BF16 positions for the d >= 8 graphs
 }
 BATCH_WORKLOADS = {"sbm-batch-256", "sbm-batch-256-bf16"}
+# serving form: Poisson arrivals (50 jobs/s) of R-MAT embedding jobs under a 120 GB device budget
+SERVE_WORKLOADS = {"rmat-serve-poisson50": {}}
+FORMS.update(SERVE_WORKLOADS)
 L2_FLUSH_BYTES = 256 << 20
 EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
 UNIT_PAIRS = 128     # edge + sample slots per packed work unit of the d <= 4 sweep
@@ -503,6 +506,117 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """The serving form.  --steps jobs arrive as a Poisson stream (mean 50 per
+    second): each an R-MAT graph with scale uniform in 10..18 and edge factor
+    uniform in 8..16 (a pool of two graphs per scale, generated before the
+    timed region), d from {2, 32, 128}, 100-300 epochs, k = 10, its own seed.
+    They are submitted through gempe_server_submit at their arrival times to a
+    server with a 120 GB budget and 32 job slots; the line reports the
+    pair-update throughput over the whole run and the p50/p99 completion
+    latency (arrival to positions on the host).  --warmup jobs run first,
+    untimed."""
+    import numpy as np
+    import torch
+
+    from paper_2011_03479_gb300 import binding as B
+    from paper_2011_03479_gb300 import inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(5000 + rank)
+    pool = {}
+    for scale in range(10, 19):
+        pool[scale] = []
+        for r in range(2):
+            ef = int(rng.integers(8, 17))
+            rp, ci = inputs.rmat(scale, ef, seed=5001 + 100 * scale + r)
+            pool[scale].append((rp, ci, ef))
+    k = 10
+    budget = 120 * (1 << 30)
+    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED)
+
+    def draw_job(q):
+        scale = int(rng.integers(10, 19))
+        rp, ci, ef = pool[scale][int(rng.integers(0, 2))]
+        return dict(rp=rp, ci=ci, d=int(rng.choice([2, 32, 128])), epochs=int(rng.integers(100, 301)),
+                    seed=inputs.EMBED_SEED ^ (q + 1), scale=scale, ef=ef)
+
+    srv = B.gempe_server_create(budget, max_jobs=32, params=p)
+    for q in range(args.warmup):
+        j = draw_job(-1 - q)
+        jid = B.gempe_server_submit(srv, j["rp"], j["ci"], j["d"], 20, j["seed"])
+        B.gempe_server_wait(srv, jid, 600000)
+        B.gempe_server_result(srv, jid)
+    jobs = [draw_job(q) for q in range(args.steps)]
+    gaps = rng.exponential(1.0 / 50.0, size=len(jobs))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ids = []
+    t_next = 0.0
+    for j, g in zip(jobs, gaps):
+        t_next += g
+        dt = t_next - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(B.gempe_server_submit(srv, j["rp"], j["ci"], j["d"], j["epochs"], j["seed"]))
+    infos = [B.gempe_server_wait(srv, i, 3600 * 1000) for i in ids]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    for i in ids:
+        B.gempe_server_result(srv, i)
+    stats = B.gempe_server_stats(srv)
+    srv.close()
+    sub = np.array([inf["submit_ns"] for inf in infos], dtype=np.float64)
+    adm = np.array([inf["admit_ns"] for inf in infos], dtype=np.float64)
+    done = np.array([inf["done_ns"] for inf in infos], dtype=np.float64)
+    pairs = float(sum(inf["pairs"] for inf in infos))
+    span = (done.max() - sub.min()) / 1e9
+    lat = (done - sub) / 1e6
+    wait = (adm - sub) / 1e6
+    arrivals = (sub.max() - sub.min()) / 1e9
+    value = pairs / span
+    if world > 1:
+        import torch.distributed as dist
+        v = torch.tensor([value], dtype=torch.float64, device=torch.device("cuda", local))
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        value = v.item()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    h2d = float(np.mean([j["rp"].nbytes + j["ci"].nbytes for j in jobs]))
+    d2h = float(np.mean([4 * (len(j["rp"]) - 1) * j["d"] for j in jobs]))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * span / len(jobs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "jobs": len(jobs), "arrival_rate_per_s": 50,
+                   "scale": "U{10..18}", "edge_factor": "U{8..16}", "d": [2, 32, 128], "epochs": "U{100..300}",
+                   "k": k, "budget_bytes": budget, "max_jobs": 32,
+                   "step": "one job: arrival to positions on the host (gempe_server_submit .. gempe_server_result)",
+                   "l2": "inputs (many jobs' device state) larger than L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "offered_pairs_per_s": pairs / max(arrivals, 1e-9),
+        "peak_device_bytes": stats["peak_bytes_in_use"],
+        "failed_jobs": stats["failed"],
+        "roofline": None,
+        "clocks": clk,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "step": "one job through the public serving calls (submit from host CSR, result to host)"},
+        "gpu_launches": None,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -552,6 +666,8 @@ def main():
         run_reference(args)
     elif args.workload in BATCH_WORKLOADS:
         run_batch(args)
+    elif args.workload in SERVE_WORKLOADS:
+        run_serve(args)
     else:
         run_gempe(args)
 

@@ -243,6 +243,60 @@ gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_stats_t* out
  * the pack, out[5] tuned sweep time in ns (0 if not tuned). */
 gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out6);
 
+/* ------------------------------------------------------------------------
+ * Serving form: embedding jobs admitted by device-memory budget and run with
+ * continuous batching.
+ *
+ * A server owns max_jobs job slots (CUDA streams) and two host threads.  Jobs
+ * are admitted in arrival order as soon as a slot is free and the job's
+ * device bytes (gempe_job_bytes) fit in the budget next to the running jobs;
+ * a running job keeps its CSR, edge set, positions and accumulators resident
+ * on the device and runs its epochs on its slot's stream, so the kernels of
+ * all running jobs overlap.  When its epochs are done its positions go to
+ * pinned host memory and its device memory returns to the budget.  A job
+ * computes what gempe_create + gempe_step(epochs) compute with params.seed =
+ * the job's seed (up to the order of FP32 atomic additions).  The server's
+ * params apply to every job (precision 1 and block sampling only for d >= 8).
+ * ------------------------------------------------------------------------ */
+typedef struct gempe_server gempe_server;
+
+typedef struct gempe_job_desc {
+    const int32_t* row_ptr;  /* host int32[n+1], copied at submit */
+    const int32_t* col_idx;  /* host int32[row_ptr[n]], copied at submit */
+    int32_t n;
+    int32_t d;
+    int32_t epochs;
+    uint64_t seed;           /* Philox key of the job */
+} gempe_job_desc;
+
+typedef struct gempe_job_info {
+    int32_t state;           /* 0 queued, 1 running, 2 done; a negative gempe_status if it failed */
+    int32_t epochs, epochs_done;
+    uint64_t submit_ns, admit_ns, done_ns;   /* steady clock, ns since the server was created */
+    uint64_t device_bytes;   /* device bytes reserved for the job */
+    uint64_t pairs;          /* pair-updates of the finished job: epochs * m + sampled non-edges used */
+    float sigma;             /* final slope of the finished job */
+} gempe_job_info;
+
+/* Device bytes a job of n vertices and nnz CSR slots holds while it runs
+ * (0 for invalid arguments).  Pure host arithmetic. */
+size_t gempe_job_bytes(int32_t n, int64_t nnz, int32_t d, const gempe_params* p);
+/* max_jobs in [1, 256]; p->dev_alloc must be NULL (jobs allocate stream-ordered). */
+gempe_status gempe_server_create(size_t hbm_budget_bytes, int32_t max_jobs, const gempe_params* p,
+                                 gempe_server** out);
+/* Stops the threads; running jobs finish their enqueued work and are dropped. */
+void gempe_server_destroy(gempe_server* s);
+/* Queue a job (copies the CSR).  GEMPE_E_BUDGET if the job alone exceeds the
+ * budget; invalid graphs are reported by poll / wait / result. */
+gempe_status gempe_server_submit(gempe_server* s, const gempe_job_desc* job, uint64_t* job_id);
+gempe_status gempe_server_poll(gempe_server* s, uint64_t job_id, gempe_job_info* info);
+/* Block until the job is done or failed, at most timeout_ms (GEMPE_E_TIMEOUT). */
+gempe_status gempe_server_wait(gempe_server* s, uint64_t job_id, int32_t timeout_ms, gempe_job_info* info);
+/* Positions of a finished job to host float[n*d]; releases the job record. */
+gempe_status gempe_server_result(gempe_server* s, uint64_t job_id, float* host_out, size_t count);
+/* out6: queued, running, completed, failed, device bytes in use, peak bytes in use. */
+gempe_status gempe_server_stats(gempe_server* s, int64_t* out6);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* gempe_last_error(void);
 

@@ -78,6 +78,31 @@ class gempe_graph_desc(ctypes.Structure):
     ]
 
 
+class gempe_job_desc(ctypes.Structure):
+    _fields_ = [
+        ("row_ptr", ctypes.c_void_p),
+        ("col_idx", ctypes.c_void_p),
+        ("n", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("epochs", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class gempe_job_info(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int32),
+        ("epochs", ctypes.c_int32),
+        ("epochs_done", ctypes.c_int32),
+        ("submit_ns", ctypes.c_uint64),
+        ("admit_ns", ctypes.c_uint64),
+        ("done_ns", ctypes.c_uint64),
+        ("device_bytes", ctypes.c_uint64),
+        ("pairs", ctypes.c_uint64),
+        ("sigma", ctypes.c_float),
+    ]
+
+
 class GempeError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -132,6 +157,14 @@ def load(build: bool = True):
         "gempe_batch_loss": (st, [vp, i32, P(ctypes.c_double), P(ctypes.c_float)]),
         "gempe_batch_stats": (st, [vp, i32, P(gempe_stats_t)]),
         "gempe_batch_shape": (st, [vp, i32, P(i64)]),
+        "gempe_job_bytes": (sz, [i32, i64, i32, P(gempe_params)]),
+        "gempe_server_create": (st, [sz, i32, P(gempe_params), P(vp)]),
+        "gempe_server_destroy": (None, [vp]),
+        "gempe_server_submit": (st, [vp, P(gempe_job_desc), P(ctypes.c_uint64)]),
+        "gempe_server_poll": (st, [vp, ctypes.c_uint64, P(gempe_job_info)]),
+        "gempe_server_wait": (st, [vp, ctypes.c_uint64, i32, P(gempe_job_info)]),
+        "gempe_server_result": (st, [vp, ctypes.c_uint64, vp, sz]),
+        "gempe_server_stats": (st, [vp, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -408,6 +441,94 @@ def gempe_batch_shape(b: _Batch, d: int) -> dict:
     _check(load().gempe_batch_shape(b.handle, int(d), out))
     return {"unit": out[0], "lanes": out[1], "blocks_per_sm": out[2], "grid": out[3], "graphs": out[4],
             "tuned_sweep_ns": out[5]}
+
+
+def gempe_job_bytes(n: int, nnz: int, d: int, params: gempe_params | None = None) -> int:
+    p = params or gempe_default_params()
+    return int(load().gempe_job_bytes(int(n), int(nnz), int(d), ctypes.byref(p)))
+
+
+class _Server:
+    """Owned server handle (gempe_server_destroy on close / GC)."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = handle
+        self.shapes = {}     # job id -> (n, d)
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            load().gempe_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def gempe_server_create(hbm_budget_bytes: int, max_jobs: int = 32, params: gempe_params | None = None) -> _Server:
+    p = params or gempe_default_params()
+    h = ctypes.c_void_p()
+    _check(load().gempe_server_create(int(hbm_budget_bytes), int(max_jobs), ctypes.byref(p), ctypes.byref(h)))
+    return _Server(h, keep=(p,))
+
+
+def gempe_server_destroy(s: _Server) -> None:
+    s.close()
+
+
+def gempe_server_submit(s: _Server, row_ptr, col_idx, d: int, epochs: int, seed: int) -> int:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    desc = gempe_job_desc()
+    desc.row_ptr = rp.ctypes.data
+    desc.col_idx = ci.ctypes.data if len(ci) else None
+    desc.n = len(rp) - 1
+    desc.d = int(d)
+    desc.epochs = int(epochs)
+    desc.seed = int(seed)
+    jid = ctypes.c_uint64()
+    _check(load().gempe_server_submit(s.handle, ctypes.byref(desc), ctypes.byref(jid)))
+    s.shapes[jid.value] = (len(rp) - 1, int(d))
+    return jid.value
+
+
+def _info(i: gempe_job_info) -> dict:
+    return {f: getattr(i, f) for f, _ in gempe_job_info._fields_}
+
+
+def gempe_server_poll(s: _Server, job_id: int) -> dict:
+    info = gempe_job_info()
+    _check(load().gempe_server_poll(s.handle, ctypes.c_uint64(job_id), ctypes.byref(info)))
+    return _info(info)
+
+
+def gempe_server_wait(s: _Server, job_id: int, timeout_ms: int = 60000) -> dict:
+    info = gempe_job_info()
+    _check(load().gempe_server_wait(s.handle, ctypes.c_uint64(job_id), int(timeout_ms), ctypes.byref(info)))
+    return _info(info)
+
+
+def gempe_server_result(s: _Server, job_id: int) -> np.ndarray:
+    n, d = s.shapes.pop(job_id)
+    out = np.empty((n, d), dtype=np.float32)
+    _check(load().gempe_server_result(s.handle, ctypes.c_uint64(job_id), _ptr(out), out.size))
+    return out
+
+
+def gempe_server_stats(s: _Server) -> dict:
+    out = (ctypes.c_int64 * 6)()
+    _check(load().gempe_server_stats(s.handle, out))
+    return {"queued": out[0], "running": out[1], "completed": out[2], "failed": out[3], "bytes_in_use": out[4],
+            "peak_bytes_in_use": out[5]}
 
 
 def gempe_last_error() -> str:

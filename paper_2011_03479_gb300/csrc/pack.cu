@@ -361,6 +361,23 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     return set_shape(PackShape{});
 }
 
+size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p) {
+    auto al = [](size_t b) { return (b + 511) / 512 * 512; };   // allocation granularity
+    const bool blk = p.block_partners > 0 && d >= 8;
+    const size_t R = (size_t)n + 1, k = (size_t)p.neg_per_vertex, bins = (size_t)p.hist_bins;
+    const size_t tiles = blk ? ((size_t)n + kBlockT - 1) / kBlockT : 0;
+    const size_t units_max = (size_t)n + (size_t)nnz / 32 + 16;
+    size_t b = 0;
+    b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1)) + al(8 * table_slots(nnz));
+    b += al(4 * R * d) + al(4 * R * acc_stride_for(d));
+    if (p.precision == 1 && d >= 8) b += al(2 * R * d);
+    b += al(bins * 20) + al(sizeof(GraphInfo)) + al(sizeof(GraphState)) + al(sizeof(PackState)) + al(4);
+    b += al(16 * (((size_t)n + kVChunk - 1) / kVChunk)) + al(4 * R * std::max<size_t>(k, 1));
+    b += al(4 * std::max<size_t>(blk ? 1 : 2 * R * k, 1)) + al(16 * units_max);
+    if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
+    return b;
+}
+
 gempe_status Pack::set_shape(const PackShape& s) {
     PackShape sh = s;
     if (!sweep_lanes_supported(d, sh.lanes)) return pack_fail(GEMPE_E_INVALID_ARG, "unsupported lanes per pair");

@@ -113,6 +113,10 @@ struct Pack {
     gempe_status enqueue_update();   // position update + slope fits; joins `side`
     gempe_status read_status();      // synchronises; reports and clears a device-side error
     int32_t slots_per_vertex() const { return block ? kBlockP : k; }
+
+    // Device bytes a pack of one graph with n vertices and nnz CSR slots
+    // allocates (an upper bound: the sweep units are counted at their most).
+    static size_t bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p);
 };
 
 }  // namespace gempe
