@@ -568,7 +568,15 @@ def run_serve(args):
     for i in ids:
         B.gempe_server_result(srv, i)
     stats = B.gempe_server_stats(srv)
+    # capacity: the first jobs again, all submitted at once (closed loop)
+    cap_jobs = jobs[: min(len(jobs), 100)]
+    cids = [B.gempe_server_submit(srv, j["rp"], j["ci"], j["d"], j["epochs"], j["seed"]) for j in cap_jobs]
+    cinfos = [B.gempe_server_wait(srv, i, 3600 * 1000) for i in cids]
+    for i in cids:
+        B.gempe_server_result(srv, i)
     srv.close()
+    cap_span = (max(c["done_ns"] for c in cinfos) - min(c["submit_ns"] for c in cinfos)) / 1e9
+    capacity = sum(c["pairs"] for c in cinfos) / cap_span
     sub = np.array([inf["submit_ns"] for inf in infos], dtype=np.float64)
     adm = np.array([inf["admit_ns"] for inf in infos], dtype=np.float64)
     done = np.array([inf["done_ns"] for inf in infos], dtype=np.float64)
@@ -603,6 +611,9 @@ def run_serve(args):
                        "mean": float(lat.mean()), "max": float(lat.max())},
         "queue_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
         "offered_pairs_per_s": pairs / max(arrivals, 1e-9),
+        "capacity_pairs_per_s": capacity,
+        "capacity_note": f"{len(cap_jobs)} of the same jobs submitted at once; when the offered load is above "
+                         "this the latency is dominated by the queue",
         "peak_device_bytes": stats["peak_bytes_in_use"],
         "failed_jobs": stats["failed"],
         "roofline": None,

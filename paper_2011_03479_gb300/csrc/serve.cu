@@ -1,18 +1,20 @@
 // Serving form of the C ABI (include/gempe.h): embedding jobs admitted by
 // device-memory budget and run with continuous batching.
 //
-// Two native threads per server:
-//  - the admitter takes submitted jobs in arrival order, validates the CSR
-//    on the host, waits until a job slot is free and the job's device bytes
-//    fit in the budget next to the running jobs, then builds the job's
-//    device-resident state (CSR, edge set, positions, accumulators; a pack
-//    of one graph, stream-ordered allocations on the slot's stream) and
-//    captures its epoch graphs;
-//  - the stepper keeps every running job's epochs in flight on its own
+// Native threads per server:
+//  - admission workers (a small pool) take submitted jobs in arrival order
+//    and validate their CSR on the host in parallel; each job then waits for
+//    its turn -- capacity is reserved strictly in arrival order -- until a
+//    job slot is free and the job's device bytes fit in the budget next to
+//    the running jobs; the worker then builds the job's device-resident
+//    state (CSR, edge set, positions, accumulators; a pack of one graph,
+//    stream-ordered allocations on the slot's stream) and captures its epoch
+//    graphs, while other workers build other jobs;
+//  - one stepper keeps every running job's epochs in flight on its own
 //    stream (chunks of up to kChunk epochs, at most two chunks ahead), so
 //    the kernels of all running jobs overlap on the device; a job whose
 //    epochs are done has its positions copied to pinned host memory and its
-//    device memory released, which lets the admitter start the next job.
+//    device memory released, which lets the next job in line start.
 // A job's arithmetic is the same as gempe_create + gempe_step with the
 // job's seed: only the order of FP32 atomic additions can differ.
 #include <cuda_runtime.h>
@@ -52,6 +54,7 @@ void job_free(void* ptr, void* user);
 
 struct Job {
     uint64_t id = 0;
+    uint64_t ticket = 0;                // arrival order: capacity is reserved in this order
     std::vector<int32_t> rp, ci;
     int32_t n = 0, d = 0, epochs = 0;
     uint64_t seed = 0;
@@ -131,13 +134,16 @@ struct gempe_server {
     PackState* slot_ps = nullptr;       // pinned [max_jobs]
     std::mutex mu;
     std::condition_variable cv_pending, cv_capacity, cv_done, cv_work;
-    std::deque<Job*> pending;
+    std::deque<Job*> pending;           // submitted, not yet taken by a worker
+    size_t waiting = 0;                 // taken by a worker, capacity not yet reserved
+    uint64_t next_ticket = 0, tickets = 0;
     std::vector<Job*> active;
     std::map<uint64_t, std::unique_ptr<Job>> jobs;
     uint64_t next_id = 1;
     uint64_t completed = 0, failed = 0;
     std::atomic<bool> stop{false};
-    std::thread admitter, stepper;
+    std::vector<std::thread> admitters;
+    std::thread stepper;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     // pinned host buffers kept for reuse (freeing pinned memory can synchronise the device)
     std::multimap<size_t, float*> pinned_pool;
@@ -262,47 +268,54 @@ void gempe_server::admit_loop() {
             cv_pending.wait(lock, [&] { return stop.load() || !pending.empty(); });
             if (stop.load()) return;
             j = pending.front();
-        }
-        // host validation (the job record is immutable while queued)
-        gempe_status rc = validate_csr(j->rp.data(), j->ci.data(), j->n);
-        if (rc != GEMPE_OK) {
-            std::lock_guard<std::mutex> lock(mu);
             pending.pop_front();
-            j->error = gempe_last_error();
-            j->done_ns = now_ns(t0);
-            ++failed;
-            j->state.store(rc);
-            cv_done.notify_all();
-            continue;
+            ++waiting;
         }
+        // host validation, in parallel with other workers
+        const gempe_status vrc = validate_csr(j->rp.data(), j->ci.data(), j->n);
+        const std::string verr = vrc != GEMPE_OK ? std::string(gempe_last_error()) : std::string();
         int slot = -1;
         {
             std::unique_lock<std::mutex> lock(mu);
             cv_capacity.wait(lock, [&] {
                 if (stop.load()) return true;
+                if (j->ticket != next_ticket) return false;
+                if (vrc != GEMPE_OK) return true;
                 if (in_use + j->bytes > budget) return false;
-                for (size_t s = 0; s < slot_busy.size(); ++s)
-                    if (!slot_busy[s]) return true;
+                for (size_t s2 = 0; s2 < slot_busy.size(); ++s2)
+                    if (!slot_busy[s2]) return true;
                 return false;
             });
             if (stop.load()) return;
-            for (size_t s = 0; s < slot_busy.size(); ++s)
-                if (!slot_busy[s]) {
-                    slot = (int)s;
+            --waiting;
+            ++next_ticket;
+            if (vrc != GEMPE_OK) {
+                j->error = verr;
+                j->done_ns = now_ns(t0);
+                ++failed;
+                j->state.store(vrc);
+                cv_capacity.notify_all();
+                cv_done.notify_all();
+                continue;
+            }
+            for (size_t s2 = 0; s2 < slot_busy.size(); ++s2)
+                if (!slot_busy[s2]) {
+                    slot = (int)s2;
                     break;
                 }
             slot_busy[slot] = 1;
             in_use += j->bytes;
             peak_in_use = std::max(peak_in_use, in_use);
-            pending.pop_front();
             j->slot = slot;
             j->stream = slot_streams[slot];
             j->host_state = slot_state + slot;
             j->host_ps = slot_ps + slot;
+            j->admit_ns = now_ns(t0);
+            cv_capacity.notify_all();   // the next ticket may proceed
         }
         j->host_x_bytes = sizeof(float) * (size_t)j->n * j->d;
         j->host_x = take_pinned(j->host_x_bytes);
-        rc = j->host_x ? start_job(j) : pack_fail(GEMPE_E_OOM, "pinned host buffer");
+        gempe_status rc = j->host_x ? start_job(j) : pack_fail(GEMPE_E_OOM, "pinned host buffer");
         if (rc != GEMPE_OK) {
             j->error = gempe_last_error();
             finish_job(j, rc);
@@ -310,7 +323,6 @@ void gempe_server::admit_loop() {
         }
         {
             std::lock_guard<std::mutex> lock(mu);
-            j->admit_ns = now_ns(t0);
             j->state.store(kRunning);
             active.push_back(j);
         }
@@ -445,7 +457,9 @@ GEMPE_API gempe_status gempe_server_create(size_t hbm_budget_bytes, int32_t max_
     s->slot_state = (GraphState*)hs;
     s->slot_ps = (PackState*)hp;
     gempe_server* raw = s.release();
-    raw->admitter = std::thread([raw] { raw->admit_loop(); });
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int workers = std::max(2, std::min(8, (int)(hw ? hw / 2 : 2)));
+    for (int q = 0; q < workers; ++q) raw->admitters.emplace_back([raw] { raw->admit_loop(); });
     raw->stepper = std::thread([raw] { raw->step_loop(); });
     *out = raw;
     return GEMPE_OK;
@@ -461,7 +475,8 @@ GEMPE_API void gempe_server_destroy(gempe_server* s) {
         s->cv_work.notify_all();
         s->cv_done.notify_all();
     }
-    if (s->admitter.joinable()) s->admitter.join();
+    for (auto& t : s->admitters)
+        if (t.joinable()) t.join();
     if (s->stepper.joinable()) s->stepper.join();
     for (auto& kv : s->jobs) kv.second->release_device();
     for (cudaStream_t st : s->slot_streams) {
@@ -500,6 +515,7 @@ GEMPE_API gempe_status gempe_server_submit(gempe_server* s, const gempe_job_desc
     j->bytes = bytes;
     std::lock_guard<std::mutex> lock(s->mu);
     j->id = s->next_id++;
+    j->ticket = s->tickets++;
     j->submit_ns = now_ns(s->t0);
     *job_id = j->id;
     s->pending.push_back(j.get());
@@ -573,7 +589,7 @@ GEMPE_API gempe_status gempe_server_result(gempe_server* s, uint64_t job_id, flo
 GEMPE_API gempe_status gempe_server_stats(gempe_server* s, int64_t* out6) {
     if (!s || !out6) return pack_fail(GEMPE_E_INVALID_ARG, "null argument");
     std::lock_guard<std::mutex> lock(s->mu);
-    out6[0] = (int64_t)s->pending.size();
+    out6[0] = (int64_t)(s->pending.size() + s->waiting);
     out6[1] = (int64_t)s->active.size();
     out6[2] = (int64_t)s->completed;
     out6[3] = (int64_t)s->failed;
