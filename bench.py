@@ -427,6 +427,27 @@ def run_batch(args):
     value = pairs_all / t_all
     b.close()
 
+    # the plain form: every graph in its own FP32 context, one after the other
+    alone_steps = min(args.steps, 20)
+    alone_pairs, alone_s = 0, 0.0
+    pa = B.gempe_default_params(neg_per_vertex=k)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for q, g in enumerate(graphs):
+        pa.seed = inputs.EMBED_SEED ^ q
+        c = B.gempe_create(g["row_ptr"], g["col_idx"], g["d"], pa, stream=stream)
+        with torch.cuda.stream(stream):
+            B.gempe_step(c, 1)          # captures the epoch graph
+            u0 = B.gempe_stats(c)["used"]
+            flush.zero_()
+            ea.record(stream)
+            B.gempe_step(c, alone_steps)
+            eb.record(stream)
+            eb.synchronize()
+        alone_s += ea.elapsed_time(eb) / 1e3
+        alone_pairs += alone_steps * (len(g["col_idx"]) // 2) + B.gempe_stats(c)["used"] - u0
+        c.close()
+    alone_value = alone_pairs / alone_s
+
     # end to end: one batch job (create from pinned host CSR, `epochs` epochs, positions back)
     pinned = [(torch.from_numpy(g["row_ptr"]).pin_memory().numpy(), torch.from_numpy(g["col_idx"]).pin_memory().numpy(),
                g["d"]) for g in graphs]
@@ -477,6 +498,9 @@ def run_batch(args):
         "pairs_per_epoch": pairs / args.steps,
         "shapes": {str(d): sh for d, sh in shapes.items()},
         "create_s": create_s,
+        "alone_fp32": {"value": alone_value, "unit": UNIT, "ratio": value / alone_value,
+                       "how": f"each graph in its own FP32 context (gempe_create + gempe_step), one after the "
+                              f"other, {alone_steps} epochs each, CUDA events around each graph's epochs"},
         "roofline": {"bound": "hbm", "kernel": "epoch (sweeps of all packs, concurrent)", "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": byts, "traffic": None,
