@@ -449,95 +449,137 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
 }
 
 // ---------------------------------------------------------------------------
-// Pair sweep for d >= 8: one warp per work unit (one vertex, or one chunk of
-// a hub's row), G lanes per pair, each lane owning D/G coordinates.
+// Pair sweep for d >= 8.  A warp is 32/G lane groups of G lanes; each group
+// owns one work unit (a vertex with its samples, or one chunk of a hub's
+// row), lane gl of the group owning coordinates [gl*P, gl*P + P) of every
+// row, P = D/G.  The host packs the units into warp tasks of 32/G units of
+// similar size, so the groups of a warp run the same number of rounds.
+//
+// A round takes G pairs of the group's vertex, one per lane:
+//   (A) G sub-rounds: the group gathers pair s's row chunk by chunk and sums
+//       the squared differences over its lanes; lane s keeps the distance;
+//   (B) every lane evaluates the pair term of its own pair (one math pass
+//       per G pairs per group, 32 per warp);
+//   (C) G sub-rounds: the group gathers pair s's row again (an L1 hit) and
+//       adds c (x_i - x_j) to its own coordinates of the vertex's sum, and
+//       the negated term to a sampled partner's accumulator row.
+// Each lane's vertex sum covers its own coordinates, so no reduction across
+// lanes is needed except for z.
 // ---------------------------------------------------------------------------
 template <int D, int G, typename PT>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int P = D / G;
-    constexpr int PAIRS = 32 / G;
+    constexpr int PG = 32 / G;            // groups (units) per warp task
     const PT* X = pos_of<PT>(a);
     extern __shared__ unsigned int s_u32[];
-    const BlockHist hist = block_hist(s_u32, a.bins, home_graph(a));
+    const int n_tasks = a.n_items / PG;
+    // tasks of this warp: a contiguous range per block in packs of several graphs
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    int t_begin, t_end, t_step, home;
+    if (a.blocked) {
+        const int lo = (int)((long long)n_tasks * blockIdx.x / gridDim.x);
+        t_begin = lo + wib;
+        t_end = (int)((long long)n_tasks * (blockIdx.x + 1) / gridDim.x);
+        t_step = wpb;
+        home = lo < t_end ? (__ldg(&a.items[(size_t)lo * PG].y) >> kGraphShift) : -1;
+    } else {
+        t_begin = blockIdx.x * wpb + wib;
+        t_end = n_tasks;
+        t_step = gridDim.x * wpb;
+        home = a.n_graphs == 1 ? 0 : -1;
+    }
+    const BlockHist hist = block_hist(s_u32, a.bins, home);
     __shared__ unsigned int s_used;
     hist_clear(hist, a.bins);
     if (threadIdx.x == 0) s_used = 0u;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const int grp = lane / G;
-    const int gl = lane % G;
+    const int gl = lane % G;               // lane within the group
+    const int gbase = lane - gl;           // first lane of the group
     const bool block = a.block_P > 0;
     const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex
-    const UnitRange ur = warp_units(a);
 
-    for (int it = ur.begin; it < ur.end; it += ur.step) {
-        const int4 item = __ldg(a.items + it);
-        const int i = item.x;
+    for (int task = t_begin; task < t_end; task += t_step) {
+        const int4 item = __ldg(a.items + (size_t)task * PG + lane / G);
+        const int i = item.x;                              // -1: padding
         const int graph = item.y >> kGraphShift;
-        const bool has_samples = (item.w & kUnitHasSamples) && k_eff > 0 && a.sweep_samples;
+        const bool live = i >= 0;
+        const bool has_samples = live && (item.w & kUnitHasSamples) && k_eff > 0 && a.sweep_samples;
         const int p0 = item.z, p1 = item.w & ~kUnitHasSamples;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
-        const int e0 = __ldg(a.row_ptr + i);
-        const int deg = __ldg(a.row_ptr + i + 1) - e0;
+        int e0 = 0, deg = 0;
         float xi[P];
-        load_chunk<D, P>(X, i, gl, xi);
-
-        // Sampled non-edges of this vertex: lane t owns slots t and t + 32.
-        int g0 = -1, g1 = -1;
+        if (live) {
+            e0 = __ldg(a.row_ptr + i);
+            deg = __ldg(a.row_ptr + i + 1) - e0;
+            load_chunk<D, P>(X, i, gl, xi);
+        } else {
+#pragma unroll
+            for (int c = 0; c < P; ++c) xi[c] = 0.0f;
+        }
+        const int ne = live ? p1 - p0 : 0;
+        // the vertex's sampled partners: masks / buffer, accepted count
         int k_acc = 0;
+        unsigned long long bmask_v = 0ull;
+        const int32_t* tp = nullptr;
+        const int32_t* sp = nullptr;
         if (has_samples) {
             if (block) {
                 unsigned long long* bm = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows + i;
-                const unsigned long long m = *bm;
-                __syncwarp();
-                if (lane == 0) *bm = 0ull;   // read once: the buffer starts empty two epochs on
+                bmask_v = *bm;
                 const int gv0 = __ldg(&a.graphs[graph].v0), gt0 = __ldg(&a.graphs[graph].t0);
                 const int tile = gt0 + (i - gv0) / kBlockT;
-                const int32_t* tp = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
-                g0 = ((m >> lane) & 1ull) ? -1 : __ldg(tp + lane);
-                g1 = ((m >> (lane + 32)) & 1ull) ? -1 : __ldg(tp + lane + 32);
-                k_acc = kBlockP - __popcll(m);
+                tp = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
+                k_acc = kBlockP - __popcll(bmask_v);
             } else {
-                const int32_t* samples = a.samples + ((size_t)(epoch & 1) * (size_t)a.rows + i) * a.k;
-                if (lane < a.k) g0 = __ldg(samples + lane);
-                k_acc = __popc(__ballot_sync(kFull, g0 >= 0));
+                sp = a.samples + ((size_t)(epoch & 1) * (size_t)a.rows + i) * a.k;
+                for (int t = gl; t < a.k; t += G) k_acc += (__ldg(sp + t) >= 0);
             }
-            if (lane == 0 && k_acc) {
-                if (graph == hist.home) atomicAdd(&s_used, (unsigned)k_acc);
+        }
+        // group sum of the per-vertex count: every lane of the warp takes part
+        // (groups without samples add zeros); the block form's count is
+        // already complete in every lane of its group
+        if (!block) {
+#pragma unroll
+            for (int o = G / 2; o >= 1; o >>= 1) k_acc += __shfl_xor_sync(kFull, k_acc, o);
+        }
+        __syncwarp();
+        if (has_samples && gl == 0) {
+            if (block) a.block_mask[(size_t)(epoch & 1) * (size_t)a.rows + i] = 0ull;   // read once
+            if (k_acc) {
+                if (graph == home) atomicAdd(&s_used, (unsigned)k_acc);
                 else atomicAdd(&a.gst[graph].used, (unsigned long long)k_acc);
             }
         }
-
-        const int ne = p1 - p0;
         const int total = ne + (has_samples ? k_eff : 0);
+        const int rounds = (total + G - 1) / G;
+        const int rmax = (int)__reduce_max_sync(kFull, (unsigned)rounds);
+
         float dacc[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) dacc[c] = 0.0f;
         float zacc = 0.0f;
-        // Macro-rounds of 32 pairs: (A) G sub-rounds of PAIRS pairs gather the
-        // squared distances, lane grp*G + s keeping sub-round s's pair; (B) each
-        // lane evaluates the pair term of its own pair (one math pass per 32
-        // pairs); (C) the terms go back to the groups for the vector sums.
-        for (int base = 0; base < total; base += 32) {
-            const int left = total - base;
-            const int nsub = min(G, (left + PAIRS - 1) / PAIRS);
+        for (int r = 0; r < rmax; ++r) {
+            // this lane's pair of the round
+            const int q = r * G + gl;
+            int my_j = -1;
+            if (q < ne) {
+                my_j = __ldg(a.col_idx + e0 + p0 + q);
+            } else if (q < total) {
+                const int t = q - ne;
+                if (block) my_j = ((bmask_v >> t) & 1ull) ? -1 : __ldg(tp + t);
+                else my_j = __ldg(sp + t);
+            }
+            // (A) distances
             float my_ss = 0.0f;
-            int my_j = -1, my_edge = 0;
-            for (int sr = 0; sr < nsub; ++sr) {
-                const int q = base + PAIRS * sr + grp;
-                const bool active = q < total;
-                const bool is_edge = q < ne;
-                const int sidx = q - ne;
-                const int s0 = __shfl_sync(kFull, g0, sidx & 31);
-                const int s1 = __shfl_sync(kFull, g1, sidx & 31);
-                int j = -1;
-                if (active) j = is_edge ? __ldg(a.col_idx + e0 + p0 + q) : (sidx < 32 ? s0 : s1);
-                const bool valid = active && j >= 0;
+#pragma unroll
+            for (int s2 = 0; s2 < G; ++s2) {
+                const int j = __shfl_sync(kFull, my_j, gbase + s2);
                 float xj[P];
-                if (valid) {
+                if (j >= 0) {
                     load_chunk<D, P>(X, j, gl, xj);
                 } else {
 #pragma unroll
@@ -551,17 +593,15 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 }
 #pragma unroll
                 for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
-                if (gl == sr) {
-                    my_ss = ss;
-                    my_j = valid ? j : -1;
-                    my_edge = is_edge ? 1 : 0;
-                }
+                if (gl == s2) my_ss = ss;
             }
+            // (B) the pair term of this lane's pair
+            const bool my_edge = q < ne;
             float my_c = 0.0f, my_w = 0.0f;
             if (my_j >= 0) {
                 float delta, inv_delta;
                 dist_of(my_ss, delta, inv_delta);
-                const PairTerm t = pair_term(delta, inv_delta, my_edge != 0, K);
+                const PairTerm t = pair_term(delta, inv_delta, my_edge, K);
                 my_c = t.c;
                 my_w = t.w;
                 zacc += t.w;
@@ -572,12 +612,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                     hist_sample(hist, a, graph, bin, deg, k_acc, k_eff);
                 }
             }
-            for (int sr = 0; sr < nsub; ++sr) {
-                const int src = grp * G + sr;
-                const int j = __shfl_sync(kFull, my_j, src);
-                const float c = __shfl_sync(kFull, my_c, src);
-                const float wv = __shfl_sync(kFull, my_w, src);
-                const int e = __shfl_sync(kFull, my_edge, src);
+            // (C) the vertex's sum and the sampled partners' terms
+#pragma unroll
+            for (int s2 = 0; s2 < G; ++s2) {
+                const int j = __shfl_sync(kFull, my_j, gbase + s2);
+                const float c = __shfl_sync(kFull, my_c, gbase + s2);
+                const float wv = __shfl_sync(kFull, my_w, gbase + s2);
                 if (j >= 0) {
                     float xj[P];
                     load_chunk<D, P>(X, j, gl, xj);
@@ -587,7 +627,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                         diff[cc] = xi[cc] - xj[cc];
                         dacc[cc] = fmaf(c, diff[cc], dacc[cc]);
                     }
-                    if (!e && a.symmetric) {
+                    if (r * G + s2 >= ne && a.symmetric) {
                         float pv[P];
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) pv[cc] = -c * diff[cc];
@@ -596,18 +636,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 }
             }
         }
-        // per-vertex reduction: coordinates over lanes with equal gl, z over all
+        // z over the group; each lane adds its own coordinates of the sum
 #pragma unroll
-        for (int o = 16; o >= G; o >>= 1)
-#pragma unroll
-            for (int c = 0; c < P; ++c) dacc[c] += __shfl_xor_sync(kFull, dacc[c], o);
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) zacc += __shfl_xor_sync(kFull, zacc, o);
-        if (lane < G) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
+        for (int o = G / 2; o >= 1; o >>= 1) zacc += __shfl_xor_sync(kFull, zacc, o);
+        if (total > 0) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
     __syncthreads();
     hist_merge(hist, a);
-    if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
+    if (threadIdx.x == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,6 +131,25 @@ void chunk_units(const int32_t* rp, int32_t v0, int32_t n, int chunk, int32_t g,
     }
 }
 
+// Warp tasks of the d >= 8 sweep: groups of `pg` units (one per lane group)
+// of similar size, so that the groups of a warp run the same number of
+// rounds.  Within windows of 16 * pg consecutive units the units are sorted
+// by their pair count, then cut into consecutive tasks; the list is padded to
+// a multiple of pg with empty units (vertex -1).
+void wide_tasks(std::vector<int4>& units, int pg, int k_slots) {
+    if (pg <= 1) return;
+    auto pairs = [&](const int4& u) {
+        return (u.w & ~kUnitHasSamples) - u.z + ((u.w & kUnitHasSamples) ? k_slots : 0);
+    };
+    const size_t window = 16 * (size_t)pg;
+    for (size_t w0 = 0; w0 < units.size(); w0 += window) {
+        const size_t w1 = std::min(units.size(), w0 + window);
+        std::stable_sort(units.begin() + w0, units.begin() + w1,
+                         [&](const int4& x, const int4& y) { return pairs(x) > pairs(y); });
+    }
+    while (units.size() % pg) units.push_back(make_int4(-1, 0, 0, 0));
+}
+
 unsigned long long table_slots(int64_t nnz) {
     unsigned long long s = 16;
     while (s < 2ull * (unsigned long long)nnz) s <<= 1;
@@ -387,6 +406,10 @@ gempe_status Pack::set_shape(const PackShape& s) {
         const GraphInfo& gi = info[g];
         if (d <= kPackedMaxDim) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
         else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, units);
+    }
+    if (d > kPackedMaxDim) {
+        const int lanes = sh.lanes ? sh.lanes : d / 8;
+        wide_tasks(units, 32 / lanes, (tiles ? 0 : slots_per_vertex()));
     }
     if (items && (size_t)n_items < units.size()) {
         release(items);
