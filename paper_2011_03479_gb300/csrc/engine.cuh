@@ -107,6 +107,7 @@ struct EpochArgs {
     // work lists
     const int4* items;        // sweep units
     int32_t n_items;
+    const int32_t* task_bounds;   // d >= 8: first task of each sweep block (grid + 1 entries)
     int32_t blocked;          // 1: block b takes a contiguous range of units (packs of several graphs)
     const int4* vchunks;      // {row begin, count <= kVChunk, graph, 0}
     int32_t n_vchunks;

@@ -472,26 +472,20 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int PG = 32 / G;            // groups (units) per warp task
     const PT* X = pos_of<PT>(a);
     extern __shared__ unsigned int s_u32[];
-    const int n_tasks = a.n_items / PG;
-    // tasks of this warp: a contiguous range per block in packs of several graphs
-    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    int t_begin, t_end, t_step, home;
-    if (a.blocked) {
-        const int lo = (int)((long long)n_tasks * blockIdx.x / gridDim.x);
-        t_begin = lo + wib;
-        t_end = (int)((long long)n_tasks * (blockIdx.x + 1) / gridDim.x);
-        t_step = wpb;
-        home = lo < t_end ? (__ldg(&a.items[(size_t)lo * PG].y) >> kGraphShift) : -1;
-    } else {
-        t_begin = blockIdx.x * wpb + wib;
-        t_end = n_tasks;
-        t_step = gridDim.x * wpb;
-        home = a.n_graphs == 1 ? 0 : -1;
-    }
+    // block b takes the tasks [bounds[b], bounds[b+1]) (ranges of equal
+    // estimated work, cut on the host) and hands them to its warps one at a
+    // time (a shared counter), so that its warps finish together
+    const int t_lo = __ldg(a.task_bounds + blockIdx.x);
+    const int t_end = __ldg(a.task_bounds + blockIdx.x + 1);
+    const int home = (a.n_graphs == 1) ? 0 : (t_lo < t_end ? (__ldg(&a.items[(size_t)t_lo * PG].y) >> kGraphShift) : -1);
     const BlockHist hist = block_hist(s_u32, a.bins, home);
     __shared__ unsigned int s_used;
+    __shared__ int s_next;
     hist_clear(hist, a.bins);
-    if (threadIdx.x == 0) s_used = 0u;
+    if (threadIdx.x == 0) {
+        s_used = 0u;
+        s_next = t_lo;
+    }
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -500,7 +494,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     const bool block = a.block_P > 0;
     const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex
 
-    for (int task = t_begin; task < t_end; task += t_step) {
+    for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(&s_next, 1);
+        task = __shfl_sync(kFull, task, 0);
+        if (task >= t_end) break;
         const int4 item = __ldg(a.items + (size_t)task * PG + lane / G);
         const int i = item.x;                              // -1: padding
         const int graph = item.y >> kGraphShift;

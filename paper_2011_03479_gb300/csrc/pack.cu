@@ -392,7 +392,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     if (p.precision == 1 && d >= 8) b += al(2 * R * d);
     b += al(bins * 20) + al(sizeof(GraphInfo)) + al(sizeof(GraphState)) + al(sizeof(PackState)) + al(4);
     b += al(16 * (((size_t)n + kVChunk - 1) / kVChunk)) + al(4 * R * std::max<size_t>(k, 1));
-    b += al(4 * std::max<size_t>(blk ? 1 : 2 * R * k, 1)) + al(16 * units_max);
+    b += al(4 * std::max<size_t>(blk ? 1 : 2 * R * k, 1)) + al(16 * units_max) + al(4 * 4097);
     if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
     return b;
 }
@@ -407,9 +407,35 @@ gempe_status Pack::set_shape(const PackShape& s) {
         if (d <= kPackedMaxDim) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
         else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, units);
     }
+    const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm);
+    std::vector<int32_t> bounds;
     if (d > kPackedMaxDim) {
         const int lanes = sh.lanes ? sh.lanes : d / 8;
-        wide_tasks(units, 32 / lanes, (tiles ? 0 : slots_per_vertex()));
+        const int pg = 32 / lanes;
+        const int k_slots = tiles ? 0 : slots_per_vertex();
+        wide_tasks(units, pg, k_slots);
+        // per-block task ranges of equal estimated work: a task costs its
+        // longest unit's rounds plus a fixed set-up
+        const size_t n_tasks = units.size() / pg;
+        std::vector<double> cum(n_tasks + 1, 0.0);
+        for (size_t t = 0; t < n_tasks; ++t) {
+            int rounds = 0;
+            for (int g2 = 0; g2 < pg; ++g2) {
+                const int4& u = units[t * pg + g2];
+                if (u.x < 0) continue;
+                const int pairs = (u.w & ~kUnitHasSamples) - u.z + ((u.w & kUnitHasSamples) ? k_slots : 0);
+                rounds = std::max(rounds, (pairs + lanes - 1) / lanes);
+            }
+            cum[t + 1] = cum[t] + rounds + 1.0;
+        }
+        bounds.assign(grid + 1, 0);
+        size_t t = 0;
+        for (int b = 1; b < grid; ++b) {
+            const double target = cum[n_tasks] * b / grid;
+            while (t < n_tasks && cum[t + 1] <= target) ++t;
+            bounds[b] = (int32_t)t;
+        }
+        bounds[grid] = (int32_t)n_tasks;
     }
     if (items && (size_t)n_items < units.size()) {
         release(items);
@@ -423,8 +449,22 @@ gempe_status Pack::set_shape(const PackShape& s) {
     if (!units.empty())
         PK(cudaMemcpyAsync(items, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, stream),
            "copy work units");
+    if (!bounds.empty()) {
+        if (task_bounds && task_bounds_cap < (int32_t)bounds.size()) {
+            release(task_bounds);
+            task_bounds = nullptr;
+        }
+        if (!task_bounds) {
+            task_bounds = (int32_t*)alloc(sizeof(int32_t) * bounds.size());
+            if (!task_bounds) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+            task_bounds_cap = (int32_t)bounds.size();
+        }
+        PK(cudaMemcpyAsync(task_bounds, bounds.data(), sizeof(int32_t) * bounds.size(), cudaMemcpyHostToDevice,
+                           stream),
+           "copy task ranges");
+    }
     PK(cudaStreamSynchronize(stream), "copy work units");
-    sweep_grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm);
+    sweep_grid = grid;
     shape = sh;
     return GEMPE_OK;
 }
@@ -449,6 +489,7 @@ EpochArgs Pack::args() const {
     a.hist_x = hist_x;
     a.items = items;
     a.n_items = n_items;
+    a.task_bounds = task_bounds;
     a.blocked = G > 1 ? 1 : 0;
     a.vchunks = vchunks;
     a.n_vchunks = n_vchunks;

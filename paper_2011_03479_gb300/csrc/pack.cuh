@@ -73,6 +73,8 @@ struct Pack {
     float* hist_x = nullptr;
     int4* items = nullptr;
     int32_t n_items = 0;
+    int32_t* task_bounds = nullptr;  // d >= 8: sweep block b takes tasks [bounds[b], bounds[b+1])
+    int32_t task_bounds_cap = 0;
     int4* vchunks = nullptr;
     int32_t n_vchunks = 0;
     int32_t* samples = nullptr;      // [2][rows][k]
