@@ -202,6 +202,16 @@ gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float 
 
 gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
 
+/* Launch shape of the context's pair sweep (what the autotuner chooses):
+ * shape5 = {unit pair budget of a packed unit (64 or 128, d <= 4), CSR
+ * slots per work unit (8..1024, the per-unit kernel), lanes per pair (d >= 8:
+ * d/8 or d/4; 0 = default), sweep CTAs per SM (0 = all that fit), kernel
+ * (d <= 4: 0 packed units, 1 one lane per vertex)}.  Only the launch shape
+ * changes, never the arithmetic of a pair; not allowed between gempe_sweep
+ * and gempe_update.  gempe_get_shape: the same five, then the sweep grid. */
+gempe_status gempe_set_shape(gempe_ctx* ctx, const int32_t* shape5);
+gempe_status gempe_get_shape(gempe_ctx* ctx, int32_t* out6);
+
 /* ------------------------------------------------------------------------
  * Batched form: many independent graphs stepped together.
  *

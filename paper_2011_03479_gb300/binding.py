@@ -149,6 +149,8 @@ def load(build: bool = True):
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
+        "gempe_set_shape": (st, [vp, P(i32)]),
+        "gempe_get_shape": (st, [vp, P(i32)]),
         "gempe_last_error": (ctypes.c_char_p, []),
         "gempe_batch_create": (st, [i32, P(gempe_graph_desc), P(gempe_params), vp, P(vp)]),
         "gempe_batch_destroy": (None, [vp]),
@@ -529,6 +531,19 @@ def gempe_server_stats(s: _Server) -> dict:
     _check(load().gempe_server_stats(s.handle, out))
     return {"queued": out[0], "running": out[1], "completed": out[2], "failed": out[3], "bytes_in_use": out[4],
             "peak_bytes_in_use": out[5]}
+
+
+def gempe_set_shape(ctx: _Ctx, unit_pairs: int = 128, edge_chunk: int = 64, lanes: int = 0, blocks_per_sm: int = 0,
+                    kernel: int = 0) -> None:
+    arr = (ctypes.c_int32 * 5)(unit_pairs, edge_chunk, lanes, blocks_per_sm, kernel)
+    _check(load().gempe_set_shape(ctx.handle, arr))
+
+
+def gempe_get_shape(ctx: _Ctx) -> dict:
+    out = (ctypes.c_int32 * 6)()
+    _check(load().gempe_get_shape(ctx.handle, out))
+    return {"unit_pairs": out[0], "edge_chunk": out[1], "lanes": out[2], "blocks_per_sm": out[3], "kernel": out[4],
+            "grid": out[5]}
 
 
 def gempe_last_error() -> str:

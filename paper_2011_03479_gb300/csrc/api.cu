@@ -413,6 +413,38 @@ GEMPE_API gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, flo
     return GEMPE_OK;
 }
 
+GEMPE_API gempe_status gempe_set_shape(gempe_ctx* c, const int32_t* shape5) {
+    if (!c || !shape5) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    if (c->pk->swept) return fail(GEMPE_E_INVALID_ARG, "gempe_set_shape after gempe_sweep: call gempe_update first");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    PackShape sh;
+    sh.unit_pairs = shape5[0];
+    sh.edge_chunk = shape5[1];
+    sh.lanes = shape5[2];
+    sh.blocks_per_sm = shape5[3];
+    sh.kernel = shape5[4];
+    gempe_status s = c->pk->set_shape(sh);
+    if (s != GEMPE_OK) return s;
+    // the captured epoch holds the old work list and grid
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_get_shape(gempe_ctx* c, int32_t* out6) {
+    if (!c || !out6) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    const PackShape& sh = c->pk->shape;
+    out6[0] = sh.unit_pairs;
+    out6[1] = sh.edge_chunk;
+    out6[2] = sh.lanes ? sh.lanes : (c->pk->d <= kPackedMaxDim ? 1 : c->pk->d / 8);
+    out6[3] = sh.blocks_per_sm;
+    out6[4] = sh.kernel;
+    out6[5] = c->pk->sweep_grid;
+    return GEMPE_OK;
+}
+
 GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
     if (!c || !out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     gempe_status rc;

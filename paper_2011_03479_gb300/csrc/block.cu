@@ -202,6 +202,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 // Shared-memory layout of k_tile_bf16 (rows padded by 8 BF16 so that the
 // eight 16-byte rows an ldmatrix reads fall into distinct banks).
@@ -209,19 +211,51 @@ template <int D>
 struct TileSmem {
     static constexpr int kXS = D + 8;          // row stride (elements) of X_T, X_P
     static constexpr int kCS = kBlockP + 8;    // row stride of C
-    __nv_bfloat16 xt[kBlockT * kXS];
-    __nv_bfloat16 xp[kBlockP * kXS];
+    __nv_bfloat16 xt[2][kBlockT * kXS];   // double buffer: the next tile's rows load during this one
+    __nv_bfloat16 xp[2][kBlockP * kXS];
     __nv_bfloat16 cs[kBlockT * kCS];
     float nt[kBlockT], np[kBlockP];
     float row_c[kBlockT], row_w[kBlockT];
     float col_c[8][kBlockP], col_w[8][kBlockP];
     unsigned long long mask[kBlockT];
     int deg[kBlockT], kacc[kBlockT];
-    int part[kBlockP];
+    int part[2][kBlockP];
 };
 
+// Start the asynchronous loads of tile item `it` (if below `end`) into
+// buffer b: its partner list, X_T (zero rows past the graph's end) and X_P;
+// always commits one cp.async group.
+template <int D>
+__device__ __forceinline__ void stage_tile(const EpochArgs& a, TileSmem<D>& sm, int it, int end, int b) {
+    constexpr int XS = TileSmem<D>::kXS;
+    constexpr int CH = D / 8;   // 16-byte chunks per row
+    if (it < end) {
+        const int2 ti = __ldg(a.tile_items + it);
+        const int tile = ti.x, graph = ti.y;
+        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
+        const int lt = tile - __ldg(&a.graphs[graph].t0);
+        const int v0 = gv0 + lt * kBlockT;
+        const int nv = min(kBlockT, gn - lt * kBlockT);
+        const int epoch = a.gst[graph].epoch;
+        const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
+        if (threadIdx.x < kBlockP) sm.part[b][threadIdx.x] = __ldg(part + threadIdx.x);
+        for (int c = threadIdx.x; c < kBlockT * CH; c += blockDim.x) {
+            const int r = c / CH, q = c - r * CH;
+            __nv_bfloat16* dst = sm.xt[b] + r * XS + q * 8;
+            if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + q * 8);
+            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        for (int c = threadIdx.x; c < kBlockP * CH; c += blockDim.x) {
+            const int r = c / CH, q = c - r * CH;
+            cp_async16(sm.xp[b] + r * XS + q * 8, a.xb + (size_t)__ldg(part + r) * D + q * 8);
+        }
+    }
+    cp_async_commit();
+}
+
 // ---------------------------------------------------------------------------
-// k_tile_bf16: block-sampled non-edges of one tile per CTA iteration.
+// k_tile_bf16: block-sampled non-edges of one tile per CTA iteration; the
+// next tile's rows are staged (cp.async) while the current one computes.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
@@ -259,7 +293,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = lane >> 2, t4 = lane & 3;
 
-    for (int it = it0; it < it1; it += istep) {
+    stage_tile<D>(a, sm, it0, it1, 0);
+    int buf = 0;
+    for (int it = it0; it < it1; it += istep, buf ^= 1) {
         const int2 ti = __ldg(a.tile_items + it);
         const int tile = ti.x, graph = ti.y;
         const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
@@ -269,11 +305,13 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
-        const int32_t* part = a.block_part + (size_t)(epoch & 1) * (size_t)a.n_tiles * kBlockP;
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
-        __syncthreads();   // the previous tile's shared data is no longer read
-        // ---- stage partners, masks, degrees, X_T and X_P ----
-        if (threadIdx.x < kBlockP) sm.part[threadIdx.x] = __ldg(part + (size_t)tile * kBlockP + threadIdx.x);
+        __syncthreads();   // the previous tile's shared data (and buffer buf ^ 1) is no longer read
+        stage_tile<D>(a, sm, it + istep, it1, buf ^ 1);
+        const __nv_bfloat16* xt = sm.xt[buf];
+        const __nv_bfloat16* xp = sm.xp[buf];
+        const int* prt = sm.part[buf];
+        // ---- masks and degrees (X_T, X_P and the partners were staged one tile ahead) ----
         for (int v = threadIdx.x; v < kBlockT; v += blockDim.x) {
             if (v < nv) {
                 const unsigned long long m = bmask[v0 + v];
@@ -288,19 +326,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                 sm.kacc[v] = 0;
             }
         }
-        __syncthreads();
-        constexpr int CH = D / 8;   // 16-byte chunks per row
-        for (int c = threadIdx.x; c < kBlockT * CH; c += blockDim.x) {
-            const int r = c / CH, q = c - r * CH;
-            __nv_bfloat16* dst = sm.xt + r * XS + q * 8;
-            if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + q * 8);
-            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        for (int c = threadIdx.x; c < kBlockP * CH; c += blockDim.x) {
-            const int r = c / CH, q = c - r * CH;
-            cp_async16(sm.xp + r * XS + q * 8, a.xb + (size_t)sm.part[r] * D + q * 8);
-        }
-        cp_async_wait_all();
+        cp_async_wait_prev();   // this tile's group has landed (the next one may still be loading)
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_tile_used) {
@@ -310,7 +336,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
             s_tile_used = 0u;
         }
         for (int r = threadIdx.x; r < kBlockT + kBlockP; r += blockDim.x) {
-            const __nv_bfloat16* row = (r < kBlockT) ? sm.xt + r * XS : sm.xp + (r - kBlockT) * XS;
+            const __nv_bfloat16* row = (r < kBlockT) ? xt + r * XS : xp + (r - kBlockT) * XS;
             float s = 0.0f;
 #pragma unroll 8
             for (int c = 0; c < D; ++c) {
@@ -333,13 +359,13 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
             uint32_t af[4];
             {
                 const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4(af, sm.xt + (r0 + rr + 8 * (mat & 1)) * XS + 16 * ks + 8 * (mat >> 1));
+                ldsm_x4(af, xt + (r0 + rr + 8 * (mat & 1)) * XS + 16 * ks + 8 * (mat >> 1));
             }
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
                 uint32_t bf[4];
                 const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4(bf, sm.xp + (8 * (j + (mat >> 1)) + rr) * XS + 16 * ks + 8 * (mat & 1));
+                ldsm_x4(bf, xp + (8 * (j + (mat >> 1)) + rr) * XS + 16 * ks + 8 * (mat & 1));
                 mma_16816(S[j], af, bf[0], bf[1]);
                 mma_16816(S[j + 1], af, bf[2], bf[3]);
             }
@@ -418,7 +444,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
             for (int kk = 0; kk < 4; ++kk) {
                 uint32_t bf[4];
                 const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4_t(bf, sm.xp + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (jd + (mat >> 1)));
+                ldsm_x4_t(bf, xp + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (jd + (mat >> 1)));
                 mma_16816(A0, Af[kk], bf[0], bf[1]);
                 mma_16816(A1, Af[kk], bf[2], bf[3]);
             }
@@ -431,8 +457,8 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                     const int il = r0 + g + 8 * h;
                     if (il < nv && sm.kacc[il] > 0) {
                         const float s = sm.row_c[il];
-                        const float v0f = bf16_at(sm.xt + il * XS + dim) * s - Ar[2 * h];
-                        const float v1f = bf16_at(sm.xt + il * XS + dim + 1) * s - Ar[2 * h + 1];
+                        const float v0f = bf16_at(xt + il * XS + dim) * s - Ar[2 * h];
+                        const float v1f = bf16_at(xt + il * XS + dim + 1) * s - Ar[2 * h + 1];
                         atomicAdd(reinterpret_cast<float2*>(a.acc + (size_t)(v0 + il) * a.acc_stride + dim),
                                   make_float2(v0f, v1f));
                     }
@@ -469,7 +495,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                 for (int j = 0; j < NW; j += 2) {
                     uint32_t bf[4];
                     const int mat = lane >> 3, rr = lane & 7;
-                    ldsm_x4_t(bf, sm.xt + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (nbase + j + (mat >> 1)));
+                    ldsm_x4_t(bf, xt + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (nbase + j + (mat >> 1)));
                     mma_16816(Bacc[j], af, bf[0], bf[1]);
                     if (j + 1 < NW) mma_16816(Bacc[j + 1], af, bf[2], bf[3]);
                 }
@@ -484,18 +510,19 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                     wsum += sm.col_w[q][p];
                 }
                 if (wsum == 0.0f && csum == 0.0f) continue;   // every pair of this partner masked or underflowed
-                const int gv = sm.part[p];
+                const int gv = prt[p];
 #pragma unroll
                 for (int j = 0; j < NW; ++j) {
                     const int dim = 8 * (nbase + j) + 2 * t4;
-                    const float v0f = bf16_at(sm.xp + p * XS + dim) * csum - Bacc[j][2 * h];
-                    const float v1f = bf16_at(sm.xp + p * XS + dim + 1) * csum - Bacc[j][2 * h + 1];
+                    const float v0f = bf16_at(xp + p * XS + dim) * csum - Bacc[j][2 * h];
+                    const float v1f = bf16_at(xp + p * XS + dim + 1) * csum - Bacc[j][2 * h + 1];
                     atomicAdd(reinterpret_cast<float2*>(a.acc + (size_t)gv * a.acc_stride + dim), make_float2(v0f, v1f));
                 }
                 if (t4 == 0 && (w & 1) == 0) atomicAdd(a.acc + (size_t)gv * a.acc_stride + D, wsum);
             }
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     hist_merge(hist, a);
     if (threadIdx.x == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);

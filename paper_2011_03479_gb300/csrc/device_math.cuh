@@ -132,12 +132,16 @@ __device__ __forceinline__ float mills_tail_T(float v) {
 // h(v) = phi(v)/Q(v) and T(v) = h(v) - v > 0.  On the table range both come
 // from the interpolated logarithms; from kMillsV1 on, T by the continued
 // fraction and h = v + T; below kMillsV0, h is below the FP32 range (h = 0).
-__device__ __forceinline__ void mills(float v, float& h, float& T, const MillsCoef* tab) {
+// kGlobal: the table is in global memory (read through the read-only
+// cache); otherwise it is a copy in shared memory.
+template <bool kGlobal>
+__device__ __forceinline__ void mills_t(float v, float& h, float& T, const MillsCoef* tab) {
     if (v < kMillsV1) {
         const float pos = (fmaxf(v, kMillsV0) - kMillsV0) * (float)kMillsStepsPerUnit;
         const int i = min((int)pos, kMillsIntervals - 1);
         const float x = pos - (float)i;
-        const float4 a = __ldg(&tab[i].lh), b = __ldg(&tab[i].lt);
+        const float4 a = kGlobal ? __ldg(&tab[i].lh) : tab[i].lh;
+        const float4 b = kGlobal ? __ldg(&tab[i].lt) : tab[i].lt;
         const float lh = fmaf(fmaf(fmaf(a.w, x, a.z), x, a.y), x, a.x);
         const float lt = fmaf(fmaf(fmaf(b.w, x, b.z), x, b.y), x, b.x);
         h = (v < kMillsV0) ? 0.0f : exp2f(lh);
@@ -146,6 +150,10 @@ __device__ __forceinline__ void mills(float v, float& h, float& T, const MillsCo
         T = mills_tail_T(v);
         h = v + T;
     }
+}
+
+__device__ __forceinline__ void mills(float v, float& h, float& T, const MillsCoef* tab) {
+    mills_t<true>(v, h, T, tab);
 }
 
 struct PairTerm {

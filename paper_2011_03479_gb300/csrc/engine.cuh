@@ -141,11 +141,13 @@ cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_
 struct SweepShape {
     int grid = 0;
     int lanes = 0;      // d >= 8: lanes per pair (0: d / 8)
+    int kernel = 0;     // d <= 4: 0 packed units, 1 one lane per vertex (the d >= 8 kernel with G = 1)
 };
 cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream_t s);
-int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm);
+int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int kernel);
 bool sweep_lanes_supported(int d, int lanes);
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s);
+cudaError_t prepare_update_kernels(int bins);   // shared-memory size of the slope-fit blocks
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,

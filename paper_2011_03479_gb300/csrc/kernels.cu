@@ -666,12 +666,14 @@ struct SigmaSmem {
     int iters;
 };
 
-// F and F' terms of one bin at 1/sigma = inv_s (F without the positive factor).
-__device__ __forceinline__ float2 dpe_bin(float ce, float cn, float centre, float mu, float inv_s) {
+// F and F' terms of one bin at 1/sigma = inv_s (F without the positive
+// factor); tab: the Mills-ratio table copied to shared memory.
+__device__ __forceinline__ float2 dpe_bin(float ce, float cn, float centre, float mu, float inv_s,
+                                          const MillsCoef* tab) {
     const float u = (centre - mu) * inv_s;
     float h, T, g, Tn;
-    mills(u, h, T, g_mills);     // edge side: h(u), T(u)
-    mills(-u, g, Tn, g_mills);   // non-edge side: g(u) = h(-u), T(-u) = g + u
+    mills_t<false>(u, h, T, tab);     // edge side: h(u), T(u)
+    mills_t<false>(-u, g, Tn, tab);   // non-edge side: g(u) = h(-u), T(-u) = g + u
     const float uh = u * h, ug = u * g;
     return make_float2(fmaf(ce, -uh, cn * ug),
                        fmaf(ce * uh, fmaf(u, T, 1.0f), -cn * ug * fmaf(-u, Tn, 1.0f)));
@@ -718,11 +720,12 @@ __device__ __forceinline__ void newton_update(float f, float df, bool lo_pos, fl
     sm.inv_s = expf(-t);
 }
 
-// Returns the new sigma (valid in every thread).  he/hn: shared-memory bins.
-// The first pass evaluates F at both bracket ends (sigma = 1e-3, 1e3) and
-// (F, F') at the previous sigma together.
+// Returns the new sigma (valid in every thread).  he/hn: shared-memory bins;
+// tab: the Mills-ratio table in shared memory.  Empty bins contribute
+// nothing and are skipped.  The first pass evaluates F at both bracket ends
+// (sigma = 1e-3, 1e3) and (F, F') at the previous sigma together.
 __device__ float block_fit_sigma(const float* he, const float* hn, int bins, float hist_max, float mu,
-                                 float sigma_prev, SigmaSmem& sm) {
+                                 float sigma_prev, const MillsCoef* tab, SigmaSmem& sm) {
     const float bin_w = hist_max / (float)bins;
     const bool lead = threadIdx.x == 0;
     float lo = -6.9077553f, hi = 6.9077553f;   // ln 1e-3, ln 1e3
@@ -732,9 +735,10 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int b = threadIdx.x; b < bins; b += blockDim.x) {
         const float ce = he[b], cn = hn[b], c = ((float)b + 0.5f) * bin_w;
-        acc.x += dpe_bin(ce, cn, c, mu, 1e3f).x;     // sigma = 1e-3
-        acc.y += dpe_bin(ce, cn, c, mu, 1e-3f).x;    // sigma = 1e3
-        const float2 f0 = dpe_bin(ce, cn, c, mu, inv_s0);
+        if (ce == 0.0f && cn == 0.0f) continue;
+        acc.x += dpe_bin(ce, cn, c, mu, 1e3f, tab).x;     // sigma = 1e-3
+        acc.y += dpe_bin(ce, cn, c, mu, 1e-3f, tab).x;    // sigma = 1e3
+        const float2 f0 = dpe_bin(ce, cn, c, mu, inv_s0, tab);
         acc.z += f0.x;
         acc.w += f0.y;
     }
@@ -756,7 +760,8 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
         const float inv_s = sm.inv_s;
         float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-            const float2 fd = dpe_bin(he[b], hn[b], ((float)b + 0.5f) * bin_w, mu, inv_s);
+            if (he[b] == 0.0f && hn[b] == 0.0f) continue;
+            const float2 fd = dpe_bin(he[b], hn[b], ((float)b + 0.5f) * bin_w, mu, inv_s, tab);
             p.x += fd.x;
             p.y += fd.y;
         }
@@ -765,6 +770,18 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
         __syncthreads();
     }
     return 1.0f / sm.inv_s;
+}
+
+// Copy the Mills-ratio table into shared memory (all threads of the block).
+__device__ __forceinline__ void load_mills_smem(MillsCoef* dst) {
+    const float4* src = reinterpret_cast<const float4*>(g_mills);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int q = threadIdx.x; q < 2 * kMillsIntervals; q += blockDim.x) d4[q] = __ldg(src + q);
+}
+
+// Shared memory of the slope-fit blocks: [2][bins] floats, then the table.
+__host__ __device__ inline size_t fit_smem_bytes(int bins) {
+    return ((2 * (size_t)bins * sizeof(float) + 15) / 16) * 16 + sizeof(MillsCoef) * kMillsIntervals;
 }
 
 // Load one graph's histograms into shared memory as floats: edge counts, and
@@ -784,15 +801,19 @@ __device__ void load_hist_smem(const EpochArgs& a, size_t off, int n, int k_slot
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
     if ((int)blockIdx.x < a.n_active) {
         __shared__ SigmaSmem sm;
-        extern __shared__ float s_bins[];   // [2][bins]
+        extern __shared__ __align__(16) float s_bins[];   // [2][bins], then the Mills table
+        MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
+                                                        ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
         const int graph = a.active[blockIdx.x];
         GraphState* st = a.gst + graph;
         const size_t off = (size_t)graph * a.bins;
         const int epoch = st->epoch;
         if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0) {
             const int k_slots = a.block_P > 0 ? kBlockP : a.k;
+            load_mills_smem(s_tab);
             load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);
-            const float s = block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, st->sigma, sm);
+            const float s =
+                block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, st->sigma, s_tab, sm);
             if (threadIdx.x == 0) {
                 st->sigma = s;
                 st->sigma_iters = sm.iters;
@@ -901,10 +922,13 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
 __global__ void __launch_bounds__(kUpdateThreads) k_fit_sigma(const float* hist, int bins, float hist_max, float mu,
                                                                float* sigma) {
     __shared__ SigmaSmem sm;
-    extern __shared__ float s_bins[];
+    extern __shared__ __align__(16) float s_bins[];
+    MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
+                                                    ((2 * (size_t)bins * sizeof(float) + 15) / 16) * 16);
+    load_mills_smem(s_tab);
     for (int b = threadIdx.x; b < 2 * bins; b += blockDim.x) s_bins[b] = hist[b];
     __syncthreads();
-    const float s = block_fit_sigma(s_bins, s_bins + bins, bins, hist_max, mu, 1.0f, sm);
+    const float s = block_fit_sigma(s_bins, s_bins + bins, bins, hist_max, mu, 1.0f, s_tab, sm);
     if (threadIdx.x == 0) *sigma = s;
 }
 
@@ -1026,6 +1050,8 @@ __global__ void k_is_edge(const unsigned long long* keys, unsigned long long buc
 // (8 or 4 coordinates per lane) for the autotuner, the first the default.
 // ---------------------------------------------------------------------------
 #define GEMPE_PACKED_DIMS(X) X(1) X(2) X(3) X(4)
+// d <= 4 also has the per-unit kernel with one lane per vertex (G = 1)
+#define GEMPE_LANE_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1)
 #define GEMPE_WIDE(X) X(8, 1) X(8, 2) X(16, 2) X(16, 4) X(32, 4) X(32, 8) X(64, 8) X(64, 16) X(128, 16) X(128, 32) X(256, 32)
 #define GEMPE_LOSS_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 1) X(16, 2) X(32, 4) X(64, 8) X(128, 16) X(256, 32)
 
@@ -1099,20 +1125,30 @@ bool sweep_lanes_supported(int d, int lanes) {
 // One resident wave (SM count x blocks per SM, at most what fits): the
 // sweep strides over its work units, so a second wave would only add
 // histogram merges.
-int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm) {
+int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int kernel) {
     int fit = 1;
     if (lanes == 0) lanes = d <= kPackedMaxDim ? 1 : d / 8;
-    switch (d) {
+    if (d <= kPackedMaxDim && kernel == 1) {
+        switch (d) {
+#define GEMPE_CASE(D, G) \
+    case D: fit = wide_blocks_per_sm<D, G>(bins); break;
+            GEMPE_LANE_DIMS(GEMPE_CASE)
+#undef GEMPE_CASE
+            default: break;
+        }
+    } else {
+        switch (d) {
 #define GEMPE_CASE(D) \
     case D: fit = packed_blocks_per_sm<D>(bins); break;
-        GEMPE_PACKED_DIMS(GEMPE_CASE)
+            GEMPE_PACKED_DIMS(GEMPE_CASE)
 #undef GEMPE_CASE
-        default:
+            default:
 #define GEMPE_CASE(D, G) \
     if (d == D && lanes == G) fit = wide_blocks_per_sm<D, G>(bins);
-            GEMPE_WIDE(GEMPE_CASE)
+                GEMPE_WIDE(GEMPE_CASE)
 #undef GEMPE_CASE
-            break;
+                break;
+        }
     }
     const int b = (blocks_per_sm > 0 && blocks_per_sm < fit) ? blocks_per_sm : fit;
     return sm_count * b;
@@ -1141,6 +1177,15 @@ cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_
 cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream_t s) {
     if (a.n_items == 0) return cudaSuccess;
     const int lanes = shape.lanes ? shape.lanes : (a.d <= kPackedMaxDim ? 1 : a.d / 8);
+    if (a.d <= kPackedMaxDim && shape.kernel == 1) {
+        switch (a.d) {
+#define GEMPE_CASE(D, G) \
+    case D: return wide_sweep<D, G>(a, shape.grid, s);
+            GEMPE_LANE_DIMS(GEMPE_CASE)
+#undef GEMPE_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.d) {
 #define GEMPE_CASE(D) \
     case D: return packed_sweep<D>(a, shape.grid, s);
@@ -1168,8 +1213,15 @@ cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s) {
     }
 }
 
+cudaError_t prepare_update_kernels(int bins) {
+    const int smem = (int)fit_smem_bytes(bins);
+    cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {
-    k_update<<<grid, kUpdateThreads, 2 * (size_t)a.bins * sizeof(float), s>>>(a);
+    k_update<<<grid, kUpdateThreads, fit_smem_bytes(a.bins), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1228,7 +1280,9 @@ cudaError_t upload_mills_table(const void* host_coefs, size_t bytes) {
 
 cudaError_t launch_fit_sigma(const float* hist, int32_t bins, float hist_max, float mu,
                              float* sigma_inout, cudaStream_t s) {
-    k_fit_sigma<<<1, kUpdateThreads, 2 * (size_t)bins * sizeof(float), s>>>(hist, bins, hist_max, mu, sigma_inout);
+    cudaError_t e = prepare_update_kernels(bins);
+    if (e != cudaSuccess) return e;
+    k_fit_sigma<<<1, kUpdateThreads, fit_smem_bytes(bins), s>>>(hist, bins, hist_max, mu, sigma_inout);
     return cudaGetLastError();
 }
 

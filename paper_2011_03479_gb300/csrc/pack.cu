@@ -263,6 +263,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     mills = mills_table_device();
     if (!mills) return pack_fail(GEMPE_E_CUDA, "Mills table address");
     if (tiles) PK(prepare_tile_kernel(d, bins), "tile kernel attributes");
+    PK(prepare_update_kernels(bins), "update kernel attributes");
 
     // host copies of the pack CSR
     row_ptr_h.assign((size_t)rows + 1, 0);
@@ -400,17 +401,23 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
 gempe_status Pack::set_shape(const PackShape& s) {
     PackShape sh = s;
     if (!sweep_lanes_supported(d, sh.lanes)) return pack_fail(GEMPE_E_INVALID_ARG, "unsupported lanes per pair");
+    if (sh.kernel != 0 && (sh.kernel != 1 || d > kPackedMaxDim))
+        return pack_fail(GEMPE_E_INVALID_ARG, "kernel 1 (one lane per vertex) is for d <= 4");
+    if (sh.unit_pairs != 64 && sh.unit_pairs != 128) return pack_fail(GEMPE_E_INVALID_ARG, "unit pairs: 64 or 128");
+    if (sh.edge_chunk < 8 || sh.edge_chunk > 1024) return pack_fail(GEMPE_E_INVALID_ARG, "edge chunk in [8, 1024]");
+    if (sh.blocks_per_sm < 0 || sh.blocks_per_sm > 8) return pack_fail(GEMPE_E_INVALID_ARG, "blocks per SM in [0, 8]");
     std::vector<int4> units;
     units.reserve((size_t)rows + (size_t)slots / 32 + 16);
+    const bool per_unit = d > kPackedMaxDim || sh.kernel == 1;   // the kernel with lane groups per unit
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
-        if (d <= kPackedMaxDim) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
+        if (!per_unit) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
         else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, units);
     }
-    const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm);
+    const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm, sh.kernel);
     std::vector<int32_t> bounds;
-    if (d > kPackedMaxDim) {
-        const int lanes = sh.lanes ? sh.lanes : d / 8;
+    if (per_unit) {
+        const int lanes = sh.lanes ? sh.lanes : (d <= kPackedMaxDim ? 1 : d / 8);
         const int pg = 32 / lanes;
         const int k_slots = tiles ? 0 : slots_per_vertex();
         wide_tasks(units, pg, k_slots);
@@ -548,6 +555,7 @@ gempe_status Pack::enqueue_sweep() {
     SweepShape ss;
     ss.grid = sweep_grid;
     ss.lanes = shape.lanes;
+    ss.kernel = shape.kernel;
     PK(launch_sweep(args(), ss, stream), "sweep");
     if (tiles) PK(launch_tile_bf16(args(), tile_grid, stream), "tiles");
     return GEMPE_OK;
@@ -618,6 +626,12 @@ gempe_status Pack::autotune() {
                 s.blocks_per_sm = bps;
                 cands.push_back(s);
             }
+        for (int chunk : {16, 32, 64}) {   // one lane per vertex
+            PackShape s;
+            s.kernel = 1;
+            s.edge_chunk = chunk;
+            cands.push_back(s);
+        }
     } else {
         for (int lanes : {d / 8, d / 4})
             for (int chunk : {32, 64, 128}) {
@@ -657,6 +671,7 @@ gempe_status Pack::autotune() {
             SweepShape ss;
             ss.grid = sweep_grid;
             ss.lanes = shape.lanes;
+            ss.kernel = shape.kernel;
             if (err == cudaSuccess) err = cudaEventRecord(e0, stream);
             if (err == cudaSuccess) err = launch_sweep(args(), ss, stream);
             if (err == cudaSuccess) err = cudaEventRecord(e1, stream);

@@ -26,6 +26,7 @@ struct PackShape {
     int edge_chunk = kEdgeChunk;   // d >= 8: CSR slots per work unit (32, 64, 128)
     int lanes = 0;                 // d >= 8: lanes per pair (d/8 or d/4; 0 = d/8)
     int blocks_per_sm = 0;         // sweep CTAs per SM (0 = as many as fit)
+    int kernel = 0;                // d <= 4: 0 packed units, 1 one lane per vertex
     float sweep_us = 0.0f;         // measured sweep time of the chosen shape (autotuner)
 };
 

@@ -39,6 +39,21 @@ def _delta_err(r):
     return _rel_err_rows(r["delta"], r["ref"]["delta"], r["ref"]["abs_terms"])
 
 
+def _xnew_err(r):
+    """x_new = x + Delta/z inherits Delta's bar: its error is judged against
+    max(|x_new|, |Delta|/z, 1e-2 A/z) (the step's own size), since a vertex
+    that lands near the origin (common at d = 1) makes |x_new| alone tiny."""
+    ref = r["ref"]
+    got = np.asarray(r["xn"], np.float64).reshape(len(ref["x_new"]), -1)
+    xr = np.asarray(ref["x_new"], np.float64).reshape(len(got), -1)
+    z = np.maximum(np.asarray(ref["z"], np.float64), 1e-300)
+    scale = np.maximum.reduce([np.linalg.norm(xr, axis=1),
+                               np.linalg.norm(np.asarray(ref["delta"]).reshape(len(got), -1), axis=1) / z,
+                               1e-2 * np.asarray(ref["abs_terms"]) / z])
+    scale = np.maximum(scale, 1e-6 * max(scale.mean(), 1e-300))
+    return np.linalg.norm(got - xr, axis=1) / scale
+
+
 @pytest.fixture(scope="module")
 def B():
     from paper_2011_03479_gb300 import binding
@@ -111,9 +126,11 @@ def test_sampler_bit_exact(B, O, rmat_s12, epoch):
                 np.testing.assert_array_equal(got, ref)
 
 
-def _sweep_compare(B, O, rp, ci, d, x, sigma, epoch, **kw):
+def _sweep_compare(B, O, rp, ci, d, x, sigma, epoch, shape=None, **kw):
     ctx, p = _ctx(B, rp, ci, d, **kw)
     with ctx:
+        if shape:
+            B.gempe_set_shape(ctx, **shape)
         B.gempe_set_positions(ctx, x)
         B.gempe_set_state(ctx, sigma, epoch)
         samples = B.gempe_sweep(ctx, record_samples=True)
@@ -142,6 +159,29 @@ def test_sweep_and_update_parity(B, O, sbm_1000, d):
     assert _rel_err_rows(r["z"], ref["z"]).max() <= TOL
     assert _rel_err_rows(r["xn"], ref["x_new"]).max() <= TOL
     assert r["epoch"] == 6
+
+
+SHAPES = [("packed64", 2, dict(unit_pairs=64)), ("packed128-2cta", 2, dict(unit_pairs=128, blocks_per_sm=2)),
+          ("lane16", 2, dict(kernel=1, edge_chunk=16)), ("lane64", 2, dict(kernel=1, edge_chunk=64)),
+          ("lane32-d3", 3, dict(kernel=1, edge_chunk=32)), ("lane32-d1", 1, dict(kernel=1, edge_chunk=32)),
+          ("lane32-d4", 4, dict(kernel=1, edge_chunk=32)),
+          ("d16-g2-c32", 16, dict(lanes=2, edge_chunk=32)), ("d16-g4-c128", 16, dict(lanes=4, edge_chunk=128)),
+          ("d64-g16-c32", 64, dict(lanes=16, edge_chunk=32)), ("d8-g2-c64", 8, dict(lanes=2, edge_chunk=64))]
+
+
+@pytest.mark.parametrize("name,d,shape", SHAPES, ids=[t[0] for t in SHAPES])
+def test_every_sweep_shape_parity(B, O, rmat_s12, name, d, shape):
+    """Every launch shape the autotuner may choose gives the same epoch (R-MAT
+    scale 12: hubs cut into several work units, isolated vertices)."""
+    rp, ci = rmat_s12
+    n = len(rp) - 1
+    x = (np.random.default_rng(31 + d).standard_normal((n, d)) * 1.1).astype(np.float32)
+    r = _sweep_compare(B, O, rp, ci, d, x, 0.8, 3, shape=shape, neg_per_vertex=7)
+    ref = r["ref"]
+    assert _delta_err(r).max() <= TOL
+    assert _rel_err_rows(r["z"], ref["z"]).max() <= TOL
+    assert _xnew_err(r).max() <= TOL
+    assert r["he"].sum() == len(ci) // 2
 
 
 @pytest.mark.parametrize("w_formula,clamp,symmetric", [(1, 1, 1), (0, 0, 1), (0, 1, 0)])
