@@ -44,6 +44,7 @@ FORMS = {
     "rmat-s16-ef16": {},
     "ba-n1m-m8": {"block_partners": 64, "precision": 1},          # BF16 + tensor-core tiles
     "ba-n1m-m8-fp32": {"block_partners": 64, "precision": 0},     # the plain FP32 run of the same seed
+    "ba-n300k-m8": {"block_partners": 64, "precision": 1},        # the same kernels at a size for full ncu captures
     # batched form: 256 SBM graphs, d in {2, 16, 64}, one CUDA-graph launch per epoch
     "sbm-batch-256": {"autotune": 1},
     "sbm-batch-256-bf16": {"autotune": 1, "precision": 1},         # BF16 positions for the d >= 8 graphs
@@ -76,6 +77,14 @@ def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted):
     acc_row = 4 * (((d + 1) + 3) // 4 * 4)
     return (4 * (n + 1) + 4 * nnz + 16 * n_units + 4 * n * k + n * row + nnz * row
             + accepted * (row + 2 * acc_row) + n * 2 * acc_row)
+
+
+def tile_algorithmic_bytes(n, d, n_tiles, partners=64):
+    """Block-sampled non-edges on the tensor-core tiles: every vertex's BF16 row
+    and mask once, every tile's partner rows, a read-modify-write of every
+    anchor's and every partner's accumulator row."""
+    acc_row = 4 * (((d + 1) + 3) // 4 * 4)
+    return n * (2 * d + 8 + 2 * acc_row) + n_tiles * partners * (4 + 2 * d + 2 * acc_row)
 
 
 def sampler_algorithmic_bytes(n, k, draws):
@@ -191,15 +200,23 @@ def _dist():
     return world, rank, local
 
 
-def _profile_traffic(kernel_src_hash):
+PROFILE_TRAFFIC = {   # workload -> (summary under profiles/, key of the per-launch DRAM bytes of the timed kernel)
+    "rmat-s16-ef16": ("sweep_rmat-s16-ef16.md", "traffic_bytes_per_launch"),
+    "ba-n1m-m8": ("epoch_ba-n1m-m8.md", "traffic_bytes_per_launch_scaled"),
+}
+
+
+def _profile_traffic(kernel_src_hash, workload=WORKLOAD):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "sweep_rmat-s16-ef16.md")
+    if workload not in PROFILE_TRAFFIC:
+        return None
+    fname, key = PROFILE_TRAFFIC[workload]
     try:
-        text = open(path).read()
+        text = open(os.path.join(ROOT, "profiles", fname)).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    m = re.search(key + r":\s*([0-9]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not h or h.group(1) != kernel_src_hash:
         return None
@@ -322,11 +339,14 @@ def run_gempe(args):
 
     peak, peak_kind = _peaks()
     units = work_units(rp, k, d)
-    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, 0 if form else k, units,
-                                              0 if form else accepted / args.steps)
+    block = bool(form.get("block_partners"))
+    bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, 0 if block else k, units,
+                                              0 if block else accepted / args.steps)
+    if block and form.get("precision") and d in (16, 32, 64):
+        bytes_per_sweep += tile_algorithmic_bytes(n, d, (n + 127) // 128)
     sweep_s = statistics.mean(sweep_ms) / 1e3
     achieved = bytes_per_sweep / sweep_s / 1e9
-    traffic = _profile_traffic(kernel_source_hash())
+    traffic = _profile_traffic(kernel_source_hash(), workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -342,7 +362,9 @@ def run_gempe(args):
         "sigma_fit_steps_last": s1["sigma_iters"],
         "sweep_ms": statistics.mean(sweep_ms),
         "update_ms": statistics.mean(step_ms) - statistics.mean(sweep_ms),
-        "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_sweep + k_tile_bf16" if (block and form.get("precision")) else "k_sweep",
+                     "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic,
                      "note": "sweep window = sweep kernel with the next epoch's sampler running beside it"},
@@ -428,11 +450,11 @@ def run_batch(args):
     b.close()
 
     # the plain form: every graph in its own FP32 context, one after the other
-    alone_steps = min(args.steps, 20)
+    alone_steps = min(args.steps, 20) if not args.no_alone_baseline else 0
     alone_pairs, alone_s = 0, 0.0
     pa = B.gempe_default_params(neg_per_vertex=k)
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for q, g in enumerate(graphs):
+    for q, g in enumerate(graphs if alone_steps else []):
         pa.seed = inputs.EMBED_SEED ^ q
         c = B.gempe_create(g["row_ptr"], g["col_idx"], g["d"], pa, stream=stream)
         with torch.cuda.stream(stream):
@@ -446,7 +468,7 @@ def run_batch(args):
         alone_s += ea.elapsed_time(eb) / 1e3
         alone_pairs += alone_steps * (len(g["col_idx"]) // 2) + B.gempe_stats(c)["used"] - u0
         c.close()
-    alone_value = alone_pairs / alone_s
+    alone_value = alone_pairs / alone_s if alone_s else None
 
     # end to end: one batch job (create from pinned host CSR, `epochs` epochs, positions back)
     pinned = [(torch.from_numpy(g["row_ptr"]).pin_memory().numpy(), torch.from_numpy(g["col_idx"]).pin_memory().numpy(),
@@ -498,7 +520,7 @@ def run_batch(args):
         "pairs_per_epoch": pairs / args.steps,
         "shapes": {str(d): sh for d, sh in shapes.items()},
         "create_s": create_s,
-        "alone_fp32": {"value": alone_value, "unit": UNIT, "ratio": value / alone_value,
+        "alone_fp32": {"value": alone_value, "unit": UNIT, "ratio": value / alone_value if alone_value else None,
                        "how": f"each graph in its own FP32 context (gempe_create + gempe_step), one after the "
                               f"other, {alone_steps} epochs each, CUDA events around each graph's epochs"},
         "roofline": {"bound": "hbm", "kernel": "epoch (sweeps of all packs, concurrent)", "achieved": achieved,
@@ -692,6 +714,8 @@ def main():
     ap.add_argument("--e2e-jobs", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-alone-baseline", action="store_true",
+                    help="batched workloads: leave out the every-graph-alone comparison (measured after the timed region)")
     ap.add_argument("--workload", choices=sorted(FORMS), default=WORKLOAD,
                     help="graph-drawing workload (default) or the representation-learning forms")
     args = ap.parse_args()

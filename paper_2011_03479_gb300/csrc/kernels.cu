@@ -237,7 +237,7 @@ template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16
 // The sampler: for each stepped graph, one thread per (vertex, sample slot)
 // of the graph's epoch sample_epoch, written to samples[sample_epoch & 1] as
 // pack rows.  It depends on the graph and the epoch only, so it runs beside
-// the previous epoch's sweep.  Blocks take 128-vertex pieces of the vertex
+// the previous epoch's sweep.  Blocks take 64-vertex pieces of the vertex
 // chunks (one graph each).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
@@ -247,13 +247,19 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
     constexpr int kSubs = kVChunk / kSamplerSub;
     const int n_sub = a.n_vchunks * kSubs;
     const int k = a.k;
-    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted
+    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted of graph cur
+    int cur = -1;                   // block-uniform
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
         const int4 ch = __ldg(a.vchunks + s / kSubs);
         const int sub = s % kSubs;
         const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
         if (cnt <= 0) continue;   // uniform over the block
         const int graph = ch.z;
+        if (graph != cur) {
+            // the counts go to the graph's statistics once per run of pieces of one graph
+            if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
+            cur = graph;
+        }
         const GraphInfo gi = load_graph(a, graph);
         const int se = a.gst[graph].sample_epoch;
         const int row0 = ch.x + sub * kSamplerSub;
@@ -266,8 +272,8 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
             out[idx] = g >= 0 ? gi.v0 + g : -1;
             if (g >= 0) ++c[0]; else ++c[2];
         }
-        block_count3(c, s_cnt, a.gst + graph);
     }
+    if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
     sampler_done(a);
 }
 

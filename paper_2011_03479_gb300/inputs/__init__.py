@@ -105,6 +105,12 @@ def ba_1m():
     return dict(name="ba-n1m-m8", row_ptr=rp, col_idx=ci, d=64, k=10, epochs=100)
 
 
+def ba_300k():
+    """Barabasi-Albert n=300,000, m=8 (the BA workload's kernels at a size for full profiler captures)."""
+    rp, ci = barabasi_albert(300_000, 8, seed=3001)
+    return dict(name="ba-n300k-m8", row_ptr=rp, col_idx=ci, d=64, k=10, epochs=100)
+
+
 def sbm_batch(count: int, n_lo: int, n_hi: int, dims=(2, 16, 64), deg_lo: float = 4.0, deg_hi: float = 32.0,
               blocks_lo: int = 2, blocks_hi: int = 8, intra: float = 0.9, seed: int = 4000):
     """`count` independent SBM graphs: n log-uniform in [n_lo, n_hi], blocks
@@ -136,4 +142,4 @@ def sbm_batch_256():
     return dict(name="sbm-batch-256", graphs=sbm_batch(256, 500, 50_000), k=5, epochs=200)
 
 
-WORKLOADS = {"sbm-n1000-b4": sbm_1000, "rmat-s16-ef16": rmat_s16, "ba-n1m-m8": ba_1m}
+WORKLOADS = {"sbm-n1000-b4": sbm_1000, "rmat-s16-ef16": rmat_s16, "ba-n1m-m8": ba_1m, "ba-n300k-m8": ba_300k}
