@@ -206,6 +206,32 @@ PROFILE_TRAFFIC = {   # workload -> (summary under profiles/, key of the per-lau
 }
 
 
+def combine_ranks(t_total, pairs, device=None):
+    """Whole-job figures over the replicas: the slowest rank's time and the sum
+    of all ranks' pair-updates (one process per GPU, no data-path collective;
+    this is the only exchange, after the timed region)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_total), float(pairs)
+    tt = torch.tensor([float(t_total)], dtype=torch.float64, device=device)
+    pp = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+    return tt.item(), pp.item()
+
+
+def sum_ranks(value, device=None):
+    """Sum of a per-rank rate over the replicas (the e2e figures)."""
+    import torch
+    import torch.distributed as dist
+    if value is None or not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    v = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return v.item()
+
+
 def _profile_traffic(kernel_src_hash, workload=WORKLOAD):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -286,15 +312,7 @@ def run_gempe(args):
     draws = (s1["draws"] - s0["draws"]) * accepted / max(1, s1["accepted"] - s0["accepted"])
     pairs = args.steps * m + accepted
     t_total = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        pp = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        t_all, pairs_all = tt.item(), pp.item()
-    else:
-        t_all, pairs_all = t_total, float(pairs)
+    t_all, pairs_all = combine_ranks(t_total, pairs, dev)
     value = pairs_all / t_all
     ctx.close()
 
@@ -327,10 +345,7 @@ def run_gempe(args):
                    f"gempe_step({epochs}), gempe_positions to pinned host memory",
            "ms_per_job": 1e3 * e2e_t / e2e_jobs if e2e_jobs else None}
     if world > 1 and e2e_jobs:
-        import torch.distributed as dist
-        v = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-        e2e["value"] = v.item()
+        e2e["value"] = sum_ranks(e2e["value"], dev)
 
     if rank != 0:
         if world > 1:
@@ -437,15 +452,7 @@ def run_batch(args):
     step_ms = [a.elapsed_time(c) for a, c in ev]
     pairs = args.steps * m_tot + used
     t_total = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        pp = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        t_all, pairs_all = tt.item(), pp.item()
-    else:
-        t_all, pairs_all = t_total, float(pairs)
+    t_all, pairs_all = combine_ranks(t_total, pairs, dev)
     value = pairs_all / t_all
     b.close()
 
@@ -631,12 +638,7 @@ def run_serve(args):
     lat = (done - sub) / 1e6
     wait = (adm - sub) / 1e6
     arrivals = (sub.max() - sub.min()) / 1e9
-    value = pairs / span
-    if world > 1:
-        import torch.distributed as dist
-        v = torch.tensor([value], dtype=torch.float64, device=torch.device("cuda", local))
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-        value = v.item()
+    value = sum_ranks(pairs / span, torch.device("cuda", local))
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

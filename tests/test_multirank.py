@@ -1,0 +1,71 @@
+"""The N > 1 path of bench.py on CPU: world-size-2 gloo process groups.
+
+The bench runs one independent replica per GPU and exchanges only the whole-
+job figures after the timed region: the slowest rank's time (MAX) and the sum
+of the ranks' pair-updates (SUM).  Under torchrun the reference arm runs on
+rank 0 only; other ranks exit 0 without work.
+"""
+import json
+import multiprocessing as mp
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_combine_ranks_gloo_world_2():
+    import _rank_worker
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker.combine, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=120) for _ in procs)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert all(p.exitcode == 0 for p in procs)
+    for rank, t, pairs, v, none in res:
+        assert t == 2.0            # slowest rank
+        assert pairs == 300.0      # 100 + 200
+        assert v == 6.0            # 2 + 4
+        assert none is None
+
+
+def test_combine_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.combine_ranks(1.5, 10) == (1.5, 10.0)
+    assert bench.sum_ranks(3.0) == 3.0
+
+
+@pytest.mark.parametrize("rank", [0, 1])
+def test_reference_arm_rank_zero_only(rank):
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    if rank == 0:
+        assert len(lines) == 1
+        line = json.loads(lines[0])
+        assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+        assert line["cpu_baseline"]["kind"] == "oracle"
+        assert line["e2e"]["h2d_bytes_per_step"] == 0
+    else:
+        assert lines == []
