@@ -69,6 +69,8 @@ def _load():
         "orc_hist_pe": (F64, [_f64p, _f64p, I32, F64, F64, F64]),
         "orc_sigma_fit": (F64, [_f64p, _f64p, I32, F64, F64, F64, F64, I32]),
         "orc_loss_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64]),
+        "orc_dpe_dsigma_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64]),
+        "orc_sigma_fit_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, F64, I32]),
         "orc_loss_sampled": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32]),
         "orc_run": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, _c.POINTER(F64), F64, I32, I32,
                                U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32]),
@@ -215,6 +217,19 @@ def loss_exact(row_ptr, col_idx, x, sigma, mu=MU):
     x = _f64(x)
     return _load().orc_loss_exact(len(row_ptr) - 1, _i32(row_ptr), _i32(col_idx), x.shape[1], x,
                                   sigma, mu)
+
+
+def dpe_dsigma_exact(row_ptr, col_idx, x, sigma, mu=MU):
+    """dPE/dsigma over all pairs, times N (the number of unordered pairs)."""
+    x = _f64(x)
+    return _load().orc_dpe_dsigma_exact(len(row_ptr) - 1, _i32(row_ptr), _i32(col_idx), x.shape[1], x, mu, sigma)
+
+
+def sigma_fit_exact(row_ptr, col_idx, x, mu=MU, lo=1e-3, hi=1e3, iters=60):
+    """The slope minimising the exact Eq. 2 (bisection on the exact derivative)."""
+    x = _f64(x)
+    return _load().orc_sigma_fit_exact(len(row_ptr) - 1, _i32(row_ptr), _i32(col_idx), x.shape[1], x, mu,
+                                       lo, hi, iters)
 
 
 def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES):

@@ -21,6 +21,8 @@
  *   orc_sigma_fit          Sec. III.F: bisection for dPE/dsigma = 0 on the
  *                          edge / non-edge distance histograms, mu fixed
  *   orc_loss_exact         Eq. 2 at a given sigma, all n(n-1)/2 pairs
+ *   orc_dpe_dsigma_exact,  Eq. 2 differentiated in sigma over all pairs, and
+ *   orc_sigma_fit_exact    its zero (the slope minimising Eq. 2, mu fixed)
  *   orc_loss_sampled       Eq. 2 estimated from all edges plus sampled
  *                          non-edges weighted to the non-edge count
  *   orc_edge_terms_*       the edge part of Eq. 3 in the paper's edge-list
@@ -470,6 +472,37 @@ double orc_loss_exact(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
         for (int32_t j = i + 1; j < n; ++j)
             s += orc_dl(dist(x, d, i, j), mu, sigma, orc_is_edge(row_ptr, col_idx, i, j));
     return s / N;
+}
+
+/* dPE/dsigma over all n(n-1)/2 pairs (Eq. 2 differentiated in sigma, mu
+ * fixed), up to the positive factor 1/N: the exact counterpart of
+ * orc_dpe_dsigma, with each pair at its own distance instead of a bin centre. */
+double orc_dpe_dsigma_exact(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                            const double* x, double mu, double sigma) {
+    double s = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j) {
+            double u = (dist(x, d, i, j) - mu) / sigma;
+            s += orc_is_edge(row_ptr, col_idx, i, j) ? -u * inv_mills(u) : u * inv_mills(-u);
+        }
+    return s / (sigma * ORC_LN2);
+}
+
+/* The slope minimising Eq. 2 exactly (mu fixed): the zero of the exact
+ * dPE/dsigma, by the bisection of Sec. III.F in log sigma on [lo, hi];
+ * without a sign change, the bracket end with the lower entropy. */
+double orc_sigma_fit_exact(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                           const double* x, double mu, double lo, double hi, int32_t iters) {
+    double flo = orc_dpe_dsigma_exact(n, row_ptr, col_idx, d, x, mu, lo);
+    double fhi = orc_dpe_dsigma_exact(n, row_ptr, col_idx, d, x, mu, hi);
+    if ((flo > 0.0) == (fhi > 0.0)) return (flo > 0.0) ? lo : hi;
+    int lo_pos = flo > 0.0;
+    for (int32_t it = 0; it < iters; ++it) {
+        double mid = sqrt(lo * hi);
+        double fm = orc_dpe_dsigma_exact(n, row_ptr, col_idx, d, x, mu, mid);
+        if ((fm > 0.0) == lo_pos) lo = mid; else hi = mid;
+    }
+    return sqrt(lo * hi);
 }
 
 double orc_loss_sampled(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,

@@ -363,6 +363,43 @@ def test_loss_exact_against_scipy(oracle_mod, sbm_small):
     assert oracle_mod.loss_exact(rp, ci, x, sigma) == pytest.approx(ref, rel=1e-12)
 
 
+def test_exact_dpe_dsigma_is_the_derivative(oracle_mod, sbm_small):
+    """The exact dPE/dsigma against central differences of the exact Eq. 2
+    (a different code path: orc_loss_exact sums dl directly)."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    N = n * (n - 1) / 2
+    x = np.random.default_rng(8).normal(size=(n, 3)) * 1.3
+    for sigma in (0.3, 0.9, 2.5):
+        h = 1e-5 * sigma
+        fd = (oracle_mod.loss_exact(rp, ci, x, sigma + h) - oracle_mod.loss_exact(rp, ci, x, sigma - h)) / (2 * h)
+        assert oracle_mod.dpe_dsigma_exact(rp, ci, x, sigma) / N == pytest.approx(fd, rel=1e-6, abs=1e-12)
+
+
+def test_exact_sigma_fit_minimises_eq2(oracle_mod, sbm_small):
+    """The exact slope is a minimum of the exact Eq. 2 (mu fixed), and it is
+    close to the slope fitted on fine distance histograms of the same pairs."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    x = np.random.default_rng(9).normal(size=(n, 2))
+    s = oracle_mod.sigma_fit_exact(rp, ci, x)
+    pe = oracle_mod.loss_exact(rp, ci, x, s)
+    for f in (0.98, 0.995, 1.005, 1.02):
+        assert oracle_mod.loss_exact(rp, ci, x, s * f) >= pe
+    assert abs(oracle_mod.dpe_dsigma_exact(rp, ci, x, s)) < 1e-6 * abs(oracle_mod.dpe_dsigma_exact(rp, ci, x, 2 * s))
+    # all pairs binned into 8192 bins on [0, 12): the histogram fit lands within a bin width or so
+    adj = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        adj[i, ci[rp[i]:rp[i + 1]]] = True
+    iu = np.triu_indices(n, 1)
+    dist = np.linalg.norm(x[iu[0]] - x[iu[1]], axis=1)
+    B = 8192
+    b = np.minimum((dist / (12.0 / B)).astype(int), B - 1)
+    he = np.bincount(b[adj[iu]], minlength=B).astype(float)
+    hn = np.bincount(b[~adj[iu]], minlength=B).astype(float)
+    assert oracle_mod.sigma_fit(he, hn, 12.0, MU) == pytest.approx(s, rel=2e-3)
+
+
 def test_sampled_loss_is_unbiased(oracle_mod, sbm_small):
     rp, ci = sbm_small
     n = len(rp) - 1
