@@ -179,6 +179,16 @@ gempe_status gempe_is_edge(gempe_ctx* ctx, const int32_t* host_pairs, size_t cou
  * FP64.  Synchronises. */
 gempe_status gempe_loss(gempe_ctx* ctx, double* out_pe_bits, float* out_sigma);
 
+/* Exact predictive entropy (Eq. 2) over all n(n-1)/2 pairs at the current
+ * positions, mu fixed: with fit_sigma = 0 at the context's sigma; with
+ * fit_sigma = 1 at the sigma that minimises it (Eq. 2's min over sigma),
+ * found by Newton steps on the exact dPE/dsigma (safeguarded by bisection in
+ * ln sigma on [1e-3, 1e3]), returned in *out_sigma (the context's sigma is
+ * not changed).  Each evaluation is one pass over all pairs (O(n^2 d)), meant
+ * for graphs up to ~10^5 vertices.  Per-pair terms in FP32, sums in FP64.
+ * Synchronises. */
+gempe_status gempe_loss_exact(gempe_ctx* ctx, int32_t fit_sigma, double* out_pe_bits, float* out_sigma);
+
 /* Slope fit of Sec. III.F on a given histogram (host float[2*B], edge bins
  * then non-edge bins) on the GPU: bisection of dPE/dsigma = 0 in log sigma
  * on [1e-3, 1e3]; without a sign change the end with the lower entropy.

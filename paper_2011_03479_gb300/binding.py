@@ -146,6 +146,7 @@ def load(build: bool = True):
         "gempe_sample": (st, [vp, i32, vp, sz]),
         "gempe_is_edge": (st, [vp, vp, sz, vp]),
         "gempe_loss": (st, [vp, P(ctypes.c_double), P(ctypes.c_float)]),
+        "gempe_loss_exact": (st, [vp, i32, P(ctypes.c_double), P(ctypes.c_float)]),
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
@@ -338,6 +339,14 @@ def gempe_loss(ctx: _Ctx):
     pe = ctypes.c_double()
     s = ctypes.c_float()
     _check(load().gempe_loss(ctx.handle, ctypes.byref(pe), ctypes.byref(s)))
+    return pe.value, s.value
+
+
+def gempe_loss_exact(ctx: _Ctx, fit_sigma: bool = False):
+    """Exact Eq. 2 over all pairs; with fit_sigma the minimum over sigma: (PE bits, sigma)."""
+    pe = ctypes.c_double()
+    s = ctypes.c_float()
+    _check(load().gempe_loss_exact(ctx.handle, 1 if fit_sigma else 0, ctypes.byref(pe), ctypes.byref(s)))
     return pe.value, s.value
 
 

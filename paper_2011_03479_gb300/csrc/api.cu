@@ -395,6 +395,82 @@ GEMPE_API gempe_status gempe_loss(gempe_ctx* c, double* out_pe_bits, float* out_
     return GEMPE_OK;
 }
 
+namespace {
+// {sum dl, F, F'} of the exact Eq. 2 at sigma (one all-pairs pass + the edge pass).
+gempe_status exact_eval(gempe_ctx* c, double* dbuf, float sigma, double out[3]) {
+    Pack& pk = *c->pk;
+    CK(launch_exact_pe(pk.row_ptr, pk.col_idx, pk.x, c->n, pk.d, pk.p.mu, sigma, pk.mills, dbuf, pk.sm_count,
+                       c->stream),
+       "exact loss");
+    CK(cudaMemcpyAsync(out, dbuf, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read sums");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return GEMPE_OK;
+}
+}  // namespace
+
+GEMPE_API gempe_status gempe_loss_exact(gempe_ctx* c, int32_t fit_sigma, double* out_pe_bits, float* out_sigma) {
+    if (!c || !out_pe_bits) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    if (fit_sigma != 0 && fit_sigma != 1) return fail(GEMPE_E_INVALID_ARG, "fit_sigma must be 0 or 1");
+    gempe_status rc;
+    const GraphState st = read_graph_state(c, &rc);
+    if (rc != GEMPE_OK) return rc;
+    double* dbuf = nullptr;
+    CK(cudaMallocAsync((void**)&dbuf, 3 * sizeof(double), c->stream), "alloc");
+    const double N = 0.5 * (double)c->n * ((double)c->n - 1.0);
+    double v[3];
+    double t = std::log((double)st.sigma);
+    rc = exact_eval(c, dbuf, (float)std::exp(t), v);
+    if (rc == GEMPE_OK && fit_sigma) {
+        // zero of F (the sign of dPE/dsigma) in t = ln sigma on [ln 1e-3, ln 1e3]:
+        // bracket by steps away from the current slope, then Newton steps
+        // safeguarded by bisection
+        const double t_min = std::log(1e-3), t_max = std::log(1e3);
+        double lo = t_min, hi = t_max, f_t = v[1];
+        double vt[3] = {v[0], v[1], v[2]};
+        bool bracket = false;
+        double a = t, fa = f_t, step = 0.25;
+        for (int q = 0; q < 40 && rc == GEMPE_OK; ++q) {
+            const double b = std::min(t_max, std::max(t_min, a + (fa > 0 ? -step : step)));
+            double vb[3];
+            rc = exact_eval(c, dbuf, (float)std::exp(b), vb);
+            if (rc != GEMPE_OK) break;
+            if ((vb[1] > 0) != (fa > 0)) {
+                lo = std::min(a, b);
+                hi = std::max(a, b);
+                // keep the evaluated point closest to the root as the Newton start
+                t = b;
+                std::memcpy(vt, vb, sizeof(vt));
+                bracket = true;
+                break;
+            }
+            if (b == t_min || b == t_max) {   // no sign change: the end with the lower entropy
+                t = b;
+                std::memcpy(vt, vb, sizeof(vt));
+                break;
+            }
+            a = b;
+            fa = vb[1];
+            step *= 2.0;
+        }
+        // F > 0 at hi's side and < 0 at lo's side (dPE/dsigma rises through the minimum)
+        for (int q = 0; bracket && q < 60 && rc == GEMPE_OK; ++q) {
+            double tn = (vt[2] > 0.0) ? t - vt[1] / vt[2] : 0.5 * (lo + hi);
+            if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+            const bool done = std::fabs(tn - t) < 1e-7 || (hi - lo) < 1e-7;
+            rc = exact_eval(c, dbuf, (float)std::exp(tn), vt);
+            t = tn;
+            if (rc != GEMPE_OK || done) break;
+            if (vt[1] > 0.0) hi = t; else lo = t;
+        }
+        std::memcpy(v, vt, sizeof(v));
+    }
+    cudaFreeAsync(dbuf, c->stream);
+    if (rc != GEMPE_OK) return rc;
+    *out_pe_bits = v[0] / N;
+    if (out_sigma) *out_sigma = (float)std::exp(t);
+    return GEMPE_OK;
+}
+
 GEMPE_API gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_max, float mu,
                                        void* cuda_stream, float* out_sigma) {
     if (!host_hist || !out_sigma) return fail(GEMPE_E_INVALID_ARG, "null argument");

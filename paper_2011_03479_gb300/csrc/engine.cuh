@@ -172,5 +172,9 @@ const struct MillsCoef* mills_table_device();
 cudaError_t upload_mills_table(const void* host_coefs, size_t bytes);
 cudaError_t launch_fit_sigma(const float* hist, int32_t bins, float hist_max, float mu,
                              float* sigma_inout, cudaStream_t s);
+// Exact Eq. 2 at sigma over all pairs of one graph (rows 0..n-1): out3 = {sum dl,
+// F, dF/d ln sigma} (FP64; F has the sign of dPE/dsigma).
+cudaError_t launch_exact_pe(const int32_t* row_ptr, const int32_t* col_idx, const float* x, int n, int d, float mu,
+                            float sigma, const struct MillsCoef* tab, double* out3, int sm_count, cudaStream_t s);
 
 }  // namespace gempe
