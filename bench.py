@@ -314,6 +314,15 @@ def run_gempe(args):
     t_total = sum(step_ms) / 1e3
     t_all, pairs_all = combine_ranks(t_total, pairs, dev)
     value = pairs_all / t_all
+    # the exact Eq. 2 over all n(n-1)/2 pairs (on demand, not part of an epoch)
+    exact = None
+    if n <= 131072:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pe_exact, s_exact = B.gempe_loss_exact(ctx)
+        dt = time.perf_counter() - t0
+        exact = {"pairs_per_s": 0.5 * n * (n - 1) / dt, "ms": 1e3 * dt, "pe_bits": pe_exact, "sigma": s_exact,
+                 "how": "gempe_loss_exact(ctx, 0) once after the timed steps, host wall clock around the call"}
     ctx.close()
 
     # ---------------- end to end through the C ABI, host buffers ----------------
@@ -384,6 +393,7 @@ def run_gempe(args):
                      "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic,
                      "note": "sweep window = sweep kernel with the next epoch's sampler running beside it"},
         "sampler_algorithmic_bytes_per_launch": sampler_algorithmic_bytes(n, k, draws / args.steps),
+        "exact_pe": exact,
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,

@@ -58,7 +58,7 @@ def _load():
         "orc_sample": (None, [_i32p, _i32p, I32, I32, U64, I32, I32, I32, _i32p]),
         "orc_epoch": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
                                  I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
-                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p]),
+                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32]),
         "orc_block_partners": (None, [I32, I32, I32, U64, I32, _i32p]),
         "orc_edge_terms_edgelist": (None, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, I32,
                                            _f64p, _f64p]),
@@ -73,7 +73,7 @@ def _load():
         "orc_sigma_fit_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, F64, I32]),
         "orc_loss_sampled": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32]),
         "orc_run": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, _c.POINTER(F64), F64, I32, I32,
-                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32]),
+                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -152,16 +152,18 @@ def block_partners(n, tile, epoch_idx, seed, P):
 
 def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES,
           symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
-          hist_max=HIST_MAX, block_partners=0, tile_vertices=128):
+          hist_max=HIST_MAX, block_partners=0, tile_vertices=128, per_slot=0):
     """One epoch of Fig. 4; returns a dict of FP64 results.  ``abs_terms[i]`` is the
     sum of the sizes of the pair terms of y_i - z_i x_i (the scale of that sum's
-    rounding when its terms cancel)."""
+    rounding when its terms cancel).  per_slot=1: Sec. III.C's policy, one
+    sample per CSR slot (``samples`` then has one entry per slot)."""
     n = len(row_ptr) - 1
+    nnz = int(row_ptr[-1])
     x = _f64(x)
     d = x.shape[1]
     y = np.zeros((n, d)); z = np.zeros(n); xn = np.zeros((n, d))
     he = np.zeros(hist_bins); hn = np.zeros(hist_bins)
-    smp = np.zeros(n * max(k, 1), dtype=np.int32)
+    smp = np.zeros(max(nnz, 1) if per_slot else n * max(k, 1), dtype=np.int32)
     st = np.zeros(4, dtype=np.int64)
     absd = np.zeros(n)
     n_tiles = (n + tile_vertices - 1) // tile_vertices
@@ -169,10 +171,11 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
     rc = _load().orc_epoch(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
                            max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
                            hist_max, y, z, xn, he, hn, smp, st, absd, block_partners,
-                           tile_vertices, parts)
+                           tile_vertices, parts, per_slot)
     if rc != 0:
         raise MemoryError("oracle epoch failed")
-    return dict(y=y, z=z, x_new=xn, hist_e=he, hist_n=hn, samples=smp[: n * k].reshape(n, k),
+    samples = smp[:nnz] if per_slot else smp[: n * k].reshape(n, k)
+    return dict(y=y, z=z, x_new=xn, hist_e=he, hist_n=hn, samples=samples,
                 accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]), draws=int(st[3]),
                 delta=y - z[:, None] * x, abs_terms=absd,
                 partners=parts[: n_tiles * block_partners].reshape(n_tiles, block_partners)
@@ -240,7 +243,7 @@ def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retr
 
 def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retries=MAX_RETRIES,
         symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
-        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128):
+        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0):
     """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats)."""
     n = len(row_ptr) - 1
     x = np.array(x, dtype=np.float64, order="C", copy=True)
@@ -248,7 +251,7 @@ def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retrie
     st = np.zeros(4, dtype=np.int64)
     rc = _load().orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
                          epoch0, epochs, seed, k, max_retries, symmetric, w_formula, clamp_neg_d,
-                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices)
+                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot)
     if rc != 0:
         raise MemoryError("oracle run failed")
     return x, s.value, dict(accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]))

@@ -56,6 +56,8 @@
  *   epoch samples      (i, epoch, t, 0x0B000000|a>>2) -> word a&3 (attempt a)
  *   loss samples       (i, epoch, t, 0x0E000000|a>>2) -> word a&3
  *   block partners     (tile, epoch, p>>2, 0x0D000000) -> word p&3
+ *   per-slot samples   (e, epoch, 0, 0x0C000000|a>>2)  -> word a&3 (Sec. III.C's
+ *                      policy: one sample per CSR slot e, anchored at its row)
  * A 32-bit word r maps to vertex floor(r * n / 2^32).
  *
  * Block sampling (the representation-learning form): vertices are cut into
@@ -264,6 +266,27 @@ static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_
     }
 }
 
+/* Sec. III.C's policy: every CSR slot e = (i, j) of row i carries one
+ * non-edge partner of i, drawn with counter (e, epoch, 0, 0x0C000000 | a>>2)
+ * word a & 3 (e counted from the start of the graph's CSR), redrawn while it
+ * hits i or an edge, at most max_retries times.  out[t]: the partner of slot
+ * row_ptr[i] + t, or -1. */
+static void sample_slots(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
+                         int32_t epoch, uint64_t seed, int32_t max_retries, int32_t* out,
+                         int64_t* rejected, int64_t* exhausted) {
+    for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        int32_t got = -1;
+        for (int32_t a = 0; a < max_retries; ++a) {
+            uint32_t r = philox_word(seed, (uint32_t)e, (uint32_t)epoch, 0u, 0x0C000000u | ((uint32_t)a >> 2), a & 3);
+            int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
+            if (g != i && !orc_is_edge(row_ptr, col_idx, i, g)) { got = g; break; }
+            if (rejected) ++*rejected;
+        }
+        if (got < 0 && exhausted) ++*exhausted;
+        out[e - row_ptr[i]] = got;
+    }
+}
+
 /* Partners of tile `tile` in block sampling (P of them, duplicates kept). */
 void orc_block_partners(int32_t n, int32_t tile, int32_t epoch, uint64_t seed, int32_t P, int32_t* out) {
     for (int32_t p = 0; p < P; ++p) {
@@ -289,10 +312,13 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
               double* y, double* z, double* x_new, double* hist_e, double* hist_n,
               int32_t* samples_out, int64_t* stats, double* absd,
-              int32_t block_P, int32_t block_T, int32_t* partners_out) {
-    /* block sampling replaces the per-vertex samples */
-    if (block_P > 0) k = 0;
-    int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+              int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot) {
+    /* block sampling or the per-slot policy replace the k per-vertex samples */
+    if (block_P > 0) { k = 0; per_slot = 0; }
+    int32_t smp_cap = k > 0 ? k : 1;
+    if (per_slot)
+        for (int32_t i = 0; i < n; ++i) smp_cap = (row_ptr[i + 1] - row_ptr[i] > smp_cap) ? row_ptr[i + 1] - row_ptr[i] : smp_cap;
+    int32_t* smp = (int32_t*)malloc((size_t)smp_cap * sizeof(int32_t));
     int32_t* part = (int32_t*)malloc((size_t)(block_P > 0 ? block_P : 1) * sizeof(int32_t));
     if (!smp || !part) { free(smp); free(part); return -1; }
     g_absd = absd;
@@ -311,16 +337,22 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
             add_wm_term(y, z, x, d, i, j, delta, dd, w);
             if (hist_e && j > i) hist_e[hist_bin(delta, B, hist_max)] += 1.0;
         }
-        /* sampled non-edges anchored at i */
-        sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp,
-                      &rejected, &exhausted);
+        /* sampled non-edges anchored at i: k of them, or one per CSR slot */
+        int32_t ki = k;
+        if (per_slot) {
+            ki = row_ptr[i + 1] - row_ptr[i];
+            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, smp, &rejected, &exhausted);
+        } else {
+            sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp,
+                          &rejected, &exhausted);
+        }
         int32_t acc = 0;
-        for (int32_t t = 0; t < k; ++t) acc += (smp[t] >= 0);
+        for (int32_t t = 0; t < ki; ++t) acc += (smp[t] >= 0);
         accepted += acc;
         double deg = (double)(row_ptr[i + 1] - row_ptr[i]);
         double omega = acc ? ((double)n - 1.0 - deg) / (2.0 * acc) : 0.0;
-        for (int32_t t = 0; t < k; ++t) {
-            if (samples_out) samples_out[(int64_t)i * k + t] = smp[t];
+        for (int32_t t = 0; t < ki; ++t) {
+            if (samples_out) samples_out[per_slot ? (int64_t)row_ptr[i] + t : (int64_t)i * k + t] = smp[t];
             int32_t g = smp[t];
             if (g < 0) continue;
             double delta = dist(x, d, i, g), dd, w;
@@ -533,7 +565,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
             double* x, double* sigma, double mu, int32_t epoch0, int32_t epochs, uint64_t seed,
             int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
             double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats,
-            int32_t block_P, int32_t block_T) {
+            int32_t block_P, int32_t block_T, int32_t per_slot) {
     size_t nd = (size_t)n * d;
     double* y = (double*)malloc(nd * sizeof(double));
     double* z = (double*)malloc((size_t)n * sizeof(double));
@@ -547,7 +579,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
         int32_t ep = epoch0 + e;
         orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
                   w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL,
-                  block_P, block_T, NULL);
+                  block_P, block_T, NULL, per_slot);
         memcpy(x, xn, nd * sizeof(double));
         if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0)
             *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);

@@ -481,3 +481,55 @@ def test_block_sampling_semantics(oracle_mod, sbm_small):
             g = (oracle_mod.surrogate_L(rp, ci, xp, 0.8, samples)
                  - oracle_mod.surrogate_L(rp, ci, xm, 0.8, samples)) / (2 * h)
             assert r["delta"][i, c] == pytest.approx(-0.5 * g, rel=2e-6, abs=1e-8)
+
+
+def test_per_slot_sampling_semantics(oracle_mod, sbm_small):
+    """Sec. III.C's policy: one sample per CSR slot, anchored at the slot's
+    row (so vertex i gets deg(i) samples), redrawn while it hits the anchor or
+    an edge.  Checked: the draws follow the stated counter layout, every
+    accepted sample is a non-edge of its anchor, the weights add up to the
+    number of non-edges, k plays no part, and the epoch's sums obey the
+    gradient identity of Eq. 3 for these pairs."""
+    rp, ci = sbm_small
+    n, nnz = len(rp) - 1, int(rp[-1])
+    seed, ep = 4242, 5
+    adj = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(n)]
+    x = np.random.default_rng(12).normal(size=(n, 2)) * 1.2
+    r = oracle_mod.epoch(rp, ci, x, 0.8, ep, seed, k=3, per_slot=1, clamp_neg_d=0)
+    smp = r["samples"]
+    assert smp.shape == (nnz,)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    rejected = 0
+    for i in range(n):
+        for e in range(rp[i], rp[i + 1]):
+            got = -1
+            for a in range(32):
+                word = int(oracle_mod.philox4x32_10([e, ep, 0, 0x0C000000 | (a >> 2)], key)[a & 3])
+                g = (word * n) >> 32
+                if g != i and g not in adj[i]:
+                    got = g
+                    break
+                rejected += 1
+            assert smp[e] == got
+            if got >= 0:
+                assert got != i and got not in adj[i]
+    assert r["rejected"] == rejected and r["accepted"] == int((smp >= 0).sum())
+    if r["exhausted"] == 0:
+        assert r["hist_n"].sum() == pytest.approx(n * (n - 1) / 2 - nnz // 2, rel=1e-12)
+    # k plays no part in the per-slot policy
+    r7 = oracle_mod.epoch(rp, ci, x, 0.8, ep, seed, k=7, per_slot=1, clamp_neg_d=0)
+    np.testing.assert_array_equal(r7["samples"], smp)
+    np.testing.assert_allclose(r7["delta"], r["delta"], rtol=0, atol=0)
+    # gradient identity with the per-vertex lists of these samples
+    maxdeg = int(np.diff(rp).max())
+    lists = np.full((n, maxdeg), -1, dtype=np.int32)
+    for i in range(n):
+        lists[i, : rp[i + 1] - rp[i]] = smp[rp[i]:rp[i + 1]]
+    h = 1e-6
+    for i in range(0, n, 9):
+        for c in range(2):
+            xp = x.copy(); xp[i, c] += h
+            xm = x.copy(); xm[i, c] -= h
+            g = (oracle_mod.surrogate_L(rp, ci, xp, 0.8, lists)
+                 - oracle_mod.surrogate_L(rp, ci, xm, 0.8, lists)) / (2 * h)
+            assert r["delta"][i, c] == pytest.approx(-0.5 * g, rel=2e-6, abs=1e-8)
