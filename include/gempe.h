@@ -72,6 +72,11 @@ typedef struct gempe_params {
                                pairs with the vertex itself or a neighbour are masked; d >= 8.  With
                                precision 1 and d in {16, 32, 64} the tiles run on tensor cores */
     int32_t tile_vertices;  /* 128 (the only tile size) */
+    int32_t sampling;       /* 0: neg_per_vertex samples per vertex; 1: Sec. III.C's policy, one sample
+                               per CSR slot (every edge endpoint draws one non-edge partner, so
+                               vertex i has deg(i) samples); not with block sampling.  The loss
+                               estimator (gempe_loss) draws neg_per_vertex samples per vertex
+                               either way */
     int32_t autotune;       /* 1: time the sweep's launch shapes (units, lanes per pair, CTAs per
                                SM) on the graph at create and keep the fastest; 0: fixed defaults.
                                Only the launch shape changes, never the arithmetic of a pair */

@@ -45,6 +45,7 @@ class gempe_params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("block_partners", ctypes.c_int32),
         ("tile_vertices", ctypes.c_int32),
+        ("sampling", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -209,10 +210,11 @@ def gempe_default_params(**overrides) -> gempe_params:
 class _Ctx:
     """Owned context handle (destroyed with gempe_destroy on close / GC)."""
 
-    def __init__(self, handle, n, d, k, keep=(), slots=None):
+    def __init__(self, handle, n, d, k, keep=(), slots=None, per_slot=False, nnz=0):
         self.handle = handle
         self.n, self.d, self.k = n, d, k
         self.slots = k if slots is None else slots   # sample slots per vertex in a sweep
+        self.per_slot, self.nnz = per_slot, nnz      # Sec. III.C's policy: one sample per CSR slot
         self._keep = keep   # allocator callbacks must outlive the context
 
     def close(self):
@@ -241,7 +243,8 @@ def gempe_create(row_ptr, col_idx, d: int, params: gempe_params | None = None, s
     h = ctypes.c_void_p()
     _check(load().gempe_create(_ptr(rp), _ptr(ci) if len(ci) else ctypes.c_void_p(None), n, d,
                                ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
-    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex)
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex,
+                per_slot=(p.sampling == 1), nnz=len(ci))
 
 
 def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | None = None,
@@ -267,6 +270,10 @@ def gempe_step(ctx: _Ctx, iters: int = 1) -> None:
 
 def gempe_sweep(ctx: _Ctx, record_samples: bool = False):
     slots = ctx.slots
+    if record_samples and ctx.per_slot:
+        out = np.empty(max(ctx.nnz, 1), dtype=np.int32)
+        _check(load().gempe_sweep(ctx.handle, _ptr(out)))
+        return out[: ctx.nnz]
     if record_samples and slots > 0:
         out = np.empty(ctx.n * slots, dtype=np.int32)
         _check(load().gempe_sweep(ctx.handle, _ptr(out)))

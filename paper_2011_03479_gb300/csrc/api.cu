@@ -219,7 +219,16 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
     gempe_status s = pk.enqueue_sweep();
     if (s != GEMPE_OK) return s;
     pk.swept = true;
-    if (host_samples && pk.slots_per_vertex() > 0) {
+    if (host_samples && pk.per_slot) {
+        int32_t epoch = 0;
+        CK(cudaMemcpyAsync(&epoch, &pk.gst->epoch, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "epoch");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+        if (pk.slots > 0)
+            CK(cudaMemcpyAsync(host_samples, pk.samples + (size_t)(epoch & 1) * pk.slots,
+                               sizeof(int32_t) * (size_t)pk.slots, cudaMemcpyDeviceToHost, c->stream),
+               "copy samples");
+        CK(cudaStreamSynchronize(c->stream), "synchronize");
+    } else if (host_samples && pk.slots_per_vertex() > 0) {
         int32_t epoch = 0;
         CK(cudaMemcpyAsync(&epoch, &pk.gst->epoch, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "epoch");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
@@ -332,10 +341,11 @@ GEMPE_API gempe_status gempe_histograms(gempe_ctx* c, float* host_out, size_t co
     const unsigned int* he = (const unsigned int*)(hd + B);
     const unsigned int* hc = he + B;
     const float* hx = (const float*)(hc + B);
-    const int ks = pk.slots_per_vertex();
+    const int ks = pk.per_slot ? 0 : pk.slots_per_vertex();   // per-slot weights are all in hist_x
     for (size_t b = 0; b < B; ++b) {
         host_out[b] = (float)he[b];
-        host_out[B + b] = ks > 0 ? (float)(((double)(c->n - 1) * hc[b] - (double)hd[b]) / (2.0 * ks) + hx[b]) : 0.0f;
+        host_out[B + b] = ks > 0 ? (float)(((double)(c->n - 1) * hc[b] - (double)hd[b]) / (2.0 * ks) + hx[b])
+                                 : (pk.per_slot ? hx[b] : 0.0f);
     }
     return GEMPE_OK;
 }
@@ -344,8 +354,8 @@ GEMPE_API gempe_status gempe_sample(gempe_ctx* c, int32_t stream_id, int32_t* ho
     if (!c || !host_out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     Pack& pk = *c->pk;
     if (stream_id != 0 && stream_id != 1) return fail(GEMPE_E_INVALID_ARG, "stream_id must be 0 or 1");
-    if (stream_id == 0 && pk.block)
-        return fail(GEMPE_E_INVALID_ARG, "block sampling: the epoch's samples come from gempe_sweep's record");
+    if (stream_id == 0 && (pk.block || pk.per_slot))
+        return fail(GEMPE_E_INVALID_ARG, "block or per-slot sampling: the epoch's samples come from gempe_sweep's record");
     if (count != (size_t)c->n * pk.k) return fail(GEMPE_E_INVALID_ARG, "count must be n*k");
     if (pk.k == 0) return GEMPE_OK;
     CK(launch_sample(pk.args(), stream_id ? 0x0E000000u : 0x0B000000u, pk.scratch, c->stream), "sample");

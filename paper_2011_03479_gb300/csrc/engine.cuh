@@ -77,7 +77,10 @@ constexpr int kBlockP = 64;
 constexpr int kBlockT = 128;
 constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
 
-inline size_t hist_smem_bytes(int bins) { return (size_t)bins * 3 * sizeof(unsigned int); }
+// he, hc, hd (u32) and hw (f32, the per-slot policy's sample weights)
+inline size_t hist_smem_bytes(int bins) { return (size_t)bins * 4 * sizeof(unsigned int); }
+
+constexpr uint32_t kTagSlot = 0x0C000000u;   // counter tag of the per-slot samples
 
 inline size_t packed_smem_bytes(int d, int bins) {
     const int as = ((d + 1) + 3) / 4 * 4;
@@ -113,7 +116,11 @@ struct EpochArgs {
     int32_t n_vchunks;
     int32_t rows, d, acc_stride, k, max_retries, symmetric, w_formula, clamp_neg_d, bins;
     float mu, hist_scale;     // hist_scale = bins / hist_max
-    int32_t* samples;         // [2][rows][k] accepted partners (-1 = dropped), buffer = epoch & 1
+    int32_t* samples;         // [2][rows][k] accepted partners (-1 = dropped), buffer = epoch & 1;
+                              // per-slot policy: [2][n_slots], one partner per CSR slot
+    int32_t per_slot;         // 1: Sec. III.C's policy, one sample per CSR slot of the anchor's row
+    int32_t n_slots;          // CSR slots of the pack
+    int32_t* vacc;            // per-slot policy: [2][rows] accepted samples per vertex
     // block sampling: tiles of kBlockT rows share kBlockP partners
     int32_t block_P, n_tiles;
     int32_t* block_part;             // [2][n_tiles][kBlockP] partner rows, buffer = epoch & 1
@@ -149,7 +156,7 @@ bool sweep_lanes_supported(int d, int lanes);
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t prepare_update_kernels(int bins);   // shared-memory size of the slope-fit blocks
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
-cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);   // k per vertex, or one per slot
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
                                  cudaStream_t s);
 cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s);

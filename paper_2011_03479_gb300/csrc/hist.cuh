@@ -23,6 +23,7 @@ struct BlockHist {
     unsigned int* he;
     unsigned int* hc;
     unsigned int* hd;
+    float* hw;        // per-slot policy: sums of the samples' weights
     int home;
 };
 
@@ -31,6 +32,7 @@ __device__ __forceinline__ BlockHist block_hist(unsigned int* base, int bins, in
     h.he = base;
     h.hc = base + bins;
     h.hd = base + 2 * bins;
+    h.hw = reinterpret_cast<float*>(base + 3 * bins);
     h.home = home;
     return h;
 }
@@ -40,6 +42,7 @@ __device__ __forceinline__ void hist_clear(const BlockHist& h, int bins) {
         h.he[t] = 0u;
         h.hc[t] = 0u;
         h.hd[t] = 0u;
+        h.hw[t] = 0.0f;
     }
 }
 
@@ -51,7 +54,17 @@ __device__ __forceinline__ void hist_merge(const BlockHist& h, const EpochArgs& 
         if (e) atomicAdd(a.hist_e + off + t, e);
         if (c) atomicAdd(a.hist_c + off + t, c);
         if (d) atomicAdd(a.hist_d + off + t, (unsigned long long)d);
+        if (a.per_slot && h.hw[t] != 0.0f) atomicAdd(a.hist_x + off + t, h.hw[t]);
     }
+}
+
+// A per-slot sample anchored at a vertex of degree deg with k_acc accepted
+// samples weighs (n-1-deg)/(2 k_acc): added as a float.
+__device__ __forceinline__ void hist_sample_w(const BlockHist& h, const EpochArgs& a, int graph, int bin, int deg,
+                                              int k_acc) {
+    const float w = (float)(__ldg(&a.graphs[graph].n) - 1 - deg) / (2.0f * (float)k_acc);
+    if (graph == h.home) atomicAdd(h.hw + bin, w);
+    else atomicAdd(a.hist_x + (size_t)graph * a.bins + bin, w);
 }
 
 __device__ __forceinline__ void hist_edge(const BlockHist& h, const EpochArgs& a, int graph, int bin) {

@@ -165,6 +165,24 @@ __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigne
     return -1;
 }
 
+// Sec. III.C's policy: the partner (local id) of CSR slot e_local of the
+// graph, anchored at local vertex i (the slot's row); counter
+// (e_local, epoch, 0, kTagSlot | attempt >> 2), -1 after max_retries draws.
+__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+                                            int i, int e_local, int epoch, unsigned& rejected) {
+    const unsigned long long* table = keys + gi.key_off;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    for (int att = 0; att < max_retries; ++att) {
+        if ((att & 3) == 0)
+            r = philox4x32_10(make_uint4((uint32_t)e_local, (uint32_t)epoch, 0u, kTagSlot | ((uint32_t)att >> 2)),
+                              gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        if (g != i && !hash_contains(table, gi.bucket_mask, edge_key(i, g))) return g;
+        ++rejected;
+    }
+    return -1;
+}
+
 __device__ __forceinline__ GraphInfo load_graph(const EpochArgs& a, int g) {
     GraphInfo gi;
     const int4 w0 = __ldg(reinterpret_cast<const int4*>(a.graphs + g));
@@ -278,6 +296,63 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// The per-slot sampler (Sec. III.C's policy): one thread per CSR slot of the
+// 64-vertex pieces, the slot's row found by a binary search in the piece's
+// row offsets (shared memory); the accepted count of every vertex of the
+// piece goes to vacc for the sweep's histogram weights.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
+    __shared__ unsigned s_cnt[3];
+    __shared__ int s_rp[kSamplerSub + 1];
+    __shared__ int s_acc[kSamplerSub];
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
+    constexpr int kSubs = kVChunk / kSamplerSub;
+    const int n_sub = a.n_vchunks * kSubs;
+    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted of graph cur
+    int cur = -1;                   // block-uniform
+    for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + s / kSubs);
+        const int sub = s % kSubs;
+        const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
+        if (cnt <= 0) continue;   // uniform over the block
+        const int graph = ch.z;
+        if (graph != cur) {
+            if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
+            cur = graph;
+        }
+        const GraphInfo gi = load_graph(a, graph);
+        const int se = a.gst[graph].sample_epoch;
+        const int row0 = ch.x + sub * kSamplerSub;
+        __syncthreads();   // the previous piece's shared data is no longer read
+        for (int t = threadIdx.x; t <= cnt; t += blockDim.x) s_rp[t] = __ldg(a.row_ptr + row0 + t);
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) s_acc[t] = 0;
+        __syncthreads();
+        const int s0 = __ldg(a.row_ptr + gi.v0);   // the graph's first CSR slot
+        int32_t* out = a.samples + (size_t)(se & 1) * (size_t)a.n_slots;
+        const int e0 = s_rp[0], e1 = s_rp[cnt];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int lo = 0, hi = cnt - 1;   // row of slot e: the last r with s_rp[r] <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int g = slot_partner(gi, a.keys, a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1]);
+            out[e] = g >= 0 ? gi.v0 + g : -1;
+            if (g >= 0) {
+                ++c[0];
+                atomicAdd(&s_acc[lo], 1);
+            } else {
+                ++c[2];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) a.vacc[(size_t)(se & 1) * a.rows + row0 + t] = s_acc[t];
+    }
+    if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
+    sampler_done(a);
+}
+
+// ---------------------------------------------------------------------------
 // Packed pair sweep for d <= 4 (one lane per pair).
 //
 // A work unit is either up to 32 consecutive vertices of one graph whose edge
@@ -318,13 +393,15 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         const int4 unit = __ldg(a.items + it);
         const int v0 = unit.x, nv = unit.y & ((1 << kGraphShift) - 1), graph = unit.y >> kGraphShift;
         const bool whole_rows = unit.z < 0;
-        const bool has_s = (unit.w & kUnitHasSamples) && k > 0;
+        const bool slots = a.per_slot != 0;   // Sec. III.C's policy: one sample per CSR slot
+        const bool has_s = (unit.w & kUnitHasSamples) && (k > 0 || slots);
         const int e_lo = whole_rows ? 0 : unit.z;
         const int e_hi = unit.w & ~kUnitHasSamples;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, g_mills);
-        const int32_t* samples = a.samples + (size_t)(epoch & 1) * (size_t)a.rows * k;
+        const int32_t* samples =
+            a.samples + (size_t)(epoch & 1) * (slots ? (size_t)a.n_slots : (size_t)a.rows * k);
 
         // per-vertex layout: lane l < nv describes vertex v0 + l
         int rs = 0, deg = 0, ne = 0;
@@ -334,7 +411,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
             ne = whole_rows ? deg : e_hi - e_lo;
         }
         const int ebase = rs + e_lo;
-        const int np = (lane < nv) ? ne + (has_s ? k : 0) : 0;
+        const int np = (lane < nv) ? ne + (has_s ? (slots ? ne : k) : 0) : 0;
         int incl = np;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -348,9 +425,13 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
             for (int c = 0; c < AS; ++c) s_acc[lane * AS + c] = 0.0f;
         }
 
-        // the unit's sampled partners (contiguous in the sample buffer)
+        // the unit's sampled partners (contiguous in the sample buffer); in the
+        // per-slot policy they are read pair by pair and counted per vertex
+        // by the sampler
         int k_acc = 0;
-        if (has_s) {
+        if (has_s && slots) {
+            if (lane < nv) k_acc = __ldg(a.vacc + (size_t)(epoch & 1) * a.rows + v0 + lane);
+        } else if (has_s) {
             const int ns = nv * k;
             const int32_t* src = samples + (size_t)v0 * k;
             for (int s = lane; s < ns; s += 32) s_g[s] = __ldg(src + s);
@@ -366,6 +447,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
             }
         }
         __syncwarp();
+        int slot_used = 0;   // per-slot policy: accepted samples this lane processed
 
         for (int base = 0; base < total; base += 32) {
             const int q = base + lane;
@@ -386,8 +468,12 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
             const int v = v0 + l;
             const bool is_edge = r < ne_l;
             int j = -1;
-            if (active) j = is_edge ? __ldg(a.col_idx + eb_l + r) : s_g[l * k + (r - ne_l)];
+            if (active) {
+                if (is_edge) j = __ldg(a.col_idx + eb_l + r);
+                else j = slots ? __ldg(samples + eb_l + (r - ne_l)) : s_g[l * k + (r - ne_l)];
+            }
             const bool valid = active && j >= 0;
+            slot_used += (slots && valid && !is_edge) ? 1 : 0;
 
             float val[D + 1];
 #pragma unroll
@@ -413,7 +499,8 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
                 if (is_edge) {
                     if (j > v) hist_edge(hist, a, graph, bin);
                 } else {
-                    hist_sample(hist, a, graph, bin, deg_l, kacc_l, k);
+                    if (slots) hist_sample_w(hist, a, graph, bin, deg_l, kacc_l);
+                    else hist_sample(hist, a, graph, bin, deg_l, kacc_l, k);
                     if (a.symmetric) {
                         float pv[D];
 #pragma unroll
@@ -439,6 +526,14 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
                 for (int c = 0; c <= D; ++c) s_acc[l * AS + c] += val[c];
             }
             __syncwarp();
+        }
+        if (slots) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) slot_used += __shfl_xor_sync(kFull, slot_used, o);
+            if (lane == 0 && slot_used) {
+                if (graph == hist.home) atomicAdd(&s_used, (unsigned)slot_used);
+                else atomicAdd(&a.gst[graph].used, (unsigned long long)slot_used);
+            }
         }
         // one vector atomic per vertex into the global accumulator
         if (lane < nv && s_acc[lane * AS + D] != 0.0f) {
@@ -498,7 +593,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     const int gl = lane % G;               // lane within the group
     const int gbase = lane - gl;           // first lane of the group
     const bool block = a.block_P > 0;
-    const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex
+    const bool slots = a.per_slot != 0;          // Sec. III.C's policy: one sample per CSR slot
+    const int k_eff = block ? kBlockP : a.k;     // sample slots per vertex (k and block forms)
 
     for (;;) {
         int task = 0;
@@ -509,7 +605,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         const int i = item.x;                              // -1: padding
         const int graph = item.y >> kGraphShift;
         const bool live = i >= 0;
-        const bool has_samples = live && (item.w & kUnitHasSamples) && k_eff > 0 && a.sweep_samples;
+        const bool has_samples = live && (item.w & kUnitHasSamples) && (k_eff > 0 || slots) && a.sweep_samples;
         const int p0 = item.z, p1 = item.w & ~kUnitHasSamples;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
@@ -530,7 +626,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         unsigned long long bmask_v = 0ull;
         const int32_t* tp = nullptr;
         const int32_t* sp = nullptr;
-        if (has_samples) {
+        if (has_samples && slots) {
+            sp = a.samples + (size_t)(epoch & 1) * (size_t)a.n_slots + e0 + p0;   // this unit's slots
+            k_acc = __ldg(a.vacc + (size_t)(epoch & 1) * a.rows + i);
+        } else if (has_samples) {
             if (block) {
                 unsigned long long* bm = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows + i;
                 bmask_v = *bm;
@@ -546,19 +645,20 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         // group sum of the per-vertex count: every lane of the warp takes part
         // (groups without samples add zeros); the block form's count is
         // already complete in every lane of its group
-        if (!block) {
+        if (!block && !slots) {
 #pragma unroll
             for (int o = G / 2; o >= 1; o >>= 1) k_acc += __shfl_xor_sync(kFull, k_acc, o);
         }
         __syncwarp();
-        if (has_samples && gl == 0) {
+        if (has_samples && !slots && gl == 0) {
             if (block) a.block_mask[(size_t)(epoch & 1) * (size_t)a.rows + i] = 0ull;   // read once
             if (k_acc) {
                 if (graph == home) atomicAdd(&s_used, (unsigned)k_acc);
                 else atomicAdd(&a.gst[graph].used, (unsigned long long)k_acc);
             }
         }
-        const int total = ne + (has_samples ? k_eff : 0);
+        const int total = ne + (has_samples ? (slots ? ne : k_eff) : 0);
+        int slot_used = 0;   // per-slot policy: accepted samples this lane evaluated
         const int rounds = (total + G - 1) / G;
         const int rmax = (int)__reduce_max_sync(kFull, (unsigned)rounds);
 
@@ -612,6 +712,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
                 if (my_edge) {
                     if (my_j > i) hist_edge(hist, a, graph, bin);
+                } else if (slots) {
+                    hist_sample_w(hist, a, graph, bin, deg, k_acc);
+                    ++slot_used;
                 } else {
                     hist_sample(hist, a, graph, bin, deg, k_acc, k_eff);
                 }
@@ -643,6 +746,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         // z over the group; each lane adds its own coordinates of the sum
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) zacc += __shfl_xor_sync(kFull, zacc, o);
+        if (slots) {
+#pragma unroll
+            for (int o = G / 2; o >= 1; o >>= 1) slot_used += __shfl_xor_sync(kFull, slot_used, o);
+            if (gl == 0 && slot_used) {
+                if (graph == home) atomicAdd(&s_used, (unsigned)slot_used);
+                else atomicAdd(&a.gst[graph].used, (unsigned long long)slot_used);
+            }
+        }
         if (total > 0) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
     __syncthreads();
@@ -1241,7 +1352,8 @@ int sampler_grid(int rows, int k, int sm_count) {
 }
 
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
-    k_sampler<<<grid, 256, 0, s>>>(a);
+    if (a.per_slot) k_sampler_slots<<<grid, 256, 0, s>>>(a);
+    else k_sampler<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,9 @@ gempe_status check_params(const gempe_params* p, int32_t d) {
     if (p->block_partners && (d < 8 || (p->tile_vertices != 0 && p->tile_vertices != kBlockT)))
         return pack_fail(GEMPE_E_INVALID_ARG, "block sampling needs d >= 8 and tile_vertices 128");
     if (p->autotune != 0 && p->autotune != 1) return pack_fail(GEMPE_E_INVALID_ARG, "autotune must be 0 or 1");
+    if (p->sampling != 0 && p->sampling != 1) return pack_fail(GEMPE_E_INVALID_ARG, "sampling must be 0 or 1");
+    if (p->sampling == 1 && p->block_partners)
+        return pack_fail(GEMPE_E_INVALID_ARG, "the per-slot sampling policy excludes block sampling");
     return GEMPE_OK;
 }
 
@@ -87,19 +90,23 @@ namespace {
 // runs of up to 32 consecutive vertices with at most `budget` edge + sample
 // slots in total; a vertex with more is cut into `budget`-slot chunks of its
 // row, the last chunk carrying the samples.
-void packed_units(const int32_t* rp, int32_t v0, int32_t n, int32_t k, int budget, int32_t g,
+// per_slot: Sec. III.C's policy, every CSR slot carries its own sample, so a
+// vertex has 2 deg pairs and a hub chunk of c slots carries c samples.
+void packed_units(const int32_t* rp, int32_t v0, int32_t n, int32_t k, int budget, int32_t g, bool per_slot,
                   std::vector<int4>& units) {
-    const int smp = k > 0 ? kUnitHasSamples : 0;
+    const int smp = (k > 0 || per_slot) ? kUnitHasSamples : 0;
     const int gy = g << kGraphShift;
     int32_t i = v0;
     const int32_t end = v0 + n;
     while (i < end) {
         const int32_t deg = rp[i + 1] - rp[i];
-        if (deg + k > budget) {
+        const int32_t pairs_i = per_slot ? 2 * deg : deg + k;
+        if (pairs_i > budget) {
+            const int32_t chunk = per_slot ? budget / 2 : budget;
             int32_t e = 0;
-            while (deg - e > budget) {
-                units.push_back(make_int4(i, gy | 1, e, e + budget));
-                e += budget;
+            while (deg - e > chunk) {
+                units.push_back(make_int4(i, gy | 1, e, (e + chunk) | (per_slot ? smp : 0)));
+                e += chunk;
             }
             units.push_back(make_int4(i, gy | 1, e, deg | smp));
             ++i;
@@ -108,7 +115,7 @@ void packed_units(const int32_t* rp, int32_t v0, int32_t n, int32_t k, int budge
         const int32_t u0 = i;
         int32_t pairs = 0;
         while (i < end && i - u0 < 32) {
-            const int32_t di = rp[i + 1] - rp[i] + k;
+            const int32_t di = per_slot ? 2 * (rp[i + 1] - rp[i]) : rp[i + 1] - rp[i] + k;
             if (di > budget || pairs + di > budget) break;
             pairs += di;
             ++i;
@@ -119,14 +126,16 @@ void packed_units(const int32_t* rp, int32_t v0, int32_t n, int32_t k, int budge
 
 // Work units of the per-unit sweep (d >= 8): each vertex's CSR slots in
 // chunks of `chunk`, the last chunk also carrying the vertex's samples.
-void chunk_units(const int32_t* rp, int32_t v0, int32_t n, int chunk, int32_t g, std::vector<int4>& units) {
+// per_slot: every chunk carries the samples of its own slots.
+void chunk_units(const int32_t* rp, int32_t v0, int32_t n, int chunk, int32_t g, bool per_slot,
+                 std::vector<int4>& units) {
     const int gy = (g << kGraphShift) | 1;
     for (int32_t i = v0; i < v0 + n; ++i) {
         const int32_t deg = rp[i + 1] - rp[i];
         const int32_t chunks = std::max<int32_t>(1, (deg + chunk - 1) / chunk);
         for (int32_t c = 0; c < chunks; ++c) {
             const int32_t p0 = c * chunk, p1 = std::min(deg, (c + 1) * chunk);
-            units.push_back(make_int4(i, gy, p0, p1 | (c == chunks - 1 ? kUnitHasSamples : 0)));
+            units.push_back(make_int4(i, gy, p0, p1 | ((per_slot || c == chunks - 1) ? kUnitHasSamples : 0)));
         }
     }
 }
@@ -136,11 +145,14 @@ void chunk_units(const int32_t* rp, int32_t v0, int32_t n, int chunk, int32_t g,
 // rounds.  Within windows of 16 * pg consecutive units the units are sorted
 // by their pair count, then cut into consecutive tasks; the list is padded to
 // a multiple of pg with empty units (vertex -1).
-void wide_tasks(std::vector<int4>& units, int pg, int k_slots) {
+int unit_pairs_of(const int4& u, int k_slots, bool per_slot) {
+    const int ne = (u.w & ~kUnitHasSamples) - u.z;
+    return ne + ((u.w & kUnitHasSamples) ? (per_slot ? ne : k_slots) : 0);
+}
+
+void wide_tasks(std::vector<int4>& units, int pg, int k_slots, bool per_slot) {
     if (pg <= 1) return;
-    auto pairs = [&](const int4& u) {
-        return (u.w & ~kUnitHasSamples) - u.z + ((u.w & kUnitHasSamples) ? k_slots : 0);
-    };
+    auto pairs = [&](const int4& u) { return unit_pairs_of(u, k_slots, per_slot); };
     const size_t window = 16 * (size_t)pg;
     for (size_t w0 = 0; w0 < units.size(); w0 += window) {
         const size_t w1 = std::min(units.size(), w0 + window);
@@ -212,6 +224,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     stream = s;
     block = p.block_partners > 0;
     tiles = block && p.precision == 1 && tile_dim(d);
+    per_slot = p.sampling == 1;
 
     // layout
     long long rows_ll = 0, slots_ll = 0, tiles_ll = 0;
@@ -230,7 +243,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         }
         nnz[g] = in.row_ptr[in.n];
         // the per-block sums of sampled anchors' degrees are 32-bit
-        if ((unsigned long long)std::max(k, slots_per_vertex()) * (unsigned long long)nnz[g] >= (1ull << 32))
+        if (!per_slot && (unsigned long long)std::max(k, slots_per_vertex()) * (unsigned long long)nnz[g] >= (1ull << 32))
             return pack_fail(GEMPE_E_INVALID_ARG, "sample slots * nnz must be below 2^32");
         GraphInfo& gi = info[g];
         gi.v0 = (int32_t)rows_ll;
@@ -323,7 +336,12 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     active = (int32_t*)alloc(sizeof(int32_t) * G);
     vchunks = (int4*)alloc(sizeof(int4) * vch.size());
     scratch = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>(R * std::max(k, 1), 1));
-    samples = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>(block ? 1 : 2 * R * k, 1));
+    samples = (int32_t*)alloc(sizeof(int32_t) *
+                              std::max<size_t>(block ? 1 : (per_slot ? 2 * (size_t)slots : 2 * R * k), 1));
+    if (per_slot) {
+        vacc = (int32_t*)alloc(sizeof(int32_t) * 2 * R);
+        if (!vacc) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+    }
     if (p.precision == 1) xb = (__nv_bfloat16*)alloc(sizeof(__nv_bfloat16) * R * d);
     if (block) {
         block_part = (int32_t*)alloc(sizeof(int32_t) * 2 * (size_t)std::max(n_tiles, 1) * kBlockP);
@@ -386,14 +404,16 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     const bool blk = p.block_partners > 0 && d >= 8;
     const size_t R = (size_t)n + 1, k = (size_t)p.neg_per_vertex, bins = (size_t)p.hist_bins;
     const size_t tiles = blk ? ((size_t)n + kBlockT - 1) / kBlockT : 0;
-    const size_t units_max = (size_t)n + (size_t)nnz / 32 + 16;
+    const size_t units_max = (size_t)n + (size_t)nnz / 8 + 16;
     size_t b = 0;
     b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1)) + al(8 * table_slots(nnz));
     b += al(4 * R * d) + al(4 * R * acc_stride_for(d));
     if (p.precision == 1 && d >= 8) b += al(2 * R * d);
     b += al(bins * 20) + al(sizeof(GraphInfo)) + al(sizeof(GraphState)) + al(sizeof(PackState)) + al(4);
     b += al(16 * (((size_t)n + kVChunk - 1) / kVChunk)) + al(4 * R * std::max<size_t>(k, 1));
-    b += al(4 * std::max<size_t>(blk ? 1 : 2 * R * k, 1)) + al(16 * units_max) + al(4 * 4097);
+    const bool ps = p.sampling == 1;
+    b += al(4 * std::max<size_t>(blk ? 1 : (ps ? 2 * (size_t)nnz : 2 * R * k), 1)) + al(16 * units_max) + al(4 * 4097);
+    if (ps) b += al(8 * R);
     if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
     return b;
 }
@@ -411,8 +431,8 @@ gempe_status Pack::set_shape(const PackShape& s) {
     const bool per_unit = d > kPackedMaxDim || sh.kernel == 1;   // the kernel with lane groups per unit
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
-        if (!per_unit) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, units);
-        else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, units);
+        if (!per_unit) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, per_slot, units);
+        else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, per_slot, units);
     }
     const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm, sh.kernel);
     std::vector<int32_t> bounds;
@@ -420,7 +440,7 @@ gempe_status Pack::set_shape(const PackShape& s) {
         const int lanes = sh.lanes ? sh.lanes : (d <= kPackedMaxDim ? 1 : d / 8);
         const int pg = 32 / lanes;
         const int k_slots = tiles ? 0 : slots_per_vertex();
-        wide_tasks(units, pg, k_slots);
+        wide_tasks(units, pg, k_slots, per_slot);
         // per-block task ranges of equal estimated work: a task costs its
         // longest unit's rounds plus a fixed set-up
         const size_t n_tasks = units.size() / pg;
@@ -430,7 +450,7 @@ gempe_status Pack::set_shape(const PackShape& s) {
             for (int g2 = 0; g2 < pg; ++g2) {
                 const int4& u = units[t * pg + g2];
                 if (u.x < 0) continue;
-                const int pairs = (u.w & ~kUnitHasSamples) - u.z + ((u.w & kUnitHasSamples) ? k_slots : 0);
+                const int pairs = unit_pairs_of(u, k_slots, per_slot);
                 rounds = std::max(rounds, (pairs + lanes - 1) / lanes);
             }
             cum[t + 1] = cum[t] + rounds + 1.0;
@@ -512,6 +532,9 @@ EpochArgs Pack::args() const {
     a.mu = p.mu;
     a.hist_scale = (float)bins / p.hist_max;
     a.samples = samples;
+    a.per_slot = per_slot ? 1 : 0;
+    a.n_slots = (int32_t)slots;
+    a.vacc = vacc;
     a.block_P = block ? kBlockP : 0;
     a.n_tiles = n_tiles;
     a.block_part = block_part;
@@ -534,7 +557,7 @@ cudaError_t launch_epoch_sampler(const Pack& pk, cudaStream_t s) {
 }  // namespace
 
 gempe_status Pack::prime() {
-    if (primed || slots_per_vertex() == 0) return GEMPE_OK;
+    if (primed || !sampled()) return GEMPE_OK;
     PK(launch_epoch_sampler(*this, stream), "sampler");
     primed = true;
     return GEMPE_OK;
@@ -545,7 +568,7 @@ gempe_status Pack::prime() {
 gempe_status Pack::enqueue_sweep() {
     gempe_status s = prime();
     if (s != GEMPE_OK) return s;
-    if (slots_per_vertex() > 0 && !sampled_ahead) {
+    if (sampled() && !sampled_ahead) {
         PK(cudaEventRecord(fork_ev, stream), "fork");
         PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
         PK(launch_epoch_sampler(*this, side), "sampler");

@@ -43,6 +43,7 @@ struct Pack {
     int64_t slots = 0;
     unsigned long long key_slots = 0;
     bool block = false, tiles = false;
+    bool per_slot = false;           // Sec. III.C's policy: one sample per CSR slot
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;   // set by the owner (context or batch), not owned
     cudaStream_t side = nullptr;     // owned: the next epoch's sampler runs here
@@ -78,7 +79,8 @@ struct Pack {
     int32_t task_bounds_cap = 0;
     int4* vchunks = nullptr;
     int32_t n_vchunks = 0;
-    int32_t* samples = nullptr;      // [2][rows][k]
+    int32_t* samples = nullptr;      // [2][rows][k], per-slot policy [2][slots]
+    int32_t* vacc = nullptr;         // per-slot policy: [2][rows] accepted samples per vertex
     int32_t* block_part = nullptr;   // [2][n_tiles][64]
     unsigned long long* block_mask = nullptr;   // [2][rows]
     int4* sampler_units = nullptr;   // block sampler {tile, e_lo, e_hi, graph << 1 | first}
@@ -116,6 +118,7 @@ struct Pack {
     gempe_status enqueue_update();   // position update + slope fits; joins `side`
     gempe_status read_status();      // synchronises; reports and clears a device-side error
     int32_t slots_per_vertex() const { return block ? kBlockP : k; }
+    bool sampled() const { return per_slot ? slots > 0 : slots_per_vertex() > 0; }
 
     // Device bytes a pack of one graph with n vertices and nnz CSR slots
     // allocates (an upper bound: the sweep units are counted at their most).
