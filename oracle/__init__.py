@@ -73,7 +73,8 @@ def _load():
         "orc_sigma_fit_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, F64, I32]),
         "orc_loss_sampled": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32]),
         "orc_run": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, _c.POINTER(F64), F64, I32, I32,
-                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32]),
+                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32, I32]),
+        "orc_hist_pass": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, I32, U64, I32, I32, I32, F64, _f64p, _f64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -235,6 +236,19 @@ def sigma_fit_exact(row_ptr, col_idx, x, mu=MU, lo=1e-3, hi=1e3, iters=60):
                                        lo, hi, iters)
 
 
+def hist_pass(row_ptr, col_idx, x, epoch_idx, seed, k, max_retries=MAX_RETRIES, hist_bins=HIST_BINS,
+              hist_max=HIST_MAX):
+    """Sec. III.F's separate histogram pass: all edges and k fresh samples per vertex at x."""
+    x = _f64(x)
+    he = np.zeros(hist_bins)
+    hn = np.zeros(hist_bins)
+    rc = _load().orc_hist_pass(len(row_ptr) - 1, _i32(row_ptr), _i32(col_idx), x.shape[1], x, epoch_idx, seed, k,
+                               max_retries, hist_bins, hist_max, he, hn)
+    if rc != 0:
+        raise MemoryError("oracle histogram pass failed")
+    return he, hn
+
+
 def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES):
     x = _f64(x)
     return _load().orc_loss_sampled(len(row_ptr) - 1, _i32(row_ptr), _i32(col_idx), x.shape[1], x,
@@ -243,7 +257,7 @@ def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retr
 
 def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retries=MAX_RETRIES,
         symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
-        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0):
+        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0, sigma_source=0):
     """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats)."""
     n = len(row_ptr) - 1
     x = np.array(x, dtype=np.float64, order="C", copy=True)
@@ -251,7 +265,7 @@ def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retrie
     st = np.zeros(4, dtype=np.int64)
     rc = _load().orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
                          epoch0, epochs, seed, k, max_retries, symmetric, w_formula, clamp_neg_d,
-                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot)
+                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot, sigma_source)
     if rc != 0:
         raise MemoryError("oracle run failed")
     return x, s.value, dict(accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]))

@@ -58,6 +58,8 @@
  *   block partners     (tile, epoch, p>>2, 0x0D000000) -> word p&3
  *   per-slot samples   (e, epoch, 0, 0x0C000000|a>>2)  -> word a&3 (Sec. III.C's
  *                      policy: one sample per CSR slot e, anchored at its row)
+ *   slope samples      (i, epoch, t, 0x0F000000|a>>2) -> word a&3 (the separate
+ *                      histogram pass of Sec. III.F)
  * A 32-bit word r maps to vertex floor(r * n / 2^32).
  *
  * Block sampling (the representation-learning form): vertices are cut into
@@ -558,6 +560,33 @@ double orc_loss_sampled(int32_t n, const int32_t* row_ptr, const int32_t* col_id
     return s / N;
 }
 
+/* Sec. III.F's second way to collect the slope histograms: in a separate
+ * step, all edges (once each) and k fresh non-edge samples per vertex
+ * (stream 0x0F000000, the same per-vertex draw as the epoch's samples)
+ * binned at the given positions, a sample anchored at i weighing
+ * (n-1-deg_i)/(2 accepted_i). */
+int orc_hist_pass(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d, const double* x,
+                  int32_t epoch, uint64_t seed, int32_t k, int32_t max_retries, int32_t B, double hist_max,
+                  double* hist_e, double* hist_n) {
+    int32_t* smp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+    if (!smp) return -1;
+    memset(hist_e, 0, sizeof(double) * (size_t)B);
+    memset(hist_n, 0, sizeof(double) * (size_t)B);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col_idx[e] > i) hist_e[hist_bin(dist(x, d, i, col_idx[e]), B, hist_max)] += 1.0;
+        sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0F000000u, k, max_retries, smp, NULL, NULL);
+        int32_t acc = 0;
+        for (int32_t t = 0; t < k; ++t) acc += (smp[t] >= 0);
+        if (!acc) continue;
+        double omega = ((double)n - 1.0 - (double)(row_ptr[i + 1] - row_ptr[i])) / (2.0 * acc);
+        for (int32_t t = 0; t < k; ++t)
+            if (smp[t] >= 0) hist_n[hist_bin(dist(x, d, i, smp[t]), B, hist_max)] += omega;
+    }
+    free(smp);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Full run: Fig. 4 repeated for a fixed number of epochs               */
 /* ------------------------------------------------------------------ */
@@ -565,7 +594,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
             double* x, double* sigma, double mu, int32_t epoch0, int32_t epochs, uint64_t seed,
             int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
             double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats,
-            int32_t block_P, int32_t block_T, int32_t per_slot) {
+            int32_t block_P, int32_t block_T, int32_t per_slot, int32_t sigma_source) {
     size_t nd = (size_t)n * d;
     double* y = (double*)malloc(nd * sizeof(double));
     double* z = (double*)malloc((size_t)n * sizeof(double));
@@ -581,8 +610,13 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
                   w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL,
                   block_P, block_T, NULL, per_slot);
         memcpy(x, xn, nd * sizeof(double));
-        if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0)
+        if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0) {
+            /* sigma_source 1: histograms of a separate pass at the new positions */
+            if (sigma_source == 1 &&
+                orc_hist_pass(n, row_ptr, col_idx, d, x, ep, seed, k, max_retries, B, hist_max, he, hn) != 0)
+                break;
             *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);
+        }
         if (stats) for (int q = 0; q < 4; ++q) stats[q] += st[q];
     }
     free(y); free(z); free(xn); free(he); free(hn);

@@ -533,3 +533,30 @@ def test_per_slot_sampling_semantics(oracle_mod, sbm_small):
             g = (oracle_mod.surrogate_L(rp, ci, xp, 0.8, lists)
                  - oracle_mod.surrogate_L(rp, ci, xm, 0.8, lists)) / (2 * h)
             assert r["delta"][i, c] == pytest.approx(-0.5 * g, rel=2e-6, abs=1e-8)
+
+
+def test_separate_histogram_pass(oracle_mod, sbm_small):
+    """Sec. III.F's separate pass: every edge once with weight 1, non-edge
+    weights adding up to the number of non-edges, samples that are non-edges
+    of their anchors; a run with it refits sigma from the new positions."""
+    rp, ci = sbm_small
+    n, m = len(rp) - 1, len(ci) // 2
+    x = np.random.default_rng(21).normal(size=(n, 2))
+    he, hn = oracle_mod.hist_pass(rp, ci, x, 3, 77, 6)
+    assert he.sum() == m
+    assert hn.sum() == pytest.approx(n * (n - 1) / 2 - m, rel=1e-12)
+    # the edge histogram is the binned edge distances at x
+    iu = [(i, j) for i in range(n) for j in ci[rp[i]:rp[i + 1]] if j > i]
+    dist = np.array([np.linalg.norm(x[i] - x[j]) for i, j in iu])
+    np.testing.assert_array_equal(he, np.bincount(np.minimum((dist / (12.0 / 1024)).astype(int), 1023),
+                                                  minlength=1024))
+    x0 = oracle_mod.init_positions(n, 2, 5)
+    xa, sa, _ = oracle_mod.run(rp, ci, x0, 1.0, 3, 5, 4, sigma_source=1)
+    xb, sb, _ = oracle_mod.run(rp, ci, x0, 1.0, 3, 5, 4, sigma_source=0)
+    assert sa != sb
+    # the last refit of the sigma_source=1 run is the fit on the pass at the
+    # positions after its last epoch (epoch index 2)
+    xr, sr, _ = oracle_mod.run(rp, ci, x0, 1.0, 2, 5, 4, sigma_source=1)
+    r = oracle_mod.epoch(rp, ci, xr, sr, 2, 5, 4)
+    he2, hn2 = oracle_mod.hist_pass(rp, ci, r["x_new"], 2, 5, 4)
+    assert oracle_mod.sigma_fit(he2, hn2, 12.0, MU) == pytest.approx(sa, rel=1e-12)
