@@ -77,6 +77,10 @@ typedef struct gempe_params {
                                vertex i has deg(i) samples); not with block sampling.  The loss
                                estimator (gempe_loss) draws neg_per_vertex samples per vertex
                                either way */
+    int32_t sigma_source;   /* 0: the slope fit bins the distances the sweep computes anyway (the
+                               epoch's start positions, Sec. III.F's first way); 1: a separate pass
+                               after the update bins all edges and neg_per_vertex fresh samples per
+                               vertex at the new positions (Sec. III.F's second way) */
     int32_t autotune;       /* 1: time the sweep's launch shapes (units, lanes per pair, CTAs per
                                SM) on the graph at create and keep the fastest; 0: fixed defaults.
                                Only the launch shape changes, never the arithmetic of a pair */
@@ -170,7 +174,8 @@ gempe_status gempe_histograms(gempe_ctx* ctx, float* host_out, size_t count);
 
 /* Draw the sampled non-edges of the current epoch without using them:
  * host int32[n*k] partners or -1.  stream_id 0 = the epoch's sampler, 1 =
- * the loss estimator's sampler.  Synchronises. */
+ * the loss estimator's sampler, 2 = the separate histogram pass's sampler.
+ * Synchronises. */
 gempe_status gempe_sample(gempe_ctx* ctx, int32_t stream_id, int32_t* host_out, size_t count);
 
 /* Membership test against the device edge hash set (Sec. III.C, exact):

@@ -46,6 +46,7 @@ class gempe_params(ctypes.Structure):
         ("block_partners", ctypes.c_int32),
         ("tile_vertices", ctypes.c_int32),
         ("sampling", ctypes.c_int32),
+        ("sigma_source", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -329,9 +330,11 @@ def gempe_histograms(ctx: _Ctx, bins: int):
     return out[:bins].copy(), out[bins:].copy()
 
 
-def gempe_sample(ctx: _Ctx, loss_stream: bool = False) -> np.ndarray:
+def gempe_sample(ctx: _Ctx, loss_stream: bool = False, stream_id: int | None = None) -> np.ndarray:
+    """stream_id: 0 the epoch's samples, 1 the loss estimator's, 2 the separate histogram pass's."""
+    sid = (1 if loss_stream else 0) if stream_id is None else int(stream_id)
     out = np.empty(ctx.n * ctx.k, dtype=np.int32)
-    _check(load().gempe_sample(ctx.handle, 1 if loss_stream else 0, _ptr(out), out.size))
+    _check(load().gempe_sample(ctx.handle, sid, _ptr(out), out.size))
     return out.reshape(ctx.n, ctx.k)
 
 

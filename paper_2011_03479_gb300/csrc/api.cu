@@ -353,12 +353,13 @@ GEMPE_API gempe_status gempe_histograms(gempe_ctx* c, float* host_out, size_t co
 GEMPE_API gempe_status gempe_sample(gempe_ctx* c, int32_t stream_id, int32_t* host_out, size_t count) {
     if (!c || !host_out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     Pack& pk = *c->pk;
-    if (stream_id != 0 && stream_id != 1) return fail(GEMPE_E_INVALID_ARG, "stream_id must be 0 or 1");
+    if (stream_id < 0 || stream_id > 2) return fail(GEMPE_E_INVALID_ARG, "stream_id must be 0, 1 or 2");
     if (stream_id == 0 && (pk.block || pk.per_slot))
         return fail(GEMPE_E_INVALID_ARG, "block or per-slot sampling: the epoch's samples come from gempe_sweep's record");
     if (count != (size_t)c->n * pk.k) return fail(GEMPE_E_INVALID_ARG, "count must be n*k");
     if (pk.k == 0) return GEMPE_OK;
-    CK(launch_sample(pk.args(), stream_id ? 0x0E000000u : 0x0B000000u, pk.scratch, c->stream), "sample");
+    const uint32_t tags[3] = {0x0B000000u, 0x0E000000u, 0x0F000000u};   // epoch, loss, histogram pass
+    CK(launch_sample(pk.args(), tags[stream_id], pk.scratch, c->stream), "sample");
     CK(cudaMemcpyAsync(host_out, pk.scratch, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, c->stream),
        "copy samples");
     CK(cudaStreamSynchronize(c->stream), "synchronize");

@@ -33,6 +33,7 @@ __device__ __forceinline__ int32_t draw_vertex(uint32_t r, uint32_t n) { return 
 constexpr uint32_t kTagInit = 0x0A000000u;
 constexpr uint32_t kTagEpoch = 0x0B000000u;
 constexpr uint32_t kTagLoss = 0x0E000000u;
+constexpr uint32_t kTagSlope = 0x0F000000u;   // the separate histogram pass of the slope fit
 
 // --------------------------------------------------------------------------
 // Exact edge set: open addressing over 64-bit keys (i << 32 | j), buckets of

@@ -130,6 +130,8 @@ struct EpochArgs {
     int32_t sweep_samples;           // 0: the sweep leaves the sampled non-edges to the tile kernel
     // update
     int32_t sigma_every;
+    int32_t sigma_source;     // 0: histograms from the sweep; 1: a separate pass after the update (Sec. III.F)
+    int32_t sweep_hist;       // 1: the sweep kernels bin their distances
     float z_min, hist_max;
     const struct MillsCoef* mills;   // Mills-ratio table on this device
 };
@@ -155,6 +157,10 @@ int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int 
 bool sweep_lanes_supported(int d, int lanes);
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t prepare_update_kernels(int bins);   // shared-memory size of the slope-fit blocks
+// sigma_source 1: the separate histogram pass at the updated positions, then
+// the per-graph slope fits on it
+cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s);
+cudaError_t launch_fit_graphs(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);   // k per vertex, or one per slot
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,

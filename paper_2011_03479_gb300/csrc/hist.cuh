@@ -62,12 +62,14 @@ __device__ __forceinline__ void hist_merge(const BlockHist& h, const EpochArgs& 
 // samples weighs (n-1-deg)/(2 k_acc): added as a float.
 __device__ __forceinline__ void hist_sample_w(const BlockHist& h, const EpochArgs& a, int graph, int bin, int deg,
                                               int k_acc) {
+    if (!a.sweep_hist) return;
     const float w = (float)(__ldg(&a.graphs[graph].n) - 1 - deg) / (2.0f * (float)k_acc);
     if (graph == h.home) atomicAdd(h.hw + bin, w);
     else atomicAdd(a.hist_x + (size_t)graph * a.bins + bin, w);
 }
 
 __device__ __forceinline__ void hist_edge(const BlockHist& h, const EpochArgs& a, int graph, int bin) {
+    if (!a.sweep_hist) return;
     if (graph == h.home) atomicAdd(h.he + bin, 1u);
     else atomicAdd(a.hist_e + (size_t)graph * a.bins + bin, 1u);
 }
@@ -75,6 +77,7 @@ __device__ __forceinline__ void hist_edge(const BlockHist& h, const EpochArgs& a
 // k_slots: sample slots per vertex (k, or the block partner count)
 __device__ __forceinline__ void hist_sample(const BlockHist& h, const EpochArgs& a, int graph, int bin, int deg,
                                             int k_acc, int k_slots) {
+    if (!a.sweep_hist) return;
     if (graph == h.home) {
         atomicAdd(h.hc + bin, 1u);
         atomicAdd(h.hd + bin, (unsigned int)deg);

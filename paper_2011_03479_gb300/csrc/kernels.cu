@@ -925,7 +925,8 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
         GraphState* st = a.gst + graph;
         const size_t off = (size_t)graph * a.bins;
         const int epoch = st->epoch;
-        if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0) {
+        // sigma_source 1: the fit follows in k_fit_graphs on the separate pass's histograms
+        if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0 && a.sigma_source == 0) {
             const int k_slots = a.block_P > 0 ? kBlockP : a.k;
             load_mills_smem(s_tab);
             load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);
@@ -1047,6 +1048,105 @@ __global__ void __launch_bounds__(kUpdateThreads) k_fit_sigma(const float* hist,
     __syncthreads();
     const float s = block_fit_sigma(s_bins, s_bins + bins, bins, hist_max, mu, 1.0f, s_tab, sm);
     if (threadIdx.x == 0) *sigma = s;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. III.F's separate histogram pass (sigma_source 1), after the update:
+// every edge once and k fresh samples per vertex (stream kTagSlope, drawn for
+// the epoch just completed) at the new positions.  One block per vertex
+// chunk, a warp per vertex, G lanes per pair; shared bins per chunk, merged
+// into the chunk's graph.
+// ---------------------------------------------------------------------------
+template <int D, int G>
+__global__ void __launch_bounds__(256) k_hist_pass(const EpochArgs a) {
+    constexpr int P = D / G;
+    constexpr int PAIRS = 32 / G;
+    extern __shared__ unsigned int s_u32[];
+    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
+    const int wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < a.n_vchunks; c += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + c);
+        const int graph = ch.z;
+        const BlockHist hist = block_hist(s_u32, a.bins, graph);
+        __syncthreads();   // the previous chunk's bins are merged
+        hist_clear(hist, a.bins);
+        __syncthreads();
+        const GraphInfo gi = load_graph(a, graph);
+        const int epoch = a.gst[graph].epoch - 1;   // the epoch just completed
+        for (int vi = wib; vi < ch.y; vi += wpb) {
+            const int i = ch.x + vi;
+            const int e0 = __ldg(a.row_ptr + i);
+            const int deg = __ldg(a.row_ptr + i + 1) - e0;
+            float xi[P];
+            load_chunk<D, P>(a.x, i, gl, xi);
+            int g_mine = -1;
+            unsigned rej = 0;
+            if (lane < a.k) {
+                const int g = sample_partner(gi, a.keys, a.max_retries, i - gi.v0, epoch, lane, kTagSlope, rej);
+                g_mine = g >= 0 ? gi.v0 + g : -1;
+            }
+            const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
+            const int total = deg + a.k;
+            for (int base = 0; base < total; base += PAIRS) {
+                const int q = base + grp;
+                const bool is_edge = q < deg;
+                const int sidx = q - deg;
+                const int gs = __shfl_sync(kFull, g_mine, (sidx >= 0 && sidx < 32) ? sidx : 0);
+                int j = -1;
+                if (q < total) j = is_edge ? __ldg(a.col_idx + e0 + q) : gs;
+                const bool valid = (q < total) && j >= 0 && (!is_edge || j > i);
+                float xj[P];
+                if (valid) {
+                    load_chunk<D, P>(a.x, j, gl, xj);
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < P; ++cc) xj[cc] = xi[cc];
+                }
+                float ss = 0.0f;
+#pragma unroll
+                for (int cc = 0; cc < P; ++cc) {
+                    const float df = xi[cc] - xj[cc];
+                    ss = fmaf(df, df, ss);
+                }
+#pragma unroll
+                for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+                if (valid && gl == 0) {
+                    const int bin = min((int)(sqrtf(ss) * a.hist_scale), a.bins - 1);
+                    if (is_edge) hist_edge(hist, a, graph, bin);
+                    else hist_sample(hist, a, graph, bin, deg, k_acc, a.k);
+                }
+            }
+        }
+        __syncthreads();
+        hist_merge(hist, a);
+    }
+}
+
+// The slope fits of the stepped graphs on the separate pass's histograms
+// (one block per graph; the epoch counter has already advanced).
+__global__ void __launch_bounds__(kUpdateThreads) k_fit_graphs(const EpochArgs a) {
+    __shared__ SigmaSmem sm;
+    extern __shared__ __align__(16) float s_bins[];   // [2][bins], then the Mills table
+    MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
+                                                    ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
+    const int graph = a.active[blockIdx.x];
+    GraphState* st = a.gst + graph;
+    const size_t off = (size_t)graph * a.bins;
+    if (a.sigma_every > 0 && (st->epoch % a.sigma_every) == 0) {
+        load_mills_smem(s_tab);
+        load_hist_smem(a, off, __ldg(&a.graphs[graph].n), a.k, s_bins, s_bins + a.bins);
+        const float s = block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, st->sigma, s_tab, sm);
+        if (threadIdx.x == 0) {
+            st->sigma = s;
+            st->sigma_iters = sm.iters;
+        }
+    }
+    for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
+        a.hist_e[off + t] = 0u;
+        a.hist_c[off + t] = 0u;
+        a.hist_d[off + t] = 0ull;
+        a.hist_x[off + t] = 0.0f;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1334,7 +1434,35 @@ cudaError_t prepare_update_kernels(int bins) {
     const int smem = (int)fit_smem_bytes(bins);
     cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_graphs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
+}
+
+template <int D, int G>
+cudaError_t hist_pass_for(const EpochArgs& a, int grid, cudaStream_t s) {
+    EpochArgs b = a;
+    b.sweep_hist = 1;          // this pass bins its own distances
+    b.per_slot = 0;            // with the integer sample weights of k samples per vertex
+    k_hist_pass<D, G><<<grid, 256, hist_smem_bytes(a.bins), s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s) {
+    int grid = a.n_vchunks;
+    if (grid > 4096) grid = 4096;
+    if (grid < 1) grid = 1;
+    switch (a.d) {
+#define GEMPE_CASE(D, G) \
+    case D: return hist_pass_for<D, G>(a, grid, s);
+        GEMPE_LOSS_DIMS(GEMPE_CASE)
+#undef GEMPE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fit_graphs(const EpochArgs& a, cudaStream_t s) {
+    k_fit_graphs<<<a.n_active, kUpdateThreads, fit_smem_bytes(a.bins), s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {

@@ -55,6 +55,8 @@ gempe_status check_params(const gempe_params* p, int32_t d) {
         return pack_fail(GEMPE_E_INVALID_ARG, "block sampling needs d >= 8 and tile_vertices 128");
     if (p->autotune != 0 && p->autotune != 1) return pack_fail(GEMPE_E_INVALID_ARG, "autotune must be 0 or 1");
     if (p->sampling != 0 && p->sampling != 1) return pack_fail(GEMPE_E_INVALID_ARG, "sampling must be 0 or 1");
+    if (p->sigma_source != 0 && p->sigma_source != 1)
+        return pack_fail(GEMPE_E_INVALID_ARG, "sigma_source must be 0 or 1");
     if (p->sampling == 1 && p->block_partners)
         return pack_fail(GEMPE_E_INVALID_ARG, "the per-slot sampling policy excludes block sampling");
     return GEMPE_OK;
@@ -543,6 +545,8 @@ EpochArgs Pack::args() const {
     a.n_tile_items = n_tile_items;
     a.sweep_samples = tiles ? 0 : 1;
     a.sigma_every = p.sigma_every;
+    a.sigma_source = p.sigma_source;
+    a.sweep_hist = p.sigma_source == 0 ? 1 : 0;
     a.z_min = p.z_min;
     a.hist_max = p.hist_max;
     a.mills = mills;
@@ -587,6 +591,10 @@ gempe_status Pack::enqueue_sweep() {
 // The position update and slope fits, then the join with the side stream.
 gempe_status Pack::enqueue_update() {
     PK(launch_update(args(), update_grid, stream), "update");
+    if (p.sigma_source == 1 && p.sigma_every > 0) {
+        PK(launch_hist_pass(args(), stream), "histogram pass");
+        PK(launch_fit_graphs(args(), stream), "slope fit");
+    }
     if (sampled_ahead) {
         PK(cudaStreamWaitEvent(stream, join_ev, 0), "join");
         sampled_ahead = false;
