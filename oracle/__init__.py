@@ -58,7 +58,9 @@ def _load():
         "orc_sample": (None, [_i32p, _i32p, I32, I32, U64, I32, I32, I32, _i32p]),
         "orc_epoch": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
                                  I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
-                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32]),
+                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32, I32, I32, I32]),
+        "orc_bytemap_addr": (None, [I32, U64, I32, I32, _i32p, I64, _c.POINTER(_c.c_uint32),
+                                    _c.POINTER(_c.c_uint32)]),
         "orc_block_partners": (None, [I32, I32, I32, U64, I32, _i32p]),
         "orc_edge_terms_edgelist": (None, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, I32,
                                            _f64p, _f64p]),
@@ -73,7 +75,8 @@ def _load():
         "orc_sigma_fit_exact": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, F64, I32]),
         "orc_loss_sampled": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32]),
         "orc_run": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, _c.POINTER(F64), F64, I32, I32,
-                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32, I32]),
+                               U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32, I32,
+                               I32, I32, I32]),
         "orc_hist_pass": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, I32, U64, I32, I32, I32, F64, _f64p, _f64p]),
     }
     for name, (res, args) in sig.items():
@@ -153,7 +156,8 @@ def block_partners(n, tile, epoch_idx, seed, P):
 
 def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES,
           symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
-          hist_max=HIST_MAX, block_partners=0, tile_vertices=128, per_slot=0):
+          hist_max=HIST_MAX, block_partners=0, tile_vertices=128, per_slot=0, membership=0, bytemap_log2=24,
+          rename_every=0):
     """One epoch of Fig. 4; returns a dict of FP64 results.  ``abs_terms[i]`` is the
     sum of the sizes of the pair terms of y_i - z_i x_i (the scale of that sum's
     rounding when its terms cancel).  per_slot=1: Sec. III.C's policy, one
@@ -165,19 +169,20 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
     y = np.zeros((n, d)); z = np.zeros(n); xn = np.zeros((n, d))
     he = np.zeros(hist_bins); hn = np.zeros(hist_bins)
     smp = np.zeros(max(nnz, 1) if per_slot else n * max(k, 1), dtype=np.int32)
-    st = np.zeros(4, dtype=np.int64)
+    st = np.zeros(5, dtype=np.int64)
     absd = np.zeros(n)
     n_tiles = (n + tile_vertices - 1) // tile_vertices
     parts = np.zeros(max(1, n_tiles * block_partners), dtype=np.int32)
     rc = _load().orc_epoch(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
                            max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
                            hist_max, y, z, xn, he, hn, smp, st, absd, block_partners,
-                           tile_vertices, parts, per_slot)
+                           tile_vertices, parts, per_slot, membership, bytemap_log2, rename_every)
     if rc != 0:
         raise MemoryError("oracle epoch failed")
     samples = smp[:nnz] if per_slot else smp[: n * k].reshape(n, k)
     return dict(y=y, z=z, x_new=xn, hist_e=he, hist_n=hn, samples=samples,
                 accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]), draws=int(st[3]),
+                false_pos=int(st[4]),
                 delta=y - z[:, None] * x, abs_terms=absd,
                 partners=parts[: n_tiles * block_partners].reshape(n_tiles, block_partners)
                 if block_partners else None)
@@ -236,6 +241,16 @@ def sigma_fit_exact(row_ptr, col_idx, x, mu=MU, lo=1e-3, hi=1e3, iters=60):
                                        lo, hi, iters)
 
 
+def bytemap_addr(n, seed, period, log2_size, pairs):
+    """Byte-map addresses of (i, j) pairs under the renaming of `period`, and (a, b) of that renaming."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(pairs), dtype=np.uint32)
+    ab = np.zeros(2, dtype=np.uint32)
+    _load().orc_bytemap_addr(n, seed, period, log2_size, pairs.ravel(), len(pairs),
+                             out.ctypes.data_as(_c.POINTER(_c.c_uint32)), ab.ctypes.data_as(_c.POINTER(_c.c_uint32)))
+    return out, (int(ab[0]), int(ab[1]))
+
+
 def hist_pass(row_ptr, col_idx, x, epoch_idx, seed, k, max_retries=MAX_RETRIES, hist_bins=HIST_BINS,
               hist_max=HIST_MAX):
     """Sec. III.F's separate histogram pass: all edges and k fresh samples per vertex at x."""
@@ -257,15 +272,17 @@ def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retr
 
 def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retries=MAX_RETRIES,
         symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
-        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0, sigma_source=0):
+        hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0, sigma_source=0, membership=0,
+        bytemap_log2=24, rename_every=0):
     """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats)."""
     n = len(row_ptr) - 1
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     s = ctypes.c_double(sigma)
-    st = np.zeros(4, dtype=np.int64)
+    st = np.zeros(5, dtype=np.int64)
     rc = _load().orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
                          epoch0, epochs, seed, k, max_retries, symmetric, w_formula, clamp_neg_d,
-                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot, sigma_source)
+                         z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot, sigma_source,
+                         membership, bytemap_log2, rename_every)
     if rc != 0:
         raise MemoryError("oracle run failed")
-    return x, s.value, dict(accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]))
+    return x, s.value, dict(accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]), false_pos=int(st[4]))

@@ -60,6 +60,8 @@
  *                      policy: one sample per CSR slot e, anchored at its row)
  *   slope samples      (i, epoch, t, 0x0F000000|a>>2) -> word a&3 (the separate
  *                      histogram pass of Sec. III.F)
+ *   renaming           (period, 0, 0, 0x09000000)     -> words 0, 1 (byte-map
+ *                      membership, Sec. III.C)
  * A 32-bit word r maps to vertex floor(r * n / 2^32).
  *
  * Block sampling (the representation-learning form): vertices are cut into
@@ -249,23 +251,108 @@ static int32_t hist_bin(double delta, int32_t B, double hist_max) {
     return (int32_t)f;
 }
 
+/* ------------------------------------------------------------------ */
+/* Sec. III.C's lossy membership test (the byte map)                    */
+/* ------------------------------------------------------------------ */
+/* A byte map of s = 2^b entries marks, for every edge (i, j), the address
+ *   hash(i', j') = ((i' * n + j') * 1103515245) & (s - 1)
+ * computed in 32-bit arithmetic with wrap-around (as printed), on the names
+ * i' = pi(i), j' = pi(j) of the current random renaming.  A draw is taken
+ * for an edge when its address is marked: no edge is missed, a non-edge
+ * whose address collides with an edge's is rejected like an edge.
+ * Renaming (redrawn every `rename_every` sample epochs, period
+ * r = epoch / rename_every, r = 0 throughout when rename_every = 0):
+ * pi(v) = (a v + b) mod n with a = 1 + (w0 mod (n-1)) stepped up to the next
+ * value coprime to n and b = w1 mod n, (w0, w1) the first two words of
+ * Philox counter (r, 0, 0, 0x09000000). */
+typedef struct {
+    uint8_t* map;
+    uint32_t mask, n, a, b;
+    int32_t period;
+} orc_bytemap;
+
+static uint32_t gcd_u32(uint32_t x, uint32_t y) {
+    while (y) { uint32_t t = x % y; x = y; y = t; }
+    return x;
+}
+
+static void bytemap_perm(uint64_t seed, int32_t period, uint32_t n, uint32_t* a, uint32_t* b) {
+    uint32_t w0 = philox_word(seed, (uint32_t)period, 0u, 0u, 0x09000000u, 0);
+    uint32_t w1 = philox_word(seed, (uint32_t)period, 0u, 0u, 0x09000000u, 1);
+    uint32_t aa = 1u + (n > 1 ? w0 % (n - 1) : 0u);
+    while (gcd_u32(aa, n) != 1u) aa = (aa + 1u >= n) ? 1u : aa + 1u;
+    *a = aa;
+    *b = w1 % n;
+}
+
+static uint32_t bytemap_name(const orc_bytemap* m, uint32_t v) {
+    return (uint32_t)(((uint64_t)m->a * v + m->b) % m->n);
+}
+
+static uint32_t bytemap_addr(const orc_bytemap* m, uint32_t i, uint32_t j) {
+    uint32_t ii = bytemap_name(m, i), jj = bytemap_name(m, j);
+    return ((ii * m->n + jj) * 1103515245u) & m->mask;
+}
+
+/* (Re)build the map for the renaming of `period`. */
+static void bytemap_build(orc_bytemap* m, const int32_t* row_ptr, const int32_t* col_idx, int32_t n,
+                          uint64_t seed, int32_t period) {
+    memset(m->map, 0, (size_t)m->mask + 1);
+    m->n = (uint32_t)n;
+    bytemap_perm(seed, period, (uint32_t)n, &m->a, &m->b);
+    m->period = period;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            m->map[bytemap_addr(m, (uint32_t)i, (uint32_t)col_idx[e])] = 1;
+}
+
+/* Membership as the sampler sees it: exact (m == NULL) or the byte map. */
+static int sampler_is_edge(const orc_bytemap* m, const int32_t* row_ptr, const int32_t* col_idx, int32_t i,
+                           int32_t g, int64_t* false_pos) {
+    if (!m) return orc_is_edge(row_ptr, col_idx, i, g);
+    int marked = m->map[bytemap_addr(m, (uint32_t)i, (uint32_t)g)] != 0;
+    if (marked && false_pos && !orc_is_edge(row_ptr, col_idx, i, g)) ++*false_pos;
+    return marked;
+}
+
 /* Accepted non-edge partners of vertex i for sample slots t = 0..k-1
- * (g or -1 when all attempts hit an edge or i itself). */
-static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
-                          int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
-                          int32_t* out, int64_t* rejected, int64_t* exhausted) {
+ * (g or -1 when all attempts hit an edge or i itself); bm: NULL for the
+ * exact membership test, else the byte map. */
+static void sample_vertex_bm(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
+                             int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
+                             const orc_bytemap* bm, int32_t* out, int64_t* rejected, int64_t* exhausted,
+                             int64_t* false_pos) {
     for (int32_t t = 0; t < k; ++t) {
         int32_t got = -1;
         for (int32_t a = 0; a < max_retries; ++a) {
             uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t,
                                      tag | ((uint32_t)a >> 2), a & 3);
             int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
-            if (g != i && !orc_is_edge(row_ptr, col_idx, i, g)) { got = g; break; }
+            if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;
         }
         if (got < 0 && exhausted) ++*exhausted;
         out[t] = got;
     }
+}
+
+static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
+                          int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
+                          int32_t* out, int64_t* rejected, int64_t* exhausted) {
+    sample_vertex_bm(row_ptr, col_idx, n, i, epoch, seed, tag, k, max_retries, NULL, out, rejected, exhausted,
+                     NULL);
+}
+
+/* Byte-map addresses of pairs under the renaming of `period` (inspection). */
+void orc_bytemap_addr(int32_t n, uint64_t seed, int32_t period, int32_t log2_size, const int32_t* pairs,
+                      int64_t count, uint32_t* out, uint32_t* perm_ab) {
+    orc_bytemap m;
+    m.map = NULL;
+    m.mask = (uint32_t)((1ull << log2_size) - 1ull);
+    m.n = (uint32_t)n;
+    bytemap_perm(seed, period, (uint32_t)n, &m.a, &m.b);
+    if (perm_ab) { perm_ab[0] = m.a; perm_ab[1] = m.b; }
+    for (int64_t q = 0; q < count; ++q) out[q] = bytemap_addr(&m, (uint32_t)pairs[2 * q], (uint32_t)pairs[2 * q + 1]);
 }
 
 /* Sec. III.C's policy: every CSR slot e = (i, j) of row i carries one
@@ -274,14 +361,14 @@ static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_
  * hits i or an edge, at most max_retries times.  out[t]: the partner of slot
  * row_ptr[i] + t, or -1. */
 static void sample_slots(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
-                         int32_t epoch, uint64_t seed, int32_t max_retries, int32_t* out,
-                         int64_t* rejected, int64_t* exhausted) {
+                         int32_t epoch, uint64_t seed, int32_t max_retries, const orc_bytemap* bm, int32_t* out,
+                         int64_t* rejected, int64_t* exhausted, int64_t* false_pos) {
     for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int32_t got = -1;
         for (int32_t a = 0; a < max_retries; ++a) {
             uint32_t r = philox_word(seed, (uint32_t)e, (uint32_t)epoch, 0u, 0x0C000000u | ((uint32_t)a >> 2), a & 3);
             int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
-            if (g != i && !orc_is_edge(row_ptr, col_idx, i, g)) { got = g; break; }
+            if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;
         }
         if (got < 0 && exhausted) ++*exhausted;
@@ -314,15 +401,28 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
               double* y, double* z, double* x_new, double* hist_e, double* hist_n,
               int32_t* samples_out, int64_t* stats, double* absd,
-              int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot) {
+              int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
+              int32_t membership, int32_t bytemap_log2, int32_t rename_every) {
     /* block sampling or the per-slot policy replace the k per-vertex samples */
     if (block_P > 0) { k = 0; per_slot = 0; }
+    /* membership 1: the sampler tests pairs against the byte map of the
+     * renaming period of this epoch */
+    orc_bytemap bm;
+    orc_bytemap* bmp = NULL;
+    if (membership == 1 && block_P == 0) {
+        bm.mask = (uint32_t)((1ull << bytemap_log2) - 1ull);
+        bm.map = (uint8_t*)malloc((size_t)bm.mask + 1);
+        if (!bm.map) return -1;
+        bytemap_build(&bm, row_ptr, col_idx, n, seed, rename_every > 0 ? epoch / rename_every : 0);
+        bmp = &bm;
+    }
+    int64_t false_pos = 0;
     int32_t smp_cap = k > 0 ? k : 1;
     if (per_slot)
         for (int32_t i = 0; i < n; ++i) smp_cap = (row_ptr[i + 1] - row_ptr[i] > smp_cap) ? row_ptr[i + 1] - row_ptr[i] : smp_cap;
     int32_t* smp = (int32_t*)malloc((size_t)smp_cap * sizeof(int32_t));
     int32_t* part = (int32_t*)malloc((size_t)(block_P > 0 ? block_P : 1) * sizeof(int32_t));
-    if (!smp || !part) { free(smp); free(part); return -1; }
+    if (!smp || !part) { free(smp); free(part); if (bmp) free(bm.map); return -1; }
     g_absd = absd;
     if (absd) memset(absd, 0, sizeof(double) * (size_t)n);
     memset(y, 0, sizeof(double) * (size_t)n * d);          /* zero numerators ... */
@@ -343,10 +443,11 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
         int32_t ki = k;
         if (per_slot) {
             ki = row_ptr[i + 1] - row_ptr[i];
-            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, smp, &rejected, &exhausted);
+            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, bmp, smp, &rejected, &exhausted,
+                         &false_pos);
         } else {
-            sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp,
-                          &rejected, &exhausted);
+            sample_vertex_bm(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, bmp, smp,
+                             &rejected, &exhausted, &false_pos);
         }
         int32_t acc = 0;
         for (int32_t t = 0; t < ki; ++t) acc += (smp[t] >= 0);
@@ -395,10 +496,17 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
         for (int32_t c = 0; c < d; ++c)
             x_new[(int64_t)i * d + c] = (z[i] >= z_min) ? y[(int64_t)i * d + c] / z[i]
                                                          : x[(int64_t)i * d + c];
-    if (stats) { stats[0] = accepted; stats[1] = rejected; stats[2] = exhausted; stats[3] = accepted + rejected; }
+    if (stats) {
+        stats[0] = accepted;
+        stats[1] = rejected;
+        stats[2] = exhausted;
+        stats[3] = accepted + rejected;
+        stats[4] = false_pos;
+    }
     g_absd = NULL;
     free(smp);
     free(part);
+    if (bmp) free(bm.map);
     return 0;
 }
 
@@ -594,7 +702,8 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
             double* x, double* sigma, double mu, int32_t epoch0, int32_t epochs, uint64_t seed,
             int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
             double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats,
-            int32_t block_P, int32_t block_T, int32_t per_slot, int32_t sigma_source) {
+            int32_t block_P, int32_t block_T, int32_t per_slot, int32_t sigma_source, int32_t membership,
+            int32_t bytemap_log2, int32_t rename_every) {
     size_t nd = (size_t)n * d;
     double* y = (double*)malloc(nd * sizeof(double));
     double* z = (double*)malloc((size_t)n * sizeof(double));
@@ -602,13 +711,13 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
     double* he = (double*)malloc((size_t)B * sizeof(double));
     double* hn = (double*)malloc((size_t)B * sizeof(double));
     if (!y || !z || !xn || !he || !hn) { free(y); free(z); free(xn); free(he); free(hn); return -1; }
-    int64_t st[4];
-    if (stats) memset(stats, 0, 4 * sizeof(int64_t));
+    int64_t st[5];
+    if (stats) memset(stats, 0, 5 * sizeof(int64_t));
     for (int32_t e = 0; e < epochs; ++e) {
         int32_t ep = epoch0 + e;
         orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
                   w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL,
-                  block_P, block_T, NULL, per_slot);
+                  block_P, block_T, NULL, per_slot, membership, bytemap_log2, rename_every);
         memcpy(x, xn, nd * sizeof(double));
         if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0) {
             /* sigma_source 1: histograms of a separate pass at the new positions */
@@ -617,7 +726,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
                 break;
             *sigma = orc_sigma_fit(he, hn, B, hist_max, mu, 1e-3, 1e3, 60);
         }
-        if (stats) for (int q = 0; q < 4; ++q) stats[q] += st[q];
+        if (stats) for (int q = 0; q < 5; ++q) stats[q] += st[q];
     }
     free(y); free(z); free(xn); free(he); free(hn);
     return 0;

@@ -560,3 +560,54 @@ def test_separate_histogram_pass(oracle_mod, sbm_small):
     r = oracle_mod.epoch(rp, ci, xr, sr, 2, 5, 4)
     he2, hn2 = oracle_mod.hist_pass(rp, ci, r["x_new"], 2, 5, 4)
     assert oracle_mod.sigma_fit(he2, hn2, 12.0, MU) == pytest.approx(sa, rel=1e-12)
+
+
+def test_bytemap_membership(oracle_mod, sbm_small):
+    """Sec. III.C's lossy membership test.  The renaming is a bijection; with
+    a map large enough that the low bits of (i' n + j') never collide the
+    byte map is exact (the samples equal the exact test's); with a small map
+    no edge is ever accepted, colliding non-edges are rejected, and those
+    false positives are what the count reports."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    adj = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(n)]
+    for period in (0, 1, 7):
+        _, (a, b) = oracle_mod.bytemap_addr(n, 33, period, 12, [[0, 1]])
+        assert math.gcd(a, n) == 1 and 1 <= a < n and 0 <= b < n
+        assert sorted((a * v + b) % n for v in range(n)) == list(range(n))
+    x = np.random.default_rng(5).normal(size=(n, 2))
+    exact = oracle_mod.epoch(rp, ci, x, 0.8, 4, 33, 6)
+    big = oracle_mod.epoch(rp, ci, x, 0.8, 4, 33, 6, membership=1, bytemap_log2=20)
+    np.testing.assert_array_equal(big["samples"], exact["samples"])
+    assert big["false_pos"] == 0
+    small = oracle_mod.epoch(rp, ci, x, 0.8, 4, 33, 6, membership=1, bytemap_log2=8)
+    smp = small["samples"]
+    assert small["false_pos"] > 0
+    for i in range(n):
+        for g in smp[i]:
+            if g >= 0:
+                assert g != i and g not in adj[i]
+    # replay the draws: a draw is rejected when it is i, an edge, or a pair
+    # whose address is marked by some edge; the collisions are the false positives
+    pairs = [(i, j) for i in range(n) for j in adj[i]]
+    marked = set(oracle_mod.bytemap_addr(n, 33, 0, 8, pairs)[0].tolist())
+    key = [33, 0]
+    fp = rej = 0
+    for i in range(n):
+        for t in range(6):
+            for att in range(32):
+                w = int(oracle_mod.philox4x32_10([i, 4, t, 0x0B000000 | (att >> 2)], key)[att & 3])
+                g = (w * n) >> 32
+                addr = int(oracle_mod.bytemap_addr(n, 33, 0, 8, [[i, g]])[0][0])
+                if g != i and addr not in marked:
+                    assert smp[i, t] == g
+                    break
+                rej += 1
+                fp += int(g != i and g not in adj[i])
+    assert small["rejected"] == rej and small["false_pos"] == fp
+    # renaming every 2 epochs: epochs 4 and 5 share a renaming, epoch 6 does not
+    r4 = oracle_mod.epoch(rp, ci, x, 0.8, 4, 33, 6, membership=1, bytemap_log2=8, rename_every=2)
+    assert r4["false_pos"] != small["false_pos"] or not np.array_equal(r4["samples"], smp)
+    _, ab2 = oracle_mod.bytemap_addr(n, 33, 2, 8, [[0, 1]])
+    _, ab3 = oracle_mod.bytemap_addr(n, 33, 3, 8, [[0, 1]])
+    assert ab2 != ab3
