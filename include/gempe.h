@@ -84,6 +84,19 @@ typedef struct gempe_params {
     int32_t autotune;       /* 1: time the sweep's launch shapes (units, lanes per pair, CTAs per
                                SM) on the graph at create and keep the fastest; 0: fixed defaults.
                                Only the launch shape changes, never the arithmetic of a pair */
+    int32_t membership;     /* how the sampler tells edges from non-edges (Sec. III.C, Fig. 2):
+                               0: the exact edge set; 1: the paper's byte map -- s = 2^bytemap_log2
+                               bytes, edge (i, j) marks ((pi(i) n + pi(j)) * 1103515245) & (s - 1)
+                               (32-bit wrap), a draw whose address is marked is redrawn, so
+                               non-edges that collide with an edge are lost (counted in
+                               gempe_stats_t.false_pos); not with block sampling.  The loss
+                               estimator always uses the exact set */
+    int32_t bytemap_log2;   /* log2 s, 6..32; 0: nnz rounded up to a power of two times 128,
+                               clamped to [2^12, 2^30] */
+    int32_t rename_every;   /* the random renaming pi(v) = (alpha v + beta) mod n (alpha coprime
+                               to n, drawn from counter (period, 0, 0, 0x09000000)) is redrawn and
+                               the map rebuilt every rename_every epochs (period = sample epoch /
+                               rename_every); 0: one renaming for the whole run */
     /* Optional device allocator (e.g. a framework's caching allocator).  When
      * dev_alloc is null the engine uses cudaMalloc / cudaFree. */
     void* (*dev_alloc)(size_t bytes, void* user);
@@ -102,6 +115,7 @@ typedef struct gempe_stats_t {
     int64_t n_edges;               /* m, undirected */
     int32_t n, d, k;
     int32_t sigma_iters;           /* root-finding steps of the last slope fit */
+    uint64_t false_pos;            /* byte-map membership: rejected draws that are not edges */
 } gempe_stats_t;
 
 typedef struct gempe_ctx gempe_ctx;
@@ -109,7 +123,8 @@ typedef struct gempe_ctx gempe_ctx;
 /* Fill *p with the defaults: mu 1.5, sigma0 1, sigma_every 1, k 5, max_retries
  * 32, symmetric 1, derived w, clamp 1, z_min 1e-30, init_range 1, seed
  * 0x6E6D7065, 1024 bins on [0, 12), FP32, per-vertex sampling (tile size
- * 128 for block sampling), no autotuning, no custom allocator. */
+ * 128 for block sampling), no autotuning, the exact membership test, no
+ * custom allocator. */
 void gempe_default_params(gempe_params* p);
 
 /* Create an embedding context from a host CSR graph (Sec. II.A: G, n, d).

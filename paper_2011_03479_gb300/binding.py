@@ -48,6 +48,9 @@ class gempe_params(ctypes.Structure):
         ("sampling", ctypes.c_int32),
         ("sigma_source", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("membership", ctypes.c_int32),
+        ("bytemap_log2", ctypes.c_int32),
+        ("rename_every", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
@@ -68,6 +71,7 @@ class gempe_stats_t(ctypes.Structure):
         ("d", ctypes.c_int32),
         ("k", ctypes.c_int32),
         ("sigma_iters", ctypes.c_int32),
+        ("false_pos", ctypes.c_uint64),
     ]
 
 

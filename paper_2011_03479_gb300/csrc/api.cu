@@ -550,6 +550,7 @@ GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
     out->d = pk.d;
     out->k = pk.k;
     out->sigma_iters = h.sigma_iters;
+    out->false_pos = h.false_pos;
     return GEMPE_OK;
 }
 

@@ -241,6 +241,7 @@ GEMPE_API gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_st
     out->d = pk->d;
     out->k = pk->k;
     out->sigma_iters = h.sigma_iters;
+    out->false_pos = h.false_pos;
     return GEMPE_OK;
 }
 

@@ -34,6 +34,7 @@ constexpr uint32_t kTagInit = 0x0A000000u;
 constexpr uint32_t kTagEpoch = 0x0B000000u;
 constexpr uint32_t kTagLoss = 0x0E000000u;
 constexpr uint32_t kTagSlope = 0x0F000000u;   // the separate histogram pass of the slope fit
+constexpr uint32_t kTagRename = 0x09000000u;  // the byte map's random renaming (Sec. III.C)
 
 // --------------------------------------------------------------------------
 // Exact edge set: open addressing over 64-bit keys (i << 32 | j), buckets of

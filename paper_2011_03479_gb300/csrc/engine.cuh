@@ -19,8 +19,7 @@
 namespace gempe {
 
 // Per-graph constants (read-only while an epoch runs).  48 bytes, 16-byte
-// aligned: the kernels read the first 40 bytes as one int4, one
-// ulonglong2 and one u64.
+// aligned: the kernels read them as one int4 and two ulonglong2.
 struct alignas(16) GraphInfo {
     int32_t v0;                       // first row of the graph in the pack
     int32_t n;                        // vertices
@@ -29,7 +28,8 @@ struct alignas(16) GraphInfo {
     uint32_t key_lo, key_hi;          // Philox key
     unsigned long long key_off;       // first slot of the graph's edge table
     unsigned long long bucket_mask;   // buckets - 1 of that table
-    unsigned long long reserved;
+    unsigned long long map;           // byte-map membership: offset of the graph's map in the pack's
+                                      // map array (a multiple of 64) | log2 of its size; 0 without
 };
 static_assert(sizeof(GraphInfo) == 48, "GraphInfo layout");
 
@@ -43,6 +43,9 @@ struct GraphState {
     unsigned long long accepted, rejected, exhausted, draws;   // sampler statistics
     unsigned long long used;    // sampled non-edges consumed by sweeps
     double loss_sum;
+    int32_t map_period;         // renaming period the byte map holds (-1: none yet)
+    int32_t pad;
+    unsigned long long false_pos;   // draws the byte map rejected that are not edges
 };
 
 // Pack-wide device scalars.
@@ -134,6 +137,11 @@ struct EpochArgs {
     int32_t sweep_hist;       // 1: the sweep kernels bin their distances
     float z_min, hist_max;
     const struct MillsCoef* mills;   // Mills-ratio table on this device
+    // byte-map membership (Sec. III.C): the sampler tests draws against the
+    // graph's byte map under the renaming of period sample_epoch / rename_every
+    int32_t membership;       // 0: the exact edge sets; 1: the byte maps
+    int32_t rename_every;     // 0: one renaming (period 0) for the whole run
+    uint8_t* bytemap;
 };
 
 int acc_stride_for(int d);
@@ -163,6 +171,9 @@ cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_fit_graphs(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_sample(const EpochArgs& a, uint32_t tag, int32_t* out, cudaStream_t s);
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s);   // k per vertex, or one per slot
+// Byte maps of the graphs whose map does not hold the renaming period of their
+// sample epoch (all graphs when force): cleared, then every edge marked.
+cudaError_t launch_bytemap_build(const EpochArgs& a, int force, int sm_count, cudaStream_t s);
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
                                  cudaStream_t s);
 cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s);

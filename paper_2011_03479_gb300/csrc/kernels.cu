@@ -147,47 +147,11 @@ __device__ __forceinline__ void acc_add(float* row, int gl, const float* v, floa
     }
 }
 
-// Draw the accepted partner (local id) of sample slot t of local vertex i of
-// a graph (Fig. 2: redraw while the pair is an edge; also redraw g == i), or
-// -1 after max_retries draws.
-__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
-                                              int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
-    const unsigned long long* table = keys + gi.key_off;
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    for (int att = 0; att < max_retries; ++att) {
-        if ((att & 3) == 0)
-            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
-                              gi.key_lo, gi.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
-        if (g != i && !hash_contains(table, gi.bucket_mask, edge_key(i, g))) return g;
-        ++rejected;
-    }
-    return -1;
-}
-
-// Sec. III.C's policy: the partner (local id) of CSR slot e_local of the
-// graph, anchored at local vertex i (the slot's row); counter
-// (e_local, epoch, 0, kTagSlot | attempt >> 2), -1 after max_retries draws.
-__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
-                                            int i, int e_local, int epoch, unsigned& rejected) {
-    const unsigned long long* table = keys + gi.key_off;
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    for (int att = 0; att < max_retries; ++att) {
-        if ((att & 3) == 0)
-            r = philox4x32_10(make_uint4((uint32_t)e_local, (uint32_t)epoch, 0u, kTagSlot | ((uint32_t)att >> 2)),
-                              gi.key_lo, gi.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
-        if (g != i && !hash_contains(table, gi.bucket_mask, edge_key(i, g))) return g;
-        ++rejected;
-    }
-    return -1;
-}
-
 __device__ __forceinline__ GraphInfo load_graph(const EpochArgs& a, int g) {
     GraphInfo gi;
     const int4 w0 = __ldg(reinterpret_cast<const int4*>(a.graphs + g));
     const ulonglong2 w1 = __ldg(reinterpret_cast<const ulonglong2*>(a.graphs + g) + 1);
-    const unsigned long long w2 = __ldg(reinterpret_cast<const unsigned long long*>(a.graphs + g) + 4);
+    const ulonglong2 w2 = __ldg(reinterpret_cast<const ulonglong2*>(a.graphs + g) + 2);
     gi.v0 = w0.x;
     gi.n = w0.y;
     gi.t0 = w0.z;
@@ -195,35 +159,151 @@ __device__ __forceinline__ GraphInfo load_graph(const EpochArgs& a, int g) {
     gi.key_lo = (uint32_t)w1.x;
     gi.key_hi = (uint32_t)(w1.x >> 32);
     gi.key_off = w1.y;
-    gi.bucket_mask = w2;
+    gi.bucket_mask = w2.x;
+    gi.map = w2.y;
     return gi;
 }
 
-// Sum of a per-thread counter triple over the block, added to a graph's
-// sampler statistics by thread 0 (all threads must call it).
-__device__ __forceinline__ void block_count3(unsigned (&v)[3], unsigned* s_cnt, GraphState* st) {
+// ---------------------------------------------------------------------------
+// Membership as the sampler sees it (Sec. III.C).  Exact: the graph's edge
+// hash set.  Byte map: a byte array of s = 2^b entries in which every edge
+// (i, j) marks address ((pi(i) n + pi(j)) * 1103515245) & (s - 1), in 32-bit
+// arithmetic with wrap-around, pi a random renaming pi(v) = (alpha v + beta)
+// mod n with alpha coprime to n; a draw whose address is marked is taken
+// for an edge.  No edge is missed; a non-edge that collides with an edge is
+// rejected too, and counted as a false positive against the exact set.
+// ---------------------------------------------------------------------------
+struct Membership {
+    const uint8_t* map;   // null: exact
+    uint32_t mask, n, alpha, beta;
+};
+
+__device__ __forceinline__ uint32_t gcd_u32(uint32_t x, uint32_t y) {
+    while (y != 0u) {
+        const uint32_t t = x % y;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+// The renaming of `period`: alpha = 1 + (w0 mod (n - 1)), stepped up (past
+// n - 1 back to 1) to the first value coprime to n, beta = w1 mod n, with
+// (w0, w1) the first two words of counter (period, 0, 0, kTagRename).
+__device__ __forceinline__ void renaming(uint32_t key_lo, uint32_t key_hi, int period, uint32_t n,
+                                         uint32_t& alpha, uint32_t& beta) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)period, 0u, 0u, kTagRename), key_lo, key_hi);
+    uint32_t al = 1u + (n > 1u ? r.x % (n - 1u) : 0u);
+    while (gcd_u32(al, n) != 1u) al = (al + 1u >= n) ? 1u : al + 1u;   // ends at alpha = 1 at the latest
+    alpha = al;
+    beta = r.y % n;
+}
+
+__device__ __forceinline__ int map_period_of(const EpochArgs& a, int sample_epoch) {
+    return a.rename_every > 0 ? sample_epoch / a.rename_every : 0;
+}
+
+__device__ __forceinline__ Membership membership_of(const EpochArgs& a, const GraphInfo& gi, int sample_epoch) {
+    Membership m{nullptr, 0u, (uint32_t)gi.n, 1u, 0u};
+    if (!a.membership) return m;
+    m.map = a.bytemap + (gi.map & ~63ull);
+    m.mask = (uint32_t)((1ull << (gi.map & 63ull)) - 1ull);
+    renaming(gi.key_lo, gi.key_hi, map_period_of(a, sample_epoch), m.n, m.alpha, m.beta);
+    return m;
+}
+
+__device__ __forceinline__ uint32_t renamed(const Membership& m, uint32_t v) {
+    return (uint32_t)(((unsigned long long)m.alpha * v + m.beta) % m.n);
+}
+
+__device__ __forceinline__ uint32_t map_address(const Membership& m, uint32_t name_i, uint32_t name_j) {
+    return ((name_i * m.n + name_j) * 1103515245u) & m.mask;
+}
+
+// Is the draw (i, g) taken for an edge?  name_i = pi(i) (byte map only).
+__device__ __forceinline__ bool taken_for_edge(const GraphInfo& gi, const unsigned long long* keys,
+                                               const Membership& m, uint32_t name_i, int i, int g,
+                                               unsigned& false_pos) {
+    const unsigned long long* table = keys + gi.key_off;
+    if (!m.map) return hash_contains(table, gi.bucket_mask, edge_key(i, g));
+    if (!__ldg(m.map + map_address(m, name_i, renamed(m, (uint32_t)g)))) return false;
+    if (!hash_contains(table, gi.bucket_mask, edge_key(i, g))) ++false_pos;
+    return true;
+}
+
+// Draw the accepted partner (local id) of sample slot t of local vertex i of
+// a graph (Fig. 2: redraw while the pair is taken for an edge; also redraw
+// g == i), or -1 after max_retries draws.
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+                                              int i, int epoch, int t, uint32_t tag, unsigned& rejected,
+                                              const Membership& m, unsigned& false_pos) {
+    const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    for (int att = 0; att < max_retries; ++att) {
+        if ((att & 3) == 0)
+            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
+                              gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
+        ++rejected;
+    }
+    return -1;
+}
+
+// The same with the exact edge set (loss, slope-pass and inspection draws).
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+                                              int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
+    unsigned unused = 0u;
+    const Membership exact{nullptr, 0u, (uint32_t)gi.n, 1u, 0u};
+    return sample_partner(gi, keys, max_retries, i, epoch, t, tag, rejected, exact, unused);
+}
+
+// Sec. III.C's policy: the partner (local id) of CSR slot e_local of the
+// graph, anchored at local vertex i (the slot's row); counter
+// (e_local, epoch, 0, kTagSlot | attempt >> 2), -1 after max_retries draws.
+__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+                                            int i, int e_local, int epoch, unsigned& rejected, const Membership& m,
+                                            unsigned& false_pos) {
+    const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    for (int att = 0; att < max_retries; ++att) {
+        if ((att & 3) == 0)
+            r = philox4x32_10(make_uint4((uint32_t)e_local, (uint32_t)epoch, 0u, kTagSlot | ((uint32_t)att >> 2)),
+                              gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
+        ++rejected;
+    }
+    return -1;
+}
+
+// Sum of the per-thread sampler counters {accepted, rejected, exhausted,
+// false positives} over the block, added to a graph's statistics by thread 0
+// (all threads must call it).
+__device__ __forceinline__ void block_count4(unsigned (&v)[4], unsigned* s_cnt, GraphState* st) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 4; ++q) {
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) v[q] += __shfl_xor_sync(kFull, v[q], o);
     }
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 4; ++q)
             if (v[q]) atomicAdd(&s_cnt[q], v[q]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned acc = s_cnt[0], rej = s_cnt[1], exh = s_cnt[2];
+        const unsigned acc = s_cnt[0], rej = s_cnt[1], exh = s_cnt[2], fp = s_cnt[3];
         if (acc) atomicAdd(&st->accepted, (unsigned long long)acc);
         if (rej) atomicAdd(&st->rejected, (unsigned long long)rej);
         if (exh) atomicAdd(&st->exhausted, (unsigned long long)exh);
+        if (fp) atomicAdd(&st->false_pos, (unsigned long long)fp);
         if (acc + rej) atomicAdd(&st->draws, (unsigned long long)(acc + rej));
-        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0u;
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 3; ++q) v[q] = 0u;
+    for (int q = 0; q < 4; ++q) v[q] = 0u;
 }
 
 // Sampler completion: the last block to finish advances every stepped
@@ -259,40 +339,91 @@ template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16
 // chunks (one graph each).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
-    __shared__ unsigned s_cnt[3];
-    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
+    __shared__ unsigned s_cnt[4];
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     constexpr int kSubs = kVChunk / kSamplerSub;
     const int n_sub = a.n_vchunks * kSubs;
     const int k = a.k;
-    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted of graph cur
-    int cur = -1;                   // block-uniform
+    unsigned c[4] = {0u, 0u, 0u, 0u};   // accepted, rejected, exhausted, false positives of graph cur
+    int cur = -1;                       // block-uniform
+    Membership m{nullptr, 0u, 0u, 1u, 0u};
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
         const int4 ch = __ldg(a.vchunks + s / kSubs);
         const int sub = s % kSubs;
         const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
         if (cnt <= 0) continue;   // uniform over the block
         const int graph = ch.z;
-        if (graph != cur) {
-            // the counts go to the graph's statistics once per run of pieces of one graph
-            if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
-            cur = graph;
-        }
         const GraphInfo gi = load_graph(a, graph);
         const int se = a.gst[graph].sample_epoch;
+        if (graph != cur) {
+            // the counts go to the graph's statistics once per run of pieces of one graph
+            if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
+            cur = graph;
+            m = membership_of(a, gi, se);
+            // the map holds this period now (the map builders, which read it, ran before)
+            if (a.membership && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
+        }
         const int row0 = ch.x + sub * kSamplerSub;
         const int local0 = row0 - gi.v0;
         int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0) * k;
         const int total = cnt * k;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int i = idx / k, t = idx - i * k;
-            const int g = sample_partner(gi, a.keys, a.max_retries, local0 + i, se, t, kTagEpoch, c[1]);
+            const int g = sample_partner(gi, a.keys, a.max_retries, local0 + i, se, t, kTagEpoch, c[1], m, c[3]);
             out[idx] = g >= 0 ? gi.v0 + g : -1;
             if (g >= 0) ++c[0]; else ++c[2];
         }
     }
-    if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
+    if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
     sampler_done(a);
+}
+
+// ---------------------------------------------------------------------------
+// Byte-map (re)build for the renaming period of each graph's sample epoch,
+// run before the sampler on the sampler's stream.  A graph's map is rebuilt
+// when it does not hold that period (the sampler records the period it used)
+// or when force is set (at create): k_bytemap_clear zeroes it, then
+// k_bytemap_mark sets the byte of every CSR slot (i, j) -- both orientations
+// of each edge, one warp per row.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool map_due(const EpochArgs& a, int graph, int force) {
+    if (force) return true;
+    const GraphState* st = a.gst + graph;
+    return st->map_period != map_period_of(a, st->sample_epoch);
+}
+
+__global__ void __launch_bounds__(256) k_bytemap_clear(const EpochArgs a, int force) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int g = 0; g < a.n_graphs; ++g) {
+        if (!map_due(a, g, force)) continue;
+        const unsigned long long mp = a.graphs[g].map;
+        uint4* p = reinterpret_cast<uint4*>(a.bytemap + (mp & ~63ull));
+        const size_t words = (1ull << (mp & 63ull)) / sizeof(uint4);
+        for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < words; q += stride)
+            p[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bytemap_mark(const EpochArgs a, int force) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < a.n_vchunks; c += gridDim.x) {
+        const int4 ch = __ldg(a.vchunks + c);
+        const int graph = ch.z;
+        if (!map_due(a, graph, force)) continue;
+        const GraphInfo gi = load_graph(a, graph);
+        const Membership m = membership_of(a, gi, a.gst[graph].sample_epoch);
+        uint8_t* map = a.bytemap + (gi.map & ~63ull);
+        for (int v = warp; v < ch.y; v += warps) {
+            const int row = ch.x + v;
+            const uint32_t name_i = renamed(m, (uint32_t)(row - gi.v0));
+            const int e1 = __ldg(a.row_ptr + row + 1);
+            for (int e = __ldg(a.row_ptr + row) + lane; e < e1; e += 32) {
+                const uint32_t j = (uint32_t)(__ldg(a.col_idx + e) - gi.v0);
+                map[map_address(m, name_i, renamed(m, j))] = 1;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -302,26 +433,29 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
 // piece goes to vacc for the sweep's histogram weights.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
-    __shared__ unsigned s_cnt[3];
+    __shared__ unsigned s_cnt[4];
     __shared__ int s_rp[kSamplerSub + 1];
     __shared__ int s_acc[kSamplerSub];
-    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     constexpr int kSubs = kVChunk / kSamplerSub;
     const int n_sub = a.n_vchunks * kSubs;
-    unsigned c[3] = {0u, 0u, 0u};   // accepted, rejected, exhausted of graph cur
-    int cur = -1;                   // block-uniform
+    unsigned c[4] = {0u, 0u, 0u, 0u};   // accepted, rejected, exhausted, false positives of graph cur
+    int cur = -1;                       // block-uniform
+    Membership m{nullptr, 0u, 0u, 1u, 0u};
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
         const int4 ch = __ldg(a.vchunks + s / kSubs);
         const int sub = s % kSubs;
         const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
         if (cnt <= 0) continue;   // uniform over the block
         const int graph = ch.z;
-        if (graph != cur) {
-            if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
-            cur = graph;
-        }
         const GraphInfo gi = load_graph(a, graph);
         const int se = a.gst[graph].sample_epoch;
+        if (graph != cur) {
+            if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
+            cur = graph;
+            m = membership_of(a, gi, se);
+            if (a.membership && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
+        }
         const int row0 = ch.x + sub * kSamplerSub;
         __syncthreads();   // the previous piece's shared data is no longer read
         for (int t = threadIdx.x; t <= cnt; t += blockDim.x) s_rp[t] = __ldg(a.row_ptr + row0 + t);
@@ -336,7 +470,7 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
             }
-            const int g = slot_partner(gi, a.keys, a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1]);
+            const int g = slot_partner(gi, a.keys, a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1], m, c[3]);
             out[e] = g >= 0 ? gi.v0 + g : -1;
             if (g >= 0) {
                 ++c[0];
@@ -348,7 +482,7 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) a.vacc[(size_t)(se & 1) * a.rows + row0 + t] = s_acc[t];
     }
-    if (cur >= 0) block_count3(c, s_cnt, a.gst + cur);
+    if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
     sampler_done(a);
 }
 
@@ -1482,6 +1616,17 @@ int sampler_grid(int rows, int k, int sm_count) {
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
     if (a.per_slot) k_sampler_slots<<<grid, 256, 0, s>>>(a);
     else k_sampler<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bytemap_build(const EpochArgs& a, int force, int sm_count, cudaStream_t s) {
+    if (!a.membership) return cudaSuccess;
+    k_bytemap_clear<<<sm_count * 4, 256, 0, s>>>(a, force);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int grid = a.n_vchunks < sm_count * 8 ? a.n_vchunks : sm_count * 8;
+    if (grid < 1) grid = 1;
+    k_bytemap_mark<<<grid, 256, 0, s>>>(a, force);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,12 @@ gempe_status check_params(const gempe_params* p, int32_t d) {
         return pack_fail(GEMPE_E_INVALID_ARG, "sigma_source must be 0 or 1");
     if (p->sampling == 1 && p->block_partners)
         return pack_fail(GEMPE_E_INVALID_ARG, "the per-slot sampling policy excludes block sampling");
+    if (p->membership != 0 && p->membership != 1) return pack_fail(GEMPE_E_INVALID_ARG, "membership must be 0 or 1");
+    if (p->membership == 1 && p->block_partners)
+        return pack_fail(GEMPE_E_INVALID_ARG, "byte-map membership applies to the sampled non-edges, not block sampling");
+    if (p->bytemap_log2 != 0 && (p->bytemap_log2 < 6 || p->bytemap_log2 > 32))
+        return pack_fail(GEMPE_E_INVALID_ARG, "bytemap_log2 must be 0 (automatic) or in [6, 32]");
+    if (p->rename_every < 0) return pack_fail(GEMPE_E_INVALID_ARG, "rename_every must be >= 0");
     return GEMPE_OK;
 }
 
@@ -230,7 +236,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
 
     // layout
     long long rows_ll = 0, slots_ll = 0, tiles_ll = 0;
-    unsigned long long kslots = 0;
+    unsigned long long kslots = 0, map_off = 0;
     info.assign(G, GraphInfo{});
     nnz.assign(G, 0);
     for (int32_t g = 0; g < G; ++g) {
@@ -257,6 +263,12 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         gi.key_off = kslots;
         const unsigned long long ts = table_slots(nnz[g]);
         gi.bucket_mask = ts / 4 - 1;
+        if (p.membership == 1) {
+            // each map's size is a power of two >= 64, so every offset is a multiple of 64
+            const int lg = bytemap_log2_for(nnz[g], p);
+            gi.map = map_off | (unsigned long long)lg;
+            map_off += 1ull << lg;
+        }
         rows_ll += (long long)in.n + 1;
         slots_ll += nnz[g];
         tiles_ll += gi.n_tiles;
@@ -268,6 +280,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     slots = slots_ll;
     n_tiles = (int32_t)tiles_ll;
     key_slots = kslots;
+    bytemap_bytes = (size_t)map_off;
 
     PK(cudaGetDevice(&device), "cudaGetDevice");
     PK(ensure_mills_table(), "Mills table");
@@ -345,6 +358,10 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         if (!vacc) return pack_fail(GEMPE_E_OOM, "device allocation failed");
     }
     if (p.precision == 1) xb = (__nv_bfloat16*)alloc(sizeof(__nv_bfloat16) * R * d);
+    if (bytemap_bytes) {
+        bytemap = (uint8_t*)alloc(bytemap_bytes);
+        if (!bytemap) return pack_fail(GEMPE_E_OOM, "device allocation failed (byte maps)");
+    }
     if (block) {
         block_part = (int32_t*)alloc(sizeof(int32_t) * 2 * (size_t)std::max(n_tiles, 1) * kBlockP);
         block_mask = (unsigned long long*)alloc(sizeof(unsigned long long) * 2 * R);
@@ -361,7 +378,10 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     for (int32_t g = 0; g < G; ++g) act[g] = g;
     std::vector<GraphState> st0(G);
     std::memset(st0.data(), 0, sizeof(GraphState) * G);
-    for (auto& st : st0) st.sigma = p.sigma0;
+    for (auto& st : st0) {
+        st.sigma = p.sigma0;
+        st.map_period = bytemap ? 0 : -1;   // the maps are built below for period 0
+    }
     PK(cudaMemcpyAsync(row_ptr, row_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s), "copy row_ptr");
     PK(cudaMemcpyAsync(col_idx, col_h.data(), sizeof(int32_t) * col_h.size(), cudaMemcpyHostToDevice, s), "copy col_idx");
     PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
@@ -390,6 +410,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
                                  gi.key_hi, p.init_range, s),
            "init positions");
     }
+    if (bytemap) PK(launch_bytemap_build(args(), 1, sm_count, s), "byte-map build");
     int32_t hash_fail = 0;
     PK(cudaMemcpyAsync(&hash_fail, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read flag");
     PK(cudaStreamSynchronize(s), "create");
@@ -399,6 +420,13 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
     tile_grid = gempe::tile_grid(n_tile_items, sm_count, 0);
     return set_shape(PackShape{});
+}
+
+int Pack::bytemap_log2_for(int64_t nnz, const gempe_params& p) {
+    if (p.bytemap_log2 > 0) return p.bytemap_log2;
+    int lg = 0;
+    while ((1ll << lg) < std::max<int64_t>(nnz, 1)) ++lg;
+    return std::min(30, std::max(12, lg + 7));
 }
 
 size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p) {
@@ -416,6 +444,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     const bool ps = p.sampling == 1;
     b += al(4 * std::max<size_t>(blk ? 1 : (ps ? 2 * (size_t)nnz : 2 * R * k), 1)) + al(16 * units_max) + al(4 * 4097);
     if (ps) b += al(8 * R);
+    if (p.membership == 1 && !blk) b += al((size_t)1 << bytemap_log2_for(nnz, p));
     if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
     return b;
 }
@@ -550,12 +579,20 @@ EpochArgs Pack::args() const {
     a.z_min = p.z_min;
     a.hist_max = p.hist_max;
     a.mills = mills;
+    a.membership = bytemap ? 1 : 0;
+    a.rename_every = p.rename_every;
+    a.bytemap = bytemap;
     return a;
 }
 
 namespace {
 cudaError_t launch_epoch_sampler(const Pack& pk, cudaStream_t s) {
     if (pk.block) return launch_block_sampler(pk.args(), pk.sampler_units, pk.n_sampler_units, pk.sm_count, s);
+    if (pk.bytemap && pk.p.rename_every > 0) {
+        // a new renaming period: rebuild the maps that hold another one
+        const cudaError_t e = launch_bytemap_build(pk.args(), 0, pk.sm_count, s);
+        if (e != cudaSuccess) return e;
+    }
     return launch_sampler(pk.args(), pk.sampler_grid, s);
 }
 }  // namespace
@@ -642,7 +679,7 @@ int ilog2(long long v) {
 }  // namespace
 
 gempe_status Pack::autotune() {
-    const TuneKey key{d, p.precision, block ? 1 : 0, k, ilog2(rows), ilog2(std::max<int64_t>(slots, 1)), G > 1};
+    const TuneKey key{d, p.precision, block ? 1 : (per_slot ? 2 : 0), k, ilog2(rows), ilog2(std::max<int64_t>(slots, 1)), G > 1};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);

@@ -88,6 +88,8 @@ struct Pack {
     int2* tile_items = nullptr;      // {tile, graph}
     int32_t n_tile_items = 0;
     int32_t* scratch = nullptr;      // rows * max(k, 1) int32: inspection samples, flags
+    uint8_t* bytemap = nullptr;      // byte-map membership: the graphs' maps back to back
+    size_t bytemap_bytes = 0;
     const MillsCoef* mills = nullptr;
     int sweep_grid = 0, sampler_grid = 0, update_grid = 0, tile_grid = 0;
     std::vector<void*> allocations;
@@ -120,6 +122,9 @@ struct Pack {
     int32_t slots_per_vertex() const { return block ? kBlockP : k; }
     bool sampled() const { return per_slot ? slots > 0 : slots_per_vertex() > 0; }
 
+    // log2 of the byte-map size of a graph with nnz CSR slots (the parameter,
+    // or nnz rounded up to a power of two times 128, in [2^12, 2^30])
+    static int bytemap_log2_for(int64_t nnz, const gempe_params& p);
     // Device bytes a pack of one graph with n vertices and nnz CSR slots
     // allocates (an upper bound: the sweep units are counted at their most).
     static size_t bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p);

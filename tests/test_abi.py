@@ -76,6 +76,14 @@ def test_invalid_args_rejected_on_host():
     st, _ = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data),
                     1, 2, ctypes.byref(p), None)
     assert st == -1
+    # byte-map membership: 0/1, log2 0 or 6..32, rename_every >= 0, not with block sampling
+    for kw, d in ((dict(membership=2), 2), (dict(membership=1, bytemap_log2=5), 2),
+                  (dict(membership=1, bytemap_log2=33), 2), (dict(membership=1, rename_every=-1), 2),
+                  (dict(membership=1, block_partners=64), 16)):
+        p = binding.gempe_default_params(**kw)
+        st, _ = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data),
+                        2, d, ctypes.byref(p), None)
+        assert st == -1, kw
     with pytest.raises(binding.GempeError):
         binding.gempe_create(np.array([0, 1, 1], np.int32), np.array([1], np.int32), 2)
 
@@ -129,3 +137,8 @@ def test_job_bytes_formula():
     pb = B.gempe_default_params(neg_per_vertex=10, precision=1)
     assert B.gempe_job_bytes(n, nnz, 32, pb) > B.gempe_job_bytes(n, nnz, 32, p)
     assert B.gempe_job_bytes(1, 0, 2, p) == 0 and B.gempe_job_bytes(n, nnz, 5, p) == 0
+    # the byte map adds its 2^log2 bytes; automatic size: nnz to a power of two, times 128, at most 2^30
+    pm = B.gempe_default_params(neg_per_vertex=10, membership=1, bytemap_log2=20)
+    assert B.gempe_job_bytes(n, nnz, 32, pm) - B.gempe_job_bytes(n, nnz, 32, p) == 1 << 20
+    pa = B.gempe_default_params(neg_per_vertex=10, membership=1)
+    assert B.gempe_job_bytes(n, nnz, 32, pa) - B.gempe_job_bytes(n, nnz, 32, p) == 1 << 28
