@@ -382,8 +382,8 @@ GEMPE_API gempe_status gempe_is_edge(gempe_ctx* c, const int32_t* host_pairs, si
     }
     e = cudaMemcpyAsync(dpairs, host_pairs, sizeof(int32_t) * 2 * count, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = launch_is_edge(pk.keys + pk.info[0].key_off, pk.info[0].bucket_mask, dpairs, (int64_t)count, dout,
-                           c->stream);
+        e = launch_is_edge(pk.keys, pk.narrow_keys ? 1 : 0, pk.info[0].key_off, pk.info[0].bucket_mask, dpairs,
+                           (int64_t)count, dout, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, dout, count, cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(dpairs, c->stream);
     cudaFreeAsync(dout, c->stream);

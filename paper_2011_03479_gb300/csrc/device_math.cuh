@@ -37,13 +37,22 @@ constexpr uint32_t kTagSlope = 0x0F000000u;   // the separate histogram pass of 
 constexpr uint32_t kTagRename = 0x09000000u;  // the byte map's random renaming (Sec. III.C)
 
 // --------------------------------------------------------------------------
-// Exact edge set: open addressing over 64-bit keys (i << 32 | j), buckets of
-// four 8-byte slots (one 32-byte sector), linear probing bucket by bucket.
+// Exact edge set: every undirected edge {i, j} once, keyed by (min, max),
+// open addressing with linear probing bucket by bucket over 32-byte buckets
+// (one sector).  Narrow sets (every graph of the pack has n <= 65536) hold
+// u32 keys min << 16 | max, eight per bucket; wide sets u64 keys
+// min << 32 | max, four per bucket.  All-ones marks an empty slot (never a
+// key: min < max).
 // --------------------------------------------------------------------------
 constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr uint32_t kEmptyKey32 = ~0u;
 
 __device__ __forceinline__ unsigned long long edge_key(int32_t i, int32_t j) {
-    return ((unsigned long long)(uint32_t)i << 32) | (uint32_t)j;
+    return ((unsigned long long)(uint32_t)min(i, j) << 32) | (uint32_t)max(i, j);
+}
+
+__device__ __forceinline__ uint32_t edge_key32(int32_t i, int32_t j) {
+    return ((uint32_t)min(i, j) << 16) | (uint32_t)max(i, j);
 }
 
 // splitmix64 finaliser (Steele, Lea, Flood, OOPSLA 2014) as the bucket hash.
@@ -53,7 +62,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-// Membership of key in the table of (bucket_mask + 1) buckets.
+// Membership of key in a wide table of (bucket_mask + 1) buckets.
 __device__ __forceinline__ bool hash_contains(const unsigned long long* __restrict__ keys,
                                               unsigned long long bucket_mask, unsigned long long key) {
     unsigned long long b = mix64(key) & bucket_mask;
@@ -66,6 +75,32 @@ __device__ __forceinline__ bool hash_contains(const unsigned long long* __restri
         b = (b + 1) & bucket_mask;
     }
     return false;
+}
+
+// Membership of key in a narrow table of (bucket_mask + 1) buckets.
+__device__ __forceinline__ bool hash_contains32(const uint32_t* __restrict__ keys, unsigned long long bucket_mask,
+                                                uint32_t key) {
+    unsigned long long b = mix64(key) & bucket_mask;
+    for (unsigned long long probe = 0; probe <= bucket_mask; ++probe) {
+        const uint4* p = reinterpret_cast<const uint4*>(keys + 8 * b);
+        const uint4 s03 = __ldg(p), s47 = __ldg(p + 1);
+        if (s03.x == key || s03.y == key || s03.z == key || s03.w == key || s47.x == key || s47.y == key ||
+            s47.z == key || s47.w == key)
+            return true;
+        if (s03.x == kEmptyKey32 || s03.y == kEmptyKey32 || s03.z == kEmptyKey32 || s03.w == kEmptyKey32 ||
+            s47.x == kEmptyKey32 || s47.y == kEmptyKey32 || s47.z == kEmptyKey32 || s47.w == kEmptyKey32)
+            return false;
+        b = (b + 1) & bucket_mask;
+    }
+    return false;
+}
+
+// Is {i, j} (local ids) an edge of the graph whose table starts at slot
+// key_off of the pack's key array?
+__device__ __forceinline__ bool edge_set_contains(const void* keys, int narrow, unsigned long long key_off,
+                                                  unsigned long long bucket_mask, int32_t i, int32_t j) {
+    if (narrow) return hash_contains32(static_cast<const uint32_t*>(keys) + key_off, bucket_mask, edge_key32(i, j));
+    return hash_contains(static_cast<const unsigned long long*>(keys) + key_off, bucket_mask, edge_key(i, j));
 }
 
 // --------------------------------------------------------------------------

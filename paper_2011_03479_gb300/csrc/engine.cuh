@@ -54,6 +54,10 @@ struct PackState {
     unsigned int sample_done;   // blocks of the running sampler that finished
 };
 
+// Packs whose graphs all have at most this many vertices key their edge
+// sets by u32 (min << 16 | max), others by u64.
+constexpr int kNarrowKeysMaxN = 65536;
+
 // Chunk size (CSR slots) of the per-unit sweep used for d >= 8 (default;
 // the autotuner may pick another).
 constexpr int kEdgeChunk = 64;
@@ -101,7 +105,13 @@ struct EpochArgs {
     // CSR, edge sets, positions, accumulators
     const int32_t* row_ptr;   // [rows + 1] absolute slot offsets
     const int32_t* col_idx;   // pack row ids
-    const unsigned long long* keys;
+    // degree-oriented CSR (d <= 4, k-per-vertex policy): each undirected edge
+    // once, in the row of its endpoint with the larger (degree, id)
+    const int32_t* orow_ptr;
+    const int32_t* ocol_idx;
+    int32_t oriented;         // 1: the packed sweep takes its edge slots from it
+    const void* keys;         // edge sets: u32 keys when narrow_keys, else u64 (device_math.cuh)
+    int32_t narrow_keys;
     float* x;
     __nv_bfloat16* xb;        // BF16 shadow of x (precision form), else null
     float* acc;               // [rows][acc_stride]: d values of y - z x, then z
@@ -149,7 +159,7 @@ bool supported_dim(int d);
 
 // Per-graph set-up (rows and slots of one graph of the pack).
 cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
-                              unsigned long long* keys, unsigned long long bucket_mask,
+                              void* keys, int narrow, unsigned long long bucket_mask,
                               int32_t* fail_flag, cudaStream_t s);
 cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_t d, uint32_t key_lo,
                                   uint32_t key_hi, float range, cudaStream_t s);
@@ -184,7 +194,7 @@ cudaError_t prepare_tile_kernel(int d, int bins);
 cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, cudaStream_t s);
 int sampler_grid(int rows, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);
-cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
+cudaError_t launch_is_edge(const void* keys, int narrow, unsigned long long key_off, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s);
 // Message for gempe_last_error() on the calling thread.
 void set_last_error(const char* msg);

@@ -13,6 +13,8 @@
 //  k_loss          sampled predictive entropy (Eq. 2) with FP64 sums
 //  k_sample        the sampler alone (inspection)
 //  k_is_edge       membership probes (inspection)
+#include <type_traits>
+
 #include "device_math.cuh"
 #include "engine.cuh"
 #include "hist.cuh"
@@ -30,24 +32,31 @@ __device__ MillsCoef g_mills[kMillsIntervals];
 // ---------------------------------------------------------------------------
 // Graph set-up (one graph of the pack per launch)
 // ---------------------------------------------------------------------------
+template <bool kNarrow>
 __global__ void k_hash_build(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t v0,
-                             int32_t n, unsigned long long* keys, unsigned long long bucket_mask, int32_t* fail_flag) {
+                             int32_t n, void* keys_v, unsigned long long bucket_mask, int32_t* fail_flag) {
+    using Key = typename std::conditional<kNarrow, unsigned int, unsigned long long>::type;
+    constexpr int kPerBucket = kNarrow ? 8 : 4;
+    constexpr Key kEmpty = (Key)~0ull;
+    Key* keys = static_cast<Key*>(keys_v);
     const int32_t* rp = row_ptr + v0;
     const int64_t e0 = __ldg(rp), e1 = __ldg(rp + n);
-    const unsigned long long slot_mask = 4ull * bucket_mask + 3ull;
+    const unsigned long long slot_mask = (unsigned long long)kPerBucket * bucket_mask + (kPerBucket - 1);
     for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = __ldg(col_idx + e) - v0;
         // local row of CSR slot e: the last i with rp[i] <= e
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (__ldg(rp + mid) <= e) lo = mid; else hi = mid - 1;
         }
-        const unsigned long long key = edge_key(lo, __ldg(col_idx + e) - v0);
-        unsigned long long slot = 4ull * (mix64(key) & bucket_mask);
+        if (j <= lo) continue;   // each undirected edge once, from its lower end
+        const Key key = kNarrow ? (Key)edge_key32(lo, j) : (Key)edge_key(lo, j);
+        unsigned long long slot = (unsigned long long)kPerBucket * (mix64(key) & bucket_mask);
         bool done = false;
         for (unsigned long long probe = 0; probe <= slot_mask; ++probe) {
-            const unsigned long long prev = atomicCAS(keys + slot, kEmptyKey, key);
-            if (prev == kEmptyKey || prev == key) { done = true; break; }
+            const Key prev = atomicCAS(keys + slot, kEmpty, key);
+            if (prev == kEmpty || prev == key) { done = true; break; }
             slot = (slot + 1) & slot_mask;
         }
         if (!done) atomicExch(fail_flag, 1);
@@ -164,6 +173,14 @@ __device__ __forceinline__ GraphInfo load_graph(const EpochArgs& a, int g) {
     return gi;
 }
 
+// The pack's exact edge sets (key array and width).
+struct EdgeSets {
+    const void* keys;
+    int narrow;
+};
+
+__device__ __forceinline__ EdgeSets edge_sets(const EpochArgs& a) { return EdgeSets{a.keys, a.narrow_keys}; }
+
 // ---------------------------------------------------------------------------
 // Membership as the sampler sees it (Sec. III.C).  Exact: the graph's edge
 // hash set.  Byte map: a byte array of s = 2^b entries in which every edge
@@ -221,20 +238,18 @@ __device__ __forceinline__ uint32_t map_address(const Membership& m, uint32_t na
 }
 
 // Is the draw (i, g) taken for an edge?  name_i = pi(i) (byte map only).
-__device__ __forceinline__ bool taken_for_edge(const GraphInfo& gi, const unsigned long long* keys,
-                                               const Membership& m, uint32_t name_i, int i, int g,
-                                               unsigned& false_pos) {
-    const unsigned long long* table = keys + gi.key_off;
-    if (!m.map) return hash_contains(table, gi.bucket_mask, edge_key(i, g));
+__device__ __forceinline__ bool taken_for_edge(const GraphInfo& gi, const EdgeSets& es, const Membership& m,
+                                               uint32_t name_i, int i, int g, unsigned& false_pos) {
+    if (!m.map) return edge_set_contains(es.keys, es.narrow, gi.key_off, gi.bucket_mask, i, g);
     if (!__ldg(m.map + map_address(m, name_i, renamed(m, (uint32_t)g)))) return false;
-    if (!hash_contains(table, gi.bucket_mask, edge_key(i, g))) ++false_pos;
+    if (!edge_set_contains(es.keys, es.narrow, gi.key_off, gi.bucket_mask, i, g)) ++false_pos;
     return true;
 }
 
 // Draw the accepted partner (local id) of sample slot t of local vertex i of
 // a graph (Fig. 2: redraw while the pair is taken for an edge; also redraw
 // g == i), or -1 after max_retries draws.
-__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
                                               int i, int epoch, int t, uint32_t tag, unsigned& rejected,
                                               const Membership& m, unsigned& false_pos) {
     const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
@@ -251,7 +266,7 @@ __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigne
 }
 
 // The same with the exact edge set (loss, slope-pass and inspection draws).
-__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
                                               int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
     unsigned unused = 0u;
     const Membership exact{nullptr, 0u, (uint32_t)gi.n, 1u, 0u};
@@ -261,7 +276,7 @@ __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const unsigne
 // Sec. III.C's policy: the partner (local id) of CSR slot e_local of the
 // graph, anchored at local vertex i (the slot's row); counter
 // (e_local, epoch, 0, kTagSlot | attempt >> 2), -1 after max_retries draws.
-__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const unsigned long long* keys, int max_retries,
+__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
                                             int i, int e_local, int epoch, unsigned& rejected, const Membership& m,
                                             unsigned& false_pos) {
     const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
@@ -370,7 +385,7 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
         const int total = cnt * k;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int i = idx / k, t = idx - i * k;
-            const int g = sample_partner(gi, a.keys, a.max_retries, local0 + i, se, t, kTagEpoch, c[1], m, c[3]);
+            const int g = sample_partner(gi, edge_sets(a), a.max_retries, local0 + i, se, t, kTagEpoch, c[1], m, c[3]);
             out[idx] = g >= 0 ? gi.v0 + g : -1;
             if (g >= 0) ++c[0]; else ++c[2];
         }
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
             }
-            const int g = slot_partner(gi, a.keys, a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1], m, c[3]);
+            const int g = slot_partner(gi, edge_sets(a), a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1], m, c[3]);
             out[e] = g >= 0 ? gi.v0 + g : -1;
             if (g >= 0) {
                 ++c[0];
@@ -497,13 +512,22 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
 // sums are formed by a segmented warp scan and kept in a per-warp shared row
 // until the unit ends, then added to the global accumulator with one vector
 // atomic per vertex.  Sampled partners receive their term by vector atomics.
+//
+// Oriented form (a.oriented, the k-per-vertex policy): the edge slots are
+// those of the degree-oriented CSR, in which each undirected edge appears
+// once, at the endpoint with the larger (degree, id); that endpoint
+// evaluates the pair and the other receives its term by a vector atomic,
+// like a sampled partner.  Each edge's term is then evaluated once instead
+// of once per endpoint, and no vertex receives more atomics than it has
+// neighbours of larger degree, so hubs (which process their whole rows)
+// see few.
 // ---------------------------------------------------------------------------
 template <int D>
 struct PackedAcc {
     static constexpr int kStride = ((D + 1) + 3) / 4 * 4;   // floats per vertex row
 };
 
-template <int D>
+template <int D, bool kOriented>
 __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochArgs a) {
     constexpr int AS = PackedAcc<D>::kStride;
     constexpr int kWarps = kPackedThreads / 32;
@@ -527,7 +551,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         const int4 unit = __ldg(a.items + it);
         const int v0 = unit.x, nv = unit.y & ((1 << kGraphShift) - 1), graph = unit.y >> kGraphShift;
         const bool whole_rows = unit.z < 0;
-        const bool slots = a.per_slot != 0;   // Sec. III.C's policy: one sample per CSR slot
+        const bool slots = !kOriented && a.per_slot != 0;   // Sec. III.C's policy: one sample per CSR slot
         const bool has_s = (unit.w & kUnitHasSamples) && (k > 0 || slots);
         const int e_lo = whole_rows ? 0 : unit.z;
         const int e_hi = unit.w & ~kUnitHasSamples;
@@ -537,12 +561,15 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         const int32_t* samples =
             a.samples + (size_t)(epoch & 1) * (slots ? (size_t)a.n_slots : (size_t)a.rows * k);
 
-        // per-vertex layout: lane l < nv describes vertex v0 + l
+        // per-vertex layout: lane l < nv describes vertex v0 + l (edge slots
+        // from the oriented CSR in the oriented form; deg is the full degree)
+        const int32_t* erow = kOriented ? a.orow_ptr : a.row_ptr;
         int rs = 0, deg = 0, ne = 0;
         if (lane < nv) {
-            rs = __ldg(a.row_ptr + v0 + lane);
-            deg = __ldg(a.row_ptr + v0 + lane + 1) - rs;
-            ne = whole_rows ? deg : e_hi - e_lo;
+            rs = __ldg(erow + v0 + lane);
+            const int deg_e = __ldg(erow + v0 + lane + 1) - rs;
+            deg = kOriented ? __ldg(a.row_ptr + v0 + lane + 1) - __ldg(a.row_ptr + v0 + lane) : deg_e;
+            ne = whole_rows ? deg_e : e_hi - e_lo;
         }
         const int ebase = rs + e_lo;
         const int np = (lane < nv) ? ne + (has_s ? (slots ? ne : k) : 0) : 0;
@@ -603,7 +630,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
             const bool is_edge = r < ne_l;
             int j = -1;
             if (active) {
-                if (is_edge) j = __ldg(a.col_idx + eb_l + r);
+                if (is_edge) j = __ldg((kOriented ? a.ocol_idx : a.col_idx) + eb_l + r);
                 else j = slots ? __ldg(samples + eb_l + (r - ne_l)) : s_g[l * k + (r - ne_l)];
             }
             const bool valid = active && j >= 0;
@@ -631,16 +658,17 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
                 val[D] = t.w;
                 const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
                 if (is_edge) {
-                    if (j > v) hist_edge(hist, a, graph, bin);
+                    if (kOriented || j > v) hist_edge(hist, a, graph, bin);
                 } else {
                     if (slots) hist_sample_w(hist, a, graph, bin, deg_l, kacc_l);
                     else hist_sample(hist, a, graph, bin, deg_l, kacc_l, k);
-                    if (a.symmetric) {
-                        float pv[D];
+                }
+                // the other endpoint of an oriented edge, or a sampled partner
+                if (is_edge ? kOriented : a.symmetric) {
+                    float pv[D];
 #pragma unroll
-                        for (int c = 0; c < D; ++c) pv[c] = -val[c];
-                        acc_add<D, 1, D>(a.acc + (size_t)j * a.acc_stride, 0, pv, t.w);
-                    }
+                    for (int c = 0; c < D; ++c) pv[c] = -val[c];
+                    acc_add<D, 1, D>(a.acc + (size_t)j * a.acc_stride, 0, pv, t.w);
                 }
             }
             // segmented inclusive scan over lanes of the same vertex
@@ -956,19 +984,45 @@ __device__ __forceinline__ float4 block_sum4(float4 v, SigmaSmem& sm) {
     return t;
 }
 
-// Newton step in t = ln sigma inside the sign-change bracket [lo, hi]
-// (halving whenever the step leaves it); run by one thread.
-__device__ __forceinline__ void newton_update(float f, float df, bool lo_pos, float& lo, float& hi, float& t,
-                                              SigmaSmem& sm, int iter) {
-    if ((f > 0.0f) == lo_pos) lo = t; else hi = t;
-    float tn = t - f / df;
-    if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
-    // stop at 3e-6 in ln sigma: the FP32 evaluation of F leaves the root
-    // uncertain at about that level, far inside 1e-4 relative
-    sm.done = (fabsf(tn - t) < 3e-6f || (hi - lo) < 6e-6f) ? 1 : 0;
+// The root search's state, kept by one thread: the sign-change bracket
+// [lo, hi] with F at both ends, the side that was moved last (for the
+// Illinois rule) and the current point t.
+struct SigmaSearch {
+    float lo, hi, f_lo, f_hi, t;
+    int side;   // -1: lo moved last, +1: hi moved last, 0: none yet
+};
+
+// One step: F(t) = f, F'(t) = df have been evaluated.  Newton's step is
+// taken when it stays inside the bracket; otherwise a regula-falsi step on
+// the bracket with the Illinois rule (the value at an end kept twice in a row
+// is halved), which keeps convergence superlinear where Newton overshoots.
+// The search stops when the step, or the bracket, is below 1e-5 in ln sigma:
+// the FP32 evaluation of F leaves the root uncertain at about 1e-6, so
+// smaller thresholds only make the steps follow the rounding.  Run by one
+// thread.
+__device__ __forceinline__ void newton_update(float f, float df, bool lo_pos, SigmaSearch& q, SigmaSmem& sm,
+                                              int iter) {
+    if ((f > 0.0f) == lo_pos) {
+        q.lo = q.t;
+        q.f_lo = f;
+        if (q.side == -1) q.f_hi *= 0.5f;
+        q.side = -1;
+    } else {
+        q.hi = q.t;
+        q.f_hi = f;
+        if (q.side == 1) q.f_lo *= 0.5f;
+        q.side = 1;
+    }
+    float tn = q.t - f / df;
+    if (!(tn > q.lo && tn < q.hi)) {
+        const float den = q.f_hi - q.f_lo;
+        tn = (den != 0.0f) ? (q.lo * q.f_hi - q.hi * q.f_lo) / den : 0.5f * (q.lo + q.hi);
+        if (!(tn > q.lo && tn < q.hi)) tn = 0.5f * (q.lo + q.hi);
+    }
+    sm.done = (fabsf(tn - q.t) < 1e-5f || (q.hi - q.lo) < 1e-5f) ? 1 : 0;
     sm.iters = iter;
-    t = tn;
-    sm.inv_s = expf(-t);
+    q.t = tn;
+    sm.inv_s = expf(-tn);
 }
 
 // Returns the new sigma (valid in every thread).  he/hn: shared-memory bins;
@@ -979,10 +1033,10 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
                                  float sigma_prev, const MillsCoef* tab, SigmaSmem& sm) {
     const float bin_w = hist_max / (float)bins;
     const bool lead = threadIdx.x == 0;
-    float lo = -6.9077553f, hi = 6.9077553f;   // ln 1e-3, ln 1e3
-    float t = (sigma_prev > 0.0f) ? logf(sigma_prev) : 0.0f;
-    if (!(t > lo && t < hi)) t = 0.0f;
-    const float inv_s0 = expf(-t);
+    SigmaSearch q{-6.9077553f, 6.9077553f, 0.0f, 0.0f, 0.0f, 0};   // ln 1e-3, ln 1e3
+    q.t = (sigma_prev > 0.0f) ? logf(sigma_prev) : 0.0f;
+    if (!(q.t > q.lo && q.t < q.hi)) q.t = 0.0f;
+    const float inv_s0 = expf(-q.t);
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int b = threadIdx.x; b < bins; b += blockDim.x) {
         const float ce = he[b], cn = hn[b], c = ((float)b + 0.5f) * bin_w;
@@ -1003,7 +1057,9 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
             sm.done = 1;
             sm.iters = 0;
         } else {
-            newton_update(tot.z, tot.w, lo_pos, lo, hi, t, sm, 1);
+            q.f_lo = tot.x;
+            q.f_hi = tot.y;
+            newton_update(tot.z, tot.w, lo_pos, q, sm, 1);
         }
     }
     __syncthreads();
@@ -1017,7 +1073,7 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
             p.y += fd.y;
         }
         const float4 fd = block_sum4(p, sm);
-        if (lead) newton_update(fd.x, fd.y, lo_pos, lo, hi, t, sm, it);
+        if (lead) newton_update(fd.x, fd.y, lo_pos, q, sm, it);
         __syncthreads();
     }
     return 1.0f / sm.inv_s;
@@ -1216,7 +1272,7 @@ __global__ void __launch_bounds__(256) k_hist_pass(const EpochArgs a) {
             int g_mine = -1;
             unsigned rej = 0;
             if (lane < a.k) {
-                const int g = sample_partner(gi, a.keys, a.max_retries, i - gi.v0, epoch, lane, kTagSlope, rej);
+                const int g = sample_partner(gi, edge_sets(a), a.max_retries, i - gi.v0, epoch, lane, kTagSlope, rej);
                 g_mine = g >= 0 ? gi.v0 + g : -1;
             }
             const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
@@ -1298,7 +1354,7 @@ __global__ void k_sample(const EpochArgs a, uint32_t tag, int32_t* out) {
             const int v = ch.x + vi;
             unsigned rej = 0;
             if (lane < a.k) {
-                const int g = sample_partner(gi, a.keys, a.max_retries, v - gi.v0, epoch, lane, tag, rej);
+                const int g = sample_partner(gi, edge_sets(a), a.max_retries, v - gi.v0, epoch, lane, tag, rej);
                 out[(size_t)v * a.k + lane] = g >= 0 ? gi.v0 + g : -1;
             }
         }
@@ -1333,7 +1389,7 @@ __global__ void __launch_bounds__(256) k_loss(const EpochArgs a) {
             int g_mine = -1;
             unsigned rej = 0;
             if (lane < a.k) {
-                const int g = sample_partner(gi, a.keys, a.max_retries, i - gi.v0, epoch, lane, kTagLoss, rej);
+                const int g = sample_partner(gi, edge_sets(a), a.max_retries, i - gi.v0, epoch, lane, kTagLoss, rej);
                 g_mine = g >= 0 ? gi.v0 + g : -1;
             }
             const int k_acc = __popc(__ballot_sync(kFull, g_mine >= 0));
@@ -1388,11 +1444,13 @@ __global__ void k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict
         xb[t] = __float2bfloat16_rn(x[t]);
 }
 
-__global__ void k_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
+__global__ void k_is_edge(const void* keys, int narrow, unsigned long long key_off, unsigned long long bucket_mask,
                           const int32_t* pairs, int64_t count, uint8_t* out) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
-         p += (int64_t)gridDim.x * blockDim.x)
-        out[p] = hash_contains(keys, bucket_mask, edge_key(pairs[2 * p], pairs[2 * p + 1])) ? 1 : 0;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+        out[p] = (i != j && edge_set_contains(keys, narrow, key_off, bucket_mask, i, j)) ? 1 : 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1415,7 +1473,8 @@ cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
 
 template <int D>
 cudaError_t packed_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    k_sweep_packed<D><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
+    if (a.oriented) k_sweep_packed<D, true><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
+    else k_sweep_packed<D, false><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1429,8 +1488,9 @@ template <int D>
 int packed_blocks_per_sm(int bins) {
     int blocks = 0;
     const size_t smem = packed_smem_bytes(D, bins);
-    cudaFuncSetAttribute(k_sweep_packed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D>, kPackedThreads, smem) !=
+    cudaFuncSetAttribute(k_sweep_packed<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sweep_packed<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D, false>, kPackedThreads, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         blocks = 1;
@@ -1506,12 +1566,13 @@ int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int 
 }
 
 cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
-                              unsigned long long* keys, unsigned long long bucket_mask, int32_t* fail_flag,
+                              void* keys, int narrow, unsigned long long bucket_mask, int32_t* fail_flag,
                               cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     long long grid = (nnz + 255) / 256;
     if (grid > 65535) grid = 65535;
-    k_hash_build<<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, v0, n, keys, bucket_mask, fail_flag);
+    if (narrow) k_hash_build<true><<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, v0, n, keys, bucket_mask, fail_flag);
+    else k_hash_build<false><<<(int)grid, 256, 0, s>>>(row_ptr, col_idx, v0, n, keys, bucket_mask, fail_flag);
     return cudaGetLastError();
 }
 
@@ -1646,12 +1707,12 @@ cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_is_edge(const unsigned long long* keys, unsigned long long bucket_mask,
+cudaError_t launch_is_edge(const void* keys, int narrow, unsigned long long key_off, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s) {
     long long grid = (count + 255) / 256;
     if (grid > 65535) grid = 65535;
     if (grid < 1) grid = 1;
-    k_is_edge<<<(int)grid, 256, 0, s>>>(keys, bucket_mask, pairs, count, out);
+    k_is_edge<<<(int)grid, 256, 0, s>>>(keys, narrow, key_off, bucket_mask, pairs, count, out);
     return cudaGetLastError();
 }
 

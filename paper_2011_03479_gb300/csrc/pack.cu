@@ -170,9 +170,11 @@ void wide_tasks(std::vector<int4>& units, int pg, int k_slots, bool per_slot) {
     while (units.size() % pg) units.push_back(make_int4(-1, 0, 0, 0));
 }
 
+// Slots of a graph's edge set: every undirected edge once (nnz / 2 keys) at
+// a load of at most 1/2.
 unsigned long long table_slots(int64_t nnz) {
     unsigned long long s = 16;
-    while (s < 2ull * (unsigned long long)nnz) s <<= 1;
+    while (s < (unsigned long long)std::max<int64_t>(nnz, 0)) s <<= 1;
     return s;
 }
 
@@ -233,6 +235,9 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     block = p.block_partners > 0;
     tiles = block && p.precision == 1 && tile_dim(d);
     per_slot = p.sampling == 1;
+    narrow_keys = true;
+    for (const GraphInput& in : gs) narrow_keys = narrow_keys && in.n <= kNarrowKeysMaxN;
+    const unsigned long long per_bucket = narrow_keys ? 8 : 4;
 
     // layout
     long long rows_ll = 0, slots_ll = 0, tiles_ll = 0;
@@ -262,7 +267,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         gi.key_hi = (uint32_t)(in.key >> 32);
         gi.key_off = kslots;
         const unsigned long long ts = table_slots(nnz[g]);
-        gi.bucket_mask = ts / 4 - 1;
+        gi.bucket_mask = ts / per_bucket - 1;
         if (p.membership == 1) {
             // each map's size is a power of two >= 64, so every offset is a multiple of 64
             const int lg = bytemap_log2_for(nnz[g], p);
@@ -306,6 +311,25 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         if (g + 1 < G) row_ptr_h[(size_t)gi.v0 + in.n + 1] = s0 + (int32_t)nnz[g];
     }
     row_ptr_h[(size_t)rows] = (int32_t)slots;
+    // the degree-oriented CSR of the packed sweep: edge (i, j) in row i when
+    // (deg j, j) < (deg i, i), so every undirected edge once
+    std::vector<int32_t> ocol_h;
+    orow_ptr_h.clear();
+    if (d <= kPackedMaxDim && !per_slot && !block) {
+        orow_ptr_h.assign((size_t)rows + 1, 0);
+        ocol_h.reserve((size_t)slots / 2 + 1);
+        for (int32_t r = 0; r < rows; ++r) {
+            orow_ptr_h[r] = (int32_t)ocol_h.size();
+            const int32_t dr = row_ptr_h[(size_t)r + 1] - row_ptr_h[r];
+            for (int32_t e = row_ptr_h[r]; e < row_ptr_h[(size_t)r + 1]; ++e) {
+                const int32_t j = col_h[e];
+                const int32_t dj = row_ptr_h[(size_t)j + 1] - row_ptr_h[j];
+                if (dj < dr || (dj == dr && j < r)) ocol_h.push_back(j);
+            }
+        }
+        orow_ptr_h[rows] = (int32_t)ocol_h.size();
+        if (ocol_h.empty()) ocol_h.push_back(0);
+    }
     // vertex chunks and tile lists
     std::vector<int4> vch;
     std::vector<int2> titems;
@@ -333,7 +357,12 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     const size_t R = (size_t)rows;
     row_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
     col_idx = (int32_t*)alloc(sizeof(int32_t) * col_h.size());
-    keys = (unsigned long long*)alloc(sizeof(unsigned long long) * key_slots);
+    keys = alloc((narrow_keys ? 4 : 8) * key_slots);
+    if (!orow_ptr_h.empty()) {
+        orow_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
+        ocol_idx = (int32_t*)alloc(sizeof(int32_t) * ocol_h.size());
+        if (!orow_ptr || !ocol_idx) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+    }
     x = (float*)alloc(sizeof(float) * R * d);
     acc = (float*)alloc(sizeof(float) * R * acc_stride);
     const size_t GB = (size_t)G * bins;
@@ -384,12 +413,18 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     }
     PK(cudaMemcpyAsync(row_ptr, row_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s), "copy row_ptr");
     PK(cudaMemcpyAsync(col_idx, col_h.data(), sizeof(int32_t) * col_h.size(), cudaMemcpyHostToDevice, s), "copy col_idx");
+    if (orow_ptr) {
+        PK(cudaMemcpyAsync(orow_ptr, orow_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s),
+           "copy oriented row_ptr");
+        PK(cudaMemcpyAsync(ocol_idx, ocol_h.data(), sizeof(int32_t) * ocol_h.size(), cudaMemcpyHostToDevice, s),
+           "copy oriented col_idx");
+    }
     PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
     PK(cudaMemcpyAsync(gst, st0.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, s), "init graph state");
     PK(cudaMemsetAsync(ps, 0, sizeof(PackState), s), "init pack state");
     PK(cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "copy active list");
     PK(cudaMemcpyAsync(vchunks, vch.data(), sizeof(int4) * vch.size(), cudaMemcpyHostToDevice, s), "copy chunks");
-    PK(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * key_slots, s), "clear edge sets");
+    PK(cudaMemsetAsync(keys, 0xFF, (narrow_keys ? 4 : 8) * key_slots, s), "clear edge sets");
     PK(cudaMemsetAsync(x, 0, sizeof(float) * R * d, s), "clear x");
     if (xb) PK(cudaMemsetAsync(xb, 0, sizeof(__nv_bfloat16) * R * d, s), "clear xb");
     PK(cudaMemsetAsync(acc, 0, sizeof(float) * R * acc_stride, s), "clear acc");
@@ -404,7 +439,9 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     PK(cudaMemsetAsync(scratch, 0, sizeof(int32_t), s), "clear flag");
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
-        PK(launch_hash_build(row_ptr, col_idx, gi.v0, gi.n, nnz[g], keys + gi.key_off, gi.bucket_mask, scratch, s),
+        PK(launch_hash_build(row_ptr, col_idx, gi.v0, gi.n, nnz[g],
+                             static_cast<char*>(keys) + (narrow_keys ? 4 : 8) * gi.key_off, narrow_keys ? 1 : 0,
+                             gi.bucket_mask, scratch, s),
            "hash build");
         PK(launch_init_positions(x + (size_t)gi.v0 * d, xb ? xb + (size_t)gi.v0 * d : nullptr, gi.n, d, gi.key_lo,
                                  gi.key_hi, p.init_range, s),
@@ -436,7 +473,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     const size_t tiles = blk ? ((size_t)n + kBlockT - 1) / kBlockT : 0;
     const size_t units_max = (size_t)n + (size_t)nnz / 8 + 16;
     size_t b = 0;
-    b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1)) + al(8 * table_slots(nnz));
+    b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1)) + al((n <= kNarrowKeysMaxN ? 4 : 8) * table_slots(nnz));
     b += al(4 * R * d) + al(4 * R * acc_stride_for(d));
     if (p.precision == 1 && d >= 8) b += al(2 * R * d);
     b += al(bins * 20) + al(sizeof(GraphInfo)) + al(sizeof(GraphState)) + al(sizeof(PackState)) + al(4);
@@ -444,6 +481,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     const bool ps = p.sampling == 1;
     b += al(4 * std::max<size_t>(blk ? 1 : (ps ? 2 * (size_t)nnz : 2 * R * k), 1)) + al(16 * units_max) + al(4 * 4097);
     if (ps) b += al(8 * R);
+    if (d <= kPackedMaxDim && !ps && !blk) b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz / 2, 1));
     if (p.membership == 1 && !blk) b += al((size_t)1 << bytemap_log2_for(nnz, p));
     if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
     return b;
@@ -462,7 +500,9 @@ gempe_status Pack::set_shape(const PackShape& s) {
     const bool per_unit = d > kPackedMaxDim || sh.kernel == 1;   // the kernel with lane groups per unit
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
-        if (!per_unit) packed_units(row_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g, per_slot, units);
+        if (!per_unit)
+            packed_units(orow_ptr_h.empty() ? row_ptr_h.data() : orow_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g,
+                         per_slot, units);
         else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, per_slot, units);
     }
     const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm, sh.kernel);
@@ -537,7 +577,11 @@ EpochArgs Pack::args() const {
     a.n_active = G;
     a.row_ptr = row_ptr;
     a.col_idx = col_idx;
+    a.orow_ptr = orow_ptr;
+    a.ocol_idx = ocol_idx;
+    a.oriented = (orow_ptr && shape.kernel == 0) ? 1 : 0;
     a.keys = keys;
+    a.narrow_keys = narrow_keys ? 1 : 0;
     a.x = x;
     a.xb = xb;
     a.acc = acc;

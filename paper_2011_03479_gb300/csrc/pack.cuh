@@ -42,6 +42,7 @@ struct Pack {
     int32_t G = 0, rows = 0, n_tiles = 0;
     int64_t slots = 0;
     unsigned long long key_slots = 0;
+    bool narrow_keys = false;        // every graph has n <= 65536: u32 edge keys
     bool block = false, tiles = false;
     bool per_slot = false;           // Sec. III.C's policy: one sample per CSR slot
     int device = 0, sm_count = 0;
@@ -54,6 +55,7 @@ struct Pack {
     std::vector<GraphInfo> info;     // host copies
     std::vector<int64_t> nnz;
     std::vector<int32_t> row_ptr_h;  // pack CSR offsets, rows + 1
+    std::vector<int32_t> orow_ptr_h; // degree-oriented CSR offsets (d <= 4, k-per-vertex policy), else empty
     PackShape shape;
 
     // device memory
@@ -63,7 +65,9 @@ struct Pack {
     int32_t* active = nullptr;
     int32_t* row_ptr = nullptr;
     int32_t* col_idx = nullptr;
-    unsigned long long* keys = nullptr;
+    int32_t* orow_ptr = nullptr;     // degree-oriented CSR (see orow_ptr_h)
+    int32_t* ocol_idx = nullptr;
+    void* keys = nullptr;            // edge sets, key_slots keys of 4 (narrow) or 8 bytes
     float* x = nullptr;
     __nv_bfloat16* xb = nullptr;
     float* acc = nullptr;

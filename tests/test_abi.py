@@ -119,15 +119,16 @@ def test_batch_rejects_invalid_graphs_on_host():
 
 def test_job_bytes_formula():
     """gempe_job_bytes (host arithmetic) covers at least the resident state
-    the serving admission counts: CSR, edge table (next power of two of
-    2 nnz, 8-byte keys), positions, accumulators; it grows with n, nnz, d
-    and with the BF16 shadow; invalid arguments give 0."""
+    the serving admission counts: CSR, edge table (every undirected edge
+    once at load 1/2: next power of two of nnz slots, 8-byte keys above
+    65,536 vertices, 4-byte keys up to it), positions, accumulators; it
+    grows with n, nnz, d and with the BF16 shadow; invalid arguments give 0."""
     from paper_2011_03479_gb300 import binding as B
     p = B.gempe_default_params(neg_per_vertex=10)
     n, nnz = 100_000, 1_600_000
     for d in (2, 32, 128):
         b = B.gempe_job_bytes(n, nnz, d, p)
-        table = 8 * (1 << int(np.ceil(np.log2(2 * nnz))))
+        table = 8 * (1 << int(np.ceil(np.log2(nnz))))
         floor = 4 * (n + 1) + 4 * nnz + table + 4 * n * d + 4 * n * (d + 1)
         assert b >= floor
         assert b < 2 * floor + (64 << 20)
