@@ -67,16 +67,34 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted):
+def oriented_degrees(row_ptr, col_idx):
+    """Out-degrees of the degree-oriented CSR the packed sweep (d <= 4, k
+    samples per vertex) runs on: edge (i, j) belongs to i when
+    (deg j, j) < (deg i, i), so each undirected edge appears once."""
+    import numpy as np
+    deg = np.diff(row_ptr).astype(np.int64)
+    rows = np.repeat(np.arange(len(deg)), deg)
+    ci = np.asarray(col_idx, dtype=np.int64)
+    keep = (deg[ci] < deg[rows]) | ((deg[ci] == deg[rows]) & (ci < rows))
+    return np.bincount(rows[keep], minlength=len(deg))
+
+
+def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted, oriented=False):
     """Bytes one sweep launch must move at least, each random gather paid once
     at its minimum size (no reuse): CSR streamed once, work units, the sample
-    slots, own row, one neighbour row per CSR slot, the partner row and a
-    read-modify-write of the partner's accumulator row per accepted sample,
-    a read-modify-write of every own accumulator row."""
+    slots, own row, a read-modify-write of every own accumulator row, the
+    partner row and a read-modify-write of the partner's accumulator row per
+    accepted sample, and per edge slot the neighbour's row -- once per CSR
+    slot when each endpoint sums its own edges, or (oriented form) once per
+    undirected edge plus the read-modify-write of the other endpoint's
+    accumulator row, with the full row offsets read for the degrees."""
     row = 4 * d
     acc_row = 4 * (((d + 1) + 3) // 4 * 4)
-    return (4 * (n + 1) + 4 * nnz + 16 * n_units + 4 * n * k + n * row + nnz * row
-            + accepted * (row + 2 * acc_row) + n * 2 * acc_row)
+    common = 16 * n_units + 4 * n * k + n * row + n * 2 * acc_row + accepted * (row + 2 * acc_row)
+    if oriented:
+        m = nnz // 2
+        return common + 8 * (n + 1) + 4 * m + m * (row + 2 * acc_row)
+    return common + 4 * (n + 1) + 4 * nnz + nnz * row
 
 
 def tile_algorithmic_bytes(n, d, n_tiles, partners=64):
@@ -92,12 +110,16 @@ def sampler_algorithmic_bytes(n, k, draws):
     return 32 * draws + 4 * n * k
 
 
-def work_units(row_ptr, k, d, edge_chunk=EDGE_CHUNK, unit_pairs=UNIT_PAIRS):
-    """Number of sweep work units (mirrors the library's unit building)."""
+def work_units(row_ptr, k, d, edge_chunk=EDGE_CHUNK, unit_pairs=UNIT_PAIRS, out_degrees=None, kernel=0):
+    """Number of sweep work units (mirrors the library's unit building: d >= 8
+    or kernel 1, chunks of each vertex's row; d <= 4 packed units, over the
+    oriented CSR's out-degrees when they are given)."""
     import numpy as np
     deg = np.diff(row_ptr).astype(np.int64)
-    if d > 4:
+    if d > 4 or kernel == 1:
         return int(np.maximum(1, (deg + edge_chunk - 1) // edge_chunk).sum())
+    if out_degrees is not None:
+        deg = np.asarray(out_degrees, dtype=np.int64)
     units, i, n = 0, 0, len(deg)
     pairs = deg + k
     while i < n:
@@ -362,10 +384,11 @@ def run_gempe(args):
         return
 
     peak, peak_kind = _peaks()
-    units = work_units(rp, k, d)
     block = bool(form.get("block_partners"))
+    oriented = d <= 4 and not block and not form.get("sampling")
+    units = work_units(rp, k, d, out_degrees=oriented_degrees(rp, ci) if oriented else None)
     bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, 0 if block else k, units,
-                                              0 if block else accepted / args.steps)
+                                              0 if block else accepted / args.steps, oriented=oriented)
     if block and form.get("precision") and d in (16, 32, 64):
         bytes_per_sweep += tile_algorithmic_bytes(n, d, (n + 127) // 128)
     sweep_s = statistics.mean(sweep_ms) / 1e3
@@ -520,8 +543,10 @@ def run_batch(args):
         rp, ci, d = g["row_ptr"], g["col_idx"], g["d"]
         n = len(rp) - 1
         sh = shapes[d]
-        units = work_units(rp, k, d, edge_chunk=sh["unit"], unit_pairs=sh["unit"])
-        byts += sweep_algorithmic_bytes(n, len(ci), d, k, units, acc_per_epoch * (n / n_tot))
+        oriented = d <= 4 and sh.get("kernel", 0) == 0
+        units = work_units(rp, k, d, edge_chunk=sh["unit"], unit_pairs=sh["unit"],
+                           out_degrees=oriented_degrees(rp, ci) if oriented else None, kernel=sh.get("kernel", 0))
+        byts += sweep_algorithmic_bytes(n, len(ci), d, k, units, acc_per_epoch * (n / n_tot), oriented=oriented)
     step_s = statistics.mean(step_ms) / 1e3
     achieved = byts / step_s / 1e9
     line = {

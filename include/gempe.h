@@ -283,10 +283,12 @@ gempe_status gempe_batch_positions(gempe_batch* b, int32_t graph, float* host_ou
 gempe_status gempe_batch_loss(gempe_batch* b, int32_t graph, double* out_pe_bits, float* out_sigma);
 gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_stats_t* out);
 /* Launch shape of the pack holding dimension d: out[0] unit pair budget
- * (d <= 4) or CSR slots per unit (d >= 8), out[1] lanes per pair, out[2]
- * sweep CTAs per SM (0 = all that fit), out[3] sweep grid, out[4] graphs in
- * the pack, out[5] tuned sweep time in ns (0 if not tuned). */
-gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out6);
+ * (packed units, d <= 4) or CSR slots per unit (one lane group per vertex),
+ * out[1] lanes per pair, out[2] sweep CTAs per SM (0 = all that fit), out[3]
+ * sweep grid, out[4] graphs in the pack, out[5] tuned sweep time in ns (0 if
+ * not tuned), out[6] the sweep kernel (d <= 4: 0 packed units, 1 one lane per
+ * vertex; 0 for d >= 8). */
+gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out7);
 
 /* ------------------------------------------------------------------------
  * Serving form: embedding jobs admitted by device-memory budget and run with

@@ -462,10 +462,10 @@ def gempe_batch_stats(b: _Batch, graph: int) -> dict:
 
 
 def gempe_batch_shape(b: _Batch, d: int) -> dict:
-    out = (ctypes.c_int64 * 6)()
+    out = (ctypes.c_int64 * 7)()
     _check(load().gempe_batch_shape(b.handle, int(d), out))
     return {"unit": out[0], "lanes": out[1], "blocks_per_sm": out[2], "grid": out[3], "graphs": out[4],
-            "tuned_sweep_ns": out[5]}
+            "tuned_sweep_ns": out[5], "kernel": out[6]}
 
 
 def gempe_job_bytes(n: int, nnz: int, d: int, params: gempe_params | None = None) -> int:

@@ -245,16 +245,18 @@ GEMPE_API gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_st
     return GEMPE_OK;
 }
 
-GEMPE_API gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out6) {
-    if (!b || !out6) return pack_fail(GEMPE_E_INVALID_ARG, "null argument");
+GEMPE_API gempe_status gempe_batch_shape(gempe_batch* b, int32_t d, int64_t* out7) {
+    if (!b || !out7) return pack_fail(GEMPE_E_INVALID_ARG, "null argument");
     for (auto& pk : b->packs) {
         if (pk->d != d) continue;
-        out6[0] = d <= kPackedMaxDim ? pk->shape.unit_pairs : pk->shape.edge_chunk;
-        out6[1] = pk->shape.lanes ? pk->shape.lanes : (d <= kPackedMaxDim ? 1 : d / 8);
-        out6[2] = pk->shape.blocks_per_sm;
-        out6[3] = pk->sweep_grid;
-        out6[4] = pk->G;
-        out6[5] = (int64_t)(pk->shape.sweep_us * 1000.0f);
+        const bool packed = d <= kPackedMaxDim && pk->shape.kernel == 0;
+        out7[0] = packed ? pk->shape.unit_pairs : pk->shape.edge_chunk;
+        out7[1] = pk->shape.lanes ? pk->shape.lanes : (d <= kPackedMaxDim ? 1 : d / 8);
+        out7[2] = pk->shape.blocks_per_sm;
+        out7[3] = pk->sweep_grid;
+        out7[4] = pk->G;
+        out7[5] = (int64_t)(pk->shape.sweep_us * 1000.0f);
+        out7[6] = pk->shape.kernel;
         return GEMPE_OK;
     }
     return pack_fail(GEMPE_E_INVALID_ARG, "no graph of that dimension in the batch");

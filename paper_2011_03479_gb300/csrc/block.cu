@@ -151,8 +151,7 @@ __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const Epoc
     }
     __syncthreads();
     if (s_last) {
-        for (int t = threadIdx.x; t < a.n_active; t += blockDim.x) {
-            const int graph = a.active[t];
+        for (int graph = threadIdx.x; graph < a.n_graphs; graph += blockDim.x) {
             GraphState* st = a.gst + graph;
             const unsigned long long slots = (unsigned long long)__ldg(&a.graphs[graph].n) * kBlockP;
             atomicAdd(&st->accepted, slots);
@@ -574,12 +573,11 @@ cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s) {
     if (a.n_tile_items == 0) return cudaSuccess;
     const size_t smem = tile_smem_bytes(a.d, a.bins);
     switch (a.d) {
-        case 16: k_tile_bf16<16><<<grid, kTileThreads, smem, s>>>(a); break;
-        case 32: k_tile_bf16<32><<<grid, kTileThreads, smem, s>>>(a); break;
-        case 64: k_tile_bf16<64><<<grid, kTileThreads, smem, s>>>(a); break;
+        case 16: return launch_critical(k_tile_bf16<16>, grid, kTileThreads, smem, s, a);
+        case 32: return launch_critical(k_tile_bf16<32>, grid, kTileThreads, smem, s, a);
+        case 64: return launch_critical(k_tile_bf16<64>, grid, kTileThreads, smem, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace gempe

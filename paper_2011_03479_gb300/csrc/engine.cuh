@@ -67,6 +67,7 @@ constexpr int kUpdateThreads = 1024;
 constexpr int kSigmaMaxIters = 60;
 constexpr int kVChunk = 1024;          // vertices per vertex chunk
 constexpr int kSamplerSub = 64;        // vertices per sampler block iteration
+constexpr int kSamplerBatch = 1;       // draws a sampler thread keeps in flight
 constexpr int kGraphShift = 8;         // unit.y = graph << kGraphShift | vertex count
 
 // Work units: int4 {v0, graph << 8 | nv, e_lo, e_hi | flags}.  e_lo < 0: nv
@@ -100,8 +101,6 @@ struct EpochArgs {
     GraphState* gst;
     PackState* ps;
     int32_t n_graphs;
-    const int32_t* active;    // graphs this epoch steps (slope fit, epoch and sampler advance)
-    int32_t n_active;
     // CSR, edge sets, positions, accumulators
     const int32_t* row_ptr;   // [rows + 1] absolute slot offsets
     const int32_t* col_idx;   // pack row ids
@@ -196,6 +195,27 @@ int sampler_grid(int rows, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);
 cudaError_t launch_is_edge(const void* keys, int narrow, unsigned long long key_off, unsigned long long bucket_mask,
                            const int32_t* pairs, int64_t count, uint8_t* out, cudaStream_t s);
+// Kernels on an epoch's critical path (sweeps, tiles, update, slope fit)
+// launch at the device's highest stream priority, so that when SMs free up
+// their blocks are dispatched ahead of those of the next epoch's sampler,
+// which runs beside them on the side stream and has until the next sweep.
+int critical_priority();
+template <typename... KArgs, typename... Args>
+cudaError_t launch_critical(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributePriority;
+    attr.val.priority = critical_priority();
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Message for gempe_last_error() on the calling thread.
 void set_last_error(const char* msg);
 

@@ -265,6 +265,70 @@ __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSet
     return -1;
 }
 
+// Attempts att0, att0 + 1, ... of the same draw (att0 >= 1: the earlier
+// attempts were rejected by the caller, who counted them).
+__device__ __forceinline__ int sample_partner_from(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
+                                                   int i, int epoch, int t, uint32_t tag, int att0,
+                                                   unsigned& rejected, const Membership& m, unsigned& false_pos) {
+    const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    for (int att = att0; att < max_retries; ++att) {
+        if ((att & 3) == 0 || att == att0)
+            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
+                              gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
+        ++rejected;
+    }
+    return -1;
+}
+
+// The first bucket of an exact-set probe, loaded ahead of its use so that a
+// thread keeps several probes in flight.
+struct FirstProbe {
+    uint4 lo, hi;
+};
+
+__device__ __forceinline__ FirstProbe probe_issue(const EdgeSets& es, const GraphInfo& gi, int i, int g) {
+    const uint4* q;
+    if (es.narrow) {
+        const unsigned long long b = mix64(edge_key32(i, g)) & gi.bucket_mask;
+        q = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(es.keys) + gi.key_off + 8 * b);
+    } else {
+        const unsigned long long b = mix64(edge_key(i, g)) & gi.bucket_mask;
+        q = reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(es.keys) + gi.key_off + 4 * b);
+    }
+    FirstProbe p;
+    p.lo = __ldg(q);
+    p.hi = __ldg(q + 1);
+    return p;
+}
+
+// Membership of {i, g} from its first bucket: decided there unless the
+// bucket is full without the key, then by a full probe.
+__device__ __forceinline__ bool probe_resolve(const EdgeSets& es, const GraphInfo& gi, int i, int g,
+                                              const FirstProbe& p) {
+    bool hit, open;
+    if (es.narrow) {
+        const uint32_t key = edge_key32(i, g);
+        hit = p.lo.x == key || p.lo.y == key || p.lo.z == key || p.lo.w == key || p.hi.x == key ||
+              p.hi.y == key || p.hi.z == key || p.hi.w == key;
+        open = p.lo.x == kEmptyKey32 || p.lo.y == kEmptyKey32 || p.lo.z == kEmptyKey32 || p.lo.w == kEmptyKey32 ||
+               p.hi.x == kEmptyKey32 || p.hi.y == kEmptyKey32 || p.hi.z == kEmptyKey32 || p.hi.w == kEmptyKey32;
+    } else {
+        const unsigned long long key = edge_key(i, g);
+        const unsigned long long k0 = ((unsigned long long)p.lo.y << 32) | p.lo.x;
+        const unsigned long long k1 = ((unsigned long long)p.lo.w << 32) | p.lo.z;
+        const unsigned long long k2 = ((unsigned long long)p.hi.y << 32) | p.hi.x;
+        const unsigned long long k3 = ((unsigned long long)p.hi.w << 32) | p.hi.z;
+        hit = k0 == key || k1 == key || k2 == key || k3 == key;
+        open = k0 == kEmptyKey || k1 == kEmptyKey || k2 == kEmptyKey || k3 == kEmptyKey;
+    }
+    if (hit) return true;
+    if (open) return false;
+    return edge_set_contains(es.keys, es.narrow, gi.key_off, gi.bucket_mask, i, g);
+}
+
 // The same with the exact edge set (loss, slope-pass and inspection draws).
 __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
                                               int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
@@ -333,8 +397,8 @@ __device__ __forceinline__ void sampler_done(const EpochArgs& a) {
     }
     __syncthreads();
     if (s_last) {
-        for (int t = threadIdx.x; t < a.n_active; t += blockDim.x) {
-            GraphState* st = a.gst + a.active[t];
+        for (int t = threadIdx.x; t < a.n_graphs; t += blockDim.x) {
+            GraphState* st = a.gst + t;
             st->sample_epoch = st->sample_epoch + 1;
         }
         if (threadIdx.x == 0) a.ps->sample_done = 0u;
@@ -383,11 +447,41 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
         const int local0 = row0 - gi.v0;
         int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0) * k;
         const int total = cnt * k;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int i = idx / k, t = idx - i * k;
-            const int g = sample_partner(gi, edge_sets(a), a.max_retries, local0 + i, se, t, kTagEpoch, c[1], m, c[3]);
-            out[idx] = g >= 0 ? gi.v0 + g : -1;
-            if (g >= 0) ++c[0]; else ++c[2];
+        const EdgeSets es = edge_sets(a);
+        // kSamplerBatch draws per thread at a time: their first attempts and
+        // first-bucket probes are all issued before any is resolved
+        for (int base = 0; base < total; base += kSamplerBatch * blockDim.x) {
+            int g0[kSamplerBatch];
+            FirstProbe pr[kSamplerBatch];
+#pragma unroll
+            for (int q = 0; q < kSamplerBatch; ++q) {
+                const int idx = base + q * blockDim.x + threadIdx.x;
+                g0[q] = -1;
+                if (idx < total) {
+                    const int i = local0 + idx / k, t = idx % k;
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)t, kTagEpoch),
+                                                  gi.key_lo, gi.key_hi);
+                    g0[q] = draw_vertex(r.x, (uint32_t)gi.n);
+                    if (!m.map && g0[q] != i) pr[q] = probe_issue(es, gi, i, g0[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kSamplerBatch; ++q) {
+                const int idx = base + q * blockDim.x + threadIdx.x;
+                if (idx >= total) continue;
+                const int i = local0 + idx / k, t = idx % k;
+                int g = g0[q];
+                bool taken;
+                if (g == i) taken = true;
+                else if (m.map) taken = taken_for_edge(gi, es, m, renamed(m, (uint32_t)i), i, g, c[3]);
+                else taken = probe_resolve(es, gi, i, g, pr[q]);
+                if (taken) {
+                    ++c[1];
+                    g = sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
+                }
+                out[idx] = g >= 0 ? gi.v0 + g : -1;
+                if (g >= 0) ++c[0]; else ++c[2];
+            }
         }
     }
     if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
@@ -931,12 +1025,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 //   F(t)  = sum_b c_e[b] (-u h(u)) + c_n[b] (u g(u)),     g(u) = h(-u),
 // and, from h' = h (h - u) = h T,
 //   F'(t) = sum_b c_e[b] u h (1 + u T(u)) - c_n[b] u g (1 - u T(-u)).
-// The root is bracketed as in the paper's bisection (log sigma on
-// [1e-3, 1e3]; no sign change -> the end with the lower entropy) and found
-// by Newton steps in t from the previous sigma, falling back to halving the
-// bracket whenever a step leaves it.  One whole block runs the search on a
-// shared-memory copy of the histograms: per-bin terms in FP32, block sums
-// by warp shuffles, the Newton step by one thread.
+// The paper bisects in log sigma on [1e-3, 1e3] (no sign change: the end
+// with the lower entropy).  The same root is found here by Newton steps in t
+// from the previous sigma, with that bracket as the fallback (see
+// block_fit_sigma).  One whole block runs the search on a shared-memory copy
+// of the histograms: per-bin terms in FP32, block sums by warp shuffles, the
+// step by one thread.
 // ---------------------------------------------------------------------------
 struct SigmaSmem {
     float4 part[32];
@@ -1025,18 +1119,77 @@ __device__ __forceinline__ void newton_update(float f, float df, bool lo_pos, Si
     sm.inv_s = expf(-tn);
 }
 
+// Block sums of F and F' at t = -ln(inv_s) over the non-empty bins.
+__device__ __forceinline__ float4 block_dpe(const float* he, const float* hn, int bins, float bin_w, float mu,
+                                            float inv_s, const MillsCoef* tab, SigmaSmem& sm) {
+    float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+        if (he[b] == 0.0f && hn[b] == 0.0f) continue;
+        const float2 fd = dpe_bin(he[b], hn[b], ((float)b + 0.5f) * bin_w, mu, inv_s, tab);
+        p.x += fd.x;
+        p.y += fd.y;
+    }
+    return block_sum4(p, sm);
+}
+
 // Returns the new sigma (valid in every thread).  he/hn: shared-memory bins;
 // tab: the Mills-ratio table in shared memory.  Empty bins contribute
-// nothing and are skipped.  The first pass evaluates F at both bracket ends
-// (sigma = 1e-3, 1e3) and (F, F') at the previous sigma together.
+// nothing and are skipped.
+//
+// Newton steps in t from the previous sigma come first: while F' > 0 (F
+// rises through the root, the minimum of PE in sigma), each step is at most
+// 2 in t and stays in [ln 1e-3, ln 1e3], they converge to the root the
+// bracketed search would find, at one evaluation of (F, F') per step.  If
+// a step breaks one of those conditions, or 8 steps do not converge, the
+// bracketed search runs: F at both ends of [1e-3, 1e3] (no sign change: the
+// end with the lower entropy, as the paper's bisection does), then Newton
+// inside the bracket with the Illinois fallback.
 __device__ float block_fit_sigma(const float* he, const float* hn, int bins, float hist_max, float mu,
                                  float sigma_prev, const MillsCoef* tab, SigmaSmem& sm) {
+    constexpr int kFreeSteps = 8;
     const float bin_w = hist_max / (float)bins;
     const bool lead = threadIdx.x == 0;
-    SigmaSearch q{-6.9077553f, 6.9077553f, 0.0f, 0.0f, 0.0f, 0};   // ln 1e-3, ln 1e3
-    q.t = (sigma_prev > 0.0f) ? logf(sigma_prev) : 0.0f;
-    if (!(q.t > q.lo && q.t < q.hi)) q.t = 0.0f;
-    const float inv_s0 = expf(-q.t);
+    const float t_lo = -6.9077553f, t_hi = 6.9077553f;   // ln 1e-3, ln 1e3
+    float t0 = (sigma_prev > 0.0f) ? logf(sigma_prev) : 0.0f;
+    if (!(t0 > t_lo && t0 < t_hi)) t0 = 0.0f;
+    float t = t0;
+    if (lead) {
+        sm.inv_s = expf(-t0);
+        sm.done = 0;
+        sm.iters = 0;
+    }
+    __syncthreads();
+    int it = 0;
+    bool bracketed = true;
+    while (it < kFreeSteps) {
+        ++it;
+        const float4 fd = block_dpe(he, hn, bins, bin_w, mu, sm.inv_s, tab, sm);
+        if (lead) {
+            const float step = -fd.x / fd.y;
+            const float tn = t + step;
+            if (!(fd.y > 0.0f) || !(fabsf(step) <= 2.0f) || !(tn > t_lo && tn < t_hi)) {
+                sm.done = 2;   // leave the search to the bracket
+            } else {
+                sm.done = fabsf(step) < 1e-5f ? 1 : 0;
+                t = tn;
+                sm.inv_s = expf(-tn);
+                sm.iters = it;
+            }
+        }
+        __syncthreads();
+        const int done = sm.done;
+        __syncthreads();   // every thread has read sm.done before it changes
+        if (done == 1) {
+            bracketed = false;
+            break;
+        }
+        if (done == 2) break;
+    }
+    if (!bracketed) return 1.0f / sm.inv_s;
+
+    // the bracketed search from the previous sigma
+    SigmaSearch q{t_lo, t_hi, 0.0f, 0.0f, t0, 0};
+    const float inv_s0 = expf(-t0);
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int b = threadIdx.x; b < bins; b += blockDim.x) {
         const float ce = he[b], cn = hn[b], c = ((float)b + 0.5f) * bin_w;
@@ -1049,30 +1202,23 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
     }
     const float4 tot = block_sum4(acc, sm);
     bool lo_pos = false;
+    ++it;
     if (lead) {
         lo_pos = tot.x > 0.0f;
         if ((tot.x > 0.0f) == (tot.y > 0.0f)) {
             // no sign change: the bracket end with the lower entropy
             sm.inv_s = lo_pos ? 1e3f : 1e-3f;
             sm.done = 1;
-            sm.iters = 0;
+            sm.iters = it;
         } else {
             q.f_lo = tot.x;
             q.f_hi = tot.y;
-            newton_update(tot.z, tot.w, lo_pos, q, sm, 1);
+            newton_update(tot.z, tot.w, lo_pos, q, sm, it);
         }
     }
     __syncthreads();
-    for (int it = 2; it <= kSigmaMaxIters && !sm.done; ++it) {
-        const float inv_s = sm.inv_s;
-        float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-            if (he[b] == 0.0f && hn[b] == 0.0f) continue;
-            const float2 fd = dpe_bin(he[b], hn[b], ((float)b + 0.5f) * bin_w, mu, inv_s, tab);
-            p.x += fd.x;
-            p.y += fd.y;
-        }
-        const float4 fd = block_sum4(p, sm);
+    for (++it; it <= kSigmaMaxIters && !sm.done; ++it) {
+        const float4 fd = block_dpe(he, hn, bins, bin_w, mu, sm.inv_s, tab, sm);
         if (lead) newton_update(fd.x, fd.y, lo_pos, q, sm, it);
         __syncthreads();
     }
@@ -1102,26 +1248,29 @@ __device__ void load_hist_smem(const EpochArgs& a, size_t off, int n, int k_slot
     __syncthreads();
 }
 
-// Blocks [0, n_active): the slope fit, histogram reset and epoch advance of
+// Blocks [0, n_graphs): the slope fit, histogram reset and epoch advance of
 // one stepped graph each.  The other blocks: x_i := y_i / z_i over the vertex
 // chunks, accumulators cleared for the next epoch.
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
-    if ((int)blockIdx.x < a.n_active) {
+    if ((int)blockIdx.x < a.n_graphs) {
         __shared__ SigmaSmem sm;
         extern __shared__ __align__(16) float s_bins[];   // [2][bins], then the Mills table
         MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
                                                         ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
-        const int graph = a.active[blockIdx.x];
+        const int graph = blockIdx.x;
         GraphState* st = a.gst + graph;
         const size_t off = (size_t)graph * a.bins;
         const int epoch = st->epoch;
+        const float sigma_prev = st->sigma;
         // sigma_source 1: the fit follows in k_fit_graphs on the separate pass's histograms
-        if (a.sigma_every > 0 && ((epoch + 1) % a.sigma_every) == 0 && a.sigma_source == 0) {
+        const bool fit = a.sigma_source == 0 &&
+                         (a.sigma_every == 1 || (a.sigma_every > 1 && ((epoch + 1) % a.sigma_every) == 0));
+        if (fit) {
             const int k_slots = a.block_P > 0 ? kBlockP : a.k;
             load_mills_smem(s_tab);
             load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);
             const float s =
-                block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, st->sigma, s_tab, sm);
+                block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, sigma_prev, s_tab, sm);
             if (threadIdx.x == 0) {
                 st->sigma = s;
                 st->sigma_iters = sm.iters;
@@ -1136,7 +1285,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
         if (threadIdx.x == 0) st->epoch = epoch + 1;
         return;
     }
-    const int vblk = blockIdx.x - a.n_active, n_vblk = gridDim.x - a.n_active;
+    const int vblk = blockIdx.x - a.n_graphs, n_vblk = gridDim.x - a.n_graphs;
     if (a.d >= 8) {
         // L = min(32, d/4) lanes per vertex, float4 over the dimensions (at most 2 per lane)
         const int lane = threadIdx.x & 31;
@@ -1319,7 +1468,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_fit_graphs(const EpochArgs a
     extern __shared__ __align__(16) float s_bins[];   // [2][bins], then the Mills table
     MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
                                                     ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
-    const int graph = a.active[blockIdx.x];
+    const int graph = blockIdx.x;
     GraphState* st = a.gst + graph;
     const size_t off = (size_t)graph * a.bins;
     if (a.sigma_every > 0 && (st->epoch % a.sigma_every) == 0) {
@@ -1466,16 +1615,14 @@ __global__ void k_is_edge(const void* keys, int narrow, unsigned long long key_o
 
 template <int D, int G>
 cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.xb) k_sweep<D, G, __nv_bfloat16><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
-    else k_sweep<D, G, float><<<grid, kSweepThreads, hist_smem_bytes(a.bins), s>>>(a);
-    return cudaGetLastError();
+    if (a.xb) return launch_critical(k_sweep<D, G, __nv_bfloat16>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, a);
+    return launch_critical(k_sweep<D, G, float>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, a);
 }
 
 template <int D>
 cudaError_t packed_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.oriented) k_sweep_packed<D, true><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
-    else k_sweep_packed<D, false><<<grid, kPackedThreads, packed_smem_bytes(D, a.bins), s>>>(a);
-    return cudaGetLastError();
+    if (a.oriented) return launch_critical(k_sweep_packed<D, true>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, a);
+    return launch_critical(k_sweep_packed<D, false>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, a);
 }
 
 template <int D, int G>
@@ -1638,7 +1785,8 @@ cudaError_t hist_pass_for(const EpochArgs& a, int grid, cudaStream_t s) {
     EpochArgs b = a;
     b.sweep_hist = 1;          // this pass bins its own distances
     b.per_slot = 0;            // with the integer sample weights of k samples per vertex
-    k_hist_pass<D, G><<<grid, 256, hist_smem_bytes(a.bins), s>>>(b);
+    const cudaError_t e = launch_critical(k_hist_pass<D, G>, grid, 256, hist_smem_bytes(a.bins), s, b);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1656,12 +1804,14 @@ cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fit_graphs(const EpochArgs& a, cudaStream_t s) {
-    k_fit_graphs<<<a.n_active, kUpdateThreads, fit_smem_bytes(a.bins), s>>>(a);
+    const cudaError_t e = launch_critical(k_fit_graphs, a.n_graphs, kUpdateThreads, fit_smem_bytes(a.bins), s, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {
-    k_update<<<grid, kUpdateThreads, fit_smem_bytes(a.bins), s>>>(a);
+    const cudaError_t e = launch_critical(k_update, grid, kUpdateThreads, fit_smem_bytes(a.bins), s, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1678,6 +1828,18 @@ cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
     if (a.per_slot) k_sampler_slots<<<grid, 256, 0, s>>>(a);
     else k_sampler<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+int critical_priority() {
+    static const int prio = [] {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return greatest;
+    }();
+    return prio;
 }
 
 cudaError_t launch_bytemap_build(const EpochArgs& a, int force, int sm_count, cudaStream_t s) {

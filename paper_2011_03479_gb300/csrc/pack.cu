@@ -377,7 +377,6 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     graphs = (GraphInfo*)alloc(sizeof(GraphInfo) * G);
     gst = (GraphState*)alloc(sizeof(GraphState) * G);
     ps = (PackState*)alloc(sizeof(PackState));
-    active = (int32_t*)alloc(sizeof(int32_t) * G);
     vchunks = (int4*)alloc(sizeof(int4) * vch.size());
     scratch = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>(R * std::max(k, 1), 1));
     samples = (int32_t*)alloc(sizeof(int32_t) *
@@ -399,12 +398,10 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         if (!block_part || !block_mask || !sampler_units || !tile_items)
             return pack_fail(GEMPE_E_OOM, "device allocation failed");
     }
-    if (!row_ptr || !col_idx || !keys || !x || !acc || !hist || !graphs || !gst || !ps || !active || !vchunks ||
+    if (!row_ptr || !col_idx || !keys || !x || !acc || !hist || !graphs || !gst || !ps || !vchunks ||
         !scratch || !samples || (p.precision == 1 && !xb))
         return pack_fail(GEMPE_E_OOM, "device allocation failed");
 
-    std::vector<int32_t> act(G);
-    for (int32_t g = 0; g < G; ++g) act[g] = g;
     std::vector<GraphState> st0(G);
     std::memset(st0.data(), 0, sizeof(GraphState) * G);
     for (auto& st : st0) {
@@ -422,7 +419,6 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
     PK(cudaMemcpyAsync(gst, st0.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, s), "init graph state");
     PK(cudaMemsetAsync(ps, 0, sizeof(PackState), s), "init pack state");
-    PK(cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s), "copy active list");
     PK(cudaMemcpyAsync(vchunks, vch.data(), sizeof(int4) * vch.size(), cudaMemcpyHostToDevice, s), "copy chunks");
     PK(cudaMemsetAsync(keys, 0xFF, (narrow_keys ? 4 : 8) * key_slots, s), "clear edge sets");
     PK(cudaMemsetAsync(x, 0, sizeof(float) * R * d, s), "clear x");
@@ -573,8 +569,6 @@ EpochArgs Pack::args() const {
     a.gst = gst;
     a.ps = ps;
     a.n_graphs = G;
-    a.active = active;
-    a.n_active = G;
     a.row_ptr = row_ptr;
     a.col_idx = col_idx;
     a.orow_ptr = orow_ptr;
@@ -653,19 +647,23 @@ gempe_status Pack::prime() {
 gempe_status Pack::enqueue_sweep() {
     gempe_status s = prime();
     if (s != GEMPE_OK) return s;
-    if (sampled() && !sampled_ahead) {
-        PK(cudaEventRecord(fork_ev, stream), "fork");
-        PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
-        PK(launch_epoch_sampler(*this, side), "sampler");
-        PK(cudaEventRecord(join_ev, side), "join");
-        sampled_ahead = true;
-    }
+    // the sweep is launched first (at high priority), the sampler after it
+    // from the same point of the stream, so that the sweep's resident wave
+    // takes the SMs and the sampler fills them as the sweep's blocks retire
+    const bool fork = sampled() && !sampled_ahead;
+    if (fork) PK(cudaEventRecord(fork_ev, stream), "fork");
     SweepShape ss;
     ss.grid = sweep_grid;
     ss.lanes = shape.lanes;
     ss.kernel = shape.kernel;
     PK(launch_sweep(args(), ss, stream), "sweep");
     if (tiles) PK(launch_tile_bf16(args(), tile_grid, stream), "tiles");
+    if (fork) {
+        PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
+        PK(launch_epoch_sampler(*this, side), "sampler");
+        PK(cudaEventRecord(join_ev, side), "join");
+        sampled_ahead = true;
+    }
     return GEMPE_OK;
 }
 

@@ -62,7 +62,6 @@ struct Pack {
     GraphInfo* graphs = nullptr;
     GraphState* gst = nullptr;
     PackState* ps = nullptr;
-    int32_t* active = nullptr;
     int32_t* row_ptr = nullptr;
     int32_t* col_idx = nullptr;
     int32_t* orow_ptr = nullptr;     // degree-oriented CSR (see orow_ptr_h)
