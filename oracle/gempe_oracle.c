@@ -53,12 +53,13 @@
  * "Parallel random numbers: as easy as 1, 2, 3", SC 2011), key =
  * (seed_lo, seed_hi); counter words:
  *   initial positions  (i, q, 0, 0x0A000000)         -> coordinates 4q..4q+3
- *   epoch samples      (i, epoch, t, 0x0B000000|a>>2) -> word a&3 (attempt a)
- *   loss samples       (i, epoch, t, 0x0E000000|a>>2) -> word a&3
+ *   epoch samples      (i, epoch, t>>2, 0x0B000000|a) -> word t&3 (slot t,
+ *                      attempt a: one call serves the attempt a of four slots)
+ *   loss samples       (i, epoch, t>>2, 0x0E000000|a) -> word t&3
  *   block partners     (tile, epoch, p>>2, 0x0D000000) -> word p&3
- *   per-slot samples   (e, epoch, 0, 0x0C000000|a>>2)  -> word a&3 (Sec. III.C's
+ *   per-slot samples   (e>>2, epoch, 0, 0x0C000000|a)  -> word e&3 (Sec. III.C's
  *                      policy: one sample per CSR slot e, anchored at its row)
- *   slope samples      (i, epoch, t, 0x0F000000|a>>2) -> word a&3 (the separate
+ *   slope samples      (i, epoch, t>>2, 0x0F000000|a) -> word t&3 (the separate
  *                      histogram pass of Sec. III.F)
  *   renaming           (period, 0, 0, 0x09000000)     -> words 0, 1 (byte-map
  *                      membership, Sec. III.C)
@@ -325,8 +326,7 @@ static void sample_vertex_bm(const int32_t* row_ptr, const int32_t* col_idx, int
     for (int32_t t = 0; t < k; ++t) {
         int32_t got = -1;
         for (int32_t a = 0; a < max_retries; ++a) {
-            uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t,
-                                     tag | ((uint32_t)a >> 2), a & 3);
+            uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t >> 2, tag | (uint32_t)a, t & 3);
             int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
             if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;
@@ -356,8 +356,8 @@ void orc_bytemap_addr(int32_t n, uint64_t seed, int32_t period, int32_t log2_siz
 }
 
 /* Sec. III.C's policy: every CSR slot e = (i, j) of row i carries one
- * non-edge partner of i, drawn with counter (e, epoch, 0, 0x0C000000 | a>>2)
- * word a & 3 (e counted from the start of the graph's CSR), redrawn while it
+ * non-edge partner of i, drawn with counter (e>>2, epoch, 0, 0x0C000000 | a)
+ * word e & 3 (e counted from the start of the graph's CSR), redrawn while it
  * hits i or an edge, at most max_retries times.  out[t]: the partner of slot
  * row_ptr[i] + t, or -1. */
 static void sample_slots(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
@@ -366,7 +366,7 @@ static void sample_slots(const int32_t* row_ptr, const int32_t* col_idx, int32_t
     for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int32_t got = -1;
         for (int32_t a = 0; a < max_retries; ++a) {
-            uint32_t r = philox_word(seed, (uint32_t)e, (uint32_t)epoch, 0u, 0x0C000000u | ((uint32_t)a >> 2), a & 3);
+            uint32_t r = philox_word(seed, (uint32_t)e >> 2, (uint32_t)epoch, 0u, 0x0C000000u | (uint32_t)a, e & 3);
             int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
             if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;

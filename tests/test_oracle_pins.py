@@ -276,7 +276,7 @@ def test_sampling_semantics(oracle_mod, sbm_small):
             # replay the candidate sequence from the (pinned) Philox words
             got = -1
             for a in range(R):
-                r = int(oracle_mod.philox4x32_10([i, ep, t, 0x0B000000 | (a >> 2)], key)[a & 3])
+                r = int(oracle_mod.philox4x32_10([i, ep, t >> 2, 0x0B000000 | a], key)[t & 3])
                 g = (r * n) >> 32
                 if g != i and g not in adj[i]:
                     got = g
@@ -504,7 +504,7 @@ def test_per_slot_sampling_semantics(oracle_mod, sbm_small):
         for e in range(rp[i], rp[i + 1]):
             got = -1
             for a in range(32):
-                word = int(oracle_mod.philox4x32_10([e, ep, 0, 0x0C000000 | (a >> 2)], key)[a & 3])
+                word = int(oracle_mod.philox4x32_10([e >> 2, ep, 0, 0x0C000000 | a], key)[e & 3])
                 g = (word * n) >> 32
                 if g != i and g not in adj[i]:
                     got = g
@@ -596,7 +596,7 @@ def test_bytemap_membership(oracle_mod, sbm_small):
     for i in range(n):
         for t in range(6):
             for att in range(32):
-                w = int(oracle_mod.philox4x32_10([i, 4, t, 0x0B000000 | (att >> 2)], key)[att & 3])
+                w = int(oracle_mod.philox4x32_10([i, 4, t >> 2, 0x0B000000 | att], key)[t & 3])
                 g = (w * n) >> 32
                 addr = int(oracle_mod.bytemap_addr(n, 33, 0, 8, [[i, g]])[0][0])
                 if g != i and addr not in marked:
