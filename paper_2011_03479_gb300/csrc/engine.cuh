@@ -67,7 +67,6 @@ constexpr int kUpdateThreads = 1024;
 constexpr int kSigmaMaxIters = 60;
 constexpr int kVChunk = 1024;          // vertices per vertex chunk
 constexpr int kSamplerSub = 64;        // vertices per sampler block iteration
-constexpr int kSamplerBatch = 1;       // draws a sampler thread keeps in flight
 constexpr int kGraphShift = 8;         // unit.y = graph << kGraphShift | vertex count
 
 // Work units: int4 {v0, graph << 8 | nv, e_lo, e_hi | flags}.  e_lo < 0: nv

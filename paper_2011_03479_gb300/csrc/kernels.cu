@@ -246,87 +246,36 @@ __device__ __forceinline__ bool taken_for_edge(const GraphInfo& gi, const EdgeSe
     return true;
 }
 
-// Draw the accepted partner (local id) of sample slot t of local vertex i of
-// a graph (Fig. 2: redraw while the pair is taken for an edge; also redraw
-// g == i), or -1 after max_retries draws.
-__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
-                                              int i, int epoch, int t, uint32_t tag, unsigned& rejected,
-                                              const Membership& m, unsigned& false_pos) {
-    const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    for (int att = 0; att < max_retries; ++att) {
-        if ((att & 3) == 0)
-            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
-                              gi.key_lo, gi.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
-        if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
-        ++rejected;
-    }
-    return -1;
+// Attempts of sample slot t of local vertex i of a graph: attempt a is word
+// t & 3 of counter (i, epoch, t >> 2, tag | a), so one Philox call gives
+// attempt a of four consecutive slots.
+__device__ __forceinline__ int draw_attempt(const GraphInfo& gi, int i, int epoch, int t, uint32_t tag, int att) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t >> 2, tag | (uint32_t)att),
+                                  gi.key_lo, gi.key_hi);
+    return draw_vertex(word_of(r, t & 3), (uint32_t)gi.n);
 }
 
-// Attempts att0, att0 + 1, ... of the same draw (att0 >= 1: the earlier
-// attempts were rejected by the caller, who counted them).
+// Attempts att0, att0 + 1, ... of slot t of local vertex i (Fig. 2: redraw
+// while the pair is taken for an edge; also redraw g == i); the accepted
+// partner (local id), or -1 after max_retries attempts in all.  att0 >= 1:
+// the caller drew and counted the earlier attempts.
 __device__ __forceinline__ int sample_partner_from(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
                                                    int i, int epoch, int t, uint32_t tag, int att0,
                                                    unsigned& rejected, const Membership& m, unsigned& false_pos) {
     const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
     for (int att = att0; att < max_retries; ++att) {
-        if ((att & 3) == 0 || att == att0)
-            r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)epoch, (uint32_t)t, tag | ((uint32_t)att >> 2)),
-                              gi.key_lo, gi.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+        const int g = draw_attempt(gi, i, epoch, t, tag, att);
         if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
         ++rejected;
     }
     return -1;
 }
 
-// The first bucket of an exact-set probe, loaded ahead of its use so that a
-// thread keeps several probes in flight.
-struct FirstProbe {
-    uint4 lo, hi;
-};
-
-__device__ __forceinline__ FirstProbe probe_issue(const EdgeSets& es, const GraphInfo& gi, int i, int g) {
-    const uint4* q;
-    if (es.narrow) {
-        const unsigned long long b = mix64(edge_key32(i, g)) & gi.bucket_mask;
-        q = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(es.keys) + gi.key_off + 8 * b);
-    } else {
-        const unsigned long long b = mix64(edge_key(i, g)) & gi.bucket_mask;
-        q = reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(es.keys) + gi.key_off + 4 * b);
-    }
-    FirstProbe p;
-    p.lo = __ldg(q);
-    p.hi = __ldg(q + 1);
-    return p;
-}
-
-// Membership of {i, g} from its first bucket: decided there unless the
-// bucket is full without the key, then by a full probe.
-__device__ __forceinline__ bool probe_resolve(const EdgeSets& es, const GraphInfo& gi, int i, int g,
-                                              const FirstProbe& p) {
-    bool hit, open;
-    if (es.narrow) {
-        const uint32_t key = edge_key32(i, g);
-        hit = p.lo.x == key || p.lo.y == key || p.lo.z == key || p.lo.w == key || p.hi.x == key ||
-              p.hi.y == key || p.hi.z == key || p.hi.w == key;
-        open = p.lo.x == kEmptyKey32 || p.lo.y == kEmptyKey32 || p.lo.z == kEmptyKey32 || p.lo.w == kEmptyKey32 ||
-               p.hi.x == kEmptyKey32 || p.hi.y == kEmptyKey32 || p.hi.z == kEmptyKey32 || p.hi.w == kEmptyKey32;
-    } else {
-        const unsigned long long key = edge_key(i, g);
-        const unsigned long long k0 = ((unsigned long long)p.lo.y << 32) | p.lo.x;
-        const unsigned long long k1 = ((unsigned long long)p.lo.w << 32) | p.lo.z;
-        const unsigned long long k2 = ((unsigned long long)p.hi.y << 32) | p.hi.x;
-        const unsigned long long k3 = ((unsigned long long)p.hi.w << 32) | p.hi.z;
-        hit = k0 == key || k1 == key || k2 == key || k3 == key;
-        open = k0 == kEmptyKey || k1 == kEmptyKey || k2 == kEmptyKey || k3 == kEmptyKey;
-    }
-    if (hit) return true;
-    if (open) return false;
-    return edge_set_contains(es.keys, es.narrow, gi.key_off, gi.bucket_mask, i, g);
+// All attempts of slot t of local vertex i.
+__device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries, int i,
+                                              int epoch, int t, uint32_t tag, unsigned& rejected,
+                                              const Membership& m, unsigned& false_pos) {
+    return sample_partner_from(gi, keys, max_retries, i, epoch, t, tag, 0, rejected, m, false_pos);
 }
 
 // The same with the exact edge set (loss, slope-pass and inspection draws).
@@ -334,22 +283,22 @@ __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSet
                                               int i, int epoch, int t, uint32_t tag, unsigned& rejected) {
     unsigned unused = 0u;
     const Membership exact{nullptr, 0u, (uint32_t)gi.n, 1u, 0u};
-    return sample_partner(gi, keys, max_retries, i, epoch, t, tag, rejected, exact, unused);
+    return sample_partner_from(gi, keys, max_retries, i, epoch, t, tag, 0, rejected, exact, unused);
 }
 
-// Sec. III.C's policy: the partner (local id) of CSR slot e_local of the
-// graph, anchored at local vertex i (the slot's row); counter
-// (e_local, epoch, 0, kTagSlot | attempt >> 2), -1 after max_retries draws.
-__device__ __forceinline__ int slot_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
-                                            int i, int e_local, int epoch, unsigned& rejected, const Membership& m,
-                                            unsigned& false_pos) {
+// Sec. III.C's policy: attempt a of CSR slot e_local of the graph (anchored
+// at local vertex i, the slot's row) is word e_local & 3 of counter
+// (e_local >> 2, epoch, 0, kTagSlot | a); the partner, or -1 after
+// max_retries attempts.  att0 >= 1: the earlier attempts were drawn and
+// counted by the caller.
+__device__ __forceinline__ int slot_partner_from(const GraphInfo& gi, const EdgeSets& keys, int max_retries,
+                                                 int i, int e_local, int epoch, int att0, unsigned& rejected,
+                                                 const Membership& m, unsigned& false_pos) {
     const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    for (int att = 0; att < max_retries; ++att) {
-        if ((att & 3) == 0)
-            r = philox4x32_10(make_uint4((uint32_t)e_local, (uint32_t)epoch, 0u, kTagSlot | ((uint32_t)att >> 2)),
-                              gi.key_lo, gi.key_hi);
-        const int g = draw_vertex(word_of(r, att & 3), (uint32_t)gi.n);
+    for (int att = att0; att < max_retries; ++att) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)e_local >> 2, (uint32_t)epoch, 0u, kTagSlot | (uint32_t)att),
+                                      gi.key_lo, gi.key_hi);
+        const int g = draw_vertex(word_of(r, e_local & 3), (uint32_t)gi.n);
         if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
         ++rejected;
     }
@@ -411,26 +360,37 @@ template <> __device__ __forceinline__ const float* pos_of<float>(const EpochArg
 template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16>(const EpochArgs& a) { return a.xb; }
 
 // ---------------------------------------------------------------------------
-// The sampler: for each stepped graph, one thread per (vertex, sample slot)
-// of the graph's epoch sample_epoch, written to samples[sample_epoch & 1] as
-// pack rows.  It depends on the graph and the epoch only, so it runs beside
-// the previous epoch's sweep.  Blocks take 64-vertex pieces of the vertex
-// chunks (one graph each).
+// The sampler: for every graph of the pack, the k samples of each vertex for
+// the graph's epoch sample_epoch, written to samples[sample_epoch & 1] as pack
+// rows.  It depends on the graph and the epoch only, so it runs beside the
+// previous epoch's sweep.  A thread takes one vertex's group of (up to) four
+// consecutive slots, whose first attempts come from one Philox call; a
+// rejected slot draws its further attempts alone.  Blocks take pieces of
+// sampler_piece(k) vertices of the vertex chunks (one graph each).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
+__host__ __device__ inline int sampler_groups(int k) { return (k + 3) / 4; }
+__host__ __device__ inline int sampler_piece(int k) {
+    const int g = sampler_groups(k);
+    return g > 0 ? 256 / g : 256;
+}
+
+template <bool kMap>
+__global__ void __launch_bounds__(256, kMap ? 3 : 5) k_sampler(const EpochArgs a) {
     __shared__ unsigned s_cnt[4];
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
-    constexpr int kSubs = kVChunk / kSamplerSub;
-    const int n_sub = a.n_vchunks * kSubs;
     const int k = a.k;
+    const int groups = sampler_groups(k), piece = sampler_piece(k);
+    const int per_chunk = (kVChunk + piece - 1) / piece;
+    const int n_sub = a.n_vchunks * per_chunk;
+    const EdgeSets es = edge_sets(a);
     unsigned c[4] = {0u, 0u, 0u, 0u};   // accepted, rejected, exhausted, false positives of graph cur
     int cur = -1;                       // block-uniform
     Membership m{nullptr, 0u, 0u, 1u, 0u};
     for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
-        const int4 ch = __ldg(a.vchunks + s / kSubs);
-        const int sub = s % kSubs;
-        const int cnt = min(kSamplerSub, ch.y - sub * kSamplerSub);
+        const int4 ch = __ldg(a.vchunks + s / per_chunk);
+        const int sub = s % per_chunk;
+        const int cnt = min(piece, ch.y - sub * piece);
         if (cnt <= 0) continue;   // uniform over the block
         const int graph = ch.z;
         const GraphInfo gi = load_graph(a, graph);
@@ -439,47 +399,28 @@ __global__ void __launch_bounds__(256) k_sampler(const EpochArgs a) {
             // the counts go to the graph's statistics once per run of pieces of one graph
             if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
             cur = graph;
-            m = membership_of(a, gi, se);
+            if (kMap) m = membership_of(a, gi, se);
             // the map holds this period now (the map builders, which read it, ran before)
-            if (a.membership && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
+            if (kMap && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
         }
-        const int row0 = ch.x + sub * kSamplerSub;
-        const int local0 = row0 - gi.v0;
-        int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0) * k;
-        const int total = cnt * k;
-        const EdgeSets es = edge_sets(a);
-        // kSamplerBatch draws per thread at a time: their first attempts and
-        // first-bucket probes are all issued before any is resolved
-        for (int base = 0; base < total; base += kSamplerBatch * blockDim.x) {
-            int g0[kSamplerBatch];
-            FirstProbe pr[kSamplerBatch];
+        const int row0 = ch.x + sub * piece;
+        const int vi = threadIdx.x / groups, q = threadIdx.x - vi * groups;
+        if (vi < cnt) {
+            const int i = row0 - gi.v0 + vi;
+            const uint32_t name_i = kMap ? renamed(m, (uint32_t)i) : 0u;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)q, kTagEpoch),
+                                          gi.key_lo, gi.key_hi);
+            int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0 + vi) * k;
 #pragma unroll
-            for (int q = 0; q < kSamplerBatch; ++q) {
-                const int idx = base + q * blockDim.x + threadIdx.x;
-                g0[q] = -1;
-                if (idx < total) {
-                    const int i = local0 + idx / k, t = idx % k;
-                    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)t, kTagEpoch),
-                                                  gi.key_lo, gi.key_hi);
-                    g0[q] = draw_vertex(r.x, (uint32_t)gi.n);
-                    if (!m.map && g0[q] != i) pr[q] = probe_issue(es, gi, i, g0[q]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kSamplerBatch; ++q) {
-                const int idx = base + q * blockDim.x + threadIdx.x;
-                if (idx >= total) continue;
-                const int i = local0 + idx / k, t = idx % k;
-                int g = g0[q];
-                bool taken;
-                if (g == i) taken = true;
-                else if (m.map) taken = taken_for_edge(gi, es, m, renamed(m, (uint32_t)i), i, g, c[3]);
-                else taken = probe_resolve(es, gi, i, g, pr[q]);
-                if (taken) {
+            for (int w = 0; w < 4; ++w) {
+                const int t = 4 * q + w;
+                if (t >= k) break;
+                int g = draw_vertex(word_of(r, w), (uint32_t)gi.n);
+                if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
                     ++c[1];
                     g = sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
                 }
-                out[idx] = g >= 0 ? gi.v0 + g : -1;
+                out[t] = g >= 0 ? gi.v0 + g : -1;
                 if (g >= 0) ++c[0]; else ++c[2];
             }
         }
@@ -536,11 +477,14 @@ __global__ void __launch_bounds__(256) k_bytemap_mark(const EpochArgs a, int for
 }
 
 // ---------------------------------------------------------------------------
-// The per-slot sampler (Sec. III.C's policy): one thread per CSR slot of the
-// 64-vertex pieces, the slot's row found by a binary search in the piece's
-// row offsets (shared memory); the accepted count of every vertex of the
-// piece goes to vacc for the sweep's histogram weights.
+// The per-slot sampler (Sec. III.C's policy) over 64-vertex pieces: a thread
+// takes a group of four consecutive CSR slots (graph-local slot numbers 4g ..
+// 4g + 3, cut to the piece), whose first attempts come from one Philox call;
+// each slot's row is found by a binary search in the piece's row offsets
+// (shared memory) and advanced from slot to slot.  The accepted count of
+// every vertex of the piece goes to vacc for the sweep's histogram weights.
 // ---------------------------------------------------------------------------
+template <bool kMap>
 __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
     __shared__ unsigned s_cnt[4];
     __shared__ int s_rp[kSamplerSub + 1];
@@ -548,6 +492,7 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     constexpr int kSubs = kVChunk / kSamplerSub;
     const int n_sub = a.n_vchunks * kSubs;
+    const EdgeSets es = edge_sets(a);
     unsigned c[4] = {0u, 0u, 0u, 0u};   // accepted, rejected, exhausted, false positives of graph cur
     int cur = -1;                       // block-uniform
     Membership m{nullptr, 0u, 0u, 1u, 0u};
@@ -562,8 +507,8 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
         if (graph != cur) {
             if (cur >= 0) block_count4(c, s_cnt, a.gst + cur);
             cur = graph;
-            m = membership_of(a, gi, se);
-            if (a.membership && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
+            if (kMap) m = membership_of(a, gi, se);
+            if (kMap && threadIdx.x == 0) a.gst[graph].map_period = map_period_of(a, se);
         }
         const int row0 = ch.x + sub * kSamplerSub;
         __syncthreads();   // the previous piece's shared data is no longer read
@@ -573,19 +518,31 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
         const int s0 = __ldg(a.row_ptr + gi.v0);   // the graph's first CSR slot
         int32_t* out = a.samples + (size_t)(se & 1) * (size_t)a.n_slots;
         const int e0 = s_rp[0], e1 = s_rp[cnt];
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            int lo = 0, hi = cnt - 1;   // row of slot e: the last r with s_rp[r] <= e
+        const int g_first = (e0 - s0) >> 2, g_last = e1 > e0 ? (e1 - 1 - s0) >> 2 : g_first - 1;
+        for (int grp = g_first + (int)threadIdx.x; grp <= g_last; grp += blockDim.x) {
+            const int ea = max(e0, s0 + 4 * grp), eb = min(e1, s0 + 4 * grp + 4);
+            int lo = 0, hi = cnt - 1;   // row of slot ea: the last r with s_rp[r] <= ea
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
+                if (s_rp[mid] <= ea) lo = mid; else hi = mid - 1;
             }
-            const int g = slot_partner(gi, edge_sets(a), a.max_retries, row0 + lo - gi.v0, e - s0, se, c[1], m, c[3]);
-            out[e] = g >= 0 ? gi.v0 + g : -1;
-            if (g >= 0) {
-                ++c[0];
-                atomicAdd(&s_acc[lo], 1);
-            } else {
-                ++c[2];
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)se, 0u, kTagSlot), gi.key_lo, gi.key_hi);
+            for (int e = ea; e < eb; ++e) {
+                while (s_rp[lo + 1] <= e) ++lo;   // rows may be empty
+                const int i = row0 + lo - gi.v0, el = e - s0;
+                const uint32_t name_i = kMap ? renamed(m, (uint32_t)i) : 0u;
+                int g = draw_vertex(word_of(r, el & 3), (uint32_t)gi.n);
+                if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
+                    ++c[1];
+                    g = slot_partner_from(gi, es, a.max_retries, i, el, se, 1, c[1], m, c[3]);
+                }
+                out[e] = g >= 0 ? gi.v0 + g : -1;
+                if (g >= 0) {
+                    ++c[0];
+                    atomicAdd(&s_acc[lo], 1);
+                } else {
+                    ++c[2];
+                }
             }
         }
         __syncthreads();
@@ -1816,17 +1773,21 @@ cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {
 }
 
 int sampler_grid(int rows, int k, int sm_count) {
-    const long long subs = ((long long)rows + kSamplerSub - 1) / kSamplerSub + 1;
+    const long long subs = ((long long)rows + sampler_piece(k) - 1) / sampler_piece(k) + 1;
     long long grid = subs;
     const long long cap = (long long)sm_count * 8;
     if (grid > cap) grid = cap;
-    (void)k;
     return grid < 1 ? 1 : (int)grid;
 }
 
 cudaError_t launch_sampler(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.per_slot) k_sampler_slots<<<grid, 256, 0, s>>>(a);
-    else k_sampler<<<grid, 256, 0, s>>>(a);
+    if (a.per_slot) {
+        if (a.membership) k_sampler_slots<true><<<grid, 256, 0, s>>>(a);
+        else k_sampler_slots<false><<<grid, 256, 0, s>>>(a);
+    } else {
+        if (a.membership) k_sampler<true><<<grid, 256, 0, s>>>(a);
+        else k_sampler<false><<<grid, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
