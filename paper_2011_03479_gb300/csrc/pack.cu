@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -68,27 +69,93 @@ gempe_status check_params(const gempe_params* p, int32_t d) {
     return GEMPE_OK;
 }
 
-// Symmetric, sorted, loop-free, duplicate-free, in-range CSR.
-gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n) {
+int host_threads(int64_t work) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t by_work = work / (1 << 16) + 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 32, by_work}));
+}
+
+namespace {
+
+// Runs fn(begin, end) over [0, count) cut into `parts` consecutive ranges of
+// (roughly) equal weight, one thread per range (the caller runs the first).
+// cum(i): the weight of [0, i), non-decreasing.
+template <typename Cum, typename F>
+void parallel_ranges(int64_t count, int parts, Cum cum, F fn) {
+    if (parts <= 1 || count < 2) {
+        fn((int64_t)0, count);
+        return;
+    }
+    std::vector<int64_t> cut(parts + 1, 0);
+    const int64_t total = cum(count);
+    for (int t = 1; t < parts; ++t) {
+        const int64_t target = total * t / parts;
+        int64_t lo = cut[t - 1], hi = count;   // first i with cum(i) >= target
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (cum(mid) < target) lo = mid + 1; else hi = mid;
+        }
+        cut[t] = lo;
+    }
+    cut[parts] = count;
+    std::vector<std::thread> th;
+    th.reserve(parts - 1);
+    for (int t = 1; t < parts; ++t) th.emplace_back(fn, cut[t], cut[t + 1]);
+    fn(cut[0], cut[1]);
+    for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+// Symmetric, sorted, loop-free, duplicate-free, in-range CSR.  The rows are
+// checked in parallel (ranges of equal CSR slots); the error reported is the
+// one of the lowest row, as a row-by-row check would find it: first the
+// per-row checks of every row, then the symmetry (binary search of (j, i) in
+// row j for every slot (i, j)).
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads) {
     if (rp[0] != 0) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr[0] must be 0");
     for (int32_t i = 0; i < n; ++i)
         if (rp[i + 1] < rp[i]) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr must be non-decreasing");
-    for (int32_t i = 0; i < n; ++i) {
-        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
-            const int32_t j = ci[e];
-            if (j < 0 || j >= n) return pack_fail(GEMPE_E_INVALID_GRAPH, "column index out of range");
-            if (j == i) return pack_fail(GEMPE_E_INVALID_GRAPH, "self loop at vertex " + std::to_string(i));
-            if (e > rp[i] && ci[e - 1] >= j)
-                return pack_fail(GEMPE_E_INVALID_GRAPH, "row " + std::to_string(i) + " not strictly increasing");
+    const int parts = threads > 0 ? threads : host_threads(rp[n]);
+    auto cum = [&](int64_t i) { return (int64_t)rp[i] + i; };
+    std::mutex mu;
+    int32_t bad_row = n, bad_kind = 0, bad_j = 0;
+    auto report = [&](int32_t i, int kind, int32_t j) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (i < bad_row) {
+            bad_row = i;
+            bad_kind = kind;
+            bad_j = j;
         }
-    }
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
-            const int32_t j = ci[e];
-            if (!std::binary_search(ci + rp[j], ci + rp[j + 1], i))
-                return pack_fail(GEMPE_E_INVALID_GRAPH, "graph not symmetric: (" + std::to_string(i) + "," +
-                                                            std::to_string(j) + ") without its reverse");
-        }
+    };
+    parallel_ranges(n, parts, cum, [&](int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; ++i)
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t j = ci[e];
+                const int kind = (j < 0 || j >= n) ? 1 : (j == i) ? 2 : (e > rp[i] && ci[e - 1] >= j) ? 3 : 0;
+                if (kind) {
+                    report((int32_t)i, kind, j);
+                    return;
+                }
+            }
+    });
+    if (bad_kind == 1) return pack_fail(GEMPE_E_INVALID_GRAPH, "column index out of range");
+    if (bad_kind == 2) return pack_fail(GEMPE_E_INVALID_GRAPH, "self loop at vertex " + std::to_string(bad_row));
+    if (bad_kind == 3)
+        return pack_fail(GEMPE_E_INVALID_GRAPH, "row " + std::to_string(bad_row) + " not strictly increasing");
+    parallel_ranges(n, parts, cum, [&](int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; ++i)
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t j = ci[e];
+                if (!std::binary_search(ci + rp[j], ci + rp[j + 1], (int32_t)i)) {
+                    report((int32_t)i, 4, j);
+                    return;
+                }
+            }
+    });
+    if (bad_kind == 4)
+        return pack_fail(GEMPE_E_INVALID_GRAPH, "graph not symmetric: (" + std::to_string(bad_row) + "," +
+                                                    std::to_string(bad_j) + ") without its reverse");
     return GEMPE_OK;
 }
 
@@ -189,17 +256,47 @@ Pack::~Pack() {
     if (side) cudaStreamDestroy(side);
 }
 
+namespace {
+// The default allocation path is stream-ordered (the device's default memory
+// pool, cudaMallocAsync on the pack's stream): a context that is created
+// and destroyed per job reuses the pool's memory instead of mapping and
+// unmapping it (and synchronising the device) every time.  The pool keeps
+// what it holds between jobs (release threshold: unlimited) for the life of
+// the process.
+void keep_pool_memory(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return;
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(device);
+}
+}  // namespace
+
 void* Pack::alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* ptr = nullptr;
     if (p.dev_alloc) {
         ptr = p.dev_alloc(bytes, p.alloc_user);
-    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        ptr = nullptr;
+    } else {
+        keep_pool_memory(device);
+        if (cudaMallocAsync(&ptr, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            ptr = nullptr;
+        }
     }
     if (ptr) allocations.push_back(ptr);
     return ptr;
+}
+
+void Pack::free_one(void* ptr) {
+    if (p.dev_free) p.dev_free(ptr, p.alloc_user);
+    else cudaFreeAsync(ptr, stream);
 }
 
 void Pack::release(void* ptr) {
@@ -207,16 +304,13 @@ void Pack::release(void* ptr) {
     auto it = std::find(allocations.begin(), allocations.end(), ptr);
     if (it == allocations.end()) return;
     allocations.erase(it);
-    if (p.dev_free) p.dev_free(ptr, p.alloc_user);
-    else cudaFree(ptr);
+    free_one(ptr);
 }
 
 void Pack::release_all() {
-    for (void* ptr : allocations) {
-        if (p.dev_free) p.dev_free(ptr, p.alloc_user);
-        else cudaFree(ptr);
-    }
+    for (void* ptr : allocations) free_one(ptr);
     allocations.clear();
+    if (!p.dev_free && stream) cudaStreamSynchronize(stream);
 }
 
 gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const gempe_params& params,
@@ -312,23 +406,35 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     }
     row_ptr_h[(size_t)rows] = (int32_t)slots;
     // the degree-oriented CSR of the packed sweep: edge (i, j) in row i when
-    // (deg j, j) < (deg i, i), so every undirected edge once
+    // (deg j, j) < (deg i, i), so every undirected edge once (rows counted,
+    // then filled, in parallel)
     std::vector<int32_t> ocol_h;
     orow_ptr_h.clear();
     if (d <= kPackedMaxDim && !per_slot && !block) {
         orow_ptr_h.assign((size_t)rows + 1, 0);
-        ocol_h.reserve((size_t)slots / 2 + 1);
-        for (int32_t r = 0; r < rows; ++r) {
-            orow_ptr_h[r] = (int32_t)ocol_h.size();
+        auto keep = [&](int32_t r, int32_t j) {
             const int32_t dr = row_ptr_h[(size_t)r + 1] - row_ptr_h[r];
-            for (int32_t e = row_ptr_h[r]; e < row_ptr_h[(size_t)r + 1]; ++e) {
-                const int32_t j = col_h[e];
-                const int32_t dj = row_ptr_h[(size_t)j + 1] - row_ptr_h[j];
-                if (dj < dr || (dj == dr && j < r)) ocol_h.push_back(j);
+            const int32_t dj = row_ptr_h[(size_t)j + 1] - row_ptr_h[j];
+            return dj < dr || (dj == dr && j < r);
+        };
+        const int parts = host_threads(slots);
+        auto cum = [&](int64_t r) { return (int64_t)row_ptr_h[r] + r; };
+        parallel_ranges(rows, parts, cum, [&](int64_t r0, int64_t r1) {
+            for (int64_t r = r0; r < r1; ++r) {
+                int32_t c = 0;
+                for (int32_t e = row_ptr_h[r]; e < row_ptr_h[r + 1]; ++e) c += keep((int32_t)r, col_h[e]) ? 1 : 0;
+                orow_ptr_h[r + 1] = c;
             }
-        }
-        orow_ptr_h[rows] = (int32_t)ocol_h.size();
-        if (ocol_h.empty()) ocol_h.push_back(0);
+        });
+        for (int32_t r = 0; r < rows; ++r) orow_ptr_h[(size_t)r + 1] += orow_ptr_h[r];
+        ocol_h.resize(std::max<size_t>((size_t)orow_ptr_h[rows], 1));
+        parallel_ranges(rows, parts, cum, [&](int64_t r0, int64_t r1) {
+            for (int64_t r = r0; r < r1; ++r) {
+                int32_t o = orow_ptr_h[r];
+                for (int32_t e = row_ptr_h[r]; e < row_ptr_h[r + 1]; ++e)
+                    if (keep((int32_t)r, col_h[e])) ocol_h[o++] = col_h[e];
+            }
+        });
     }
     // vertex chunks and tile lists
     std::vector<int4> vch;

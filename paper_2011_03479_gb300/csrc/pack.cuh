@@ -34,7 +34,10 @@ struct PackShape {
 gempe_status pack_fail(gempe_status st, const std::string& msg);
 gempe_status pack_cuda_fail(cudaError_t e, const char* what);
 gempe_status check_params(const gempe_params* p, int32_t d);
-gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n);
+// threads: host threads for the check (0: by the size of the graph)
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads = 0);
+// Host threads for O(work) set-up loops: one per 65,536 items, at most 32.
+int host_threads(int64_t work);
 
 struct Pack {
     gempe_params p{};
@@ -102,8 +105,9 @@ struct Pack {
     Pack& operator=(const Pack&) = delete;
     ~Pack();
 
-    void* alloc(size_t bytes);
+    void* alloc(size_t bytes);       // on `stream` (set before the first call)
     void release(void* ptr);
+    void free_one(void* ptr);
     void release_all();
 
     // Lays the graphs out, copies them and builds their edge sets and initial

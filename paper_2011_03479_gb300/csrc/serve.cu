@@ -272,7 +272,7 @@ void gempe_server::admit_loop() {
             ++waiting;
         }
         // host validation, in parallel with other workers
-        const gempe_status vrc = validate_csr(j->rp.data(), j->ci.data(), j->n);
+        const gempe_status vrc = validate_csr(j->rp.data(), j->ci.data(), j->n, 1);   // the workers run in parallel
         const std::string verr = vrc != GEMPE_OK ? std::string(gempe_last_error()) : std::string();
         int slot = -1;
         {
