@@ -127,13 +127,22 @@ typedef struct gempe_ctx gempe_ctx;
  * custom allocator. */
 void gempe_default_params(gempe_params* p);
 
+/* Check a host CSR graph on the host alone: row_ptr[0] = 0 and
+ * non-decreasing, column indices in range, no self loops, rows strictly
+ * increasing (no duplicates), and symmetric (every (i, j) has its (j, i)).
+ * GEMPE_OK or GEMPE_E_INVALID_GRAPH with the lowest offending row in
+ * gempe_last_error().  Needs no GPU. */
+gempe_status gempe_validate_csr(const int32_t* row_ptr, const int32_t* col_idx, int32_t n);
+
 /* Create an embedding context from a host CSR graph (Sec. II.A: G, n, d).
  * row_ptr: host int32[n+1]; col_idx: host int32[row_ptr[n]].  d must be one
  * of 1,2,3,4,8,16,32,64,128,256.  cuda_stream: a cudaStream_t for all work of
  * the context, or NULL for a stream the context creates.  Validates the
- * graph (GEMPE_E_INVALID_GRAPH), uploads it, builds the exact edge hash set,
- * draws the initial positions (Fig. 4: uniform random) and sets sigma = sigma0,
- * epoch = 0.  On success *out owns the context; on failure *out is NULL. */
+ * graph (GEMPE_E_INVALID_GRAPH: the row checks of gempe_validate_csr on the
+ * host before any device work, the symmetry on the device against the edge
+ * set), uploads it, builds the exact edge hash set, draws the initial
+ * positions (Fig. 4: uniform random) and sets sigma = sigma0, epoch = 0.  On
+ * success *out owns the context; on failure *out is NULL. */
 gempe_status gempe_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
                           const gempe_params* p, void* cuda_stream, gempe_ctx** out);
 

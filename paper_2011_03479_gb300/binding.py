@@ -136,6 +136,7 @@ def load(build: bool = True):
     st = ctypes.c_int
     sig = {
         "gempe_default_params": (None, [P(gempe_params)]),
+        "gempe_validate_csr": (st, [vp, vp, i32]),
         "gempe_create": (st, [vp, vp, i32, i32, P(gempe_params), vp, P(vp)]),
         "gempe_create_device": (st, [vp, vp, i32, i64, i32, P(gempe_params), vp, P(vp)]),
         "gempe_destroy": (None, [vp]),
@@ -267,6 +268,13 @@ def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | Non
 
 def gempe_destroy(ctx: _Ctx) -> None:
     ctx.close()
+
+
+def gempe_validate_csr(row_ptr, col_idx) -> None:
+    """Host-only check of a CSR graph (raises GempeError when it is invalid)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    _check(load().gempe_validate_csr(_ptr(rp), _ptr(ci) if ci.size else None, len(rp) - 1))
 
 
 def gempe_step(ctx: _Ctx, iters: int = 1) -> None:

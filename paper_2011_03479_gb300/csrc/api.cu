@@ -65,7 +65,9 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
     if (s != GEMPE_OK) return s;
     if (n < 2) return fail(GEMPE_E_INVALID_ARG, "n must be at least 2");
     if (rp_host[n] < 0) return fail(GEMPE_E_INVALID_GRAPH, "row_ptr[n] negative");
-    s = validate_csr(rp_host, ci_host, n);   // on the host, before any device work
+    // rows sorted, in range and loop-free on the host, before any device
+    // work; the symmetry is checked on the device against the edge set
+    s = validate_csr(rp_host, ci_host, n, 0, false);
     if (s != GEMPE_OK) return s;
     std::unique_ptr<gempe_ctx> c(new gempe_ctx());
     c->n = n;
@@ -100,6 +102,13 @@ GraphState read_graph_state(gempe_ctx* c, gempe_status* rc) {
 }
 
 }  // namespace
+
+GEMPE_API gempe_status gempe_validate_csr(const int32_t* row_ptr, const int32_t* col_idx, int32_t n) {
+    if (!row_ptr || n < 0) return fail(GEMPE_E_INVALID_ARG, "null row_ptr or negative n");
+    if (!col_idx && n > 0 && row_ptr[n] > 0) return fail(GEMPE_E_INVALID_ARG, "null col_idx");
+    static const int32_t empty = 0;
+    return validate_csr(row_ptr, col_idx ? col_idx : &empty, n);
+}
 
 GEMPE_API void gempe_default_params(gempe_params* p) {
     if (!p) return;

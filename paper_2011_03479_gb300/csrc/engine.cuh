@@ -159,6 +159,17 @@ bool supported_dim(int d);
 cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
                               void* keys, int narrow, unsigned long long bucket_mask,
                               int32_t* fail_flag, cudaStream_t s);
+// Symmetry check of one graph of the pack against its edge set (rows sorted
+// and in range): counts3 += {slots above the diagonal, below, below without
+// their reverse}; symmetric iff above == below and none missing.
+cudaError_t launch_check_symmetric(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
+                                   const void* keys, int narrow, unsigned long long key_off,
+                                   unsigned long long bucket_mask, unsigned long long* counts3, cudaStream_t s);
+// Degree-oriented CSR of the pack (rows + 1 offsets, kept slots in row
+// order); scratch: orient_scratch_ints(rows) ints.
+size_t orient_scratch_ints(int rows);
+cudaError_t launch_orient(const int32_t* row_ptr, const int32_t* col_idx, int rows, int32_t* orow_ptr,
+                          int32_t* ocol_idx, int32_t* scratch, int sm_count, cudaStream_t s);
 cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_t d, uint32_t key_lo,
                                   uint32_t key_hi, float range, cudaStream_t s);
 

@@ -110,9 +110,9 @@ void parallel_ranges(int64_t count, int parts, Cum cum, F fn) {
 // Symmetric, sorted, loop-free, duplicate-free, in-range CSR.  The rows are
 // checked in parallel (ranges of equal CSR slots); the error reported is the
 // one of the lowest row, as a row-by-row check would find it: first the
-// per-row checks of every row, then the symmetry (binary search of (j, i) in
-// row j for every slot (i, j)).
-gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads) {
+// per-row checks of every row, then (symmetry) the symmetry by a binary
+// search of (j, i) in row j for every slot (i, j).
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads, bool symmetry) {
     if (rp[0] != 0) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr[0] must be 0");
     for (int32_t i = 0; i < n; ++i)
         if (rp[i + 1] < rp[i]) return pack_fail(GEMPE_E_INVALID_GRAPH, "row_ptr must be non-decreasing");
@@ -143,6 +143,7 @@ gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int t
     if (bad_kind == 2) return pack_fail(GEMPE_E_INVALID_GRAPH, "self loop at vertex " + std::to_string(bad_row));
     if (bad_kind == 3)
         return pack_fail(GEMPE_E_INVALID_GRAPH, "row " + std::to_string(bad_row) + " not strictly increasing");
+    if (!symmetry) return GEMPE_OK;
     parallel_ranges(n, parts, cum, [&](int64_t r0, int64_t r1) {
         for (int64_t i = r0; i < r1; ++i)
             for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
@@ -405,37 +406,10 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         if (g + 1 < G) row_ptr_h[(size_t)gi.v0 + in.n + 1] = s0 + (int32_t)nnz[g];
     }
     row_ptr_h[(size_t)rows] = (int32_t)slots;
-    // the degree-oriented CSR of the packed sweep: edge (i, j) in row i when
-    // (deg j, j) < (deg i, i), so every undirected edge once (rows counted,
-    // then filled, in parallel)
-    std::vector<int32_t> ocol_h;
+    // the degree-oriented CSR of the packed sweep is built on the device
+    // (setup.cu); its row offsets come back to orow_ptr_h for the work units
+    const bool oriented_csr = d <= kPackedMaxDim && !per_slot && !block;
     orow_ptr_h.clear();
-    if (d <= kPackedMaxDim && !per_slot && !block) {
-        orow_ptr_h.assign((size_t)rows + 1, 0);
-        auto keep = [&](int32_t r, int32_t j) {
-            const int32_t dr = row_ptr_h[(size_t)r + 1] - row_ptr_h[r];
-            const int32_t dj = row_ptr_h[(size_t)j + 1] - row_ptr_h[j];
-            return dj < dr || (dj == dr && j < r);
-        };
-        const int parts = host_threads(slots);
-        auto cum = [&](int64_t r) { return (int64_t)row_ptr_h[r] + r; };
-        parallel_ranges(rows, parts, cum, [&](int64_t r0, int64_t r1) {
-            for (int64_t r = r0; r < r1; ++r) {
-                int32_t c = 0;
-                for (int32_t e = row_ptr_h[r]; e < row_ptr_h[r + 1]; ++e) c += keep((int32_t)r, col_h[e]) ? 1 : 0;
-                orow_ptr_h[r + 1] = c;
-            }
-        });
-        for (int32_t r = 0; r < rows; ++r) orow_ptr_h[(size_t)r + 1] += orow_ptr_h[r];
-        ocol_h.resize(std::max<size_t>((size_t)orow_ptr_h[rows], 1));
-        parallel_ranges(rows, parts, cum, [&](int64_t r0, int64_t r1) {
-            for (int64_t r = r0; r < r1; ++r) {
-                int32_t o = orow_ptr_h[r];
-                for (int32_t e = row_ptr_h[r]; e < row_ptr_h[r + 1]; ++e)
-                    if (keep((int32_t)r, col_h[e])) ocol_h[o++] = col_h[e];
-            }
-        });
-    }
     // vertex chunks and tile lists
     std::vector<int4> vch;
     std::vector<int2> titems;
@@ -464,10 +438,18 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     row_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
     col_idx = (int32_t*)alloc(sizeof(int32_t) * col_h.size());
     keys = alloc((narrow_keys ? 4 : 8) * key_slots);
-    if (!orow_ptr_h.empty()) {
+    // set-up scratch: per graph {slots above, below, below without reverse}
+    // of the symmetry check, then the oriented rows' counts and scan sums
+    unsigned long long* sym = (unsigned long long*)alloc(sizeof(unsigned long long) * 3 * (size_t)G);
+    int32_t* oscratch = nullptr;
+    if (!sym) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+    if (oriented_csr) {
+        // ocol_idx holds every slot at most (exactly half of them for a
+        // symmetric graph, which is checked only after the build)
         orow_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
-        ocol_idx = (int32_t*)alloc(sizeof(int32_t) * ocol_h.size());
-        if (!orow_ptr || !ocol_idx) return pack_fail(GEMPE_E_OOM, "device allocation failed");
+        ocol_idx = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>((size_t)slots, 1));
+        oscratch = (int32_t*)alloc(sizeof(int32_t) * orient_scratch_ints(rows));
+        if (!orow_ptr || !ocol_idx || !oscratch) return pack_fail(GEMPE_E_OOM, "device allocation failed");
     }
     x = (float*)alloc(sizeof(float) * R * d);
     acc = (float*)alloc(sizeof(float) * R * acc_stride);
@@ -516,12 +498,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     }
     PK(cudaMemcpyAsync(row_ptr, row_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s), "copy row_ptr");
     PK(cudaMemcpyAsync(col_idx, col_h.data(), sizeof(int32_t) * col_h.size(), cudaMemcpyHostToDevice, s), "copy col_idx");
-    if (orow_ptr) {
-        PK(cudaMemcpyAsync(orow_ptr, orow_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s),
-           "copy oriented row_ptr");
-        PK(cudaMemcpyAsync(ocol_idx, ocol_h.data(), sizeof(int32_t) * ocol_h.size(), cudaMemcpyHostToDevice, s),
-           "copy oriented col_idx");
-    }
+    PK(cudaMemsetAsync(sym, 0, sizeof(unsigned long long) * 3 * (size_t)G, s), "clear counts");
     PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
     PK(cudaMemcpyAsync(gst, st0.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, s), "init graph state");
     PK(cudaMemsetAsync(ps, 0, sizeof(PackState), s), "init pack state");
@@ -549,11 +526,34 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
                                  gi.key_hi, p.init_range, s),
            "init positions");
     }
+    for (int32_t g = 0; g < G; ++g) {
+        const GraphInfo& gi = info[g];
+        PK(launch_check_symmetric(row_ptr, col_idx, gi.v0, gi.n, nnz[g], keys, narrow_keys ? 1 : 0, gi.key_off,
+                                  gi.bucket_mask, sym + 3 * (size_t)g, s),
+           "symmetry check");
+    }
+    if (oriented_csr) {
+        PK(launch_orient(row_ptr, col_idx, rows, orow_ptr, ocol_idx, oscratch, sm_count, s), "oriented CSR");
+        orow_ptr_h.assign((size_t)rows + 1, 0);
+        PK(cudaMemcpyAsync(orow_ptr_h.data(), orow_ptr, sizeof(int32_t) * (R + 1), cudaMemcpyDeviceToHost, s),
+           "read oriented row_ptr");
+    }
     if (bytemap) PK(launch_bytemap_build(args(), 1, sm_count, s), "byte-map build");
     int32_t hash_fail = 0;
+    std::vector<unsigned long long> sym_h(3 * (size_t)G);
     PK(cudaMemcpyAsync(&hash_fail, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read flag");
+    PK(cudaMemcpyAsync(sym_h.data(), sym, sizeof(unsigned long long) * sym_h.size(), cudaMemcpyDeviceToHost, s),
+       "read counts");
     PK(cudaStreamSynchronize(s), "create");
+    release(sym);
+    if (oscratch) release(oscratch);
     if (hash_fail) return pack_fail(GEMPE_E_INVALID_GRAPH, "edge hash set build failed");
+    for (int32_t g = 0; g < G; ++g) {
+        if (sym_h[3 * g] == sym_h[3 * g + 1] && sym_h[3 * g + 2] == 0) continue;
+        // not symmetric: the host check names the lowest row with a slot whose reverse is missing
+        const gempe_status vs = validate_csr(gs[g].row_ptr, gs[g].col_idx, gs[g].n);
+        return vs != GEMPE_OK ? vs : pack_fail(GEMPE_E_INVALID_GRAPH, "graph not symmetric");
+    }
 
     sampler_grid = gempe::sampler_grid(rows, k, sm_count);
     update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
@@ -583,7 +583,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     const bool ps = p.sampling == 1;
     b += al(4 * std::max<size_t>(blk ? 1 : (ps ? 2 * (size_t)nnz : 2 * R * k), 1)) + al(16 * units_max) + al(4 * 4097);
     if (ps) b += al(8 * R);
-    if (d <= kPackedMaxDim && !ps && !blk) b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz / 2, 1));
+    if (d <= kPackedMaxDim && !ps && !blk) b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1));
     if (p.membership == 1 && !blk) b += al((size_t)1 << bytemap_log2_for(nnz, p));
     if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
     return b;

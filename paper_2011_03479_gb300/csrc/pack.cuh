@@ -34,8 +34,9 @@ struct PackShape {
 gempe_status pack_fail(gempe_status st, const std::string& msg);
 gempe_status pack_cuda_fail(cudaError_t e, const char* what);
 gempe_status check_params(const gempe_params* p, int32_t d);
-// threads: host threads for the check (0: by the size of the graph)
-gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads = 0);
+// threads: host threads for the check (0: by the size of the graph);
+// symmetry = false leaves the symmetry to the device check of Pack::build.
+gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads = 0, bool symmetry = true);
 // Host threads for O(work) set-up loops: one per 65,536 items, at most 32.
 int host_threads(int64_t work);
 

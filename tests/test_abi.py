@@ -47,19 +47,57 @@ def _status(fn, *args):
     return fn(*args, ctypes.byref(h)), h
 
 
-@pytest.mark.parametrize("case", ["asym", "loop", "dup", "range", "unsorted"])
-def test_invalid_graphs_rejected_on_host(case):
-    from paper_2011_03479_gb300 import binding
-    lib = binding.load()
-    rows = {"asym": [[1], [], []], "loop": [[0, 1], [0], []], "dup": [[1, 1], [0, 0], []],
-            "range": [[5], [0], []], "unsorted": [[2, 1], [0], [0]]}[case]
+INVALID = {"asym": [[1], [], []], "loop": [[0, 1], [0], []], "dup": [[1, 1], [0, 0], []],
+           "range": [[5], [0], []], "unsorted": [[2, 1], [0], [0]]}
+
+
+def _csr(rows):
     rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
     ci = np.array(sum(rows, []), dtype=np.int32)
+    return rp, ci
+
+
+@pytest.mark.parametrize("case", ["loop", "dup", "range", "unsorted"])
+def test_invalid_graphs_rejected_on_host(case):
+    """The row checks run on the host before any device work (no GPU here)."""
+    from paper_2011_03479_gb300 import binding
+    lib = binding.load()
+    rp, ci = _csr(INVALID[case])
     p = binding.gempe_default_params()
-    st, h = _status(lib.gempe_create, ci.ctypes.data and ctypes.c_void_p(rp.ctypes.data),
-                    ctypes.c_void_p(ci.ctypes.data), len(rows), 2, ctypes.byref(p), None)
+    st, h = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data),
+                    ctypes.c_void_p(ci.ctypes.data), len(rp) - 1, 2, ctypes.byref(p), None)
     assert st == -2, binding.gempe_last_error()
     assert not h.value
+
+
+@pytest.mark.parametrize("case", sorted(INVALID))
+def test_validate_csr_host(case):
+    """gempe_validate_csr: every check, symmetry included, on the host."""
+    from paper_2011_03479_gb300 import binding
+    rp, ci = _csr(INVALID[case])
+    with pytest.raises(binding.GempeError) as ei:
+        binding.gempe_validate_csr(rp, ci)
+    assert ei.value.status == -2
+    msg = str(ei.value)
+    if case == "asym":
+        assert "(0,1) without its reverse" in msg
+
+
+def test_validate_csr_reports_lowest_row():
+    """Errors in several rows: the lowest row is named, whichever thread finds it."""
+    from paper_2011_03479_gb300 import binding, inputs
+    rp, ci = inputs.rmat(12, 8, seed=99)
+    binding.gempe_validate_csr(rp, ci)            # a valid graph passes
+    ci2 = ci.copy()
+    rows = [int(np.searchsorted(rp, len(ci) * f, side="right") - 1) for f in (0.3, 0.7)]
+    for r in rows:                                 # make two rows' first entries self loops
+        if rp[r + 1] > rp[r]:
+            ci2[rp[r]] = r
+    with pytest.raises(binding.GempeError) as ei:
+        binding.gempe_validate_csr(rp, ci2)
+    first = min(r for r in rows if rp[r + 1] > rp[r])
+    msg = str(ei.value)
+    assert f"self loop at vertex {first}" in msg or f"row {first} not strictly increasing" in msg, msg
 
 
 def test_invalid_args_rejected_on_host():
