@@ -279,8 +279,11 @@ typedef struct gempe_graph_desc {
 typedef struct gempe_batch gempe_batch;
 
 /* Validate, upload and initialise n_graphs graphs (copied; the caller keeps
- * ownership of the arrays).  cuda_stream as in gempe_create.  With
- * p->autotune each pack's sweep shape is tuned before the first epoch. */
+ * ownership of the arrays).  As in gempe_create, the rows are checked on
+ * the host before any device work and the symmetry on the device; an error
+ * names the graph by its index ("graph g: ...").  cuda_stream as in
+ * gempe_create.  With p->autotune each pack's sweep shape is tuned before
+ * the first epoch. */
 gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_desc* graphs, const gempe_params* p,
                                 void* cuda_stream, gempe_batch** out);
 void gempe_batch_destroy(gempe_batch* b);
@@ -343,7 +346,9 @@ gempe_status gempe_server_create(size_t hbm_budget_bytes, int32_t max_jobs, cons
 /* Stops the threads; running jobs finish their enqueued work and are dropped. */
 void gempe_server_destroy(gempe_server* s);
 /* Queue a job (copies the CSR).  GEMPE_E_BUDGET if the job alone exceeds the
- * budget; invalid graphs are reported by poll / wait / result. */
+ * budget; invalid graphs are reported by poll / wait / result (rows checked
+ * on the host before admission, the symmetry on the device when the job
+ * starts). */
 gempe_status gempe_server_submit(gempe_server* s, const gempe_job_desc* job, uint64_t* job_id);
 gempe_status gempe_server_poll(gempe_server* s, uint64_t job_id, gempe_job_info* info);
 /* Block until the job is done or failed, at most timeout_ms (GEMPE_E_TIMEOUT). */

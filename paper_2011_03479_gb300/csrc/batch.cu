@@ -72,7 +72,8 @@ GEMPE_API gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_de
             return pack_fail(GEMPE_E_INVALID_ARG, "graph " + std::to_string(g) + ": null CSR or n < 2");
         gempe_status rc = check_params(p, graphs[g].d >= 8 ? graphs[g].d : 8);
         if (rc != GEMPE_OK) return rc;
-        rc = validate_csr(graphs[g].row_ptr, graphs[g].col_idx, graphs[g].n);   // host, before device work
+        // the rows on the host, before device work; the symmetry on the device (Pack::build)
+        rc = validate_csr(graphs[g].row_ptr, graphs[g].col_idx, graphs[g].n, 0, false);
         if (rc != GEMPE_OK)
             return pack_fail(rc, "graph " + std::to_string(g) + ": " + std::string(gempe_last_error()));
         by_dim[graphs[g].d].push_back(g);
@@ -102,6 +103,7 @@ GEMPE_API gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_de
             gi.col_idx = graphs[g].col_idx;
             gi.n = graphs[g].n;
             gi.key = p->seed ^ (uint64_t)g;
+            gi.label = g;
             in.push_back(gi);
             b->pack_of[g] = (int)b->packs.size();
             b->index_in_pack[g] = (int)q;

@@ -552,7 +552,9 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         if (sym_h[3 * g] == sym_h[3 * g + 1] && sym_h[3 * g + 2] == 0) continue;
         // not symmetric: the host check names the lowest row with a slot whose reverse is missing
         const gempe_status vs = validate_csr(gs[g].row_ptr, gs[g].col_idx, gs[g].n);
-        return vs != GEMPE_OK ? vs : pack_fail(GEMPE_E_INVALID_GRAPH, "graph not symmetric");
+        std::string msg = vs != GEMPE_OK ? std::string(gempe_last_error()) : std::string("graph not symmetric");
+        if (gs[g].label >= 0) msg = "graph " + std::to_string(gs[g].label) + ": " + msg;
+        return pack_fail(GEMPE_E_INVALID_GRAPH, msg);
     }
 
     sampler_grid = gempe::sampler_grid(rows, k, sm_count);

@@ -18,6 +18,7 @@ struct GraphInput {
     const int32_t* col_idx;   // host, row_ptr[n]
     int32_t n;
     uint64_t key;             // Philox key of the graph
+    int32_t label = -1;       // index of the graph in the caller's list (error messages), -1: none
 };
 
 // Launch shape of the sweep (the autotuner's search space).

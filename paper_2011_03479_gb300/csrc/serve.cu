@@ -271,8 +271,9 @@ void gempe_server::admit_loop() {
             pending.pop_front();
             ++waiting;
         }
-        // host validation, in parallel with other workers
-        const gempe_status vrc = validate_csr(j->rp.data(), j->ci.data(), j->n, 1);   // the workers run in parallel
+        // the rows checked on the host, in parallel with other workers (one
+        // thread each); the symmetry on the device when the job starts
+        const gempe_status vrc = validate_csr(j->rp.data(), j->ci.data(), j->n, 1, false);
         const std::string verr = vrc != GEMPE_OK ? std::string(gempe_last_error()) : std::string();
         int slot = -1;
         {

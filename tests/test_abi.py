@@ -142,13 +142,14 @@ def test_generated_graphs_are_valid_csr(sbm_1000):
 
 
 def test_batch_rejects_invalid_graphs_on_host():
-    """gempe_batch_create validates every graph on the host before any device
-    work: an asymmetric graph or an unsupported dimension fails cleanly."""
+    """gempe_batch_create checks every graph's rows on the host before any
+    device work (the symmetry follows on the device): a self loop or an
+    unsupported dimension fails cleanly."""
     from paper_2011_03479_gb300 import binding
     good = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), 2)
-    asym = (np.array([0, 1, 1], np.int32), np.array([1], np.int32), 2)
+    loop = (np.array([0, 2, 3], np.int32), np.array([0, 1, 0], np.int32), 2)
     with pytest.raises(binding.GempeError) as ei:
-        binding.gempe_batch_create([good, asym])
+        binding.gempe_batch_create([good, loop])
     assert ei.value.status == -2 and "graph 1" in str(ei.value)
     with pytest.raises(binding.GempeError) as ei:
         binding.gempe_batch_create([good, (good[0], good[1], 5)])

@@ -52,3 +52,12 @@ def test_tiny_asymmetric_graph(B):
     with pytest.raises(B.GempeError) as ei:
         B.gempe_create(rp, ci, 2)
     assert ei.value.status == -2 and "(0,1) without its reverse" in str(ei.value)
+
+
+def test_batch_asymmetric_graph_named(B):
+    """In a batch the device check names the graph by its index."""
+    good = (np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), 2)
+    asym = (np.array([0, 1, 1], np.int32), np.array([1], np.int32), 2)
+    with pytest.raises(B.GempeError) as ei:
+        B.gempe_batch_create([good, good, asym])
+    assert ei.value.status == -2 and "graph 2" in str(ei.value) and "without its reverse" in str(ei.value)
