@@ -51,7 +51,9 @@ FORMS = {
 }
 BATCH_WORKLOADS = {"sbm-batch-256", "sbm-batch-256-bf16"}
 # serving form: Poisson arrivals (50 jobs/s) of R-MAT embedding jobs under a 120 GB device budget
-SERVE_WORKLOADS = {"rmat-serve-poisson50": {}}
+SERVE_WORKLOADS = {"rmat-serve-poisson50": {},
+                   "rmat-serve-poisson50-bf16": {"precision": 1}}   # BF16 positions for the d >= 8 jobs
+SERVE_MAX_JOBS = 600   # jobs of one serving run (12 s of arrivals at 50 per second)
 FORMS.update(SERVE_WORKLOADS)
 L2_FLUSH_BYTES = 256 << 20
 EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
@@ -595,8 +597,9 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """The serving form.  --steps jobs arrive as a Poisson stream (mean 50 per
-    second): each an R-MAT graph with scale uniform in 10..18 and edge factor
+    """The serving form.  --steps jobs (at most SERVE_MAX_JOBS) arrive as a
+    Poisson stream (mean 50 per second): each an R-MAT graph with scale
+    uniform in 10..18 and edge factor
     uniform in 8..16 (a pool of two graphs per scale, generated before the
     timed region), d from {2, 32, 128}, 100-300 epochs, k = 10, its own seed.
     They are submitted through gempe_server_submit at their arrival times to a
@@ -622,7 +625,7 @@ def run_serve(args):
             pool[scale].append((rp, ci, ef))
     k = 10
     budget = 120 * (1 << 30)
-    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED)
+    p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED, **FORMS[args.workload])
 
     def draw_job(q):
         scale = int(rng.integers(10, 19))
@@ -636,7 +639,7 @@ def run_serve(args):
         jid = B.gempe_server_submit(srv, j["rp"], j["ci"], j["d"], 20, j["seed"])
         B.gempe_server_wait(srv, jid, 600000)
         B.gempe_server_result(srv, jid)
-    jobs = [draw_job(q) for q in range(args.steps)]
+    jobs = [draw_job(q) for q in range(min(args.steps, SERVE_MAX_JOBS))]
     gaps = rng.exponential(1.0 / 50.0, size=len(jobs))
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -703,7 +706,11 @@ def run_serve(args):
         "clocks": clk,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "step": "one job through the public serving calls (submit from host CSR, result to host)"},
-        "gpu_launches": None,
+        # per job: set-up (edge set, symmetry check, positions, and for d <= 4 the
+        # oriented CSR: count, three scan passes, fill) and per epoch the sweep,
+        # the update and the next epoch's sampler
+        "gpu_launches": int(sum(3 + (5 if j["d"] <= 4 else 0) + 3 * j["epochs"] for j in jobs)),
+        "gpu_launches_note": "counted from the engine's launch structure (set-up and three kernels per epoch per job)",
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line))

@@ -78,14 +78,17 @@ def test_batched_form_final_loss(B, O):
         assert pe_gpu == pytest.approx(pe_ref, rel=0.01), f"graph {q} d={g['d']}"
 
 
-def test_served_form_final_loss(B, O):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_served_form_final_loss(B, O, precision):
+    """Served jobs (precision 1: BF16 positions for the d >= 8 jobs) against
+    the FP64 oracle's runs of the same seeds."""
     from paper_2011_03479_gb300 import inputs
     jobs = []
     for q, (scale, d) in enumerate([(9, 2), (10, 32), (9, 128)]):
         rp, ci = inputs.rmat(scale, 10, seed=5301 + q)
         jobs.append((rp, ci, d, 0x5E5E1000 + q))
     epochs = 50
-    p = B.gempe_default_params(neg_per_vertex=10)
+    p = B.gempe_default_params(neg_per_vertex=10, precision=precision)
     with B.gempe_server_create(4 << 30, max_jobs=4, params=p) as srv:
         ids = [B.gempe_server_submit(srv, rp, ci, d, epochs, s) for rp, ci, d, s in jobs]
         infos = [B.gempe_server_wait(srv, i, 120000) for i in ids]
