@@ -10,15 +10,18 @@
 //
 //  k_block_sampler  partners and per-vertex masks of the next epoch (runs on
 //                   the side stream beside the current epoch's sweep)
-//  k_tile_bf16      one CTA per tile: with BF16 positions X_T (128 x d) and
-//                   X_P (64 x d), tensor-core tiles (mma.sync m16n8k16, FP32
-//                   accumulation) give
+//  k_tile_tc        one CTA per tile: with BF16 positions X_T (128 x d) and
+//                   X_P (64 x d), 5th-generation tensor cores (tcgen05.mma,
+//                   operands in shared memory, FP32 accumulators in TMEM) give
 //                     S = X_T X_P^T,  delta^2 = |x_i|^2 + |x_g|^2 - 2 S,
-//                   the pair terms (c, w) of Eq. 3-5 per (i, g), then
+//                   the pair terms (c, w) of Eq. 3-5 per (i, g) (rounded to
+//                   BF16 for the next products), then
 //                     A = C X_P    -> y_i - z_i x_i += x_i rowsum(C) - A_i
 //                     B = C^T X_T  -> y_g - z_g x_g += x_g colsum(C) - B_g
 //                   and z_i += rowsum(W), z_g += colsum(W).
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "device_math.cuh"
 #include "engine.cuh"
@@ -33,6 +36,9 @@ constexpr uint32_t kTagBlock = 0x0D000000u;
 constexpr int kTileThreads = 256;          // 8 warps, 16 tile rows each
 constexpr int kSamplerWarps = 8;
 constexpr int kMiniHash = 128;             // slots of the per-warp partner hash
+constexpr int kTileWaitLimit = 1 << 22;    // mbarrier polls before a tile CTA gives up
+constexpr int32_t kStatusTimeout = -5;     // gempe_status of a bounded device wait that gave up
+constexpr size_t kTileMinSmem = 80 * 1024; // keeps tile CTAs at two per SM (TMEM columns)
 
 // ---------------------------------------------------------------------------
 // k_block_sampler: one warp per tile.
@@ -164,28 +170,76 @@ __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const Epoc
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core helpers (mma.sync m16n8k16, BF16 inputs, FP32 accumulation)
+// 5th-generation tensor cores (tcgen05): operands in shared memory, the
+// accumulators in tensor memory (TMEM).
+//
+// Operand layout: every BF16 matrix of the tile kernel is stored in 8-row x
+// 16-byte core matrices; element (r, c) of an R x W buffer sits at byte
+//   (r / 8) * (W / 8) * 128 + (c / 8) * 128 + (r % 8) * 16 + (c % 8) * 2.
+// Read with K along c (K-major) its shared-memory descriptor has leading
+// byte offset (between core matrices along K) 128 and stride byte offset
+// (between 8-row groups) (W / 8) * 128; read with K along r (MN-major, the
+// 16-byte rows running along M or N) the leading offset is (W / 8) * 128 and
+// the stride offset 128.  No swizzling.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
+__host__ __device__ constexpr uint32_t core_off(int r, int c, int W) {
+    return (uint32_t)((r >> 3) * (W / 8) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// A / B major (0 K-major, 1 MN-major), N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) = A B (+ D when accumulate); issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// The mbarrier completes one phase when every MMA issued so far by this
+// thread has finished.
+__device__ __forceinline__ void tc_commit(unsigned long long* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(mbar)));
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kTileWaitLimit && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity));
+    return done != 0;
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane (the warp's quadrant).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    return __uint_as_float(r);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -193,78 +247,60 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ float bf16_at(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-// Shared-memory layout of k_tile_bf16 (rows padded by 8 BF16 so that the
-// eight 16-byte rows an ldmatrix reads fall into distinct banks).
+// Shared memory of the tile kernel.  XT: the tile's BF16 rows (128 x DP),
+// XP: the partners' rows (64 x DP), DP = d + 16: column d holds 1 (so that
+// the products with them also give the row and column sums), d + 1 .. d + 15
+// zero.  CW: the pair coefficients, C in columns 0..63, W in 64..127.
 template <int D>
-struct TileSmem {
-    static constexpr int kXS = D + 8;          // row stride (elements) of X_T, X_P
-    static constexpr int kCS = kBlockP + 8;    // row stride of C
-    __nv_bfloat16 xt[2][kBlockT * kXS];   // double buffer: the next tile's rows load during this one
-    __nv_bfloat16 xp[2][kBlockP * kXS];
-    __nv_bfloat16 cs[kBlockT * kCS];
+struct TileTc {
+    static constexpr int DP = D + 16;
+    static constexpr uint32_t kCols = 256;                   // TMEM columns: S, A, B
+    static constexpr uint32_t kColS = 0, kColA = 64, kColB = 64 + DP;
+    __nv_bfloat16 xt[kBlockT * DP];
+    __nv_bfloat16 xp[kBlockP * DP];
+    __nv_bfloat16 cw[kBlockT * 2 * kBlockP];
     float nt[kBlockT], np[kBlockP];
-    float row_c[kBlockT], row_w[kBlockT];
-    float col_c[8][kBlockP], col_w[8][kBlockP];
+    float row_w[2][kBlockT];
+    float col_w[kBlockP];
     unsigned long long mask[kBlockT];
     int deg[kBlockT], kacc[kBlockT];
-    int part[2][kBlockP];
+    int part[kBlockP];
+    unsigned long long mbar;
+    uint32_t tmem;
+    int abort;
 };
 
-// Start the asynchronous loads of tile item `it` (if below `end`) into
-// buffer b: its partner list, X_T (zero rows past the graph's end) and X_P;
-// always commits one cp.async group.
-template <int D>
-__device__ __forceinline__ void stage_tile(const EpochArgs& a, TileSmem<D>& sm, int it, int end, int b) {
-    constexpr int XS = TileSmem<D>::kXS;
-    constexpr int CH = D / 8;   // 16-byte chunks per row
-    if (it < end) {
-        const int2 ti = __ldg(a.tile_items + it);
-        const int tile = ti.x, graph = ti.y;
-        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
-        const int lt = tile - __ldg(&a.graphs[graph].t0);
-        const int v0 = gv0 + lt * kBlockT;
-        const int nv = min(kBlockT, gn - lt * kBlockT);
-        const int epoch = a.gst[graph].epoch;
-        const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
-        if (threadIdx.x < kBlockP) sm.part[b][threadIdx.x] = __ldg(part + threadIdx.x);
-        for (int c = threadIdx.x; c < kBlockT * CH; c += blockDim.x) {
-            const int r = c / CH, q = c - r * CH;
-            __nv_bfloat16* dst = sm.xt[b] + r * XS + q * 8;
-            if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + q * 8);
-            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        }
-        for (int c = threadIdx.x; c < kBlockP * CH; c += blockDim.x) {
-            const int r = c / CH, q = c - r * CH;
-            cp_async16(sm.xp[b] + r * XS + q * 8, a.xb + (size_t)__ldg(part + r) * D + q * 8);
-        }
-    }
-    cp_async_commit();
-}
-
 // ---------------------------------------------------------------------------
-// k_tile_bf16: block-sampled non-edges of one tile per CTA iteration; the
-// next tile's rows are staged (cp.async) while the current one computes.
+// k_tile_tc: block-sampled non-edges, one tile per CTA iteration, 8 warps.
+//   (1) S = X_T X_P^T (M 128, N 64, K d) into TMEM;
+//   (2) warp w reads rows 32 (w % 4) .. of S, partner columns 32 (w / 4) ..,
+//       forms the pair terms (c, w) with the masks and histograms, and
+//       writes them rounded to BF16 into CW;
+//   (3) A = C [X_P | 1] (K 64) gives sum_g c_ig x_g and rowsum(C);
+//       B = [C | W]^T [X_T | 1] (M 128, K 128) gives sum_i c_ig x_i and
+//       colsum(C) in rows 0..63, colsum(W) in rows 64..127;
+//   (4) x_i rowsum(C) - A_i and the row sums of W go to the anchors'
+//       accumulators, x_g colsum(C) - B_g and colsum(W) to the partners'.
+// One thread issues the MMAs; their completion is signalled on an mbarrier
+// (bounded waits: a timeout sets the pack's status and ends the kernel).
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
-    constexpr int KS = D / 16;          // k-steps of S = X_T X_P^T
-    constexpr int ND = D / 8;           // n-tiles over the dimensions
-    constexpr int XS = TileSmem<D>::kXS, CS = TileSmem<D>::kCS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem<D>& sm = *reinterpret_cast<TileSmem<D>*>(smem_raw);
-    unsigned int* hist_base = reinterpret_cast<unsigned int*>(smem_raw + sizeof(TileSmem<D>));
-    // tile items: a contiguous range per block in packs of several graphs
+__global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) {
+    using L = TileTc<D>;
+    constexpr int DP = L::DP;
+    constexpr int CH = D / 8;                     // 16-byte chunks of a row
+    constexpr uint32_t kSbT = (DP / 8) * 128;     // stride of 8-row groups of XT, XP
+    constexpr uint32_t kSbC = (2 * kBlockP / 8) * 128;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    L& sm = *reinterpret_cast<L*>(smem_raw);
+    unsigned int* hist_base = reinterpret_cast<unsigned int*>(smem_raw + sizeof(L));
     int it0, it1, istep, home;
     if (a.blocked) {
         it0 = (int)((long long)a.n_tile_items * blockIdx.x / gridDim.x);
@@ -279,22 +315,42 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
     }
     const BlockHist hist = block_hist(hist_base, a.bins, home);
     __shared__ unsigned int s_used, s_tile_used;
-    for (int t = threadIdx.x; t < a.bins; t += blockDim.x) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int quad = w & 3, half = w >> 2;
+    for (int t = tid; t < a.bins; t += blockDim.x) {
         hist.he[t] = 0u;
         hist.hc[t] = 0u;
         hist.hd[t] = 0u;
     }
-    if (threadIdx.x == 0) {
+    // the constant columns d .. d + 15 of XT and XP: 1, then zeros
+    for (int r = tid; r < kBlockT + kBlockP; r += blockDim.x) {
+        __nv_bfloat16* base = r < kBlockT ? sm.xt : sm.xp;
+        const int rr = r < kBlockT ? r : r - kBlockT;
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(base) + core_off(rr, D, DP)) =
+            make_uint4(0x3F80u, 0u, 0u, 0u);   // BF16 1.0 in the first element
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(base) + core_off(rr, D + 8, DP)) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (tid == 0) {
         s_used = 0u;
         s_tile_used = 0u;
+        sm.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&sm.tmem)), "r"(L::kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = sm.tmem;
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;   // this warp's TMEM lanes
+    uint32_t phase = 0;
 
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int g = lane >> 2, t4 = lane & 3;
-
-    stage_tile<D>(a, sm, it0, it1, 0);
-    int buf = 0;
-    for (int it = it0; it < it1; it += istep, buf ^= 1) {
+    for (int it = it0; it < it1; it += istep) {
         const int2 ti = __ldg(a.tile_items + it);
         const int tile = ti.x, graph = ti.y;
         const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
@@ -305,13 +361,24 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
-        __syncthreads();   // the previous tile's shared data (and buffer buf ^ 1) is no longer read
-        stage_tile<D>(a, sm, it + istep, it1, buf ^ 1);
-        const __nv_bfloat16* xt = sm.xt[buf];
-        const __nv_bfloat16* xp = sm.xp[buf];
-        const int* prt = sm.part[buf];
-        // ---- masks and degrees (X_T, X_P and the partners were staged one tile ahead) ----
-        for (int v = threadIdx.x; v < kBlockT; v += blockDim.x) {
+        const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
+
+        // ---- stage: rows (cp.async into the core layout), partners, masks ----
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // the previous tile's shared data and TMEM are no longer read
+        if (tid < kBlockP) sm.part[tid] = __ldg(part + tid);
+        for (int c = tid; c < kBlockT * CH; c += blockDim.x) {
+            const int r = c / CH, q = c - r * CH;
+            unsigned char* dst = reinterpret_cast<unsigned char*>(sm.xt) + core_off(r, 8 * q, DP);
+            if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + 8 * q);
+            else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        for (int c = tid; c < kBlockP * CH; c += blockDim.x) {
+            const int r = c / CH, q = c - r * CH;
+            cp_async16(reinterpret_cast<unsigned char*>(sm.xp) + core_off(r, 8 * q, DP),
+                       a.xb + (size_t)__ldg(part + r) * D + 8 * q);
+        }
+        for (int v = tid; v < kBlockT; v += blockDim.x) {
             if (v < nv) {
                 const unsigned long long m = bmask[v0 + v];
                 bmask[v0 + v] = 0ull;   // read once: the buffer starts empty for the epoch two ahead
@@ -325,229 +392,208 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bf16(const EpochArgs a) {
                 sm.kacc[v] = 0;
             }
         }
-        cp_async_wait_prev();   // this tile's group has landed (the next one may still be loading)
+        cp_async_wait_all();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             if (s_tile_used) {
                 if (graph == home) s_used += s_tile_used;
                 else atomicAdd(&a.gst[graph].used, (unsigned long long)s_tile_used);
             }
             s_tile_used = 0u;
         }
-        for (int r = threadIdx.x; r < kBlockT + kBlockP; r += blockDim.x) {
-            const __nv_bfloat16* row = (r < kBlockT) ? xt + r * XS : xp + (r - kBlockT) * XS;
-            float s = 0.0f;
-#pragma unroll 8
-            for (int c = 0; c < D; ++c) {
-                const float v = bf16_at(row + c);
-                s = fmaf(v, v, s);
+        // squared norms of the BF16 rows (what S is made of)
+        for (int r = tid; r < kBlockT + kBlockP; r += blockDim.x) {
+            const unsigned char* base = reinterpret_cast<const unsigned char*>(r < kBlockT ? sm.xt : sm.xp);
+            const int rr = r < kBlockT ? r : r - kBlockT;
+            float s2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const uint4 u = *reinterpret_cast<const uint4*>(base + core_off(rr, 8 * q, DP));
+                const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float lo = __uint_as_float(wd[e] << 16), hi = __uint_as_float(wd[e] & 0xFFFF0000u);
+                    s2 = fmaf(lo, lo, fmaf(hi, hi, s2));
+                }
             }
-            if (r < kBlockT) sm.nt[r] = s; else sm.np[r - kBlockT] = s;
+            if (r < kBlockT) sm.nt[rr] = s2; else sm.np[rr] = s2;
         }
+        asm volatile("fence.proxy.async.shared::cta;");   // the staged rows, for the tensor cores
         __syncthreads();
 
-        // ---- S = X_T X_P^T for rows 16w..16w+15 ----
-        const int r0 = 16 * w;
-        float S[8][4];
+        // ---- (1) S = X_T X_P^T ----
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t at = smem_u32(sm.xt), ap = smem_u32(sm.xp);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) S[j][e] = 0.0f;
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            uint32_t af[4];
-            {
-                const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4(af, xt + (r0 + rr + 8 * (mat & 1)) * XS + 16 * ks + 8 * (mat >> 1));
-            }
-#pragma unroll
-            for (int j = 0; j < 8; j += 2) {
-                uint32_t bf[4];
-                const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4(bf, xp + (8 * (j + (mat >> 1)) + rr) * XS + 16 * ks + 8 * (mat & 1));
-                mma_16816(S[j], af, bf[0], bf[1]);
-                mma_16816(S[j + 1], af, bf[2], bf[3]);
-            }
+            for (int k = 0; k < D / 16; ++k)
+                tc_mma(tmem + L::kColS, smem_desc(at + 256 * k, 128, kSbT), smem_desc(ap + 256 * k, 128, kSbT),
+                       mma_idesc(128, kBlockP, 0, 0), k > 0);
+            tc_commit(&sm.mbar);
         }
+        if (!mbar_wait(&sm.mbar, phase)) atomicExch(&sm.abort, 1);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (sm.abort) break;
 
-        // ---- pair terms per (i, p); C to registers (bf16) and shared memory ----
-        // Af[kk]: A fragments of C for C X_P, k-step kk (partners 16kk..16kk+15):
-        // {C(g, 16kk+2t..), C(g+8, 16kk+2t..), C(g, 16kk+8+2t..), C(g+8, 16kk+8+2t..)}
-        uint32_t Af[4][4];
-        float rc[2] = {0.0f, 0.0f}, rw[2] = {0.0f, 0.0f};    // row sums for rows g, g + 8
+        // ---- (2) pair terms: anchor i = 32 quad + lane, partners 32 half .. 32 half + 31 ----
+        {
+            const int i = 32 * quad + lane;
+            const unsigned long long mk = sm.mask[i];
+            const float ni = sm.nt[i];
+            const int di = sm.deg[i], ki = sm.kacc[i];
+            float rw = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            float cv[4], col_c[2] = {0.0f, 0.0f}, col_w[2] = {0.0f, 0.0f};
+            for (int c8 = 0; c8 < 4; ++c8) {
+                const int p0 = 32 * half + 8 * c8;
+                float sv[8];
+                tmem_ld8(tmem + lane_base + L::kColS + (uint32_t)p0, sv);
+                float cv[8], wv[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int il = r0 + g + 8 * (e >> 1);
-                const int p = 8 * j + 2 * t4 + (e & 1);
-                const bool valid = !((sm.mask[il] >> p) & 1ull);
-                float c = 0.0f, wv = 0.0f;
-                if (valid) {
-                    const float d2 = fmaxf(sm.nt[il] + sm.np[p] - 2.0f * S[j][e], 0.0f);
-                    float delta, inv_delta;
-                    dist_of(d2, delta, inv_delta);
-                    const PairTerm pt = pair_term(delta, inv_delta, false, K);
-                    c = pt.c;
-                    wv = pt.w;
-                    const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                    hist_sample(hist, a, graph, bin, sm.deg[il], sm.kacc[il], kBlockP);
-                }
-                cv[e] = c;
-                rc[e >> 1] += c;
-                rw[e >> 1] += wv;
-                col_c[e & 1] += c;
-                col_w[e & 1] += wv;
-            }
-            const uint32_t top = pack_bf16(cv[0], cv[1]), bot = pack_bf16(cv[2], cv[3]);
-            Af[j >> 1][(j & 1) * 2 + 0] = top;
-            Af[j >> 1][(j & 1) * 2 + 1] = bot;
-            *reinterpret_cast<uint32_t*>(sm.cs + (r0 + g) * CS + 8 * j + 2 * t4) = top;
-            *reinterpret_cast<uint32_t*>(sm.cs + (r0 + g + 8) * CS + 8 * j + 2 * t4) = bot;
-            // column sums over the warp's 16 rows (lanes with equal t4)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-#pragma unroll
-                for (int o = 4; o < 32; o <<= 1) {
-                    col_c[e] += __shfl_xor_sync(kFull, col_c[e], o);
-                    col_w[e] += __shfl_xor_sync(kFull, col_w[e], o);
-                }
-                if (g == 0) {
-                    sm.col_c[w][8 * j + 2 * t4 + e] = col_c[e];
-                    sm.col_w[w][8 * j + 2 * t4 + e] = col_w[e];
-                }
-            }
-        }
-        // row sums over the quad
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            rc[h] += __shfl_xor_sync(kFull, rc[h], 1);
-            rc[h] += __shfl_xor_sync(kFull, rc[h], 2);
-            rw[h] += __shfl_xor_sync(kFull, rw[h], 1);
-            rw[h] += __shfl_xor_sync(kFull, rw[h], 2);
-        }
-        if (t4 == 0) {
-            sm.row_c[r0 + g] = rc[0];
-            sm.row_c[r0 + g + 8] = rc[1];
-            sm.row_w[r0 + g] = rw[0];
-            sm.row_w[r0 + g + 8] = rw[1];
-        }
-        __syncwarp();
-
-        // ---- A = C X_P: anchors of rows 16w..16w+15 ----
-#pragma unroll
-        for (int jd = 0; jd < ND; jd += 2) {
-            float A0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, A1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                uint32_t bf[4];
-                const int mat = lane >> 3, rr = lane & 7;
-                ldsm_x4_t(bf, xp + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (jd + (mat >> 1)));
-                mma_16816(A0, Af[kk], bf[0], bf[1]);
-                mma_16816(A1, Af[kk], bf[2], bf[3]);
-            }
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const float* Ar = hh ? A1 : A0;
-                const int dim = 8 * (jd + hh) + 2 * t4;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int il = r0 + g + 8 * h;
-                    if (il < nv && sm.kacc[il] > 0) {
-                        const float s = sm.row_c[il];
-                        const float v0f = bf16_at(xt + il * XS + dim) * s - Ar[2 * h];
-                        const float v1f = bf16_at(xt + il * XS + dim + 1) * s - Ar[2 * h + 1];
-                        atomicAdd(reinterpret_cast<float2*>(a.acc + (size_t)(v0 + il) * a.acc_stride + dim),
-                                  make_float2(v0f, v1f));
+                for (int e = 0; e < 8; ++e) {
+                    const int p = p0 + e;
+                    cv[e] = 0.0f;
+                    wv[e] = 0.0f;
+                    if (!((mk >> p) & 1ull)) {
+                        const float d2 = fmaxf(ni + sm.np[p] - 2.0f * sv[e], 0.0f);
+                        float delta, inv_delta;
+                        dist_of(d2, delta, inv_delta);
+                        const PairTerm pt = pair_term(delta, inv_delta, false, K);
+                        cv[e] = pt.c;
+                        wv[e] = pt.w;
+                        const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
+                        hist_sample(hist, a, graph, bin, di, ki, kBlockP);
                     }
+                    rw += wv[e];
                 }
+                unsigned char* cw = reinterpret_cast<unsigned char*>(sm.cw);
+                *reinterpret_cast<uint4*>(cw + core_off(i, p0, 2 * kBlockP)) =
+                    make_uint4(pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]), pack_bf16(cv[4], cv[5]),
+                               pack_bf16(cv[6], cv[7]));
+                *reinterpret_cast<uint4*>(cw + core_off(i, kBlockP + p0, 2 * kBlockP)) =
+                    make_uint4(pack_bf16(wv[0], wv[1]), pack_bf16(wv[2], wv[3]), pack_bf16(wv[4], wv[5]),
+                               pack_bf16(wv[6], wv[7]));
             }
+            sm.row_w[half][i] = rw;
         }
-        if (t4 == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int il = r0 + g + 8 * h;
-                if (il < nv && sm.kacc[il] > 0) atomicAdd(a.acc + (size_t)(v0 + il) * a.acc_stride + D, sm.row_w[il]);
-            }
-        }
-        __syncthreads();   // C in shared memory and the column sums are complete
+        asm volatile("fence.proxy.async.shared::cta;");   // CW, for the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
 
-        // ---- B = C^T X_T: partners; warp w -> partners 16*(w>>1).., dims half (w&1) ----
-        if (a.symmetric) {
-            const int m0 = 16 * (w >> 1);
-            constexpr int NW = ND / 2;     // n-tiles per warp
-            float Bacc[NW][4];
+        // ---- (3) A = C [X_P | 1],  B = [C | W]^T [X_T | 1] ----
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t at = smem_u32(sm.xt), ap = smem_u32(sm.xp), ac = smem_u32(sm.cw);
 #pragma unroll
-            for (int j = 0; j < NW; ++j)
+            for (int k = 0; k < kBlockP / 16; ++k)   // K = partners: C K-major, X_P MN-major
+                tc_mma(tmem + L::kColA, smem_desc(ac + 256 * k, 128, kSbC), smem_desc(ap + 2 * k * kSbT, kSbT, 128),
+                       mma_idesc(128, DP, 0, 1), k > 0);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) Bacc[j][e] = 0.0f;
-            const int nbase = (w & 1) * NW;
+            for (int k = 0; k < kBlockT / 16; ++k)   // K = anchors: [C | W] and X_T both MN-major
+                tc_mma(tmem + L::kColB, smem_desc(ac + 2 * k * kSbC, kSbC, 128), smem_desc(at + 2 * k * kSbT, kSbT, 128),
+                       mma_idesc(128, DP, 1, 1), k > 0);
+            tc_commit(&sm.mbar);
+        }
+        if (!mbar_wait(&sm.mbar, phase)) atomicExch(&sm.abort, 1);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (sm.abort) break;
+
+        // ---- (4) accumulators ----
+        // colsum(W) of partner g sits in TMEM lane 64 + g, column d of B
+        if (quad >= 2 && half == 0) sm.col_w[32 * (quad - 2) + lane] = tmem_ld1(tmem + lane_base + L::kColB + D);
+        {
+            // anchors: dims [half * D/2, (half + 1) * D/2)
+            const int i = 32 * quad + lane;
+            const float rsum = tmem_ld1(tmem + lane_base + L::kColA + D);   // rowsum of C (rounded terms)
+            const bool live = i < nv && sm.kacc[i] > 0;
+            float* row = a.acc + (size_t)(v0 + i) * a.acc_stride;
 #pragma unroll
-            for (int kk = 0; kk < kBlockT / 16; ++kk) {
-                uint32_t af[4];
-                {
-                    const int mat = lane >> 3, rr = lane & 7;
-                    ldsm_x4_t(af, sm.cs + (16 * kk + 8 * (mat >> 1) + rr) * CS + m0 + 8 * (mat & 1));
-                }
+            for (int c8 = 0; c8 < D / 16; ++c8) {
+                const int d0 = half * (D / 2) + 8 * c8;
+                float av[8];
+                tmem_ld8(tmem + lane_base + L::kColA + (uint32_t)d0, av);
+                if (live) {
+                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(sm.xt) +
+                                                                    core_off(i, d0, DP));
+                    const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+                    float o[8];
 #pragma unroll
-                for (int j = 0; j < NW; j += 2) {
-                    uint32_t bf[4];
-                    const int mat = lane >> 3, rr = lane & 7;
-                    ldsm_x4_t(bf, xt + (16 * kk + 8 * (mat & 1) + rr) * XS + 8 * (nbase + j + (mat >> 1)));
-                    mma_16816(Bacc[j], af, bf[0], bf[1]);
-                    if (j + 1 < NW) mma_16816(Bacc[j + 1], af, bf[2], bf[3]);
+                    for (int e = 0; e < 4; ++e) {
+                        o[2 * e] = __uint_as_float(wd[e] << 16) * rsum - av[2 * e];
+                        o[2 * e + 1] = __uint_as_float(wd[e] & 0xFFFF0000u) * rsum - av[2 * e + 1];
+                    }
+                    atomicAdd(reinterpret_cast<float4*>(row + d0), make_float4(o[0], o[1], o[2], o[3]));
+                    atomicAdd(reinterpret_cast<float4*>(row + d0 + 4), make_float4(o[4], o[5], o[6], o[7]));
                 }
             }
+            if (live && half == 0) atomicAdd(row + D, sm.row_w[0][i] + sm.row_w[1][i]);
+        }
+        __syncthreads();   // col_w
+        if (a.symmetric && quad < 2) {
+            // partners g = 32 quad + lane, dims [half * D/2, (half + 1) * D/2)
+            const int g = 32 * quad + lane;
+            const float csum = tmem_ld1(tmem + lane_base + L::kColB + D);
+            const float wsum = sm.col_w[g];
+            const int gv = sm.part[g];
+            float* row = a.acc + (size_t)gv * a.acc_stride;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int p = m0 + g + 8 * h;
-                float csum = 0.0f, wsum = 0.0f;
+            for (int c8 = 0; c8 < D / 16; ++c8) {
+                const int d0 = half * (D / 2) + 8 * c8;
+                float bv[8];
+                tmem_ld8(tmem + lane_base + L::kColB + (uint32_t)d0, bv);
+                if (wsum != 0.0f || csum != 0.0f) {
+                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(sm.xp) +
+                                                                    core_off(g, d0, DP));
+                    const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+                    float o[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    csum += sm.col_c[q][p];
-                    wsum += sm.col_w[q][p];
+                    for (int e = 0; e < 4; ++e) {
+                        o[2 * e] = __uint_as_float(wd[e] << 16) * csum - bv[2 * e];
+                        o[2 * e + 1] = __uint_as_float(wd[e] & 0xFFFF0000u) * csum - bv[2 * e + 1];
+                    }
+                    atomicAdd(reinterpret_cast<float4*>(row + d0), make_float4(o[0], o[1], o[2], o[3]));
+                    atomicAdd(reinterpret_cast<float4*>(row + d0 + 4), make_float4(o[4], o[5], o[6], o[7]));
                 }
-                if (wsum == 0.0f && csum == 0.0f) continue;   // every pair of this partner masked or underflowed
-                const int gv = prt[p];
-#pragma unroll
-                for (int j = 0; j < NW; ++j) {
-                    const int dim = 8 * (nbase + j) + 2 * t4;
-                    const float v0f = bf16_at(xp + p * XS + dim) * csum - Bacc[j][2 * h];
-                    const float v1f = bf16_at(xp + p * XS + dim + 1) * csum - Bacc[j][2 * h + 1];
-                    atomicAdd(reinterpret_cast<float2*>(a.acc + (size_t)gv * a.acc_stride + dim), make_float2(v0f, v1f));
-                }
-                if (t4 == 0 && (w & 1) == 0) atomicAdd(a.acc + (size_t)gv * a.acc_stride + D, wsum);
             }
+            if (half == 0 && (wsum != 0.0f || csum != 0.0f)) atomicAdd(row + D, wsum);
         }
     }
     cp_async_wait_all();
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (sm.abort && tid == 0) atomicExch(&a.ps->status, kStatusTimeout);
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::kCols));
     hist_merge(hist, a);
-    if (threadIdx.x == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
+    if (tid == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
 }
 
 }  // namespace
 
 bool tile_dim(int d) { return d == 16 || d == 32 || d == 64; }
 
+// Shared memory of the tile kernel: its layout, the histogram bins, and at
+// least kTileMinSmem so that no more than two CTAs share an SM (each holds
+// 256 of the SM's 512 TMEM columns for the whole launch).
 size_t tile_smem_bytes(int d, int bins) {
     size_t base = 0;
     switch (d) {
-        case 16: base = sizeof(TileSmem<16>); break;
-        case 32: base = sizeof(TileSmem<32>); break;
-        case 64: base = sizeof(TileSmem<64>); break;
+        case 16: base = sizeof(TileTc<16>); break;
+        case 32: base = sizeof(TileTc<32>); break;
+        case 64: base = sizeof(TileTc<64>); break;
         default: return 0;
     }
-    return base + hist_smem_bytes(bins);
+    return std::max<size_t>(base + hist_smem_bytes(bins), kTileMinSmem);
 }
 
 cudaError_t prepare_tile_kernel(int d, int bins) {
     const int smem = (int)tile_smem_bytes(d, bins);
     switch (d) {
-        case 16: return cudaFuncSetAttribute(k_tile_bf16<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 32: return cudaFuncSetAttribute(k_tile_bf16<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 64: return cudaFuncSetAttribute(k_tile_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 16: return cudaFuncSetAttribute(k_tile_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 32: return cudaFuncSetAttribute(k_tile_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 64: return cudaFuncSetAttribute(k_tile_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -573,9 +619,9 @@ cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s) {
     if (a.n_tile_items == 0) return cudaSuccess;
     const size_t smem = tile_smem_bytes(a.d, a.bins);
     switch (a.d) {
-        case 16: return launch_critical(k_tile_bf16<16>, grid, kTileThreads, smem, s, a);
-        case 32: return launch_critical(k_tile_bf16<32>, grid, kTileThreads, smem, s, a);
-        case 64: return launch_critical(k_tile_bf16<64>, grid, kTileThreads, smem, s, a);
+        case 16: return launch_critical(k_tile_tc<16>, grid, kTileThreads, smem, s, a);
+        case 32: return launch_critical(k_tile_tc<32>, grid, kTileThreads, smem, s, a);
+        case 64: return launch_critical(k_tile_tc<64>, grid, kTileThreads, smem, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
