@@ -798,7 +798,9 @@ gempe_status Pack::read_status() {
         cudaMemcpyAsync(&ps->status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, stream);
         cudaStreamSynchronize(stream);
         return pack_fail((gempe_status)status,
-                         "a position became non-finite during an update; it kept its old value");
+                         status == GEMPE_E_TIMEOUT
+                             ? "a tensor-core tile gave up waiting for its MMAs (bounded wait); the epoch is incomplete"
+                             : "a position became non-finite during an update; it kept its old value");
     }
     return GEMPE_OK;
 }
