@@ -450,8 +450,13 @@ def gempe_batch_step(b: _Batch, iters: int = 1) -> None:
     _check(load().gempe_batch_step(b.handle, int(iters)))
 
 
-def gempe_batch_positions(b: _Batch, graph: int) -> np.ndarray:
-    out = np.empty((b.ns[graph], b.ds[graph]), dtype=np.float32)
+def gempe_batch_positions(b: _Batch, graph: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Positions of one graph of the batch; out: a float32 (n, d) array to fill
+    (e.g. pinned host memory), else a new one."""
+    if out is None:
+        out = np.empty((b.ns[graph], b.ds[graph]), dtype=np.float32)
+    if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != b.ns[graph] * b.ds[graph]:
+        raise ValueError("out must be a C-contiguous float32 array of n*d elements")
     _check(load().gempe_batch_positions(b.handle, int(graph), _ptr(out), out.size))
     return out
 

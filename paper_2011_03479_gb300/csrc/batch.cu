@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <vector>
@@ -64,6 +65,7 @@ GEMPE_API gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_de
     *out = nullptr;
     if (n_graphs < 1 || !graphs || !p) return pack_fail(GEMPE_E_INVALID_ARG, "need n_graphs >= 1, graphs and params");
     std::map<int, std::vector<int>> by_dim;
+    std::vector<int64_t> slots_before((size_t)n_graphs + 1, 0);
     for (int32_t g = 0; g < n_graphs; ++g) {
         if (!supported_dim(graphs[g].d))
             return pack_fail(GEMPE_E_INVALID_ARG, "graph " + std::to_string(g) + ": unsupported d");
@@ -72,11 +74,34 @@ GEMPE_API gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_de
             return pack_fail(GEMPE_E_INVALID_ARG, "graph " + std::to_string(g) + ": null CSR or n < 2");
         gempe_status rc = check_params(p, graphs[g].d >= 8 ? graphs[g].d : 8);
         if (rc != GEMPE_OK) return rc;
-        // the rows on the host, before device work; the symmetry on the device (Pack::build)
-        rc = validate_csr(graphs[g].row_ptr, graphs[g].col_idx, graphs[g].n, 0, false);
-        if (rc != GEMPE_OK)
-            return pack_fail(rc, "graph " + std::to_string(g) + ": " + std::string(gempe_last_error()));
+        slots_before[g + 1] = slots_before[g] + graphs[g].row_ptr[graphs[g].n] + graphs[g].n;
         by_dim[graphs[g].d].push_back(g);
+    }
+    // the rows of every graph on host threads (graphs in ranges of equal
+    // size), before device work; the symmetry on the device (Pack::build).
+    // The error reported is the lowest failing graph's.
+    {
+        std::mutex mu;
+        int bad = n_graphs;
+        gempe_status bad_rc = GEMPE_OK;
+        std::string bad_msg;
+        parallel_for_weighted(n_graphs, host_threads(slots_before[n_graphs]),
+                              [&](int64_t g) { return slots_before[g]; },
+                              [&](int64_t g0, int64_t g1) {
+                                  for (int64_t g = g0; g < g1; ++g) {
+                                      const gempe_status rc =
+                                          validate_csr(graphs[g].row_ptr, graphs[g].col_idx, graphs[g].n, 1, false);
+                                      if (rc == GEMPE_OK) continue;
+                                      std::lock_guard<std::mutex> lock(mu);
+                                      if (g < bad) {
+                                          bad = (int)g;
+                                          bad_rc = rc;
+                                          bad_msg = gempe_last_error();   // this thread's message
+                                      }
+                                      return;
+                                  }
+                              });
+        if (bad < n_graphs) return pack_fail(bad_rc, "graph " + std::to_string(bad) + ": " + bad_msg);
     }
     std::unique_ptr<gempe_batch> b(new gempe_batch());
     if (cuda_stream) {

@@ -165,6 +165,8 @@ cudaError_t launch_hash_build(const int32_t* row_ptr, const int32_t* col_idx, in
 cudaError_t launch_check_symmetric(const int32_t* row_ptr, const int32_t* col_idx, int32_t v0, int32_t n, int64_t nnz,
                                    const void* keys, int narrow, unsigned long long key_off,
                                    unsigned long long bucket_mask, unsigned long long* counts3, cudaStream_t s);
+// v[0..count) += off (a graph's column indices to pack rows).
+cudaError_t launch_add_offset(int32_t* v, int64_t count, int32_t off, cudaStream_t s);
 // Degree-oriented CSR of the pack (rows + 1 offsets, kept slots in row
 // order); scratch: orient_scratch_ints(rows) ints.
 size_t orient_scratch_ints(int rows);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -106,6 +107,11 @@ void parallel_ranges(int64_t count, int parts, Cum cum, F fn) {
 }
 
 }  // namespace
+
+void parallel_for_weighted(int64_t count, int parts, const std::function<int64_t(int64_t)>& cum,
+                           const std::function<void(int64_t, int64_t)>& fn) {
+    parallel_ranges(count, parts, cum, fn);
+}
 
 // Symmetric, sorted, loop-free, duplicate-free, in-range CSR.  The rows are
 // checked in parallel (ranges of equal CSR slots); the error reported is the
@@ -393,15 +399,16 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     if (tiles) PK(prepare_tile_kernel(d, bins), "tile kernel attributes");
     PK(prepare_update_kernels(bins), "update kernel attributes");
 
-    // host copies of the pack CSR
+    // host copy of the pack's row offsets (the column arrays go to the
+    // device as they are and are shifted to pack rows there)
     row_ptr_h.assign((size_t)rows + 1, 0);
-    std::vector<int32_t> col_h((size_t)std::max<int64_t>(slots, 1));
+    std::vector<int32_t> slot0(G);   // first CSR slot of each graph
     for (int32_t g = 0; g < G; ++g) {
         const GraphInput& in = gs[g];
         const GraphInfo& gi = info[g];
         const int32_t s0 = (int32_t)(g == 0 ? 0 : row_ptr_h[gi.v0]);
+        slot0[g] = s0;
         for (int32_t i = 0; i <= in.n; ++i) row_ptr_h[(size_t)gi.v0 + i] = s0 + in.row_ptr[i];
-        for (int64_t e = 0; e < nnz[g]; ++e) col_h[(size_t)s0 + e] = gi.v0 + in.col_idx[e];
         // the spare row v0 + n closes the range; the next graph starts there
         if (g + 1 < G) row_ptr_h[(size_t)gi.v0 + in.n + 1] = s0 + (int32_t)nnz[g];
     }
@@ -436,7 +443,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     // device memory
     const size_t R = (size_t)rows;
     row_ptr = (int32_t*)alloc(sizeof(int32_t) * (R + 1));
-    col_idx = (int32_t*)alloc(sizeof(int32_t) * col_h.size());
+    col_idx = (int32_t*)alloc(sizeof(int32_t) * std::max<size_t>((size_t)slots, 1));
     keys = alloc((narrow_keys ? 4 : 8) * key_slots);
     // set-up scratch: per graph {slots above, below, below without reverse}
     // of the symmetry check, then the oriented rows' counts and scan sums
@@ -497,7 +504,12 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         st.map_period = bytemap ? 0 : -1;   // the maps are built below for period 0
     }
     PK(cudaMemcpyAsync(row_ptr, row_ptr_h.data(), sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s), "copy row_ptr");
-    PK(cudaMemcpyAsync(col_idx, col_h.data(), sizeof(int32_t) * col_h.size(), cudaMemcpyHostToDevice, s), "copy col_idx");
+    for (int32_t g = 0; g < G; ++g) {
+        if (nnz[g] == 0) continue;
+        PK(cudaMemcpyAsync(col_idx + slot0[g], gs[g].col_idx, sizeof(int32_t) * (size_t)nnz[g], cudaMemcpyHostToDevice, s),
+           "copy col_idx");
+        if (info[g].v0 != 0) PK(launch_add_offset(col_idx + slot0[g], nnz[g], info[g].v0, s), "col_idx to pack rows");
+    }
     PK(cudaMemsetAsync(sym, 0, sizeof(unsigned long long) * 3 * (size_t)G, s), "clear counts");
     PK(cudaMemcpyAsync(graphs, info.data(), sizeof(GraphInfo) * G, cudaMemcpyHostToDevice, s), "copy graph table");
     PK(cudaMemcpyAsync(gst, st0.data(), sizeof(GraphState) * G, cudaMemcpyHostToDevice, s), "init graph state");

@@ -5,6 +5,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,10 @@ gempe_status check_params(const gempe_params* p, int32_t d);
 gempe_status validate_csr(const int32_t* rp, const int32_t* ci, int32_t n, int threads = 0, bool symmetry = true);
 // Host threads for O(work) set-up loops: one per 65,536 items, at most 32.
 int host_threads(int64_t work);
+// fn(begin, end) over [0, count) cut into `parts` ranges of equal weight
+// (cum(i): weight of [0, i), non-decreasing), one host thread per range.
+void parallel_for_weighted(int64_t count, int parts, const std::function<int64_t(int64_t)>& cum,
+                           const std::function<void(int64_t, int64_t)>& fn);
 
 struct Pack {
     gempe_params p{};

@@ -9,6 +9,7 @@
 //  k_orient_count     one warp per row: the row's kept slots
 //  k_scan_*           exclusive scan of the counts into row offsets
 //  k_orient_fill      one warp per row: the kept slots in row order
+//  k_add_offset       a graph's column indices shifted to pack rows
 #include <cuda_runtime.h>
 
 #include "device_math.cuh"
@@ -193,6 +194,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t* __restrict__
     if (blockIdx.x == 0 && threadIdx.x == 0) out[count] = tile_sums[tiles];
 }
 
+__global__ void k_add_offset(int32_t* __restrict__ v, int64_t count, int32_t off) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+        v[q] += off;
+}
+
 int grid_for(long long items, int per_block, int cap) {
     long long g = (items + per_block - 1) / per_block;
     if (g > cap) g = cap;
@@ -207,6 +213,12 @@ cudaError_t launch_check_symmetric(const int32_t* row_ptr, const int32_t* col_id
     if (nnz == 0) return cudaSuccess;
     k_check_symmetric<<<grid_for(nnz, 256, 65535), 256, 0, s>>>(row_ptr, col_idx, v0, n, keys, narrow, key_off,
                                                                  bucket_mask, counts3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_offset(int32_t* v, int64_t count, int32_t off, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_add_offset<<<grid_for(count, 256, 4096), 256, 0, s>>>(v, count, off);
     return cudaGetLastError();
 }
 
