@@ -234,12 +234,17 @@ int unit_pairs_of(const int4& u, int k_slots, bool per_slot) {
 
 void wide_tasks(std::vector<int4>& units, int pg, int k_slots, bool per_slot) {
     if (pg <= 1) return;
-    auto pairs = [&](const int4& u) { return unit_pairs_of(u, k_slots, per_slot); };
     const size_t window = 16 * (size_t)pg;
+    // each window ordered by decreasing pair count, ties in their original
+    // order (a stable sort, without the per-call buffer of std::stable_sort)
+    std::vector<std::pair<int, int>> key(window);
+    std::vector<int4> tmp(window);
     for (size_t w0 = 0; w0 < units.size(); w0 += window) {
-        const size_t w1 = std::min(units.size(), w0 + window);
-        std::stable_sort(units.begin() + w0, units.begin() + w1,
-                         [&](const int4& x, const int4& y) { return pairs(x) > pairs(y); });
+        const size_t w1 = std::min(units.size(), w0 + window), len = w1 - w0;
+        for (size_t q = 0; q < len; ++q) key[q] = {-unit_pairs_of(units[w0 + q], k_slots, per_slot), (int)q};
+        std::sort(key.begin(), key.begin() + len);
+        for (size_t q = 0; q < len; ++q) tmp[q] = units[w0 + key[q].second];
+        std::copy(tmp.begin(), tmp.begin() + len, units.begin() + w0);
     }
     while (units.size() % pg) units.push_back(make_int4(-1, 0, 0, 0));
 }
@@ -572,7 +577,8 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     sampler_grid = gempe::sampler_grid(rows, k, sm_count);
     update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
     tile_grid = gempe::tile_grid(n_tile_items, sm_count, 0);
-    return set_shape(PackShape{});
+    // with autotuning the shape is set by autotune(), which the owner calls next
+    return p.autotune ? GEMPE_OK : set_shape(PackShape{});
 }
 
 int Pack::bytemap_log2_for(int64_t nnz, const gempe_params& p) {
