@@ -412,7 +412,7 @@ def run_gempe(args):
         "sweep_ms": statistics.mean(sweep_ms),
         "update_ms": statistics.mean(step_ms) - statistics.mean(sweep_ms),
         "roofline": {"bound": "hbm",
-                     "kernel": "k_sweep + k_tile_bf16" if (block and form.get("precision")) else "k_sweep",
+                     "kernel": "k_sweep + k_tile_tc" if (block and form.get("precision")) else "k_sweep",
                      "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} HBM copy GB/s", "unit": "GB/s", "frac": achieved / peak,
                      "algorithmic_bytes_per_launch": bytes_per_sweep, "traffic": traffic,
@@ -421,7 +421,8 @@ def run_gempe(args):
         "exact_pe": exact,
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        # per epoch: the sweep (+ the tensor-core tiles), the update, the next epoch's sampler
+        "gpu_launches": (4 if (block and form.get("precision") and d in (16, 32, 64)) else 3) * args.steps,
         "wall_s_timed_region": wall,
     }
     if not args.no_cpu_baseline:
