@@ -619,9 +619,9 @@ cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s) {
     if (a.n_tile_items == 0) return cudaSuccess;
     const size_t smem = tile_smem_bytes(a.d, a.bins);
     switch (a.d) {
-        case 16: return launch_critical(k_tile_tc<16>, grid, kTileThreads, smem, s, a);
-        case 32: return launch_critical(k_tile_tc<32>, grid, kTileThreads, smem, s, a);
-        case 64: return launch_critical(k_tile_tc<64>, grid, kTileThreads, smem, s, a);
+        case 16: return launch_critical(k_tile_tc<16>, grid, kTileThreads, smem, s, false, a);
+        case 32: return launch_critical(k_tile_tc<32>, grid, kTileThreads, smem, s, false, a);
+        case 64: return launch_critical(k_tile_tc<64>, grid, kTileThreads, smem, s, false, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -212,19 +212,25 @@ cudaError_t launch_is_edge(const void* keys, int narrow, unsigned long long key_
 // their blocks are dispatched ahead of those of the next epoch's sampler,
 // which runs beside them on the side stream and has until the next sweep.
 int critical_priority();
+// dependent: launched as a programmatic dependent of the previous kernel in
+// the stream (the kernel waits with griddepcontrol.wait before it reads what
+// that kernel wrote; the previous kernel lets it be scheduled early with
+// griddepcontrol.launch_dependents).
 template <typename... KArgs, typename... Args>
 cudaError_t launch_critical(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                            Args... args) {
+                            bool dependent, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributePriority;
-    attr.val.priority = critical_priority();
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = critical_priority();
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 

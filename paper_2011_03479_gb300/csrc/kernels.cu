@@ -757,6 +757,7 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
         }
         __syncwarp();
     }
+    asm volatile("griddepcontrol.launch_dependents;");   // the update may be scheduled (it waits for this grid)
     __syncthreads();
     hist_merge(hist, a);
     if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
@@ -969,6 +970,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         }
         if (total > 0) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
+    asm volatile("griddepcontrol.launch_dependents;");   // the update may be scheduled (it waits for this grid)
     __syncthreads();
     hist_merge(hist, a);
     if (threadIdx.x == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
@@ -1209,11 +1211,18 @@ __device__ void load_hist_smem(const EpochArgs& a, size_t off, int n, int k_slot
 // one stepped graph each.  The other blocks: x_i := y_i / z_i over the vertex
 // chunks, accumulators cleared for the next epoch.
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
+    // Launched as a programmatic dependent of the sweep (or the tiles): the
+    // slope-fit blocks copy the Mills table, which the sweep does not write,
+    // then every block waits for the sweep's grid to finish and its writes to
+    // be visible before it reads the sums and histograms.
+    extern __shared__ __align__(16) float s_bins[];   // slope fit: [2][bins], then the Mills table
+    MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
+                                                    ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
+    const bool fit_block = (int)blockIdx.x < a.n_graphs && a.sigma_source == 0 && a.sigma_every > 0;
+    if (fit_block) load_mills_smem(s_tab);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if ((int)blockIdx.x < a.n_graphs) {
         __shared__ SigmaSmem sm;
-        extern __shared__ __align__(16) float s_bins[];   // [2][bins], then the Mills table
-        MillsCoef* s_tab = reinterpret_cast<MillsCoef*>(reinterpret_cast<unsigned char*>(s_bins) +
-                                                        ((2 * (size_t)a.bins * sizeof(float) + 15) / 16) * 16);
         const int graph = blockIdx.x;
         GraphState* st = a.gst + graph;
         const size_t off = (size_t)graph * a.bins;
@@ -1224,8 +1233,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
                          (a.sigma_every == 1 || (a.sigma_every > 1 && ((epoch + 1) % a.sigma_every) == 0));
         if (fit) {
             const int k_slots = a.block_P > 0 ? kBlockP : a.k;
-            load_mills_smem(s_tab);
-            load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);
+            load_hist_smem(a, off, __ldg(&a.graphs[graph].n), k_slots, s_bins, s_bins + a.bins);   // syncs the block
             const float s =
                 block_fit_sigma(s_bins, s_bins + a.bins, a.bins, a.hist_max, a.mu, sigma_prev, s_tab, sm);
             if (threadIdx.x == 0) {
@@ -1572,14 +1580,14 @@ __global__ void k_is_edge(const void* keys, int narrow, unsigned long long key_o
 
 template <int D, int G>
 cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.xb) return launch_critical(k_sweep<D, G, __nv_bfloat16>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, a);
-    return launch_critical(k_sweep<D, G, float>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, a);
+    if (a.xb) return launch_critical(k_sweep<D, G, __nv_bfloat16>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, false, a);
+    return launch_critical(k_sweep<D, G, float>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, false, a);
 }
 
 template <int D>
 cudaError_t packed_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.oriented) return launch_critical(k_sweep_packed<D, true>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, a);
-    return launch_critical(k_sweep_packed<D, false>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, a);
+    if (a.oriented) return launch_critical(k_sweep_packed<D, true>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, false, a);
+    return launch_critical(k_sweep_packed<D, false>, grid, kPackedThreads, packed_smem_bytes(D, a.bins), s, false, a);
 }
 
 template <int D, int G>
@@ -1742,7 +1750,7 @@ cudaError_t hist_pass_for(const EpochArgs& a, int grid, cudaStream_t s) {
     EpochArgs b = a;
     b.sweep_hist = 1;          // this pass bins its own distances
     b.per_slot = 0;            // with the integer sample weights of k samples per vertex
-    const cudaError_t e = launch_critical(k_hist_pass<D, G>, grid, 256, hist_smem_bytes(a.bins), s, b);
+    const cudaError_t e = launch_critical(k_hist_pass<D, G>, grid, 256, hist_smem_bytes(a.bins), s, false, b);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1761,13 +1769,13 @@ cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fit_graphs(const EpochArgs& a, cudaStream_t s) {
-    const cudaError_t e = launch_critical(k_fit_graphs, a.n_graphs, kUpdateThreads, fit_smem_bytes(a.bins), s, a);
+    const cudaError_t e = launch_critical(k_fit_graphs, a.n_graphs, kUpdateThreads, fit_smem_bytes(a.bins), s, false, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s) {
-    const cudaError_t e = launch_critical(k_update, grid, kUpdateThreads, fit_smem_bytes(a.bins), s, a);
+    const cudaError_t e = launch_critical(k_update, grid, kUpdateThreads, fit_smem_bytes(a.bins), s, true, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
