@@ -366,7 +366,12 @@ template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16
 // previous epoch's sweep.  A thread takes one vertex's group of (up to) four
 // consecutive slots, whose first attempts come from one Philox call; a
 // rejected slot draws its further attempts alone.  Blocks take pieces of
-// sampler_piece(k) vertices of the vertex chunks (one graph each).
+// sampler_piece(k) vertices of the vertex chunks (one graph each).  With the
+// exact edge set, an anchor with at most kRowScan neighbours tests its first
+// attempts against its own CSR row, held in registers (rows of consecutive
+// vertices are adjacent in memory, so a warp's rows share a few sectors),
+// instead of one hash-table bucket per draw: the same answer, since the row
+// is the anchor's neighbour set.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int sampler_groups(int k) { return (k + 3) / 4; }
 __host__ __device__ inline int sampler_piece(int k) {
@@ -374,8 +379,10 @@ __host__ __device__ inline int sampler_piece(int k) {
     return g > 0 ? 256 / g : 256;
 }
 
+constexpr int kRowScan = 8;
+
 template <bool kMap>
-__global__ void __launch_bounds__(256, kMap ? 3 : 5) k_sampler(const EpochArgs a) {
+__global__ void __launch_bounds__(256, kMap ? 3 : 4) k_sampler(const EpochArgs a) {
     __shared__ unsigned s_cnt[4];
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
@@ -411,12 +418,30 @@ __global__ void __launch_bounds__(256, kMap ? 3 : 5) k_sampler(const EpochArgs a
             const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)q, kTagEpoch),
                                           gi.key_lo, gi.key_hi);
             int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0 + vi) * k;
+            // the anchor's neighbours (pack rows) when it has at most kRowScan, else -1s
+            int nb[kRowScan];
+            bool short_row = false;
+            if (!kMap) {
+                const int e0 = __ldg(a.row_ptr + row0 + vi), deg = __ldg(a.row_ptr + row0 + vi + 1) - e0;
+                short_row = deg <= kRowScan;
+#pragma unroll
+                for (int x = 0; x < kRowScan; ++x) nb[x] = (short_row && x < deg) ? __ldg(a.col_idx + e0 + x) : -1;
+            }
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int t = 4 * q + w;
                 if (t >= k) break;
                 int g = draw_vertex(word_of(r, w), (uint32_t)gi.n);
-                if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
+                bool taken;
+                if (!kMap && short_row) {
+                    taken = g == i;
+                    const int pg = gi.v0 + g;
+#pragma unroll
+                    for (int x = 0; x < kRowScan; ++x) taken |= nb[x] == pg;
+                } else {
+                    taken = g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3]);
+                }
+                if (taken) {
                     ++c[1];
                     g = sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
                 }
