@@ -366,12 +366,7 @@ template <> __device__ __forceinline__ const __nv_bfloat16* pos_of<__nv_bfloat16
 // previous epoch's sweep.  A thread takes one vertex's group of (up to) four
 // consecutive slots, whose first attempts come from one Philox call; a
 // rejected slot draws its further attempts alone.  Blocks take pieces of
-// sampler_piece(k) vertices of the vertex chunks (one graph each).  With the
-// exact edge set, an anchor with at most kRowScan neighbours tests its first
-// attempts against its own CSR row, held in registers (rows of consecutive
-// vertices are adjacent in memory, so a warp's rows share a few sectors),
-// instead of one hash-table bucket per draw: the same answer, since the row
-// is the anchor's neighbour set.
+// sampler_piece(k) vertices of the vertex chunks (one graph each).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int sampler_groups(int k) { return (k + 3) / 4; }
 __host__ __device__ inline int sampler_piece(int k) {
@@ -379,10 +374,8 @@ __host__ __device__ inline int sampler_piece(int k) {
     return g > 0 ? 256 / g : 256;
 }
 
-constexpr int kRowScan = 8;
-
 template <bool kMap>
-__global__ void __launch_bounds__(256, kMap ? 3 : 4) k_sampler(const EpochArgs a) {
+__global__ void __launch_bounds__(256, kMap ? 3 : 5) k_sampler(const EpochArgs a) {
     __shared__ unsigned s_cnt[4];
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
@@ -418,30 +411,12 @@ __global__ void __launch_bounds__(256, kMap ? 3 : 4) k_sampler(const EpochArgs a
             const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)q, kTagEpoch),
                                           gi.key_lo, gi.key_hi);
             int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0 + vi) * k;
-            // the anchor's neighbours (pack rows) when it has at most kRowScan, else -1s
-            int nb[kRowScan];
-            bool short_row = false;
-            if (!kMap) {
-                const int e0 = __ldg(a.row_ptr + row0 + vi), deg = __ldg(a.row_ptr + row0 + vi + 1) - e0;
-                short_row = deg <= kRowScan;
-#pragma unroll
-                for (int x = 0; x < kRowScan; ++x) nb[x] = (short_row && x < deg) ? __ldg(a.col_idx + e0 + x) : -1;
-            }
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int t = 4 * q + w;
                 if (t >= k) break;
                 int g = draw_vertex(word_of(r, w), (uint32_t)gi.n);
-                bool taken;
-                if (!kMap && short_row) {
-                    taken = g == i;
-                    const int pg = gi.v0 + g;
-#pragma unroll
-                    for (int x = 0; x < kRowScan; ++x) taken |= nb[x] == pg;
-                } else {
-                    taken = g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3]);
-                }
-                if (taken) {
+                if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
                     ++c[1];
                     g = sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
                 }
@@ -1292,6 +1267,18 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
                 const int v = ch.x + vb + sub;
                 float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
                 float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
+                // the sums and the position are loaded with z, not after it (z < z_min is rare), so
+                // that all of a vertex's loads are in flight at once
+                float4 dv[2], xo[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = ql + L * r;
+                    dv[r] = xo[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (live && q < nq) {
+                        dv[r] = row[q];
+                        xo[r] = xv[q];
+                    }
+                }
                 const float z = live ? a.acc[(size_t)v * a.acc_stride + a.d] : 0.0f;
                 const bool upd = live && z >= a.z_min;
                 float4 xn[2];
@@ -1302,9 +1289,8 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
                     for (int r = 0; r < 2; ++r) {
                         const int q = ql + L * r;
                         if (q < nq) {
-                            const float4 dv = row[q], xo = xv[q];
-                            xn[r] = make_float4(fmaf(dv.x, inv_z, xo.x), fmaf(dv.y, inv_z, xo.y),
-                                                fmaf(dv.z, inv_z, xo.z), fmaf(dv.w, inv_z, xo.w));
+                            xn[r] = make_float4(fmaf(dv[r].x, inv_z, xo[r].x), fmaf(dv[r].y, inv_z, xo[r].y),
+                                                fmaf(dv[r].z, inv_z, xo[r].z), fmaf(dv[r].w, inv_z, xo[r].w));
                             finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
                                      isfinite(xn[r].w);
                         }
@@ -1338,23 +1324,34 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
     }
     for (int c = vblk; c < a.n_vchunks; c += n_vblk) {
         const int4 ch = __ldg(a.vchunks + c);
+        // d <= 4 here (the dimensions below 8); the sums and the position are
+        // loaded with z, not after it
         for (int vi = threadIdx.x; vi < ch.y; vi += blockDim.x) {
             const int v = ch.x + vi;
             float* row = a.acc + (size_t)v * a.acc_stride;
             float* xv = a.x + (size_t)v * a.d;
+            float dv[kPackedMaxDim], xo[kPackedMaxDim];
+#pragma unroll
+            for (int c2 = 0; c2 < kPackedMaxDim; ++c2) {
+                dv[c2] = c2 < a.d ? row[c2] : 0.0f;
+                xo[c2] = c2 < a.d ? xv[c2] : 0.0f;
+            }
             const float z = row[a.d];
             if (z >= a.z_min) {
                 const float inv_z = 1.0f / z;
+                float xn[kPackedMaxDim];
                 bool bad = false;
-                for (int c2 = 0; c2 < a.d; ++c2) {
-                    const float xn = fmaf(row[c2], inv_z, xv[c2]);
-                    if (!isfinite(xn)) bad = true;
+#pragma unroll
+                for (int c2 = 0; c2 < kPackedMaxDim; ++c2) {
+                    xn[c2] = fmaf(dv[c2], inv_z, xo[c2]);
+                    if (c2 < a.d && !isfinite(xn[c2])) bad = true;
                 }
                 if (!bad) {
-                    for (int c2 = 0; c2 < a.d; ++c2) {
-                        const float xn = fmaf(row[c2], inv_z, xv[c2]);
-                        xv[c2] = xn;
-                        if (a.xb) a.xb[(size_t)v * a.d + c2] = __float2bfloat16_rn(xn);
+#pragma unroll
+                    for (int c2 = 0; c2 < kPackedMaxDim; ++c2) {
+                        if (c2 >= a.d) break;
+                        xv[c2] = xn[c2];
+                        if (a.xb) a.xb[(size_t)v * a.d + c2] = __float2bfloat16_rn(xn[c2]);
                     }
                 } else {
                     atomicCAS(&a.ps->status, 0, -6 /* GEMPE_E_NUMERIC */);
