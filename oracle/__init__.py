@@ -78,6 +78,8 @@ def _load():
                                U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32, I32,
                                I32, I32, I32]),
         "orc_hist_pass": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, I32, U64, I32, I32, I32, F64, _f64p, _f64p]),
+        "orc_vertex_terms": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32, I32, I32,
+                                        I32, I32, I32, I32, I32, _i32p, _f64p, _f64p, _f64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,6 +188,29 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
                 delta=y - z[:, None] * x, abs_terms=absd,
                 partners=parts[: n_tiles * block_partners].reshape(n_tiles, block_partners)
                 if block_partners else None)
+
+
+def vertex_terms(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, query, mu=MU, max_retries=MAX_RETRIES,
+                 symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, block_partners=0, tile_vertices=128,
+                 per_slot=0):
+    """Eq. 3 for the vertices ``query`` alone (distinct ids), with the samples
+    ``epoch`` draws: rows of y, z, delta = y - z x, abs_terms and x_new in the
+    order of ``query``.  For checks at sizes where a whole epoch here is slow."""
+    n = len(row_ptr) - 1
+    x = _f64(x)
+    d = x.shape[1]
+    q = _i32(query)
+    y = np.zeros((len(q), d)); z = np.zeros(len(q)); absd = np.zeros(len(q))
+    rc = _load().orc_vertex_terms(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
+                                  max_retries, symmetric, w_formula, clamp_neg_d, block_partners, tile_vertices,
+                                  per_slot, len(q), q, y, z, absd)
+    if rc == -2:
+        raise ValueError("query ids must be distinct vertices")
+    if rc != 0:
+        raise MemoryError("oracle vertex terms failed")
+    xq = x[q]
+    x_new = np.where((z >= z_min)[:, None], y / np.maximum(z, 1e-300)[:, None], xq)
+    return dict(y=y, z=z, delta=y - z[:, None] * xq, abs_terms=absd, x_new=x_new)
 
 
 def edge_terms(row_ptr, col_idx, x, sigma, mu=MU, w_formula=0, clamp_neg_d=1, form="csr"):

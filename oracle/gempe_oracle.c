@@ -29,6 +29,8 @@
  *                          form (Fig. 4) and in the per-vertex CSR form
  *   orc_surrogate_L        sum of dl over a frozen pair list (for the
  *                          gradient identity of Eq. 3)
+ *   orc_vertex_terms       Eq. 3's sums of chosen vertices alone, with the
+ *                          samples of orc_epoch (checks at full sizes)
  *
  * Choices where the paper is silent (the "readings"):
  *   - negative samples are drawn per vertex, k per vertex per epoch, with a
@@ -541,6 +543,111 @@ void orc_edge_terms_csr(int32_t n, const int32_t* row_ptr, const int32_t* col_id
             orc_parabola(delta, mu, sigma, 1, w_formula, clamp_neg_d, &dd, &w);
             add_wm_term(y, z, x, d, i, j, delta, dd, w);
         }
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 3 for chosen vertices only (the per-vertex view of Fig. 4)       */
+/* ------------------------------------------------------------------ */
+/* One pair's term (Eq. 3) added to query slot q of vertex a (partner b). */
+static void add_query_term(double* y, double* z, double* absd, const double* x, int32_t d, int32_t q,
+                           int64_t a, int64_t b, double delta, double dd, double w) {
+    if (!(w > 0.0)) return;
+    double s = (delta != 0.0) ? dd / delta : 0.0;
+    for (int32_t c = 0; c < d; ++c)
+        y[(int64_t)q * d + c] += w * (x[b * d + c] + s * (x[a * d + c] - x[b * d + c]));
+    z[q] += w;
+    absd[q] += w * fabs(s - 1.0) * delta;
+}
+
+static void query_pair(double* y, double* z, double* absd, const double* x, int32_t d, int32_t q, int64_t a,
+                       int64_t b, int is_edge, double sigma, double mu, int32_t w_formula, int32_t clamp_neg_d) {
+    double delta = dist(x, d, a, b), dd, w;
+    orc_parabola(delta, mu, sigma, is_edge, w_formula, clamp_neg_d, &dd, &w);
+    add_query_term(y, z, absd, x, d, q, a, b, delta, dd, w);
+}
+
+/* y_v, z_v and the size of the terms of y_v - z_v x_v for the n_query
+ * distinct vertices query[], with the samples orc_epoch draws (exact
+ * membership): Eq. 3 summed over v's edges, the non-edges sampled at v, and,
+ * when symmetric, the non-edges of other anchors whose sampled partner is v
+ * (Fig. 4 updates both ends of a sampled pair).  The same sums orc_epoch
+ * forms for every vertex, in another order; at large n it costs one pass of
+ * draws instead of every pair's arithmetic.  Returns 0, -1 when out of
+ * memory, -2 for a query out of range or repeated. */
+int orc_vertex_terms(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d, const double* x,
+                     double sigma, double mu, int32_t epoch, uint64_t seed, int32_t k, int32_t max_retries,
+                     int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d, int32_t block_P, int32_t block_T,
+                     int32_t per_slot, int32_t n_query, const int32_t* query, double* y, double* z,
+                     double* absd) {
+    if (block_P > 0) { k = 0; per_slot = 0; }
+    int32_t* qi = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t cap = k > 0 ? k : 1;
+    for (int32_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] - row_ptr[i] > cap) cap = row_ptr[i + 1] - row_ptr[i];
+    if (block_P > cap) cap = block_P;
+    int32_t* smp = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
+    if (!qi || !smp) { free(qi); free(smp); return -1; }
+    for (int32_t i = 0; i < n; ++i) qi[i] = -1;
+    for (int32_t q = 0; q < n_query; ++q) {
+        if (query[q] < 0 || query[q] >= n || qi[query[q]] >= 0) { free(qi); free(smp); return -2; }
+        qi[query[q]] = q;
+    }
+    memset(y, 0, sizeof(double) * (size_t)n_query * d);
+    memset(z, 0, sizeof(double) * (size_t)n_query);
+    memset(absd, 0, sizeof(double) * (size_t)n_query);
+    /* v's edges and the non-edges anchored at v */
+    for (int32_t q = 0; q < n_query; ++q) {
+        int32_t v = query[q];
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+            query_pair(y, z, absd, x, d, q, v, col_idx[e], 1, sigma, mu, w_formula, clamp_neg_d);
+        int32_t kv = 0;
+        if (block_P > 0) {
+            orc_block_partners(n, v / block_T, epoch, seed, block_P, smp);
+            for (int32_t p = 0; p < block_P; ++p)
+                if (smp[p] == v || orc_is_edge(row_ptr, col_idx, v, smp[p])) smp[p] = -1;   /* masked */
+            kv = block_P;
+        } else if (per_slot) {
+            sample_slots(row_ptr, col_idx, n, v, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL);
+            kv = row_ptr[v + 1] - row_ptr[v];
+        } else {
+            sample_vertex(row_ptr, col_idx, n, v, epoch, seed, 0x0B000000u, k, max_retries, smp, NULL, NULL);
+            kv = k;
+        }
+        for (int32_t t = 0; t < kv; ++t)
+            if (smp[t] >= 0) query_pair(y, z, absd, x, d, q, v, smp[t], 0, sigma, mu, w_formula, clamp_neg_d);
+    }
+    /* the non-edges of every anchor i whose partner is a queried vertex */
+    if (symmetric) {
+        if (block_P > 0) {
+            int32_t n_tiles = (n + block_T - 1) / block_T;
+            for (int32_t tile = 0; tile < n_tiles; ++tile) {
+                orc_block_partners(n, tile, epoch, seed, block_P, smp);
+                for (int32_t p = 0; p < block_P; ++p) {
+                    int32_t g = smp[p], q = qi[g];
+                    if (q < 0) continue;
+                    for (int32_t i = tile * block_T; i < n && i < (tile + 1) * block_T; ++i)
+                        if (g != i && !orc_is_edge(row_ptr, col_idx, i, g))
+                            query_pair(y, z, absd, x, d, q, g, i, 0, sigma, mu, w_formula, clamp_neg_d);
+                }
+            }
+        } else {
+            for (int32_t i = 0; i < n; ++i) {
+                int32_t ki = per_slot ? row_ptr[i + 1] - row_ptr[i] : k;
+                if (per_slot)
+                    sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL);
+                else
+                    sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp, NULL,
+                                  NULL);
+                for (int32_t t = 0; t < ki; ++t) {
+                    if (smp[t] < 0 || qi[smp[t]] < 0) continue;
+                    query_pair(y, z, absd, x, d, qi[smp[t]], smp[t], i, 0, sigma, mu, w_formula, clamp_neg_d);
+                }
+            }
+        }
+    }
+    free(qi);
+    free(smp);
+    return 0;
 }
 
 /* Sum of dl over all undirected edges and over a list of sampled non-edges

@@ -611,3 +611,34 @@ def test_bytemap_membership(oracle_mod, sbm_small):
     _, ab2 = oracle_mod.bytemap_addr(n, 33, 2, 8, [[0, 1]])
     _, ab3 = oracle_mod.bytemap_addr(n, 33, 3, 8, [[0, 1]])
     assert ab2 != ab3
+
+
+@pytest.mark.parametrize("form", [dict(k=5), dict(k=5, symmetric=0), dict(k=3, per_slot=1),
+                                  dict(k=0, block_partners=64, tile_vertices=128),
+                                  dict(k=0, block_partners=16, tile_vertices=128, symmetric=0)],
+                         ids=["per-vertex", "per-vertex-anchor-only", "per-slot", "block", "block-anchor-only"])
+def test_vertex_terms_equal_whole_epoch(oracle_mod, sbm_1000, form):
+    """Eq. 3 for chosen vertices alone (the full-size checks' reference)
+    gives each chosen vertex the sums the whole epoch gives it: its edges,
+    the non-edges sampled at it, and (symmetric) the non-edges whose sampled
+    partner it is.  A dropped or doubled pair, a partner term sent to the
+    anchor, or a mask missed changes y, z or the term sizes of some vertex."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    n = len(rp) - 1
+    x = np.random.default_rng(31).normal(size=(n, 3)) * 1.1
+    kw = dict(form)
+    k = kw.pop("k")
+    full = oracle_mod.epoch(rp, ci, x, 0.9, 6, 777, k, **kw)
+    rng = np.random.default_rng(5)
+    query = np.concatenate([[0, n - 1, int(np.argmax(np.diff(rp)))],
+                            rng.choice(np.arange(1, n - 1), 60, replace=False)])
+    query = np.unique(query)
+    part = oracle_mod.vertex_terms(rp, ci, x, 0.9, 6, 777, k, query, **kw)
+    np.testing.assert_allclose(part["y"], full["y"][query], rtol=1e-10, atol=1e-12 * float(np.abs(full["y"]).max()))
+    np.testing.assert_allclose(part["z"], full["z"][query], rtol=1e-12)
+    np.testing.assert_allclose(part["abs_terms"], full["abs_terms"][query], rtol=1e-12)
+    np.testing.assert_allclose(part["delta"], full["delta"][query], rtol=0,
+                               atol=1e-10 * float(full["abs_terms"].max()))
+    np.testing.assert_allclose(part["x_new"], full["x_new"][query], rtol=1e-10, atol=1e-12)
+    with pytest.raises(ValueError):
+        oracle_mod.vertex_terms(rp, ci, x, 0.9, 6, 777, k, [3, 3], **kw)
