@@ -224,9 +224,14 @@ gempe_status gempe_loss(gempe_ctx* ctx, double* out_pe_bits, float* out_sigma);
 gempe_status gempe_loss_exact(gempe_ctx* ctx, int32_t fit_sigma, double* out_pe_bits, float* out_sigma);
 
 /* Slope fit of Sec. III.F on a given histogram (host float[2*B], edge bins
- * then non-edge bins) on the GPU: bisection of dPE/dsigma = 0 in log sigma
- * on [1e-3, 1e3]; without a sign change the end with the lower entropy.
- * cuda_stream may be NULL.  Synchronises. */
+ * then non-edge bins, B = bins in [16, 4096], values at the bin centres of
+ * [0, hist_max)) on the GPU: the zero of dPE/dsigma in log sigma on
+ * [1e-3, 1e3] that the paper's bisection finds, reached by Newton steps from
+ * sigma = 1 with a bracketed search (Newton inside the bracket, else
+ * Illinois regula falsi) as the fallback; without a sign change the bracket
+ * end with the lower entropy.  cuda_stream may be NULL.  Synchronises.
+ * GEMPE_E_INVALID_ARG for null pointers, bins out of range, hist_max <= 0
+ * or a non-finite mu. */
 gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_max, float mu,
                              void* cuda_stream, float* out_sigma);
 
@@ -244,6 +249,8 @@ gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_ma
 gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float hist_max, float mu,
                                     void* cuda_stream, float* out_sigma);
 
+/* Counters and state of the context (gempe_stats_t), read from the device
+ * after the context's queued work.  Synchronises. */
 gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
 
 /* Launch shape of the context's pair sweep (what the autotuner chooses):
