@@ -642,3 +642,30 @@ def test_vertex_terms_equal_whole_epoch(oracle_mod, sbm_1000, form):
     np.testing.assert_allclose(part["x_new"], full["x_new"][query], rtol=1e-10, atol=1e-12)
     with pytest.raises(ValueError):
         oracle_mod.vertex_terms(rp, ci, x, 0.9, 6, 777, k, [3, 3], **kw)
+
+
+def test_run_resumes_and_refits_on_cadence(oracle_mod, sbm_small):
+    """Fig. 4 iterated: a run of 6 epochs equals 4 epochs then 2 more resumed
+    from the reached state (the epoch counter keys the draws, so a wrong
+    counter on resume changes the samples); sigma stays at sigma0 with
+    sigma_every = 0 and is refitted only after every sigma_every-th epoch
+    (Sec. III.F's fixed cadence)."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    x0 = oracle_mod.init_positions(n, 2, 99).astype(np.float64)
+    x6, s6, st6 = oracle_mod.run(rp, ci, x0, 1.0, 6, 99, 4)
+    x4, s4, st4 = oracle_mod.run(rp, ci, x0, 1.0, 4, 99, 4)
+    x6b, s6b, st2 = oracle_mod.run(rp, ci, x4, s4, 2, 99, 4, epoch0=4)
+    np.testing.assert_array_equal(x6b, x6)
+    assert s6b == s6
+    assert st4["accepted"] + st2["accepted"] == st6["accepted"]
+    # resuming with the wrong epoch counter draws other samples
+    x6c, _, _ = oracle_mod.run(rp, ci, x4, s4, 2, 99, 4, epoch0=0)
+    assert np.abs(x6c - x6).max() > 1e-6
+    # fixed sigma
+    _, s_fixed, _ = oracle_mod.run(rp, ci, x0, 1.0, 3, 99, 4, sigma_every=0)
+    assert s_fixed == 1.0
+    # cadence 2: no refit after epoch 1, a refit after epoch 2
+    _, s_one, _ = oracle_mod.run(rp, ci, x0, 1.0, 1, 99, 4, sigma_every=2)
+    _, s_two, _ = oracle_mod.run(rp, ci, x0, 1.0, 2, 99, 4, sigma_every=2)
+    assert s_one == 1.0 and s_two != 1.0
