@@ -186,6 +186,32 @@ gempe_status gempe_set_positions(gempe_ctx* ctx, const float* host_x, size_t cou
 gempe_status gempe_set_state(gempe_ctx* ctx, float sigma, int32_t epoch);
 gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
 
+/* Checkpoint of a context between epochs (not between gempe_sweep and
+ * gempe_update), so that a run of Fig. 4 can stop and resume: the FP32
+ * positions, sigma, the epoch counter and the sampler statistics, with the
+ * graph's n, d and nnz and the parameters that key the draws (seed,
+ * neg_per_vertex, max_retries, sampling, block_partners, tile_vertices,
+ * membership and, with the byte map, bytemap_log2 and rename_every).  A
+ * context created from the same graph with those parameters and loaded from
+ * the checkpoint continues as the saved one would: the same samples, sigma
+ * and statistics, positions up to the order of FP32 atomic additions.  The
+ * graph itself is checked only by n and nnz; other parameters (mu,
+ * sigma_every, precision, ...) may differ and take effect from the load on.
+ * Plain little-endian bytes: a 136-byte header, then float[n*d].
+ *
+ * gempe_save: buf NULL -> *len = the bytes needed, GEMPE_OK.  Otherwise *len
+ * must be at least that (else GEMPE_E_INVALID_ARG, *len set to the size
+ * needed); writes the checkpoint and sets *len to its size.  Synchronises;
+ * reports a pending device failure (GEMPE_E_NUMERIC) like gempe_positions.
+ * gempe_load: GEMPE_E_INVALID_ARG when buf is not a checkpoint of this
+ * format, is truncated, belongs to another graph size or other sampling
+ * parameters (the message says which), or holds a non-finite position or
+ * sigma; the context is unchanged then.  On success it redraws the samples
+ * of the saved epoch (they depend only on the graph and the epoch) and
+ * restores the statistics as saved.  Synchronises. */
+gempe_status gempe_save(gempe_ctx* ctx, void* buf, size_t* len);
+gempe_status gempe_load(gempe_ctx* ctx, const void* buf, size_t len);
+
 /* Copy the accumulators after gempe_sweep to host float[n*(d+1)]: for each
  * vertex d values of y_i - z_i x_i (the Eq. 3 numerator minus z_i x_i; the
  * update is x_i + that / z_i = y_i / z_i), then z_i.  Synchronises. */

@@ -157,6 +157,8 @@ def load(build: bool = True):
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
+        "gempe_save": (st, [vp, vp, P(sz)]),
+        "gempe_load": (st, [vp, vp, sz]),
         "gempe_set_shape": (st, [vp, P(i32)]),
         "gempe_get_shape": (st, [vp, P(i32)]),
         "gempe_last_error": (ctypes.c_char_p, []),
@@ -327,6 +329,21 @@ def gempe_get_state(ctx: _Ctx):
     e = ctypes.c_int32()
     _check(load().gempe_get_state(ctx.handle, ctypes.byref(s), ctypes.byref(e)))
     return s.value, e.value
+
+
+def gempe_save(ctx: _Ctx) -> bytes:
+    """Checkpoint of the context between epochs (positions, sigma, epoch, sampler statistics)."""
+    n = ctypes.c_size_t(0)
+    _check(load().gempe_save(ctx.handle, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().gempe_save(ctx.handle, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def gempe_load(ctx: _Ctx, data: bytes) -> None:
+    """Resume the context from a gempe_save checkpoint of the same graph and sampling parameters."""
+    b = bytes(data)
+    _check(load().gempe_load(ctx.handle, b, len(b)))
 
 
 def gempe_accumulators(ctx: _Ctx):

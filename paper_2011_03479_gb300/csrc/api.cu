@@ -323,6 +323,159 @@ GEMPE_API gempe_status gempe_get_state(gempe_ctx* c, float* sigma, int32_t* epoc
     return GEMPE_OK;
 }
 
+namespace {
+
+// Checkpoint layout: this header, then the FP32 positions [n][d].  Plain
+// fixed-width fields (8-byte aligned, no padding), written and read with
+// memcpy.
+struct CheckpointHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t n, d;
+    int64_t nnz;
+    uint64_t seed;
+    int32_t k, max_retries, sampling, block_partners;
+    int32_t tile_vertices, membership, bytemap_log2, rename_every;
+    float sigma;
+    int32_t epoch, sigma_iters, reserved;
+    uint64_t accepted, rejected, exhausted, draws, used, false_pos;
+};
+static_assert(sizeof(CheckpointHeader) == 136, "checkpoint header layout");
+
+constexpr char kCheckpointMagic[8] = {'G', 'E', 'M', 'P', 'E', 'C', 'K', '\x01'};
+constexpr uint32_t kCheckpointVersion = 1;
+
+size_t checkpoint_bytes(const gempe_ctx* c) {
+    return sizeof(CheckpointHeader) + sizeof(float) * (size_t)c->n * c->pk->d;
+}
+
+// The checkpoint belongs to a graph of this size and to the parameters that
+// key this context's draws.
+gempe_status checkpoint_matches(const CheckpointHeader& h, const gempe_ctx* c) {
+    const Pack& pk = *c->pk;
+    const gempe_params& p = pk.p;
+    if (h.n != c->n || h.d != pk.d || h.nnz != pk.nnz[0])
+        return fail(GEMPE_E_INVALID_ARG, "checkpoint of another graph: n, d or nnz differ");
+    if (h.seed != p.seed || h.k != p.neg_per_vertex || h.max_retries != p.max_retries || h.sampling != p.sampling ||
+        h.block_partners != p.block_partners || h.tile_vertices != p.tile_vertices || h.membership != p.membership)
+        return fail(GEMPE_E_INVALID_ARG,
+                    "checkpoint of other sampling parameters: seed, neg_per_vertex, max_retries, sampling, "
+                    "block_partners, tile_vertices or membership differ");
+    if (p.membership == 1 && (h.bytemap_log2 != p.bytemap_log2 || h.rename_every != p.rename_every))
+        return fail(GEMPE_E_INVALID_ARG, "checkpoint of another byte map: bytemap_log2 or rename_every differ");
+    return GEMPE_OK;
+}
+
+}  // namespace
+
+GEMPE_API gempe_status gempe_save(gempe_ctx* c, void* buf, size_t* len) {
+    if (!c || !len) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    const size_t need = checkpoint_bytes(c);
+    if (!buf) {
+        *len = need;
+        return GEMPE_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return fail(GEMPE_E_INVALID_ARG, "checkpoint buffer too small (*len now holds the size needed)");
+    }
+    Pack& pk = *c->pk;
+    if (pk.swept) return fail(GEMPE_E_INVALID_ARG, "gempe_save after gempe_sweep: call gempe_update first");
+    CK(cudaStreamSynchronize(pk.side), "synchronize");
+    gempe_status rc;
+    const GraphState g = read_graph_state(c, &rc);   // after the context's queued work
+    if (rc != GEMPE_OK) return rc;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    CK(cudaMemcpyAsync(out + sizeof(CheckpointHeader), pk.x, sizeof(float) * (size_t)c->n * pk.d,
+                       cudaMemcpyDeviceToHost, c->stream),
+       "copy x");
+    rc = pk.read_status();   // synchronises
+    if (rc != GEMPE_OK) return rc;
+    CheckpointHeader h{};
+    std::memcpy(h.magic, kCheckpointMagic, sizeof(h.magic));
+    h.version = kCheckpointVersion;
+    h.header_bytes = (uint32_t)sizeof(CheckpointHeader);
+    h.n = c->n;
+    h.d = pk.d;
+    h.nnz = pk.nnz[0];
+    h.seed = pk.p.seed;
+    h.k = pk.p.neg_per_vertex;
+    h.max_retries = pk.p.max_retries;
+    h.sampling = pk.p.sampling;
+    h.block_partners = pk.p.block_partners;
+    h.tile_vertices = pk.p.tile_vertices;
+    h.membership = pk.p.membership;
+    h.bytemap_log2 = pk.p.bytemap_log2;
+    h.rename_every = pk.p.rename_every;
+    h.sigma = g.sigma;
+    h.epoch = g.epoch;
+    h.sigma_iters = g.sigma_iters;
+    h.accepted = g.accepted;
+    h.rejected = g.rejected;
+    h.exhausted = g.exhausted;
+    h.draws = g.draws;
+    h.used = g.used;
+    h.false_pos = g.false_pos;
+    std::memcpy(out, &h, sizeof(h));
+    *len = need;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_load(gempe_ctx* c, const void* buf, size_t len) {
+    if (!c || !buf) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    CheckpointHeader h;
+    if (len < sizeof(h)) return fail(GEMPE_E_INVALID_ARG, "not a GEMPE checkpoint: too short");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kCheckpointMagic, sizeof(h.magic)) != 0 || h.version != kCheckpointVersion ||
+        h.header_bytes != sizeof(CheckpointHeader))
+        return fail(GEMPE_E_INVALID_ARG, "not a GEMPE checkpoint of this format");
+    gempe_status s = checkpoint_matches(h, c);
+    if (s != GEMPE_OK) return s;
+    if (len < checkpoint_bytes(c)) return fail(GEMPE_E_INVALID_ARG, "checkpoint truncated");
+    if (!(h.sigma > 0.0f) || !std::isfinite(h.sigma) || h.epoch < 0)
+        return fail(GEMPE_E_INVALID_ARG, "checkpoint holds an invalid sigma or epoch");
+    Pack& pk = *c->pk;
+    if (pk.swept) return fail(GEMPE_E_INVALID_ARG, "gempe_load after gempe_sweep: call gempe_update first");
+    const size_t count = (size_t)c->n * pk.d;
+    std::vector<float> x(count);
+    std::memcpy(x.data(), static_cast<const unsigned char*>(buf) + sizeof(h), sizeof(float) * count);
+    for (size_t q = 0; q < count; ++q)
+        if (!std::isfinite(x[q])) return fail(GEMPE_E_INVALID_ARG, "checkpoint holds non-finite positions");
+    // positions and their BF16 shadow, as gempe_set_positions
+    CK(cudaStreamSynchronize(pk.side), "synchronize");
+    CK(cudaMemcpyAsync(pk.x, x.data(), sizeof(float) * count, cudaMemcpyHostToDevice, c->stream), "copy x");
+    if (pk.xb) CK(launch_to_bf16(pk.x, pk.xb, (long long)count, c->stream), "BF16 shadow");
+    // sigma and the epoch, as gempe_set_state
+    gempe_status rc;
+    GraphState g = read_graph_state(c, &rc);   // synchronises
+    if (rc != GEMPE_OK) return rc;
+    g.sigma = h.sigma;
+    g.epoch = h.epoch;
+    g.sample_epoch = h.epoch;
+    g.sigma_iters = h.sigma_iters;
+    pk.primed = false;
+    if (pk.block)
+        CK(cudaMemsetAsync(pk.block_mask, 0, sizeof(unsigned long long) * 2 * (size_t)pk.rows, c->stream),
+           "clear masks");
+    CK(cudaMemsetAsync(&pk.ps->sample_done, 0, sizeof(unsigned int), c->stream), "clear sampler count");
+    CK(cudaMemcpyAsync(pk.gst, &g, sizeof(GraphState), cudaMemcpyHostToDevice, c->stream), "write state");
+    // the saved context had drawn the samples of its epoch already (the
+    // sampler runs one epoch ahead); draw them again, then restore the
+    // statistics as saved, which count those draws once
+    s = pk.prime();
+    if (s != GEMPE_OK) return s;
+    g = read_graph_state(c, &rc);   // synchronises
+    if (rc != GEMPE_OK) return rc;
+    g.accepted = h.accepted;
+    g.rejected = h.rejected;
+    g.exhausted = h.exhausted;
+    g.draws = h.draws;
+    g.used = h.used;
+    g.false_pos = h.false_pos;
+    CK(cudaMemcpyAsync(pk.gst, &g, sizeof(GraphState), cudaMemcpyHostToDevice, c->stream), "write state");
+    return pk.read_status();   // synchronises
+}
+
 GEMPE_API gempe_status gempe_accumulators(gempe_ctx* c, float* host_out, size_t count) {
     if (!c || !host_out) return fail(GEMPE_E_INVALID_ARG, "null argument");
     Pack& pk = *c->pk;

@@ -182,3 +182,15 @@ def test_job_bytes_formula():
     assert B.gempe_job_bytes(n, nnz, 32, pm) - B.gempe_job_bytes(n, nnz, 32, p) == 1 << 20
     pa = B.gempe_default_params(neg_per_vertex=10, membership=1)
     assert B.gempe_job_bytes(n, nnz, 32, pa) - B.gempe_job_bytes(n, nnz, 32, p) == 1 << 28
+
+
+def test_checkpoint_calls_reject_null_arguments():
+    """gempe_save / gempe_load check their arguments before touching a device."""
+    import ctypes
+    from paper_2011_03479_gb300 import binding
+    lib = binding.load()
+    n = ctypes.c_size_t(0)
+    assert lib.gempe_save(None, None, ctypes.byref(n)) == -1
+    assert lib.gempe_save(None, None, None) == -1
+    assert lib.gempe_load(None, b"GEMPECK", 7) == -1
+    assert lib.gempe_load(None, None, 0) == -1
