@@ -1,0 +1,33 @@
+"""Host-side logic of bench.py that needs no GPU."""
+import os
+import shutil
+
+import bench
+
+
+def test_kernel_hash_ignores_the_abi_front_ends(tmp_path):
+    """The profile summaries' DRAM traffic is keyed by a hash of the sources
+    that define the kernels and their launch shapes: editing a C-ABI front
+    end keeps it, editing a kernel or the launch configuration changes it."""
+    src = os.path.join(bench.ROOT, "paper_2011_03479_gb300", "csrc")
+    dst = tmp_path / "csrc"
+    shutil.copytree(src, dst)
+    h0 = bench.kernel_source_hash(str(dst))
+    assert h0 == bench.kernel_source_hash()
+    for fn in sorted(bench.ABI_FRONT_ENDS):
+        with open(dst / fn, "a") as f:
+            f.write("\n// edited\n")
+    assert bench.kernel_source_hash(str(dst)) == h0
+    for fn in ("kernels.cu", "pack.cu"):
+        with open(dst / fn, "a") as f:
+            f.write("\n// edited\n")
+        h1 = bench.kernel_source_hash(str(dst))
+        assert h1 != h0
+        h0 = h1
+
+
+def test_abi_front_ends_hold_no_device_code():
+    src = os.path.join(bench.ROOT, "paper_2011_03479_gb300", "csrc")
+    for fn in bench.ABI_FRONT_ENDS:
+        text = open(os.path.join(src, fn)).read()
+        assert "__global__" not in text and "__device__" not in text and "<<<" not in text, fn
