@@ -265,7 +265,8 @@ def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | Non
     _check(load().gempe_create_device(ctypes.c_void_p(d_row_ptr.data_ptr()),
                                       ctypes.c_void_p(d_col_idx.data_ptr() if nnz else None), n, nnz, d,
                                       ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
-    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex)
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex,
+                per_slot=(p.sampling == 1), nnz=nnz)
 
 
 def gempe_destroy(ctx: _Ctx) -> None:
