@@ -211,7 +211,8 @@ def cpu_baseline(w, budget_s=12.0):
     epochs = max(1, min(200, int(budget_s / max(t1, 1e-3))))
     p, t, _ = oracle_epochs(w, epochs)
     return {"value": p / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{epochs} epochs of {w['name']} from the initial positions, FP64 oracle, one thread"}
+            "sample": f"{epochs} epoch{'s' if epochs != 1 else ''} of {w['name']} from the initial positions, "
+                      "FP64 oracle, one thread"}
 
 
 # ---------------------------------------------------------------------------
