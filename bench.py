@@ -83,7 +83,13 @@ def oriented_degrees(row_ptr, col_idx):
     return np.bincount(rows[keep], minlength=len(deg))
 
 
-def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted, oriented=False):
+def position_row_bytes(d, precision):
+    """Bytes of the position row the pair arithmetic reads: the BF16 shadow
+    (2d) in the precision form (d >= 8), else the FP32 positions (4d)."""
+    return 2 * d if precision and d >= 8 else 4 * d
+
+
+def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted, oriented=False, row_bytes=None):
     """Bytes one sweep launch must move at least, each random gather paid once
     at its minimum size (no reuse): CSR streamed once, work units, the sample
     slots, own row, a read-modify-write of every own accumulator row, the
@@ -91,8 +97,9 @@ def sweep_algorithmic_bytes(n, nnz, d, k, n_units, accepted, oriented=False):
     accepted sample, and per edge slot the neighbour's row -- once per CSR
     slot when each endpoint sums its own edges, or (oriented form) once per
     undirected edge plus the read-modify-write of the other endpoint's
-    accumulator row, with the full row offsets read for the degrees."""
-    row = 4 * d
+    accumulator row, with the full row offsets read for the degrees.  A row
+    is row_bytes (position_row_bytes: 4d FP32, 2d for BF16 positions)."""
+    row = 4 * d if row_bytes is None else row_bytes
     acc_row = 4 * (((d + 1) + 3) // 4 * 4)
     common = 16 * n_units + 4 * n * k + n * row + n * 2 * acc_row + accepted * (row + 2 * acc_row)
     if oriented:
@@ -421,7 +428,8 @@ def run_gempe(args):
     oriented = d <= 4 and not block and not form.get("sampling")
     units = work_units(rp, k, d, out_degrees=oriented_degrees(rp, ci) if oriented else None)
     bytes_per_sweep = sweep_algorithmic_bytes(n, nnz, d, 0 if block else k, units,
-                                              0 if block else accepted / args.steps, oriented=oriented)
+                                              0 if block else accepted / args.steps, oriented=oriented,
+                                              row_bytes=position_row_bytes(d, form.get("precision")))
     if block and form.get("precision") and d in (16, 32, 64):
         bytes_per_sweep += tile_algorithmic_bytes(n, d, (n + 127) // 128)
     sweep_s = statistics.mean(sweep_ms) / 1e3
@@ -584,7 +592,8 @@ def run_batch(args):
         oriented = d <= 4 and sh.get("kernel", 0) == 0
         units = work_units(rp, k, d, edge_chunk=sh["unit"], unit_pairs=sh["unit"],
                            out_degrees=oriented_degrees(rp, ci) if oriented else None, kernel=sh.get("kernel", 0))
-        byts += sweep_algorithmic_bytes(n, len(ci), d, k, units, acc_per_epoch * (n / n_tot), oriented=oriented)
+        byts += sweep_algorithmic_bytes(n, len(ci), d, k, units, acc_per_epoch * (n / n_tot), oriented=oriented,
+                                        row_bytes=position_row_bytes(d, form.get("precision")))
     step_s = statistics.mean(step_ms) / 1e3
     achieved = byts / step_s / 1e9
     line = {
