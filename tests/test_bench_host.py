@@ -31,3 +31,16 @@ def test_abi_front_ends_hold_no_device_code():
     for fn in bench.ABI_FRONT_ENDS:
         text = open(os.path.join(src, fn)).read()
         assert "__global__" not in text and "__device__" not in text and "<<<" not in text, fn
+
+
+def test_byte_model_uses_the_rows_the_form_reads():
+    """The sweep's algorithmic bytes charge a position row at the size the
+    form reads: BF16 (2d) for the precision form at d >= 8, FP32 (4d)
+    otherwise; with no samples the two differ by exactly the own rows and
+    one neighbour row per CSR slot."""
+    assert bench.position_row_bytes(64, 1) == 128 and bench.position_row_bytes(64, 0) == 256
+    assert bench.position_row_bytes(2, 1) == 8      # d <= 4 stays FP32
+    n, nnz, d = 1000, 16000, 64
+    b16 = bench.sweep_algorithmic_bytes(n, nnz, d, 0, 300, 0, row_bytes=bench.position_row_bytes(d, 1))
+    b32 = bench.sweep_algorithmic_bytes(n, nnz, d, 0, 300, 0)
+    assert b32 - b16 == (n + nnz) * 2 * d
