@@ -151,6 +151,8 @@ gempe_status gempe_create_device(const int32_t* d_row_ptr, const int32_t* d_col_
                                  int64_t nnz, int32_t d, const gempe_params* p, void* cuda_stream,
                                  gempe_ctx** out);
 
+/* Release the context and all device memory it allocated (waits for its
+ * queued work first).  NULL is ignored. */
 void gempe_destroy(gempe_ctx* ctx);
 
 /* Run `iters` full epochs (Fig. 4): sweep + position update + sigma refit.
@@ -326,6 +328,7 @@ gempe_status gempe_batch_step(gempe_batch* b, int32_t iters);
 gempe_status gempe_batch_positions(gempe_batch* b, int32_t graph, float* host_out, size_t count);
 /* Sampled predictive entropy of graph `graph` (as gempe_loss). */
 gempe_status gempe_batch_loss(gempe_batch* b, int32_t graph, double* out_pe_bits, float* out_sigma);
+/* Statistics of graph `graph` (as gempe_stats).  Synchronises. */
 gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_stats_t* out);
 /* Launch shape of the pack holding dimension d: out[0] unit pair budget
  * (packed units, d <= 4) or CSR slots per unit (one lane group per vertex),
@@ -383,6 +386,9 @@ void gempe_server_destroy(gempe_server* s);
  * on the host before admission, the symmetry on the device when the job
  * starts). */
 gempe_status gempe_server_submit(gempe_server* s, const gempe_job_desc* job, uint64_t* job_id);
+/* State of a job without waiting.  GEMPE_E_INVALID_ARG for an unknown or
+ * already released job id; for a failed job, *info is filled and its
+ * gempe_status is returned (message in gempe_last_error). */
 gempe_status gempe_server_poll(gempe_server* s, uint64_t job_id, gempe_job_info* info);
 /* Block until the job is done or failed, at most timeout_ms (GEMPE_E_TIMEOUT). */
 gempe_status gempe_server_wait(gempe_server* s, uint64_t job_id, int32_t timeout_ms, gempe_job_info* info);
