@@ -44,3 +44,25 @@ def test_byte_model_uses_the_rows_the_form_reads():
     b16 = bench.sweep_algorithmic_bytes(n, nnz, d, 0, 300, 0, row_bytes=bench.position_row_bytes(d, 1))
     b32 = bench.sweep_algorithmic_bytes(n, nnz, d, 0, 300, 0)
     assert b32 - b16 == (n + nnz) * 2 * d
+
+
+def test_clock_sampler_reads_clocks_and_reasons(tmp_path, monkeypatch):
+    """The clocks record beside every bench line: median SM clock under load,
+    the maximum, and every throttle reason seen active, parsed from
+    nvidia-smi's CSV (a stand-in script prints three samples here)."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1965, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2070, 2070, 960.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ.get('PATH', '')}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    deadline = time.time() + 10
+    while time.time() < deadline and sum(1 for _ in open(cs.path)) < 3:
+        time.sleep(0.05)
+    rec = cs.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
