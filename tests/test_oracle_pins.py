@@ -669,3 +669,15 @@ def test_run_resumes_and_refits_on_cadence(oracle_mod, sbm_small):
     _, s_one, _ = oracle_mod.run(rp, ci, x0, 1.0, 1, 99, 4, sigma_every=2)
     _, s_two, _ = oracle_mod.run(rp, ci, x0, 1.0, 2, 99, 4, sigma_every=2)
     assert s_one == 1.0 and s_two != 1.0
+
+
+def test_golden_closed_forms_reproduce():
+    """The stored closed-form values are what the committed generator computes
+    from Eq. 4 / Eq. 5 with Python's math module (no oracle, no engine)."""
+    import importlib.util
+    path = os.path.join(HERE, "golden", "make_parabola_closed_forms.py")
+    spec = importlib.util.spec_from_file_location("make_parabola_closed_forms", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(os.path.join(HERE, "golden", "parabola_closed_forms.txt")) as f:
+        assert f.read() == gen.text()
