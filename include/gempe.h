@@ -193,21 +193,23 @@ gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
  * positions, sigma, the epoch counter and the sampler statistics, with the
  * graph's n, d and nnz and the parameters that key the draws (seed,
  * neg_per_vertex, max_retries, sampling, block_partners, tile_vertices,
- * membership and, with the byte map, bytemap_log2 and rename_every).  A
- * context created from the same graph with those parameters and loaded from
- * the checkpoint continues as the saved one would: the same samples, sigma
- * and statistics, positions up to the order of FP32 atomic additions.  The
- * graph itself is checked only by n and nnz; other parameters (mu,
- * sigma_every, precision, ...) may differ and take effect from the load on.
- * Plain little-endian bytes: a 136-byte header, then float[n*d].
+ * membership and, with the byte map, bytemap_log2 and rename_every) and the
+ * parameters of the run's arithmetic (mu, hist_max, z_min, hist_bins,
+ * sigma_every, sigma_source, precision, symmetric_neg, w_formula,
+ * clamp_neg_d).  A context created from the same graph with those parameters
+ * and loaded from the checkpoint continues as the saved one would: the same
+ * samples, sigma and statistics, positions up to the order of FP32 atomic
+ * additions.  The graph itself is checked only by n and nnz; the remaining
+ * parameters (autotune, the allocator) do not change the run.
+ * Plain little-endian bytes: a 176-byte header, then float[n*d].
  *
  * gempe_save: buf NULL -> *len = the bytes needed, GEMPE_OK.  Otherwise *len
  * must be at least that (else GEMPE_E_INVALID_ARG, *len set to the size
  * needed); writes the checkpoint and sets *len to its size.  Synchronises;
  * reports a pending device failure (GEMPE_E_NUMERIC) like gempe_positions.
  * gempe_load: GEMPE_E_INVALID_ARG when buf is not a checkpoint of this
- * format, is truncated, belongs to another graph size or other sampling
- * parameters (the message says which), or holds a non-finite position or
+ * format, is truncated, belongs to another graph size, other sampling
+ * parameters or another run's arithmetic (the message says which), or holds a non-finite position or
  * sigma; the context is unchanged then.  On success it redraws the samples
  * of the saved epoch (they depend only on the graph and the epoch) and
  * restores the statistics as saved.  Synchronises. */
@@ -276,6 +278,16 @@ gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_ma
  * capture.  All calls share the array: calls that overlap on the GPU race. */
 gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float hist_max, float mu,
                                     void* cuda_stream, float* out_sigma);
+
+/* Test hook for the bounded device waits of the tensor-core tile kernel
+ * (failure detection without a GPU fault; the paper has no counterpart).
+ * Launches one CTA set up like a tile CTA (256 TMEM columns allocated, an
+ * mbarrier initialised) that waits, with poll_limit polls (1 .. 2^22), for a
+ * barrier phase nothing completes -- no MMA is issued -- and then takes the
+ * tile kernel's give-up path.  *out_status receives the status it recorded
+ * (GEMPE_E_TIMEOUT when the wait ran out), *out_freed 1 once it released its
+ * TMEM.  Allocates 8 bytes of device memory; synchronises the device. */
+gempe_status gempe_test_tile_wait(int32_t poll_limit, int32_t* out_status, int32_t* out_freed);
 
 /* Counters and state of the context (gempe_stats_t), read from the device
  * after the context's queued work.  Synchronises. */

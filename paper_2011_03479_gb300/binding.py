@@ -156,6 +156,7 @@ def load(build: bool = True):
         "gempe_loss_exact": (st, [vp, i32, P(ctypes.c_double), P(ctypes.c_float)]),
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
+        "gempe_test_tile_wait": (st, [i32, P(i32), P(i32)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
         "gempe_save": (st, [vp, vp, P(sz)]),
         "gempe_load": (st, [vp, vp, sz]),
@@ -405,6 +406,14 @@ def gempe_fit_sigma_static(hist_e, hist_n, hist_max: float = 12.0, mu: float = 1
     _check(load().gempe_fit_sigma_static(_ptr(h), len(h) // 2, float(hist_max), float(mu),
                                          _stream_handle(stream), ctypes.byref(out)))
     return out.value
+
+
+def gempe_test_tile_wait(poll_limit: int) -> tuple[int, int]:
+    """Test hook: one tile-shaped CTA whose bounded mbarrier wait runs out;
+    (status it recorded, 1 if it freed its TMEM)."""
+    st, fr = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().gempe_test_tile_wait(int(poll_limit), ctypes.byref(st), ctypes.byref(fr)))
+    return st.value, fr.value
 
 
 def gempe_stats(ctx: _Ctx) -> dict:

@@ -339,11 +339,15 @@ struct CheckpointHeader {
     float sigma;
     int32_t epoch, sigma_iters, reserved;
     uint64_t accepted, rejected, exhausted, draws, used, false_pos;
+    // the parameters of the run's arithmetic (version 2)
+    float mu, hist_max, z_min;
+    int32_t hist_bins, sigma_every, sigma_source, precision;
+    int32_t symmetric_neg, w_formula, clamp_neg_d;
 };
-static_assert(sizeof(CheckpointHeader) == 136, "checkpoint header layout");
+static_assert(sizeof(CheckpointHeader) == 176, "checkpoint header layout");
 
 constexpr char kCheckpointMagic[8] = {'G', 'E', 'M', 'P', 'E', 'C', 'K', '\x01'};
-constexpr uint32_t kCheckpointVersion = 1;
+constexpr uint32_t kCheckpointVersion = 2;
 
 size_t checkpoint_bytes(const gempe_ctx* c) {
     return sizeof(CheckpointHeader) + sizeof(float) * (size_t)c->n * c->pk->d;
@@ -363,6 +367,12 @@ gempe_status checkpoint_matches(const CheckpointHeader& h, const gempe_ctx* c) {
                     "block_partners, tile_vertices or membership differ");
     if (p.membership == 1 && (h.bytemap_log2 != p.bytemap_log2 || h.rename_every != p.rename_every))
         return fail(GEMPE_E_INVALID_ARG, "checkpoint of another byte map: bytemap_log2 or rename_every differ");
+    if (h.mu != p.mu || h.hist_max != p.hist_max || h.z_min != p.z_min || h.hist_bins != p.hist_bins ||
+        h.sigma_every != p.sigma_every || h.sigma_source != p.sigma_source || h.precision != p.precision ||
+        h.symmetric_neg != p.symmetric_neg || h.w_formula != p.w_formula || h.clamp_neg_d != p.clamp_neg_d)
+        return fail(GEMPE_E_INVALID_ARG,
+                    "checkpoint of another run: mu, hist_max, z_min, hist_bins, sigma_every, sigma_source, "
+                    "precision, symmetric_neg, w_formula or clamp_neg_d differ");
     return GEMPE_OK;
 }
 
@@ -416,6 +426,16 @@ GEMPE_API gempe_status gempe_save(gempe_ctx* c, void* buf, size_t* len) {
     h.draws = g.draws;
     h.used = g.used;
     h.false_pos = g.false_pos;
+    h.mu = pk.p.mu;
+    h.hist_max = pk.p.hist_max;
+    h.z_min = pk.p.z_min;
+    h.hist_bins = pk.p.hist_bins;
+    h.sigma_every = pk.p.sigma_every;
+    h.sigma_source = pk.p.sigma_source;
+    h.precision = pk.p.precision;
+    h.symmetric_neg = pk.p.symmetric_neg;
+    h.w_formula = pk.p.w_formula;
+    h.clamp_neg_d = pk.p.clamp_neg_d;
     std::memcpy(out, &h, sizeof(h));
     *len = need;
     return GEMPE_OK;
@@ -713,6 +733,22 @@ GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
     out->k = pk.k;
     out->sigma_iters = h.sigma_iters;
     out->false_pos = h.false_pos;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_test_tile_wait(int32_t poll_limit, int32_t* out_status, int32_t* out_freed) {
+    if (!out_status || !out_freed) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    if (poll_limit < 1 || poll_limit > (1 << 22)) return fail(GEMPE_E_INVALID_ARG, "poll_limit in [1, 2^22]");
+    int32_t* dv = nullptr;
+    CK(cudaMalloc((void**)&dv, 2 * sizeof(int32_t)), "alloc");
+    int32_t h[2] = {0, 0};
+    cudaError_t e = cudaMemset(dv, 0, 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = launch_tile_wait_probe(poll_limit, dv, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(h, dv, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(dv);
+    if (e != cudaSuccess) return cuda_fail(e, "tile wait probe");
+    *out_status = h[0];
+    *out_freed = h[1];
     return GEMPE_OK;
 }
 

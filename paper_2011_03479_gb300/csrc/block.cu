@@ -215,10 +215,16 @@ __device__ __forceinline__ void tc_commit(unsigned long long* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(mbar)));
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity) {
+// Bounded wait for phase `parity` of an mbarrier; false when it gave up
+// after `limit` polls.  The give-up path of the tile kernel (leave the tile
+// loop, free the TMEM, record GEMPE_E_TIMEOUT) assumes that nothing the CTA
+// committed is still running: it is meant for the hang where the arrival
+// never comes.  Were an MMA only slow, it could still write the TMEM and
+// read the shared memory the CTA gives up, so a context whose status reads
+// GEMPE_E_TIMEOUT must be destroyed, not stepped again.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity, int limit = kTileWaitLimit) {
     uint32_t done = 0;
-    for (int it = 0; it < kTileWaitLimit && !done; ++it)
+    for (int it = 0; it < limit && !done; ++it)
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity));
     return done != 0;
@@ -570,7 +576,47 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
     if (tid == 0 && s_used && home >= 0) atomicAdd(&a.gst[home].used, (unsigned long long)s_used);
 }
 
+// ---------------------------------------------------------------------------
+// k_tile_wait_probe (test only): one CTA set up like a tile CTA -- TMEM
+// allocated, mbarrier initialised -- waits for a barrier phase that nothing
+// completes (no MMA is issued, nothing committed) with `limit` polls, then
+// takes the tile kernel's give-up path: out[0] = the status it records,
+// out[1] = 1 once the TMEM is freed.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileThreads) k_tile_wait_probe(int limit, int32_t* out) {
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, w = tid >> 5;
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_slot)), "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    if (!mbar_wait(&mbar, 0u, limit)) atomicExch(&abort_flag, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) out[0] = abort_flag ? kStatusTimeout : 0;
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256));
+    __syncthreads();
+    if (tid == 0) out[1] = 1;
+}
+
 }  // namespace
+
+cudaError_t launch_tile_wait_probe(int limit, int32_t* dev_out, cudaStream_t s) {
+    k_tile_wait_probe<<<1, kTileThreads, 0, s>>>(limit, dev_out);
+    return cudaGetLastError();
+}
 
 bool tile_dim(int d) { return d == 16 || d == 32 || d == 64; }
 
@@ -591,9 +637,9 @@ size_t tile_smem_bytes(int d, int bins) {
 cudaError_t prepare_tile_kernel(int d, int bins) {
     const int smem = (int)tile_smem_bytes(d, bins);
     switch (d) {
-        case 16: return cudaFuncSetAttribute(k_tile_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 32: return cudaFuncSetAttribute(k_tile_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 64: return cudaFuncSetAttribute(k_tile_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 16: return raise_smem_limit((const void*)k_tile_tc<16>, smem);
+        case 32: return raise_smem_limit((const void*)k_tile_tc<32>, smem);
+        case 64: return raise_smem_limit((const void*)k_tile_tc<64>, smem);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -186,6 +186,12 @@ int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int 
 bool sweep_lanes_supported(int d, int lanes);
 cudaError_t launch_update(const EpochArgs& a, int grid, cudaStream_t s);
 cudaError_t prepare_update_kernels(int bins);   // shared-memory size of the slope-fit blocks
+// Raises the dynamic shared-memory limit of `func` on the current device to
+// at least `bytes`.  The limit is one per function and device, shared by
+// every context, batch and server of the process, so it is only ever raised
+// (a running maximum under a lock): a pack built with fewer histogram bins
+// never lowers the limit another pack's launches rely on.
+cudaError_t raise_smem_limit(const void* func, int bytes);
 // sigma_source 1: the separate histogram pass at the updated positions, then
 // the per-graph slope fits on it
 cudaError_t launch_hist_pass(const EpochArgs& a, cudaStream_t s);
@@ -202,6 +208,9 @@ int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm);
 bool tile_dim(int d);
 size_t tile_smem_bytes(int d, int bins);
 cudaError_t prepare_tile_kernel(int d, int bins);
+// Test only: one tile-shaped CTA whose mbarrier wait (limit polls) runs out;
+// dev_out[0] = the status it records, dev_out[1] = 1 after it freed its TMEM.
+cudaError_t launch_tile_wait_probe(int limit, int32_t* dev_out, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* x, __nv_bfloat16* xb, long long count, cudaStream_t s);
 int sampler_grid(int rows, int k, int sm_count);
 cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s);

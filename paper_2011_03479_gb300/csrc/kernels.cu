@@ -13,7 +13,10 @@
 //  k_loss          sampled predictive entropy (Eq. 2) with FP64 sums
 //  k_sample        the sampler alone (inspection)
 //  k_is_edge       membership probes (inspection)
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "device_math.cuh"
 #include "engine.cuh"
@@ -1622,8 +1625,8 @@ template <int D>
 int packed_blocks_per_sm(int bins) {
     int blocks = 0;
     const size_t smem = packed_smem_bytes(D, bins);
-    cudaFuncSetAttribute(k_sweep_packed<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_sweep_packed<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void*)k_sweep_packed<D, true>, (int)smem);
+    raise_smem_limit((const void*)k_sweep_packed<D, false>, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_packed<D, false>, kPackedThreads, smem) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -1759,11 +1762,25 @@ cudaError_t launch_loss(const EpochArgs& a, cudaStream_t s) {
     }
 }
 
+cudaError_t raise_smem_limit(const void* func, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> limit;   // (device, function) -> bytes set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int& cur = limit[std::make_pair(dev, func)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 cudaError_t prepare_update_kernels(int bins) {
     const int smem = (int)fit_smem_bytes(bins);
-    cudaError_t e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_graphs, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_smem_limit((const void*)k_update, smem);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fit_sigma, smem);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_fit_graphs, smem);
     return e;
 }
 

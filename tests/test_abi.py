@@ -194,3 +194,12 @@ def test_checkpoint_calls_reject_null_arguments():
     assert lib.gempe_save(None, None, None) == -1
     assert lib.gempe_load(None, b"GEMPECK", 7) == -1
     assert lib.gempe_load(None, None, 0) == -1
+
+
+def test_tile_wait_probe_rejects_bad_limits_on_host():
+    """The bounded-wait test hook checks its poll limit before any CUDA call."""
+    from paper_2011_03479_gb300 import binding
+    for bad in (0, -3, (1 << 22) + 1):
+        with pytest.raises(binding.GempeError) as err:
+            binding.gempe_test_tile_wait(bad)
+        assert err.value.status == -1

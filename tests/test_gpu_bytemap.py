@@ -81,6 +81,37 @@ def test_bytemap_samples_bit_exact(B, O, rmat_s12, sampling, d):
         assert st[f] == ref[f] + ref6[f], f
 
 
+@pytest.mark.parametrize("sampling", [0, 1])
+def test_bytemap_wraps_32_bits(B, O, sampling):
+    """n = 131,072 (R-MAT scale 17): pi(i) n + pi(j) exceeds 2^32 for most
+    pairs, so the address depends on the 32-bit wrap-around Sec. III.C
+    prints; the samples of two epochs in different renaming periods are
+    bit-exact and the rejected and false-positive counts exact."""
+    from paper_2011_03479_gb300 import inputs
+    rp, ci = inputs.rmat(17, 8, seed=177)
+    n = len(rp) - 1
+    assert n == 131072 and (n - 1) * n >= 1 << 32
+    log2 = 22
+    p = B.gempe_default_params(sampling=sampling, neg_per_vertex=10, membership=1, bytemap_log2=log2,
+                               rename_every=RENAME)
+    x = np.zeros((n, 2), dtype=np.float32)
+    with B.gempe_create(rp, ci, 2, p) as ctx:
+        B.gempe_set_positions(ctx, x)
+        B.gempe_set_state(ctx, 1.0, 5)
+        s5 = B.gempe_sweep(ctx, record_samples=True)
+        B.gempe_update(ctx)
+        st = B.gempe_stats(ctx)
+        s6 = B.gempe_sweep(ctx, record_samples=True)
+        B.gempe_update(ctx)
+    refs = [O.epoch(rp, ci, x.astype(np.float64), 1.0, e, p.seed, 10, per_slot=sampling, membership=1,
+                    bytemap_log2=log2, rename_every=RENAME) for e in (5, 6)]
+    np.testing.assert_array_equal(s5, refs[0]["samples"])
+    np.testing.assert_array_equal(s6, refs[1]["samples"])
+    assert refs[0]["false_pos"] > 0
+    for f in ("accepted", "rejected", "exhausted", "false_pos"):
+        assert st[f] == refs[0][f] + refs[1][f], f
+
+
 def test_bytemap_run_counts(B, O, rmat_s12):
     """Twelve epochs with a renaming every three: the sampler's counts over
     epochs 0..12 (the run samples one epoch ahead) equal the oracle's."""

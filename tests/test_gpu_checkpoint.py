@@ -84,3 +84,7 @@ def test_mismatched_checkpoint_refused(B, sbm_1000):
     with B.gempe_create(rp, ci, 4, p) as e:
         with pytest.raises(B.GempeError, match="another graph"):
             B.gempe_load(e, blob)
+    for kw in (dict(mu=1.4), dict(hist_bins=512), dict(sigma_every=2), dict(w_formula=1), dict(clamp_neg_d=0)):
+        with B.gempe_create(rp, ci, 2, B.gempe_default_params(neg_per_vertex=5, **kw)) as f:
+            with pytest.raises(B.GempeError, match="another run"):
+                B.gempe_load(f, blob)

@@ -613,6 +613,47 @@ def test_bytemap_membership(oracle_mod, sbm_small):
     assert ab2 != ab3
 
 
+def _bytemap_addr_restated(n, w0, w1, log2_size, i, j):
+    """Sec. III.C's address, restated with Python integers from its definition:
+    the renaming pi(v) = (a v + b) mod n (a = 1 + w0 mod (n-1), stepped up,
+    wrapping to 1, to the first value coprime to n; b = w1 mod n), then
+    hash = ((pi(i) n + pi(j)) * 1103515245) mod 2^32, masked to the map's
+    s = 2^log2_size bytes.  Every 32-bit step is reduced mod 2^32 explicitly."""
+    a = 1 + (w0 % (n - 1))
+    while math.gcd(a, n) != 1:
+        a = 1 if a + 1 >= n else a + 1
+    b = w1 % n
+    pi, pj = (a * i + b) % n, (a * j + b) % n
+    t = (pi * n) % (1 << 32)
+    t = (t + pj) % (1 << 32)
+    t = (t * 1103515245) % (1 << 32)
+    return t & ((1 << log2_size) - 1), (a, b)
+
+
+@pytest.mark.parametrize("n", [1000, 70001, 131072, 1000003])
+def test_bytemap_address_restated(oracle_mod, n):
+    """The oracle's byte-map address equals its definition (Sec. III.C)
+    restated here with Python integers, for graphs where pi(i) n + pi(j)
+    stays below 2^32 (n = 1000) and where it wraps (n > 65536): operands in
+    the other order, the map size s in place of s - 1, or a renaming other
+    than the affine one fails.  The renaming's words come from the Philox
+    function, which is pinned against cuRAND separately."""
+    seed, rng = 0x1234ABCD, np.random.default_rng(n)
+    for period, log2 in ((0, 12), (3, 20), (11, 30)):
+        w0, w1 = (int(v) for v in oracle_mod.philox4x32_10([period, 0, 0, 0x09000000],
+                                                          [seed & 0xFFFFFFFF, seed >> 32])[:2])
+        pairs = rng.integers(0, n, size=(400, 2)).astype(np.int32)
+        pairs[:4] = [[0, 0], [n - 1, n - 1], [0, n - 1], [n - 1, 0]]
+        got, ab = oracle_mod.bytemap_addr(n, seed, period, log2, pairs)
+        want = [_bytemap_addr_restated(n, w0, w1, log2, int(i), int(j)) for i, j in pairs]
+        assert tuple(ab) == want[0][1]
+        np.testing.assert_array_equal(got, np.array([w for w, _ in want], dtype=np.uint32))
+        if n > 65536:
+            a, b = want[0][1]
+            big = [((a * int(i) + b) % n) * n + (a * int(j) + b) % n for i, j in pairs]
+            assert max(big) >= 1 << 32, "the 32-bit wrap of pi(i) n + pi(j) is exercised"
+
+
 @pytest.mark.parametrize("form", [dict(k=5), dict(k=5, symmetric=0), dict(k=3, per_slot=1),
                                   dict(k=0, block_partners=64, tile_vertices=128),
                                   dict(k=0, block_partners=16, tile_vertices=128, symmetric=0)],
