@@ -204,6 +204,12 @@ cudaError_t launch_bytemap_build(const EpochArgs& a, int force, int sm_count, cu
 cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_units, int sm_count,
                                  cudaStream_t s);
 cudaError_t launch_tile_bf16(const EpochArgs& a, int grid, cudaStream_t s);
+// FP32 tiles of block-sampled non-edges (precision 0, d in {16, 32, 64, 128}).
+bool tile_dim_f32(int d);
+size_t tile_f32_smem_bytes(int d, int bins);
+cudaError_t prepare_tile_f32_kernel(int d, int bins);
+int tile_f32_blocks_per_sm(int d, int bins);
+cudaError_t launch_tile_f32(const EpochArgs& a, int grid, cudaStream_t s);
 int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm);
 bool tile_dim(int d);
 size_t tile_smem_bytes(int d, int bins);

@@ -339,7 +339,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     G = (int32_t)gs.size();
     stream = s;
     block = p.block_partners > 0;
-    tiles = block && p.precision == 1 && tile_dim(d);
+    tiles = block && (p.precision == 1 ? tile_dim(d) : tile_dim_f32(d));
     per_slot = p.sampling == 1;
     narrow_keys = true;
     for (const GraphInput& in : gs) narrow_keys = narrow_keys && in.n <= kNarrowKeysMaxN;
@@ -401,7 +401,8 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     PK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming), "cudaEventCreate");
     mills = mills_table_device();
     if (!mills) return pack_fail(GEMPE_E_CUDA, "Mills table address");
-    if (tiles) PK(prepare_tile_kernel(d, bins), "tile kernel attributes");
+    if (tiles)
+        PK(p.precision == 1 ? prepare_tile_kernel(d, bins) : prepare_tile_f32_kernel(d, bins), "tile kernel attributes");
     PK(prepare_update_kernels(bins), "update kernel attributes");
 
     // host copy of the pack's row offsets (the column arrays go to the
@@ -576,7 +577,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
 
     sampler_grid = gempe::sampler_grid(rows, k, sm_count);
     update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
-    tile_grid = gempe::tile_grid(n_tile_items, sm_count, 0);
+    tile_grid = gempe::tile_grid(n_tile_items, sm_count, p.precision == 1 ? 0 : tile_f32_blocks_per_sm(d, bins));
     // with autotuning the shape is set by autotune(), which the owner calls next
     return p.autotune ? GEMPE_OK : set_shape(PackShape{});
 }
@@ -783,7 +784,9 @@ gempe_status Pack::enqueue_sweep() {
     ss.lanes = shape.lanes;
     ss.kernel = shape.kernel;
     PK(launch_sweep(args(), ss, stream), "sweep");
-    if (tiles) PK(launch_tile_bf16(args(), tile_grid, stream), "tiles");
+    if (tiles)
+        PK(p.precision == 1 ? launch_tile_bf16(args(), tile_grid, stream) : launch_tile_f32(args(), tile_grid, stream),
+           "tiles");
     if (fork) {
         PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
         PK(launch_epoch_sampler(*this, side), "sampler");

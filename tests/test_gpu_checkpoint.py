@@ -27,9 +27,9 @@ def B():
 
 
 @pytest.mark.parametrize("form", [dict(neg_per_vertex=5), dict(neg_per_vertex=5, sampling=1),
-                                  dict(block_partners=64, precision=1),
+                                  dict(block_partners=64, precision=1), dict(block_partners=64, precision=0),
                                   dict(neg_per_vertex=5, membership=1, rename_every=2)],
-                         ids=["per-vertex", "per-slot", "block-bf16", "bytemap"])
+                         ids=["per-vertex", "per-slot", "block-bf16", "block-fp32", "bytemap"])
 def test_resume_continues_the_run(B, sbm_1000, form):
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     d = 16 if form.get("block_partners") else 2
@@ -42,7 +42,7 @@ def test_resume_continues_the_run(B, sbm_1000, form):
         B.gempe_step(a, 4)
         x_a = B.gempe_positions(a)
         st_a = B.gempe_stats(a)
-    assert len(blob) == 136 + 4 * x_saved.size
+    assert len(blob) == 176 + 4 * x_saved.size
     with B.gempe_create(rp, ci, d, p) as b:
         B.gempe_load(b, blob)
         st_b0 = B.gempe_stats(b)

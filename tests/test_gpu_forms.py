@@ -64,7 +64,7 @@ def _run(B, O, rp, ci, d, x, sigma, epoch, **kw):
         stats = B.gempe_stats(ctx)
     ref = O.epoch(rp, ci, x.astype(np.float64), sigma, epoch, p.seed, p.neg_per_vertex,
                   block_partners=p.block_partners, tile_vertices=128, hist_bins=p.hist_bins,
-                  hist_max=p.hist_max)
+                  hist_max=p.hist_max, symmetric=p.symmetric_neg)
     return dict(samples=samples, delta=delta, z=z, he=he, hn=hn, xn=xn, ref=ref, p=p, stats=stats, x0=x)
 
 
@@ -88,11 +88,13 @@ def test_block_samples_bit_exact(B, O, sbm_1000, precision, d):
     assert int((exp >= 0).sum()) == r["ref"]["accepted"]
 
 
-@pytest.mark.parametrize("d", [8, 16, 64])
-def test_block_fp32_parity(B, O, sbm_1000, d):
+@pytest.mark.parametrize("d,symmetric", [(8, 1), (16, 1), (32, 1), (64, 1), (128, 1), (32, 0)],
+                         ids=["d8-sweep", "d16", "d32", "d64", "d128", "d32-anchor-only"])
+def test_block_fp32_parity(B, O, sbm_1000, d, symmetric):
+    """d = 8: the pair sweep takes the block samples; d >= 16: the FP32 tiles."""
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     x = (np.random.default_rng(d).normal(size=(1000, d)) * 0.9).astype(np.float32)
-    r = _run(B, O, rp, ci, d, x, 0.8, 2, block_partners=64)
+    r = _run(B, O, rp, ci, d, x, 0.8, 2, block_partners=64, symmetric_neg=symmetric)
     ref = r["ref"]
     assert _err_rows(r["delta"], ref["delta"], ref["abs_terms"]).max() <= TOL32
     assert _err_rows(r["z"], ref["z"]).max() <= TOL32
@@ -146,3 +148,23 @@ def test_ba_bf16_tiles_parity(B, O, ba_20k):
     e_delta, e_z, e_x = _bf16_errors(r)
     print(f"BA 20k bf16 tiles: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
     assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
+
+
+def test_ba_fp32_tiles_parity(B, O, ba_20k):
+    """The FP32 tiles on the Barabasi-Albert graph (n = 20,000: 157 tiles, the
+    last one ragged, hubs of high degree), d = 64, within the FP32 bar."""
+    rp, ci = ba_20k
+    n = len(rp) - 1
+    x = (np.random.default_rng(6).normal(size=(n, 64)) * 0.7).astype(np.float32)
+    r = _run(B, O, rp, ci, 64, x, 0.7, 9, block_partners=64, precision=0)
+    ref = r["ref"]
+    exp = _expected_block_samples(rp, ci, ref["partners"])
+    np.testing.assert_array_equal(r["samples"], exp)
+    e_delta = _err_rows(r["delta"], ref["delta"], ref["abs_terms"])
+    plain = float(np.mean(_err_rows(r["delta"], ref["delta"]) <= TOL32))
+    print(f"BA 20k fp32 tiles: delta {e_delta.max():.2e} plain-bar fraction {plain:.4f}")
+    assert e_delta.max() <= TOL32 and plain >= 0.99
+    assert _err_rows(r["z"], ref["z"]).max() <= TOL32
+    assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
+    assert r["stats"]["used"] == ref["accepted"]
+    assert r["he"].sum() == len(ci) // 2
