@@ -174,6 +174,17 @@ gempe_status gempe_sweep(gempe_ctx* ctx, int32_t* host_samples);
  * and histograms cleared, sigma refit when due, epoch counter + 1. */
 gempe_status gempe_update(gempe_ctx* ctx);
 
+/* Per-kernel timing of the epochs run as gempe_sweep + gempe_update (not
+ * gempe_step's graph replays; the paper has no counterpart).  enable = 1:
+ * those calls record CUDA events on the context's stream before the pair
+ * sweep, after it, after the tile kernel of the block form and after the
+ * position update (the event before the update keeps it from starting while
+ * the previous kernel's last blocks run); enable = 0 stops recording.
+ * out_ms3 (may be NULL) receives the windows of the last epoch recorded,
+ * in milliseconds: {sweep, tiles (0 without tiles), update}; all 0 when no
+ * epoch was recorded.  Synchronises on the last event when out_ms3 is set. */
+gempe_status gempe_kernel_times(gempe_ctx* ctx, int32_t enable, float* out_ms3);
+
 /* Copy the positions to host float[n*d] (synchronises).  count must be n*d. */
 gempe_status gempe_positions(gempe_ctx* ctx, float* host_out, size_t count);
 

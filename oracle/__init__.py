@@ -17,8 +17,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gempe_oracle.c")
 LIB = os.path.join(HERE, "libgempe_oracle.so")
+LIB_OMP = os.path.join(HERE, "libgempe_oracle_omp.so")
 
 _lib = None
+_lib_omp = None
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
@@ -41,11 +43,47 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_omp(force: bool = False) -> str:
+    """The same source with OpenMP (-fopenmp): orc_epoch's vertex and tile
+    loops over all host threads, shared sums by atomic additions.  Only the
+    benchmark's CPU baseline runs it; the parity tests use the serial build."""
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(SRC) > os.path.getmtime(LIB_OMP):
+        tmp = LIB_OMP + ".tmp%d" % os.getpid()
+        res = subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fno-fast-math", "-ffp-contract=off",
+                              "-shared", "-fPIC", "-o", tmp, SRC, "-lm"],
+                             capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("oracle OpenMP build failed:\n" + res.stderr)
+        os.replace(tmp, LIB_OMP)
+    return LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    if _lib_omp is not None:
+        return _lib_omp
+    lib = ctypes.CDLL(build_omp())
+    _bind(lib)
+    _lib_omp = lib
+    return lib
+
+
+def threads(parallel: bool = False) -> int:
+    """Host threads orc_epoch runs on in the serial (1) or the OpenMP build."""
+    return int((_load_omp() if parallel else _load()).orc_threads())
+
+
 def _load():
     global _lib
     if _lib is not None:
         return _lib
     lib = ctypes.CDLL(build())
+    _bind(lib)
+    _lib = lib
+    return lib
+
+
+def _bind(lib):
     I32, I64, U64, F64, F32 = _c.c_int32, _c.c_int64, _c.c_uint64, _c.c_double, _c.c_float
     sig = {
         "orc_philox4x32_10": (None, [_u32p, _u32p, _u32p]),
@@ -81,12 +119,11 @@ def _load():
         "orc_vertex_terms": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32, I32, I32,
                                         I32, I32, I32, I32, I32, _i32p, _f64p, _f64p, _f64p]),
     }
+    sig["orc_threads"] = (_c.c_int, [])
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
-    return lib
 
 
 # ---------------------------------------------------------------------------
@@ -298,13 +335,14 @@ def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retr
 def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retries=MAX_RETRIES,
         symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
         hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0, sigma_source=0, membership=0,
-        bytemap_log2=24, rename_every=0):
-    """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats)."""
+        bytemap_log2=24, rename_every=0, parallel=False):
+    """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats).
+    parallel: the OpenMP build (all host threads; sums in another order)."""
     n = len(row_ptr) - 1
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     s = ctypes.c_double(sigma)
     st = np.zeros(5, dtype=np.int64)
-    rc = _load().orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
+    rc = (_load_omp() if parallel else _load()).orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
                          epoch0, epochs, seed, k, max_retries, symmetric, w_formula, clamp_neg_d,
                          z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot, sigma_source,
                          membership, bytemap_log2, rename_every)

@@ -79,6 +79,28 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The same source also builds the timed CPU baseline with OpenMP
+ * (-fopenmp): the vertex loop and the tile loop of orc_epoch then run over
+ * all host threads, every addition into a shared sum becomes an atomic
+ * addition, and the per-thread counters are added up at the end.  Built
+ * without OpenMP (the parity reference) the pragmas are ignored and the
+ * loops run in order, one vertex after another. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_ATOMIC _Pragma("omp atomic")
+#else
+#define ORC_ATOMIC
+#endif
+
+/* Host threads the build runs orc_epoch on (1 without OpenMP). */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 #define ORC_LN2 0.69314718055994530942
 #define ORC_PI 3.14159265358979323846
 #define ORC_SQRT2 1.41421356237309504880
@@ -241,10 +263,15 @@ static void add_wm_term(double* y, double* z, const double* x, int32_t d, int64_
                         double delta, double dd, double w) {
     if (!(w > 0.0)) return;   /* an underflowed weight contributes nothing */
     double s = (delta != 0.0) ? dd / delta : 0.0;
-    for (int32_t c = 0; c < d; ++c)
-        y[a * d + c] += w * (x[b * d + c] + s * (x[a * d + c] - x[b * d + c]));
-    z[a] += w;
-    if (g_absd) g_absd[a] += w * fabs(s - 1.0) * delta;
+    for (int32_t c = 0; c < d; ++c) {
+        double t = w * (x[b * d + c] + s * (x[a * d + c] - x[b * d + c]));
+        ORC_ATOMIC y[a * d + c] += t;
+    }
+    ORC_ATOMIC z[a] += w;
+    if (g_absd) {
+        double t = w * fabs(s - 1.0) * delta;
+        ORC_ATOMIC g_absd[a] += t;
+    }
 }
 
 static int32_t hist_bin(double delta, int32_t B, double hist_max) {
@@ -422,9 +449,6 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
     int32_t smp_cap = k > 0 ? k : 1;
     if (per_slot)
         for (int32_t i = 0; i < n; ++i) smp_cap = (row_ptr[i + 1] - row_ptr[i] > smp_cap) ? row_ptr[i + 1] - row_ptr[i] : smp_cap;
-    int32_t* smp = (int32_t*)malloc((size_t)smp_cap * sizeof(int32_t));
-    int32_t* part = (int32_t*)malloc((size_t)(block_P > 0 ? block_P : 1) * sizeof(int32_t));
-    if (!smp || !part) { free(smp); free(part); if (bmp) free(bm.map); return -1; }
     g_absd = absd;
     if (absd) memset(absd, 0, sizeof(double) * (size_t)n);
     memset(y, 0, sizeof(double) * (size_t)n * d);          /* zero numerators ... */
@@ -432,6 +456,25 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
     if (hist_e) memset(hist_e, 0, sizeof(double) * (size_t)B);
     if (hist_n) memset(hist_n, 0, sizeof(double) * (size_t)B);
     int64_t accepted = 0, rejected = 0, exhausted = 0;
+    int failed = 0;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+    /* per-thread sample buffers and counters (one set without OpenMP) */
+    int32_t* smp = (int32_t*)malloc((size_t)smp_cap * sizeof(int32_t));
+    int32_t* part = (int32_t*)malloc((size_t)(block_P > 0 ? block_P : 1) * sizeof(int32_t));
+    int64_t acc_t = 0, rej_t = 0, exh_t = 0, fp_t = 0;
+    if (!smp || !part) {
+        ORC_ATOMIC failed += 1;
+    }
+#ifdef _OPENMP
+#pragma omp barrier
+#endif
+    if (!failed) {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
     for (int32_t i = 0; i < n; ++i) {
         /* edges: every CSR slot (i,j) contributes to y_i, z_i */
         for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
@@ -439,21 +482,22 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
             double delta = dist(x, d, i, j), dd, w;
             orc_parabola(delta, mu, sigma, 1, w_formula, clamp_neg_d, &dd, &w);
             add_wm_term(y, z, x, d, i, j, delta, dd, w);
-            if (hist_e && j > i) hist_e[hist_bin(delta, B, hist_max)] += 1.0;
+            if (hist_e && j > i) {
+                ORC_ATOMIC hist_e[hist_bin(delta, B, hist_max)] += 1.0;
+            }
         }
         /* sampled non-edges anchored at i: k of them, or one per CSR slot */
         int32_t ki = k;
         if (per_slot) {
             ki = row_ptr[i + 1] - row_ptr[i];
-            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, bmp, smp, &rejected, &exhausted,
-                         &false_pos);
+            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, bmp, smp, &rej_t, &exh_t, &fp_t);
         } else {
             sample_vertex_bm(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, bmp, smp,
-                             &rejected, &exhausted, &false_pos);
+                             &rej_t, &exh_t, &fp_t);
         }
         int32_t acc = 0;
         for (int32_t t = 0; t < ki; ++t) acc += (smp[t] >= 0);
-        accepted += acc;
+        acc_t += acc;
         double deg = (double)(row_ptr[i + 1] - row_ptr[i]);
         double omega = acc ? ((double)n - 1.0 - deg) / (2.0 * acc) : 0.0;
         for (int32_t t = 0; t < ki; ++t) {
@@ -464,12 +508,17 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
             orc_parabola(delta, mu, sigma, 0, w_formula, clamp_neg_d, &dd, &w);
             add_wm_term(y, z, x, d, i, g, delta, dd, w);
             if (symmetric) add_wm_term(y, z, x, d, g, i, delta, dd, w);
-            if (hist_n) hist_n[hist_bin(delta, B, hist_max)] += omega;
+            if (hist_n) {
+                ORC_ATOMIC hist_n[hist_bin(delta, B, hist_max)] += omega;
+            }
         }
     }
     /* block-sampled non-edges: every vertex of a tile against the tile's partners */
     if (block_P > 0) {
         int32_t n_tiles = (n + block_T - 1) / block_T;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
         for (int32_t tile = 0; tile < n_tiles; ++tile) {
             orc_block_partners(n, tile, epoch, seed, block_P, part);
             if (partners_out) memcpy(partners_out + (int64_t)tile * block_P, part, sizeof(int32_t) * (size_t)block_P);
@@ -477,8 +526,8 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
                 int32_t acc = 0;
                 for (int32_t p = 0; p < block_P; ++p)
                     acc += (part[p] != i && !orc_is_edge(row_ptr, col_idx, i, part[p]));
-                accepted += acc;
-                rejected += block_P - acc;
+                acc_t += acc;
+                rej_t += block_P - acc;
                 double deg = (double)(row_ptr[i + 1] - row_ptr[i]);
                 double omega = acc ? ((double)n - 1.0 - deg) / (2.0 * acc) : 0.0;
                 for (int32_t p = 0; p < block_P; ++p) {
@@ -488,10 +537,25 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
                     orc_parabola(delta, mu, sigma, 0, w_formula, clamp_neg_d, &dd, &w);
                     add_wm_term(y, z, x, d, i, g, delta, dd, w);
                     if (symmetric) add_wm_term(y, z, x, d, g, i, delta, dd, w);
-                    if (hist_n) hist_n[hist_bin(delta, B, hist_max)] += omega;
+                    if (hist_n) {
+                        ORC_ATOMIC hist_n[hist_bin(delta, B, hist_max)] += omega;
+                    }
                 }
             }
         }
+    }
+    }
+    ORC_ATOMIC accepted += acc_t;
+    ORC_ATOMIC rejected += rej_t;
+    ORC_ATOMIC exhausted += exh_t;
+    ORC_ATOMIC false_pos += fp_t;
+    free(smp);
+    free(part);
+    }
+    if (failed) {
+        g_absd = NULL;
+        if (bmp) free(bm.map);
+        return -1;
     }
     /* x_i := y_i / z_i */
     for (int32_t i = 0; i < n; ++i)
@@ -506,8 +570,6 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
         stats[4] = false_pos;
     }
     g_absd = NULL;
-    free(smp);
-    free(part);
     if (bmp) free(bm.map);
     return 0;
 }

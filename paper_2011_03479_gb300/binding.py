@@ -157,6 +157,7 @@ def load(build: bool = True):
         "gempe_fit_sigma": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_test_tile_wait": (st, [i32, P(i32), P(i32)]),
+        "gempe_kernel_times": (st, [vp, i32, P(ctypes.c_float)]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
         "gempe_save": (st, [vp, vp, P(sz)]),
         "gempe_load": (st, [vp, vp, sz]),
@@ -406,6 +407,14 @@ def gempe_fit_sigma_static(hist_e, hist_n, hist_max: float = 12.0, mu: float = 1
     _check(load().gempe_fit_sigma_static(_ptr(h), len(h) // 2, float(hist_max), float(mu),
                                          _stream_handle(stream), ctypes.byref(out)))
     return out.value
+
+
+def gempe_kernel_times(ctx: _Ctx, enable: bool = True) -> tuple[float, float, float]:
+    """Switch per-kernel event timing of gempe_sweep / gempe_update on or off;
+    returns the last recorded epoch's (sweep, tiles, update) windows in ms."""
+    out = (ctypes.c_float * 3)()
+    _check(load().gempe_kernel_times(ctx.handle, 1 if enable else 0, out))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def gempe_test_tile_wait(poll_limit: int) -> tuple[int, int]:

@@ -47,6 +47,9 @@ struct gempe_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int32_t n = 0;
+    bool time_kernels = false;   // gempe_kernel_times: record events around directly enqueued kernels
+    bool sweep_timed = false;    // the pending sweep recorded its events
+    bool timed = false;          // the events hold a whole sweep + update
 
     ~gempe_ctx() {
         if (stream) cudaStreamSynchronize(stream);
@@ -225,8 +228,11 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
            "copy masks");
         CK(cudaStreamSynchronize(c->stream), "synchronize");
     }
+    pk.time_kernels = c->time_kernels;
     gempe_status s = pk.enqueue_sweep();
+    pk.time_kernels = false;
     if (s != GEMPE_OK) return s;
+    c->sweep_timed = c->time_kernels;
     pk.swept = true;
     if (host_samples && pk.per_slot) {
         int32_t epoch = 0;
@@ -259,9 +265,34 @@ GEMPE_API gempe_status gempe_sweep(gempe_ctx* c, int32_t* host_samples) {
 
 GEMPE_API gempe_status gempe_update(gempe_ctx* c) {
     if (!c) return fail(GEMPE_E_INVALID_ARG, "ctx is null");
-    gempe_status s = c->pk->enqueue_update();
+    Pack& pk = *c->pk;
+    const bool timed = c->sweep_timed && pk.swept;
+    pk.time_kernels = timed;
+    gempe_status s = pk.enqueue_update();
+    pk.time_kernels = false;
     if (s != GEMPE_OK) return s;
-    c->pk->swept = false;
+    c->timed = timed;
+    c->sweep_timed = false;
+    pk.swept = false;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_kernel_times(gempe_ctx* c, int32_t enable, float* out_ms3) {
+    if (!c) return fail(GEMPE_E_INVALID_ARG, "ctx is null");
+    if (enable != 0 && enable != 1) return fail(GEMPE_E_INVALID_ARG, "enable must be 0 or 1");
+    Pack& pk = *c->pk;
+    if (out_ms3) {
+        out_ms3[0] = out_ms3[1] = out_ms3[2] = 0.0f;
+        if (c->timed) {
+            CK(cudaEventSynchronize(pk.tev[3]), "synchronize");
+            CK(cudaEventElapsedTime(&out_ms3[0], pk.tev[0], pk.tev[1]), "elapsed");
+            CK(cudaEventElapsedTime(&out_ms3[1], pk.tev[1], pk.tev[2]), "elapsed");
+            CK(cudaEventElapsedTime(&out_ms3[2], pk.tev[2], pk.tev[3]), "elapsed");
+        }
+    }
+    if (enable && !pk.tev[0])
+        for (cudaEvent_t& e : pk.tev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    c->time_kernels = enable != 0;
     return GEMPE_OK;
 }
 

@@ -265,6 +265,8 @@ Pack::~Pack() {
     release_all();
     if (fork_ev) cudaEventDestroy(fork_ev);
     if (join_ev) cudaEventDestroy(join_ev);
+    for (cudaEvent_t& e : tev)
+        if (e) cudaEventDestroy(e);
     if (side) cudaStreamDestroy(side);
 }
 
@@ -783,10 +785,13 @@ gempe_status Pack::enqueue_sweep() {
     ss.grid = sweep_grid;
     ss.lanes = shape.lanes;
     ss.kernel = shape.kernel;
+    if (time_kernels) PK(cudaEventRecord(tev[0], stream), "timing event");
     PK(launch_sweep(args(), ss, stream), "sweep");
+    if (time_kernels) PK(cudaEventRecord(tev[1], stream), "timing event");
     if (tiles)
         PK(p.precision == 1 ? launch_tile_bf16(args(), tile_grid, stream) : launch_tile_f32(args(), tile_grid, stream),
            "tiles");
+    if (time_kernels) PK(cudaEventRecord(tev[2], stream), "timing event");
     if (fork) {
         PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
         PK(launch_epoch_sampler(*this, side), "sampler");
@@ -799,6 +804,7 @@ gempe_status Pack::enqueue_sweep() {
 // The position update and slope fits, then the join with the side stream.
 gempe_status Pack::enqueue_update() {
     PK(launch_update(args(), update_grid, stream), "update");
+    if (time_kernels) PK(cudaEventRecord(tev[3], stream), "timing event");
     if (p.sigma_source == 1 && p.sigma_every > 0) {
         PK(launch_hist_pass(args(), stream), "histogram pass");
         PK(launch_fit_graphs(args(), stream), "slope fit");

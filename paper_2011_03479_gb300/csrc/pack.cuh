@@ -62,6 +62,10 @@ struct Pack {
     bool primed = false;             // samples of the current epoch are in the buffer
     bool sampled_ahead = false;      // the next epoch's sampler has been enqueued
     bool swept = false;              // a sweep ran without the update that clears its sums
+    // per-kernel timing of epochs enqueued directly (not captured): events on
+    // `stream` before the sweep, after it, after the tiles, after the update
+    bool time_kernels = false;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<GraphInfo> info;     // host copies
     std::vector<int64_t> nnz;
     std::vector<int32_t> row_ptr_h;  // pack CSR offsets, rows + 1

@@ -168,3 +168,30 @@ def test_ba_fp32_tiles_parity(B, O, ba_20k):
     assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
     assert r["stats"]["used"] == ref["accepted"]
     assert r["he"].sum() == len(ci) // 2
+
+
+@pytest.mark.parametrize("kw,d,tiles", [(dict(neg_per_vertex=5), 2, False), (dict(block_partners=64), 64, True),
+                                        (dict(block_partners=64, precision=1), 64, True)],
+                         ids=["per-vertex", "block-fp32", "block-bf16"])
+def test_kernel_times(B, sbm_1000, kw, d, tiles):
+    """gempe_kernel_times: per-kernel windows of an epoch run as gempe_sweep +
+    gempe_update (the tile window only in the block form); graph replays of
+    gempe_step are not recorded, and the epoch's results are unchanged."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    p = B.gempe_default_params(**kw)
+    with B.gempe_create(rp, ci, d, p) as ctx, B.gempe_create(rp, ci, d, p) as ref:
+        assert B.gempe_kernel_times(ctx, True) == (0.0, 0.0, 0.0)
+        B.gempe_sweep(ctx)
+        B.gempe_update(ctx)
+        B.gempe_sweep(ref)
+        B.gempe_update(ref)
+        sw, ti, up = B.gempe_kernel_times(ctx, True)
+        assert sw > 0 and up > 0 and (ti > 0) == tiles
+        B.gempe_step(ctx, 2)
+        B.gempe_step(ref, 2)
+        assert B.gempe_kernel_times(ctx, False) == (sw, ti, up)
+        st, sr = B.gempe_stats(ctx), B.gempe_stats(ref)
+        for f in ("epoch", "accepted", "used"):
+            assert st[f] == sr[f]
+        x, xr = B.gempe_positions(ctx), B.gempe_positions(ref)
+        np.testing.assert_allclose(x, xr, rtol=0, atol=1e-3 * max(float(np.abs(xr).max()), 1.0))

@@ -1,9 +1,11 @@
 """The N > 1 path of bench.py on CPU: world-size-2 gloo process groups.
 
-The bench runs one independent replica per GPU and exchanges only the whole-
-job figures after the timed region: the slowest rank's time (MAX) and the sum
-of the ranks' pair-updates (SUM).  Under torchrun the reference arm runs on
-rank 0 only; other ranks exit 0 without work.
+The bench runs the single-graph workloads as one independent replica per
+GPU, splits the batch's graphs and the served job stream over the ranks, and
+exchanges only the whole-job figures after the timed region: the slowest
+rank's time (MAX) and the sum of the ranks' pair-updates (SUM).  Under
+torchrun the reference arm runs on rank 0 only; other ranks exit 0 without
+work.
 """
 import json
 import multiprocessing as mp
@@ -45,6 +47,35 @@ def test_combine_ranks_gloo_world_2():
         assert pairs == 300.0      # 100 + 200
         assert v == 6.0            # 2 + 4
         assert none is None
+
+
+def test_job_shares_gloo_world_2():
+    """The batched and served forms split their independent jobs over the
+    ranks: computed on each rank alone, the shares agree, are disjoint and
+    cover every graph and every job of the stream; the graph shares carry
+    nearly equal work."""
+    import _rank_worker
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker.shares, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=120) for _ in procs)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert all(p.exitcode == 0 for p in procs)
+    (_, got0, sizes), (_, got1, _) = res
+    assert got0 == got1
+    (g0, j0), (g1, j1) = got0
+    assert sorted(g0 + g1) == list(range(256)) and not set(g0) & set(g1)
+    assert sorted(j0 + j1) == list(range(200)) and not set(j0) & set(j1)
+    w0, w1 = sum(sizes[i] for i in g0), sum(sizes[i] for i in g1)
+    assert abs(w0 - w1) <= max(sizes)
 
 
 def test_combine_ranks_single_process():
