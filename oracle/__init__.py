@@ -96,7 +96,7 @@ def _bind(lib):
         "orc_sample": (None, [_i32p, _i32p, I32, I32, U64, I32, I32, I32, _i32p]),
         "orc_epoch": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
                                  I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
-                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32, I32, I32, I32]),
+                                 _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32, I32, I32, I32, I32]),
         "orc_bytemap_addr": (None, [I32, U64, I32, I32, _i32p, I64, _c.POINTER(_c.c_uint32),
                                     _c.POINTER(_c.c_uint32)]),
         "orc_block_partners": (None, [I32, I32, I32, U64, I32, _i32p]),
@@ -114,12 +114,14 @@ def _bind(lib):
         "orc_loss_sampled": (F64, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32]),
         "orc_run": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, _c.POINTER(F64), F64, I32, I32,
                                U64, I32, I32, I32, I32, I32, F64, I32, F64, I32, _i64p, I32, I32, I32, I32,
-                               I32, I32, I32]),
+                               I32, I32, I32, I32]),
         "orc_hist_pass": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, I32, U64, I32, I32, I32, F64, _f64p, _f64p]),
         "orc_vertex_terms": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32, I32, I32,
                                         I32, I32, I32, I32, I32, _i32p, _f64p, _f64p, _f64p]),
     }
     sig["orc_threads"] = (_c.c_int, [])
+    sig["orc_lcg_next"] = (_c.c_uint32, [_c.c_uint32])
+    sig["orc_lcg_vertex"] = (I32, [_c.c_uint32, I32])
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
         f.restype = res
@@ -151,6 +153,16 @@ def philox4x32_10(ctr, key):
     _load().orc_philox4x32_10(np.ascontiguousarray(ctr, dtype=np.uint32),
                               np.ascontiguousarray(key, dtype=np.uint32), out)
     return out
+
+
+def lcg_next(state):
+    """Sec. III.C's LCG: the state after `state`."""
+    return int(_load().orc_lcg_next(int(state) & 0xFFFFFFFF))
+
+
+def lcg_vertex(state, n):
+    """Fig. 2's vertex of an LCG state (FP32 float trick, n read as 0)."""
+    return int(_load().orc_lcg_vertex(int(state) & 0xFFFFFFFF, int(n)))
 
 
 def init_positions(n, d, seed, init_range=INIT_RANGE):
@@ -196,11 +208,12 @@ def block_partners(n, tile, epoch_idx, seed, P):
 def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES,
           symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
           hist_max=HIST_MAX, block_partners=0, tile_vertices=128, per_slot=0, membership=0, bytemap_log2=24,
-          rename_every=0):
+          rename_every=0, rng=0):
     """One epoch of Fig. 4; returns a dict of FP64 results.  ``abs_terms[i]`` is the
     sum of the sizes of the pair terms of y_i - z_i x_i (the scale of that sum's
     rounding when its terms cancel).  per_slot=1: Sec. III.C's policy, one
-    sample per CSR slot (``samples`` then has one entry per slot)."""
+    sample per CSR slot (``samples`` then has one entry per slot).  rng=1: Sec. III.C's
+    LCG draws the sampled non-edges (seeded per slot from Philox)."""
     n = len(row_ptr) - 1
     nnz = int(row_ptr[-1])
     x = _f64(x)
@@ -215,7 +228,7 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
     rc = _load().orc_epoch(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
                            max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
                            hist_max, y, z, xn, he, hn, smp, st, absd, block_partners,
-                           tile_vertices, parts, per_slot, membership, bytemap_log2, rename_every)
+                           tile_vertices, parts, per_slot, membership, bytemap_log2, rename_every, rng)
     if rc != 0:
         raise MemoryError("oracle epoch failed")
     samples = smp[:nnz] if per_slot else smp[: n * k].reshape(n, k)
@@ -335,7 +348,7 @@ def loss_sampled(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retr
 def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retries=MAX_RETRIES,
         symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
         hist_max=HIST_MAX, sigma_every=1, block_partners=0, tile_vertices=128, per_slot=0, sigma_source=0, membership=0,
-        bytemap_log2=24, rename_every=0, parallel=False):
+        bytemap_log2=24, rename_every=0, parallel=False, rng=0):
     """Fig. 4 for ``epochs`` iterations from state (x, sigma); returns (x, sigma, stats).
     parallel: the OpenMP build (all host threads; sums in another order)."""
     n = len(row_ptr) - 1
@@ -345,7 +358,7 @@ def run(row_ptr, col_idx, x, sigma, epochs, seed, k, epoch0=0, mu=MU, max_retrie
     rc = (_load_omp() if parallel else _load()).orc_run(n, _i32(row_ptr), _i32(col_idx), x.shape[1], x, ctypes.byref(s), mu,
                          epoch0, epochs, seed, k, max_retries, symmetric, w_formula, clamp_neg_d,
                          z_min, hist_bins, hist_max, sigma_every, st, block_partners, tile_vertices, per_slot, sigma_source,
-                         membership, bytemap_log2, rename_every)
+                         membership, bytemap_log2, rename_every, rng)
     if rc != 0:
         raise MemoryError("oracle run failed")
     return x, s.value, dict(accepted=int(st[0]), rejected=int(st[1]), exhausted=int(st[2]), false_pos=int(st[4]))

@@ -15,7 +15,8 @@
  *                          formulas with the marked "-" signs turned into "+"
  *                          for non-edges (Sec. II.C)
  *   orc_epoch              one iteration of Fig. 4: zero y,z; edge parabolas;
- *                          sampled non-edges (Fig. 2 semantics, Sec. III.C);
+ *                          sampled non-edges (Fig. 2 semantics, Sec. III.C;
+ *                          Philox draws, or Sec. III.C's LCG with rng 1);
  *                          Eq. 3 numerators/denominators; x_i := y_i / z_i;
  *                          distance histograms (Sec. III.F)
  *   orc_sigma_fit          Sec. III.F: bisection for dPE/dsigma = 0 on the
@@ -65,7 +66,11 @@
  *                      histogram pass of Sec. III.F)
  *   renaming           (period, 0, 0, 0x09000000)     -> words 0, 1 (byte-map
  *                      membership, Sec. III.C)
- * A 32-bit word r maps to vertex floor(r * n / 2^32).
+ *   LCG seeds (rng 1)  (i, epoch, t>>2, 0x08000000)   -> word t&3: the state of
+ *                      sample slot t of vertex i; (e>>2, epoch, 0, 0x07000000)
+ *                      -> word e&3: the state of CSR slot e (per-slot policy)
+ * A 32-bit word r maps to vertex floor(r * n / 2^32); with rng 1 attempt a of
+ * a slot draws lcg_vertex of the slot's state advanced a + 1 times.
  *
  * Block sampling (the representation-learning form): vertices are cut into
  * tiles of T consecutive ids; every vertex of a tile takes the same P
@@ -130,6 +135,33 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 static uint32_t draw_vertex(uint32_t r, uint32_t n) { return (uint32_t)(((uint64_t)r * n) >> 32); }
+
+/* Sec. III.C's generator for the non-edge partners (rng = 1): a 32-bit
+ * linear congruential generator with multiplier 1103515245 and increment 1,
+ * state := state * 1103515245 + 1 (mod 2^32), advanced before every draw as
+ * Fig. 2 advances its state vector. */
+static uint32_t lcg_next(uint32_t s) { return s * 1103515245u + 1u; }
+
+/* Fig. 2's map of a state to a vertex, in FP32 with one rounding per
+ * operation: the low 23 bits of the state as the mantissa of a float f in
+ * [1, 2), then f * n - n, rounded to the nearest integer (ties to even).
+ * Reading: the rounding can reach n, which is taken as vertex 0 (so every
+ * vertex gets an interval of width one); for n > 2^23 only 2^23 vertices are
+ * reachable, as with the paper's 23-bit mantissa. */
+static int32_t lcg_vertex(uint32_t s, int32_t n) {
+    uint32_t bits = 0x3F800000u | (s & 0x007FFFFFu);
+    float f, nf = (float)n;
+    memcpy(&f, &bits, sizeof f);
+    float t = f * nf;
+    t = t - nf;
+    int32_t g = (int32_t)rintf(t);
+    if (g >= n) g -= n;
+    return g;
+}
+
+/* Inspection: the generator's next state and the vertex of a state. */
+uint32_t orc_lcg_next(uint32_t s) { return lcg_next(s); }
+int32_t orc_lcg_vertex(uint32_t s, int32_t n) { return lcg_vertex(s, n); }
 
 static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int word) {
     uint32_t ctr[4] = { c0, c1, c2, c3 };
@@ -351,12 +383,19 @@ static int sampler_is_edge(const orc_bytemap* m, const int32_t* row_ptr, const i
 static void sample_vertex_bm(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
                              int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
                              const orc_bytemap* bm, int32_t* out, int64_t* rejected, int64_t* exhausted,
-                             int64_t* false_pos) {
+                             int64_t* false_pos, int32_t rng) {
     for (int32_t t = 0; t < k; ++t) {
         int32_t got = -1;
+        uint32_t state = rng ? philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t >> 2, 0x08000000u, t & 3) : 0u;
         for (int32_t a = 0; a < max_retries; ++a) {
-            uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t >> 2, tag | (uint32_t)a, t & 3);
-            int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
+            int32_t g;
+            if (rng) {
+                state = lcg_next(state);
+                g = lcg_vertex(state, n);
+            } else {
+                uint32_t r = philox_word(seed, (uint32_t)i, (uint32_t)epoch, (uint32_t)t >> 2, tag | (uint32_t)a, t & 3);
+                g = (int32_t)draw_vertex(r, (uint32_t)n);
+            }
             if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;
         }
@@ -369,7 +408,7 @@ static void sample_vertex(const int32_t* row_ptr, const int32_t* col_idx, int32_
                           int32_t epoch, uint64_t seed, uint32_t tag, int32_t k, int32_t max_retries,
                           int32_t* out, int64_t* rejected, int64_t* exhausted) {
     sample_vertex_bm(row_ptr, col_idx, n, i, epoch, seed, tag, k, max_retries, NULL, out, rejected, exhausted,
-                     NULL);
+                     NULL, 0);
 }
 
 /* Byte-map addresses of pairs under the renaming of `period` (inspection). */
@@ -391,12 +430,19 @@ void orc_bytemap_addr(int32_t n, uint64_t seed, int32_t period, int32_t log2_siz
  * row_ptr[i] + t, or -1. */
 static void sample_slots(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t i,
                          int32_t epoch, uint64_t seed, int32_t max_retries, const orc_bytemap* bm, int32_t* out,
-                         int64_t* rejected, int64_t* exhausted, int64_t* false_pos) {
+                         int64_t* rejected, int64_t* exhausted, int64_t* false_pos, int32_t rng) {
     for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int32_t got = -1;
+        uint32_t state = rng ? philox_word(seed, (uint32_t)e >> 2, (uint32_t)epoch, 0u, 0x07000000u, e & 3) : 0u;
         for (int32_t a = 0; a < max_retries; ++a) {
-            uint32_t r = philox_word(seed, (uint32_t)e >> 2, (uint32_t)epoch, 0u, 0x0C000000u | (uint32_t)a, e & 3);
-            int32_t g = (int32_t)draw_vertex(r, (uint32_t)n);
+            int32_t g;
+            if (rng) {
+                state = lcg_next(state);
+                g = lcg_vertex(state, n);
+            } else {
+                uint32_t r = philox_word(seed, (uint32_t)e >> 2, (uint32_t)epoch, 0u, 0x0C000000u | (uint32_t)a, e & 3);
+                g = (int32_t)draw_vertex(r, (uint32_t)n);
+            }
             if (g != i && !sampler_is_edge(bm, row_ptr, col_idx, i, g, false_pos)) { got = g; break; }
             if (rejected) ++*rejected;
         }
@@ -431,7 +477,7 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               double* y, double* z, double* x_new, double* hist_e, double* hist_n,
               int32_t* samples_out, int64_t* stats, double* absd,
               int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
-              int32_t membership, int32_t bytemap_log2, int32_t rename_every) {
+              int32_t membership, int32_t bytemap_log2, int32_t rename_every, int32_t rng) {
     /* block sampling or the per-slot policy replace the k per-vertex samples */
     if (block_P > 0) { k = 0; per_slot = 0; }
     /* membership 1: the sampler tests pairs against the byte map of the
@@ -490,10 +536,10 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
         int32_t ki = k;
         if (per_slot) {
             ki = row_ptr[i + 1] - row_ptr[i];
-            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, bmp, smp, &rej_t, &exh_t, &fp_t);
+            sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, bmp, smp, &rej_t, &exh_t, &fp_t, rng);
         } else {
             sample_vertex_bm(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, bmp, smp,
-                             &rej_t, &exh_t, &fp_t);
+                             &rej_t, &exh_t, &fp_t, rng);
         }
         int32_t acc = 0;
         for (int32_t t = 0; t < ki; ++t) acc += (smp[t] >= 0);
@@ -669,7 +715,7 @@ int orc_vertex_terms(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
                 if (smp[p] == v || orc_is_edge(row_ptr, col_idx, v, smp[p])) smp[p] = -1;   /* masked */
             kv = block_P;
         } else if (per_slot) {
-            sample_slots(row_ptr, col_idx, n, v, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL);
+            sample_slots(row_ptr, col_idx, n, v, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL, 0);
             kv = row_ptr[v + 1] - row_ptr[v];
         } else {
             sample_vertex(row_ptr, col_idx, n, v, epoch, seed, 0x0B000000u, k, max_retries, smp, NULL, NULL);
@@ -696,7 +742,7 @@ int orc_vertex_terms(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, 
             for (int32_t i = 0; i < n; ++i) {
                 int32_t ki = per_slot ? row_ptr[i + 1] - row_ptr[i] : k;
                 if (per_slot)
-                    sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL);
+                    sample_slots(row_ptr, col_idx, n, i, epoch, seed, max_retries, NULL, smp, NULL, NULL, NULL, 0);
                 else
                     sample_vertex(row_ptr, col_idx, n, i, epoch, seed, 0x0B000000u, k, max_retries, smp, NULL,
                                   NULL);
@@ -872,7 +918,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
             int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula, int32_t clamp_neg_d,
             double z_min, int32_t B, double hist_max, int32_t sigma_every, int64_t* stats,
             int32_t block_P, int32_t block_T, int32_t per_slot, int32_t sigma_source, int32_t membership,
-            int32_t bytemap_log2, int32_t rename_every) {
+            int32_t bytemap_log2, int32_t rename_every, int32_t rng) {
     size_t nd = (size_t)n * d;
     double* y = (double*)malloc(nd * sizeof(double));
     double* z = (double*)malloc((size_t)n * sizeof(double));
@@ -886,7 +932,7 @@ int orc_run(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d
         int32_t ep = epoch0 + e;
         orc_epoch(n, row_ptr, col_idx, d, x, *sigma, mu, ep, seed, k, max_retries, symmetric,
                   w_formula, clamp_neg_d, z_min, B, hist_max, y, z, xn, he, hn, NULL, st, NULL,
-                  block_P, block_T, NULL, per_slot, membership, bytemap_log2, rename_every);
+                  block_P, block_T, NULL, per_slot, membership, bytemap_log2, rename_every, rng);
         memcpy(x, xn, nd * sizeof(double));
         if (sigma_every > 0 && ((ep + 1) % sigma_every) == 0) {
             /* sigma_source 1: histograms of a separate pass at the new positions */

@@ -722,3 +722,90 @@ def test_golden_closed_forms_reproduce():
     spec.loader.exec_module(gen)
     with open(os.path.join(HERE, "golden", "parabola_closed_forms.txt")) as f:
         assert f.read() == gen.text()
+
+
+# ---------------------------------------------------------------------------
+# Sec. III.C's LCG and Fig. 2's float trick (rng = 1)
+# ---------------------------------------------------------------------------
+def _lcg_vertex_restated(state, n):
+    """Fig. 2's map in numpy FP32: mantissa bits of the state in [1, 2), times
+    n minus n (one FP32 rounding each), rounded to nearest-even; n is vertex 0."""
+    f = np.array([0x3F800000 | (state & 0x7FFFFF)], dtype=np.uint32).view(np.float32)[0]
+    nf = np.float32(n)
+    t = np.float32(f * nf)
+    t = np.float32(t - nf)
+    g = int(np.rint(t))
+    return g - n if g >= n else g
+
+
+def test_lcg_step_and_vertex_map(oracle_mod):
+    """The generator is s -> 1103515245 s + 1 mod 2^32; the map sends mantissa
+    0 to vertex 0, mantissa 2^22 (f = 1.5) to n/2 (ties to even for odd n),
+    the largest mantissa (f = 2 - 2^-23) to n, read as 0, for n < 2^22."""
+    s = 12345
+    for _ in range(50):
+        nxt = oracle_mod.lcg_next(s)
+        assert nxt == (s * 1103515245 + 1) % (1 << 32)
+        s = nxt
+    assert oracle_mod.lcg_next(0xFFFFFFFF) == (0xFFFFFFFF * 1103515245 + 1) % (1 << 32)
+    for n in (2, 7, 97, 1000, 65537, 1000000):
+        assert oracle_mod.lcg_vertex(0xABC00000 & ~0x7FFFFF, n) == 0
+        half = oracle_mod.lcg_vertex(0x00400000, n)
+        assert half == (n // 2 if n % 2 == 0 or (n // 2) % 2 == 0 else n // 2 + 1)
+        assert oracle_mod.lcg_vertex(0x007FFFFF, n) == 0
+    rng = np.random.default_rng(8)
+    for n in (3, 60, 1001, 131072, 2_000_003):
+        for st in rng.integers(0, 1 << 32, 300, dtype=np.uint64).tolist():
+            g = oracle_mod.lcg_vertex(st, n)
+            assert 0 <= g < n and g == _lcg_vertex_restated(int(st), n)
+
+
+def test_lcg_vertices_uniform(oracle_mod):
+    n, draws = 97, 97 * 400
+    counts = np.zeros(n)
+    s = 2024
+    for _ in range(draws):
+        s = (s * 1103515245 + 1) % (1 << 32)
+        counts[oracle_mod.lcg_vertex(s, n)] += 1
+    chi2 = ((counts - draws / n) ** 2 / (draws / n)).sum()
+    from scipy.stats import chi2 as chi2d
+    assert chi2d.sf(chi2, n - 1) > 1e-4
+
+
+@pytest.mark.parametrize("per_slot", [0, 1])
+def test_lcg_samples_replayed(oracle_mod, sbm_small, per_slot):
+    """rng = 1: every sample slot's state is seeded from its Philox word
+    ((i, epoch, t>>2, 0x08000000) word t&3; per-slot policy (e>>2, epoch, 0,
+    0x07000000) word e&3) and advanced once per attempt (Fig. 2: the state
+    moves before each draw); a draw of the anchor itself or a neighbour is
+    redrawn.  Replayed here attempt by attempt from the definition."""
+    rp, ci = sbm_small
+    n = len(rp) - 1
+    adj = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(n)]
+    seed, epoch, k = 4242, 3, 6
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    x = np.random.default_rng(2).normal(size=(n, 2))
+    r = oracle_mod.epoch(rp, ci, x, 0.9, epoch, seed, k, per_slot=per_slot, rng=1)
+    ref = oracle_mod.epoch(rp, ci, x, 0.9, epoch, seed, k, per_slot=per_slot, rng=0)
+    assert not np.array_equal(r["samples"], ref["samples"])
+    rej = 0
+    slots = [(i, rp[i] + t if per_slot else t) for i in range(n)
+             for t in (range(rp[i + 1] - rp[i]) if per_slot else range(k))]
+    got = r["samples"].reshape(-1)
+    for i, t in slots:
+        if per_slot:
+            st = int(oracle_mod.philox4x32_10([t >> 2, epoch, 0, 0x07000000], key)[t & 3])
+            out = got[t]
+        else:
+            st = int(oracle_mod.philox4x32_10([i, epoch, t >> 2, 0x08000000], key)[t & 3])
+            out = got[i * k + t]
+        want = -1
+        for _ in range(32):
+            st = (st * 1103515245 + 1) % (1 << 32)
+            g = _lcg_vertex_restated(st, n)
+            if g != i and g not in adj[i]:
+                want = g
+                break
+            rej += 1
+        assert out == want, (i, t)
+    assert r["rejected"] == rej
