@@ -97,6 +97,14 @@ typedef struct gempe_params {
                                to n, drawn from counter (period, 0, 0, 0x09000000)) is redrawn and
                                the map rebuilt every rename_every epochs (period = sample epoch /
                                rename_every); 0: one renaming for the whole run */
+    int32_t rng;            /* random numbers of the sampled non-edges (k per vertex or per slot):
+                               0: Philox4x32-10, attempt a of a slot from its own counter;
+                               1: Sec. III.C's LCG (state := state * 1103515245 + 1 mod 2^32), one
+                               state per sample slot seeded from Philox, advanced before every draw,
+                               the vertex by Fig. 2's FP32 float trick (mantissa bits in [1, 2),
+                               times n minus n, rounded to nearest; n wraps to vertex 0); not with
+                               block sampling.  The loss estimator and the separate histogram pass
+                               keep Philox */
     /* Optional device allocator (e.g. a framework's caching allocator).  When
      * dev_alloc is null the engine uses cudaMalloc / cudaFree. */
     void* (*dev_alloc)(size_t bytes, void* user);
@@ -204,7 +212,7 @@ gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
  * positions, sigma, the epoch counter and the sampler statistics, with the
  * graph's n, d and nnz and the parameters that key the draws (seed,
  * neg_per_vertex, max_retries, sampling, block_partners, tile_vertices,
- * membership and, with the byte map, bytemap_log2 and rename_every) and the
+ * membership, rng and, with the byte map, bytemap_log2 and rename_every) and the
  * parameters of the run's arithmetic (mu, hist_max, z_min, hist_bins,
  * sigma_every, sigma_source, precision, symmetric_neg, w_formula,
  * clamp_neg_d).  A context created from the same graph with those parameters
@@ -212,7 +220,7 @@ gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
  * samples, sigma and statistics, positions up to the order of FP32 atomic
  * additions.  The graph itself is checked only by n and nnz; the remaining
  * parameters (autotune, the allocator) do not change the run.
- * Plain little-endian bytes: a 176-byte header, then float[n*d].
+ * Plain little-endian bytes: a 184-byte header, then float[n*d].
  *
  * gempe_save: buf NULL -> *len = the bytes needed, GEMPE_OK.  Otherwise *len
  * must be at least that (else GEMPE_E_INVALID_ARG, *len set to the size

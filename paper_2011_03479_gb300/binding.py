@@ -51,6 +51,7 @@ class gempe_params(ctypes.Structure):
         ("membership", ctypes.c_int32),
         ("bytemap_log2", ctypes.c_int32),
         ("rename_every", ctypes.c_int32),
+        ("rng", ctypes.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),

@@ -377,9 +377,9 @@ struct CheckpointHeader {
     // the parameters of the run's arithmetic (version 2)
     float mu, hist_max, z_min;
     int32_t hist_bins, sigma_every, sigma_source, precision;
-    int32_t symmetric_neg, w_formula, clamp_neg_d;
+    int32_t symmetric_neg, w_formula, clamp_neg_d, rng, reserved2;
 };
-static_assert(sizeof(CheckpointHeader) == 176, "checkpoint header layout");
+static_assert(sizeof(CheckpointHeader) == 184, "checkpoint header layout");
 
 constexpr char kCheckpointMagic[8] = {'G', 'E', 'M', 'P', 'E', 'C', 'K', '\x01'};
 constexpr uint32_t kCheckpointVersion = 2;
@@ -396,10 +396,11 @@ gempe_status checkpoint_matches(const CheckpointHeader& h, const gempe_ctx* c) {
     if (h.n != c->n || h.d != pk.d || h.nnz != pk.nnz[0])
         return fail(GEMPE_E_INVALID_ARG, "checkpoint of another graph: n, d or nnz differ");
     if (h.seed != p.seed || h.k != p.neg_per_vertex || h.max_retries != p.max_retries || h.sampling != p.sampling ||
-        h.block_partners != p.block_partners || h.tile_vertices != p.tile_vertices || h.membership != p.membership)
+        h.block_partners != p.block_partners || h.tile_vertices != p.tile_vertices || h.membership != p.membership ||
+        h.rng != p.rng)
         return fail(GEMPE_E_INVALID_ARG,
                     "checkpoint of other sampling parameters: seed, neg_per_vertex, max_retries, sampling, "
-                    "block_partners, tile_vertices or membership differ");
+                    "block_partners, tile_vertices, membership or rng differ");
     if (p.membership == 1 && (h.bytemap_log2 != p.bytemap_log2 || h.rename_every != p.rename_every))
         return fail(GEMPE_E_INVALID_ARG, "checkpoint of another byte map: bytemap_log2 or rename_every differ");
     if (h.mu != p.mu || h.hist_max != p.hist_max || h.z_min != p.z_min || h.hist_bins != p.hist_bins ||
@@ -471,6 +472,7 @@ GEMPE_API gempe_status gempe_save(gempe_ctx* c, void* buf, size_t* len) {
     h.symmetric_neg = pk.p.symmetric_neg;
     h.w_formula = pk.p.w_formula;
     h.clamp_neg_d = pk.p.clamp_neg_d;
+    h.rng = pk.p.rng;
     std::memcpy(out, &h, sizeof(h));
     *len = need;
     return GEMPE_OK;

@@ -29,6 +29,22 @@ __device__ __forceinline__ uint32_t word_of(const uint4& r, int w) {
 // Random 32-bit word -> vertex in [0, n): floor(r * n / 2^32).
 __device__ __forceinline__ int32_t draw_vertex(uint32_t r, uint32_t n) { return (int32_t)__umulhi(r, n); }
 
+// Sec. III.C's 32-bit linear congruential generator (multiplier 1103515245,
+// increment 1), advanced before each draw as in Fig. 2.
+__device__ __forceinline__ uint32_t lcg_next(uint32_t s) { return s * 1103515245u + 1u; }
+
+// Fig. 2's vertex of a state: the low 23 bits as the mantissa of f in [1, 2),
+// then f * n - n and a round to nearest (ties to even), each an FP32
+// operation with one rounding; the value n that rounding can reach is
+// vertex 0.
+__device__ __forceinline__ int32_t lcg_vertex(uint32_t s, int32_t n) {
+    const float f = __uint_as_float(0x3F800000u | (s & 0x007FFFFFu));
+    const float nf = __int2float_rn(n);
+    const float t = __fsub_rn(__fmul_rn(f, nf), nf);
+    const int32_t g = __float2int_rn(t);
+    return g >= n ? g - n : g;
+}
+
 // Stream tags in the fourth counter word.
 constexpr uint32_t kTagInit = 0x0A000000u;
 constexpr uint32_t kTagEpoch = 0x0B000000u;

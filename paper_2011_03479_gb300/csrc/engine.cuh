@@ -88,6 +88,8 @@ constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
 inline size_t hist_smem_bytes(int bins) { return (size_t)bins * 4 * sizeof(unsigned int); }
 
 constexpr uint32_t kTagSlot = 0x0C000000u;   // counter tag of the per-slot samples
+constexpr uint32_t kTagLcg = 0x08000000u;    // LCG seeds of the per-vertex sample slots (rng 1)
+constexpr uint32_t kTagLcgSlot = 0x07000000u;   // LCG seeds of the per-slot samples (rng 1)
 
 inline size_t packed_smem_bytes(int d, int bins) {
     const int as = ((d + 1) + 3) / 4 * 4;
@@ -150,6 +152,7 @@ struct EpochArgs {
     int32_t membership;       // 0: the exact edge sets; 1: the byte maps
     int32_t rename_every;     // 0: one renaming (period 0) for the whole run
     uint8_t* bytemap;
+    int32_t rng;              // 1: Sec. III.C's LCG draws the epoch's sampled non-edges
 };
 
 int acc_stride_for(int d);

@@ -274,6 +274,21 @@ __device__ __forceinline__ int sample_partner_from(const GraphInfo& gi, const Ed
     return -1;
 }
 
+// The LCG form (rng 1) of sample_partner_from: the slot's state after the
+// attempts before att0; each further attempt advances it once and draws.
+__device__ __forceinline__ int lcg_partner_from(const GraphInfo& gi, const EdgeSets& keys, int max_retries, int i,
+                                                uint32_t state, int att0, unsigned& rejected, const Membership& m,
+                                                unsigned& false_pos) {
+    const uint32_t name_i = m.map ? renamed(m, (uint32_t)i) : 0u;
+    for (int att = att0; att < max_retries; ++att) {
+        state = lcg_next(state);
+        const int g = lcg_vertex(state, gi.n);
+        if (g != i && !taken_for_edge(gi, keys, m, name_i, i, g, false_pos)) return g;
+        ++rejected;
+    }
+    return -1;
+}
+
 // All attempts of slot t of local vertex i.
 __device__ __forceinline__ int sample_partner(const GraphInfo& gi, const EdgeSets& keys, int max_retries, int i,
                                               int epoch, int t, uint32_t tag, unsigned& rejected,
@@ -411,17 +426,26 @@ __global__ void __launch_bounds__(256, kMap ? 3 : 5) k_sampler(const EpochArgs a
         if (vi < cnt) {
             const int i = row0 - gi.v0 + vi;
             const uint32_t name_i = kMap ? renamed(m, (uint32_t)i) : 0u;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)q, kTagEpoch),
+            // Philox: attempt 0 of the four slots; LCG (rng 1): the four slots' seeds
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)se, (uint32_t)q, a.rng ? kTagLcg : kTagEpoch),
                                           gi.key_lo, gi.key_hi);
             int32_t* out = a.samples + ((size_t)(se & 1) * a.rows + row0 + vi) * k;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int t = 4 * q + w;
                 if (t >= k) break;
-                int g = draw_vertex(word_of(r, w), (uint32_t)gi.n);
+                uint32_t st = word_of(r, w);
+                int g;
+                if (a.rng) {
+                    st = lcg_next(st);
+                    g = lcg_vertex(st, gi.n);
+                } else {
+                    g = draw_vertex(st, (uint32_t)gi.n);
+                }
                 if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
                     ++c[1];
-                    g = sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
+                    g = a.rng ? lcg_partner_from(gi, es, a.max_retries, i, st, 1, c[1], m, c[3])
+                              : sample_partner_from(gi, es, a.max_retries, i, se, t, kTagEpoch, 1, c[1], m, c[3]);
                 }
                 out[t] = g >= 0 ? gi.v0 + g : -1;
                 if (g >= 0) ++c[0]; else ++c[2];
@@ -529,15 +553,24 @@ __global__ void __launch_bounds__(256) k_sampler_slots(const EpochArgs a) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (s_rp[mid] <= ea) lo = mid; else hi = mid - 1;
             }
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)se, 0u, kTagSlot), gi.key_lo, gi.key_hi);
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)se, 0u, a.rng ? kTagLcgSlot : kTagSlot),
+                                          gi.key_lo, gi.key_hi);
             for (int e = ea; e < eb; ++e) {
                 while (s_rp[lo + 1] <= e) ++lo;   // rows may be empty
                 const int i = row0 + lo - gi.v0, el = e - s0;
                 const uint32_t name_i = kMap ? renamed(m, (uint32_t)i) : 0u;
-                int g = draw_vertex(word_of(r, el & 3), (uint32_t)gi.n);
+                uint32_t st = word_of(r, el & 3);
+                int g;
+                if (a.rng) {
+                    st = lcg_next(st);
+                    g = lcg_vertex(st, gi.n);
+                } else {
+                    g = draw_vertex(st, (uint32_t)gi.n);
+                }
                 if (g == i || taken_for_edge(gi, es, m, name_i, i, g, c[3])) {
                     ++c[1];
-                    g = slot_partner_from(gi, es, a.max_retries, i, el, se, 1, c[1], m, c[3]);
+                    g = a.rng ? lcg_partner_from(gi, es, a.max_retries, i, st, 1, c[1], m, c[3])
+                              : slot_partner_from(gi, es, a.max_retries, i, el, se, 1, c[1], m, c[3]);
                 }
                 out[e] = g >= 0 ? gi.v0 + g : -1;
                 if (g >= 0) {
@@ -1493,7 +1526,17 @@ __global__ void k_sample(const EpochArgs a, uint32_t tag, int32_t* out) {
             const int v = ch.x + vi;
             unsigned rej = 0;
             if (lane < a.k) {
-                const int g = sample_partner(gi, edge_sets(a), a.max_retries, v - gi.v0, epoch, lane, tag, rej);
+                int g;
+                if (tag == kTagEpoch && a.rng) {   // the epoch's draws come from the LCG (rng 1)
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)(v - gi.v0), (uint32_t)epoch,
+                                                             (uint32_t)lane >> 2, kTagLcg), gi.key_lo, gi.key_hi);
+                    const Membership exact{nullptr, 0u, (uint32_t)gi.n, 1u, 0u};
+                    unsigned fp = 0u;
+                    g = lcg_partner_from(gi, edge_sets(a), a.max_retries, v - gi.v0, word_of(r, lane & 3), 0, rej,
+                                         exact, fp);
+                } else {
+                    g = sample_partner(gi, edge_sets(a), a.max_retries, v - gi.v0, epoch, lane, tag, rej);
+                }
                 out[(size_t)v * a.k + lane] = g >= 0 ? gi.v0 + g : -1;
             }
         }

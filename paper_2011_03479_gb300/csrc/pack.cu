@@ -67,6 +67,9 @@ gempe_status check_params(const gempe_params* p, int32_t d) {
     if (p->bytemap_log2 != 0 && (p->bytemap_log2 < 6 || p->bytemap_log2 > 32))
         return pack_fail(GEMPE_E_INVALID_ARG, "bytemap_log2 must be 0 (automatic) or in [6, 32]");
     if (p->rename_every < 0) return pack_fail(GEMPE_E_INVALID_ARG, "rename_every must be >= 0");
+    if (p->rng != 0 && p->rng != 1) return pack_fail(GEMPE_E_INVALID_ARG, "rng must be 0 or 1");
+    if (p->rng == 1 && p->block_partners)
+        return pack_fail(GEMPE_E_INVALID_ARG, "the LCG draws the sampled non-edges, not block partners");
     return GEMPE_OK;
 }
 
@@ -748,6 +751,7 @@ EpochArgs Pack::args() const {
     a.mills = mills;
     a.membership = bytemap ? 1 : 0;
     a.rename_every = p.rename_every;
+    a.rng = p.rng;
     a.bytemap = bytemap;
     return a;
 }

@@ -117,7 +117,8 @@ def test_invalid_args_rejected_on_host():
     # byte-map membership: 0/1, log2 0 or 6..32, rename_every >= 0, not with block sampling
     for kw, d in ((dict(membership=2), 2), (dict(membership=1, bytemap_log2=5), 2),
                   (dict(membership=1, bytemap_log2=33), 2), (dict(membership=1, rename_every=-1), 2),
-                  (dict(membership=1, block_partners=64), 16)):
+                  (dict(membership=1, block_partners=64), 16), (dict(rng=2), 2), (dict(rng=-1), 2),
+                  (dict(rng=1, block_partners=64), 16)):
         p = binding.gempe_default_params(**kw)
         st, _ = _status(lib.gempe_create, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data),
                         2, d, ctypes.byref(p), None)

@@ -28,8 +28,9 @@ def B():
 
 @pytest.mark.parametrize("form", [dict(neg_per_vertex=5), dict(neg_per_vertex=5, sampling=1),
                                   dict(block_partners=64, precision=1), dict(block_partners=64, precision=0),
-                                  dict(neg_per_vertex=5, membership=1, rename_every=2)],
-                         ids=["per-vertex", "per-slot", "block-bf16", "block-fp32", "bytemap"])
+                                  dict(neg_per_vertex=5, membership=1, rename_every=2),
+                                  dict(neg_per_vertex=5, rng=1)],
+                         ids=["per-vertex", "per-slot", "block-bf16", "block-fp32", "bytemap", "lcg"])
 def test_resume_continues_the_run(B, sbm_1000, form):
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     d = 16 if form.get("block_partners") else 2
@@ -42,7 +43,7 @@ def test_resume_continues_the_run(B, sbm_1000, form):
         B.gempe_step(a, 4)
         x_a = B.gempe_positions(a)
         st_a = B.gempe_stats(a)
-    assert len(blob) == 176 + 4 * x_saved.size
+    assert len(blob) == 184 + 4 * x_saved.size
     with B.gempe_create(rp, ci, d, p) as b:
         B.gempe_load(b, blob)
         st_b0 = B.gempe_stats(b)
@@ -84,6 +85,9 @@ def test_mismatched_checkpoint_refused(B, sbm_1000):
     with B.gempe_create(rp, ci, 4, p) as e:
         with pytest.raises(B.GempeError, match="another graph"):
             B.gempe_load(e, blob)
+    with B.gempe_create(rp, ci, 2, B.gempe_default_params(neg_per_vertex=5, rng=1)) as g:
+        with pytest.raises(B.GempeError, match="sampling parameters"):
+            B.gempe_load(g, blob)
     for kw in (dict(mu=1.4), dict(hist_bins=512), dict(sigma_every=2), dict(w_formula=1), dict(clamp_neg_d=0)):
         with B.gempe_create(rp, ci, 2, B.gempe_default_params(neg_per_vertex=5, **kw)) as f:
             with pytest.raises(B.GempeError, match="another run"):
