@@ -373,7 +373,7 @@ def _profile_key(workload, key):
 # ---------------------------------------------------------------------------
 # one graph: device-resident epochs, per-kernel windows, end-to-end jobs
 # ---------------------------------------------------------------------------
-def measure_single(w, form, steps, warmup, stream, flush, e2e_jobs=0, exact=False):
+def measure_single(w, form, steps, warmup, stream, flush, e2e_jobs=0, exact=False, shape=None):
     """Times `steps` epochs of workload w (after `warmup`) as gempe_step(ctx, 1),
     each bracketed by CUDA events on `stream` with an L2 flush before it;
     then as many epochs as gempe_sweep + gempe_update with the library's
@@ -391,6 +391,8 @@ def measure_single(w, form, steps, warmup, stream, flush, e2e_jobs=0, exact=Fals
     p = B.gempe_default_params(neg_per_vertex=k, seed=inputs.EMBED_SEED, **form)
     t0 = time.perf_counter()
     ctx = B.gempe_create(rp, ci, d, p, stream=stream)
+    if shape:
+        B.gempe_set_shape(ctx, **shape)
     stream.synchronize()
     create_s = time.perf_counter() - t0
     with torch.cuda.stream(stream):
@@ -444,6 +446,8 @@ def measure_single(w, form, steps, warmup, stream, flush, e2e_jobs=0, exact=Fals
 
         def job():
             c = B.gempe_create(rp_pin, ci_pin, d, p, stream=stream)
+            if shape:
+                B.gempe_set_shape(c, **shape)
             B.gempe_step(c, epochs)
             B.gempe_positions(c, out_pin)
             u = B.gempe_stats(c)["used"]

@@ -185,12 +185,13 @@ gempe_status gempe_update(gempe_ctx* ctx);
 /* Per-kernel timing of the epochs run as gempe_sweep + gempe_update (not
  * gempe_step's graph replays; the paper has no counterpart).  enable = 1:
  * those calls record CUDA events on the context's stream before the pair
- * sweep, after it, after the tile kernel of the block form and after the
- * position update (the event before the update keeps it from starting while
- * the previous kernel's last blocks run); enable = 0 stops recording.
- * out_ms3 (may be NULL) receives the windows of the last epoch recorded,
- * in milliseconds: {sweep, tiles (0 without tiles), update}; all 0 when no
- * epoch was recorded.  Synchronises on the last event when out_ms3 is set. */
+ * sweep and after it, before and after the tile kernel of the block form
+ * (on its own stream when it runs beside the sweep), after their join and
+ * after the position update (the event before the update keeps it from
+ * starting while the previous kernel's last blocks run); enable = 0 stops
+ * recording.  out_ms3 (may be NULL) receives the windows of the last epoch
+ * recorded, in milliseconds: {sweep, tiles (0 without tiles), update}; all 0
+ * when no epoch was recorded.  Synchronises on the last event when out_ms3 is set. */
 gempe_status gempe_kernel_times(gempe_ctx* ctx, int32_t enable, float* out_ms3);
 
 /* Copy the positions to host float[n*d] (synchronises).  count must be n*d. */
@@ -316,7 +317,9 @@ gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
  * shape5 = {unit pair budget of a packed unit (64 or 128, d <= 4), CSR
  * slots per work unit (8..1024, the per-unit kernel), lanes per pair (d >= 8:
  * d/8 or d/4; 0 = default), sweep CTAs per SM (0 = all that fit), kernel
- * (d <= 4: 0 packed units, 1 one lane per vertex)}.  Only the launch shape
+ * (d <= 4: 0 packed units, 1 one lane per vertex; d >= 8 in the block form
+ * with tiles: 0 the tiles after the sweep, 2 the sweep in 512-thread blocks,
+ * one per SM, beside one tile CTA per SM on a second stream)}.  Only the launch shape
  * changes, never the arithmetic of a pair; not allowed between gempe_sweep
  * and gempe_update.  gempe_get_shape: the same five, then the sweep grid. */
 gempe_status gempe_set_shape(gempe_ctx* ctx, const int32_t* shape5);

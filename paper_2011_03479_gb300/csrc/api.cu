@@ -284,13 +284,13 @@ GEMPE_API gempe_status gempe_kernel_times(gempe_ctx* c, int32_t enable, float* o
     if (out_ms3) {
         out_ms3[0] = out_ms3[1] = out_ms3[2] = 0.0f;
         if (c->timed) {
-            CK(cudaEventSynchronize(pk.tev[3]), "synchronize");
+            CK(cudaEventSynchronize(pk.tev[5]), "synchronize");
             CK(cudaEventElapsedTime(&out_ms3[0], pk.tev[0], pk.tev[1]), "elapsed");
             if (pk.tiles) {
-                CK(cudaEventElapsedTime(&out_ms3[1], pk.tev[1], pk.tev[2]), "elapsed");
-                CK(cudaEventElapsedTime(&out_ms3[2], pk.tev[2], pk.tev[3]), "elapsed");
-            } else {   // no tile kernel: the gap between its two events goes to the update's window
-                CK(cudaEventElapsedTime(&out_ms3[2], pk.tev[1], pk.tev[3]), "elapsed");
+                CK(cudaEventElapsedTime(&out_ms3[1], pk.tev[2], pk.tev[3]), "elapsed");
+                CK(cudaEventElapsedTime(&out_ms3[2], pk.tev[4], pk.tev[5]), "elapsed");
+            } else {   // no tile kernel: the gap between its events goes to the update's window
+                CK(cudaEventElapsedTime(&out_ms3[2], pk.tev[1], pk.tev[5]), "elapsed");
             }
         }
     }

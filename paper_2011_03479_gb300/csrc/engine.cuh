@@ -182,8 +182,12 @@ cudaError_t launch_init_positions(float* x, __nv_bfloat16* xb, int32_t n, int32_
 struct SweepShape {
     int grid = 0;
     int lanes = 0;      // d >= 8: lanes per pair (0: d / 8)
-    int kernel = 0;     // d <= 4: 0 packed units, 1 one lane per vertex (the d >= 8 kernel with G = 1)
+    int kernel = 0;     // d <= 4: 0 packed units, 1 one lane per vertex (the d >= 8 kernel with G = 1);
+                        // d >= 8 with tiles: 2 the sweep beside the tile kernel (kSweepThreadsBeside per block)
 };
+// Threads of a d >= 8 sweep block that shares its SM with a tile CTA: half the
+// register file, so that one block of each kernel is resident on every SM.
+constexpr int kSweepThreadsBeside = 512;
 cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream_t s);
 int sweep_grid(int d, int lanes, int bins, int sm_count, int blocks_per_sm, int kernel);
 bool sweep_lanes_supported(int d, int lanes);

@@ -1,0 +1,34 @@
+// Packed FP32 pairs (sm_100 and later): one instruction applies add, sub or
+// fma to both halves of a 64-bit register pair, each half rounded as the
+// scalar FP32 operation (round to nearest even), so a packed loop gives
+// the same numbers as the scalar loop it replaces with half the issue slots.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gempe {
+
+using f2 = unsigned long long;   // {lo, hi} FP32 pair in one 64-bit register
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+}  // namespace gempe

@@ -1647,9 +1647,9 @@ __global__ void k_is_edge(const void* keys, int narrow, unsigned long long key_o
 #define GEMPE_LOSS_DIMS(X) X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(8, 1) X(16, 2) X(32, 4) X(64, 8) X(128, 16) X(256, 32)
 
 template <int D, int G>
-cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s) {
-    if (a.xb) return launch_critical(k_sweep<D, G, __nv_bfloat16>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, false, a);
-    return launch_critical(k_sweep<D, G, float>, grid, kSweepThreads, hist_smem_bytes(a.bins), s, false, a);
+cudaError_t wide_sweep(const EpochArgs& a, int grid, cudaStream_t s, int threads = kSweepThreads) {
+    if (a.xb) return launch_critical(k_sweep<D, G, __nv_bfloat16>, grid, threads, hist_smem_bytes(a.bins), s, false, a);
+    return launch_critical(k_sweep<D, G, float>, grid, threads, hist_smem_bytes(a.bins), s, false, a);
 }
 
 template <int D>
@@ -1785,7 +1785,8 @@ cudaError_t launch_sweep(const EpochArgs& a, const SweepShape& shape, cudaStream
 #undef GEMPE_CASE
         default:
 #define GEMPE_CASE(D, G) \
-    if (a.d == D && lanes == G) return wide_sweep<D, G>(a, shape.grid, s);
+    if (a.d == D && lanes == G) \
+        return wide_sweep<D, G>(a, shape.grid, s, shape.kernel == 2 ? kSweepThreadsBeside : kSweepThreads);
             GEMPE_WIDE(GEMPE_CASE)
 #undef GEMPE_CASE
             return cudaErrorInvalidValue;

@@ -265,7 +265,11 @@ unsigned long long table_slots(int64_t nnz) {
 Pack::~Pack() {
     if (stream) cudaStreamSynchronize(stream);
     if (side) cudaStreamSynchronize(side);
+    if (tile_stream) cudaStreamSynchronize(tile_stream);
     release_all();
+    if (tile_fork) cudaEventDestroy(tile_fork);
+    if (tile_join) cudaEventDestroy(tile_join);
+    if (tile_stream) cudaStreamDestroy(tile_stream);
     if (fork_ev) cudaEventDestroy(fork_ev);
     if (join_ev) cudaEventDestroy(join_ev);
     for (cudaEvent_t& e : tev)
@@ -402,6 +406,11 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     PK(ensure_mills_table(), "Mills table");
     PK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device), "cudaDeviceGetAttribute");
     PK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (tiles) {
+        PK(cudaStreamCreateWithPriority(&tile_stream, cudaStreamNonBlocking, critical_priority()), "cudaStreamCreate");
+        PK(cudaEventCreateWithFlags(&tile_fork, cudaEventDisableTiming), "cudaEventCreate");
+        PK(cudaEventCreateWithFlags(&tile_join, cudaEventDisableTiming), "cudaEventCreate");
+    }
     PK(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming), "cudaEventCreate");
     PK(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming), "cudaEventCreate");
     mills = mills_table_device();
@@ -582,7 +591,6 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
 
     sampler_grid = gempe::sampler_grid(rows, k, sm_count);
     update_grid = G + std::min<int>(sm_count * 2, std::max(n_vchunks, 1));
-    tile_grid = gempe::tile_grid(n_tile_items, sm_count, p.precision == 1 ? 0 : tile_f32_blocks_per_sm(d, bins));
     // with autotuning the shape is set by autotune(), which the owner calls next
     return p.autotune ? GEMPE_OK : set_shape(PackShape{});
 }
@@ -618,7 +626,9 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
 gempe_status Pack::set_shape(const PackShape& s) {
     PackShape sh = s;
     if (!sweep_lanes_supported(d, sh.lanes)) return pack_fail(GEMPE_E_INVALID_ARG, "unsupported lanes per pair");
-    if (sh.kernel != 0 && (sh.kernel != 1 || d > kPackedMaxDim))
+    if (sh.kernel == 2 && !tiles)
+        return pack_fail(GEMPE_E_INVALID_ARG, "kernel 2 (the sweep beside the tiles) needs block sampling with tiles");
+    if (sh.kernel != 0 && sh.kernel != 2 && (sh.kernel != 1 || d > kPackedMaxDim))
         return pack_fail(GEMPE_E_INVALID_ARG, "kernel 1 (one lane per vertex) is for d <= 4");
     if (sh.unit_pairs != 64 && sh.unit_pairs != 128) return pack_fail(GEMPE_E_INVALID_ARG, "unit pairs: 64 or 128");
     if (sh.edge_chunk < 8 || sh.edge_chunk > 1024) return pack_fail(GEMPE_E_INVALID_ARG, "edge chunk in [8, 1024]");
@@ -633,7 +643,9 @@ gempe_status Pack::set_shape(const PackShape& s) {
                          per_slot, units);
         else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, per_slot, units);
     }
-    const int grid = gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm, sh.kernel);
+    // kernel 2: one sweep block of kSweepThreadsBeside threads per SM (the
+    // tile kernel takes the other half of every SM's registers)
+    const int grid = sh.kernel == 2 ? sm_count : gempe::sweep_grid(d, sh.lanes, bins, sm_count, sh.blocks_per_sm, sh.kernel);
     std::vector<int32_t> bounds;
     if (per_unit) {
         const int lanes = sh.lanes ? sh.lanes : (d <= kPackedMaxDim ? 1 : d / 8);
@@ -691,6 +703,8 @@ gempe_status Pack::set_shape(const PackShape& s) {
     }
     PK(cudaStreamSynchronize(stream), "copy work units");
     sweep_grid = grid;
+    tile_grid = gempe::tile_grid(n_tile_items, sm_count,
+                                 sh.kernel == 2 ? 1 : (p.precision == 1 ? 0 : tile_f32_blocks_per_sm(d, bins)));
     shape = sh;
     return GEMPE_OK;
 }
@@ -789,13 +803,27 @@ gempe_status Pack::enqueue_sweep() {
     ss.grid = sweep_grid;
     ss.lanes = shape.lanes;
     ss.kernel = shape.kernel;
+    // kernel 2: the tiles on tile_stream, beside the sweep (both only add into
+    // the sums and bins, by atomics), joined before the update
+    const bool beside = tiles && shape.kernel == 2;
+    cudaStream_t ts = beside ? tile_stream : stream;
+    if (beside) {
+        PK(cudaEventRecord(tile_fork, stream), "fork");
+        PK(cudaStreamWaitEvent(tile_stream, tile_fork, 0), "fork");
+    }
     if (time_kernels) PK(cudaEventRecord(tev[0], stream), "timing event");
     PK(launch_sweep(args(), ss, stream), "sweep");
     if (time_kernels) PK(cudaEventRecord(tev[1], stream), "timing event");
+    if (time_kernels) PK(cudaEventRecord(tev[2], ts), "timing event");
     if (tiles)
-        PK(p.precision == 1 ? launch_tile_bf16(args(), tile_grid, stream) : launch_tile_f32(args(), tile_grid, stream),
+        PK(p.precision == 1 ? launch_tile_bf16(args(), tile_grid, ts) : launch_tile_f32(args(), tile_grid, ts),
            "tiles");
-    if (time_kernels) PK(cudaEventRecord(tev[2], stream), "timing event");
+    if (time_kernels) PK(cudaEventRecord(tev[3], ts), "timing event");
+    if (beside) {
+        PK(cudaEventRecord(tile_join, tile_stream), "join");
+        PK(cudaStreamWaitEvent(stream, tile_join, 0), "join");
+    }
+    if (time_kernels) PK(cudaEventRecord(tev[4], stream), "timing event");
     if (fork) {
         PK(cudaStreamWaitEvent(side, fork_ev, 0), "fork");
         PK(launch_epoch_sampler(*this, side), "sampler");
@@ -808,7 +836,7 @@ gempe_status Pack::enqueue_sweep() {
 // The position update and slope fits, then the join with the side stream.
 gempe_status Pack::enqueue_update() {
     PK(launch_update(args(), update_grid, stream), "update");
-    if (time_kernels) PK(cudaEventRecord(tev[3], stream), "timing event");
+    if (time_kernels) PK(cudaEventRecord(tev[5], stream), "timing event");
     if (p.sigma_source == 1 && p.sigma_every > 0) {
         PK(launch_hist_pass(args(), stream), "histogram pass");
         PK(launch_fit_graphs(args(), stream), "slope fit");

@@ -28,7 +28,8 @@ struct PackShape {
     int edge_chunk = kEdgeChunk;   // d >= 8: CSR slots per work unit (32, 64, 128)
     int lanes = 0;                 // d >= 8: lanes per pair (d/8 or d/4; 0 = d/8)
     int blocks_per_sm = 0;         // sweep CTAs per SM (0 = as many as fit)
-    int kernel = 0;                // d <= 4: 0 packed units, 1 one lane per vertex
+    int kernel = 0;                // d <= 4: 0 packed units, 1 one lane per vertex; d >= 8 with tiles:
+                                   // 2 the sweep (512-thread blocks, one per SM) beside one tile CTA per SM
     float sweep_us = 0.0f;         // measured sweep time of the chosen shape (autotuner)
 };
 
@@ -59,13 +60,19 @@ struct Pack {
     cudaStream_t stream = nullptr;   // set by the owner (context or batch), not owned
     cudaStream_t side = nullptr;     // owned: the next epoch's sampler runs here
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // launch shape kernel 2 (block form with tiles): the tile kernel runs on
+    // tile_stream beside the sweep, forked and joined by these events
+    cudaStream_t tile_stream = nullptr;
+    cudaEvent_t tile_fork = nullptr, tile_join = nullptr;
     bool primed = false;             // samples of the current epoch are in the buffer
     bool sampled_ahead = false;      // the next epoch's sampler has been enqueued
     bool swept = false;              // a sweep ran without the update that clears its sums
     // per-kernel timing of epochs enqueued directly (not captured): events on
     // `stream` before the sweep, after it, after the tiles, after the update
+    // (events: before the sweep, after it, before the tiles, after them, after
+    // the join, after the update)
     bool time_kernels = false;
-    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<GraphInfo> info;     // host copies
     std::vector<int64_t> nnz;
     std::vector<int32_t> row_ptr_h;  // pack CSR offsets, rows + 1

@@ -10,13 +10,14 @@
 //       FP32, are staged in shared memory (cp.async);
 //   (2) every pair's squared distance is summed from coordinate differences,
 //       as the sweep and the oracle form it (no |x|^2 + |y|^2 - 2 x.y
-//       cancellation): thread (ta, tp) holds the 8 x 4 pairs of anchors
-//       ta + 16 r and partners tp + 16 j;
-//   (3) the pair terms (c, w) of unmasked pairs (c the coefficient of
-//       x_self - x_other in y - z x, w the weight added to z), C into shared
-//       memory, the row sums of C and W by shuffles, the column sums through
-//       per-warp partials; the pairs' distances go to the histograms;
-//   (4) A = C X_P and B = C^T X_T by register-tiled FFMA, then
+//       cancellation): thread (ta, tp) holds the pairs of anchors ta + 16 r
+//       and partners tp + 16 j, in two passes of 4 x 4 pairs, with packed
+//       FP32 pairs (f32x2.cuh: even and odd coordinates in the two halves);
+//   (3) after each pass, the pair terms (c, w) of its unmasked pairs (c the
+//       coefficient of x_self - x_other in y - z x, w the weight added to z),
+//       C into shared memory, the row sums of C and W by shuffles; the column
+//       sums through per-warp partials; the distances go to the histograms;
+//   (4) A = C X_P and B = C^T X_T by register tiles of packed FP32 FMAs, then
 //         y_i - z_i x_i += x_i rowsum(C)_i - A_i,   z_i += rowsum(W)_i,
 //         y_g - z_g x_g += x_g colsum(C)_g - B_g,   z_g += colsum(W)_g
 //       by vector atomics (partners only in the symmetric form).
@@ -27,6 +28,7 @@
 
 #include "device_math.cuh"
 #include "engine.cuh"
+#include "f32x2.cuh"
 #include "hist.cuh"
 
 namespace gempe {
@@ -181,77 +183,81 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
             s_tile_used = 0u;
         }
 
-        // ---- (2) squared distances of anchors ta + 16 r and partners tp + 16 j ----
-        float s2[8][4];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) s2[r][j] = 0.0f;
-#pragma unroll 2
-        for (int kc = 0; kc < D / 4; ++kc) {
-            float4 b[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const float4*>(sm.xp + (tp + 16 * j) * R + 4 * kc);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const float4 av = *reinterpret_cast<const float4*>(sm.xt + (ta + 16 * r) * R + 4 * kc);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float t = av.x - b[j].x;
-                    s2[r][j] = fmaf(t, t, s2[r][j]);
-                    t = av.y - b[j].y;
-                    s2[r][j] = fmaf(t, t, s2[r][j]);
-                    t = av.z - b[j].z;
-                    s2[r][j] = fmaf(t, t, s2[r][j]);
-                    t = av.w - b[j].w;
-                    s2[r][j] = fmaf(t, t, s2[r][j]);
-                }
-            }
-        }
-
-        // ---- (3) pair terms, C, row / column sums, histograms ----
-        float rc[8], rw[8], cc[4], cw[4];
+        // ---- (2, 3) in two passes over anchor halves h: anchors ta + 16 (4 h + r),
+        // partners tp + 16 j; squared distances summed in packed pairs (even and odd
+        // coordinates in the two halves), then the pair terms, C, row sums and the
+        // histograms of the half ----
+        float cc[4], cw[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) cc[j] = cw[j] = 0.0f;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            f2 acc2[4][4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int i = ta + 16 * r;
-            const unsigned long long mk = sm.mask[i];
-            const int di = sm.deg[i], ki = sm.kacc[i];
-            rc[r] = rw[r] = 0.0f;
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int p = tp + 16 * j;
-                float cv = 0.0f, wv = 0.0f;
-                if (!((mk >> p) & 1ull)) {
-                    float delta, inv_delta;
-                    dist_of(s2[r][j], delta, inv_delta);
-                    const PairTerm pt = pair_term(delta, inv_delta, false, K);
-                    cv = pt.c;
-                    wv = pt.w;
-                    const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                    hist_sample(hist, a, graph, bin, di, ki, kBlockP);
+                for (int j = 0; j < 4; ++j) acc2[r][j] = 0ull;
+#pragma unroll 2
+            for (int kc = 0; kc < D / 4; ++kc) {
+                ulonglong2 b[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    b[j] = *reinterpret_cast<const ulonglong2*>(sm.xp + (tp + 16 * j) * R + 4 * kc);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const ulonglong2 av =
+                        *reinterpret_cast<const ulonglong2*>(sm.xt + (ta + 16 * (4 * h + r)) * R + 4 * kc);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        f2 t = f2_sub(av.x, b[j].x);
+                        acc2[r][j] = f2_fma(t, t, acc2[r][j]);
+                        t = f2_sub(av.y, b[j].y);
+                        acc2[r][j] = f2_fma(t, t, acc2[r][j]);
+                    }
                 }
-                sm.c[i * RC + p] = cv;
-                rc[r] += cv;
-                rw[r] += wv;
-                cc[j] += cv;
-                cw[j] += wv;
             }
-        }
-        // row sums over the 16 lanes of a half-warp (one anchor group)
+            float rc[4], rw[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < 4; ++r) {
+                const int i = ta + 16 * (4 * h + r);
+                const unsigned long long mk = sm.mask[i];
+                const int di = sm.deg[i], ki = sm.kacc[i];
+                rc[r] = rw[r] = 0.0f;
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                rc[r] += __shfl_xor_sync(0xFFFFFFFFu, rc[r], o);
-                rw[r] += __shfl_xor_sync(0xFFFFFFFFu, rw[r], o);
+                for (int j = 0; j < 4; ++j) {
+                    const int p = tp + 16 * j;
+                    float cv = 0.0f, wv = 0.0f;
+                    if (!((mk >> p) & 1ull)) {
+                        float lo, hi, delta, inv_delta;
+                        f2_unpack(acc2[r][j], lo, hi);
+                        dist_of(lo + hi, delta, inv_delta);
+                        const PairTerm pt = pair_term(delta, inv_delta, false, K);
+                        cv = pt.c;
+                        wv = pt.w;
+                        const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
+                        hist_sample(hist, a, graph, bin, di, ki, kBlockP);
+                    }
+                    sm.c[i * RC + p] = cv;
+                    rc[r] += cv;
+                    rw[r] += wv;
+                    cc[j] += cv;
+                    cw[j] += wv;
+                }
             }
-        }
+            // row sums over the 16 lanes of a half-warp (one anchor group)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            if (tp == r) sm.rsum_c[ta + 16 * r] = rc[r];
-            if (tp == 8 + r) sm.rsum_w[ta + 16 * r] = rw[r];
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1) {
+                    rc[r] += __shfl_xor_sync(0xFFFFFFFFu, rc[r], o);
+                    rw[r] += __shfl_xor_sync(0xFFFFFFFFu, rw[r], o);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (tp == r) sm.rsum_c[ta + 16 * (4 * h + r)] = rc[r];
+                if (tp == 8 + r) sm.rsum_w[ta + 16 * (4 * h + r)] = rw[r];
+            }
         }
         // column sums: the warp's two anchor groups, then per-warp partials
 #pragma unroll
@@ -278,23 +284,49 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         // ---- (4a) A = C X_P: anchors ta + 16 r, coordinates CK tp .. ----
         {
             float A[8][CK];
+            if constexpr (CK >= 2) {   // packed coordinate pairs, c broadcast to both halves
+                f2 A2[8][CK / 2];
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+                for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int e = 0; e < CK; ++e) A[r][e] = 0.0f;
+                    for (int e = 0; e < CK / 2; ++e) A2[r][e] = 0ull;
 #pragma unroll 2
-            for (int pc = 0; pc < kBlockP / 4; ++pc) {
-                float xr[4][CK];
+                for (int pc = 0; pc < kBlockP / 4; ++pc) {
+                    f2 xr[4][CK / 2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) load_chunk<CK>(sm.xp + (4 * pc + q) * R + CK * tp, xr[q]);
+                    for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const float4 c4 = *reinterpret_cast<const float4*>(sm.c + (ta + 16 * r) * RC + 4 * pc);
+                        for (int e = 0; e < CK / 2; ++e)
+                            xr[q][e] = *reinterpret_cast<const f2*>(sm.xp + (4 * pc + q) * R + CK * tp + 2 * e);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float cq = comp(c4, q);
+                    for (int r = 0; r < 8; ++r) {
+                        const float4 c4 = *reinterpret_cast<const float4*>(sm.c + (ta + 16 * r) * RC + 4 * pc);
 #pragma unroll
-                        for (int e = 0; e < CK; ++e) A[r][e] = fmaf(cq, xr[q][e], A[r][e]);
+                        for (int q = 0; q < 4; ++q) {
+                            const float cq = comp(c4, q);
+                            const f2 cc = f2_pack(cq, cq);
+#pragma unroll
+                            for (int e = 0; e < CK / 2; ++e) A2[r][e] = f2_fma(cc, xr[q][e], A2[r][e]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int e = 0; e < CK / 2; ++e) f2_unpack(A2[r][e], A[r][2 * e], A[r][2 * e + 1]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) A[r][0] = 0.0f;
+#pragma unroll 2
+                for (int pc = 0; pc < kBlockP / 4; ++pc) {
+                    float xr[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) xr[q] = sm.xp[(4 * pc + q) * R + tp];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const float4 c4 = *reinterpret_cast<const float4*>(sm.c + (ta + 16 * r) * RC + 4 * pc);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) A[r][0] = fmaf(comp(c4, q), xr[q], A[r][0]);
                     }
                 }
             }
@@ -316,20 +348,39 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         // ---- (4b) B = C^T X_T: partners 4 ta .. 4 ta + 3, coordinates CK tp .. ----
         if (a.symmetric) {
             float Bv[4][CK];
+            if constexpr (CK >= 2) {
+                f2 B2[4][CK / 2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int e = 0; e < CK; ++e) Bv[q][e] = 0.0f;
+                    for (int e = 0; e < CK / 2; ++e) B2[q][e] = 0ull;
 #pragma unroll 4
-            for (int i = 0; i < nv; ++i) {   // rows of vertices past the graph have c = 0
-                const float4 c4 = *reinterpret_cast<const float4*>(sm.c + i * RC + 4 * ta);
-                float xi[CK];
-                load_chunk<CK>(sm.xt + i * R + CK * tp, xi);
+                for (int i = 0; i < nv; ++i) {   // rows of vertices past the graph have c = 0
+                    const float4 c4 = *reinterpret_cast<const float4*>(sm.c + i * RC + 4 * ta);
+                    f2 xi[CK / 2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float cq = comp(c4, q);
+                    for (int e = 0; e < CK / 2; ++e) xi[e] = *reinterpret_cast<const f2*>(sm.xt + i * R + CK * tp + 2 * e);
 #pragma unroll
-                    for (int e = 0; e < CK; ++e) Bv[q][e] = fmaf(cq, xi[e], Bv[q][e]);
+                    for (int q = 0; q < 4; ++q) {
+                        const float cq = comp(c4, q);
+                        const f2 cc = f2_pack(cq, cq);
+#pragma unroll
+                        for (int e = 0; e < CK / 2; ++e) B2[q][e] = f2_fma(cc, xi[e], B2[q][e]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < CK / 2; ++e) f2_unpack(B2[q][e], Bv[q][2 * e], Bv[q][2 * e + 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Bv[q][0] = 0.0f;
+#pragma unroll 4
+                for (int i = 0; i < nv; ++i) {
+                    const float4 c4 = *reinterpret_cast<const float4*>(sm.c + i * RC + 4 * ta);
+                    const float xi = sm.xt[i * R + tp];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Bv[q][0] = fmaf(comp(c4, q), xi, Bv[q][0]);
                 }
             }
             __syncthreads();   // the column sums

@@ -51,9 +51,11 @@ def _err_rows(got, ref, abs_terms=None, floor_frac=1e-2):
     return np.linalg.norm(got - ref, axis=1) / scale
 
 
-def _run(B, O, rp, ci, d, x, sigma, epoch, **kw):
+def _run(B, O, rp, ci, d, x, sigma, epoch, shape=None, **kw):
     p = B.gempe_default_params(**kw)
     with B.gempe_create(rp, ci, d, p) as ctx:
+        if shape is not None:
+            B.gempe_set_shape(ctx, **shape)
         B.gempe_set_positions(ctx, x)
         B.gempe_set_state(ctx, sigma, epoch)
         samples = B.gempe_sweep(ctx, record_samples=True)
@@ -88,13 +90,19 @@ def test_block_samples_bit_exact(B, O, sbm_1000, precision, d):
     assert int((exp >= 0).sum()) == r["ref"]["accepted"]
 
 
-@pytest.mark.parametrize("d,symmetric", [(8, 1), (16, 1), (32, 1), (64, 1), (128, 1), (32, 0)],
-                         ids=["d8-sweep", "d16", "d32", "d64", "d128", "d32-anchor-only"])
-def test_block_fp32_parity(B, O, sbm_1000, d, symmetric):
-    """d = 8: the pair sweep takes the block samples; d >= 16: the FP32 tiles."""
+BESIDE = dict(kernel=2)   # launch shape: the sweep beside the tile kernel, on two streams
+
+
+@pytest.mark.parametrize("d,symmetric,shape", [(8, 1, None), (16, 1, None), (32, 1, None), (64, 1, None),
+                                               (128, 1, None), (32, 0, None), (64, 1, BESIDE), (128, 1, BESIDE)],
+                         ids=["d8-sweep", "d16", "d32", "d64", "d128", "d32-anchor-only", "d64-beside",
+                              "d128-beside"])
+def test_block_fp32_parity(B, O, sbm_1000, d, symmetric, shape):
+    """d = 8: the pair sweep takes the block samples; d >= 16: the FP32 tiles,
+    after the sweep or beside it."""
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     x = (np.random.default_rng(d).normal(size=(1000, d)) * 0.9).astype(np.float32)
-    r = _run(B, O, rp, ci, d, x, 0.8, 2, block_partners=64, symmetric_neg=symmetric)
+    r = _run(B, O, rp, ci, d, x, 0.8, 2, shape=shape, block_partners=64, symmetric_neg=symmetric)
     ref = r["ref"]
     assert _err_rows(r["delta"], ref["delta"], ref["abs_terms"]).max() <= TOL32
     assert _err_rows(r["z"], ref["z"]).max() <= TOL32
@@ -114,12 +122,13 @@ def _bf16_errors(r):
     return e_delta, e_z, e_x
 
 
-@pytest.mark.parametrize("d", [16, 32, 64])
-def test_block_bf16_tiles_parity(B, O, sbm_1000, d):
+@pytest.mark.parametrize("d,shape", [(16, None), (32, None), (64, None), (64, BESIDE)],
+                         ids=["d16", "d32", "d64", "d64-beside"])
+def test_block_bf16_tiles_parity(B, O, sbm_1000, d, shape):
     """Tensor-core tiles (BF16 positions, FP32 accumulation) against the FP64 oracle."""
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
     x = (np.random.default_rng(100 + d).normal(size=(1000, d)) * 0.9).astype(np.float32)
-    r = _run(B, O, rp, ci, d, x, 0.8, 4, block_partners=64, precision=1)
+    r = _run(B, O, rp, ci, d, x, 0.8, 4, shape=shape, block_partners=64, precision=1)
     e_delta, e_z, e_x = _bf16_errors(r)
     print(f"d={d} bf16 tiles: delta {e_delta.max():.2e} (q99 {np.quantile(e_delta, .99):.2e}) "
           f"z {e_z.max():.2e} step {e_x.max():.2e}")
@@ -171,15 +180,20 @@ def test_ba_fp32_tiles_parity(B, O, ba_20k):
 
 
 @pytest.mark.parametrize("kw,d,tiles", [(dict(neg_per_vertex=5), 2, False), (dict(block_partners=64), 64, True),
-                                        (dict(block_partners=64, precision=1), 64, True)],
-                         ids=["per-vertex", "block-fp32", "block-bf16"])
+                                        (dict(block_partners=64, precision=1), 64, True),
+                                        (dict(block_partners=64, shape=BESIDE), 64, True)],
+                         ids=["per-vertex", "block-fp32", "block-bf16", "block-fp32-beside"])
 def test_kernel_times(B, sbm_1000, kw, d, tiles):
     """gempe_kernel_times: per-kernel windows of an epoch run as gempe_sweep +
     gempe_update (the tile window only in the block form); graph replays of
     gempe_step are not recorded, and the epoch's results are unchanged."""
     rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    kw = dict(kw)
+    shape = kw.pop("shape", None)
     p = B.gempe_default_params(**kw)
     with B.gempe_create(rp, ci, d, p) as ctx, B.gempe_create(rp, ci, d, p) as ref:
+        if shape:
+            B.gempe_set_shape(ctx, **shape)
         assert B.gempe_kernel_times(ctx, True) == (0.0, 0.0, 0.0)
         B.gempe_sweep(ctx)
         B.gempe_update(ctx)
@@ -195,3 +209,10 @@ def test_kernel_times(B, sbm_1000, kw, d, tiles):
             assert st[f] == sr[f]
         x, xr = B.gempe_positions(ctx), B.gempe_positions(ref)
         np.testing.assert_allclose(x, xr, rtol=0, atol=1e-3 * max(float(np.abs(xr).max()), 1.0))
+
+
+def test_beside_shape_needs_tiles(B, sbm_1000):
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    with B.gempe_create(rp, ci, 8, B.gempe_default_params(block_partners=64)) as ctx:   # d = 8: no tiles
+        with pytest.raises(B.GempeError, match="kernel 2"):
+            B.gempe_set_shape(ctx, kernel=2)

@@ -58,8 +58,9 @@ def _err_rows(got, ref, floor=None):
     return np.linalg.norm(got - ref, axis=1) / scale
 
 
-@pytest.mark.parametrize("precision", [1, 0], ids=["bf16-tcgen05-tiles", "fp32-tiles"])
-def test_ba_1m_tiles_sampled_vertices(B, O, precision):
+@pytest.mark.parametrize("precision,kernel", [(1, 0), (0, 0), (1, 2), (0, 2)],
+                         ids=["bf16-tcgen05-tiles", "fp32-tiles", "bf16-beside", "fp32-beside"])
+def test_ba_1m_tiles_sampled_vertices(B, O, precision, kernel):
     from paper_2011_03479_gb300 import inputs
     w = inputs.ba_1m()
     rp, ci, d = w["row_ptr"], w["col_idx"], 64
@@ -69,6 +70,7 @@ def test_ba_1m_tiles_sampled_vertices(B, O, precision):
     p = B.gempe_default_params(neg_per_vertex=w["k"], seed=inputs.EMBED_SEED, block_partners=64,
                                precision=precision)
     with B.gempe_create(rp, ci, d, p) as ctx:
+        B.gempe_set_shape(ctx, kernel=kernel)
         B.gempe_set_positions(ctx, x)
         B.gempe_set_state(ctx, sigma, epoch)
         masks = B.gempe_sweep(ctx, record_samples=True)
