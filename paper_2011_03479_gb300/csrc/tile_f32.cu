@@ -8,11 +8,16 @@
 //
 //   (1) the anchors' rows X_T (128 x D) and the partners' rows X_P (64 x D),
 //       FP32, are staged in shared memory (cp.async);
-//   (2) every pair's squared distance is summed from coordinate differences,
-//       as the sweep and the oracle form it (no |x|^2 + |y|^2 - 2 x.y
-//       cancellation): thread (ta, tp) holds the pairs of anchors ta + 16 r
-//       and partners tp + 16 j, in two passes of 4 x 4 pairs, with packed
-//       FP32 pairs (f32x2.cuh: even and odd coordinates in the two halves);
+//   (2) every row is centred on the mean c of the tile's anchor rows (the
+//       terms depend on differences only), and each pair's squared distance
+//       is |x_i - c|^2 + |x_g - c|^2 - 2 (x_i - c).(x_g - c): thread (ta, tp)
+//       holds the dot products of anchors ta + 16 r and partners tp + 16 j,
+//       in two passes of 4 x 4 pairs, by packed FP32 FMAs (f32x2.cuh: even
+//       and odd coordinates in the two halves).  A pair closer than half of
+//       |x_i - c|^2 + |x_g - c|^2 (where the difference would lose digits)
+//       is summed again from coordinate differences, as the sweep forms it;
+//       above that line the relative error of the squared distance stays
+//       within twice that of the sum of squared differences;
 //   (3) after each pass, the pair terms (c, w) of its unmasked pairs (c the
 //       coefficient of x_self - x_other in y - z x, w the weight added to z),
 //       C into shared memory, the row sums of C and W by shuffles; the column
@@ -55,6 +60,8 @@ struct TileF32 {
     float c[kBlockT * RC];
     float col_part[kF32Threads / 32][2][kBlockP];   // per-warp column sums of C and W
     float rsum_c[kBlockT], rsum_w[kBlockT];
+    float centre[D];                         // mean of the tile's anchor rows
+    float nt[kBlockT], np[kBlockP];          // squared norms of the centred rows
     float csum_c[kBlockP], csum_w[kBlockP];
     unsigned long long mask[kBlockT];
     int deg[kBlockT], kacc[kBlockT];
@@ -182,6 +189,30 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
             }
             s_tile_used = 0u;
         }
+        // centre every row on the anchors' mean (the pair terms depend on
+        // differences only), then the squared norms of the centred rows
+        for (int k = tid; k < D; k += blockDim.x) {
+            float m = 0.0f;
+            for (int r = 0; r < nv; ++r) m += sm.xt[r * R + k];
+            sm.centre[k] = m / (float)nv;
+        }
+        __syncthreads();
+        for (int r = tid; r < kBlockT + kBlockP; r += blockDim.x) {
+            float* row = r < kBlockT ? sm.xt + r * R : sm.xp + (r - kBlockT) * R;
+            float n2 = 0.0f;
+            if (r >= nv && r < kBlockT) {   // a row past the graph stays zero (its pairs are masked)
+                sm.nt[r] = 0.0f;
+                continue;
+            }
+#pragma unroll 8
+            for (int k = 0; k < D; ++k) {
+                const float v = row[k] - sm.centre[k];
+                row[k] = v;
+                n2 = fmaf(v, v, n2);
+            }
+            if (r < kBlockT) sm.nt[r] = n2; else sm.np[r - kBlockT] = n2;
+        }
+        __syncthreads();
 
         // ---- (2, 3) in two passes over anchor halves h: anchors ta + 16 (4 h + r),
         // partners tp + 16 j; squared distances summed in packed pairs (even and odd
@@ -209,10 +240,8 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                         *reinterpret_cast<const ulonglong2*>(sm.xt + (ta + 16 * (4 * h + r)) * R + 4 * kc);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        f2 t = f2_sub(av.x, b[j].x);
-                        acc2[r][j] = f2_fma(t, t, acc2[r][j]);
-                        t = f2_sub(av.y, b[j].y);
-                        acc2[r][j] = f2_fma(t, t, acc2[r][j]);
+                        acc2[r][j] = f2_fma(av.x, b[j].x, acc2[r][j]);
+                        acc2[r][j] = f2_fma(av.y, b[j].y, acc2[r][j]);
                     }
                 }
             }
@@ -230,7 +259,20 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                     if (!((mk >> p) & 1ull)) {
                         float lo, hi, delta, inv_delta;
                         f2_unpack(acc2[r][j], lo, hi);
-                        dist_of(lo + hi, delta, inv_delta);
+                        const float nn = sm.nt[i] + sm.np[p];
+                        float d2 = fmaf(-2.0f, lo + hi, nn);
+                        if (d2 < 0.5f * nn) {
+                            // close pair: |x|^2 + |y|^2 - 2 x.y would lose digits, so the
+                            // squared distance is summed from differences as in the sweep
+                            const float* xa = sm.xt + i * R;
+                            const float* xb = sm.xp + p * R;
+                            d2 = 0.0f;
+                            for (int k = 0; k < D; ++k) {
+                                const float t = xa[k] - xb[k];
+                                d2 = fmaf(t, t, d2);
+                            }
+                        }
+                        dist_of(d2, delta, inv_delta);
                         const PairTerm pt = pair_term(delta, inv_delta, false, K);
                         cv = pt.c;
                         wv = pt.w;

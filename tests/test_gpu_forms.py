@@ -216,3 +216,28 @@ def test_beside_shape_needs_tiles(B, sbm_1000):
     with B.gempe_create(rp, ci, 8, B.gempe_default_params(block_partners=64)) as ctx:   # d = 8: no tiles
         with pytest.raises(B.GempeError, match="kernel 2"):
             B.gempe_set_shape(ctx, kernel=2)
+
+
+@pytest.mark.parametrize("layout", ["far-from-origin", "tight-clusters"])
+def test_block_fp32_tiles_centring_and_close_pairs(B, O, sbm_1000, layout):
+    """The FP32 tiles form squared distances as |x_i - c|^2 + |x_g - c|^2 -
+    2 (x_i - c).(x_g - c) with c the tile's anchor mean, and sum the close
+    pairs again from differences: an embedding translated far from the origin
+    and one of four tight clusters (many close pairs) meet the FP32 bar."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    rng = np.random.default_rng(17)
+    d = 64
+    if layout == "far-from-origin":
+        x = rng.normal(size=(1000, d)) * 0.8 + 300.0
+    else:
+        centres = rng.normal(size=(4, d)) * 20.0
+        x = centres[np.arange(1000) // 250] + rng.normal(size=(1000, d)) * 0.05
+    x = x.astype(np.float32)
+    r = _run(B, O, rp, ci, d, x, 1.1, 3, block_partners=64)
+    ref = r["ref"]
+    assert _err_rows(r["delta"], ref["delta"], ref["abs_terms"]).max() <= TOL32
+    assert _err_rows(r["z"], ref["z"]).max() <= TOL32
+    x0 = x.astype(np.float64)
+    step = _err_rows(r["xn"].astype(np.float64) - x0, ref["x_new"] - x0,
+                     ref["abs_terms"] / np.maximum(ref["z"], 1e-300))
+    assert step.max() <= TOL32
