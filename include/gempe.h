@@ -299,6 +299,43 @@ gempe_status gempe_fit_sigma(const float* host_hist, int32_t bins, float hist_ma
 gempe_status gempe_fit_sigma_static(const float* host_hist, int32_t bins, float hist_max, float mu,
                                     void* cuda_stream, float* out_sigma);
 
+/* ------------------------------------------------------------------------
+ * One graph over several GPUs: a vertex-range shard per rank (Sec. III.E's
+ * parallel reduction of the numerators and denominators of Eq. 3, with the
+ * ranks in place of the paper's threads).
+ *
+ * gempe_create_shard: a context holding the whole graph and every position
+ * (the same seed gives every rank the same initial positions) whose epochs
+ * evaluate the anchors v_begin <= i < v_end only: their edges (each
+ * undirected edge once in the d <= 4 oriented form, at its endpoint of
+ * larger degree), their sampled non-edges and, in the block form, their
+ * tiles (the range then starts and ends on a tile of 128 vertices, or at n).
+ * The sums of all vertices receive this shard's terms.  One epoch over R
+ * ranks: gempe_sweep on every rank; the sums (what 0) and the four
+ * histogram arrays (1-4) copied out, summed over the ranks and copied back;
+ * gempe_update on every rank (its own rows, and the same sigma on every rank,
+ * fitted on the summed histograms; the other rows' sums are cleared); the
+ * positions (5) copied out, each rank's own rows gathered from every rank,
+ * and copied back.  Arguments and errors as gempe_create, plus
+ * GEMPE_E_INVALID_ARG for a range outside [0, n) or not on tiles.
+ * gempe_stats counts this shard's samples; gempe_loss is this shard's part.
+ *
+ * gempe_shard_layout: out4 = {floats of the sums (n * stride), stride,
+ * histogram bins, floats of the positions (n * d)}.
+ * gempe_shard_copy: what 0 the sums (float [n][stride]: d values of
+ * y - z x, then z, padded), 1 the edge counts (uint32 [bins]), 2 the sample
+ * counts (uint32 [bins]), 3 the samples' anchor-degree sums (uint64 [bins]),
+ * 4 the weight corrections (float [bins]), 5 the positions (float [n][d]);
+ * direction 0 copies the context's array into device_buf, 1 device_buf
+ * into the context (positions: the BF16 shadow is refreshed).  Sums and
+ * histograms move between gempe_sweep and gempe_update, positions after
+ * gempe_update.  Device-to-device copies ordered on the context's stream. */
+gempe_status gempe_create_shard(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
+                                int32_t v_begin, int32_t v_end, const gempe_params* p, void* cuda_stream,
+                                gempe_ctx** out);
+gempe_status gempe_shard_layout(gempe_ctx* ctx, int64_t* out4);
+gempe_status gempe_shard_copy(gempe_ctx* ctx, int32_t what, int32_t direction, void* device_buf);
+
 /* Test hook for the bounded device waits of the tensor-core tile kernel
  * (failure detection without a GPU fault; the paper has no counterpart).
  * Launches one CTA set up like a tile CTA (256 TMEM columns allocated, an

@@ -97,6 +97,10 @@ def _bind(lib):
         "orc_epoch": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
                                  I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
                                  _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32, I32, I32, I32, I32]),
+        "orc_epoch_range": (_c.c_int, [I32, _i32p, _i32p, I32, _f64p, F64, F64, I32, U64, I32, I32,
+                                       I32, I32, I32, F64, I32, F64, _f64p, _f64p, _f64p, _f64p,
+                                       _f64p, _i32p, _i64p, _f64p, I32, I32, _i32p, I32, I32, I32, I32, I32,
+                                       I32, I32]),
         "orc_bytemap_addr": (None, [I32, U64, I32, I32, _i32p, I64, _c.POINTER(_c.c_uint32),
                                     _c.POINTER(_c.c_uint32)]),
         "orc_block_partners": (None, [I32, I32, I32, U64, I32, _i32p]),
@@ -208,12 +212,14 @@ def block_partners(n, tile, epoch_idx, seed, P):
 def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX_RETRIES,
           symmetric=1, w_formula=0, clamp_neg_d=1, z_min=Z_MIN, hist_bins=HIST_BINS,
           hist_max=HIST_MAX, block_partners=0, tile_vertices=128, per_slot=0, membership=0, bytemap_log2=24,
-          rename_every=0, rng=0):
+          rename_every=0, rng=0, anchors=None):
     """One epoch of Fig. 4; returns a dict of FP64 results.  ``abs_terms[i]`` is the
     sum of the sizes of the pair terms of y_i - z_i x_i (the scale of that sum's
     rounding when its terms cancel).  per_slot=1: Sec. III.C's policy, one
     sample per CSR slot (``samples`` then has one entry per slot).  rng=1: Sec. III.C's
-    LCG draws the sampled non-edges (seeded per slot from Philox)."""
+    LCG draws the sampled non-edges (seeded per slot from Philox).  anchors=(lo, hi):
+    the terms of those anchors alone (y, z, histograms and counts of their pairs;
+    x_new is then not an epoch's)."""
     n = len(row_ptr) - 1
     nnz = int(row_ptr[-1])
     x = _f64(x)
@@ -225,10 +231,16 @@ def epoch(row_ptr, col_idx, x, sigma, epoch_idx, seed, k, mu=MU, max_retries=MAX
     absd = np.zeros(n)
     n_tiles = (n + tile_vertices - 1) // tile_vertices
     parts = np.zeros(max(1, n_tiles * block_partners), dtype=np.int32)
-    rc = _load().orc_epoch(n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
-                           max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
-                           hist_max, y, z, xn, he, hn, smp, st, absd, block_partners,
-                           tile_vertices, parts, per_slot, membership, bytemap_log2, rename_every, rng)
+    args = (n, _i32(row_ptr), _i32(col_idx), d, x, sigma, mu, epoch_idx, seed, k,
+            max_retries, symmetric, w_formula, clamp_neg_d, z_min, hist_bins,
+            hist_max, y, z, xn, he, hn, smp, st, absd, block_partners,
+            tile_vertices, parts, per_slot, membership, bytemap_log2, rename_every, rng)
+    if anchors is None:
+        rc = _load().orc_epoch(*args)
+    else:
+        rc = _load().orc_epoch_range(*args, int(anchors[0]), int(anchors[1]))
+    if rc == -2:
+        raise ValueError("anchor range outside [0, n)")
     if rc != 0:
         raise MemoryError("oracle epoch failed")
     samples = smp[:nnz] if per_slot else smp[: n * k].reshape(n, k)

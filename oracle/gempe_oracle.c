@@ -32,6 +32,8 @@
  *                          gradient identity of Eq. 3)
  *   orc_vertex_terms       Eq. 3's sums of chosen vertices alone, with the
  *                          samples of orc_epoch (checks at full sizes)
+ *   orc_epoch_range        the terms of a range of anchors (Sec. III.E's
+ *                          split of Eq. 3's sums over workers)
  *
  * Choices where the paper is silent (the "readings"):
  *   - negative samples are drawn per vertex, k per vertex per epoch, with a
@@ -470,6 +472,16 @@ void orc_sample(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32
 /* ------------------------------------------------------------------ */
 /* One epoch (Fig. 4) in the per-vertex CSR form                        */
 /* ------------------------------------------------------------------ */
+static int epoch_range(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                       const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
+                       int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
+                       int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
+                       double* y, double* z, double* x_new, double* hist_e, double* hist_n,
+                       int32_t* samples_out, int64_t* stats, double* absd,
+                       int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
+                       int32_t membership, int32_t bytemap_log2, int32_t rename_every, int32_t rng,
+                       int32_t a_lo, int32_t a_hi);
+
 int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
               const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
               int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
@@ -478,6 +490,44 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
               int32_t* samples_out, int64_t* stats, double* absd,
               int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
               int32_t membership, int32_t bytemap_log2, int32_t rename_every, int32_t rng) {
+    return epoch_range(n, row_ptr, col_idx, d, x, sigma, mu, epoch, seed, k, max_retries, symmetric, w_formula,
+                       clamp_neg_d, z_min, B, hist_max, y, z, x_new, hist_e, hist_n, samples_out, stats, absd,
+                       block_P, block_T, partners_out, per_slot, membership, bytemap_log2, rename_every, rng, 0, n);
+}
+
+/* The terms of the anchors a_lo <= i < a_hi alone (Sec. III.E's split of
+ * the numerators and denominators of Eq. 3 over workers): their edges (each
+ * undirected edge's histogram entry at its smaller endpoint), their sampled
+ * non-edges and, in block sampling, their rows of each tile; y, z hold the
+ * sums these terms give every vertex, the histograms and counts these
+ * anchors' pairs.  Summed over a partition of [0, n) they are orc_epoch's.
+ * x_new is computed from these partial sums (meaningful for a_lo = 0,
+ * a_hi = n only). */
+int orc_epoch_range(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                    const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
+                    int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
+                    int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
+                    double* y, double* z, double* x_new, double* hist_e, double* hist_n,
+                    int32_t* samples_out, int64_t* stats, double* absd,
+                    int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
+                    int32_t membership, int32_t bytemap_log2, int32_t rename_every, int32_t rng,
+                    int32_t a_lo, int32_t a_hi) {
+    if (a_lo < 0 || a_hi > n || a_lo > a_hi) return -2;
+    return epoch_range(n, row_ptr, col_idx, d, x, sigma, mu, epoch, seed, k, max_retries, symmetric, w_formula,
+                       clamp_neg_d, z_min, B, hist_max, y, z, x_new, hist_e, hist_n, samples_out, stats, absd,
+                       block_P, block_T, partners_out, per_slot, membership, bytemap_log2, rename_every, rng, a_lo,
+                       a_hi);
+}
+
+static int epoch_range(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t d,
+                       const double* x, double sigma, double mu, int32_t epoch, uint64_t seed,
+                       int32_t k, int32_t max_retries, int32_t symmetric, int32_t w_formula,
+                       int32_t clamp_neg_d, double z_min, int32_t B, double hist_max,
+                       double* y, double* z, double* x_new, double* hist_e, double* hist_n,
+                       int32_t* samples_out, int64_t* stats, double* absd,
+                       int32_t block_P, int32_t block_T, int32_t* partners_out, int32_t per_slot,
+                       int32_t membership, int32_t bytemap_log2, int32_t rename_every, int32_t rng,
+                       int32_t a_lo, int32_t a_hi) {
     /* block sampling or the per-slot policy replace the k per-vertex samples */
     if (block_P > 0) { k = 0; per_slot = 0; }
     /* membership 1: the sampler tests pairs against the byte map of the
@@ -521,7 +571,7 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 64)
 #endif
-    for (int32_t i = 0; i < n; ++i) {
+    for (int32_t i = a_lo; i < a_hi; ++i) {
         /* edges: every CSR slot (i,j) contributes to y_i, z_i */
         for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             int32_t j = col_idx[e];
@@ -566,9 +616,11 @@ int orc_epoch(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
 #pragma omp for schedule(dynamic, 4)
 #endif
         for (int32_t tile = 0; tile < n_tiles; ++tile) {
+            if ((tile + 1) * block_T <= a_lo || tile * block_T >= a_hi) continue;   /* no anchor of the range */
             orc_block_partners(n, tile, epoch, seed, block_P, part);
             if (partners_out) memcpy(partners_out + (int64_t)tile * block_P, part, sizeof(int32_t) * (size_t)block_P);
-            for (int32_t i = tile * block_T; i < n && i < (tile + 1) * block_T; ++i) {
+            for (int32_t i = (tile * block_T > a_lo ? tile * block_T : a_lo);
+                 i < n && i < a_hi && i < (tile + 1) * block_T; ++i) {
                 int32_t acc = 0;
                 for (int32_t p = 0; p < block_P; ++p)
                     acc += (part[p] != i && !orc_is_edge(row_ptr, col_idx, i, part[p]));

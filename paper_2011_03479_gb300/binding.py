@@ -159,6 +159,9 @@ def load(build: bool = True):
         "gempe_fit_sigma_static": (st, [vp, i32, ctypes.c_float, ctypes.c_float, vp, P(ctypes.c_float)]),
         "gempe_test_tile_wait": (st, [i32, P(i32), P(i32)]),
         "gempe_kernel_times": (st, [vp, i32, P(ctypes.c_float)]),
+        "gempe_create_shard": (st, [vp, vp, i32, i32, i32, i32, P(gempe_params), vp, P(vp)]),
+        "gempe_shard_layout": (st, [vp, P(i64)]),
+        "gempe_shard_copy": (st, [vp, i32, i32, vp]),
         "gempe_stats": (st, [vp, P(gempe_stats_t)]),
         "gempe_save": (st, [vp, vp, P(sz)]),
         "gempe_load": (st, [vp, vp, sz]),
@@ -256,6 +259,36 @@ def gempe_create(row_ptr, col_idx, d: int, params: gempe_params | None = None, s
                                ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
     return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex,
                 per_slot=(p.sampling == 1), nnz=len(ci))
+
+
+def gempe_create_shard(row_ptr, col_idx, d: int, v_begin: int, v_end: int, params: gempe_params | None = None,
+                       stream=None) -> _Ctx:
+    """A shard of one graph: anchors v_begin <= i < v_end (see shard.py)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    n = len(rp) - 1
+    p = params or gempe_default_params()
+    h = ctypes.c_void_p()
+    _check(load().gempe_create_shard(_ptr(rp), _ptr(ci) if len(ci) else ctypes.c_void_p(None), n, d, int(v_begin),
+                                     int(v_end), ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)))
+    return _Ctx(h, n, d, p.neg_per_vertex, keep=(p,), slots=p.block_partners or p.neg_per_vertex,
+                per_slot=(p.sampling == 1), nnz=len(ci))
+
+
+SHARD_SUMS, SHARD_HIST_E, SHARD_HIST_C, SHARD_HIST_D, SHARD_HIST_X, SHARD_POSITIONS = range(6)
+
+
+def gempe_shard_layout(ctx: _Ctx) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(load().gempe_shard_layout(ctx.handle, out))
+    return {"sum_floats": int(out[0]), "stride": int(out[1]), "bins": int(out[2]), "position_floats": int(out[3])}
+
+
+def gempe_shard_copy(ctx: _Ctx, what: int, direction: int, device_buf) -> None:
+    """direction 0: the context's array `what` into device_buf (a CUDA tensor
+    or a device address); 1: device_buf into the context."""
+    ptr = device_buf.data_ptr() if hasattr(device_buf, "data_ptr") else int(device_buf)
+    _check(load().gempe_shard_copy(ctx.handle, int(what), int(direction), ctypes.c_void_p(ptr)))
 
 
 def gempe_create_device(d_row_ptr, d_col_idx, d: int, params: gempe_params | None = None,

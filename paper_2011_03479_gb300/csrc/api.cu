@@ -63,10 +63,17 @@ struct gempe_ctx {
 namespace {
 
 gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t n, int32_t d,
-                         const gempe_params* p, void* stream, gempe_ctx** out) {
+                         const gempe_params* p, void* stream, gempe_ctx** out, int32_t own_lo = 0,
+                         int32_t own_hi = -1) {
     gempe_status s = check_params(p, d);
     if (s != GEMPE_OK) return s;
     if (n < 2) return fail(GEMPE_E_INVALID_ARG, "n must be at least 2");
+    if (own_hi >= 0) {
+        if (own_lo < 0 || own_lo >= own_hi || own_hi > n)
+            return fail(GEMPE_E_INVALID_ARG, "shard range must satisfy 0 <= v_begin < v_end <= n");
+        if (p->block_partners && (own_lo % kBlockT != 0 || (own_hi % kBlockT != 0 && own_hi != n)))
+            return fail(GEMPE_E_INVALID_ARG, "block sampling: a shard range starts and ends on a tile of 128 vertices");
+    }
     if (rp_host[n] < 0) return fail(GEMPE_E_INVALID_GRAPH, "row_ptr[n] negative");
     // rows sorted, in range and loop-free on the host, before any device
     // work; the symmetry is checked on the device against the edge set
@@ -81,6 +88,8 @@ gempe_status create_impl(const int32_t* rp_host, const int32_t* ci_host, int32_t
         c->own_stream = true;
     }
     c->pk.reset(new Pack());
+    c->pk->own_lo = own_lo;
+    c->pk->own_hi = own_hi;
     std::vector<GraphInput> g(1);
     g[0].row_ptr = rp_host;
     g[0].col_idx = ci_host;
@@ -770,6 +779,60 @@ GEMPE_API gempe_status gempe_stats(gempe_ctx* c, gempe_stats_t* out) {
     out->k = pk.k;
     out->sigma_iters = h.sigma_iters;
     out->false_pos = h.false_pos;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_create_shard(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
+                                          int32_t v_begin, int32_t v_end, const gempe_params* p, void* cuda_stream,
+                                          gempe_ctx** out) {
+    if (!out) return fail(GEMPE_E_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!row_ptr || !p) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    if (n < 2) return fail(GEMPE_E_INVALID_ARG, "n must be at least 2");
+    if (!col_idx && row_ptr[n] > 0) return fail(GEMPE_E_INVALID_ARG, "null col_idx");
+    static const int32_t empty = 0;
+    if (v_begin < 0 || v_end < 0) return fail(GEMPE_E_INVALID_ARG, "shard range must satisfy 0 <= v_begin < v_end <= n");
+    return create_impl(row_ptr, col_idx ? col_idx : &empty, n, d, p, cuda_stream, out, v_begin, v_end);
+}
+
+GEMPE_API gempe_status gempe_shard_layout(gempe_ctx* c, int64_t* out4) {
+    if (!c || !out4) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    const Pack& pk = *c->pk;
+    out4[0] = (int64_t)c->n * pk.acc_stride;
+    out4[1] = pk.acc_stride;
+    out4[2] = pk.bins;
+    out4[3] = (int64_t)c->n * pk.d;
+    return GEMPE_OK;
+}
+
+GEMPE_API gempe_status gempe_shard_copy(gempe_ctx* c, int32_t what, int32_t direction, void* device_buf) {
+    if (!c || !device_buf) return fail(GEMPE_E_INVALID_ARG, "null argument");
+    if (direction != 0 && direction != 1) return fail(GEMPE_E_INVALID_ARG, "direction must be 0 or 1");
+    Pack& pk = *c->pk;
+    if (!pk.sharded()) return fail(GEMPE_E_INVALID_ARG, "not a shard context (gempe_create_shard)");
+    const size_t bins = (size_t)pk.bins;
+    void* src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+        case 0: src = pk.acc; bytes = sizeof(float) * (size_t)c->n * pk.acc_stride; break;
+        case 1: src = pk.hist_e; bytes = sizeof(unsigned int) * bins; break;
+        case 2: src = pk.hist_c; bytes = sizeof(unsigned int) * bins; break;
+        case 3: src = pk.hist_d; bytes = sizeof(unsigned long long) * bins; break;
+        case 4: src = pk.hist_x; bytes = sizeof(float) * bins; break;
+        case 5: src = pk.x; bytes = sizeof(float) * (size_t)c->n * pk.d; break;
+        default: return fail(GEMPE_E_INVALID_ARG, "what must be in [0, 5]");
+    }
+    if (what <= 4 && !pk.swept)
+        return fail(GEMPE_E_INVALID_ARG, "sums and histograms are exchanged between gempe_sweep and gempe_update");
+    if (what == 5 && pk.swept)
+        return fail(GEMPE_E_INVALID_ARG, "positions are exchanged after gempe_update");
+    if (direction == 0) {
+        CK(cudaMemcpyAsync(device_buf, src, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy out");
+    } else {
+        CK(cudaMemcpyAsync(src, device_buf, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy in");
+        if (what == 5 && pk.xb)
+            CK(launch_to_bf16(pk.x, pk.xb, (long long)c->n * pk.d, c->stream), "BF16 shadow");
+    }
     return GEMPE_OK;
 }
 

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const Epoc
     if (s_last) {
         for (int graph = threadIdx.x; graph < a.n_graphs; graph += blockDim.x) {
             GraphState* st = a.gst + graph;
-            const unsigned long long slots = (unsigned long long)__ldg(&a.graphs[graph].n) * kBlockP;
+            const int own = a.own_n > 0 ? a.own_n : __ldg(&a.graphs[graph].n);   // a shard draws for its range
+            const unsigned long long slots = (unsigned long long)own * kBlockP;
             atomicAdd(&st->accepted, slots);
             atomicAdd(&st->draws, slots);
             st->sample_epoch = st->sample_epoch + 1;

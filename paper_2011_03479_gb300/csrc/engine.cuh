@@ -153,6 +153,7 @@ struct EpochArgs {
     int32_t rename_every;     // 0: one renaming (period 0) for the whole run
     uint8_t* bytemap;
     int32_t rng;              // 1: Sec. III.C's LCG draws the epoch's sampled non-edges
+    int32_t own_n;            // shard of one graph: vertices whose anchors this pack evaluates (0: all)
 };
 
 int acc_stride_for(int d);

@@ -443,8 +443,10 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
     std::vector<int4> sunits;
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
-        for (int32_t o = 0; o < gi.n; o += kVChunk) vch.push_back(make_int4(gi.v0 + o, std::min(kVChunk, gi.n - o), g, 0));
-        for (int32_t t = 0; t < gi.n_tiles; ++t) {
+        // a shard takes the chunks and tiles of its own vertex range only
+        const int32_t lo = sharded() ? own_lo : 0, hi = sharded() ? own_hi : gi.n;
+        for (int32_t o = lo; o < hi; o += kVChunk) vch.push_back(make_int4(gi.v0 + o, std::min(kVChunk, hi - o), g, 0));
+        for (int32_t t = lo / kBlockT; t < (block ? (hi + kBlockT - 1) / kBlockT : 0); ++t) {
             titems.push_back(make_int2(gi.t0 + t, g));
             const int32_t a0 = gi.v0 + t * kBlockT, a1 = gi.v0 + std::min(gi.n, (t + 1) * kBlockT);
             const int32_t e0 = row_ptr_h[a0], e1 = row_ptr_h[a1];
@@ -638,10 +640,11 @@ gempe_status Pack::set_shape(const PackShape& s) {
     const bool per_unit = d > kPackedMaxDim || sh.kernel == 1;   // the kernel with lane groups per unit
     for (int32_t g = 0; g < G; ++g) {
         const GraphInfo& gi = info[g];
+        const int32_t v0 = sharded() ? gi.v0 + own_lo : gi.v0, nv = sharded() ? own_hi - own_lo : gi.n;
         if (!per_unit)
-            packed_units(orow_ptr_h.empty() ? row_ptr_h.data() : orow_ptr_h.data(), gi.v0, gi.n, k, sh.unit_pairs, g,
+            packed_units(orow_ptr_h.empty() ? row_ptr_h.data() : orow_ptr_h.data(), v0, nv, k, sh.unit_pairs, g,
                          per_slot, units);
-        else chunk_units(row_ptr_h.data(), gi.v0, gi.n, sh.edge_chunk, g, per_slot, units);
+        else chunk_units(row_ptr_h.data(), v0, nv, sh.edge_chunk, g, per_slot, units);
     }
     // kernel 2: one sweep block of kSweepThreadsBeside threads per SM (the
     // tile kernel takes the other half of every SM's registers)
@@ -766,6 +769,7 @@ EpochArgs Pack::args() const {
     a.membership = bytemap ? 1 : 0;
     a.rename_every = p.rename_every;
     a.rng = p.rng;
+    a.own_n = sharded() ? own_hi - own_lo : 0;
     a.bytemap = bytemap;
     return a;
 }
@@ -836,6 +840,14 @@ gempe_status Pack::enqueue_sweep() {
 // The position update and slope fits, then the join with the side stream.
 gempe_status Pack::enqueue_update() {
     PK(launch_update(args(), update_grid, stream), "update");
+    if (sharded()) {
+        // the update clears the sums of the shard's own rows; the rows of the
+        // other shards' vertices held this shard's partner terms (and, after
+        // the exchange, everyone's) and start the next epoch at zero too
+        const size_t row = sizeof(float) * (size_t)acc_stride;
+        if (own_lo > 0) PK(cudaMemsetAsync(acc, 0, row * own_lo, stream), "clear sums");
+        if (own_hi < rows) PK(cudaMemsetAsync(acc + (size_t)own_hi * acc_stride, 0, row * (rows - own_hi), stream), "clear sums");
+    }
     if (time_kernels) PK(cudaEventRecord(tev[5], stream), "timing event");
     if (p.sigma_source == 1 && p.sigma_every > 0) {
         PK(launch_hist_pass(args(), stream), "histogram pass");

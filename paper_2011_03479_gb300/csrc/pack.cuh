@@ -72,6 +72,10 @@ struct Pack {
     // (events: before the sweep, after it, before the tiles, after them, after
     // the join, after the update)
     bool time_kernels = false;
+    // shard of one graph (set before build): anchors [own_lo, own_hi) only;
+    // own_hi < 0: every vertex
+    int32_t own_lo = 0, own_hi = -1;
+    bool sharded() const { return own_hi >= 0; }
     cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<GraphInfo> info;     // host copies
     std::vector<int64_t> nnz;

@@ -39,3 +39,72 @@ def shares(rank, world, port, queue):
         queue.put((rank, got, sizes))
     finally:
         dist.destroy_process_group()
+
+
+class OracleShard:
+    """A shard engine on the host for the exchange tests: the oracle's terms
+    of the anchors [lo, hi) (orc_epoch_range) as the partial sums, and the
+    update x_i := y_i / z_i of the own rows with sigma refitted on the summed
+    histograms (Fig. 4, Sec. III.F)."""
+
+    def __init__(self, oracle, rp, ci, x0, seed, k, lo, hi, form):
+        self.o, self.rp, self.ci, self.seed, self.k = oracle, rp, ci, seed, k
+        self.lo, self.hi, self.form = lo, hi, form
+        self.x = x0.copy()
+        self.sigma, self.epoch = 1.0, 0
+
+    def sweep(self):
+        import torch
+        r = self.o.epoch(self.rp, self.ci, self.x, self.sigma, self.epoch, self.seed, self.k,
+                         anchors=(self.lo, self.hi), **self.form)
+        self.parts = [torch.from_numpy(r[f].copy()) for f in ("y", "z", "hist_e", "hist_n")]
+
+    def partials(self):
+        return self.parts
+
+    def set_partials(self, tensors):
+        self.parts = tensors
+
+    def update(self):
+        y, z, he, hn = (t.numpy() for t in self.parts)
+        xn = self.x.copy()
+        for i in range(self.lo, self.hi):
+            if z[i] >= 1e-30:
+                xn[i] = y[i] / z[i]
+        self.x = xn
+        self.sigma = self.o.sigma_fit(he, hn)
+        self.epoch += 1
+
+    def positions(self):
+        import torch
+        return torch.from_numpy(self.x.copy())
+
+    def set_positions(self, x):
+        self.x = x.numpy().copy()
+
+
+def shard_epochs(rank, world, port, queue, form_name):
+    """Each rank runs two epochs of its vertex range with the product's
+    exchange (ShardRank over gloo) on an oracle-backed engine."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2011_03479_gb300 import inputs, shard
+        oracle.build()
+        w = inputs.sbm_1000()
+        rp, ci = w["row_ptr"], w["col_idx"]
+        forms = {"per-vertex": (2, 5, {}), "block": (16, 0, {"block_partners": 64})}
+        d, k, form = forms[form_name]
+        ranges = shard.vertex_ranges(rp, world, block=bool(form))
+        lo, hi = ranges[rank]
+        x0 = oracle.init_positions(len(rp) - 1, d, 99).astype("float64")
+        eng = OracleShard(oracle, rp, ci, x0, 99, k, lo, hi, form)
+        shard.ShardRank(eng).step(2)
+        queue.put((rank, ranges, eng.x, eng.sigma))
+    finally:
+        dist.destroy_process_group()

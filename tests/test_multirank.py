@@ -100,3 +100,63 @@ def test_reference_arm_rank_zero_only(rank):
         assert line["e2e"]["h2d_bytes_per_step"] == 0
     else:
         assert lines == []
+
+
+@pytest.mark.parametrize("form", ["per-vertex", "block"])
+def test_sharded_graph_gloo_world_2(form):
+    """One graph over two ranks (Sec. III.E's split of Eq. 3's sums): each
+    rank evaluates its vertex range, the product's exchange (ShardRank:
+    all-reduce of the sums and histograms, gather of the positions) runs over
+    gloo, and after two epochs both ranks hold the positions and sigma of the
+    oracle's whole-graph run (up to the order of FP64 additions)."""
+    import _rank_worker
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2011_03479_gb300 import inputs
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker.shard_epochs, args=(r, 2, port, q, form)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert all(p.exitcode == 0 for p in procs)
+    w = inputs.sbm_1000()
+    rp, ci = w["row_ptr"], w["col_idx"]
+    d, k, kw = (2, 5, {}) if form == "per-vertex" else (16, 0, {"block_partners": 64})
+    x0 = oracle.init_positions(1000, d, 99).astype(np.float64)
+    xr, sr, _ = oracle.run(rp, ci, x0, 1.0, 2, 99, k, **kw)
+    (_, ranges, x0r, s0), (_, _, x1r, s1) = res
+    assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == 1000
+    assert 0 < ranges[0][1] < 1000
+    for x, s in ((x0r, s0), (x1r, s1)):
+        np.testing.assert_allclose(x, xr, rtol=1e-9, atol=1e-9 * float(np.abs(xr).max()))
+        assert s == pytest.approx(sr, rel=1e-9)
+
+
+def test_vertex_ranges_cover_and_balance():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from paper_2011_03479_gb300 import inputs, shard
+    rp, _ = inputs.rmat(12, 16, seed=5)
+    n = len(rp) - 1
+    work = np.diff(rp) + 1
+    for world in (1, 2, 3, 4, 7):
+        for block in (False, True):
+            rs = shard.vertex_ranges(rp, world, block)
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            if block:
+                assert all(lo % 128 == 0 for lo, _ in rs)
+            loads = [int(work[lo:hi].sum()) for lo, hi in rs]
+            unit = 128 if block else 1
+            biggest = max(int(work[i:i + unit].sum()) for i in range(0, n, unit))
+            assert max(loads) - min(loads) <= 2 * biggest

@@ -809,3 +809,26 @@ def test_lcg_samples_replayed(oracle_mod, sbm_small, per_slot):
             rej += 1
         assert out == want, (i, t)
     assert r["rejected"] == rej
+
+
+@pytest.mark.parametrize("form", [dict(k=5), dict(k=3, per_slot=1), dict(k=0, block_partners=64),
+                                  dict(k=4, symmetric=0)], ids=["per-vertex", "per-slot", "block", "anchor-only"])
+def test_epoch_over_anchor_ranges_adds_up(oracle_mod, sbm_1000, form):
+    """Sec. III.E splits Eq. 3's numerators and denominators over workers:
+    the terms of the anchors of each range of a partition, added up, are the
+    whole epoch's sums, histograms, counts and samples (ranges on tiles of
+    128 in the block form)."""
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    x = np.random.default_rng(12).normal(size=(1000, 3))
+    kw = dict(form)
+    k = kw.pop("k")
+    full = oracle_mod.epoch(rp, ci, x, 0.9, 4, 77, k, **kw)
+    cuts = [0, 256, 640, 1000] if kw.get("block_partners") else [0, 333, 334, 801, 1000]
+    parts = [oracle_mod.epoch(rp, ci, x, 0.9, 4, 77, k, anchors=(a, b), **kw) for a, b in zip(cuts, cuts[1:])]
+    for f in ("y", "z", "hist_e", "hist_n"):
+        tot = sum(p[f] for p in parts)
+        np.testing.assert_allclose(tot, full[f], rtol=1e-12, atol=1e-12 * float(np.abs(full[f]).max()))
+    for f in ("accepted", "rejected", "exhausted"):
+        assert sum(p[f] for p in parts) == full[f]
+    with pytest.raises(ValueError):
+        oracle_mod.epoch(rp, ci, x, 0.9, 4, 77, k, anchors=(10, 5), **kw)
