@@ -70,7 +70,6 @@ SERVE_WORKLOADS = {"rmat-serve-poisson50": {},
 SERVE_MAX_JOBS = 600   # jobs of one serving run (12 s of arrivals at 50 per second)
 FORMS.update(SERVE_WORKLOADS)
 L2_FLUSH_BYTES = 256 << 20
-EDGE_CHUNK = 64      # CSR slots per work unit of the d >= 8 sweep
 UNIT_PAIRS = 128     # edge + sample slots per packed work unit of the d <= 4 sweep
 BLOCK_P, BLOCK_T = 64, 128
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz

@@ -639,7 +639,7 @@ def gempe_server_stats(s: _Server) -> dict:
             "peak_bytes_in_use": out[5]}
 
 
-def gempe_set_shape(ctx: _Ctx, unit_pairs: int = 128, edge_chunk: int = 64, lanes: int = 0, blocks_per_sm: int = 0,
+def gempe_set_shape(ctx: _Ctx, unit_pairs: int = 128, edge_chunk: int = 32, lanes: int = 0, blocks_per_sm: int = 0,
                     kernel: int = 0) -> None:
     arr = (ctypes.c_int32 * 5)(unit_pairs, edge_chunk, lanes, blocks_per_sm, kernel)
     _check(load().gempe_set_shape(ctx.handle, arr))

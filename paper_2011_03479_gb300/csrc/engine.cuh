@@ -60,7 +60,7 @@ constexpr int kNarrowKeysMaxN = 65536;
 
 // Chunk size (CSR slots) of the per-unit sweep used for d >= 8 (default;
 // the autotuner may pick another).
-constexpr int kEdgeChunk = 64;
+constexpr int kEdgeChunk = 32;
 constexpr int kMaxK = 32;
 constexpr int kSweepThreads = 1024;
 constexpr int kUpdateThreads = 1024;

@@ -23,7 +23,8 @@ on one GPU.  An engine is any object with sweep(), partials() -> tensors,
 set_partials(tensors), update(), positions() -> tensor [n, d],
 set_positions(tensor) and own rows (lo, hi); `GpuShard` is the engine of
 the C ABI (gempe_create_shard), whose work and the exchange's torch
-operations run on one stream (torch's current stream by default).
+operations run on one stream (a non-default one: ShardRank and
+local_epochs make it current around their torch operations).
 """
 from __future__ import annotations
 
@@ -67,8 +68,12 @@ class GpuShard:
         import torch
         self.lo, self.hi = int(lo), int(hi)
         # the context's work and the exchange's torch operations share one
-        # stream (torch's current stream unless given), which orders them
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        # stream, which orders them: a given one, else a new one (never the
+        # default stream, whose null handle would give the context a stream
+        # of its own)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        if self.stream.cuda_stream == 0:
+            raise ValueError("a shard needs a non-default stream")
         self.ctx = B.gempe_create_shard(row_ptr, col_idx, d, lo, hi, params, stream=self.stream)
         lay = B.gempe_shard_layout(self.ctx)
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -116,6 +121,16 @@ def _own_rows_only(x, lo, hi):
     return y
 
 
+def _on_stream(engine):
+    """The torch stream context of an engine's stream (none for host engines)."""
+    import contextlib
+    s = getattr(engine, "stream", None)
+    if s is None:
+        return contextlib.nullcontext()
+    import torch
+    return torch.cuda.stream(s)
+
+
 class ShardRank:
     """The epochs of one rank over a torch.distributed process group."""
 
@@ -126,30 +141,36 @@ class ShardRank:
     def step(self, epochs: int = 1):
         import torch.distributed as dist
         e = self.engine
-        for _ in range(epochs):
-            e.sweep()
-            parts = e.partials()
-            for t in parts:
-                dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
-            e.set_partials(parts)
-            e.update()
-            x = _own_rows_only(e.positions(), e.lo, e.hi)
-            dist.all_reduce(x, op=dist.ReduceOp.SUM, group=self.group)
-            e.set_positions(x)
+        with _on_stream(e):
+            for _ in range(epochs):
+                e.sweep()
+                parts = e.partials()
+                for t in parts:
+                    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
+                e.set_partials(parts)
+                e.update()
+                x = _own_rows_only(e.positions(), e.lo, e.hi)
+                dist.all_reduce(x, op=dist.ReduceOp.SUM, group=self.group)
+                e.set_positions(x)
 
 
 def local_epochs(engines, epochs: int = 1):
     """Several shards of one graph in one process, in lock step: the same
-    exchange as ShardRank with every all-reduce a plain sum."""
-    for _ in range(epochs):
-        for e in engines:
-            e.sweep()
-        parts = [[t.clone() for t in e.partials()] for e in engines]
-        total = [sum(p[q] for p in parts) for q in range(len(parts[0]))]
-        for e in engines:
-            e.set_partials([t.clone() for t in total])
-        for e in engines:
-            e.update()
-        x = sum(_own_rows_only(e.positions(), e.lo, e.hi) for e in engines)
-        for e in engines:
-            e.set_positions(x.clone())
+    exchange as ShardRank with every all-reduce a plain sum.  The engines
+    share one stream (GpuShard(..., stream=s) with the same s)."""
+    streams = {id(getattr(e, "stream", None)) for e in engines}
+    if len(streams) != 1:
+        raise ValueError("the shards of local_epochs share one stream")
+    with _on_stream(engines[0]):
+        for _ in range(epochs):
+            for e in engines:
+                e.sweep()
+            parts = [[t.clone() for t in e.partials()] for e in engines]
+            total = [sum(p[q] for p in parts) for q in range(len(parts[0]))]
+            for e in engines:
+                e.set_partials([t.clone() for t in total])
+            for e in engines:
+                e.update()
+            x = sum(_own_rows_only(e.positions(), e.lo, e.hi) for e in engines)
+            for e in engines:
+                e.set_positions(x.clone())

@@ -59,21 +59,23 @@ def test_sharded_epoch_matches_oracle(B, O, sbm_1000, name, d, kw, tol, floor, w
     ranges = shard.vertex_ranges(rp, world, block=bool(kw.get("block_partners")))
     x = (np.random.default_rng(d + world).normal(size=(n, d)) * 0.9).astype(np.float32)
     sigma, epoch = 0.85, 3
-    engines = [shard.GpuShard(rp, ci, d, lo, hi, p) for lo, hi in ranges]
+    s = torch.cuda.Stream()
+    engines = [shard.GpuShard(rp, ci, d, lo, hi, p, stream=s) for lo, hi in ranges]
     try:
-        xt = torch.from_numpy(x).cuda()
-        for e in engines:
-            e.set_positions(xt)
-            B.gempe_set_state(e.ctx, sigma, epoch)
-        for e in engines:
-            e.sweep()
-        parts = [[t.clone() for t in e.partials()] for e in engines]
-        total = [sum(q[i] for q in parts) for i in range(len(parts[0]))]
-        for e in engines:
-            e.set_partials([t.clone() for t in total])
-            e.update()
-        xn = sum(shard._own_rows_only(e.positions(), e.lo, e.hi) for e in engines).cpu().numpy()
-        acc = total[0].view(n, -1).cpu().numpy()
+        with torch.cuda.stream(s):
+            xt = torch.from_numpy(x).cuda()
+            for e in engines:
+                e.set_positions(xt)
+                B.gempe_set_state(e.ctx, sigma, epoch)
+            for e in engines:
+                e.sweep()
+            parts = [[t.clone() for t in e.partials()] for e in engines]
+            total = [sum(q[i] for q in parts) for i in range(len(parts[0]))]
+            for e in engines:
+                e.set_partials([t.clone() for t in total])
+                e.update()
+            xn = sum(shard._own_rows_only(e.positions(), e.lo, e.hi) for e in engines).cpu().numpy()
+            acc = total[0].view(n, -1).cpu().numpy()
         stats = [B.gempe_stats(e.ctx) for e in engines]
         sig = [B.gempe_get_state(e.ctx)[0] for e in engines]
     finally:
@@ -108,12 +110,14 @@ def test_sharded_run_matches_whole_graph(B, sbm_1000, d, kw):
             B.gempe_update(whole)
         xw = B.gempe_positions(whole)
         sw = B.gempe_stats(whole)
-    engines = [shard.GpuShard(rp, ci, d, lo, hi, p) for lo, hi in ranges]
+    s = torch.cuda.Stream()
+    engines = [shard.GpuShard(rp, ci, d, lo, hi, p, stream=s) for lo, hi in ranges]
     try:
         shard.local_epochs(engines, 6)
-        xs = engines[0].positions().cpu().numpy()
-        for e in engines[1:]:
-            np.testing.assert_array_equal(e.positions().cpu().numpy(), xs)
+        with torch.cuda.stream(s):
+            xs = engines[0].positions().cpu().numpy()
+            for e in engines[1:]:
+                np.testing.assert_array_equal(e.positions().cpu().numpy(), xs)
         st = [B.gempe_stats(e.ctx) for e in engines]
         ss = B.gempe_get_state(engines[0].ctx)[0]
     finally:
@@ -138,3 +142,6 @@ def test_shard_arguments_checked(B, sbm_1000):
         import torch
         with pytest.raises(B.GempeError, match="not a shard"):
             B.gempe_shard_copy(ctx, 0, 0, torch.zeros(10, device="cuda"))
+    with pytest.raises(ValueError, match="non-default stream"):
+        from paper_2011_03479_gb300 import shard
+        shard.GpuShard(rp, ci, 2, 0, 500, B.gempe_default_params(), stream=torch.cuda.default_stream())
