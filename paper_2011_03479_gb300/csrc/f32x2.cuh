@@ -25,6 +25,12 @@ __device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
     return d;
 }
 
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
     f2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));

@@ -20,6 +20,7 @@
 
 #include "device_math.cuh"
 #include "engine.cuh"
+#include "f32x2.cuh"
 #include "hist.cuh"
 
 namespace gempe {
@@ -131,6 +132,33 @@ __device__ __forceinline__ void load_chunk(const __nv_bfloat16* __restrict__ x, 
 #pragma unroll
         for (int c = 0; c < P; ++c) out[c] = __uint_as_float((uint32_t)__ldg(q + c) << 16);
     }
+}
+
+// The same chunks as packed FP32 pairs (P even): coordinates 2c, 2c + 1 in
+// the two halves of out[c].
+template <int D, int P>
+__device__ __forceinline__ void load_pairs(const float* __restrict__ x, int row, int gl, f2* out) {
+    static_assert(P % 2 == 0, "packed pairs need an even chunk");
+    const float* p = x + (size_t)row * D + gl * P;
+    if constexpr (P % 4 == 0) {
+#pragma unroll
+        for (int c = 0; c < P; c += 4) {
+            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p + c));
+            out[c / 2] = v.x;
+            out[c / 2 + 1] = v.y;
+        }
+    } else {
+        out[0] = __ldg(reinterpret_cast<const unsigned long long*>(p));
+    }
+}
+
+template <int D, int P>
+__device__ __forceinline__ void load_pairs(const __nv_bfloat16* __restrict__ x, int row, int gl, f2* out) {
+    static_assert(P % 2 == 0, "packed pairs need an even chunk");
+    float v[P];
+    load_chunk<D, P>(x, row, gl, v);
+#pragma unroll
+    for (int c = 0; c < P / 2; ++c) out[c] = f2_pack(v[2 * c], v[2 * c + 1]);
 }
 
 // acc row layout: D values then z, padded to a multiple of 4 floats.
@@ -912,6 +940,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         const int rounds = (total + G - 1) / G;
         const int rmax = (int)__reduce_max_sync(kFull, (unsigned)rounds);
 
+        // even chunks run on packed FP32 pairs (coordinates 2c, 2c + 1 in the
+        // two halves of a 64-bit register: the same roundings, half the
+        // instructions); odd ones (d <= 4 with one lane per vertex) on scalars
+        constexpr bool kPk = (P % 2 == 0);
+        constexpr int PH = kPk ? P / 2 : 1;
+        f2 xi2[PH], dacc2[PH];
+#pragma unroll
+        for (int c = 0; c < PH; ++c) {
+            xi2[c] = kPk ? f2_pack(xi[2 * c], xi[(2 * c + 1) % P]) : 0ull;
+            dacc2[c] = 0ull;
+        }
         float dacc[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) dacc[c] = 0.0f;
@@ -932,18 +971,34 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 #pragma unroll
             for (int s2 = 0; s2 < G; ++s2) {
                 const int j = __shfl_sync(kFull, my_j, gbase + s2);
-                float xj[P];
-                if (j >= 0) {
-                    load_chunk<D, P>(X, j, gl, xj);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < P; ++c) xj[c] = xi[c];
-                }
                 float ss = 0.0f;
+                if constexpr (kPk) {
+                    f2 a2 = 0ull;
+                    if (j >= 0) {
+                        f2 xj2[PH];
+                        load_pairs<D, P>(X, j, gl, xj2);
 #pragma unroll
-                for (int c = 0; c < P; ++c) {
-                    const float df = xi[c] - xj[c];
-                    ss = fmaf(df, df, ss);
+                        for (int c = 0; c < PH; ++c) {
+                            const f2 t = f2_sub(xi2[c], xj2[c]);
+                            a2 = f2_fma(t, t, a2);
+                        }
+                    }
+                    float lo, hi;
+                    f2_unpack(a2, lo, hi);
+                    ss = lo + hi;
+                } else {
+                    float xj[P];
+                    if (j >= 0) {
+                        load_chunk<D, P>(X, j, gl, xj);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < P; ++c) xj[c] = xi[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < P; ++c) {
+                        const float df = xi[c] - xj[c];
+                        ss = fmaf(df, df, ss);
+                    }
                 }
 #pragma unroll
                 for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
@@ -975,7 +1030,25 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 const int j = __shfl_sync(kFull, my_j, gbase + s2);
                 const float c = __shfl_sync(kFull, my_c, gbase + s2);
                 const float wv = __shfl_sync(kFull, my_w, gbase + s2);
-                if (j >= 0) {
+                if constexpr (kPk) {
+                  if (j >= 0) {
+                    f2 xj2[PH], d2[PH];
+                    load_pairs<D, P>(X, j, gl, xj2);
+                    const f2 c2 = f2_pack(c, c);
+#pragma unroll
+                    for (int cc = 0; cc < PH; ++cc) {
+                        d2[cc] = f2_sub(xi2[cc], xj2[cc]);
+                        dacc2[cc] = f2_fma(c2, d2[cc], dacc2[cc]);
+                    }
+                    if (r * G + s2 >= ne && a.symmetric) {
+                        float pv[P];
+                        const f2 nc2 = f2_pack(-c, -c);
+#pragma unroll
+                        for (int cc = 0; cc < PH; ++cc) f2_unpack(f2_mul(nc2, d2[cc]), pv[2 * cc], pv[(2 * cc + 1) % P]);
+                        acc_add<D, G, P>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
+                    }
+                  }
+                } else if (j >= 0) {
                     float xj[P];
                     load_chunk<D, P>(X, j, gl, xj);
                     float diff[P];
@@ -1003,6 +1076,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 if (graph == home) atomicAdd(&s_used, (unsigned)slot_used);
                 else atomicAdd(&a.gst[graph].used, (unsigned long long)slot_used);
             }
+        }
+        if constexpr (kPk) {
+#pragma unroll
+            for (int c = 0; c < PH; ++c) f2_unpack(dacc2[c], dacc[2 * c], dacc[(2 * c + 1) % P]);
         }
         if (total > 0) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
