@@ -38,7 +38,8 @@ constexpr int kSamplerWarps = 8;
 constexpr int kMiniHash = 128;             // slots of the per-warp partner hash
 constexpr int kTileWaitLimit = 1 << 22;    // mbarrier polls before a tile CTA gives up
 constexpr int32_t kStatusTimeout = -5;     // gempe_status of a bounded device wait that gave up
-constexpr size_t kTileMinSmem = 80 * 1024; // keeps tile CTAs at two per SM (TMEM columns)
+constexpr int kTileCtasPerSm = 2;          // 128 TMEM columns and about 85 KB of shared memory each
+constexpr size_t kTileMinSmem = 48 * 1024; // at most four tile CTAs per SM: never more TMEM columns than 512
 
 // ---------------------------------------------------------------------------
 // k_block_sampler: one warp per tile.
@@ -242,13 +243,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-    uint32_t r;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    return __uint_as_float(r);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
@@ -261,21 +255,24 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
 
-// Shared memory of the tile kernel.  XT: the tile's BF16 rows (128 x DP),
-// XP: the partners' rows (64 x DP), DP = d + 16: column d holds 1 (so that
-// the products with them also give the row and column sums), d + 1 .. d + 15
-// zero.  CW: the pair coefficients, C in columns 0..63, W in 64..127.
+// Shared memory of the tile kernel.  XT: the tile's BF16 rows (128 x D),
+// XP: the partners' rows (64 x D).  CW: the pair coefficients, C in columns
+// 0..63, W in 64..127 (W fills the 128 rows the B product needs; its row and
+// column sums come from the epilogue and from CW).  TMEM: S in columns
+// 0..63, then A in 0..D-1 once the epilogue has read S, B in 64..64+D-1:
+// 128 columns, so that three CTAs share an SM.
 template <int D>
 struct TileTc {
-    static constexpr int DP = D + 16;
-    static constexpr uint32_t kCols = 256;                   // TMEM columns: S, A, B
-    static constexpr uint32_t kColS = 0, kColA = 64, kColB = 64 + DP;
+    static constexpr int DP = D;
+    static constexpr uint32_t kCols = 128;                   // TMEM columns: S then A, and B
+    static constexpr uint32_t kColS = 0, kColA = 0, kColB = 64;
     __nv_bfloat16 xt[kBlockT * DP];
     __nv_bfloat16 xp[kBlockP * DP];
     __nv_bfloat16 cw[kBlockT * 2 * kBlockP];
     float nt[kBlockT], np[kBlockP];
-    float row_w[2][kBlockT];
-    float col_w[kBlockP];
+    float row_w[2][kBlockT], row_c[2][kBlockT];   // per partner half: sums of w and of the rounded c
+    float col[2][2 * kBlockP];                    // per anchor half: column sums of the rounded C | W
+    MillsCoef mills[kMillsIntervals];             // the Mills-ratio table (pair terms)
     unsigned long long mask[kBlockT];
     int deg[kBlockT], kacc[kBlockT];
     int part[kBlockP];
@@ -288,18 +285,19 @@ struct TileTc {
 // k_tile_tc: block-sampled non-edges, one tile per CTA iteration, 8 warps.
 //   (1) S = X_T X_P^T (M 128, N 64, K d) into TMEM;
 //   (2) warp w reads rows 32 (w % 4) .. of S, partner columns 32 (w / 4) ..,
-//       forms the pair terms (c, w) with the masks and histograms, and
-//       writes them rounded to BF16 into CW;
-//   (3) A = C [X_P | 1] (K 64) gives sum_g c_ig x_g and rowsum(C);
-//       B = [C | W]^T [X_T | 1] (M 128, K 128) gives sum_i c_ig x_i and
-//       colsum(C) in rows 0..63, colsum(W) in rows 64..127;
+//       forms the pair terms (c, w) with the masks and histograms, writes
+//       them rounded to BF16 into CW and sums, per anchor and partner half,
+//       w and the rounded c (the row sums);
+//   (3) A = C X_P (K 64) gives sum_g c_ig x_g; B = [C | W]^T X_T (M 128,
+//       K 128) gives sum_i c_ig x_i in rows 0..63; meanwhile the column
+//       sums of the rounded C and W are added up from CW;
 //   (4) x_i rowsum(C) - A_i and the row sums of W go to the anchors'
 //       accumulators, x_g colsum(C) - B_g and colsum(W) to the partners'.
 // One thread issues the MMAs; their completion is signalled on an mbarrier
 // (bounded waits: a timeout sets the pack's status and ends the kernel).
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const EpochArgs a) {
     using L = TileTc<D>;
     constexpr int DP = L::DP;
     constexpr int CH = D / 8;                     // 16-byte chunks of a row
@@ -329,15 +327,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
         hist.hc[t] = 0u;
         hist.hd[t] = 0u;
     }
-    // the constant columns d .. d + 15 of XT and XP: 1, then zeros
-    for (int r = tid; r < kBlockT + kBlockP; r += blockDim.x) {
-        __nv_bfloat16* base = r < kBlockT ? sm.xt : sm.xp;
-        const int rr = r < kBlockT ? r : r - kBlockT;
-        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(base) + core_off(rr, D, DP)) =
-            make_uint4(0x3F80u, 0u, 0u, 0u);   // BF16 1.0 in the first element
-        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(base) + core_off(rr, D + 8, DP)) =
-            make_uint4(0u, 0u, 0u, 0u);
-    }
+    for (int t = tid; t < kMillsIntervals; t += blockDim.x) sm.mills[t].lh = __ldg(&a.mills[t].lh);
     if (tid == 0) {
         s_used = 0u;
         s_tile_used = 0u;
@@ -366,7 +356,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
         const int nv = min(kBlockT, gn - lt * kBlockT);
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
-        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
+        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills);
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
         const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
 
@@ -450,39 +440,46 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
             const unsigned long long mk = sm.mask[i];
             const float ni = sm.nt[i];
             const int di = sm.deg[i], ki = sm.kacc[i];
-            float rw = 0.0f;
+            float rw = 0.0f, rc = 0.0f;
 #pragma unroll
             for (int c8 = 0; c8 < 4; ++c8) {
                 const int p0 = 32 * half + 8 * c8;
                 float sv[8];
                 tmem_ld8(tmem + lane_base + L::kColS + (uint32_t)p0, sv);
+                // the eight terms without branches (masked pairs give 0),
+                // then their histogram counts
                 float cv[8], wv[8];
+                int bn[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int p = p0 + e;
-                    cv[e] = 0.0f;
-                    wv[e] = 0.0f;
-                    if (!((mk >> p) & 1ull)) {
-                        const float d2 = fmaxf(ni + sm.np[p] - 2.0f * sv[e], 0.0f);
-                        float delta, inv_delta;
-                        dist_of(d2, delta, inv_delta);
-                        const PairTerm pt = pair_term(delta, inv_delta, false, K);
-                        cv[e] = pt.c;
-                        wv[e] = pt.w;
-                        const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                        hist_sample(hist, a, graph, bin, di, ki, kBlockP);
-                    }
+                    const bool live = !((mk >> (p0 + e)) & 1ull);
+                    const float d2 = fmaxf(ni + sm.np[p0 + e] - 2.0f * sv[e], 0.0f);
+                    float delta, inv_delta;
+                    dist_of(d2, delta, inv_delta);
+                    const PairTerm pt = pair_term<false>(delta, inv_delta, false, K);
+                    cv[e] = live ? pt.c : 0.0f;
+                    wv[e] = live ? pt.w : 0.0f;
+                    bn[e] = live ? min((int)(delta * a.hist_scale), a.bins - 1) : -1;
                     rw += wv[e];
                 }
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (bn[e] >= 0) hist_sample(hist, a, graph, bn[e], di, ki, kBlockP);
                 unsigned char* cw = reinterpret_cast<unsigned char*>(sm.cw);
-                *reinterpret_cast<uint4*>(cw + core_off(i, p0, 2 * kBlockP)) =
-                    make_uint4(pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]), pack_bf16(cv[4], cv[5]),
-                               pack_bf16(cv[6], cv[7]));
+                const uint4 cpk = make_uint4(pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]), pack_bf16(cv[4], cv[5]),
+                                             pack_bf16(cv[6], cv[7]));
+                // the row sum of C as the products see it: of the rounded terms
+                rc += ((__uint_as_float(cpk.x << 16) + __uint_as_float(cpk.x & 0xFFFF0000u)) +
+                       (__uint_as_float(cpk.y << 16) + __uint_as_float(cpk.y & 0xFFFF0000u))) +
+                      ((__uint_as_float(cpk.z << 16) + __uint_as_float(cpk.z & 0xFFFF0000u)) +
+                       (__uint_as_float(cpk.w << 16) + __uint_as_float(cpk.w & 0xFFFF0000u)));
+                *reinterpret_cast<uint4*>(cw + core_off(i, p0, 2 * kBlockP)) = cpk;
                 *reinterpret_cast<uint4*>(cw + core_off(i, kBlockP + p0, 2 * kBlockP)) =
                     make_uint4(pack_bf16(wv[0], wv[1]), pack_bf16(wv[2], wv[3]), pack_bf16(wv[4], wv[5]),
                                pack_bf16(wv[6], wv[7]));
             }
             sm.row_w[half][i] = rw;
+            sm.row_c[half][i] = rc;
         }
         asm volatile("fence.proxy.async.shared::cta;");   // CW, for the tensor cores
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -502,6 +499,36 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
                        mma_idesc(128, DP, 1, 1), k > 0);
             tc_commit(&sm.mbar);
         }
+        {
+            // beside the products: the column sums of the rounded C and W.
+            // Eight lanes read rows 8 rb + j (j = lane % 8) of one 8-column
+            // group (128 contiguous bytes: no bank conflicts), over half of
+            // the row blocks; three halving exchanges leave lane j with the
+            // sum of column j of its group.
+            const int j = lane & 7, gid = 4 * w + (lane >> 3);   // 32 = 16 column groups x 2 anchor halves
+            const int cg = gid & 15, ah = gid >> 4;
+            const unsigned char* cwb = reinterpret_cast<const unsigned char*>(sm.cw);
+            float sv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int rb = 8 * ah; rb < 8 * ah + 8; ++rb) {
+                const uint4 u = *reinterpret_cast<const uint4*>(cwb + core_off(8 * rb + j, 8 * cg, 2 * kBlockP));
+                const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    sv[2 * e] += __uint_as_float(wd[e] << 16);
+                    sv[2 * e + 1] += __uint_as_float(wd[e] & 0xFFFF0000u);
+                }
+            }
+            const bool b4 = (j & 4) != 0, b2 = (j & 2) != 0, b1 = (j & 1) != 0;
+            float t4[4], t2[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                t4[q] = (b4 ? sv[4 + q] : sv[q]) + __shfl_xor_sync(0xffffffffu, b4 ? sv[q] : sv[4 + q], 4);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                t2[q] = (b2 ? t4[2 + q] : t4[q]) + __shfl_xor_sync(0xffffffffu, b2 ? t4[q] : t4[2 + q], 2);
+            sm.col[ah][8 * cg + j] = (b1 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? t2[0] : t2[1], 1);
+        }
         if (!mbar_wait(&sm.mbar, phase)) atomicExch(&sm.abort, 1);
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -509,12 +536,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
         if (sm.abort) break;
 
         // ---- (4) accumulators ----
-        // colsum(W) of partner g sits in TMEM lane 64 + g, column d of B
-        if (quad >= 2 && half == 0) sm.col_w[32 * (quad - 2) + lane] = tmem_ld1(tmem + lane_base + L::kColB + D);
         {
             // anchors: dims [half * D/2, (half + 1) * D/2)
             const int i = 32 * quad + lane;
-            const float rsum = tmem_ld1(tmem + lane_base + L::kColA + D);   // rowsum of C (rounded terms)
+            const float rsum = sm.row_c[0][i] + sm.row_c[1][i];   // rowsum of C (rounded terms)
             const bool live = i < nv && sm.kacc[i] > 0;
             float* row = a.acc + (size_t)(v0 + i) * a.acc_stride;
 #pragma unroll
@@ -538,12 +563,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile_tc(const EpochArgs a) 
             }
             if (live && half == 0) atomicAdd(row + D, sm.row_w[0][i] + sm.row_w[1][i]);
         }
-        __syncthreads();   // col_w
         if (a.symmetric && quad < 2) {
             // partners g = 32 quad + lane, dims [half * D/2, (half + 1) * D/2)
             const int g = 32 * quad + lane;
-            const float csum = tmem_ld1(tmem + lane_base + L::kColB + D);
-            const float wsum = sm.col_w[g];
+            const float csum = sm.col[0][g] + sm.col[1][g];
+            const float wsum = sm.col[0][kBlockP + g] + sm.col[1][kBlockP + g];
             const int gv = sm.part[g];
             float* row = a.acc + (size_t)gv * a.acc_stride;
 #pragma unroll
@@ -621,9 +645,11 @@ cudaError_t launch_tile_wait_probe(int limit, int32_t* dev_out, cudaStream_t s) 
 
 bool tile_dim(int d) { return d == 16 || d == 32 || d == 64; }
 
-// Shared memory of the tile kernel: its layout, the histogram bins, and at
-// least kTileMinSmem so that no more than two CTAs share an SM (each holds
-// 256 of the SM's 512 TMEM columns for the whole launch).
+// Shared memory of the tile kernel: its layout and three of the four
+// histogram arrays (edge counts stay zero, the per-slot weights are never
+// used: block sampling excludes that policy), at least kTileMinSmem so that
+// no more than four CTAs share an SM (each holds 128 of the SM's 512 TMEM
+// columns for the whole launch).
 size_t tile_smem_bytes(int d, int bins) {
     size_t base = 0;
     switch (d) {
@@ -632,7 +658,39 @@ size_t tile_smem_bytes(int d, int bins) {
         case 64: base = sizeof(TileTc<64>); break;
         default: return 0;
     }
-    return std::max<size_t>(base + hist_smem_bytes(bins), kTileMinSmem);
+    return std::max<size_t>(base + hist_smem_bytes(bins) / 4 * 3, kTileMinSmem);
+}
+
+// CTAs of the tile kernel per SM: what its registers, shared memory and
+// TMEM columns allow, at most kTileCtasPerSm.  Worked out here because the
+// runtime's occupancy query answers one CTA per SM for this kernel at any
+// shared-memory size, although two fit and run side by side (measured: the
+// launch with two per SM takes 0.64 of the time of the one with one).
+int tile_bf16_blocks_per_sm(int d, int bins) {
+    const void* f = nullptr;
+    int cols = 0;
+    switch (d) {
+        case 16: f = (const void*)k_tile_tc<16>; cols = (int)TileTc<16>::kCols; break;
+        case 32: f = (const void*)k_tile_tc<32>; cols = (int)TileTc<32>::kCols; break;
+        case 64: f = (const void*)k_tile_tc<64>; cols = (int)TileTc<64>::kCols; break;
+        default: return 1;
+    }
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const size_t smem_cta = tile_smem_bytes(d, bins) + fa.sharedSizeBytes + (size_t)reserved;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;   // allocated per warp in units of 256
+    const int by_regs = regs_sm / (regs_warp * (kTileThreads / 32));
+    const int by_smem = (int)((size_t)smem_sm / smem_cta);
+    const int by_tmem = 512 / cols;
+    const int blocks = std::min(std::min(by_regs, by_smem), std::min(by_tmem, kTileCtasPerSm));
+    return blocks < 1 ? 1 : blocks;
 }
 
 cudaError_t prepare_tile_kernel(int d, int bins) {
@@ -655,7 +713,7 @@ cudaError_t launch_block_sampler(const EpochArgs& a, const int4* units, int n_un
     return cudaGetLastError();
 }
 
-// blocks_per_sm: 0 = two CTAs per SM (what fits with the histogram bins)
+// blocks_per_sm: CTAs per SM (0: two)
 int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm) {
     const int per_sm = blocks_per_sm > 0 ? blocks_per_sm : 2;
     int grid = n_tile_items < sm_count * per_sm ? n_tile_items : sm_count * per_sm;

@@ -136,9 +136,12 @@ __device__ __forceinline__ bool edge_set_contains(const void* keys, int narrow, 
 // delta = 0, or when d < 0 is clamped to 0, s = 0 and c = -w.
 // --------------------------------------------------------------------------
 // Mills-ratio table: on [kMillsV0, kMillsV1) with kMillsStepsPerUnit
-// intervals per unit of v, interval i holds cubic coefficients (in the local
-// coordinate x in [0, 1)) of log2 h(v) and of log2 T(v), built on the host
-// from Hermite data (log2 h)' = T / ln2, (log2 T)' = (h T - 1) / (T ln2).
+// intervals per unit of v, interval i holds the cubic coefficients (in the
+// local coordinate x in [0, 1)) of log2 h(v), the Hermite interpolant built
+// on the host from the values and the slopes (log2 h)' = T / ln2.  Since
+// h' = h T, T itself is ln2 times the derivative of that cubic in v: one
+// 16-byte entry per interval gives both h and T (FP32 relative error about
+// 1.6e-7 for either, the same as a second table of log2 T would give).
 constexpr float kMillsV0 = -14.0f;
 constexpr float kMillsV1 = 8.0f;
 constexpr int kMillsStepsPerUnit = 32;
@@ -146,7 +149,6 @@ constexpr int kMillsIntervals = (int)((kMillsV1 - kMillsV0) * kMillsStepsPerUnit
 
 struct MillsCoef {
     float4 lh;   // log2 h: c0 + x (c1 + x (c2 + x c3))
-    float4 lt;   // log2 T
 };
 
 struct PairConsts {
@@ -182,9 +184,10 @@ __device__ __forceinline__ float mills_tail_T(float v) {
     return 1.0f / t;
 }
 
-// h(v) = phi(v)/Q(v) and T(v) = h(v) - v > 0.  On the table range both come
-// from the interpolated logarithms; from kMillsV1 on, T by the continued
-// fraction and h = v + T; below kMillsV0, h is below the FP32 range (h = 0).
+// h(v) = phi(v)/Q(v) and T(v) = h(v) - v > 0.  On the table range h comes
+// from the interpolated logarithm and T from its slope, T = ln2 d(log2 h)/dv;
+// from kMillsV1 on, T by the continued fraction and h = v + T; below
+// kMillsV0, h is below the FP32 range (h = 0, T = -v).
 // kGlobal: the table is in global memory (read through the read-only
 // cache); otherwise it is a copy in shared memory.
 template <bool kGlobal>
@@ -194,11 +197,11 @@ __device__ __forceinline__ void mills_t(float v, float& h, float& T, const Mills
         const int i = min((int)pos, kMillsIntervals - 1);
         const float x = pos - (float)i;
         const float4 a = kGlobal ? __ldg(&tab[i].lh) : tab[i].lh;
-        const float4 b = kGlobal ? __ldg(&tab[i].lt) : tab[i].lt;
         const float lh = fmaf(fmaf(fmaf(a.w, x, a.z), x, a.y), x, a.x);
-        const float lt = fmaf(fmaf(fmaf(b.w, x, b.z), x, b.y), x, b.x);
+        const float dlh = fmaf(fmaf(3.0f * a.w, x, 2.0f * a.z), x, a.y);   // d(log2 h)/dx
+        constexpr float kTScale = 0.69314718055994531f * (float)kMillsStepsPerUnit;
         h = (v < kMillsV0) ? 0.0f : exp2f(lh);
-        T = (v < kMillsV0) ? -v : exp2f(lt);
+        T = (v < kMillsV0) ? -v : dlh * kTScale;
     } else {
         T = mills_tail_T(v);
         h = v + T;
@@ -214,12 +217,14 @@ struct PairTerm {
     float w;   // weight added to z_self
 };
 
-// delta = sqrt(ss), inv_delta = 1/delta (0 when delta = 0)
+// delta = sqrt(ss), inv_delta = 1/delta (0 when delta = 0).  kGlobal: the
+// table K.mills is in global memory, else a copy in shared memory.
+template <bool kGlobal = true>
 __device__ __forceinline__ PairTerm pair_term(float delta, float inv_delta, bool edge, const PairConsts& K) {
     const float u = (delta - K.mu) * K.inv_sigma;
     const float v = edge ? u : -u;
     float h, T;
-    mills(v, h, T, K.mills);
+    mills_t<kGlobal>(v, h, T, K.mills);
     const float w = h * (K.printed ? (h + T) : T) * K.w_scale;
     const float g = h * K.g_scale;                   // |dl'| / 2
     // d = delta - g/w (edge) < 0  <=>  g > w delta

@@ -222,6 +222,7 @@ int tile_grid(int n_tile_items, int sm_count, int blocks_per_sm);
 bool tile_dim(int d);
 size_t tile_smem_bytes(int d, int bins);
 cudaError_t prepare_tile_kernel(int d, int bins);
+int tile_bf16_blocks_per_sm(int d, int bins);
 // Test only: one tile-shaped CTA whose mbarrier wait (limit polls) runs out;
 // dev_out[0] = the status it records, dev_out[1] = 1 after it freed its TMEM.
 cudaError_t launch_tile_wait_probe(int limit, int32_t* dev_out, cudaStream_t s);

@@ -1301,7 +1301,8 @@ __device__ float block_fit_sigma(const float* he, const float* hn, int bins, flo
 __device__ __forceinline__ void load_mills_smem(MillsCoef* dst) {
     const float4* src = reinterpret_cast<const float4*>(g_mills);
     float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int q = threadIdx.x; q < 2 * kMillsIntervals; q += blockDim.x) d4[q] = __ldg(src + q);
+    constexpr int kQuads = (int)(sizeof(MillsCoef) / sizeof(float4)) * kMillsIntervals;
+    for (int q = threadIdx.x; q < kQuads; q += blockDim.x) d4[q] = __ldg(src + q);
 }
 
 // Shared memory of the slope-fit blocks: [2][bins] floats, then the table.

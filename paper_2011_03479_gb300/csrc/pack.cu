@@ -707,7 +707,8 @@ gempe_status Pack::set_shape(const PackShape& s) {
     PK(cudaStreamSynchronize(stream), "copy work units");
     sweep_grid = grid;
     tile_grid = gempe::tile_grid(n_tile_items, sm_count,
-                                 sh.kernel == 2 ? 1 : (p.precision == 1 ? 0 : tile_f32_blocks_per_sm(d, bins)));
+                                 sh.kernel == 2 ? 1
+                                 : (p.precision == 1 ? tile_bf16_blocks_per_sm(d, bins) : tile_f32_blocks_per_sm(d, bins)));
     shape = sh;
     return GEMPE_OK;
 }
