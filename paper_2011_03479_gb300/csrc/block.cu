@@ -281,6 +281,47 @@ struct TileTc {
     int abort;
 };
 
+// The global words a tile's staging needs, loaded one tile ahead so that
+// their latency hides behind the previous tile: the tile and its graph, the
+// anchor's mask word and degree (thread t < 128 stages anchor t), the
+// partner ids of this thread's 16-byte row chunks, and partner t (t < 64).
+template <int D>
+struct TileAhead {
+    static constexpr int kChunks = (kBlockP * (D / 8) + kTileThreads - 1) / kTileThreads;
+    int tile, graph, v0, nv;
+    unsigned long long m;
+    int deg, part;
+    int pid[kChunks];
+};
+
+template <int D>
+__device__ __forceinline__ TileAhead<D> tile_ahead(const EpochArgs& a, int it, int tid) {
+    constexpr int CH = D / 8;
+    TileAhead<D> t;
+    const int2 ti = __ldg(a.tile_items + it);
+    t.tile = ti.x;
+    t.graph = ti.y;
+    const int gv0 = __ldg(&a.graphs[t.graph].v0), gn = __ldg(&a.graphs[t.graph].n);
+    const int lt = t.tile - __ldg(&a.graphs[t.graph].t0);
+    t.v0 = gv0 + lt * kBlockT;
+    t.nv = min(kBlockT, gn - lt * kBlockT);
+    const int epoch = a.gst[t.graph].epoch;
+    const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + t.tile) * kBlockP;
+    t.m = ~0ull;
+    t.deg = 0;
+    if (tid < t.nv) {   // nv <= kBlockT
+        t.m = a.block_mask[(size_t)(epoch & 1) * (size_t)a.rows + t.v0 + tid];
+        t.deg = __ldg(a.row_ptr + t.v0 + tid + 1) - __ldg(a.row_ptr + t.v0 + tid);
+    }
+#pragma unroll
+    for (int j = 0; j < TileAhead<D>::kChunks; ++j) {
+        const int c = tid + kTileThreads * j;
+        t.pid[j] = c < kBlockP * CH ? __ldg(part + c / CH) : 0;
+    }
+    t.part = tid < kBlockP ? __ldg(part + tid) : 0;
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // k_tile_tc: block-sampled non-edges, one tile per CTA iteration, 8 warps.
 //   (1) S = X_T X_P^T (M 128, N 64, K d) into TMEM;
@@ -295,6 +336,9 @@ struct TileTc {
 //       accumulators, x_g colsum(C) - B_g and colsum(W) to the partners'.
 // One thread issues the MMAs; their completion is signalled on an mbarrier
 // (bounded waits: a timeout sets the pack's status and ends the kernel).
+// The global words of the next tile's staging are loaded while this tile
+// runs; the pair-term loop over the four 8-partner chunks is kept rolled
+// (the unrolled kernel stalled on instruction fetch).
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const EpochArgs a) {
@@ -347,40 +391,42 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;   // this warp's TMEM lanes
     uint32_t phase = 0;
 
+    TileAhead<D> nxt;
+    if (it0 < it1) nxt = tile_ahead<D>(a, it0, tid);
     for (int it = it0; it < it1; it += istep) {
-        const int2 ti = __ldg(a.tile_items + it);
-        const int tile = ti.x, graph = ti.y;
-        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
-        const int lt = tile - __ldg(&a.graphs[graph].t0);
-        const int v0 = gv0 + lt * kBlockT;
-        const int nv = min(kBlockT, gn - lt * kBlockT);
+        const TileAhead<D> cur = nxt;
+        const int tile = cur.tile, graph = cur.graph, v0 = cur.v0, nv = cur.nv;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills);
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
-        const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
 
         // ---- stage: rows (cp.async into the core layout), partners, masks ----
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();   // the previous tile's shared data and TMEM are no longer read
-        if (tid < kBlockP) sm.part[tid] = __ldg(part + tid);
+        if (tid < kBlockP) sm.part[tid] = cur.part;
         for (int c = tid; c < kBlockT * CH; c += blockDim.x) {
             const int r = c / CH, q = c - r * CH;
             unsigned char* dst = reinterpret_cast<unsigned char*>(sm.xt) + core_off(r, 8 * q, DP);
             if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + 8 * q);
             else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
         }
-        for (int c = tid; c < kBlockP * CH; c += blockDim.x) {
-            const int r = c / CH, q = c - r * CH;
-            cp_async16(reinterpret_cast<unsigned char*>(sm.xp) + core_off(r, 8 * q, DP),
-                       a.xb + (size_t)__ldg(part + r) * D + 8 * q);
+#pragma unroll
+        for (int j = 0; j < TileAhead<D>::kChunks; ++j) {
+            const int c = tid + kTileThreads * j;
+            if (c < kBlockP * CH) {
+                const int r = c / CH, q = c - r * CH;
+                cp_async16(reinterpret_cast<unsigned char*>(sm.xp) + core_off(r, 8 * q, DP),
+                           a.xb + (size_t)cur.pid[j] * D + 8 * q);
+            }
         }
-        for (int v = tid; v < kBlockT; v += blockDim.x) {
+        if (tid < kBlockT) {
+            const int v = tid;
             if (v < nv) {
-                const unsigned long long m = bmask[v0 + v];
+                const unsigned long long m = cur.m;
                 bmask[v0 + v] = 0ull;   // read once: the buffer starts empty for the epoch two ahead
                 sm.mask[v] = m;
-                sm.deg[v] = __ldg(a.row_ptr + v0 + v + 1) - __ldg(a.row_ptr + v0 + v);
+                sm.deg[v] = cur.deg;
                 sm.kacc[v] = kBlockP - __popcll(m);
                 atomicAdd(&s_tile_used, (unsigned)(kBlockP - __popcll(m)));
             } else {
@@ -389,6 +435,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
                 sm.kacc[v] = 0;
             }
         }
+        if (it + istep < it1) nxt = tile_ahead<D>(a, it + istep, tid);
         cp_async_wait_all();
         __syncthreads();
         if (tid == 0) {
@@ -441,7 +488,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             const float ni = sm.nt[i];
             const int di = sm.deg[i], ki = sm.kacc[i];
             float rw = 0.0f, rc = 0.0f;
-#pragma unroll
+#pragma unroll 1
             for (int c8 = 0; c8 < 4; ++c8) {
                 const int p0 = 32 * half + 8 * c8;
                 float sv[8];
