@@ -26,6 +26,7 @@
 #include "device_math.cuh"
 #include "engine.cuh"
 #include "hist.cuh"
+#include "tile_ahead.cuh"
 
 namespace gempe {
 
@@ -281,47 +282,6 @@ struct TileTc {
     int abort;
 };
 
-// The global words a tile's staging needs, loaded one tile ahead so that
-// their latency hides behind the previous tile: the tile and its graph, the
-// anchor's mask word and degree (thread t < 128 stages anchor t), the
-// partner ids of this thread's 16-byte row chunks, and partner t (t < 64).
-template <int D>
-struct TileAhead {
-    static constexpr int kChunks = (kBlockP * (D / 8) + kTileThreads - 1) / kTileThreads;
-    int tile, graph, v0, nv;
-    unsigned long long m;
-    int deg, part;
-    int pid[kChunks];
-};
-
-template <int D>
-__device__ __forceinline__ TileAhead<D> tile_ahead(const EpochArgs& a, int it, int tid) {
-    constexpr int CH = D / 8;
-    TileAhead<D> t;
-    const int2 ti = __ldg(a.tile_items + it);
-    t.tile = ti.x;
-    t.graph = ti.y;
-    const int gv0 = __ldg(&a.graphs[t.graph].v0), gn = __ldg(&a.graphs[t.graph].n);
-    const int lt = t.tile - __ldg(&a.graphs[t.graph].t0);
-    t.v0 = gv0 + lt * kBlockT;
-    t.nv = min(kBlockT, gn - lt * kBlockT);
-    const int epoch = a.gst[t.graph].epoch;
-    const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + t.tile) * kBlockP;
-    t.m = ~0ull;
-    t.deg = 0;
-    if (tid < t.nv) {   // nv <= kBlockT
-        t.m = a.block_mask[(size_t)(epoch & 1) * (size_t)a.rows + t.v0 + tid];
-        t.deg = __ldg(a.row_ptr + t.v0 + tid + 1) - __ldg(a.row_ptr + t.v0 + tid);
-    }
-#pragma unroll
-    for (int j = 0; j < TileAhead<D>::kChunks; ++j) {
-        const int c = tid + kTileThreads * j;
-        t.pid[j] = c < kBlockP * CH ? __ldg(part + c / CH) : 0;
-    }
-    t.part = tid < kBlockP ? __ldg(part + tid) : 0;
-    return t;
-}
-
 // ---------------------------------------------------------------------------
 // k_tile_tc: block-sampled non-edges, one tile per CTA iteration, 8 warps.
 //   (1) S = X_T X_P^T (M 128, N 64, K d) into TMEM;
@@ -391,10 +351,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;   // this warp's TMEM lanes
     uint32_t phase = 0;
 
-    TileAhead<D> nxt;
-    if (it0 < it1) nxt = tile_ahead<D>(a, it0, tid);
+    using Ahead = TileAhead<CH, kTileThreads>;
+    Ahead nxt;
+    if (it0 < it1) nxt = tile_ahead<CH, kTileThreads>(a, it0, tid);
     for (int it = it0; it < it1; it += istep) {
-        const TileAhead<D> cur = nxt;
+        const Ahead cur = nxt;
         const int tile = cur.tile, graph = cur.graph, v0 = cur.v0, nv = cur.nv;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
@@ -412,7 +373,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
-        for (int j = 0; j < TileAhead<D>::kChunks; ++j) {
+        for (int j = 0; j < Ahead::kChunks; ++j) {
             const int c = tid + kTileThreads * j;
             if (c < kBlockP * CH) {
                 const int r = c / CH, q = c - r * CH;
@@ -435,7 +396,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
                 sm.kacc[v] = 0;
             }
         }
-        if (it + istep < it1) nxt = tile_ahead<D>(a, it + istep, tid);
+        if (it + istep < it1) nxt = tile_ahead<CH, kTileThreads>(a, it + istep, tid);
         cp_async_wait_all();
         __syncthreads();
         if (tid == 0) {

@@ -23,13 +23,17 @@
 //       by vector atomics (partners only in the symmetric form).
 //
 // Every product and sum is FP32 on the CUDA cores; only the order of the
-// additions differs from the per-pair evaluation of the sweep.
+// additions differs from the per-pair evaluation of the sweep.  The global
+// words of the next tile's staging are loaded while a tile runs, and the
+// pair-term loop stays rolled over anchor rows (its squared distances wait
+// in C's slots), which keeps the kernel's code small.
 #include <algorithm>
 
 #include "device_math.cuh"
 #include "engine.cuh"
 #include "f32x2.cuh"
 #include "hist.cuh"
+#include "tile_ahead.cuh"
 
 namespace gempe {
 
@@ -132,39 +136,42 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         s_tile_used = 0u;
     }
 
+    constexpr int CH = D / 4;   // 16-byte chunks of a row
+    using Ahead = TileAhead<CH, kF32Threads>;
+    Ahead nxt;
+    if (it0 < it1) nxt = tile_ahead<CH, kF32Threads>(a, it0, tid);
     for (int it = it0; it < it1; it += istep) {
-        const int2 ti = __ldg(a.tile_items + it);
-        const int tile = ti.x, graph = ti.y;
-        const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
-        const int lt = tile - __ldg(&a.graphs[graph].t0);
-        const int v0 = gv0 + lt * kBlockT;
-        const int nv = min(kBlockT, gn - lt * kBlockT);
+        const Ahead cur = nxt;
+        const int graph = cur.graph, v0 = cur.v0, nv = cur.nv;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
-        const int32_t* part = a.block_part + ((size_t)(epoch & 1) * (size_t)a.n_tiles + tile) * kBlockP;
 
         // ---- (1) stage rows, partners, masks ----
         __syncthreads();   // the previous tile's shared data is no longer read
-        if (tid < kBlockP) sm.part[tid] = __ldg(part + tid);
-        constexpr int CH = D / 4;   // 16-byte chunks of a row
+        if (tid < kBlockP) sm.part[tid] = cur.part;
         for (int q = tid; q < kBlockT * CH; q += blockDim.x) {
             const int r = q / CH, c4 = q - r * CH;
             float* dst = sm.xt + r * R + 4 * c4;
             if (r < nv) copy16_async(dst, a.x + (size_t)(v0 + r) * D + 4 * c4);
             else *reinterpret_cast<float4*>(dst) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        for (int q = tid; q < kBlockP * CH; q += blockDim.x) {
-            const int r = q / CH, c4 = q - r * CH;
-            copy16_async(sm.xp + r * R + 4 * c4, a.x + (size_t)__ldg(part + r) * D + 4 * c4);
+#pragma unroll
+        for (int j = 0; j < Ahead::kChunks; ++j) {
+            const int q = tid + kF32Threads * j;
+            if (q < kBlockP * CH) {
+                const int r = q / CH, c4 = q - r * CH;
+                copy16_async(sm.xp + r * R + 4 * c4, a.x + (size_t)cur.pid[j] * D + 4 * c4);
+            }
         }
-        for (int v = tid; v < kBlockT; v += blockDim.x) {
+        if (tid < kBlockT) {
+            const int v = tid;
             if (v < nv) {
-                const unsigned long long m = bmask[v0 + v];
+                const unsigned long long m = cur.m;
                 bmask[v0 + v] = 0ull;   // read once: the buffer starts empty for the epoch two ahead
                 sm.mask[v] = m;
-                sm.deg[v] = __ldg(a.row_ptr + v0 + v + 1) - __ldg(a.row_ptr + v0 + v);
+                sm.deg[v] = cur.deg;
                 sm.kacc[v] = kBlockP - __popcll(m);
                 atomicAdd(&s_tile_used, (unsigned)(kBlockP - __popcll(m)));
             } else {
@@ -173,6 +180,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                 sm.kacc[v] = 0;
             }
         }
+        if (it + istep < it1) nxt = tile_ahead<CH, kF32Threads>(a, it + istep, tid);
         copy_async_wait_all();
         __syncthreads();
         if (tid == 0) {
@@ -216,47 +224,56 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                     }
                 }
             }
-            float rc[4], rw[4];
+            // the squared distances wait in C's slots (each thread reads back
+            // only its own), so that the term loop below stays rolled over r
 #pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float lo, hi;
+                    f2_unpack(acc2[r][j], lo, hi);
+                    sm.c[(ta + 16 * (4 * h + r)) * RC + tp + 16 * j] = lo + hi;
+                }
+#pragma unroll 1
             for (int r = 0; r < 4; ++r) {
                 const int i = ta + 16 * (4 * h + r);
                 const unsigned long long mk = sm.mask[i];
                 const int di = sm.deg[i], ki = sm.kacc[i];
-                rc[r] = rw[r] = 0.0f;
+                float cv[4], wv[4];
+                int bn[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {   // the four terms without branches (masked pairs give 0)
+                    const int p = tp + 16 * j;
+                    const bool live = !((mk >> p) & 1ull);
+                    float delta, inv_delta;
+                    dist_of(sm.c[i * RC + p], delta, inv_delta);
+                    const PairTerm pt = pair_term(delta, inv_delta, false, K);
+                    cv[j] = live ? pt.c : 0.0f;
+                    wv[j] = live ? pt.w : 0.0f;
+                    bn[j] = live ? min((int)(delta * a.hist_scale), a.bins - 1) : -1;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (bn[j] >= 0) hist_sample(hist, a, graph, bn[j], di, ki, kBlockP);
+                float rc = 0.0f, rw = 0.0f;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int p = tp + 16 * j;
-                    float cv = 0.0f, wv = 0.0f;
-                    if (!((mk >> p) & 1ull)) {
-                        float lo, hi, delta, inv_delta;
-                        f2_unpack(acc2[r][j], lo, hi);
-                        dist_of(lo + hi, delta, inv_delta);
-                        const PairTerm pt = pair_term(delta, inv_delta, false, K);
-                        cv = pt.c;
-                        wv = pt.w;
-                        const int bin = min((int)(delta * a.hist_scale), a.bins - 1);
-                        hist_sample(hist, a, graph, bin, di, ki, kBlockP);
-                    }
-                    sm.c[i * RC + p] = cv;
-                    rc[r] += cv;
-                    rw[r] += wv;
-                    cc[j] += cv;
-                    cw[j] += wv;
+                    sm.c[i * RC + tp + 16 * j] = cv[j];
+                    rc += cv[j];
+                    rw += wv[j];
+                    cc[j] += cv[j];
+                    cw[j] += wv[j];
                 }
-            }
-            // row sums over the 16 lanes of a half-warp (one anchor group)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
+                // row sums over the 16 lanes of a half-warp (one anchor group)
 #pragma unroll
                 for (int o = 1; o < 16; o <<= 1) {
-                    rc[r] += __shfl_xor_sync(0xFFFFFFFFu, rc[r], o);
-                    rw[r] += __shfl_xor_sync(0xFFFFFFFFu, rw[r], o);
+                    rc += __shfl_xor_sync(0xFFFFFFFFu, rc, o);
+                    rw += __shfl_xor_sync(0xFFFFFFFFu, rw, o);
                 }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (tp == r) sm.rsum_c[ta + 16 * (4 * h + r)] = rc[r];
-                if (tp == 8 + r) sm.rsum_w[ta + 16 * (4 * h + r)] = rw[r];
+                if (tp == 0) {
+                    sm.rsum_c[i] = rc;
+                    sm.rsum_w[i] = rw;
+                }
             }
         }
         // column sums: the warp's two anchor groups, then per-warp partials
