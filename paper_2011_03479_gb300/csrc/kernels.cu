@@ -89,16 +89,27 @@ __global__ void k_init(float* __restrict__ x, __nv_bfloat16* __restrict__ xb, in
 }
 
 // ---------------------------------------------------------------------------
-// Coordinate chunks: a pair is handled by G lanes, lane gl owning the P = D/G
-// coordinates [gl*P, gl*P + P).
+// Coordinate chunks: a pair is handled by G = D/P lanes, each owning P of the
+// row's coordinates.  The row is cut into 16-byte units (U = 4 coordinates of
+// FP32 positions, 8 of BF16 ones); when P is a multiple of U, lane gl owns
+// the units gl, gl + G, gl + 2G, ..., so that each load instruction of the
+// G lanes reads one contiguous stretch of the row (whole 32-byte sectors);
+// otherwise lane gl owns the coordinates [gl*P, gl*P + P).  chunk_unit_off
+// gives the first coordinate of the lane's unit q.
 // ---------------------------------------------------------------------------
+template <int D, int P, int U>
+__device__ __forceinline__ int chunk_unit_off(int gl, int q) {
+    return U * gl + U * (D / P) * q;
+}
+
 template <int D, int P>
 __device__ __forceinline__ void load_chunk(const float* __restrict__ x, int row, int gl, float* out) {
     const float* p = x + (size_t)row * D + gl * P;
     if constexpr (P % 4 == 0) {
+        const float* r = x + (size_t)row * D;
 #pragma unroll
         for (int c = 0; c < P; c += 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(p + c));
+            const float4 v = __ldg(reinterpret_cast<const float4*>(r + chunk_unit_off<D, P, 4>(gl, c / 4)));
             out[c] = v.x; out[c + 1] = v.y; out[c + 2] = v.z; out[c + 3] = v.w;
         }
     } else if constexpr (P == 2) {
@@ -118,9 +129,10 @@ template <int D, int P>
 __device__ __forceinline__ void load_chunk(const __nv_bfloat16* __restrict__ x, int row, int gl, float* out) {
     const __nv_bfloat16* p = x + (size_t)row * D + gl * P;
     if constexpr (P % 8 == 0) {
+        const __nv_bfloat16* r = x + (size_t)row * D;
 #pragma unroll
         for (int c = 0; c < P; c += 8) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + c));
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(r + chunk_unit_off<D, P, 8>(gl, c / 8)));
             out[c] = bf16_lo(v.x); out[c + 1] = bf16_hi(v.x); out[c + 2] = bf16_lo(v.y); out[c + 3] = bf16_hi(v.y);
             out[c + 4] = bf16_lo(v.z); out[c + 5] = bf16_hi(v.z); out[c + 6] = bf16_lo(v.w); out[c + 7] = bf16_hi(v.w);
         }
@@ -141,9 +153,10 @@ __device__ __forceinline__ void load_pairs(const float* __restrict__ x, int row,
     static_assert(P % 2 == 0, "packed pairs need an even chunk");
     const float* p = x + (size_t)row * D + gl * P;
     if constexpr (P % 4 == 0) {
+        const float* r = x + (size_t)row * D;
 #pragma unroll
         for (int c = 0; c < P; c += 4) {
-            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p + c));
+            const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(r + chunk_unit_off<D, P, 4>(gl, c / 4)));
             out[c / 2] = v.x;
             out[c / 2 + 1] = v.y;
         }
@@ -161,8 +174,10 @@ __device__ __forceinline__ void load_pairs(const __nv_bfloat16* __restrict__ x, 
     for (int c = 0; c < P / 2; ++c) out[c] = f2_pack(v[2 * c], v[2 * c + 1]);
 }
 
-// acc row layout: D values then z, padded to a multiple of 4 floats.
-template <int D, int G, int P>
+// acc row layout: D values then z, padded to a multiple of 4 floats.  U:
+// the 16-byte unit of the positions the lane's coordinates were loaded with
+// (4 for FP32, 8 for BF16), so that v[] maps to the same coordinates.
+template <int D, int G, int P, int U = 4>
 __device__ __forceinline__ void acc_add(float* row, int gl, const float* v, float z) {
     if constexpr (D <= 3) {   // G == 1: the whole row is one float4 {v..., z, 0...}
         float4 q;
@@ -173,7 +188,13 @@ __device__ __forceinline__ void acc_add(float* row, int gl, const float* v, floa
         atomicAdd(reinterpret_cast<float4*>(row), q);
     } else {
         float* p = row + gl * P;
-        if constexpr (P % 4 == 0) {
+        if constexpr (P % U == 0) {
+#pragma unroll
+            for (int c = 0; c < P; c += 4) {
+                const int off = chunk_unit_off<D, P, U>(gl, c / U) + c % U;
+                atomicAdd(reinterpret_cast<float4*>(row + off), make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]));
+            }
+        } else if constexpr (P % 4 == 0) {
 #pragma unroll
             for (int c = 0; c < P; c += 4)
                 atomicAdd(reinterpret_cast<float4*>(p + c), make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]));
@@ -827,11 +848,32 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
     if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
 }
 
+// Sums over the G lanes of a group (G a power of two, groups aligned to G
+// lanes) of G values per lane, scattered: lane gl returns the sum of every
+// lane's v[gl].  Each halving step keeps the half of the entries whose index
+// agrees with gl in that bit and adds the partner's copy of it: G - 1
+// shuffles for the G sums, against G log2 G for G butterfly reductions.
+template <int G>
+__device__ __forceinline__ float group_sum_scatter(float (&v)[G], int gl) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (gl & o) != 0;
+#pragma unroll
+        for (int q = 0; q < o; ++q) {
+            const float keep = up ? v[o + q] : v[q];
+            const float send = up ? v[q] : v[o + q];
+            v[q] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+    return v[0];
+}
+
 // ---------------------------------------------------------------------------
 // Pair sweep for d >= 8.  A warp is 32/G lane groups of G lanes; each group
 // owns one work unit (a vertex with its samples, or one chunk of a hub's
-// row), lane gl of the group owning coordinates [gl*P, gl*P + P) of every
-// row, P = D/G.  The host packs the units into warp tasks of 32/G units of
+// row), lane gl of the group owning P = D/G coordinates of every row (the
+// 16-byte units gl, gl + G, ... of the row when P is a multiple of a unit:
+// each load instruction of the group then reads a contiguous stretch).  The host packs the units into warp tasks of 32/G units of
 // similar size, so the groups of a warp run the same number of rounds.
 //
 // A round takes G pairs of the group's vertex, one per lane:
@@ -849,6 +891,7 @@ template <int D, int G, typename PT>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
     constexpr int P = D / G;
     constexpr int PG = 32 / G;            // groups (units) per warp task
+    constexpr int kU = sizeof(PT) == 2 ? 8 : 4;   // coordinates per 16-byte unit of the positions
     const PT* X = pos_of<PT>(a);
     extern __shared__ unsigned int s_u32[];
     // block b takes the tasks [bounds[b], bounds[b+1]) (ranges of equal
@@ -939,6 +982,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
         int slot_used = 0;   // per-slot policy: accepted samples this lane evaluated
         const int rounds = (total + G - 1) / G;
         const int rmax = (int)__reduce_max_sync(kFull, (unsigned)rounds);
+        // the partners' weights travel only when some group of the warp has
+        // samples whose terms go to the partners as well
+        const bool pass_w = a.symmetric && __any_sync(kFull, has_samples);
 
         // even chunks run on packed FP32 pairs (coordinates 2c, 2c + 1 in the
         // two halves of a 64-bit register: the same roundings, half the
@@ -966,11 +1012,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 if (block) my_j = ((bmask_v >> t) & 1ull) ? -1 : __ldg(tp + t);
                 else my_j = __ldg(sp + t);
             }
-            // (A) distances
+            // (A) distances.  With FP32 positions small groups keep the
+            // partners' ids for (C) and leave each lane's partial sums to one
+            // scattered reduction (fewer shuffles; with BF16 positions the
+            // same change measured slower, so those keep the butterflies).
+            constexpr bool kKeep = G <= 8 && sizeof(PT) == 4;
+            int js[kKeep ? G : 1];
+            float part[kKeep ? G : 1];
             float my_ss = 0.0f;
 #pragma unroll
             for (int s2 = 0; s2 < G; ++s2) {
                 const int j = __shfl_sync(kFull, my_j, gbase + s2);
+                if constexpr (kKeep) js[s2] = j;
                 float ss = 0.0f;
                 if constexpr (kPk) {
                     f2 a2 = 0ull;
@@ -1000,10 +1053,15 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                         ss = fmaf(df, df, ss);
                     }
                 }
+                if constexpr (kKeep) {
+                    part[s2] = ss;
+                } else {
 #pragma unroll
-                for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
-                if (gl == s2) my_ss = ss;
+                    for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+                    if (gl == s2) my_ss = ss;
+                }
             }
+            if constexpr (kKeep) my_ss = group_sum_scatter<G>(part, gl);
             // (B) the pair term of this lane's pair
             const bool my_edge = q < ne;
             float my_c = 0.0f, my_w = 0.0f;
@@ -1027,9 +1085,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
             // (C) the vertex's sum and the sampled partners' terms
 #pragma unroll
             for (int s2 = 0; s2 < G; ++s2) {
-                const int j = __shfl_sync(kFull, my_j, gbase + s2);
+                int j;
+                if constexpr (kKeep) j = js[s2];
+                else j = __shfl_sync(kFull, my_j, gbase + s2);
                 const float c = __shfl_sync(kFull, my_c, gbase + s2);
-                const float wv = __shfl_sync(kFull, my_w, gbase + s2);
+                const float wv = pass_w ? __shfl_sync(kFull, my_w, gbase + s2) : 0.0f;
                 if constexpr (kPk) {
                   if (j >= 0) {
                     f2 xj2[PH], d2[PH];
@@ -1045,7 +1105,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                         const f2 nc2 = f2_pack(-c, -c);
 #pragma unroll
                         for (int cc = 0; cc < PH; ++cc) f2_unpack(f2_mul(nc2, d2[cc]), pv[2 * cc], pv[(2 * cc + 1) % P]);
-                        acc_add<D, G, P>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
+                        acc_add<D, G, P, kU>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
                     }
                   }
                 } else if (j >= 0) {
@@ -1061,7 +1121,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                         float pv[P];
 #pragma unroll
                         for (int cc = 0; cc < P; ++cc) pv[cc] = -c * diff[cc];
-                        acc_add<D, G, P>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
+                        acc_add<D, G, P, kU>(a.acc + (size_t)j * a.acc_stride, gl, pv, wv);
                     }
                 }
             }
@@ -1081,7 +1141,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
 #pragma unroll
             for (int c = 0; c < PH; ++c) f2_unpack(dacc2[c], dacc[2 * c], dacc[(2 * c + 1) % P]);
         }
-        if (total > 0) acc_add<D, G, P>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
+        if (total > 0) acc_add<D, G, P, kU>(a.acc + (size_t)i * a.acc_stride, gl, dacc, zacc);
     }
     asm volatile("griddepcontrol.launch_dependents;");   // the update may be scheduled (it waits for this grid)
     __syncthreads();
