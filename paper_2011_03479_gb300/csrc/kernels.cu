@@ -848,26 +848,6 @@ __global__ void __launch_bounds__(kPackedThreads, 3) k_sweep_packed(const EpochA
     if (threadIdx.x == 0 && s_used && hist.home >= 0) atomicAdd(&a.gst[hist.home].used, (unsigned long long)s_used);
 }
 
-// Sums over the G lanes of a group (G a power of two, groups aligned to G
-// lanes) of G values per lane, scattered: lane gl returns the sum of every
-// lane's v[gl].  Each halving step keeps the half of the entries whose index
-// agrees with gl in that bit and adds the partner's copy of it: G - 1
-// shuffles for the G sums, against G log2 G for G butterfly reductions.
-template <int G>
-__device__ __forceinline__ float group_sum_scatter(float (&v)[G], int gl) {
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        const bool up = (gl & o) != 0;
-#pragma unroll
-        for (int q = 0; q < o; ++q) {
-            const float keep = up ? v[o + q] : v[q];
-            const float send = up ? v[q] : v[o + q];
-            v[q] = keep + __shfl_xor_sync(kFull, send, o);
-        }
-    }
-    return v[0];
-}
-
 // ---------------------------------------------------------------------------
 // Pair sweep for d >= 8.  A warp is 32/G lane groups of G lanes; each group
 // owns one work unit (a vertex with its samples, or one chunk of a hub's
@@ -1012,18 +992,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                 if (block) my_j = ((bmask_v >> t) & 1ull) ? -1 : __ldg(tp + t);
                 else my_j = __ldg(sp + t);
             }
-            // (A) distances.  With FP32 positions small groups keep the
-            // partners' ids for (C) and leave each lane's partial sums to one
-            // scattered reduction (fewer shuffles; with BF16 positions the
-            // same change measured slower, so those keep the butterflies).
-            constexpr bool kKeep = G <= 8 && sizeof(PT) == 4;
-            int js[kKeep ? G : 1];
-            float part[kKeep ? G : 1];
+            // the lane's partner row on its way to L1 before the group's
+            // gathers reach it
+            if (my_j >= 0) {
+                const char* rp = reinterpret_cast<const char*>(X + (size_t)my_j * D);
+#pragma unroll
+                for (int b = 0; b < D * (int)sizeof(PT); b += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + b));
+            }
+            // (A) distances
             float my_ss = 0.0f;
 #pragma unroll
             for (int s2 = 0; s2 < G; ++s2) {
                 const int j = __shfl_sync(kFull, my_j, gbase + s2);
-                if constexpr (kKeep) js[s2] = j;
                 float ss = 0.0f;
                 if constexpr (kPk) {
                     f2 a2 = 0ull;
@@ -1053,15 +1033,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
                         ss = fmaf(df, df, ss);
                     }
                 }
-                if constexpr (kKeep) {
-                    part[s2] = ss;
-                } else {
 #pragma unroll
-                    for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
-                    if (gl == s2) my_ss = ss;
-                }
+                for (int o = G / 2; o >= 1; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+                if (gl == s2) my_ss = ss;
             }
-            if constexpr (kKeep) my_ss = group_sum_scatter<G>(part, gl);
+            
             // (B) the pair term of this lane's pair
             const bool my_edge = q < ne;
             float my_c = 0.0f, my_w = 0.0f;
@@ -1085,9 +1061,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const EpochArgs a) {
             // (C) the vertex's sum and the sampled partners' terms
 #pragma unroll
             for (int s2 = 0; s2 < G; ++s2) {
-                int j;
-                if constexpr (kKeep) j = js[s2];
-                else j = __shfl_sync(kFull, my_j, gbase + s2);
+                const int j = __shfl_sync(kFull, my_j, gbase + s2);
                 const float c = __shfl_sync(kFull, my_c, gbase + s2);
                 const float wv = pass_w ? __shfl_sync(kFull, my_w, gbase + s2) : 0.0f;
                 if constexpr (kPk) {
