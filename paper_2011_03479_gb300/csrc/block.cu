@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
         const int tile = cur.tile, graph = cur.graph, v0 = cur.v0, nv = cur.nv;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
-        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills);
+        const NonEdgeConsts NK =
+            make_nonedge_consts(make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills));
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
 
         // ---- stage: rows (cp.async into the core layout), partners, masks ----
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
                     const float d2 = fmaxf(ni + sm.np[p0 + e] - 2.0f * sv[e], 0.0f);
                     float delta, inv_delta;
                     dist_of(d2, delta, inv_delta);
-                    const PairTerm pt = pair_term<false>(delta, inv_delta, false, K);
+                    const PairTerm pt = nonedge_term<false>(delta, inv_delta, NK);
                     cv[e] = live ? pt.c : 0.0f;
                     wv[e] = live ? pt.w : 0.0f;
                     bn[e] = live ? min((int)(delta * a.hist_scale), a.bins - 1) : -1;

@@ -235,6 +235,66 @@ __device__ __forceinline__ PairTerm pair_term(float delta, float inv_delta, bool
     return r;
 }
 
+// 2^x by the hardware's base-2 exponential, results below the FP32 normal
+// range flushed to zero.
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Non-edge pair terms with the epoch's constants folded in (the tile
+// kernels, where every pair is a sampled non-edge).  With v = (mu - delta) /
+// sigma, the table coordinate pos = (v - kMillsV0) * kMillsStepsPerUnit is
+// one FMA of delta; pos < 0 is v < kMillsV0 (h = 0, T = -v), pos past the
+// last interval is v >= kMillsV1 (the continued fraction).  The same h, T,
+// w, c as pair_term(delta, inv_delta, false, K) up to rounding; an h below
+// the FP32 normal range (v < -13.2) is taken as 0.
+struct NonEdgeConsts {
+    float pos_a, pos_b;   // pos = pos_a - pos_b * delta
+    float w_scale, g_scale;
+    int printed;
+    const MillsCoef* mills;
+};
+
+__device__ __forceinline__ NonEdgeConsts make_nonedge_consts(const PairConsts& K) {
+    NonEdgeConsts n;
+    n.pos_b = K.inv_sigma * (float)kMillsStepsPerUnit;
+    n.pos_a = (K.mu * K.inv_sigma - kMillsV0) * (float)kMillsStepsPerUnit;
+    n.w_scale = K.w_scale;
+    n.g_scale = K.g_scale;
+    n.printed = K.printed;
+    n.mills = K.mills;
+    return n;
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ PairTerm nonedge_term(float delta, float inv_delta, const NonEdgeConsts& N) {
+    constexpr float kInvSteps = 1.0f / (float)kMillsStepsPerUnit;
+    const float pos_raw = fmaf(-N.pos_b, delta, N.pos_a);
+    float h, T;
+    if (pos_raw < (float)kMillsIntervals) {
+        const float pos = fmaxf(pos_raw, 0.0f);
+        const int i = (int)pos;   // < kMillsIntervals
+        const float x = pos - (float)i;
+        const float4 c = kGlobal ? __ldg(&N.mills[i].lh) : N.mills[i].lh;
+        const float lh = fmaf(fmaf(fmaf(c.w, x, c.z), x, c.y), x, c.x);
+        const float dlh = fmaf(fmaf(3.0f * c.w, x, 2.0f * c.z), x, c.y);
+        constexpr float kTScale = 0.69314718055994531f * (float)kMillsStepsPerUnit;
+        const bool below = pos_raw < 0.0f;
+        h = below ? 0.0f : ex2_ftz(lh);
+        T = below ? -fmaf(pos_raw, kInvSteps, kMillsV0) : dlh * kTScale;
+    } else {
+        const float v = fmaf(pos_raw, kInvSteps, kMillsV0);
+        T = mills_tail_T(v);
+        h = v + T;
+    }
+    PairTerm r;
+    r.w = h * (N.printed ? (h + T) : T) * N.w_scale;
+    r.c = delta > 0.0f ? h * N.g_scale * inv_delta : -r.w;
+    return r;
+}
+
 // sqrt and reciprocal of a squared distance (both 0 for ss = 0)
 __device__ __forceinline__ void dist_of(float ss, float& delta, float& inv_delta) {
     const float r = rsqrtf(ss);

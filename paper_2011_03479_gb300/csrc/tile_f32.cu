@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         const int graph = cur.graph, v0 = cur.v0, nv = cur.nv;
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
-        const PairConsts K = make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills);
+        const NonEdgeConsts NK =
+            make_nonedge_consts(make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills));
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
 
         // ---- (1) stage rows, partners, masks ----
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                     const bool live = !((mk >> p) & 1ull);
                     float delta, inv_delta;
                     dist_of(sm.c[i * RC + p], delta, inv_delta);
-                    const PairTerm pt = pair_term(delta, inv_delta, false, K);
+                    const PairTerm pt = nonedge_term<true>(delta, inv_delta, NK);
                     cv[j] = live ? pt.c : 0.0f;
                     wv[j] = live ? pt.w : 0.0f;
                     bn[j] = live ? min((int)(delta * a.hist_scale), a.bins - 1) : -1;
