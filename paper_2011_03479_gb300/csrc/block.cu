@@ -36,55 +36,38 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kTagBlock = 0x0D000000u;
 constexpr int kTileThreads = 256;          // 8 warps, 16 tile rows each
 constexpr int kSamplerWarps = 8;
-constexpr int kMiniHash = 128;             // slots of the per-warp partner hash
 constexpr int kTileWaitLimit = 1 << 22;    // mbarrier polls before a tile CTA gives up
 constexpr int32_t kStatusTimeout = -5;     // gempe_status of a bounded device wait that gave up
 constexpr int kTileCtasPerSm = 2;          // 128 TMEM columns and about 85 KB of shared memory each
 constexpr size_t kTileMinSmem = 48 * 1024; // at most four tile CTAs per SM: never more TMEM columns than 512
 
 // ---------------------------------------------------------------------------
-// k_block_sampler: one warp per tile.
+// k_block_sampler: one warp per tile {tile, -, -, graph << 1 | 1}.  Lane l
+// draws the tile's partners p = l and l + 32 (the Philox counter takes the
+// tile's index within its graph and the graph's key, so a graph draws the
+// same partners alone or in a pack), writes them, and the warp builds the
+// tile's 128 mask words in shared memory: bit p of anchor v is set when
+// partner p is v itself or a neighbour of v.  As the CSR is symmetric, the
+// neighbours are found from the partners' side: every id of partner p's row
+// that falls inside the tile's anchor range [v0, v0 + nv) marks that anchor
+// (64 rows of random vertices per tile, a range test per slot, where the
+// anchors' own rows would need a membership probe per slot).  Rows of up to
+// kSamplerRowLane slots are scanned by their lane, longer ones by the whole
+// warp.  Each tile has one warp, so the mask words are stored, not merged.
 // ---------------------------------------------------------------------------
-struct WarpHash {
-    int key[kMiniHash];
-    unsigned int lo[kMiniHash];   // bits of partner positions 0..31
-    unsigned int hi[kMiniHash];   // bits of positions 32..63
-};
+constexpr int kSamplerRowLane = 32;
 
-__device__ __forceinline__ unsigned hash_slot(int g) { return ((unsigned)g * 0x9E3779B1u) >> 25; }   // 7 bits
-
-// Positions p whose partner equals j (as a 64-bit mask).
-__device__ __forceinline__ unsigned long long partner_bits(const WarpHash& h, int j) {
-    unsigned s = hash_slot(j);
-    for (int probe = 0; probe < kMiniHash; ++probe) {
-        const int k = h.key[s];
-        if (k == j) return ((unsigned long long)h.hi[s] << 32) | h.lo[s];
-        if (k < 0) return 0ull;
-        s = (s + 1) & (kMiniHash - 1);
-    }
-    return 0ull;
-}
-
-// One warp per work unit {tile, e_lo, e_hi, graph << 1 | first}: the unit
-// recomputes its tile's 64 partners into a small shared hash (partner row ->
-// positions), the tile's first unit writes the partners and the self-pair
-// bits, and every unit tests absolute CSR slots [e_lo, e_hi) of the tile's
-// rows against the partners, OR-ing hits into the vertices' masks (cleared
-// before the launch).  Hub tiles are thereby spread over many warps.  The
-// Philox counter takes the tile's index within its graph and the graph's
-// key, so a graph draws the same partners alone or in a pack.
 __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const EpochArgs a, const int4* units,
                                                                       int n_units) {
-    __shared__ WarpHash s_hash[kSamplerWarps];
-    __shared__ int s_rp[kSamplerWarps][kBlockT + 1];
+    __shared__ unsigned long long s_mask[kSamplerWarps][kBlockT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpHash& h = s_hash[wib];
+    unsigned long long* sm = s_mask[wib];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
 
     for (int it = warp; it < n_units; it += n_warps) {
         const int4 u = __ldg(units + it);
-        const int tile = u.x, e_lo = u.y, e_hi = u.z, first = u.w & 1, graph = u.w >> 1;
+        const int tile = u.x, graph = u.w >> 1;
         const int gv0 = __ldg(&a.graphs[graph].v0), gn = __ldg(&a.graphs[graph].n);
         const int gt0 = __ldg(&a.graphs[graph].t0);
         const uint32_t key_lo = __ldg(&a.graphs[graph].key_lo), key_hi = __ldg(&a.graphs[graph].key_hi);
@@ -94,54 +77,51 @@ __global__ void __launch_bounds__(kSamplerWarps * 32) k_block_sampler(const Epoc
         const int nv = min(kBlockT, gn - lt * kBlockT);
         int32_t* part_out = a.block_part + (size_t)(se & 1) * (size_t)a.n_tiles * kBlockP;
         unsigned long long* mask_out = a.block_mask + (size_t)(se & 1) * (size_t)a.rows;
-        unsigned c_rej = 0;
-        for (int q = lane; q < kMiniHash; q += 32) {
-            h.key[q] = -1;
-            h.lo[q] = 0u;
-            h.hi[q] = 0u;
-        }
-        for (int v = lane; v <= nv; v += 32) s_rp[wib][v] = __ldg(a.row_ptr + v0 + v);
-        __syncwarp();
+        for (int v = lane; v < kBlockT; v += 32) sm[v] = 0ull;
+        int rb[2], re[2];
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int p = lane + 32 * half;
             const uint4 r = philox4x32_10(make_uint4((uint32_t)lt, (uint32_t)se, (uint32_t)(p >> 2), kTagBlock),
                                           key_lo, key_hi);
             const int g = gv0 + draw_vertex(word_of(r, p & 3), (uint32_t)gn);
-            if (first) part_out[(size_t)tile * kBlockP + p] = g;
-            unsigned s = hash_slot(g);
-            for (int probe = 0; probe < kMiniHash; ++probe) {
-                const int prev = atomicCAS(&h.key[s], -1, g);
-                if (prev == -1 || prev == g) break;
-                s = (s + 1) & (kMiniHash - 1);
+            part_out[(size_t)tile * kBlockP + p] = g;
+            rb[half] = __ldg(a.row_ptr + g);
+            re[half] = __ldg(a.row_ptr + g + 1);
+            __syncwarp();
+            const unsigned self = (unsigned)(g - v0);   // the partner is an anchor of the tile
+            if (self < (unsigned)nv) atomicOr(&sm[self], 1ull << p);
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const unsigned long long bit = 1ull << (lane + 32 * half);
+            if (re[half] - rb[half] <= kSamplerRowLane) {
+                for (int e = rb[half]; e < re[half]; ++e) {
+                    const unsigned o = (unsigned)(__ldg(a.col_idx + e) - v0);
+                    if (o < (unsigned)nv) atomicOr(&sm[o], bit);
+                }
             }
-            if (half == 0) atomicOr(&h.lo[s], 1u << lane);
-            else atomicOr(&h.hi[s], 1u << lane);
+            unsigned longs = __ballot_sync(kFull, re[half] - rb[half] > kSamplerRowLane);
+            while (longs) {
+                const int src = __ffs(longs) - 1;
+                longs &= longs - 1;
+                const int e0 = __shfl_sync(kFull, rb[half], src), e1 = __shfl_sync(kFull, re[half], src);
+                const unsigned long long sbit = 1ull << (src + 32 * half);
+                for (int e = e0 + lane; e < e1; e += 32) {
+                    const unsigned o = (unsigned)(__ldg(a.col_idx + e) - v0);
+                    if (o < (unsigned)nv) atomicOr(&sm[o], sbit);
+                }
+            }
         }
         __syncwarp();
-        if (first) {   // self pairs
-            for (int v = lane; v < nv; v += 32) {
-                const unsigned long long b = partner_bits(h, v0 + v);
-                if (b) {
-                    atomicOr(mask_out + v0 + v, b);
-                    c_rej += __popcll(b);
-                }
-            }
+        // every masked bit is set by exactly one event (the self pair or one
+        // edge): accepted = slots - masked, the slots added at completion
+        unsigned c_rej = 0;
+        for (int v = lane; v < nv; v += 32) {
+            const unsigned long long m = sm[v];
+            mask_out[v0 + v] = m;
+            c_rej += __popcll(m);
         }
-        for (int e = e_lo + lane; e < e_hi; e += 32) {
-            const unsigned long long b = partner_bits(h, __ldg(a.col_idx + e));
-            if (b) {
-                int lo = 0, hi = nv - 1;   // row of slot e: last v with rp[v] <= e
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_rp[wib][mid] <= e) lo = mid; else hi = mid - 1;
-                }
-                atomicOr(mask_out + v0 + lo, b);
-                c_rej += __popcll(b);
-            }
-        }
-        // every masked bit is set by exactly one event (a slot or the self
-        // pair): accepted = slots - masked, the slots added at completion
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) c_rej += __shfl_xor_sync(kFull, c_rej, o);
         if (lane == 0 && c_rej) {

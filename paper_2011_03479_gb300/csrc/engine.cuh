@@ -82,7 +82,6 @@ constexpr int kPackedThreads = 512;
 // Sampled-partner layout of block sampling.
 constexpr int kBlockP = 64;
 constexpr int kBlockT = 128;
-constexpr int kSamplerChunk = 1024;   // CSR slots per block-sampler work unit
 
 // he, hc, hd (u32) and hw (f32, the per-slot policy's sample weights)
 inline size_t hist_smem_bytes(int bins) { return (size_t)bins * 4 * sizeof(unsigned int); }

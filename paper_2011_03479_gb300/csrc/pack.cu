@@ -448,14 +448,7 @@ gempe_status Pack::build(const std::vector<GraphInput>& gs, int32_t dim, const g
         for (int32_t o = lo; o < hi; o += kVChunk) vch.push_back(make_int4(gi.v0 + o, std::min(kVChunk, hi - o), g, 0));
         for (int32_t t = lo / kBlockT; t < (block ? (hi + kBlockT - 1) / kBlockT : 0); ++t) {
             titems.push_back(make_int2(gi.t0 + t, g));
-            const int32_t a0 = gi.v0 + t * kBlockT, a1 = gi.v0 + std::min(gi.n, (t + 1) * kBlockT);
-            const int32_t e0 = row_ptr_h[a0], e1 = row_ptr_h[a1];
-            int32_t e = e0;
-            do {
-                const int32_t eh = std::min(e1, e + kSamplerChunk);
-                sunits.push_back(make_int4(gi.t0 + t, e, eh, (g << 1) | (e == e0 ? 1 : 0)));
-                e = eh;
-            } while (e < e1);
+            sunits.push_back(make_int4(gi.t0 + t, 0, 0, (g << 1) | 1));
         }
     }
     n_vchunks = (int32_t)vch.size();
@@ -621,7 +614,7 @@ size_t Pack::bytes_for(int32_t n, int64_t nnz, int32_t d, const gempe_params& p)
     if (ps) b += al(8 * R);
     if (d <= kPackedMaxDim && !ps && !blk) b += al(4 * (R + 1)) + al(4 * std::max<size_t>((size_t)nnz, 1));
     if (p.membership == 1 && !blk) b += al((size_t)1 << bytemap_log2_for(nnz, p));
-    if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + (size_t)nnz / kSamplerChunk + 1)) + al(8 * tiles);
+    if (blk) b += al(8 * tiles * kBlockP) + al(16 * R) + al(16 * (tiles + 1)) + al(8 * tiles);
     return b;
 }
 

@@ -111,7 +111,7 @@ struct Pack {
     int32_t* vacc = nullptr;         // per-slot policy: [2][rows] accepted samples per vertex
     int32_t* block_part = nullptr;   // [2][n_tiles][64]
     unsigned long long* block_mask = nullptr;   // [2][rows]
-    int4* sampler_units = nullptr;   // block sampler {tile, e_lo, e_hi, graph << 1 | first}
+    int4* sampler_units = nullptr;   // block sampler, one per tile {tile, 0, 0, graph << 1 | 1}
     int32_t n_sampler_units = 0;
     int2* tile_items = nullptr;      // {tile, graph}
     int32_t n_tile_items = 0;
