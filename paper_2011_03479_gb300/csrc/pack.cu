@@ -238,17 +238,24 @@ int unit_pairs_of(const int4& u, int k_slots, bool per_slot) {
 void wide_tasks(std::vector<int4>& units, int pg, int k_slots, bool per_slot) {
     if (pg <= 1) return;
     const size_t window = 16 * (size_t)pg;
+    const int64_t n_windows = (int64_t)((units.size() + window - 1) / window);
     // each window ordered by decreasing pair count, ties in their original
-    // order (a stable sort, without the per-call buffer of std::stable_sort)
-    std::vector<std::pair<int, int>> key(window);
-    std::vector<int4> tmp(window);
-    for (size_t w0 = 0; w0 < units.size(); w0 += window) {
-        const size_t w1 = std::min(units.size(), w0 + window), len = w1 - w0;
-        for (size_t q = 0; q < len; ++q) key[q] = {-unit_pairs_of(units[w0 + q], k_slots, per_slot), (int)q};
-        std::sort(key.begin(), key.begin() + len);
-        for (size_t q = 0; q < len; ++q) tmp[q] = units[w0 + key[q].second];
-        std::copy(tmp.begin(), tmp.begin() + len, units.begin() + w0);
-    }
+    // order (a stable sort, without the per-call buffer of std::stable_sort);
+    // the windows are independent and split over host threads
+    parallel_ranges(n_windows, host_threads((int64_t)units.size()), [](int64_t i) { return i; },
+                    [&](int64_t wlo, int64_t whi) {
+                        std::vector<std::pair<int, int>> key(window);
+                        std::vector<int4> tmp(window);
+                        for (int64_t wi = wlo; wi < whi; ++wi) {
+                            const size_t w0 = (size_t)wi * window;
+                            const size_t w1 = std::min(units.size(), w0 + window), len = w1 - w0;
+                            for (size_t q = 0; q < len; ++q)
+                                key[q] = {-unit_pairs_of(units[w0 + q], k_slots, per_slot), (int)q};
+                            std::sort(key.begin(), key.begin() + len);
+                            for (size_t q = 0; q < len; ++q) tmp[q] = units[w0 + key[q].second];
+                            std::copy(tmp.begin(), tmp.begin() + len, units.begin() + w0);
+                        }
+                    });
     while (units.size() % pg) units.push_back(make_int4(-1, 0, 0, 0));
 }
 
