@@ -57,12 +57,12 @@ struct TileF32 {
     float xt[kBlockT * R];
     float xp[kBlockP * R];
     float c[kBlockT * RC];
-    float col_part[kF32Threads / 32][2][kBlockP];   // per-warp column sums of C and W
     float rsum_c[kBlockT], rsum_w[kBlockT];
     float csum_c[kBlockP], csum_w[kBlockP];
     unsigned long long mask[kBlockT];
     int deg[kBlockT], kacc[kBlockT];
     int part[kBlockP];
+    MillsCoef mills[kMillsIntervals];   // the Mills-ratio table (pair terms)
 };
 
 // CK consecutive floats of shared memory (CK = 1, 2, 4 or 8; 4-float chunks aligned).
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
     __shared__ unsigned int s_used, s_tile_used;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int ta = tid >> 4, tp = tid & 15;   // anchor group / partner (or coordinate) group
+    for (int t = tid; t < kMillsIntervals; t += blockDim.x) sm.mills[t].lh = __ldg(&a.mills[t].lh);
     for (int t = tid; t < a.bins; t += blockDim.x) {
         hist.he[t] = 0u;
         hist.hc[t] = 0u;
@@ -146,12 +147,16 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         const float sigma = a.gst[graph].sigma;
         const int epoch = a.gst[graph].epoch;
         const NonEdgeConsts NK =
-            make_nonedge_consts(make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, a.mills));
+            make_nonedge_consts(make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills));
         unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
 
         // ---- (1) stage rows, partners, masks ----
         __syncthreads();   // the previous tile's shared data is no longer read
-        if (tid < kBlockP) sm.part[tid] = cur.part;
+        if (tid < kBlockP) {
+            sm.part[tid] = cur.part;
+            sm.csum_c[tid] = 0.0f;
+            sm.csum_w[tid] = 0.0f;
+        }
         for (int q = tid; q < kBlockT * CH; q += blockDim.x) {
             const int r = q / CH, c4 = q - r * CH;
             float* dst = sm.xt + r * R + 4 * c4;
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                     const bool live = !((mk >> p) & 1ull);
                     float delta, inv_delta;
                     dist_of(sm.c[i * RC + p], delta, inv_delta);
-                    const PairTerm pt = nonedge_term<true>(delta, inv_delta, NK);
+                    const PairTerm pt = nonedge_term<false>(delta, inv_delta, NK);
                     cv[j] = live ? pt.c : 0.0f;
                     wv[j] = live ? pt.w : 0.0f;
                     bn[j] = live ? min((int)(delta * a.hist_scale), a.bins - 1) : -1;
@@ -277,7 +282,8 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                 }
             }
         }
-        // column sums: the warp's two anchor groups, then per-warp partials
+        // column sums: the warp's two anchor groups, then one shared-memory
+        // addition per warp and partner
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             cc[j] += __shfl_xor_sync(0xFFFFFFFFu, cc[j], 16);
@@ -286,18 +292,11 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
         if (lane < 16) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                sm.col_part[w][0][tp + 16 * j] = cc[j];
-                sm.col_part[w][1][tp + 16 * j] = cw[j];
+                atomicAdd(&sm.csum_c[tp + 16 * j], cc[j]);
+                atomicAdd(&sm.csum_w[tp + 16 * j], cw[j]);
             }
         }
-        __syncthreads();
-        if (tid < 2 * kBlockP) {
-            const int p = tid & (kBlockP - 1), which = tid >> 6;
-            float s = 0.0f;
-#pragma unroll
-            for (int q = 0; q < kF32Threads / 32; ++q) s += sm.col_part[q][which][p];
-            if (which == 0) sm.csum_c[p] = s; else sm.csum_w[p] = s;
-        }
+        __syncthreads();   // C for the products
 
         // ---- (4a) A = C X_P: anchors ta + 16 r, coordinates CK tp .. ----
         {
@@ -424,7 +423,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
 
 template <int D>
 size_t f32_smem(int bins) {
-    return sizeof(TileF32<D>) + hist_smem_bytes(bins);
+    return sizeof(TileF32<D>) + hist_smem_bytes(bins) / 4 * 3;   // no per-slot weights in block sampling
 }
 
 }  // namespace
