@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
     }
     const BlockHist hist = block_hist(hist_base, a.bins, home);
     __shared__ unsigned int s_used, s_tile_used;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int ta = tid >> 4, tp = tid & 15;   // anchor group / partner (or coordinate) group
     for (int t = tid; t < kMillsIntervals; t += blockDim.x) sm.mills[t].lh = __ldg(&a.mills[t].lh);
     for (int t = tid; t < a.bins; t += blockDim.x) {
