@@ -236,58 +236,72 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
 
-// Shared memory of the tile kernel.  XT: the tile's BF16 rows (128 x D),
-// XP: the partners' rows (64 x D).  CW: the pair coefficients, C in columns
-// 0..63, W in 64..127 (W fills the 128 rows the B product needs; its row and
-// column sums come from the epilogue and from CW).  TMEM: S in columns
-// 0..63, then A in 0..D-1 once the epilogue has read S, B in 64..64+D-1:
-// 128 columns, so that three CTAs share an SM.
+// Shared memory of the tile kernel, in two stages: the tile being computed
+// and the next one, whose rows are copied in while the current tile's pair
+// terms run.  Per stage, XT: the tile's BF16 rows (128 x D), XP: its
+// partners' rows (64 x D), their squared norms, masks, degrees and partner
+// ids.  CW: the pair coefficients, C in columns 0..63, W in 64..127 (W fills
+// the 128 rows the B product needs; its row and column sums come from the
+// epilogue and from CW).  TMEM, per stage: S in columns 0..63, then A in
+// 0..D-1 once the epilogue has read S, B in 64..64+D-1 (2 x 128 columns per
+// CTA, two CTAs per SM).
 template <int D>
 struct TileTc {
     static constexpr int DP = D;
-    static constexpr uint32_t kCols = 128;                   // TMEM columns: S then A, and B
+    static constexpr uint32_t kStageCols = 128;
+    static constexpr uint32_t kCols = 2 * kStageCols;        // TMEM columns of a CTA
     static constexpr uint32_t kColS = 0, kColA = 0, kColB = 64;
-    __nv_bfloat16 xt[kBlockT * DP];
-    __nv_bfloat16 xp[kBlockP * DP];
+    struct alignas(128) Stage {
+        __nv_bfloat16 xt[kBlockT * DP];
+        __nv_bfloat16 xp[kBlockP * DP];
+        float nt[kBlockT], np[kBlockP];
+        unsigned long long mask[kBlockT];
+        int deg[kBlockT], kacc[kBlockT];
+        int part[kBlockP];
+    };
+    Stage st[2];
     __nv_bfloat16 cw[kBlockT * 2 * kBlockP];
-    float nt[kBlockT], np[kBlockP];
     float row_w[2][kBlockT], row_c[2][kBlockT];   // per partner half: sums of w and of the rounded c
     float col[2][2 * kBlockP];                    // per anchor half: column sums of the rounded C | W
     MillsCoef mills[kMillsIntervals];             // the Mills-ratio table (pair terms)
-    unsigned long long mask[kBlockT];
-    int deg[kBlockT], kacc[kBlockT];
-    int part[kBlockP];
-    unsigned long long mbar;
+    unsigned long long mbar_s, mbar_ab;           // completions of the S products / of A and B
     uint32_t tmem;
     int abort;
 };
 
 // ---------------------------------------------------------------------------
-// k_tile_tc: block-sampled non-edges, one tile per CTA iteration, 8 warps.
-//   (1) S = X_T X_P^T (M 128, N 64, K d) into TMEM;
+// k_tile_tc: block-sampled non-edges, 8 warps per CTA, tiles in a pipeline
+// of two stages.  For tile t (stage b):
+//   (0) the rows, masks and partners of tile t + 1 are copied into stage
+//       1 - b (cp.async; the global words they need were loaded a tile
+//       earlier still);
+//   (1) S = X_T X_P^T (M 128, N 64, K d), issued at the end of tile t - 1,
+//       is waited for;
 //   (2) warp w reads rows 32 (w % 4) .. of S, partner columns 32 (w / 4) ..,
 //       forms the pair terms (c, w) with the masks and histograms, writes
 //       them rounded to BF16 into CW and sums, per anchor and partner half,
 //       w and the rounded c (the row sums);
 //   (3) A = C X_P (K 64) gives sum_g c_ig x_g; B = [C | W]^T X_T (M 128,
 //       K 128) gives sum_i c_ig x_i in rows 0..63; meanwhile the column
-//       sums of the rounded C and W are added up from CW;
+//       sums of the rounded C and W are added up from CW, then tile t + 1's
+//       rows are waited for, their norms taken, and its S issued behind A
+//       and B on the tensor cores;
 //   (4) x_i rowsum(C) - A_i and the row sums of W go to the anchors'
 //       accumulators, x_g colsum(C) - B_g and colsum(W) to the partners'.
-// One thread issues the MMAs; their completion is signalled on an mbarrier
-// (bounded waits: a timeout sets the pack's status and ends the kernel).
-// The global words of the next tile's staging are loaded while this tile
-// runs; the pair-term loop over the four 8-partner chunks is kept rolled
+// One thread issues the MMAs; their completions are signalled on two
+// mbarriers (bounded waits: a timeout sets the pack's status and ends the
+// kernel).  The pair-term loop over the four 8-partner chunks is kept rolled
 // (the unrolled kernel stalled on instruction fetch).
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const EpochArgs a) {
     using L = TileTc<D>;
+    using Stage = typename L::Stage;
     constexpr int DP = L::DP;
     constexpr int CH = D / 8;                     // 16-byte chunks of a row
     constexpr uint32_t kSbT = (DP / 8) * 128;     // stride of 8-row groups of XT, XP
     constexpr uint32_t kSbC = (2 * kBlockP / 8) * 128;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     L& sm = *reinterpret_cast<L*>(smem_raw);
     unsigned int* hist_base = reinterpret_cast<unsigned int*>(smem_raw + sizeof(L));
     int it0, it1, istep, home;
@@ -316,7 +330,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
         s_used = 0u;
         s_tile_used = 0u;
         sm.abort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar_s)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.mbar_ab)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (w == 0) {
@@ -329,27 +344,17 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sm.tmem;
     const uint32_t lane_base = (uint32_t)(32 * quad) << 16;   // this warp's TMEM lanes
-    uint32_t phase = 0;
-
+    uint32_t ph_s = 0, ph_ab = 0;
     using Ahead = TileAhead<CH, kTileThreads>;
-    Ahead nxt;
-    if (it0 < it1) nxt = tile_ahead<CH, kTileThreads>(a, it0, tid);
-    for (int it = it0; it < it1; it += istep) {
-        const Ahead cur = nxt;
-        const int tile = cur.tile, graph = cur.graph, v0 = cur.v0, nv = cur.nv;
-        const float sigma = a.gst[graph].sigma;
-        const int epoch = a.gst[graph].epoch;
-        const NonEdgeConsts NK =
-            make_nonedge_consts(make_pair_consts(a.mu, sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills));
-        unsigned long long* bmask = a.block_mask + (size_t)(epoch & 1) * (size_t)a.rows;
 
-        // ---- stage: rows (cp.async into the core layout), partners, masks ----
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();   // the previous tile's shared data and TMEM are no longer read
-        if (tid < kBlockP) sm.part[tid] = cur.part;
+    // Copy a tile's rows into stage s (no wait) and set its masks.
+    auto stage_tile = [&](const Ahead& t, Stage& s) {
+        const int v0 = t.v0, nv = t.nv;
+        unsigned long long* bmask = a.block_mask + (size_t)(a.gst[t.graph].epoch & 1) * (size_t)a.rows;
+        if (tid < kBlockP) s.part[tid] = t.part;
         for (int c = tid; c < kBlockT * CH; c += blockDim.x) {
             const int r = c / CH, q = c - r * CH;
-            unsigned char* dst = reinterpret_cast<unsigned char*>(sm.xt) + core_off(r, 8 * q, DP);
+            unsigned char* dst = reinterpret_cast<unsigned char*>(s.xt) + core_off(r, 8 * q, DP);
             if (r < nv) cp_async16(dst, a.xb + (size_t)(v0 + r) * D + 8 * q);
             else *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
         }
@@ -358,26 +363,30 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             const int c = tid + kTileThreads * j;
             if (c < kBlockP * CH) {
                 const int r = c / CH, q = c - r * CH;
-                cp_async16(reinterpret_cast<unsigned char*>(sm.xp) + core_off(r, 8 * q, DP),
-                           a.xb + (size_t)cur.pid[j] * D + 8 * q);
+                cp_async16(reinterpret_cast<unsigned char*>(s.xp) + core_off(r, 8 * q, DP),
+                           a.xb + (size_t)t.pid[j] * D + 8 * q);
             }
         }
         if (tid < kBlockT) {
             const int v = tid;
             if (v < nv) {
-                const unsigned long long m = cur.m;
+                const unsigned long long m = t.m;
                 bmask[v0 + v] = 0ull;   // read once: the buffer starts empty for the epoch two ahead
-                sm.mask[v] = m;
-                sm.deg[v] = cur.deg;
-                sm.kacc[v] = kBlockP - __popcll(m);
+                s.mask[v] = m;
+                s.deg[v] = t.deg;
+                s.kacc[v] = kBlockP - __popcll(m);
                 atomicAdd(&s_tile_used, (unsigned)(kBlockP - __popcll(m)));
             } else {
-                sm.mask[v] = ~0ull;
-                sm.deg[v] = 0;
-                sm.kacc[v] = 0;
+                s.mask[v] = ~0ull;
+                s.deg[v] = 0;
+                s.kacc[v] = 0;
             }
         }
-        if (it + istep < it1) nxt = tile_ahead<CH, kTileThreads>(a, it + istep, tid);
+    };
+    // Wait for stage s's rows, book its accepted samples, take the squared
+    // norms of its BF16 rows (what S is made of) and hand the rows to the
+    // tensor cores.
+    auto finish_stage = [&](Stage& s, int graph) {
         cp_async_wait_all();
         __syncthreads();
         if (tid == 0) {
@@ -387,9 +396,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             }
             s_tile_used = 0u;
         }
-        // squared norms of the BF16 rows (what S is made of)
         for (int r = tid; r < kBlockT + kBlockP; r += blockDim.x) {
-            const unsigned char* base = reinterpret_cast<const unsigned char*>(r < kBlockT ? sm.xt : sm.xp);
+            const unsigned char* base = reinterpret_cast<const unsigned char*>(r < kBlockT ? s.xt : s.xp);
             const int rr = r < kBlockT ? r : r - kBlockT;
             float s2 = 0.0f;
 #pragma unroll
@@ -402,23 +410,53 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
                     s2 = fmaf(lo, lo, fmaf(hi, hi, s2));
                 }
             }
-            if (r < kBlockT) sm.nt[rr] = s2; else sm.np[rr] = s2;
+            if (r < kBlockT) s.nt[rr] = s2; else s.np[rr] = s2;
         }
         asm volatile("fence.proxy.async.shared::cta;");   // the staged rows, for the tensor cores
         __syncthreads();
-
-        // ---- (1) S = X_T X_P^T ----
+    };
+    // S = X_T X_P^T of stage s into TMEM columns col0 .. col0 + 63.
+    auto issue_s = [&](const Stage& s, uint32_t col0) {
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t at = smem_u32(sm.xt), ap = smem_u32(sm.xp);
+            const uint32_t at = smem_u32(s.xt), ap = smem_u32(s.xp);
 #pragma unroll
             for (int k = 0; k < D / 16; ++k)
-                tc_mma(tmem + L::kColS, smem_desc(at + 256 * k, 128, kSbT), smem_desc(ap + 256 * k, 128, kSbT),
+                tc_mma(tmem + col0 + L::kColS, smem_desc(at + 256 * k, 128, kSbT), smem_desc(ap + 256 * k, 128, kSbT),
                        mma_idesc(128, kBlockP, 0, 0), k > 0);
-            tc_commit(&sm.mbar);
+            tc_commit(&sm.mbar_s);
         }
-        if (!mbar_wait(&sm.mbar, phase)) atomicExch(&sm.abort, 1);
-        phase ^= 1u;
+    };
+
+    Ahead cur, nxt;
+    if (it0 < it1) {
+        cur = tile_ahead<CH, kTileThreads>(a, it0, tid);
+        if (it0 + istep < it1) nxt = tile_ahead<CH, kTileThreads>(a, it0 + istep, tid);
+        stage_tile(cur, sm.st[0]);
+        finish_stage(sm.st[0], cur.graph);
+        issue_s(sm.st[0], 0);
+    }
+    int b = 0;
+    for (int it = it0; it < it1; it += istep, b ^= 1) {
+        Stage& S0 = sm.st[b];
+        Stage& S1 = sm.st[b ^ 1];
+        const uint32_t col0 = (uint32_t)b * L::kStageCols, col1 = (uint32_t)(b ^ 1) * L::kStageCols;
+        const int graph = cur.graph, v0 = cur.v0, nv = cur.nv;
+        const bool has_next = it + istep < it1;
+        const int next_graph = nxt.graph;
+        const NonEdgeConsts NK =
+            make_nonedge_consts(make_pair_consts(a.mu, a.gst[graph].sigma, a.w_formula == 1, a.clamp_neg_d, sm.mills));
+
+        // ---- (0) the next tile's rows into the other stage ----
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // the tile before this one no longer reads the other stage or its TMEM
+        if (has_next) stage_tile(nxt, S1);
+        Ahead after;
+        if (it + 2 * istep < it1) after = tile_ahead<CH, kTileThreads>(a, it + 2 * istep, tid);
+
+        // ---- (1) S of this tile ----
+        if (!mbar_wait(&sm.mbar_s, ph_s)) atomicExch(&sm.abort, 1);
+        ph_s ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
         if (sm.abort) break;
@@ -426,15 +464,15 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
         // ---- (2) pair terms: anchor i = 32 quad + lane, partners 32 half .. 32 half + 31 ----
         {
             const int i = 32 * quad + lane;
-            const unsigned long long mk = sm.mask[i];
-            const float ni = sm.nt[i];
-            const int di = sm.deg[i], ki = sm.kacc[i];
+            const unsigned long long mk = S0.mask[i];
+            const float ni = S0.nt[i];
+            const int di = S0.deg[i], ki = S0.kacc[i];
             float rw = 0.0f, rc = 0.0f;
 #pragma unroll 1
             for (int c8 = 0; c8 < 4; ++c8) {
                 const int p0 = 32 * half + 8 * c8;
                 float sv[8];
-                tmem_ld8(tmem + lane_base + L::kColS + (uint32_t)p0, sv);
+                tmem_ld8(tmem + lane_base + col0 + L::kColS + (uint32_t)p0, sv);
                 // the eight terms without branches (masked pairs give 0),
                 // then their histogram counts
                 float cv[8], wv[8];
@@ -442,7 +480,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const bool live = !((mk >> (p0 + e)) & 1ull);
-                    const float d2 = fmaxf(ni + sm.np[p0 + e] - 2.0f * sv[e], 0.0f);
+                    const float d2 = fmaxf(ni + S0.np[p0 + e] - 2.0f * sv[e], 0.0f);
                     float delta, inv_delta;
                     dist_of(d2, delta, inv_delta);
                     const PairTerm pt = nonedge_term<false>(delta, inv_delta, NK);
@@ -474,19 +512,19 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
 
-        // ---- (3) A = C [X_P | 1],  B = [C | W]^T [X_T | 1] ----
+        // ---- (3) A = C X_P,  B = [C | W]^T X_T ----
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t at = smem_u32(sm.xt), ap = smem_u32(sm.xp), ac = smem_u32(sm.cw);
+            const uint32_t at = smem_u32(S0.xt), ap = smem_u32(S0.xp), ac = smem_u32(sm.cw);
 #pragma unroll
             for (int k = 0; k < kBlockP / 16; ++k)   // K = partners: C K-major, X_P MN-major
-                tc_mma(tmem + L::kColA, smem_desc(ac + 256 * k, 128, kSbC), smem_desc(ap + 2 * k * kSbT, kSbT, 128),
-                       mma_idesc(128, DP, 0, 1), k > 0);
+                tc_mma(tmem + col0 + L::kColA, smem_desc(ac + 256 * k, 128, kSbC),
+                       smem_desc(ap + 2 * k * kSbT, kSbT, 128), mma_idesc(128, DP, 0, 1), k > 0);
 #pragma unroll
             for (int k = 0; k < kBlockT / 16; ++k)   // K = anchors: [C | W] and X_T both MN-major
-                tc_mma(tmem + L::kColB, smem_desc(ac + 2 * k * kSbC, kSbC, 128), smem_desc(at + 2 * k * kSbT, kSbT, 128),
-                       mma_idesc(128, DP, 1, 1), k > 0);
-            tc_commit(&sm.mbar);
+                tc_mma(tmem + col0 + L::kColB, smem_desc(ac + 2 * k * kSbC, kSbC, 128),
+                       smem_desc(at + 2 * k * kSbT, kSbT, 128), mma_idesc(128, DP, 1, 1), k > 0);
+            tc_commit(&sm.mbar_ab);
         }
         {
             // beside the products: the column sums of the rounded C and W.
@@ -518,8 +556,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
                 t2[q] = (b2 ? t4[2 + q] : t4[q]) + __shfl_xor_sync(0xffffffffu, b2 ? t4[q] : t4[2 + q], 2);
             sm.col[ah][8 * cg + j] = (b1 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? t2[0] : t2[1], 1);
         }
-        if (!mbar_wait(&sm.mbar, phase)) atomicExch(&sm.abort, 1);
-        phase ^= 1u;
+        // the next tile's rows: wait, norms, and its S behind A and B
+        if (has_next) {
+            finish_stage(S1, next_graph);
+            issue_s(S1, col1);
+        }
+        if (!mbar_wait(&sm.mbar_ab, ph_ab)) atomicExch(&sm.abort, 1);
+        ph_ab ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncthreads();
         if (sm.abort) break;
@@ -529,15 +572,15 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             // anchors: dims [half * D/2, (half + 1) * D/2)
             const int i = 32 * quad + lane;
             const float rsum = sm.row_c[0][i] + sm.row_c[1][i];   // rowsum of C (rounded terms)
-            const bool live = i < nv && sm.kacc[i] > 0;
+            const bool live = i < nv && S0.kacc[i] > 0;
             float* row = a.acc + (size_t)(v0 + i) * a.acc_stride;
 #pragma unroll
             for (int c8 = 0; c8 < D / 16; ++c8) {
                 const int d0 = half * (D / 2) + 8 * c8;
                 float av[8];
-                tmem_ld8(tmem + lane_base + L::kColA + (uint32_t)d0, av);
+                tmem_ld8(tmem + lane_base + col0 + L::kColA + (uint32_t)d0, av);
                 if (live) {
-                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(sm.xt) +
+                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(S0.xt) +
                                                                     core_off(i, d0, DP));
                     const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
                     float o[8];
@@ -557,15 +600,15 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             const int g = 32 * quad + lane;
             const float csum = sm.col[0][g] + sm.col[1][g];
             const float wsum = sm.col[0][kBlockP + g] + sm.col[1][kBlockP + g];
-            const int gv = sm.part[g];
+            const int gv = S0.part[g];
             float* row = a.acc + (size_t)gv * a.acc_stride;
 #pragma unroll
             for (int c8 = 0; c8 < D / 16; ++c8) {
                 const int d0 = half * (D / 2) + 8 * c8;
                 float bv[8];
-                tmem_ld8(tmem + lane_base + L::kColB + (uint32_t)d0, bv);
+                tmem_ld8(tmem + lane_base + col0 + L::kColB + (uint32_t)d0, bv);
                 if (wsum != 0.0f || csum != 0.0f) {
-                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(sm.xp) +
+                    const uint4 u = *reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(S0.xp) +
                                                                     core_off(g, d0, DP));
                     const uint32_t wd[4] = {u.x, u.y, u.z, u.w};
                     float o[8];
@@ -580,6 +623,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_tile_tc(const 
             }
             if (half == 0 && (wsum != 0.0f || csum != 0.0f)) atomicAdd(row + D, wsum);
         }
+        cur = nxt;
+        nxt = after;
     }
     cp_async_wait_all();
     asm volatile("tcgen05.fence::before_thread_sync;");
