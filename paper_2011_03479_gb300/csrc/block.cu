@@ -38,8 +38,8 @@ constexpr int kTileThreads = 256;          // 8 warps, 16 tile rows each
 constexpr int kSamplerWarps = 8;
 constexpr int kTileWaitLimit = 1 << 22;    // mbarrier polls before a tile CTA gives up
 constexpr int32_t kStatusTimeout = -5;     // gempe_status of a bounded device wait that gave up
-constexpr int kTileCtasPerSm = 2;          // 128 TMEM columns and about 85 KB of shared memory each
-constexpr size_t kTileMinSmem = 48 * 1024; // at most four tile CTAs per SM: never more TMEM columns than 512
+constexpr int kTileCtasPerSm = 2;          // 256 TMEM columns and about 113 KB of shared memory each
+constexpr size_t kTileMinSmem = 80 * 1024; // at most two tile CTAs per SM: never more TMEM columns than 512
 
 // ---------------------------------------------------------------------------
 // k_block_sampler: one warp per tile {tile, -, -, graph << 1 | 1}.  Lane l
@@ -682,8 +682,8 @@ bool tile_dim(int d) { return d == 16 || d == 32 || d == 64; }
 // Shared memory of the tile kernel: its layout and three of the four
 // histogram arrays (edge counts stay zero, the per-slot weights are never
 // used: block sampling excludes that policy), at least kTileMinSmem so that
-// no more than four CTAs share an SM (each holds 128 of the SM's 512 TMEM
-// columns for the whole launch).
+// no more than two CTAs of any tile kernel share an SM (each holds 256 of the
+// SM's 512 TMEM columns for the whole launch).
 size_t tile_smem_bytes(int d, int bins) {
     size_t base = 0;
     switch (d) {
