@@ -159,6 +159,32 @@ def test_ba_bf16_tiles_parity(B, O, ba_20k):
     assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_ba_tiles_several_per_cta(B, O, precision):
+    """Barabasi-Albert graph, n = 120,000 (938 tiles over at most 2 CTAs per
+    SM, so every CTA takes three or four tiles in turn: the tile kernel's
+    pipeline stages alternate and hand over), d = 64, both precisions, every
+    vertex against the oracle under its precision's bar."""
+    from paper_2011_03479_gb300 import inputs
+    rp, ci = inputs.barabasi_albert(120000, 8, seed=3102)
+    n = len(rp) - 1
+    x = (np.random.default_rng(7 + precision).normal(size=(n, 64)) * 0.7).astype(np.float32)
+    r = _run(B, O, rp, ci, 64, x, 0.7, 9, block_partners=64, precision=precision)
+    ref = r["ref"]
+    np.testing.assert_array_equal(r["samples"], _expected_block_samples(rp, ci, ref["partners"]))
+    assert r["stats"]["used"] == ref["accepted"]
+    if precision == 1:
+        e_delta, e_z, e_x = _bf16_errors(r)
+        print(f"BA 120k bf16 tiles: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
+        assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
+    else:
+        e_delta = _err_rows(r["delta"], ref["delta"], ref["abs_terms"])
+        print(f"BA 120k fp32 tiles: delta {e_delta.max():.2e}")
+        assert e_delta.max() <= TOL32
+        assert _err_rows(r["z"], ref["z"]).max() <= TOL32
+        assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
+
+
 def test_ba_fp32_tiles_parity(B, O, ba_20k):
     """The FP32 tiles on the Barabasi-Albert graph (n = 20,000: 157 tiles, the
     last one ragged, hubs of high degree), d = 64, within the FP32 bar."""
