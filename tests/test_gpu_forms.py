@@ -159,27 +159,38 @@ def test_ba_bf16_tiles_parity(B, O, ba_20k):
     assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_ba_tiles_several_per_cta(B, O, precision):
+@pytest.fixture(scope="module")
+def ba_120k():
+    from paper_2011_03479_gb300 import inputs
+    return inputs.barabasi_albert(120000, 8, seed=3102)
+
+
+@pytest.mark.parametrize("precision,d,sigma", [(1, 64, 0.7), (0, 64, 0.7), (0, 32, 0.7)],
+                         ids=["bf16-d64", "fp32-d64", "fp32-d32"])
+def test_ba_tiles_several_per_cta(B, O, ba_120k, precision, d, sigma):
     """Barabasi-Albert graph, n = 120,000 (938 tiles over at most 2 CTAs per
     SM, so every CTA takes three or four tiles in turn: the tile kernel's
-    pipeline stages alternate and hand over), d = 64, both precisions, every
-    vertex against the oracle under its precision's bar."""
-    from paper_2011_03479_gb300 import inputs
-    rp, ci = inputs.barabasi_albert(120000, 8, seed=3102)
+    pipeline stages alternate and hand over), both precisions, every vertex
+    against the oracle under its precision's bar.  (BF16 rows at d = 16 on
+    this graph move a step by up to 1.6e-2 at sigma = 0.7 and 4e-2 at
+    sigma = 2 in the worst of the 120,000 vertices, the same before and after
+    the tile pipeline: with 16 coordinates the Gram distances of BF16 rows
+    average fewer roundings; the d = 16 and d = 32 BF16 tiles are held to
+    the bar on the 1,000-vertex graph.)"""
+    rp, ci = ba_120k
     n = len(rp) - 1
-    x = (np.random.default_rng(7 + precision).normal(size=(n, 64)) * 0.7).astype(np.float32)
-    r = _run(B, O, rp, ci, 64, x, 0.7, 9, block_partners=64, precision=precision)
+    x = (np.random.default_rng(7 + precision + d).normal(size=(n, d)) * 0.7).astype(np.float32)
+    r = _run(B, O, rp, ci, d, x, sigma, 9, block_partners=64, precision=precision)
     ref = r["ref"]
     np.testing.assert_array_equal(r["samples"], _expected_block_samples(rp, ci, ref["partners"]))
     assert r["stats"]["used"] == ref["accepted"]
     if precision == 1:
         e_delta, e_z, e_x = _bf16_errors(r)
-        print(f"BA 120k bf16 tiles: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
+        print(f"BA 120k bf16 tiles d={d}: delta {e_delta.max():.2e} z {e_z.max():.2e} step {e_x.max():.2e}")
         assert e_delta.max() <= TOL16 and e_z.max() <= TOL16 and e_x.max() <= TOL16
     else:
         e_delta = _err_rows(r["delta"], ref["delta"], ref["abs_terms"])
-        print(f"BA 120k fp32 tiles: delta {e_delta.max():.2e}")
+        print(f"BA 120k fp32 tiles d={d}: delta {e_delta.max():.2e}")
         assert e_delta.max() <= TOL32
         assert _err_rows(r["z"], ref["z"]).max() <= TOL32
         assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
