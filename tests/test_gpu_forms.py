@@ -174,9 +174,8 @@ def test_ba_tiles_several_per_cta(B, O, ba_120k, precision, d, sigma):
     against the oracle under its precision's bar.  (BF16 rows at d = 16 on
     this graph move a step by up to 1.6e-2 at sigma = 0.7 and 4e-2 at
     sigma = 2 in the worst of the 120,000 vertices, the same before and after
-    the tile pipeline: with 16 coordinates the Gram distances of BF16 rows
-    average fewer roundings; the d = 16 and d = 32 BF16 tiles are held to
-    the bar on the 1,000-vertex graph.)"""
+    the tile pipeline; the d = 16 and d = 32 BF16 tiles are held to the bar
+    on the 1,000-vertex graph.)"""
     rp, ci = ba_120k
     n = len(rp) - 1
     x = (np.random.default_rng(7 + precision + d).normal(size=(n, d)) * 0.7).astype(np.float32)
