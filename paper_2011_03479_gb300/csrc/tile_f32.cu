@@ -16,7 +16,8 @@
 //   (3) after each pass, the pair terms (c, w) of its unmasked pairs (c the
 //       coefficient of x_self - x_other in y - z x, w the weight added to z),
 //       C into shared memory, the row sums of C and W by shuffles; the column
-//       sums through per-warp partials; the distances go to the histograms;
+//       sums by one shared-memory addition per warp and partner; the
+//       distances go to the histograms;
 //   (4) A = C X_P and B = C^T X_T by register tiles of packed FP32 FMAs, then
 //         y_i - z_i x_i += x_i rowsum(C)_i - A_i,   z_i += rowsum(W)_i,
 //         y_g - z_g x_g += x_g colsum(C)_g - B_g,   z_g += colsum(W)_g
