@@ -1410,62 +1410,74 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const EpochArgs a) {
         const int per_pass = (blockDim.x >> 5) * vpw;
         for (int c = vblk; c < a.n_vchunks; c += n_vblk) {
             const int4 ch = __ldg(a.vchunks + c);
-            for (int vb = (threadIdx.x >> 5) * vpw; vb < ch.y; vb += per_pass) {
-                const bool live = vb + sub < ch.y;
-                const int v = ch.x + vb + sub;
-                float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v * a.acc_stride);
-                float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v * a.d);
-                // the sums and the position are loaded with z, not after it (z < z_min is rare), so
-                // that all of a vertex's loads are in flight at once
-                float4 dv[2], xo[2];
+            // two batches of the warp's vertices per pass: all their loads
+            // are in flight before either batch is updated
+            for (int vb0 = (threadIdx.x >> 5) * vpw; vb0 < ch.y; vb0 += 2 * per_pass) {
+                float4 dv[2][2], xo[2][2];
+                float z[2];
+                bool live[2];
+                int v[2];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int q = ql + L * r;
-                    dv[r] = xo[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if (live && q < nq) {
-                        dv[r] = row[q];
-                        xo[r] = xv[q];
-                    }
-                }
-                const float z = live ? a.acc[(size_t)v * a.acc_stride + a.d] : 0.0f;
-                const bool upd = live && z >= a.z_min;
-                float4 xn[2];
-                bool finite = true;
-                if (upd) {
-                    const float inv_z = 1.0f / z;
+                for (int u = 0; u < 2; ++u) {
+                    const int vb = vb0 + u * per_pass;
+                    live[u] = vb + sub < ch.y;
+                    v[u] = ch.x + vb + sub;
+                    const float4* row = reinterpret_cast<const float4*>(a.acc + (size_t)v[u] * a.acc_stride);
+                    const float4* xv = reinterpret_cast<const float4*>(a.x + (size_t)v[u] * a.d);
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
                         const int q = ql + L * r;
-                        if (q < nq) {
-                            xn[r] = make_float4(fmaf(dv[r].x, inv_z, xo[r].x), fmaf(dv[r].y, inv_z, xo[r].y),
-                                                fmaf(dv[r].z, inv_z, xo[r].z), fmaf(dv[r].w, inv_z, xo[r].w));
-                            finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
-                                     isfinite(xn[r].w);
+                        dv[u][r] = xo[u][r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (live[u] && q < nq) {
+                            dv[u][r] = row[q];
+                            xo[u][r] = xv[q];
                         }
                     }
+                    z[u] = live[u] ? a.acc[(size_t)v[u] * a.acc_stride + a.d] : 0.0f;
                 }
-                const bool all_finite = (__ballot_sync(kFull, !finite) & group) == 0u;
-                if (upd) {
-                    if (all_finite) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float4* row = reinterpret_cast<float4*>(a.acc + (size_t)v[u] * a.acc_stride);
+                    float4* xv = reinterpret_cast<float4*>(a.x + (size_t)v[u] * a.d);
+                    const bool upd = live[u] && z[u] >= a.z_min;
+                    float4 xn[2];
+                    bool finite = true;
+                    if (upd) {
+                        const float inv_z = 1.0f / z[u];
 #pragma unroll
                         for (int r = 0; r < 2; ++r) {
                             const int q = ql + L * r;
                             if (q < nq) {
-                                xv[q] = xn[r];
-                                if (a.xb) {
-                                    __nv_bfloat162* b =
-                                        reinterpret_cast<__nv_bfloat162*>(a.xb + (size_t)v * a.d + 4 * q);
-                                    b[0] = __floats2bfloat162_rn(xn[r].x, xn[r].y);
-                                    b[1] = __floats2bfloat162_rn(xn[r].z, xn[r].w);
-                                }
+                                xn[r] = make_float4(fmaf(dv[u][r].x, inv_z, xo[u][r].x), fmaf(dv[u][r].y, inv_z, xo[u][r].y),
+                                                    fmaf(dv[u][r].z, inv_z, xo[u][r].z), fmaf(dv[u][r].w, inv_z, xo[u][r].w));
+                                finite = finite && isfinite(xn[r].x) && isfinite(xn[r].y) && isfinite(xn[r].z) &&
+                                         isfinite(xn[r].w);
                             }
                         }
-                    } else if (ql == 0) {
-                        atomicCAS(&a.ps->status, 0, -6 /* GEMPE_E_NUMERIC */);
                     }
+                    const bool all_finite = (__ballot_sync(kFull, !finite) & group) == 0u;
+                    if (upd) {
+                        if (all_finite) {
+#pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                const int q = ql + L * r;
+                                if (q < nq) {
+                                    xv[q] = xn[r];
+                                    if (a.xb) {
+                                        __nv_bfloat162* bp =
+                                            reinterpret_cast<__nv_bfloat162*>(a.xb + (size_t)v[u] * a.d + 4 * q);
+                                        bp[0] = __floats2bfloat162_rn(xn[r].x, xn[r].y);
+                                        bp[1] = __floats2bfloat162_rn(xn[r].z, xn[r].w);
+                                    }
+                                }
+                            }
+                        } else if (ql == 0) {
+                            atomicCAS(&a.ps->status, 0, -6 /* GEMPE_E_NUMERIC */);
+                        }
+                    }
+                    if (live[u])
+                        for (int q = ql; q < sq; q += L) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 }
-                if (live)
-                    for (int q = ql; q < sq; q += L) row[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
         return;
