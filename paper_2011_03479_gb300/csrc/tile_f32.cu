@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kF32Threads, D <= 64 ? 2 : 1) k_tile_f32(const
                 for (int r = 0; r < 8; ++r)
 #pragma unroll
                     for (int e = 0; e < CK / 2; ++e) A2[r][e] = 0ull;
-#pragma unroll 2
+#pragma unroll 8
                 for (int pc = 0; pc < kBlockP / 4; ++pc) {
                     f2 xr[4][CK / 2];
 #pragma unroll
