@@ -13,6 +13,16 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
+def bf16_round(x):
+    """float32 values rounded to the nearest BF16 value (8 significant bits,
+    ties to even), returned as float32: the rounding the BF16 form applies to
+    the positions its pair arithmetic reads."""
+    import numpy as np
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(x))
+
+
 def gpu_available() -> bool:
     try:
         import torch

@@ -2,17 +2,20 @@
 
 Block sampling: partners and masks bit-exact; the FP32 form within 1e-4 per
 step like the per-vertex form.  BF16 form: positions feed the pair
-arithmetic in BF16 (8-bit mantissa, relative rounding 2^-9 per coordinate),
-FP32 sums, compared with the FP64 oracle on the FP32 master positions at
-1e-2 per step: y_i - z_i x_i and the step x_new_i - x_i = (y_i - z_i x_i)/z_i
-each within 1e-2 of their own size, floored at 3e-2 of the size of the
-vertex's pair terms (A_i, resp. A_i / z_i) where those terms cancel, and
-z_i within 1e-2.
+arithmetic in BF16 (8 significant bits, relative rounding at most 2^-8 per
+coordinate), FP32 sums.  Two comparisons:
+- with the FP64 oracle on the FP32 master positions at 1e-2 per step:
+  y_i - z_i x_i and the step x_new_i - x_i = (y_i - z_i x_i)/z_i each within
+  1e-2 of their own size, floored at 3e-2 of the size of the vertex's pair
+  terms (A_i, resp. A_i / z_i) where those terms cancel, and z_i within 1e-2;
+- with the FP64 oracle on the BF16-rounded positions, which leaves the
+  kernels' own arithmetic: the FP32 bar, plus at most 2^-8 of every tile
+  term for the BF16 rounding of the tiles' coefficients.
 """
 import numpy as np
 import pytest
 
-from conftest import gpu_available
+from conftest import bf16_round, gpu_available
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
@@ -51,7 +54,9 @@ def _err_rows(got, ref, abs_terms=None, floor_frac=1e-2):
     return np.linalg.norm(got - ref, axis=1) / scale
 
 
-def _run(B, O, rp, ci, d, x, sigma, epoch, shape=None, **kw):
+def _run(B, O, rp, ci, d, x, sigma, epoch, shape=None, ref_x=None, **kw):
+    """One epoch on the GPU from positions x and the oracle's epoch from ref_x
+    (default x) with the same graph, seed, state and parameters."""
     p = B.gempe_default_params(**kw)
     with B.gempe_create(rp, ci, d, p) as ctx:
         if shape is not None:
@@ -64,7 +69,8 @@ def _run(B, O, rp, ci, d, x, sigma, epoch, shape=None, **kw):
         B.gempe_update(ctx)
         xn = B.gempe_positions(ctx)
         stats = B.gempe_stats(ctx)
-    ref = O.epoch(rp, ci, x.astype(np.float64), sigma, epoch, p.seed, p.neg_per_vertex,
+    xr = x if ref_x is None else ref_x
+    ref = O.epoch(rp, ci, xr.astype(np.float64), sigma, epoch, p.seed, p.neg_per_vertex,
                   block_partners=p.block_partners, tile_vertices=128, hist_bins=p.hist_bins,
                   hist_max=p.hist_max, symmetric=p.symmetric_neg)
     return dict(samples=samples, delta=delta, z=z, he=he, hn=hn, xn=xn, ref=ref, p=p, stats=stats, x0=x)
@@ -171,11 +177,12 @@ def test_ba_tiles_several_per_cta(B, O, ba_120k, precision, d, sigma):
     """Barabasi-Albert graph, n = 120,000 (938 tiles over at most 2 CTAs per
     SM, so every CTA takes three or four tiles in turn: the tile kernel's
     pipeline stages alternate and hand over), both precisions, every vertex
-    against the oracle under its precision's bar.  (BF16 rows at d = 16 on
-    this graph move a step by up to 1.6e-2 at sigma = 0.7 and 4e-2 at
-    sigma = 2 in the worst of the 120,000 vertices, the same before and after
-    the tile pipeline; the d = 16 and d = 32 BF16 tiles are held to the bar
-    on the 1,000-vertex graph.)"""
+    against the oracle under its precision's bar.  (At d = 16 the rounding of
+    the positions to BF16 alone moves the worst of the 120,000 steps by
+    1.7e-2 at sigma = 0.7 and 4.2e-2 at sigma = 2, past the 1e-2 bar: the
+    d = 16 BF16 tiles are held against the oracle on the rounded positions in
+    test_ba_bf16_on_rounded_positions, and to the plain bar on the
+    1,000-vertex graph.)"""
     rp, ci = ba_120k
     n = len(rp) - 1
     x = (np.random.default_rng(7 + precision + d).normal(size=(n, d)) * 0.7).astype(np.float32)
@@ -193,6 +200,70 @@ def test_ba_tiles_several_per_cta(B, O, ba_120k, precision, d, sigma):
         assert e_delta.max() <= TOL32
         assert _err_rows(r["z"], ref["z"]).max() <= TOL32
         assert _err_rows(r["xn"], ref["x_new"]).max() <= TOL32
+
+
+# BF16 unit roundoff: 8 significant bits, round to nearest even
+U16 = 2.0 ** -8
+
+
+def _rounded_bars(r, xb, tiles):
+    """Per-vertex errors of a BF16-form epoch against the oracle's FP64 epoch
+    on the BF16-rounded positions xb, and their bars.  With the positions the
+    pair arithmetic reads made equal, what is left is the kernels' own
+    arithmetic: FP32 terms and sums (the FP32 bar: 1e-4 of a sum, floored at
+    1e-2 of the size A_i of the vertex's pair terms) and, in the tensor-core
+    tiles (tiles=True), the rounding of every non-edge coefficient c and
+    weight w to BF16 before the products, at most U16 of each term: at most
+    U16 * A_i in y_i - z_i x_i and U16 * z_i in z_i.  The step
+    x_new - x = Delta/z then differs by at most |dDelta|/z + |step| |dz|/z,
+    plus one FP32 rounding of x + step per coordinate."""
+    ref = r["ref"]
+    a_i, z_ref = ref["abs_terms"], ref["z"]
+    u = U16 if tiles else 0.0
+    d_gpu = np.asarray(r["delta"], np.float64)
+    z_gpu = np.asarray(r["z"], np.float64)
+    err_d = np.linalg.norm(d_gpu - ref["delta"], axis=1)
+    bar_d = u * a_i + TOL32 * np.maximum(np.linalg.norm(ref["delta"], axis=1), 1e-2 * a_i)
+    err_z = np.abs(z_gpu - z_ref)
+    bar_z = (u + TOL32) * z_ref
+    step_gpu = r["xn"].astype(np.float64) - r["x0"].astype(np.float64)
+    step_ref = ref["x_new"] - xb.astype(np.float64)
+    err_x = np.linalg.norm(step_gpu - step_ref, axis=1)
+    bar_x = (bar_d + np.linalg.norm(step_ref, axis=1) * bar_z) / z_gpu + 2.0 ** -22 * np.linalg.norm(
+        r["xn"].astype(np.float64), axis=1)
+    return (err_d, bar_d), (err_z, bar_z), (err_x, bar_x)
+
+
+@pytest.mark.parametrize("d,sigma,block", [(16, 0.7, True), (16, 2.0, True), (32, 0.7, True), (64, 0.7, True),
+                                           (16, 2.0, False), (64, 0.7, False)],
+                         ids=["tiles-d16", "tiles-d16-sigma2", "tiles-d32", "tiles-d64", "sweep-d16-sigma2",
+                              "sweep-d64"])
+def test_ba_bf16_on_rounded_positions(B, O, ba_120k, d, sigma, block):
+    """The BF16 form against the oracle's FP64 epoch on the same positions
+    rounded to BF16 (the 120,000-vertex BA graph, every vertex): the error
+    that rounding the positions causes is the form's own (at d = 16 it moves
+    the worst vertex's step by up to 1.7e-2 at sigma = 0.7 and 4.2e-2 at
+    sigma = 2 in the oracle alone), and what remains is the kernels'
+    arithmetic, held to its derived bar.  Without tiles (k non-edges per
+    vertex, the BF16 pair sweep) that is the FP32 bar itself."""
+    rp, ci = ba_120k
+    n = len(rp) - 1
+    x = (np.random.default_rng(8 + d).normal(size=(n, d)) * 0.7).astype(np.float32)
+    xb = bf16_round(x)
+    kw = dict(block_partners=64) if block else dict(neg_per_vertex=5)
+    r = _run(B, O, rp, ci, d, x, sigma, 9, ref_x=xb, precision=1, **kw)
+    ref = r["ref"]
+    if block:
+        np.testing.assert_array_equal(r["samples"], _expected_block_samples(rp, ci, ref["partners"]))
+    else:
+        np.testing.assert_array_equal(r["samples"], ref["samples"])
+    assert r["stats"]["used"] == ref["accepted"]
+    (ed, bd), (ez, bz), (ex, bx) = _rounded_bars(r, xb, block)
+    a_i = ref["abs_terms"]
+    print(f"BA 120k bf16 {'tiles' if block else 'sweep'} d={d} sigma={sigma} against the rounded-input oracle: "
+          f"delta {np.max(ed / np.maximum(a_i, 1e-300)):.2e} A_i, {np.max(ed / bd):.2f} of its bar, "
+          f"z {np.max(ez / ref['z']):.2e} relative, step {np.max(ex / bx):.2f} of its bar")
+    assert (ed <= bd).all() and (ez <= bz).all() and (ex <= bx).all()
 
 
 def test_ba_fp32_tiles_parity(B, O, ba_20k):
