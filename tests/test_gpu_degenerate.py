@@ -1,0 +1,143 @@
+"""GPU parity on the method's degenerate inputs, in every sampling form.
+
+- a graph without edges (only sampled non-edges move the vertices; in the
+  per-slot policy nothing moves at all and both histograms stay empty);
+- the smallest graph, two vertices and one edge (in block sampling every
+  partner of the one tile is the anchor itself or its neighbour: all 64
+  pairs of each row masked);
+- a star whose centre is the only vertex of the last tile (n = 129): the
+  centre is adjacent to every other vertex, so each of its draws is
+  rejected until the sample is dropped, and every partner of its one-vertex
+  tile is masked.
+
+Each epoch is compared with the oracle's: sampled pairs bit-exact, per-step
+FP32 results under the FP32 bar (1e-4, the cancellation floor at 1e-2 of the
+size A_i of a vertex's pair terms), the BF16 form against the oracle run on
+the BF16-rounded positions under the bar its own roundings allow (2^-8 of
+each tile term), and the refitted slope against the oracle's fit of the same
+histograms (on separable histograms, where any slope with a negligible
+entropy minimises it, by the entropy at the slope).
+"""
+import numpy as np
+import pytest
+
+from conftest import bf16_round, gpu_available
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL = 1e-4
+U16 = 2.0 ** -8   # BF16 unit roundoff
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2011_03479_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _csr(rows):
+    rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    ci = np.array([j for r in rows for j in r], dtype=np.int32)
+    return rp, ci
+
+
+GRAPHS = {
+    "edgeless": _csr([[] for _ in range(300)]),
+    "one-edge": _csr([[1], [0]]),
+    "star-lone-tile": _csr([[128] for _ in range(128)] + [list(range(128))]),
+}
+
+FORMS = {
+    "vertex-d2": (2, dict(neg_per_vertex=5)),
+    "vertex-d16": (16, dict(neg_per_vertex=5)),
+    "slot-d2": (2, dict(sampling=1)),
+    "slot-d16": (16, dict(sampling=1)),
+    "block-fp32-d16": (16, dict(block_partners=64)),
+    "block-fp32-d64": (64, dict(block_partners=64)),
+    "block-bf16-d16": (16, dict(block_partners=64, precision=1)),
+    "block-bf16-d64": (64, dict(block_partners=64, precision=1)),
+}
+
+
+def _expected_block_samples(rp, ci, parts):
+    n = len(rp) - 1
+    out = np.empty((n, parts.shape[1]), dtype=np.int32)
+    for i in range(n):
+        row = set(ci[rp[i]:rp[i + 1]].tolist())
+        out[i] = [(-1 if (g == i or g in row) else g) for g in parts[i // 128].tolist()]
+    return out
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("graph", list(GRAPHS))
+def test_degenerate_graph_epoch(B, O, graph, form):
+    rp, ci = GRAPHS[graph]
+    d, kw = FORMS[form]
+    n = len(rp) - 1
+    p = B.gempe_default_params(**kw)
+    x = (np.random.default_rng(n + d).normal(size=(n, d)) * 0.9).astype(np.float32)
+    bf16 = p.precision == 1
+    xr = bf16_round(x) if bf16 else x
+    with B.gempe_create(rp, ci, d, p) as ctx:
+        B.gempe_set_positions(ctx, x)
+        B.gempe_set_state(ctx, 0.8, 3)
+        samples = B.gempe_sweep(ctx, record_samples=True)
+        delta, z = B.gempe_accumulators(ctx)
+        he, hn = B.gempe_histograms(ctx, p.hist_bins)
+        B.gempe_update(ctx)
+        xn = B.gempe_positions(ctx)
+        sigma, _ = B.gempe_get_state(ctx)
+        stats = B.gempe_stats(ctx)
+    ref = O.epoch(rp, ci, xr.astype(np.float64), 0.8, 3, p.seed, p.neg_per_vertex, mu=p.mu,
+                  max_retries=p.max_retries, symmetric=p.symmetric_neg, w_formula=p.w_formula,
+                  clamp_neg_d=p.clamp_neg_d, z_min=p.z_min, hist_bins=p.hist_bins, hist_max=p.hist_max,
+                  block_partners=p.block_partners, tile_vertices=128, per_slot=p.sampling)
+    # the sampled pairs
+    if p.block_partners:
+        np.testing.assert_array_equal(samples, _expected_block_samples(rp, ci, ref["partners"]))
+    else:
+        np.testing.assert_array_equal(samples, ref["samples"])
+    assert stats["used"] == ref["accepted"]
+    # per-step sums, weights and positions
+    a_i, zr = ref["abs_terms"], ref["z"]
+    u = U16 if bf16 else 0.0
+    err_d = np.linalg.norm(np.asarray(delta, np.float64) - ref["delta"], axis=1)
+    bar_d = u * a_i + TOL * np.maximum(np.linalg.norm(ref["delta"], axis=1), 1e-2 * a_i)
+    assert (err_d <= bar_d).all(), np.max(err_d - bar_d)
+    err_z = np.abs(np.asarray(z, np.float64) - zr)
+    assert (err_z <= (u + TOL) * zr).all(), np.max(err_z / np.maximum(zr, 1e-300))
+    moved = zr >= p.z_min
+    assert np.array_equal(xn[~moved], x[~moved])   # z below z_min: the vertex stays
+    step = xn[moved].astype(np.float64) - x[moved].astype(np.float64)
+    step_ref = ref["x_new"][moved] - xr[moved].astype(np.float64)
+    zg = np.asarray(z, np.float64)[moved]
+    bar_x = (bar_d[moved] + np.linalg.norm(step_ref, axis=1) * (u + TOL) * zr[moved]) / zg \
+        + 2.0 ** -22 * np.linalg.norm(xn[moved].astype(np.float64), axis=1)
+    assert (np.linalg.norm(step - step_ref, axis=1) <= bar_x).all()
+    # histograms and the slope refitted from them
+    assert he.sum() == len(ci) // 2
+    assert hn.sum() == pytest.approx(ref["hist_n"].sum(), rel=1e-5, abs=1e-3)
+    he64, hn64 = he.astype(np.float64), hn.astype(np.float64)
+    s_ref = O.sigma_fit(he64, hn64)
+    pe = lambda s: O.hist_pe(he64, hn64, p.hist_max, p.mu, s)   # noqa: E731
+    if pe(s_ref) <= 1e-12 * pe(1e3):
+        # separable histograms (every edge below mu, every non-edge above it):
+        # the entropy falls towards 0 as sigma -> 0 and every sigma at which it
+        # has become negligible is a minimiser; the FP64 bisection stops where
+        # its terms underflow, the FP32 search where its own do
+        assert pe(sigma) <= 1e-12 * pe(1e3)
+    else:
+        assert sigma == pytest.approx(s_ref, rel=TOL)
+    if graph == "edgeless" and p.sampling == 1:
+        assert not moved.any() and he.sum() == 0 and hn.sum() == 0 and sigma == pytest.approx(1e3)
+    print(f"{graph} {form}: delta {np.max(err_d / np.maximum(bar_d, 1e-300)):.2f} of its bar, "
+          f"sigma {sigma:.4g}, moved {int(moved.sum())} of {n}")
