@@ -135,7 +135,8 @@ typedef struct gempe_ctx gempe_ctx;
  * custom allocator. */
 void gempe_default_params(gempe_params* p);
 
-/* Check a host CSR graph on the host alone: row_ptr[0] = 0 and
+/* Check that a host CSR array describes the undirected simple graph of
+ * Sec. II.A, on the host alone: row_ptr[0] = 0 and
  * non-decreasing, column indices in range, no self loops, rows strictly
  * increasing (no duplicates), and symmetric (every (i, j) has its (j, i)).
  * GEMPE_OK or GEMPE_E_INVALID_GRAPH with the lowest offending row in
@@ -154,13 +155,14 @@ gempe_status gempe_validate_csr(const int32_t* row_ptr, const int32_t* col_idx, 
 gempe_status gempe_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t d,
                           const gempe_params* p, void* cuda_stream, gempe_ctx** out);
 
-/* Same as gempe_create with the CSR arrays in device memory (copied). */
+/* Same as gempe_create (Sec. II.A) with the CSR arrays in device memory
+ * (copied). */
 gempe_status gempe_create_device(const int32_t* d_row_ptr, const int32_t* d_col_idx, int32_t n,
                                  int64_t nnz, int32_t d, const gempe_params* p, void* cuda_stream,
                                  gempe_ctx** out);
 
 /* Release the context and all device memory it allocated (waits for its
- * queued work first).  NULL is ignored. */
+ * queued work first; the paper has no counterpart).  NULL is ignored. */
 void gempe_destroy(gempe_ctx* ctx);
 
 /* Run `iters` full epochs (Fig. 4): sweep + position update + sigma refit.
@@ -194,7 +196,8 @@ gempe_status gempe_update(gempe_ctx* ctx);
  * when no epoch was recorded.  Synchronises on the last event when out_ms3 is set. */
 gempe_status gempe_kernel_times(gempe_ctx* ctx, int32_t enable, float* out_ms3);
 
-/* Copy the positions to host float[n*d] (synchronises).  count must be n*d. */
+/* Copy the positions x_i (Sec. II.A, updated by Fig. 4's loop) to host
+ * float[n*d] (synchronises).  count must be n*d. */
 gempe_status gempe_positions(gempe_ctx* ctx, float* host_out, size_t count);
 
 /* Borrow a device pointer to the FP32 positions [n][d]; valid until the next
@@ -204,7 +207,8 @@ gempe_status gempe_positions_device(gempe_ctx* ctx, const float** d_view);
 /* Overwrite the positions from host float[n*d] (count must be n*d). */
 gempe_status gempe_set_positions(gempe_ctx* ctx, const float* host_x, size_t count);
 
-/* Set / read sigma and the epoch counter (the epoch keys the sampler). */
+/* Set / read sigma (the sigmoid slope of Sec. II.B, refitted by Sec. III.F)
+ * and the counter of Fig. 4's epoch loop (the epoch keys the sampler). */
 gempe_status gempe_set_state(gempe_ctx* ctx, float sigma, int32_t epoch);
 gempe_status gempe_get_state(gempe_ctx* ctx, float* sigma, int32_t* epoch);
 
@@ -350,7 +354,8 @@ gempe_status gempe_test_tile_wait(int32_t poll_limit, int32_t* out_status, int32
  * after the context's queued work.  Synchronises. */
 gempe_status gempe_stats(gempe_ctx* ctx, gempe_stats_t* out);
 
-/* Launch shape of the context's pair sweep (what the autotuner chooses):
+/* Launch shape of the context's pair sweep (what the autotuner chooses; a
+ * GPU launch parameter with no counterpart in the paper):
  * shape5 = {unit pair budget of a packed unit (64 or 128, d <= 4), CSR
  * slots per work unit (8..1024, the per-unit kernel), lanes per pair (d >= 8:
  * d/8 or d/4; 0 = default), sweep CTAs per SM (0 = all that fit), kernel
@@ -393,11 +398,11 @@ typedef struct gempe_batch gempe_batch;
 gempe_status gempe_batch_create(int32_t n_graphs, const gempe_graph_desc* graphs, const gempe_params* p,
                                 void* cuda_stream, gempe_batch** out);
 void gempe_batch_destroy(gempe_batch* b);
-/* `iters` epochs of every graph, asynchronous on the batch stream. */
+/* `iters` epochs (Fig. 4) of every graph, asynchronous on the batch stream. */
 gempe_status gempe_batch_step(gempe_batch* b, int32_t iters);
 /* Positions of graph `graph` to host float[n*d] (synchronises). */
 gempe_status gempe_batch_positions(gempe_batch* b, int32_t graph, float* host_out, size_t count);
-/* Sampled predictive entropy of graph `graph` (as gempe_loss). */
+/* Sampled predictive entropy (Eq. 2) of graph `graph` (as gempe_loss). */
 gempe_status gempe_batch_loss(gempe_batch* b, int32_t graph, double* out_pe_bits, float* out_sigma);
 /* Statistics of graph `graph` (as gempe_stats).  Synchronises. */
 gempe_status gempe_batch_stats(gempe_batch* b, int32_t graph, gempe_stats_t* out);
