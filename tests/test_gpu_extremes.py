@@ -1,4 +1,7 @@
-"""GPU parity on the method's degenerate inputs, in every sampling form.
+"""GPU parity on the method's degenerate inputs and at the largest dimension,
+in every sampling form.
+
+Degenerate inputs:
 
 - a graph without edges (only sampled non-edges move the vertices; in the
   per-slot policy nothing moves at all and both histograms stay empty);
@@ -9,6 +12,11 @@
   centre is adjacent to every other vertex, so each of its draws is
   rejected until the sample is dropped, and every partner of its one-vertex
   tile is masked.
+
+The largest dimension, d = 256 (one lane group of 32 lanes per vertex), in
+the per-vertex, per-slot and block forms with FP32 and BF16 positions (the
+block samples go through the pair sweep there, as at d = 8 and, with BF16
+positions, at d = 128: those two are checked as well).
 
 Each epoch is compared with the oracle's: sampled pairs bit-exact, per-step
 FP32 results under the FP32 bar (1e-4, the cancellation floor at 1e-2 of the
@@ -77,11 +85,10 @@ def _expected_block_samples(rp, ci, parts):
     return out
 
 
-@pytest.mark.parametrize("form", list(FORMS))
-@pytest.mark.parametrize("graph", list(GRAPHS))
-def test_degenerate_graph_epoch(B, O, graph, form):
-    rp, ci = GRAPHS[graph]
-    d, kw = FORMS[form]
+def _epoch_against_oracle(B, O, rp, ci, d, kw, label):
+    """One epoch on the GPU and the oracle's from the same positions (rounded
+    to BF16 for the oracle in the BF16 form), checked under the bars above;
+    returns the per-vertex step mask (z_i >= z_min) and the slope."""
     n = len(rp) - 1
     p = B.gempe_default_params(**kw)
     x = (np.random.default_rng(n + d).normal(size=(n, d)) * 0.9).astype(np.float32)
@@ -109,7 +116,9 @@ def test_degenerate_graph_epoch(B, O, graph, form):
     assert stats["used"] == ref["accepted"]
     # per-step sums, weights and positions
     a_i, zr = ref["abs_terms"], ref["z"]
-    u = U16 if bf16 else 0.0
+    # the BF16 rounding of the coefficients happens only in the tensor-core
+    # tiles (d = 16, 32, 64); the pair sweep keeps them in FP32
+    u = U16 if bf16 and p.block_partners and d in (16, 32, 64) else 0.0
     err_d = np.linalg.norm(np.asarray(delta, np.float64) - ref["delta"], axis=1)
     bar_d = u * a_i + TOL * np.maximum(np.linalg.norm(ref["delta"], axis=1), 1e-2 * a_i)
     assert (err_d <= bar_d).all(), np.max(err_d - bar_d)
@@ -137,7 +146,39 @@ def test_degenerate_graph_epoch(B, O, graph, form):
         assert pe(sigma) <= 1e-12 * pe(1e3)
     else:
         assert sigma == pytest.approx(s_ref, rel=TOL)
-    if graph == "edgeless" and p.sampling == 1:
-        assert not moved.any() and he.sum() == 0 and hn.sum() == 0 and sigma == pytest.approx(1e3)
-    print(f"{graph} {form}: delta {np.max(err_d / np.maximum(bar_d, 1e-300)):.2f} of its bar, "
+    print(f"{label}: delta {np.max(err_d / np.maximum(bar_d, 1e-300)):.2f} of its bar, "
           f"sigma {sigma:.4g}, moved {int(moved.sum())} of {n}")
+    return dict(moved=moved, he=he, hn=hn, sigma=sigma)
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("graph", list(GRAPHS))
+def test_degenerate_graph_epoch(B, O, graph, form):
+    rp, ci = GRAPHS[graph]
+    d, kw = FORMS[form]
+    r = _epoch_against_oracle(B, O, rp, ci, d, kw, f"{graph} {form}")
+    if graph == "edgeless" and kw.get("sampling") == 1:
+        # no edges and no samples: nothing moves, both histograms stay empty
+        assert not r["moved"].any() and r["he"].sum() == 0 and r["hn"].sum() == 0
+        assert r["sigma"] == pytest.approx(1e3)
+
+
+WIDE = {
+    "vertex-fp32-d256": (256, dict(neg_per_vertex=5)),
+    "vertex-bf16-d256": (256, dict(neg_per_vertex=5, precision=1)),
+    "slot-fp32-d256": (256, dict(sampling=1)),
+    "block-fp32-d256": (256, dict(block_partners=64)),
+    "block-bf16-d256": (256, dict(block_partners=64, precision=1)),
+    "block-bf16-d128": (128, dict(block_partners=64, precision=1)),
+    "block-bf16-d8": (8, dict(block_partners=64, precision=1)),
+}
+
+
+@pytest.mark.parametrize("form", list(WIDE))
+def test_largest_dimension_and_sweep_block_forms(B, O, sbm_1000, form):
+    """d = 256 in every form, and the BF16 block samples that the pair sweep
+    evaluates (d = 8, 128, 256: no tensor-core tiles there, so the BF16 form
+    is FP32 arithmetic on the rounded positions and meets the FP32 bar
+    against the oracle on those positions)."""
+    d, kw = WIDE[form]
+    _epoch_against_oracle(B, O, sbm_1000["row_ptr"], sbm_1000["col_idx"], d, kw, f"sbm-1000 {form}")
