@@ -85,13 +85,15 @@ def _expected_block_samples(rp, ci, parts):
     return out
 
 
-def _epoch_against_oracle(B, O, rp, ci, d, kw, label):
-    """One epoch on the GPU and the oracle's from the same positions (rounded
-    to BF16 for the oracle in the BF16 form), checked under the bars above;
-    returns the per-vertex step mask (z_i >= z_min) and the slope."""
+def _epoch_against_oracle(B, O, rp, ci, d, kw, label, x=None):
+    """One epoch on the GPU and the oracle's from the same positions x
+    (default: normal, 0.9 per coordinate; rounded to BF16 for the oracle in
+    the BF16 form), checked under the bars above; returns the per-vertex step
+    mask (z_i >= z_min), the histograms, the slope and the oracle's epoch."""
     n = len(rp) - 1
     p = B.gempe_default_params(**kw)
-    x = (np.random.default_rng(n + d).normal(size=(n, d)) * 0.9).astype(np.float32)
+    if x is None:
+        x = (np.random.default_rng(n + d).normal(size=(n, d)) * 0.9).astype(np.float32)
     bf16 = p.precision == 1
     xr = bf16_round(x) if bf16 else x
     with B.gempe_create(rp, ci, d, p) as ctx:
@@ -148,7 +150,7 @@ def _epoch_against_oracle(B, O, rp, ci, d, kw, label):
         assert sigma == pytest.approx(s_ref, rel=TOL)
     print(f"{label}: delta {np.max(err_d / np.maximum(bar_d, 1e-300)):.2f} of its bar, "
           f"sigma {sigma:.4g}, moved {int(moved.sum())} of {n}")
-    return dict(moved=moved, he=he, hn=hn, sigma=sigma)
+    return dict(moved=moved, he=he, hn=hn, sigma=sigma, ref=ref, s_ref=s_ref)
 
 
 @pytest.mark.parametrize("form", list(FORMS))
@@ -182,3 +184,42 @@ def test_largest_dimension_and_sweep_block_forms(B, O, sbm_1000, form):
     against the oracle on those positions)."""
     d, kw = WIDE[form]
     _epoch_against_oracle(B, O, sbm_1000["row_ptr"], sbm_1000["col_idx"], d, kw, f"sbm-1000 {form}")
+
+
+CLUSTERED = {
+    "vertex-fp32-d64": (64, dict(neg_per_vertex=5)),
+    "vertex-bf16-d64": (64, dict(neg_per_vertex=5, precision=1)),
+    "slot-fp32-d64": (64, dict(sampling=1)),
+    "block-fp32-d16": (16, dict(block_partners=64)),
+    "block-fp32-d64": (64, dict(block_partners=64)),
+    "block-fp32-d128": (128, dict(block_partners=64)),
+    "block-bf16-d16": (16, dict(block_partners=64, precision=1)),
+    "block-bf16-d64": (64, dict(block_partners=64, precision=1)),
+    "block-fp32-d256": (256, dict(block_partners=64)),
+}
+
+
+@pytest.mark.parametrize("form", list(CLUSTERED))
+def test_clustered_positions(B, O, sbm_1000, form):
+    """Positions of an embedding that has found the SBM's four blocks: each
+    block around its own centre (centres about 3 apart, points about 0.8
+    from their block mates), so edges and the many intra-block non-edges lie
+    below mu = 1.5 and inter-block pairs above it.  Unlike spread random
+    positions at large d, whose pairs all sit far in the tails of the pair
+    terms (and in the histograms' last bin), these exercise the middle of
+    the Mills-ratio table on both sides of mu in the tile kernels and the
+    sweeps, and give histograms over hundreds of bins with a slope inside the
+    bracket: the edge histogram within a few rounding moves of the oracle's
+    and the slope within 1e-4."""
+    d, kw = CLUSTERED[form]
+    rp, ci = sbm_1000["row_ptr"], sbm_1000["col_idx"]
+    n = len(rp) - 1
+    rng = np.random.default_rng(500 + d)
+    centre = rng.normal(size=(4, d)) * (3.0 / np.sqrt(2 * d))
+    x = (centre[np.arange(n) // 250] + rng.normal(size=(n, d)) * (0.8 / np.sqrt(2 * d))).astype(np.float32)
+    r = _epoch_against_oracle(B, O, rp, ci, d, kw, f"sbm-1000 clustered {form}", x=x)
+    ref = r["ref"]
+    assert np.count_nonzero(r["he"]) > 50 and 0.1 < r["s_ref"] < 10.0
+    # a pair may land in a neighbouring bin when its FP32 distance rounds across a bin edge
+    assert np.abs(r["he"] - ref["hist_e"]).sum() <= 8
+    assert r["sigma"] == pytest.approx(r["s_ref"], rel=TOL)
