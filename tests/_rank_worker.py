@@ -108,3 +108,58 @@ def shard_epochs(rank, world, port, queue, form_name):
         queue.put((rank, ranges, eng.x, eng.sigma))
     finally:
         dist.destroy_process_group()
+
+
+class InjectedFailure(RuntimeError):
+    """The host-side failure a test plants in one rank's engine."""
+
+
+class FailingShard(OracleShard):
+    """An OracleShard whose sweep raises at epoch `fail_at` (a rank that
+    fails between two of the exchange's collectives)."""
+
+    def __init__(self, *args, fail_at, **kw):
+        super().__init__(*args, **kw)
+        self.fail_at = fail_at
+
+    def sweep(self):
+        if self.epoch == self.fail_at:
+            raise InjectedFailure(f"injected failure at epoch {self.epoch}")
+        super().sweep()
+
+
+def shard_peer_fails(rank, world, port, queue, timeout_s):
+    """Two ranks run the sharded exchange; rank 1's engine fails at its
+    second epoch and the rank leaves.  Each rank reports how its step ended:
+    rank 1 with the injected failure, rank 0 with the error its next
+    collective raises (a closed connection, or the process group's timeout)."""
+    import datetime
+    import time
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=timeout_s))
+    outcome = None
+    t0 = time.monotonic()
+    try:
+        import oracle
+        from paper_2011_03479_gb300 import inputs, shard
+        oracle.build()
+        w = inputs.sbm_1000()
+        rp, ci = w["row_ptr"], w["col_idx"]
+        lo, hi = shard.vertex_ranges(rp, world)[rank]
+        x0 = oracle.init_positions(len(rp) - 1, 2, 99).astype("float64")
+        eng = FailingShard(oracle, rp, ci, x0, 99, 5, lo, hi, {}, fail_at=1 if rank == 1 else -1)
+        try:
+            shard.ShardRank(eng).step(3)
+            outcome = ("completed", eng.epoch)
+        except InjectedFailure as e:
+            outcome = ("injected", eng.epoch, str(e))
+        except Exception as e:   # the collective that lost its peer
+            outcome = ("collective error", eng.epoch, type(e).__name__)
+    finally:
+        queue.put((rank, outcome, time.monotonic() - t0))
+        if outcome and outcome[0] != "collective error":
+            dist.destroy_process_group()

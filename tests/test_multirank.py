@@ -5,7 +5,8 @@ GPU, splits the batch's graphs and the served job stream over the ranks, and
 exchanges only the whole-job figures after the timed region: the slowest
 rank's time (MAX) and the sum of the ranks' pair-updates (SUM).  Under
 torchrun the reference arm runs on rank 0 only; other ranks exit 0 without
-work.
+work.  One graph split over vertex-range shards runs the product's exchange
+over gloo on an oracle-backed engine, also with one rank failing.
 """
 import json
 import multiprocessing as mp
@@ -160,3 +161,33 @@ def test_vertex_ranges_cover_and_balance():
             unit = 128 if block else 1
             biggest = max(int(work[i:i + unit].sum()) for i in range(0, n, unit))
             assert max(loads) - min(loads) <= 2 * biggest
+
+
+def test_sharded_graph_peer_failure_gloo_world_2():
+    """Failure detection on the host (no GPU involved): rank 1's engine raises
+    at its second epoch, between two epochs' collectives, and the rank
+    leaves.  Rank 0 must not wait for it forever: the all-reduce of its
+    second epoch ends with an error (gloo reports the closed connection, a
+    10 s process-group timeout bounds it otherwise), after its first epoch
+    completed."""
+    import _rank_worker
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker.shard_peer_fails, args=(r, 2, port, q, 10)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = dict((r, (out, secs)) for r, out, secs in (q.get(timeout=240) for _ in procs))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    (out1, _), (out0, secs0) = res[1], res[0]
+    assert out1[0] == "injected" and out1[1] == 1
+    assert out0[0] == "collective error" and out0[1] == 1, out0
+    assert secs0 < 120
