@@ -208,7 +208,7 @@ def test_clustered_positions(B, O, sbm_1000, form):
     positions at large d, whose pairs all sit far in the tails of the pair
     terms (and in the histograms' last bin), these exercise the middle of
     the Mills-ratio table on both sides of mu in the tile kernels and the
-    sweeps, and give histograms over hundreds of bins with a slope inside the
+    sweeps, and give histograms over 70 to 400 bins with a slope inside the
     bracket: the edge histogram within a few rounding moves of the oracle's
     and the slope within 1e-4."""
     d, kw = CLUSTERED[form]
